@@ -1,0 +1,323 @@
+"""CPU oracle of the per-frame hand-isolation path (arXiv 1907.04393).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline / reference arm may import this package.  The product
+path (``paper_1907_04393_gb300``) never imports it and shares no code with it.
+
+This module is a thin ctypes wrapper around ``hmi_oracle.c`` (plain C, single
+threaded), which it compiles with gcc on first use.  Every function below maps
+one-to-one onto a C function whose comment cites the passage of the paper it
+follows (Sec. 2 workflow, Sec. 3.1 mask building, Sec. 3.2 luminosity).
+
+Parity status: every stage is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, library routines (scipy.ndimage, colorsys) and brute force.  The
+readings of the paper's garbled or silent passages are pinned only against
+themselves ("parity unpinned" against the authors' system, whose code,
+thresholds and data are not available).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hmi_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile hmi_oracle.c into liboracle.so (gcc, -O2, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Pointer(ctypes.Structure):
+    _fields_ = [("valid", ctypes.c_int32), ("click", ctypes.c_int32),
+                ("x", ctypes.c_float), ("y", ctypes.c_float),
+                ("area", ctypes.c_uint32),
+                ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
+                ("x1", ctypes.c_int32), ("y1", ctypes.c_int32),
+                ("label", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_u8p = _P
+_I, _U32, _U64, _I64, _SZ = ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_size_t
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        sig = {
+            "orc_learn_stats": (None, [_P, _I, _I, _I, _P, _P, _P, _P]),
+            "orc_learn_meanstd": (None, [_P, _P, _I, _SZ, _P, _P]),
+            "orc_band_low": (_I64, [_U32, _U32, _I, _I, _I]),
+            "orc_band_high": (_I64, [_U32, _U32, _I, _I, _I]),
+            "orc_learn_band": (None, [_P, _P, _P, _P, _I, _SZ, _I, _I, _I, _P, _P]),
+            "orc_luma_sum": (_U64, [_P, _SZ]),
+            "orc_ref_luma": (_U64, [_P, _I, _SZ]),
+            "orc_gain": (_U32, [_U64, _U64, _U32, _U32]),
+            "orc_apply_gain": (None, [_P, _SZ, _U32, _P]),
+            "orc_hue": (_I, [_I, _I, _I]),
+            "orc_hue_map": (None, [_P, _SZ, _P]),
+            "orc_fg": (None, [_P, _P, _P, _SZ, _I, _I, _I, _P, _P, _P, _P]),
+            "orc_erode": (None, [_P, _I, _I, _P]),
+            "orc_dilate": (None, [_P, _I, _I, _P]),
+            "orc_morph": (None, [_P, _I, _I, _I, _I, _P]),
+            "orc_label": (_I, [_P, _I, _I, _P]),
+            "orc_pointer_from_labels": (None, [_P, _I, _I, _U32, _P]),
+            "orc_click_update": (None, [_P, _P, _P, _I, _I, _I, _P]),
+            "orc_process_frame": (None, [_P, _I, _I, _P, _P, _U64, _I, _I, _I, _I, _I,
+                                         _U32, _U32, _U32, _I, _I, _I, _P, _P, _P,
+                                         _P, _P, _P, _P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+# --------------------------------------------------------------------------- #
+# Default parameters (the same documented defaults as the library's).        #
+# --------------------------------------------------------------------------- #
+DEFAULTS = dict(gray_tol=15, hue_lo=1472, hue_hi=256, bg_margin=2, bg_k_num=5,
+                bg_k_den=2, open_iters=1, close_iters=1, gain_min_q16=32768,
+                gain_max_q16=131072, min_area=50, click_on_pct=80,
+                click_off_pct=90, click_window=30)
+
+
+def params(**over) -> dict:
+    p = dict(DEFAULTS)
+    unknown = set(over) - set(p)
+    if unknown:
+        raise KeyError(f"unknown oracle params {sorted(unknown)}")
+    p.update(over)
+    return p
+
+
+# --------------------------------------------------------------------------- #
+# Stage functions                                                            #
+# --------------------------------------------------------------------------- #
+def learn_stats(frames: np.ndarray):
+    """frames: (n, H, W, 3) uint8 -> (S, Q, vmin, vmax) shaped (H, W, 3)."""
+    frames = _u8(frames)
+    n, h, w, _ = frames.shape
+    S = np.empty((h, w, 3), np.uint32)
+    Q = np.empty((h, w, 3), np.uint32)
+    vmin = np.empty((h, w, 3), np.uint8)
+    vmax = np.empty((h, w, 3), np.uint8)
+    _load().orc_learn_stats(_ptr(frames), n, w, h, _ptr(S), _ptr(Q), _ptr(vmin), _ptr(vmax))
+    return S, Q, vmin, vmax
+
+
+def learn_meanstd(S: np.ndarray, Q: np.ndarray, n: int):
+    S = np.ascontiguousarray(S, np.uint32)
+    Q = np.ascontiguousarray(Q, np.uint32)
+    mean = np.empty(S.shape, np.float32)
+    std = np.empty(S.shape, np.float32)
+    _load().orc_learn_meanstd(_ptr(S), _ptr(Q), n, S.size, _ptr(mean), _ptr(std))
+    return mean, std
+
+
+def band_low(S: int, Q: int, n: int, kn: int, kd: int) -> int:
+    if kd < 1:
+        raise ValueError("kd must be >= 1")
+    return _load().orc_band_low(S, Q, n, kn, kd)
+
+
+def band_high(S: int, Q: int, n: int, kn: int, kd: int) -> int:
+    if kd < 1:
+        raise ValueError("kd must be >= 1")
+    return _load().orc_band_high(S, Q, n, kn, kd)
+
+
+def learn_band(S, Q, vmin, vmax, n, kn, kd, delta):
+    if kd < 1:
+        raise ValueError("kd must be >= 1")
+    S = np.ascontiguousarray(S, np.uint32)
+    Q = np.ascontiguousarray(Q, np.uint32)
+    vmin, vmax = _u8(vmin), _u8(vmax)
+    lo = np.empty(S.shape, np.uint8)
+    hi = np.empty(S.shape, np.uint8)
+    _load().orc_learn_band(_ptr(S), _ptr(Q), _ptr(vmin), _ptr(vmax), n, S.size, kn, kd,
+                           delta, _ptr(lo), _ptr(hi))
+    return lo, hi
+
+
+def luma_sum(frame: np.ndarray) -> int:
+    frame = _u8(frame)
+    return _load().orc_luma_sum(_ptr(frame), frame.size // 3)
+
+
+def ref_luma(frames: np.ndarray) -> int:
+    frames = _u8(frames)
+    n = frames.shape[0]
+    return _load().orc_ref_luma(_ptr(frames), n, frames[0].size // 3)
+
+
+def gain(sy: int, syref: int, gmin: int, gmax: int) -> int:
+    return _load().orc_gain(sy, syref, gmin, gmax)
+
+
+def apply_gain(frame: np.ndarray, g: int) -> np.ndarray:
+    frame = _u8(frame)
+    out = np.empty_like(frame)
+    _load().orc_apply_gain(_ptr(frame), frame.size, g, _ptr(out))
+    return out
+
+
+def hue(r: int, g: int, b: int) -> int:
+    return _load().orc_hue(int(r), int(g), int(b))
+
+
+def hue_map(c: np.ndarray) -> np.ndarray:
+    """Integer hue of every pixel of (..., 3) uint8, int16, -1 where undefined."""
+    c = _u8(c)
+    out = np.empty(c.shape[:-1], np.int16)
+    _load().orc_hue_map(_ptr(c), c.size // 3, _ptr(out))
+    return out
+
+
+def fg(c: np.ndarray, lo: np.ndarray, hi: np.ndarray, gray_tol: int, hue_lo: int, hue_hi: int):
+    """Gain-corrected frame (..., 3) -> (fg1, fg2, fg3, raw) shaped like c[..., 0]."""
+    c, lo, hi = _u8(c), _u8(lo), _u8(hi)
+    assert c.shape == lo.shape == hi.shape and c.shape[-1] == 3
+    shp = c.shape[:-1]
+    outs = [np.empty(shp, np.uint8) for _ in range(4)]
+    _load().orc_fg(_ptr(c), _ptr(lo), _ptr(hi), c.size // 3, gray_tol, hue_lo, hue_hi,
+                   *[_ptr(o) for o in outs])
+    return tuple(outs)
+
+
+def erode(m: np.ndarray) -> np.ndarray:
+    m = _u8(m)
+    out = np.empty_like(m)
+    h, w = m.shape
+    _load().orc_erode(_ptr(m), w, h, _ptr(out))
+    return out
+
+
+def dilate(m: np.ndarray) -> np.ndarray:
+    m = _u8(m)
+    out = np.empty_like(m)
+    h, w = m.shape
+    _load().orc_dilate(_ptr(m), w, h, _ptr(out))
+    return out
+
+
+def morph(m: np.ndarray, open_iters: int, close_iters: int) -> np.ndarray:
+    m = _u8(m)
+    out = np.empty_like(m)
+    h, w = m.shape
+    _load().orc_morph(_ptr(m), w, h, open_iters, close_iters, _ptr(out))
+    return out
+
+
+def label(m: np.ndarray):
+    """Binary mask (H, W) -> (labels int32 (H, W), component count)."""
+    m = _u8(m)
+    h, w = m.shape
+    lab = np.empty((h, w), np.int32)
+    n = _load().orc_label(_ptr(m), w, h, _ptr(lab))
+    return lab, n
+
+
+def pointer_from_labels(labels: np.ndarray, min_area: int) -> dict:
+    labels = np.ascontiguousarray(labels, np.int32)
+    h, w = labels.shape
+    p = Pointer()
+    _load().orc_pointer_from_labels(_ptr(labels), w, h, min_area, ctypes.byref(p))
+    return p.as_dict()
+
+
+class ClickState:
+    """Per-stream click state machine (history of the last `window` valid areas)."""
+
+    def __init__(self, window: int):
+        self.window = int(window)
+        self.click = ctypes.c_int32(0)
+        self.count = ctypes.c_int32(0)
+        self.hist = np.zeros(max(self.window, 1), np.uint32)
+
+    def update(self, ptr: dict, on_pct: int, off_pct: int) -> dict:
+        p = Pointer(**{k: ptr[k] for k, _ in Pointer._fields_})
+        _load().orc_click_update(ctypes.byref(self.click), _ptr(self.hist),
+                                 ctypes.byref(self.count), self.window, on_pct, off_pct,
+                                 ctypes.byref(p))
+        return p.as_dict()
+
+
+class OracleStream:
+    """The whole path for one camera stream: learn once, then process frames."""
+
+    def __init__(self, w: int, h: int, **over):
+        self.w, self.h = int(w), int(h)
+        self.p = params(**over)
+        self.learned = False
+        self.click = ClickState(self.p["click_window"])
+
+    def learn(self, frames: np.ndarray) -> None:
+        frames = _u8(frames)
+        assert frames.shape[1:] == (self.h, self.w, 3)
+        n = frames.shape[0]
+        S, Q, vmin, vmax = learn_stats(frames)
+        self.n = n
+        self.S, self.Q, self.vmin, self.vmax = S, Q, vmin, vmax
+        self.lo, self.hi = learn_band(S, Q, vmin, vmax, n, self.p["bg_k_num"],
+                                      self.p["bg_k_den"], self.p["bg_margin"])
+        self.syref = ref_luma(frames)
+        self.learned = True
+
+    def stats(self):
+        return learn_meanstd(self.S, self.Q, self.n)
+
+    def process(self, frame: np.ndarray, want_labels: bool = True):
+        """Returns (mask uint8 (H,W), labels int32 (H,W) or None, pointer dict, gain)."""
+        assert self.learned
+        frame = _u8(frame)
+        assert frame.shape == (self.h, self.w, 3)
+        p = self.p
+        mask = np.empty((self.h, self.w), np.uint8)
+        labels = np.empty((self.h, self.w), np.int32) if want_labels else None
+        ptr = Pointer()
+        g = ctypes.c_uint32(0)
+        c = self.click
+        _load().orc_process_frame(
+            _ptr(frame), self.w, self.h, _ptr(self.lo), _ptr(self.hi), self.syref,
+            p["gray_tol"], p["hue_lo"], p["hue_hi"], p["open_iters"], p["close_iters"],
+            p["gain_min_q16"], p["gain_max_q16"], p["min_area"], p["click_on_pct"],
+            p["click_off_pct"], c.window, ctypes.byref(c.click), _ptr(c.hist),
+            ctypes.byref(c.count), _ptr(mask), _ptr(labels), ctypes.byref(ptr),
+            ctypes.byref(g))
+        return mask, labels, ptr.as_dict(), g.value

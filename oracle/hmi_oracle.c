@@ -1,0 +1,478 @@
+/*
+ * hmi_oracle.c -- plain, slow, single-threaded CPU oracle of the per-frame
+ * hand-isolation path of Magoules & Zou, "GPU Accelerated Contactless Human
+ * Machine Interface for Driving Car" (arXiv 1907.04393).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load this library.  The product path (the
+ * CUDA library and its Python binding) never calls it and shares no code,
+ * header, table or helper with it.
+ *
+ * Every function states the passage of the paper it follows.  Where the paper
+ * is silent, garbled or self-contradictory, the reading taken is written next
+ * to the code as "Reading:".  All arithmetic on the per-pixel path is integer;
+ * the only floating point values are the background mean/std and the pointer
+ * centroid, each computed from exact integers with one correctly rounded IEEE
+ * operation per step (compile with -ffp-contract=off so that no FMA changes
+ * a rounding).
+ *
+ * Data layouts (all packed, no padding):
+ *   frame      : H*W*3 bytes, RGB interleaved, pixel p = y*W + x at bytes 3p..3p+2
+ *   per-channel: arrays of H*W*3 entries indexed like the frame bytes
+ *   mask       : H*W bytes, 0 or 1
+ *   labels     : H*W int32, -1 for background
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+/* ------------------------------------------------------------------------ */
+/* Pointer record (the Mouse module's output: position + click state).       */
+/* Same field order as the library's public struct; defined independently.  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t valid, click;
+    float x, y;
+    uint32_t area;
+    int32_t x0, y0, x1, y1;
+    int32_t label;
+} orc_pointer;
+
+static int imin(int a, int b) { return a < b ? a : b; }
+static int imax(int a, int b) { return a > b ? a : b; }
+
+/* ======================================================================== */
+/* Step L -- background learning (Sec. 2 "the FIZI module learns the          */
+/* background without the user"; Sec. 3.1 (i) "minimum and maximum values     */
+/* learned in the initialization step"; Sec. 3.3 cites Gaussian background    */
+/* models for the learning).                                                 */
+/* ======================================================================== */
+
+/* Per pixel-channel sums over n user-free frames: S = sum v, Q = sum v^2,
+ * and the literal min / max of Sec. 3.1 (i).  Exact in uint32 for n <= 65535. */
+void orc_learn_stats(const uint8_t *frames, int n, int w, int h,
+                     uint32_t *S, uint32_t *Q, uint8_t *vmin, uint8_t *vmax)
+{
+    size_t count = (size_t)w * (size_t)h * 3u;
+    for (size_t j = 0; j < count; ++j) {
+        S[j] = 0; Q[j] = 0; vmin[j] = 255; vmax[j] = 0;
+    }
+    for (int i = 0; i < n; ++i) {
+        const uint8_t *f = frames + (size_t)i * count;
+        for (size_t j = 0; j < count; ++j) {
+            uint32_t v = f[j];
+            S[j] += v;
+            Q[j] += v * v;
+            if (v < vmin[j]) vmin[j] = (uint8_t)v;
+            if (v > vmax[j]) vmax[j] = (uint8_t)v;
+        }
+    }
+}
+
+/* FP32 mean and standard deviation of the learned Gaussian per channel:
+ *   mu    = (float)S / (float)n
+ *   sigma = sqrtf( (float)(n*Q - S^2) / (float)(n*n) )
+ * The int64 numerator and n*n are converted with C's correctly rounded
+ * integer-to-float conversion. */
+void orc_learn_meanstd(const uint32_t *S, const uint32_t *Q, int n, size_t count,
+                       float *mean, float *stdv)
+{
+    for (size_t j = 0; j < count; ++j) {
+        int64_t s = S[j], q = Q[j];
+        int64_t num = (int64_t)n * q - s * s;
+        int64_t nn = (int64_t)n * (int64_t)n;
+        mean[j] = (float)s / (float)n;
+        stdv[j] = sqrtf((float)num / (float)nn);
+    }
+}
+
+/* Gaussian band edges, exact in integers.  With D = n*Q - S^2 and k = kn/kd:
+ *   L_k = largest integer L with  n*L <= S  and  kd^2 (S - n L)^2 >= kn^2 D
+ *         (i.e. L <= mu - k sigma)
+ *   H_k = smallest integer H with n*H >= S  and  kd^2 (n H - S)^2 >= kn^2 D
+ *         (i.e. H >= mu + k sigma)
+ * Written as plain searches that step away from the mean until the condition
+ * holds.  Reading: the paper names min/max only; the k-sigma widening follows
+ * the Gaussian background models the paper cites for the learning step. */
+int64_t orc_band_low(uint32_t S, uint32_t Q, int n, int kn, int kd)
+{
+    int64_t s = S, D = (int64_t)n * (int64_t)Q - s * s;
+    int64_t L = s / n;                         /* largest L with n L <= S */
+    for (;;) {
+        int64_t gap = s - (int64_t)n * L;      /* >= 0 */
+        if ((int64_t)kd * kd * gap * gap >= (int64_t)kn * kn * D) return L;
+        --L;
+    }
+}
+
+int64_t orc_band_high(uint32_t S, uint32_t Q, int n, int kn, int kd)
+{
+    int64_t s = S, D = (int64_t)n * (int64_t)Q - s * s;
+    int64_t H = (s + n - 1) / n;               /* smallest H with n H >= S */
+    for (;;) {
+        int64_t gap = (int64_t)n * H - s;      /* >= 0 */
+        if ((int64_t)kd * kd * gap * gap >= (int64_t)kn * kn * D) return H;
+        ++H;
+    }
+}
+
+/* Band used by the background test: the paper's literal [min, max] widened to
+ * cover [mu - k sigma, mu + k sigma] and by a margin delta, clamped to bytes:
+ *   lo = clamp(min(vmin, L_k) - delta, 0, 255)
+ *   hi = clamp(max(vmax, H_k) + delta, 0, 255)
+ * k = 0, delta = 0 gives the paper-literal band [vmin, vmax]. */
+void orc_learn_band(const uint32_t *S, const uint32_t *Q,
+                    const uint8_t *vmin, const uint8_t *vmax,
+                    int n, size_t count, int kn, int kd, int delta,
+                    uint8_t *lo, uint8_t *hi)
+{
+    for (size_t j = 0; j < count; ++j) {
+        int64_t L = orc_band_low(S[j], Q[j], n, kn, kd);
+        int64_t H = orc_band_high(S[j], Q[j], n, kn, kd);
+        int64_t a = (L < vmin[j] ? L : vmin[j]) - delta;
+        int64_t b = (H > vmax[j] ? H : vmax[j]) + delta;
+        if (a < 0) a = 0;
+        if (a > 255) a = 255;
+        if (b < 0) b = 0;
+        if (b > 255) b = 255;
+        lo[j] = (uint8_t)a;
+        hi[j] = (uint8_t)b;
+    }
+}
+
+/* ======================================================================== */
+/* Step 1 -- brightness correction (Sec. 2 "The brightness is also corrected"; */
+/* Sec. 3.2 "a filter ... to modify the Luminosity component").               */
+/* Reading: the frame is rescaled so that its total luma equals the mean      */
+/* total luma of the learning frames.  A uniform RGB scale leaves hue          */
+/* unchanged and moves luminosity, which is what the filter must do.          */
+/* ======================================================================== */
+
+/* Integer BT.601 luma of one pixel: (77 R + 150 G + 29 B + 128) >> 8. */
+static uint32_t luma8(const uint8_t *p)
+{
+    return (77u * p[0] + 150u * p[1] + 29u * p[2] + 128u) >> 8;
+}
+
+/* SY = sum of luma8 over the frame. */
+uint64_t orc_luma_sum(const uint8_t *frame, size_t npx)
+{
+    uint64_t sy = 0;
+    for (size_t p = 0; p < npx; ++p) sy += luma8(frame + 3 * p);
+    return sy;
+}
+
+/* Reference luma of the learned background: floor(sum_i SY(F_i) / n). */
+uint64_t orc_ref_luma(const uint8_t *frames, int n, size_t npx)
+{
+    uint64_t tot = 0;
+    for (int i = 0; i < n; ++i) tot += orc_luma_sum(frames + (size_t)i * npx * 3u, npx);
+    return tot / (uint64_t)n;
+}
+
+/* Gain in Q16: round(SYref / SY), clamped to [gmin, gmax].  A black frame
+ * (SY = 0) gets unit gain before the clamp. */
+uint32_t orc_gain(uint64_t sy, uint64_t syref, uint32_t gmin, uint32_t gmax)
+{
+    uint64_t g = (sy == 0) ? 65536u : ((syref << 16) + sy / 2) / sy;
+    if (g < gmin) g = gmin;
+    if (g > gmax) g = gmax;
+    return (uint32_t)g;
+}
+
+/* c' = min(255, (c * g + 2^15) >> 16) on every byte of the frame. */
+void orc_apply_gain(const uint8_t *frame, size_t nbytes, uint32_t g, uint8_t *out)
+{
+    for (size_t j = 0; j < nbytes; ++j) {
+        uint64_t c = ((uint64_t)frame[j] * g + 32768u) >> 16;
+        out[j] = (uint8_t)(c > 255 ? 255 : c);
+    }
+}
+
+/* ======================================================================== */
+/* Steps 2-3 -- the three thresholded images of Sec. 3.1 and their AND.       */
+/* ======================================================================== */
+
+/* Integer hue, 1536 units per turn (256 per 60 degrees), of an RGB triple;
+ * -1 when max == min (hue undefined).  HSV and HSL share this hue, so the
+ * HSV of Sec. 3.1 (iii) item and the HSL of its text agree.
+ * The sector is chosen by the first maximum in the order R, G, B; within a
+ * sector the hexagonal hue is base + 256 * t / d, rounded half up:
+ *   h = base - 256 + floor((512 (t + d) + d) / (2 d)),  wrapped to [0,1536). */
+int orc_hue(int r, int g, int b)
+{
+    int mx = imax(r, imax(g, b)), mn = imin(r, imin(g, b));
+    int d = mx - mn, base, t;
+    if (d == 0) return -1;
+    if (r == mx)      { base = 0;    t = g - b; }
+    else if (g == mx) { base = 512;  t = b - r; }
+    else              { base = 1024; t = r - g; }
+    int h = base - 256 + (512 * (t + d) + d) / (2 * d);
+    if (h < 0) h += 1536;
+    if (h >= 1536) h -= 1536;
+    return h;
+}
+
+/* Integer hue of every pixel of a frame (-1 where undefined). */
+void orc_hue_map(const uint8_t *c, size_t npx, int16_t *out)
+{
+    for (size_t p = 0; p < npx; ++p) out[p] = (int16_t)orc_hue(c[3 * p], c[3 * p + 1], c[3 * p + 2]);
+}
+
+/* Hue inside the closed arc [a1, a2] taken modulo one turn, Sec. 3.1 (iii)
+ * "Hue in [alpha1, alpha2] % 2pi": a1 > a2 means the arc wraps through 0. */
+static int in_arc(int h, int a1, int a2)
+{
+    return (a1 <= a2) ? (h >= a1 && h <= a2) : (h >= a1 || h <= a2);
+}
+
+/* Per-pixel masks on the gain-corrected frame c (H*W*3 bytes):
+ *   fg1 (Sec. 3.1 (i))  : 1 iff some channel lies outside [lo_c, hi_c].
+ *       Reading: the printed formula keeps pixels between min and max,
+ *       which contradicts the sentence above it ("between ... are removed");
+ *       the sentence is taken, with inclusive bounds.
+ *   fg2 (Sec. 3.1 (ii)) : 1 iff max(c) - min(c) >= S (gray pixels removed).
+ *       Reading: the printed formula has no comparison; the sentence
+ *       ("lower than a tolerance S ... eliminated") is taken.
+ *   fg3 (Sec. 3.1 (iii)): 1 iff the hue is defined and inside the arc.
+ *   raw = fg1 AND fg2 AND fg3 (the merging step of Sec. 3.1).
+ * Any of the output pointers may be NULL. */
+void orc_fg(const uint8_t *c, const uint8_t *lo, const uint8_t *hi, size_t npx,
+            int gray_tol, int hue_lo, int hue_hi,
+            uint8_t *fg1, uint8_t *fg2, uint8_t *fg3, uint8_t *raw)
+{
+    for (size_t p = 0; p < npx; ++p) {
+        const uint8_t *px = c + 3 * p;
+        int outside = 0;
+        for (int k = 0; k < 3; ++k) {
+            if (px[k] < lo[3 * p + k] || px[k] > hi[3 * p + k]) outside = 1;
+        }
+        int mx = imax(px[0], imax(px[1], px[2]));
+        int mn = imin(px[0], imin(px[1], px[2]));
+        int notgray = (mx - mn) >= gray_tol;
+        int h = orc_hue(px[0], px[1], px[2]);
+        int skin = (h >= 0) && in_arc(h, hue_lo, hue_hi);
+        if (fg1) fg1[p] = (uint8_t)outside;
+        if (fg2) fg2[p] = (uint8_t)notgray;
+        if (fg3) fg3[p] = (uint8_t)skin;
+        if (raw) raw[p] = (uint8_t)(outside && notgray && skin);
+    }
+}
+
+/* ======================================================================== */
+/* Step 4 -- morphology, Sec. 3.1 "erosion and dilatation operators ... remove */
+/* the small noisy objects and connect neighborhood zones".                   */
+/* Reading: 3x3 square element; opening (erode then dilate) open_iters times,  */
+/* then closing (dilate then erode) close_iters times; pixels outside the      */
+/* image are neutral (ignored) for both operators.                             */
+/* ======================================================================== */
+
+void orc_erode(const uint8_t *in, int w, int h, uint8_t *out)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int v = 1;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                    if (!in[(size_t)yy * w + xx]) v = 0;
+                }
+            out[(size_t)y * w + x] = (uint8_t)v;
+        }
+}
+
+void orc_dilate(const uint8_t *in, int w, int h, uint8_t *out)
+{
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            int v = 0;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int yy = y + dy, xx = x + dx;
+                    if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                    if (in[(size_t)yy * w + xx]) v = 1;
+                }
+            out[(size_t)y * w + x] = (uint8_t)v;
+        }
+}
+
+void orc_morph(const uint8_t *raw, int w, int h, int open_iters, int close_iters,
+               uint8_t *out)
+{
+    size_t npx = (size_t)w * (size_t)h;
+    uint8_t *tmp = (uint8_t *)malloc(npx ? npx : 1);
+    memcpy(out, raw, npx);
+    for (int i = 0; i < open_iters; ++i) {
+        orc_erode(out, w, h, tmp);
+        orc_dilate(tmp, w, h, out);
+    }
+    for (int i = 0; i < close_iters; ++i) {
+        orc_dilate(out, w, h, tmp);
+        orc_erode(tmp, w, h, out);
+    }
+    free(tmp);
+}
+
+/* ======================================================================== */
+/* Step 5a -- connected components (Sec. 2 Mouse module: "tracks the hand     */
+/* corresponding zone" in the binary image).                                  */
+/* Reading: 8-connectivity; every component is labelled with the smallest     */
+/* linear index y*W + x of its pixels; background is -1.  Plain flood fill:   */
+/* scanning in raster order, the first unlabelled foreground pixel of a       */
+/* component is its smallest index.  Returns the number of components.       */
+/* ======================================================================== */
+int orc_label(const uint8_t *mask, int w, int h, int32_t *labels)
+{
+    size_t npx = (size_t)w * (size_t)h;
+    int32_t *queue = (int32_t *)malloc((npx ? npx : 1) * sizeof(int32_t));
+    int ncomp = 0;
+    for (size_t p = 0; p < npx; ++p) labels[p] = -1;
+    for (size_t p = 0; p < npx; ++p) {
+        if (!mask[p] || labels[p] >= 0) continue;
+        size_t head = 0, tail = 0;
+        labels[p] = (int32_t)p;
+        queue[tail++] = (int32_t)p;
+        while (head < tail) {
+            int32_t q = queue[head++];
+            int qy = q / w, qx = q % w;
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int yy = qy + dy, xx = qx + dx;
+                    if (yy < 0 || yy >= h || xx < 0 || xx >= w) continue;
+                    size_t r = (size_t)yy * w + xx;
+                    if (mask[r] && labels[r] < 0) {
+                        labels[r] = (int32_t)p;
+                        queue[tail++] = (int32_t)r;
+                    }
+                }
+        }
+        ++ncomp;
+    }
+    free(queue);
+    return ncomp;
+}
+
+/* ======================================================================== */
+/* Step 5b -- pointer (Sec. 2: "This hand zone is converted into a pointer by */
+/* the Mouse module"; the Interface reads "its movement, its state (click or  */
+/* not)").                                                                    */
+/* Reading: the hand is the largest component (ties: smaller label); the      */
+/* pointer is its centroid with pixel centres at integer coordinates, and its */
+/* inclusive bounding box; valid iff area >= min_area.  With no component:    */
+/* valid 0, area 0, label -1, box -1, x = y = -1.                             */
+/* ======================================================================== */
+void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_area,
+                             orc_pointer *out)
+{
+    size_t npx = (size_t)w * (size_t)h;
+    /* per-label accumulators, indexed by the label (= a pixel index) */
+    uint32_t *area = (uint32_t *)calloc(npx ? npx : 1, sizeof(uint32_t));
+    uint64_t *sx = (uint64_t *)calloc(npx ? npx : 1, sizeof(uint64_t));
+    uint64_t *sy = (uint64_t *)calloc(npx ? npx : 1, sizeof(uint64_t));
+    int32_t *bx0 = (int32_t *)malloc((npx ? npx : 1) * sizeof(int32_t));
+    int32_t *by0 = (int32_t *)malloc((npx ? npx : 1) * sizeof(int32_t));
+    int32_t *bx1 = (int32_t *)malloc((npx ? npx : 1) * sizeof(int32_t));
+    int32_t *by1 = (int32_t *)malloc((npx ? npx : 1) * sizeof(int32_t));
+    for (size_t p = 0; p < npx; ++p) {
+        int32_t l = labels[p];
+        if (l < 0) continue;
+        int y = (int)(p / (size_t)w), x = (int)(p % (size_t)w);
+        if (area[l] == 0) { bx0[l] = x; bx1[l] = x; by0[l] = y; by1[l] = y; }
+        area[l] += 1;
+        sx[l] += (uint64_t)x;
+        sy[l] += (uint64_t)y;
+        if (x < bx0[l]) bx0[l] = x;
+        if (x > bx1[l]) bx1[l] = x;
+        if (y < by0[l]) by0[l] = y;
+        if (y > by1[l]) by1[l] = y;
+    }
+    int32_t best = -1;
+    for (size_t l = 0; l < npx; ++l) {
+        if (area[l] == 0) continue;
+        if (best < 0 || area[l] > area[best]) best = (int32_t)l;  /* ascending l: ties keep the smaller */
+    }
+    memset(out, 0, sizeof(*out));
+    if (best < 0) {
+        out->valid = 0; out->area = 0; out->label = -1;
+        out->x0 = out->y0 = out->x1 = out->y1 = -1;
+        out->x = -1.0f; out->y = -1.0f;
+    } else {
+        out->area = area[best];
+        out->label = best;
+        out->valid = area[best] >= min_area;
+        out->x = (float)((double)sx[best] / (double)area[best]);
+        out->y = (float)((double)sy[best] / (double)area[best]);
+        out->x0 = bx0[best]; out->y0 = by0[best];
+        out->x1 = bx1[best]; out->y1 = by1[best];
+    }
+    free(area); free(sx); free(sy); free(bx0); free(by0); free(bx1); free(by1);
+}
+
+/* Click state machine of one stream (reading of "its state (click or not)").
+ * hist holds the areas of the last `window` valid frames, oldest first
+ * (hist_count entries).  For a valid frame, A_ref = max(hist):
+ *   click := 1 if 100*area < on_pct  * A_ref
+ *   click := 0 if 100*area > off_pct * A_ref   (otherwise unchanged)
+ *   no history yet => click := 0
+ * then the area is appended (dropping the oldest beyond `window`).
+ * An invalid frame changes nothing.  Writes the state into out->click. */
+void orc_click_update(int32_t *click, uint32_t *hist, int32_t *hist_count, int window,
+                      int on_pct, int off_pct, orc_pointer *out)
+{
+    if (out->valid) {
+        if (*hist_count == 0) {
+            *click = 0;
+        } else {
+            uint64_t aref = 0;
+            for (int i = 0; i < *hist_count; ++i) if (hist[i] > aref) aref = hist[i];
+            uint64_t a100 = 100u * (uint64_t)out->area;
+            if (a100 < (uint64_t)on_pct * aref) *click = 1;
+            else if (a100 > (uint64_t)off_pct * aref) *click = 0;
+        }
+        if (window > 0) {
+            if (*hist_count == window) {
+                memmove(hist, hist + 1, (size_t)(window - 1) * sizeof(uint32_t));
+                hist[window - 1] = out->area;
+            } else {
+                hist[(*hist_count)++] = out->area;
+            }
+        }
+    }
+    out->click = *click;
+}
+
+/* ======================================================================== */
+/* One frame through the whole path (Sec. 2 running step):                    */
+/* brightness -> three masks -> AND -> morphology -> components -> pointer.  */
+/* mask_out / labels_out / corrected_out may be NULL.                         */
+/* ======================================================================== */
+void orc_process_frame(const uint8_t *frame, int w, int h,
+                       const uint8_t *lo, const uint8_t *hi, uint64_t syref,
+                       int gray_tol, int hue_lo, int hue_hi,
+                       int open_iters, int close_iters,
+                       uint32_t gain_min, uint32_t gain_max, uint32_t min_area,
+                       int on_pct, int off_pct, int window,
+                       int32_t *click, uint32_t *hist, int32_t *hist_count,
+                       uint8_t *mask_out, int32_t *labels_out, orc_pointer *pointer_out,
+                       uint32_t *gain_out)
+{
+    size_t npx = (size_t)w * (size_t)h;
+    uint8_t *c = (uint8_t *)malloc(npx * 3 + 1);
+    uint8_t *raw = (uint8_t *)malloc(npx + 1);
+    uint8_t *mask = (uint8_t *)malloc(npx + 1);
+    int32_t *labels = (int32_t *)malloc((npx + 1) * sizeof(int32_t));
+    uint64_t sy = orc_luma_sum(frame, npx);
+    uint32_t g = orc_gain(sy, syref, gain_min, gain_max);
+    orc_apply_gain(frame, npx * 3, g, c);
+    orc_fg(c, lo, hi, npx, gray_tol, hue_lo, hue_hi, NULL, NULL, NULL, raw);
+    orc_morph(raw, w, h, open_iters, close_iters, mask);
+    orc_label(mask, w, h, labels);
+    orc_pointer_from_labels(labels, w, h, min_area, pointer_out);
+    orc_click_update(click, hist, hist_count, window, on_pct, off_pct, pointer_out);
+    if (mask_out) memcpy(mask_out, mask, npx);
+    if (labels_out) memcpy(labels_out, labels, npx * sizeof(int32_t));
+    if (gain_out) *gain_out = g;
+    free(c); free(raw); free(mask); free(labels);
+}

@@ -1,0 +1,463 @@
+"""Pins of the CPU oracle to things other than itself (no GPU needed).
+
+Each test checks one stage of the oracle against a closed form, a library
+routine (colorsys, scipy.ndimage, numpy), brute force on tiny inputs, a
+hand-worked fixture under tests/golden/, or the generator's ground truth, so
+that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them.
+"""
+import colorsys
+import math
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+import scipy.ndimage as ndi
+
+import oracle
+from paper_1907_04393_gb300 import synth
+
+RNG = np.random.default_rng(20190709)
+EIGHT = np.ones((3, 3), bool)
+
+
+# --------------------------------------------------------------------------- #
+# Hue (Sec. 3.1 (iii))                                                         #
+# --------------------------------------------------------------------------- #
+def _golden_rows(golden_dir, name):
+    rows = []
+    with open(f"{golden_dir}/{name}") as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line)
+    return rows
+
+
+def test_hue_special_colours(golden_dir):
+    for row in _golden_rows(golden_dir, "hue_special.txt"):
+        r, g, b, h = map(int, row.split())
+        assert oracle.hue(r, g, b) == h, (r, g, b)
+
+
+def _circ_dist(a, b, period=1536.0):
+    d = abs(a - b) % period
+    return min(d, period - d)
+
+
+def test_hue_within_half_unit_of_textbook_hsv():
+    cols = RNG.integers(0, 256, size=(20000, 3))
+    worst = 0.0
+    for r, g, b in cols:
+        h = oracle.hue(r, g, b)
+        if max(r, g, b) == min(r, g, b):
+            assert h == -1
+            continue
+        ref = colorsys.rgb_to_hsv(r / 255.0, g / 255.0, b / 255.0)[0] * 1536.0
+        d = _circ_dist(h, ref)
+        worst = max(worst, d)
+        assert d <= 0.5 + 1e-9, (r, g, b, h, ref)
+    assert worst > 0.4  # rounding is really happening (not an identity test)
+
+
+def test_hue_hsl_equals_hsv():
+    # HSV (Sec. 3.1 (iii) item) and HSL (its text) share the hue.
+    for r, g, b in RNG.integers(0, 256, size=(2000, 3)):
+        if max(r, g, b) == min(r, g, b):
+            continue
+        hv = colorsys.rgb_to_hsv(r / 255, g / 255, b / 255)[0]
+        hl = colorsys.rgb_to_hls(r / 255, g / 255, b / 255)[0]
+        assert abs(hv - hl) < 1e-12
+
+
+def _cube():
+    v = np.arange(256, dtype=np.uint8)
+    r, g, b = np.meshgrid(v, v, v, indexing="ij")
+    return np.stack([r, g, b], -1).reshape(4096, 4096, 3)
+
+
+def _textbook_hue_units(c):
+    """Float HSV hue * 1536 of an (..., 3) uint8 array (NaN where gray)."""
+    f = c.astype(np.float64)
+    r, g, b = f[..., 0], f[..., 1], f[..., 2]
+    mx, mn = f.max(-1), f.min(-1)
+    d = mx - mn
+    with np.errstate(invalid="ignore", divide="ignore"):
+        h = np.where(mx == r, (g - b) / d % 6.0,
+                     np.where(mx == g, (b - r) / d + 2.0, (r - g) / d + 4.0))
+    h = h * 256.0 % 1536.0
+    return np.where(d == 0, np.nan, h)
+
+
+def test_exhaustive_cube_integer_hue_is_rounded_textbook_hue():
+    """All 2^24 colours.  256 t / d is never within 1/510 of a half-integer
+    (d <= 255 cannot supply the factor 512), so rounding the float textbook
+    hue gives the exact integer hue; float64 error is far below that margin."""
+    c = _cube()
+    h = _textbook_hue_units(c)
+    defined = ~np.isnan(h)
+    frac = h[defined] - np.floor(h[defined])
+    assert np.abs(frac - 0.5).min() > 1.0 / 600
+    expect = np.full(h.shape, -1, np.int64)
+    expect[defined] = np.floor(h[defined] + 0.5).astype(np.int64) % 1536
+    assert np.array_equal(oracle.hue_map(c), expect)
+
+
+def _arc_table(lo, hi):
+    """Members of the closed hue arc [lo, hi] modulo one turn, walked unit by unit."""
+    t = np.zeros(1536, bool)
+    k = lo
+    while True:
+        t[k] = True
+        if k == hi:
+            return t
+        k = (k + 1) % 1536
+
+
+@pytest.mark.parametrize("hue_lo,hue_hi,tol", [(1472, 256, 15), (100, 900, 0), (1500, 20, 40),
+                                               (0, 1535, 1), (700, 700, 15), (0, 300, 9)])
+def test_exhaustive_cube_gray_and_hue_masks(hue_lo, hue_hi, tol):
+    """All 2^24 colours: fg2 against the HSV chroma (255 * S * V = max - min),
+    fg3 against the rounded textbook hue looked up in the walked arc."""
+    c = _cube()
+    lo = np.zeros_like(c)
+    hi = np.zeros_like(c)
+    fg1, fg2, fg3, raw = oracle.fg(c, lo, hi, tol, hue_lo, hue_hi)
+    f = c.astype(np.float64) / 255.0
+    hsv_s = np.where(f.max(-1) > 0, (f.max(-1) - f.min(-1)) / np.maximum(f.max(-1), 1e-300), 0.0)
+    chroma = np.rint(hsv_s * f.max(-1) * 255.0)
+    assert np.array_equal(fg2, (chroma >= tol).astype(np.uint8))
+    h = _textbook_hue_units(c)
+    defined = ~np.isnan(h)
+    hint = np.zeros(h.shape, np.int64)
+    hint[defined] = np.floor(h[defined] + 0.5).astype(np.int64) % 1536
+    expect = defined & _arc_table(hue_lo, hue_hi)[hint]
+    assert np.array_equal(fg3, expect.astype(np.uint8))
+    # fg1: a band [0, 0] keeps only pure black as background
+    assert np.array_equal(fg1, (c.max(-1) > 0).astype(np.uint8))
+    assert np.array_equal(raw, fg1 & fg2 & fg3)
+
+
+# --------------------------------------------------------------------------- #
+# Background learning (Sec. 2 FIZI init; Sec. 3.1 (i))                         #
+# --------------------------------------------------------------------------- #
+def test_learn_hand_worked_fixture(golden_dir):
+    rows = [r.split("|") for r in _golden_rows(golden_dir, "learn_3frames.txt")]
+    vals = np.array([[int(x) for x in r[0].split()] for r in rows])  # (3 ch, 3 frames)
+    frames = vals.T.reshape(3, 1, 1, 3).astype(np.uint8)
+    S, Q, vmin, vmax = oracle.learn_stats(frames)
+    mean, std = oracle.learn_meanstd(S, Q, 3)
+    lo, hi = oracle.learn_band(S, Q, vmin, vmax, 3, 5, 2, 2)
+    for c, r in enumerate(rows):
+        s, q, mn, mx = map(int, r[1].split())
+        mu, sd = map(float, r[2].split())
+        l, h = map(int, r[3].split())
+        assert (S[0, 0, c], Q[0, 0, c], vmin[0, 0, c], vmax[0, 0, c]) == (s, q, mn, mx)
+        assert mean[0, 0, c] == pytest.approx(mu, rel=1e-6)
+        assert std[0, 0, c] == pytest.approx(sd, rel=1e-6, abs=1e-7)
+        assert (lo[0, 0, c], hi[0, 0, c]) == (l, h)
+
+
+def test_learn_single_frame_closed_form():
+    f = RNG.integers(0, 256, size=(1, 7, 9, 3), dtype=np.uint8)
+    S, Q, vmin, vmax = oracle.learn_stats(f)
+    mean, std = oracle.learn_meanstd(S, Q, 1)
+    assert np.array_equal(mean, f[0].astype(np.float32))
+    assert not std.any()
+    for delta in (0, 2, 9):
+        lo, hi = oracle.learn_band(S, Q, vmin, vmax, 1, 5, 2, delta)
+        v = f[0].astype(np.int32)
+        assert np.array_equal(lo, np.clip(v - delta, 0, 255))
+        assert np.array_equal(hi, np.clip(v + delta, 0, 255))
+
+
+def test_learn_stats_against_numpy():
+    f = RNG.integers(0, 256, size=(37, 5, 6, 3), dtype=np.uint8)
+    S, Q, vmin, vmax = oracle.learn_stats(f)
+    assert np.array_equal(S, f.astype(np.uint64).sum(0))
+    assert np.array_equal(Q, (f.astype(np.uint64) ** 2).sum(0))
+    assert np.array_equal(vmin, f.min(0)) and np.array_equal(vmax, f.max(0))
+    mean, std = oracle.learn_meanstd(S, Q, 37)
+    ff = f.astype(np.float64)
+    np.testing.assert_allclose(mean, ff.mean(0), rtol=1e-6)
+    np.testing.assert_allclose(std, ff.std(0), rtol=1e-5, atol=1e-5)
+
+
+def test_paper_literal_band_is_min_max():
+    # k = 0 and delta = 0: the band is the learned [min, max] of Sec. 3.1 (i)
+    f = RNG.integers(0, 256, size=(11, 4, 5, 3), dtype=np.uint8)
+    S, Q, vmin, vmax = oracle.learn_stats(f)
+    lo, hi = oracle.learn_band(S, Q, vmin, vmax, 11, 0, 1, 0)
+    assert np.array_equal(lo, f.min(0)) and np.array_equal(hi, f.max(0))
+
+
+def test_band_edges_against_decimal_mu_minus_k_sigma():
+    getcontext().prec = 60
+    for _ in range(3000):
+        n = int(RNG.integers(1, 200))
+        spread = int(RNG.integers(0, 128))
+        centre = int(RNG.integers(0, 256))
+        v = np.clip(RNG.normal(centre, spread + 0.01, size=n).round(), 0, 255).astype(np.int64)
+        S, Q = int(v.sum()), int((v * v).sum())
+        kn, kd = int(RNG.integers(0, 16)), int(RNG.integers(1, 16))
+        D = n * Q - S * S
+        mu = Decimal(S) / n
+        ks = Decimal(kn) / kd * Decimal(D).sqrt() / n
+        lo_ref = math.floor(mu - ks)
+        hi_ref = math.ceil(mu + ks)
+        assert oracle.band_low(S, Q, n, kn, kd) == lo_ref, (n, S, Q, kn, kd)
+        assert oracle.band_high(S, Q, n, kn, kd) == hi_ref, (n, S, Q, kn, kd)
+
+
+# --------------------------------------------------------------------------- #
+# Brightness (Sec. 2 "brightness is also corrected"; Sec. 3.2)                 #
+# --------------------------------------------------------------------------- #
+def test_luma8_close_to_bt601():
+    cols = RNG.integers(0, 256, size=(5000, 3)).astype(np.uint8)
+    for c in cols:
+        y = oracle.luma_sum(c.reshape(1, 1, 3))
+        ref = 0.299 * c[0] + 0.587 * c[1] + 0.114 * c[2]
+        assert abs(y - ref) <= 1.5
+
+
+def test_ref_luma_is_floor_of_mean():
+    f = RNG.integers(0, 256, size=(7, 9, 11, 3), dtype=np.uint8)
+    sums = [oracle.luma_sum(x) for x in f]
+    assert oracle.ref_luma(f) == sum(sums) // 7
+
+
+def test_gain_closed_forms():
+    assert oracle.gain(1000, 1000, 32768, 131072) == 65536
+    assert oracle.gain(0, 5000, 32768, 131072) == 65536          # black frame
+    assert oracle.gain(2000, 1000, 32768, 131072) == 32768        # exactly 0.5
+    assert oracle.gain(4000, 1000, 32768, 131072) == 32768        # clamped low
+    assert oracle.gain(1000, 3000, 32768, 131072) == 131072       # clamped high
+    assert oracle.gain(3, 4, 0, 1 << 24) == round(4 / 3 * 65536)
+    for _ in range(500):
+        sy = int(RNG.integers(1 << 16, 1 << 30))
+        syref = int(RNG.integers(0, 1 << 30))
+        g = oracle.gain(sy, syref, 0, (1 << 32) - 1)
+        assert abs(g - syref * 65536 / sy) <= 0.5 + 1e-9
+
+
+def test_apply_gain_rounds_and_saturates():
+    c = np.arange(256, dtype=np.uint8)
+    for g in (0, 1, 32768, 65535, 65536, 65537, 98304, 131072):
+        out = oracle.apply_gain(c, g).astype(np.float64)
+        ref = np.minimum(255.0, c * (g / 65536.0))
+        assert np.all(np.abs(out - ref) <= 0.5)
+    assert np.array_equal(oracle.apply_gain(c, 65536), c)
+
+
+def test_uniform_brightness_scale_is_undone():
+    """All learning frames = B; run frame = round(s * B) without clipping:
+    the corrected frame is within 1 of B and the whole path gives an empty mask."""
+    h, w = 24, 40
+    yy, xx = np.mgrid[0:h, 0:w]
+    for s in (0.7, 0.85, 1.0, 1.13, 1.3):
+        B = np.stack([30 + 3 * xx, 40 + 4 * yy, 150 - 2 * xx], -1).astype(np.uint8)
+        B[5:12, 8:20] = (190, 140, 110)     # a skin-coloured patch in the background
+        run = np.clip(np.round(B * s), 0, 255).astype(np.uint8)
+        assert run.max() < 255
+        o = oracle.OracleStream(w, h)
+        o.learn(np.stack([B] * 4))
+        mask, labels, ptr, g = o.process(run)
+        corr = oracle.apply_gain(run, g).astype(int)
+        assert np.abs(corr - B.astype(int)).max() <= 1, s
+        assert not mask.any() and ptr["valid"] == 0 and ptr["label"] == -1
+
+
+def test_frame_equal_to_learning_frame_has_no_foreground():
+    f = synth.learn_frames(1, 0, 6)
+    S, Q, vmin, vmax = oracle.learn_stats(f)
+    lo, hi = oracle.learn_band(S, Q, vmin, vmax, 6, 5, 2, 2)
+    for i in range(6):
+        fg1, _, _, _ = oracle.fg(f[i], lo, hi, 15, 1472, 256)    # gain 1
+        assert not fg1.any()
+
+
+def test_band_edges_inclusive():
+    lo = np.full((1, 4, 3), 100, np.uint8)
+    hi = np.full((1, 4, 3), 120, np.uint8)
+    c = np.array([[[100, 110, 120], [99, 110, 110], [110, 121, 110], [120, 120, 100]]], np.uint8)
+    fg1, _, _, _ = oracle.fg(c, lo, hi, 0, 0, 1535)
+    assert fg1.tolist() == [[0, 1, 1, 0]]
+
+
+# --------------------------------------------------------------------------- #
+# Morphology (Sec. 3.1 "erosion and dilatation")                               #
+# --------------------------------------------------------------------------- #
+SIZES = [(1, 1), (1, 7), (6, 1), (2, 2), (5, 3), (8, 8), (13, 17), (37, 29), (33, 64)]
+
+
+@pytest.mark.parametrize("h,w", SIZES)
+def test_erode_dilate_against_scipy(h, w):
+    for p in (0.3, 0.6, 0.9):
+        m = (RNG.random((h, w)) < p).astype(np.uint8)
+        e = ndi.binary_erosion(m, EIGHT, border_value=1).astype(np.uint8)
+        d = ndi.binary_dilation(m, EIGHT, border_value=0).astype(np.uint8)
+        assert np.array_equal(oracle.erode(m), e)
+        assert np.array_equal(oracle.dilate(m), d)
+
+
+@pytest.mark.parametrize("oi,ci", [(0, 0), (1, 0), (0, 1), (1, 1), (2, 1), (1, 3)])
+def test_open_close_sequence_against_scipy(oi, ci):
+    m = (RNG.random((29, 41)) < 0.55).astype(np.uint8)
+    ref = m.astype(bool)
+    for _ in range(oi):
+        ref = ndi.binary_dilation(ndi.binary_erosion(ref, EIGHT, border_value=1), EIGHT, border_value=0)
+    for _ in range(ci):
+        ref = ndi.binary_erosion(ndi.binary_dilation(ref, EIGHT, border_value=0), EIGHT, border_value=1)
+    assert np.array_equal(oracle.morph(m, oi, ci), ref.astype(np.uint8))
+
+
+def test_morphology_special_cases():
+    m = np.zeros((9, 9), np.uint8)
+    m[4, 4] = 1
+    assert not oracle.morph(m, 1, 0).any()                      # isolated pixel opened away
+    m = np.zeros((9, 12), np.uint8)
+    m[2:7, 1:5] = 1
+    m[2:7, 6:10] = 1                                            # 1-px gap at column 5
+    assert oracle.morph(m, 0, 1)[2:7, 5].all()                  # bridged by closing
+    full = np.ones((5, 6), np.uint8)
+    assert oracle.erode(full).all()                             # border is neutral
+    corner = np.zeros((6, 6), np.uint8)
+    corner[:3, :3] = 1
+    assert oracle.morph(corner, 1, 1)[:3, :3].all()             # blob on the border kept
+
+
+# --------------------------------------------------------------------------- #
+# Connected components (Mouse module: the hand zone)                           #
+# --------------------------------------------------------------------------- #
+def _check_against_scipy(m):
+    lab, n = oracle.label(m)
+    ref, nref = ndi.label(m, structure=EIGHT)
+    assert n == nref
+    assert np.array_equal(lab < 0, m == 0)
+    idx = np.arange(m.size).reshape(m.shape)
+    for k in range(1, nref + 1):
+        sel = ref == k
+        vals = np.unique(lab[sel])
+        assert vals.size == 1 and vals[0] == idx[sel].min()
+
+
+@pytest.mark.parametrize("h,w", SIZES + [(64, 96), (70, 33)])
+def test_labels_against_scipy(h, w):
+    for p in (0.2, 0.45, 0.6, 0.85):
+        _check_against_scipy((RNG.random((h, w)) < p).astype(np.uint8))
+
+
+def test_hand_counted_components():
+    cb = (np.add.outer(np.arange(10), np.arange(12)) % 2).astype(np.uint8)
+    assert oracle.label(cb)[1] == 1                                   # checkerboard
+    diag = np.eye(8, dtype=np.uint8)
+    assert oracle.label(diag)[1] == 1                                 # diagonal chain
+    grid = np.zeros((9, 11), np.uint8)
+    grid[::2, ::2] = 1
+    assert oracle.label(grid)[1] == 5 * 6                             # isolated pixels
+    u = np.zeros((40, 40), np.uint8)
+    u[5:35, 5] = 1
+    u[5:35, 34] = 1
+    u[34, 5:35] = 1                                                   # U crossing 32-px tiles
+    lab, n = oracle.label(u)
+    assert n == 1 and lab[5, 5] == 5 * 40 + 5 and lab[5, 34] == 5 * 40 + 5
+    sp = np.zeros((21, 21), np.uint8)                                 # square spiral
+    y, x, dy, dx, L = 10, 10, 0, 1, 1
+    sp[y, x] = 1
+    while True:
+        for _ in range(2):
+            for _ in range(L):
+                y, x = y + dy, x + dx
+                if not (0 <= y < 21 and 0 <= x < 21):
+                    break
+                sp[y, x] = 1
+            dy, dx = dx, -dy
+        L += 2
+        if L > 21:
+            break
+    assert oracle.label(sp)[1] == 1
+    assert oracle.label(np.zeros((3, 3), np.uint8))[1] == 0
+
+
+# --------------------------------------------------------------------------- #
+# Pointer and click state (Sec. 2: pointer, "its state (click or not)")        #
+# --------------------------------------------------------------------------- #
+def _ellipse(h, w, cy, cx, a, b):
+    yy, xx = np.mgrid[0:h, 0:w]
+    return ((((xx - cx) / a) ** 2 + ((yy - cy) / b) ** 2) <= 1.0).astype(np.uint8)
+
+
+def test_ellipse_centroid_and_bbox_exact():
+    for (cy, cx, a, b) in [(20, 30, 10.0, 6.0), (31.5, 40.5, 12.3, 20.1), (50, 50, 40.0, 40.0)]:
+        m = _ellipse(101, 103, cy, cx, a, b)
+        lab, _ = oracle.label(m)
+        p = oracle.pointer_from_labels(lab, 50)
+        assert p["x"] == cx and p["y"] == cy
+        assert p["area"] == int(m.sum()) and p["valid"] == 1
+        ys, xs = np.nonzero(m)
+        assert (p["x0"], p["y0"], p["x1"], p["y1"]) == (xs.min(), ys.min(), xs.max(), ys.max())
+        # closed form of the box of a pixel-centred ellipse: centre -/+ floor(semi-axis)
+        if cx == int(cx) and cy == int(cy):
+            assert (p["x0"], p["x1"]) == (cx - math.floor(a), cx + math.floor(a))
+            assert (p["y0"], p["y1"]) == (cy - math.floor(b), cy + math.floor(b))
+
+
+def test_largest_blob_and_ties():
+    m = _ellipse(60, 80, 20, 20, 6, 6) | _ellipse(60, 80, 40, 60, 9, 9)
+    p = oracle.pointer_from_labels(oracle.label(m)[0], 1)
+    assert (p["x"], p["y"]) == (60.0, 40.0)
+    m = _ellipse(60, 80, 40, 20, 7, 7) | _ellipse(60, 80, 20, 60, 7, 7)   # equal areas
+    lab, _ = oracle.label(m)
+    p = oracle.pointer_from_labels(lab, 1)
+    assert p["label"] == min(lab[40, 20], lab[20, 60]) and (p["x"], p["y"]) == (60.0, 20.0)
+    p = oracle.pointer_from_labels(oracle.label(np.zeros((4, 4), np.uint8))[0], 1)
+    assert (p["valid"], p["area"], p["label"], p["x0"], p["x"]) == (0, 0, -1, -1, -1.0)
+    small = np.zeros((10, 10), np.uint8)
+    small[2:4, 2:4] = 1
+    p = oracle.pointer_from_labels(oracle.label(small)[0], 5)
+    assert p["valid"] == 0 and p["area"] == 4
+
+
+def test_click_state_machine_hand_worked():
+    st = oracle.ClickState(30)
+    seq = [(1, 100, 0), (1, 100, 0), (1, 50, 1), (1, 60, 1), (0, 10, 1), (1, 95, 0),
+           (1, 79, 1), (1, 91, 1), (1, 92, 0)]
+    # hand-worked: first frame has no A_ref -> 0; 100*100 > 90*100 -> 0;
+    # 5000 < 8000 -> 1; 6000 < 8000 -> 1; invalid -> unchanged; 9500 > 9000 -> 0;
+    # 7900 < 8000 -> 1; 9100 > 9000 -> 0; 9200 > 9000 -> 0
+    got = []
+    for valid, area, _ in seq:
+        p = st.update(dict(valid=valid, click=0, x=0.0, y=0.0, area=area, x0=0, y0=0, x1=0,
+                           y1=0, label=0), 80, 90)
+        got.append(p["click"])
+    assert got == [0, 0, 1, 1, 1, 0, 1, 0, 0]
+    st = oracle.ClickState(2)                              # sliding window of 2 valid frames
+    out = [st.update(dict(valid=1, click=0, x=0.0, y=0.0, area=a, x0=0, y0=0, x1=0, y1=0,
+                          label=0), 80, 90)["click"] for a in (100, 100, 70, 70, 70)]
+    # A_ref: -,100,100,100(hist 100,70),70(hist 70,70): 7000 > 6300 -> clear
+    assert out == [0, 0, 1, 1, 0]
+
+
+# --------------------------------------------------------------------------- #
+# Whole path against the generator's ground truth (sanity of the readings)     #
+# --------------------------------------------------------------------------- #
+def test_pointer_tracks_generated_hand_config1():
+    o = oracle.OracleStream(*synth.shape(1))
+    o.learn(synth.learn_frames(1))
+    for t in range(0, 60, 7):
+        _, _, p, _ = o.process(synth.run_frame(1, 0, t))
+        (cx, cy, a, b), = synth.truth(1, 0, t)[0]
+        assert p["valid"] == 1
+        assert abs(p["x"] - cx) < 0.6 and abs(p["y"] - cy) < 0.6
+        assert abs(p["area"] - math.pi * a * b) < 0.05 * math.pi * a * b
+
+
+def test_click_follows_open_closed_config2():
+    o = oracle.OracleStream(*synth.shape(2))
+    o.learn(synth.learn_frames(2))
+    agree = 0
+    ts = list(range(0, 120, 3))
+    for t in ts:
+        _, _, p, _ = o.process(synth.run_frame(2, 0, t))
+        agree += p["click"] == (0 if synth.truth(2, 0, t)[1] else 1)
+    assert agree >= 0.8 * len(ts)
