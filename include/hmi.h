@@ -1,0 +1,202 @@
+/*
+ * hmi.h -- C ABI of the GB300 hand-isolation library (libhmi.so).
+ *
+ * The library implements the per-frame path of the contactless interface of
+ * Magoules & Zou (arXiv 1907.04393): learn a background without the user
+ * (Sec. 2, initialisation step), then for every camera frame correct the
+ * brightness (Sec. 2, Sec. 3.2), build the three thresholded images and AND
+ * them (Sec. 3.1 (i)-(iii)), clean the mask with erosion/dilation (Sec. 3.1),
+ * and turn the hand zone into a pointer with a click state (Sec. 2, Mouse and
+ * Interface modules).  Every step runs in hand-written sm_103a CUDA kernels;
+ * there is no CPU fallback.
+ *
+ * Conventions (all calls):
+ *   - Return value: HMI_OK (0) or a negative HMI_ERR_* status.  Functions that
+ *     return a pointer return NULL on error; hmi_last_error() then gives the
+ *     status (thread-local).
+ *   - Frames are packed RGB8: h rows of 3*w bytes, pixel (x, y) at byte
+ *     3*(y*w + x), channels in the order R, G, B.  Masks are h*w bytes (0/1),
+ *     labels h*w int32.
+ *   - Buffers passed in are owned by the caller.  A buffer may live in host
+ *     memory (pageable or pinned) or in device memory of the stream's GPU;
+ *     the library tells them apart with cudaPointerGetAttributes.  The library
+ *     owns all per-stream device state.
+ *   - Synchronous calls return when results are in the caller's buffers.
+ *     The *_async calls only enqueue work on the given CUDA stream
+ *     (a cudaStream_t passed as void*, NULL = the legacy default stream) and
+ *     require device buffers.
+ *   - One hmi_stream is used by one host thread at a time.  Device-side errors
+ *     (a bounded wait or bounded loop that ran out) surface as
+ *     HMI_ERR_DEVICE_TIMEOUT on the next synchronous call on that stream.
+ *   - Limits: 1 <= w, h <= 8192; 1 <= n (learning frames) <= 65535.
+ */
+#ifndef HMI_H
+#define HMI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HMI_API __attribute__((visibility("default")))
+#else
+#define HMI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HMI_OK 0
+#define HMI_ERR_INVALID_ARG (-1)    /* null/odd pointer, size or parameter out of range */
+#define HMI_ERR_NOT_LEARNED (-2)    /* processing before hmi_learn_background */
+#define HMI_ERR_NO_MEMORY (-3)      /* device or host allocation failed, or admission refused */
+#define HMI_ERR_DEVICE (-4)         /* a CUDA call failed */
+#define HMI_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait/loop gave up */
+
+/* Opaque per-camera stream: geometry, parameters, learned background model,
+ * click state and device work buffers.  Created by hmi_create_stream. */
+typedef struct hmi_stream hmi_stream;
+
+/* User-adjustable thresholds (Sec. 2: the FIZI settings are "easily
+ * adjustable"; Sec. 3.1: tolerance S and hue thresholds alpha1, alpha2 are set
+ * by the user).  Defaults in brackets, set by hmi_default_params. */
+typedef struct {
+    uint32_t gain_min_q16;  /* [32768]  lower clamp of the brightness gain, Q16 (0.5) */
+    uint32_t gain_max_q16;  /* [131072] upper clamp of the brightness gain, Q16 (2.0) */
+    uint32_t min_area;      /* [50]     pointer valid iff the hand blob has >= min_area pixels */
+    uint16_t hue_lo;        /* [1472]   alpha1, hue units (1536 per turn, 256 per 60 deg) */
+    uint16_t hue_hi;        /* [256]    alpha2; hue_lo > hue_hi means the arc wraps through red */
+    uint16_t click_window;  /* [30]     valid frames remembered for the click reference area (<= 1024) */
+    uint8_t gray_tol;       /* [15]     S: pixels with max(RGB) - min(RGB) < S are gray, removed */
+    uint8_t bg_margin;      /* [2]      delta added outside the learned background band */
+    uint8_t bg_k_num;       /* [5]      band half-width k = bg_k_num / bg_k_den standard deviations */
+    uint8_t bg_k_den;       /* [2]      (1..15; numerator 0..15) */
+    uint8_t open_iters;     /* [1]      openings (erode, dilate) for noise removal */
+    uint8_t close_iters;    /* [1]      closings (dilate, erode) to connect zones; open+close <= 16 */
+    uint8_t click_on_pct;   /* [80]     click when 100*area < on_pct * reference area */
+    uint8_t click_off_pct;  /* [90]     release when 100*area > off_pct * reference area */
+    uint8_t reserved[2];    /* must be zero */
+} hmi_params;
+
+/* The Mouse module's pointer (Sec. 2): position of the hand zone and its
+ * state "click or not".  With no foreground at all: valid 0, area 0,
+ * label -1, box -1, x = y = -1. */
+typedef struct {
+    int32_t valid;    /* 1 iff the largest blob has at least min_area pixels */
+    int32_t click;    /* click state after this frame (0/1) */
+    float x, y;       /* centroid of the largest blob, pixel centres at integers */
+    uint32_t area;    /* pixels in the largest blob */
+    int32_t x0, y0;   /* inclusive bounding box of the largest blob */
+    int32_t x1, y1;
+    int32_t label;    /* the blob's label: smallest linear index y*w + x of its pixels */
+} hmi_pointer;
+
+/* Fill *p with the documented defaults.  HMI_ERR_INVALID_ARG if p is NULL. */
+HMI_API int hmi_default_params(hmi_params *p);
+
+/* Create a stream for w x h frames on the current CUDA device (Sec. 2,
+ * initialisation: reading the configuration).  p may be NULL (defaults).
+ * Allocates all device state up front.  NULL on error (invalid size or
+ * parameters: HMI_ERR_INVALID_ARG; allocation: HMI_ERR_NO_MEMORY). */
+HMI_API hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p);
+
+/* Release a stream and all of its device memory (NULL is a no-op).
+ * Any batch that contains the stream must be destroyed first. */
+HMI_API void hmi_destroy_stream(hmi_stream *s);
+
+/* Learn the background model from n user-free frames (Sec. 2: "the FIZI
+ * module learns the background without the user"; Sec. 3.1 (i): per-pixel
+ * minimum and maximum).  frames: n consecutive packed RGB8 frames
+ * (n*h*w*3 bytes), host or device.  Per pixel and channel the library keeps
+ * the exact sums S, Q and the min / max, derives the background band and the
+ * reference luma used by the brightness correction, and resets the click
+ * state.  Replaces any earlier model. */
+HMI_API int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n);
+
+/* Run the whole per-frame path on one frame (Sec. 2 running step; Sec. 3.1,
+ * 3.2): brightness gain, background / gray / hue masks, AND, morphology,
+ * 8-connected components, largest blob, pointer and click state.
+ * frame: h*w*3 bytes (host or device).  mask_out: h*w bytes or NULL.
+ * pointer_out: one hmi_pointer or NULL.  HMI_ERR_NOT_LEARNED before learning. */
+HMI_API int hmi_process_frame(hmi_stream *s, const uint8_t *frame, uint8_t *mask_out,
+                      hmi_pointer *pointer_out);
+
+/* Same work enqueued on cuda_stream; frame, mask_out and pointer_out must be
+ * device memory (mask_out and pointer_out may be NULL). */
+HMI_API int hmi_process_frame_async(hmi_stream *s, const uint8_t *frame, uint8_t *mask_out,
+                            hmi_pointer *pointer_out, void *cuda_stream);
+
+/* One frame for each of n streams (1 <= n <= 4096, all on the same device,
+ * each stream at most once), processed by single launches that cover every
+ * stream.  frames[i], masks[i] belong to s[i]; masks (or masks[i]) and
+ * ptrs may be NULL.  ptrs, when given, is an array of n hmi_pointer.
+ * The launch plan for a given list of streams is built on first use and
+ * reused while the same list is passed again. */
+HMI_API int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
+                      uint8_t *const *masks, hmi_pointer *ptrs);
+
+/* A reusable launch plan over a fixed list of streams (the batched form of
+ * hmi_process_batch).  hmi_batch_create returns NULL on error. */
+typedef struct hmi_batch hmi_batch;
+HMI_API hmi_batch *hmi_batch_create(hmi_stream *const *s, int n);
+HMI_API void hmi_batch_destroy(hmi_batch *b);
+
+/* Process one frame per stream of the batch.  Synchronous form: buffers may be
+ * host or device; frames[i] is the frame of the i-th stream given at creation.
+ * masks / ptrs as in hmi_process_batch. */
+HMI_API int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                      hmi_pointer *ptrs);
+
+/* Asynchronous form on cuda_stream: every buffer must be device memory; ptrs
+ * (device, n entries) may be NULL.  With use_graph != 0 the tick is replayed
+ * from a CUDA graph captured on first use. */
+HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                            hmi_pointer *ptrs, void *cuda_stream, int use_graph);
+
+/* Kernel timing of the batch's classification kernel (the per-pixel HBM pass).
+ * hmi_batch_profile(b, max_ticks) starts recording one CUDA-event pair around
+ * that kernel for each of the next max_ticks ticks (0 stops).
+ * hmi_batch_profile_read waits for them and returns the number of ticks timed
+ * and the sum of their durations in milliseconds. */
+HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
+HMI_API int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms);
+
+/* FP32 mean and standard deviation of the learned background per pixel and
+ * channel (h*w*3 floats each, host or device; either may be NULL):
+ * mean = S/n, std = sqrt((n*Q - S^2)/n^2), each step one IEEE operation. */
+HMI_API int hmi_get_background_stats(const hmi_stream *s, float *mean, float *std);
+
+/* Labels of the last processed frame (h*w int32, host or device): -1 for
+ * background, else the smallest linear index of the pixel's 8-connected
+ * component (Mouse module, Sec. 2).  Computed on demand from the last mask. */
+HMI_API int hmi_get_labels(const hmi_stream *s, int32_t *labels);
+
+/* Checkpoint of the learned model.  Export copies (each pointer may be NULL;
+ * host or device) the per pixel-channel sums S, Q (uint32, h*w*3), min/max
+ * and the derived band lo/hi (uint8, h*w*3, packed like the frame), the
+ * reference luma and the number of learning frames.  Import installs S, Q,
+ * min, max (all required) for n frames with reference luma syref, derives the
+ * band with the stream's parameters and resets the click state, exactly as
+ * learning from frames with those sums would.  HMI_ERR_NOT_LEARNED on export
+ * before any learning. */
+HMI_API int hmi_export_background(const hmi_stream *s, uint32_t *S, uint32_t *Q, uint8_t *vmin,
+                                  uint8_t *vmax, uint8_t *lo, uint8_t *hi, uint64_t *syref,
+                                  int *n);
+HMI_API int hmi_import_background(hmi_stream *s, const uint32_t *S, const uint32_t *Q,
+                                  const uint8_t *vmin, const uint8_t *vmax, int n, uint64_t syref);
+
+/* Brightness gain (Q16) applied to the last processed frame, or an error. */
+HMI_API int hmi_get_last_gain(const hmi_stream *s, uint32_t *gain_q16);
+
+/* Bytes of device memory held by a stream created with these arguments
+ * (the figure that admission control budgets).  0 on invalid arguments. */
+HMI_API size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p);
+
+/* Status of the last failed call on this thread, and a text for a status. */
+HMI_API int hmi_last_error(void);
+HMI_API const char *hmi_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HMI_H */

@@ -299,6 +299,18 @@ class OracleStream:
         self.syref = ref_luma(frames)
         self.learned = True
 
+    def set_background(self, S, Q, vmin, vmax, n: int, syref: int) -> None:
+        """Install learned sums directly (the state learning would leave)."""
+        self.n = int(n)
+        self.S = np.ascontiguousarray(S, np.uint32)
+        self.Q = np.ascontiguousarray(Q, np.uint32)
+        self.vmin, self.vmax = _u8(vmin), _u8(vmax)
+        self.lo, self.hi = learn_band(self.S, self.Q, self.vmin, self.vmax, self.n,
+                                      self.p["bg_k_num"], self.p["bg_k_den"], self.p["bg_margin"])
+        self.syref = int(syref)
+        self.click = ClickState(self.p["click_window"])
+        self.learned = True
+
     def stats(self):
         return learn_meanstd(self.S, self.Q, self.n)
 

@@ -1,0 +1,891 @@
+// hmi_api.cu -- host implementation of the C ABI declared in include/hmi.h.
+//
+// A stream owns one device arena (all of its buffers, allocated at creation)
+// and a one-stream launch plan.  A launch plan (hmi_batch) owns the device
+// tables the tick kernels read (stream descriptors, work pieces, prefix sums),
+// a ring of per-tick pointer slots (pinned host mirror + device copy + event),
+// and optionally one CUDA graph per slot that replays the whole tick: the
+// slot's pointer upload, luma, classification, morphology + block components,
+// merge, resolve and pointer kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "hmi_internal.cuh"
+
+using namespace hmi;
+
+namespace {
+
+thread_local int g_last_error = HMI_OK;
+
+int fail(int status)
+{
+    g_last_error = status;
+    return status;
+}
+
+int cuda_fail(cudaError_t e)
+{
+    (void)cudaGetLastError();
+    (void)e;
+    return fail(HMI_ERR_DEVICE);
+}
+
+#define HMI_CUDA(call)                               \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
+constexpr int kPieceChunks = 1024;  // 16-px chunks per CTA piece (16384 px)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool params_valid(const hmi_params &p)
+{
+    if (p.hue_lo >= 1536 || p.hue_hi >= 1536) return false;
+    if (p.bg_k_den < 1 || p.bg_k_den > 15 || p.bg_k_num > 15) return false;
+    if (p.open_iters + p.close_iters > 16) return false;
+    if (p.gain_min_q16 > p.gain_max_q16 || p.gain_max_q16 > (1u << 24)) return false;
+    if (p.click_window > 1024) return false;
+    if (p.reserved[0] || p.reserved[1]) return false;
+    return true;
+}
+
+// Hue arc [lo, hi] (mod 1536) as, per sector, up to two intervals of
+// q = floor(N / 2d) in [0, 512] with h = base - 256 + q; stored as the
+// half-open bounds of N: 2d*a <= N < 2d*(b + 1).  Empty: a = b = 513.
+void hue_intervals(int lo, int hi, int A[3][2], int B[3][2])
+{
+    for (int sec = 0; sec < 3; ++sec) {
+        const int base = 512 * sec;
+        int nint = 0;
+        A[sec][0] = A[sec][1] = B[sec][0] = B[sec][1] = 2 * 513;
+        int q = 0;
+        while (q <= 512 && nint < 2) {
+            auto in_arc = [&](int qq) {
+                int h = ((base - 256 + qq) % 1536 + 1536) % 1536;
+                return lo <= hi ? (h >= lo && h <= hi) : (h >= lo || h <= hi);
+            };
+            while (q <= 512 && !in_arc(q)) ++q;
+            if (q > 512) break;
+            int a = q;
+            while (q <= 512 && in_arc(q)) ++q;
+            A[sec][nint] = 2 * a;
+            B[sec][nint] = 2 * q;   // q is one past the run
+            ++nint;
+        }
+    }
+}
+
+struct Arena {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    }
+};
+
+struct Layout {
+    int w, h, nwords, bh, tiles_x, fpitch;
+    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, bits, comp, parent, count, mask, st,
+        hist, ds, ptr, total;
+};
+
+Layout make_layout(int w, int h, const hmi_params &p)
+{
+    Layout L;
+    L.w = w;
+    L.h = h;
+    L.nwords = (w + 31) / 32;
+    L.bh = (h + 31) / 32;
+    L.tiles_x = (L.nwords + kMorphTW - 1) / kMorphTW;
+    L.fpitch = (int)align_up((size_t)w, 16) * 3;
+    L.npx = (size_t)w * h;
+    const size_t nblk = (size_t)L.bh * L.nwords;
+    const size_t bitrows = (size_t)L.bh * 32 * L.nwords * 4;
+    Arena a;
+    L.frame = a.take((size_t)h * L.fpitch + 64);
+    L.lo = a.take((size_t)h * L.fpitch + 64);
+    L.hi = a.take((size_t)h * L.fpitch + 64);
+    L.S = a.take(L.npx * 3 * 4);
+    L.Q = a.take(L.npx * 3 * 4);
+    L.vmin = a.take(L.npx * 3);
+    L.vmax = a.take(L.npx * 3);
+    L.raw = a.take(bitrows);
+    L.bits = a.take(bitrows);
+    L.comp = a.take(nblk * kSlots * sizeof(Comp));
+    L.parent = a.take(nblk * kSlots * 4);
+    L.count = a.take(nblk * 4);
+    L.mask = a.take(L.npx);
+    L.st = a.take(sizeof(StreamState));
+    L.hist = a.take((size_t)std::max<int>(p.click_window, 1) * 4);
+    L.ds = a.take(sizeof(DevStream));
+    L.ptr = a.take(sizeof(hmi_pointer));
+    L.total = a.off;
+    return L;
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct hmi_batch;
+
+struct hmi_stream {
+    int dev = 0;
+    int w = 0, h = 0;
+    hmi_params p{};
+    Layout L{};
+    uint8_t *arena = nullptr;
+    DevStream ds{};          // host copy
+    DevStream *d_ds = nullptr;
+    StreamState *st = nullptr;
+    uint8_t *d_frame = nullptr, *d_mask = nullptr;
+    uint32_t *d_S = nullptr, *d_Q = nullptr;
+    uint8_t *d_vmin = nullptr, *d_vmax = nullptr;
+    hmi_pointer *d_ptr = nullptr;
+    int learned = 0;
+    int n_learn = 0;
+    cudaStream_t cs = nullptr;
+    hmi_batch *self = nullptr;   // one-stream plan used by hmi_process_frame
+};
+
+struct hmi_batch {
+    int dev = 0;
+    int n = 0;
+    std::vector<hmi_stream *> s;
+    uint8_t *arena = nullptr;     // device tables
+    TickIO *h_io = nullptr;       // pinned mirrors, kRing x n
+    TickIO *d_io = nullptr;       // device copies, kRing x n
+    hmi_pointer *d_ptrs = nullptr;  // n pointers for the synchronous form
+    uint32_t *d_err = nullptr;    // batch error word (device)
+    uint32_t *h_err = nullptr;    // pinned
+    cudaEvent_t slot_ev[kRing] = {};
+    bool slot_used[kRing] = {};
+    int next = 0;
+    BatchDev bd{};
+    cudaStream_t cs = nullptr;    // stream of the synchronous form and of graph capture
+    cudaGraph_t graph_src[kRing] = {};   // kept alive: its event-node handles retarget events
+    cudaGraphExec_t graph[kRing] = {};
+    cudaGraphNode_t ev_node[kRing][2] = {};
+    cudaEvent_t dummy_ev[2] = {};
+    // profiling of the classification kernel
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_max = 0, prof_used = 0;
+};
+
+namespace {
+
+std::mutex g_cache_mu;
+hmi_batch *g_cache = nullptr;    // plan reused by hmi_process_batch
+
+void fill_devstream(hmi_stream *s)
+{
+    DevStream &D = s->ds;
+    const Layout &L = s->L;
+    uint8_t *a = s->arena;
+    D.w = s->w;
+    D.h = s->h;
+    D.nwords = L.nwords;
+    D.bh = L.bh;
+    D.tiles_x = L.tiles_x;
+    D.fpitch = L.fpitch;
+    D.gray_tol = s->p.gray_tol;
+    D.open_iters = s->p.open_iters;
+    D.close_iters = s->p.close_iters;
+    D.gain_min = s->p.gain_min_q16;
+    D.gain_max = s->p.gain_max_q16;
+    D.min_area = s->p.min_area;
+    D.click_on = s->p.click_on_pct;
+    D.click_off = s->p.click_off_pct;
+    D.click_window = s->p.click_window;
+    hue_intervals(s->p.hue_lo, s->p.hue_hi, D.hueA, D.hueB);
+    D.lo = a + L.lo;
+    D.hi = a + L.hi;
+    D.raw = reinterpret_cast<uint32_t *>(a + L.raw);
+    D.bits = reinterpret_cast<uint32_t *>(a + L.bits);
+    D.comp = reinterpret_cast<Comp *>(a + L.comp);
+    D.parent = reinterpret_cast<uint32_t *>(a + L.parent);
+    D.count = reinterpret_cast<uint32_t *>(a + L.count);
+    D.st = reinterpret_cast<StreamState *>(a + L.st);
+    D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
+}
+
+int batch_free(hmi_batch *b)
+{
+    if (!b) return HMI_OK;
+    cudaSetDevice(b->dev);
+    if (b->cs) cudaStreamSynchronize(b->cs);
+    for (int i = 0; i < kRing; ++i) {
+        if (b->slot_ev[i]) cudaEventSynchronize(b->slot_ev[i]);
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+        if (b->graph_src[i]) cudaGraphDestroy(b->graph_src[i]);
+        if (b->slot_ev[i]) cudaEventDestroy(b->slot_ev[i]);
+    }
+    for (auto &e : b->dummy_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : b->prof_ev) cudaEventDestroy(e);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    if (b->arena) cudaFree(b->arena);
+    if (b->h_io) cudaFreeHost(b->h_io);
+    if (b->h_err) cudaFreeHost(b->h_err);
+    delete b;
+    return HMI_OK;
+}
+
+hmi_batch *batch_new(hmi_stream *const *s, int n)
+{
+    if (!s || n < 1 || n > kMaxBatch) {
+        fail(HMI_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!s[i] || s[i]->dev != s[0]->dev) {
+            fail(HMI_ERR_INVALID_ARG);
+            return nullptr;
+        }
+        for (int j = 0; j < i; ++j)
+            if (s[j] == s[i]) {
+                fail(HMI_ERR_INVALID_ARG);
+                return nullptr;
+            }
+    }
+    hmi_batch *b = new (std::nothrow) hmi_batch();
+    if (!b) {
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    b->dev = s[0]->dev;
+    b->n = n;
+    b->s.assign(s, s + n);
+    if (cudaSetDevice(b->dev) != cudaSuccess) {
+        delete b;
+        cuda_fail(cudaErrorInvalidDevice);
+        return nullptr;
+    }
+    // work tables
+    std::vector<unsigned long long> cpre(n + 1, 0);
+    std::vector<uint32_t> tpre(n + 1, 0), bpre(n + 1, 0);
+    std::vector<int4> pieces;
+    for (int i = 0; i < n; ++i) {
+        const Layout &L = s[i]->L;
+        const int chunks = L.h * 2 * L.nwords;
+        cpre[i + 1] = cpre[i] + (unsigned long long)chunks;
+        tpre[i + 1] = tpre[i] + (uint32_t)(L.bh * L.tiles_x);
+        bpre[i + 1] = bpre[i] + (uint32_t)(L.bh * L.nwords);
+        for (int c = 0; c < chunks; c += kPieceChunks)
+            pieces.push_back(make_int4(i, c, std::min(chunks, c + kPieceChunks), 0));
+    }
+    Arena a;
+    const size_t o_ds = a.take(sizeof(DevStream) * n);
+    const size_t o_c = a.take(sizeof(unsigned long long) * (n + 1));
+    const size_t o_t = a.take(sizeof(uint32_t) * (n + 1));
+    const size_t o_b = a.take(sizeof(uint32_t) * (n + 1));
+    const size_t o_done = a.take(sizeof(uint32_t) * 4);
+    const size_t o_p = a.take(sizeof(int4) * pieces.size());
+    const size_t o_io = a.take(sizeof(TickIO) * n * kRing);
+    const size_t o_ptr = a.take(sizeof(hmi_pointer) * n);
+    const size_t o_err = a.take(sizeof(uint32_t));
+    bool ok = cudaMalloc(&b->arena, a.off) == cudaSuccess &&
+              cudaMallocHost(&b->h_io, sizeof(TickIO) * n * kRing) == cudaSuccess &&
+              cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int i = 0; ok && i < kRing; ++i)
+        ok = cudaEventCreateWithFlags(&b->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < 2; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        batch_free(b);
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    std::vector<DevStream> ds(n);
+    for (int i = 0; i < n; ++i) ds[i] = s[i]->ds;
+    uint8_t *A = b->arena;
+    ok = cudaMemset(A, 0, a.off) == cudaSuccess &&
+         cudaMemcpy(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A + o_c, cpre.data(), sizeof(unsigned long long) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A + o_t, tpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A + o_b, bpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A + o_p, pieces.data(), sizeof(int4) * pieces.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        batch_free(b);
+        fail(HMI_ERR_DEVICE);
+        return nullptr;
+    }
+    memset(b->h_io, 0, sizeof(TickIO) * n * kRing);
+    *b->h_err = 0;
+    b->d_io = reinterpret_cast<TickIO *>(A + o_io);
+    b->d_ptrs = reinterpret_cast<hmi_pointer *>(A + o_ptr);
+    b->d_err = reinterpret_cast<uint32_t *>(A + o_err);
+    BatchDev &bd = b->bd;
+    bd.ds = reinterpret_cast<const DevStream *>(A + o_ds);
+    bd.io = b->d_io;
+    bd.n = n;
+    bd.total_chunks = cpre[n];
+    bd.total_tiles = tpre[n];
+    bd.total_blocks = bpre[n];
+    bd.chunk_prefix = reinterpret_cast<const unsigned long long *>(A + o_c);
+    bd.tile_prefix = reinterpret_cast<const uint32_t *>(A + o_t);
+    bd.block_prefix = reinterpret_cast<const uint32_t *>(A + o_b);
+    bd.done = reinterpret_cast<uint32_t *>(A + o_done);
+    bd.pieces = reinterpret_cast<const int4 *>(A + o_p);
+    bd.npieces = (int)pieces.size();
+    bd.err = b->d_err;
+    return b;
+}
+
+// Kernels of one tick on cs with the slot's pointer table; event nodes (or
+// plain event records) bracket the classification kernel.
+cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1,
+                         bool capture)
+{
+    BatchDev bd = b->bd;
+    bd.io = b->d_io + (size_t)slot * b->n;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(const_cast<TickIO *>(bd.io), b->h_io + (size_t)slot * b->n,
+                             sizeof(TickIO) * b->n, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+        return e;
+    if ((e = launch_luma(bd, cs)) != cudaSuccess) return e;
+    if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
+        return e;
+    if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;
+    if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
+        return e;
+    if ((e = launch_morph_cc(bd, cs)) != cudaSuccess) return e;
+    if ((e = launch_merge(bd, cs)) != cudaSuccess) return e;
+    if ((e = launch_resolve(bd, cs)) != cudaSuccess) return e;
+    return launch_pointer(bd, cs);
+}
+
+int build_graph(hmi_batch *b, int slot)
+{
+    cudaGraph_t g = nullptr;
+    HMI_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_tick(b, slot, b->cs, b->dummy_ev[0], b->dummy_ev[1], true);
+    cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e != cudaSuccess ? e : e2);
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    std::vector<cudaGraphNode_t> evn;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        cudaGraphNodeGetType(nd, &t);
+        if (t == cudaGraphNodeTypeEventRecord) evn.push_back(nd);
+    }
+    for (auto nd : evn) {
+        cudaEvent_t ev;
+        cudaGraphEventRecordNodeGetEvent(nd, &ev);
+        if (ev == b->dummy_ev[0]) b->ev_node[slot][0] = nd;
+        if (ev == b->dummy_ev[1]) b->ev_node[slot][1] = nd;
+    }
+    if (!b->ev_node[slot][0] || !b->ev_node[slot][1]) {
+        cudaGraphDestroy(g);
+        return fail(HMI_ERR_DEVICE);
+    }
+    e = cudaGraphInstantiate(&b->graph[slot], g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return cuda_fail(e);
+    }
+    b->graph_src[slot] = g;
+    return HMI_OK;
+}
+
+// Fill slot pointers for one tick.  Frames and masks not usable in place are
+// staged through the stream's own buffers; returns which masks need a copy out.
+int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *const *masks,
+                 bool async_mode, cudaStream_t cs, std::vector<int> *mask_copy)
+{
+    TickIO *io = b->h_io + (size_t)slot * b->n;
+    for (int i = 0; i < b->n; ++i) {
+        hmi_stream *s = b->s[i];
+        const uint8_t *f = frames[i];
+        if (!f) return fail(HMI_ERR_INVALID_ARG);
+        const bool dev = is_device_ptr(f);
+        if (async_mode && !dev) return fail(HMI_ERR_INVALID_ARG);
+        if (dev && (s->w % 16) == 0 && (reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
+            io[i].frame = f;
+            io[i].frame_pitch = 3LL * s->w;
+        } else {
+            HMI_CUDA(cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, f, 3 * (size_t)s->w, 3 * (size_t)s->w,
+                                       s->h, cudaMemcpyDefault, cs));
+            io[i].frame = s->d_frame;
+            io[i].frame_pitch = s->L.fpitch;
+        }
+        uint8_t *m = (masks != nullptr) ? masks[i] : nullptr;
+        if (m == nullptr) {
+            io[i].mask = nullptr;
+        } else if (is_device_ptr(m)) {
+            io[i].mask = m;
+        } else {
+            if (async_mode) return fail(HMI_ERR_INVALID_ARG);
+            io[i].mask = s->d_mask;
+            if (mask_copy) mask_copy->push_back(i);
+        }
+    }
+    return HMI_OK;
+}
+
+int acquire_slot(hmi_batch *b)
+{
+    const int slot = b->next;
+    b->next = (b->next + 1) % kRing;
+    if (b->slot_used[slot]) {
+        cudaError_t e = cudaEventSynchronize(b->slot_ev[slot]);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return slot;
+}
+
+int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = b->prof_used < b->prof_max;
+    if (prof) {
+        e0 = b->prof_ev[2 * b->prof_used];
+        e1 = b->prof_ev[2 * b->prof_used + 1];
+        b->prof_used++;
+    }
+    if (use_graph) {
+        if (!b->graph[slot]) {
+            int st = build_graph(b, slot);
+            if (st != HMI_OK) return st;
+        }
+        HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][0],
+                                                      e0 ? e0 : b->dummy_ev[0]));
+        HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][1],
+                                                      e1 ? e1 : b->dummy_ev[1]));
+        HMI_CUDA(cudaGraphLaunch(b->graph[slot], cs));
+    } else {
+        HMI_CUDA(enqueue_tick(b, slot, cs, e0, e1, false));
+    }
+    HMI_CUDA(cudaEventRecord(b->slot_ev[slot], cs));
+    b->slot_used[slot] = true;
+    return HMI_OK;
+}
+
+bool all_learned(hmi_batch *b)
+{
+    for (auto s : b->s)
+        if (!s->learned) return false;
+    return true;
+}
+
+int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+               hmi_pointer *ptrs)
+{
+    if (!b || !frames) return fail(HMI_ERR_INVALID_ARG);
+    if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    int slot = acquire_slot(b);
+    if (slot < 0) return slot;
+    std::vector<int> mcopy;
+    int st = prepare_slot(b, slot, frames, masks, false, b->cs, &mcopy);
+    if (st != HMI_OK) return st;
+    TickIO *io = b->h_io + (size_t)slot * b->n;
+    for (int i = 0; i < b->n; ++i) io[i].ptr_out = b->d_ptrs + i;
+    st = run_tick(b, slot, b->cs, false);
+    if (st != HMI_OK) return st;
+    for (int i : mcopy) {
+        hmi_stream *s = b->s[i];
+        HMI_CUDA(cudaMemcpyAsync(masks[i], s->d_mask, (size_t)s->w * s->h, cudaMemcpyDefault, b->cs));
+    }
+    if (ptrs) HMI_CUDA(cudaMemcpyAsync(ptrs, b->d_ptrs, sizeof(hmi_pointer) * b->n, cudaMemcpyDefault, b->cs));
+    HMI_CUDA(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->cs));
+    HMI_CUDA(cudaStreamSynchronize(b->cs));
+    if (*b->h_err) {
+        *b->h_err = 0;
+        HMI_CUDA(cudaMemset(b->d_err, 0, sizeof(uint32_t)));
+        return fail(HMI_ERR_DEVICE_TIMEOUT);
+    }
+    return HMI_OK;
+}
+
+int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                hmi_pointer *ptrs, void *cuda_stream, int use_graph)
+{
+    if (!b || !frames) return fail(HMI_ERR_INVALID_ARG);
+    if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
+    if (ptrs && !is_device_ptr(ptrs)) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int slot = acquire_slot(b);
+    if (slot < 0) return slot;
+    int st = prepare_slot(b, slot, frames, masks, true, cs, nullptr);
+    if (st != HMI_OK) return st;
+    TickIO *io = b->h_io + (size_t)slot * b->n;
+    for (int i = 0; i < b->n; ++i) io[i].ptr_out = ptrs ? ptrs + i : nullptr;
+    return run_tick(b, slot, cs, use_graph != 0);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int hmi_last_error(void) { return g_last_error; }
+
+const char *hmi_status_string(int status)
+{
+    switch (status) {
+    case HMI_OK: return "ok";
+    case HMI_ERR_INVALID_ARG: return "invalid argument";
+    case HMI_ERR_NOT_LEARNED: return "background not learned";
+    case HMI_ERR_NO_MEMORY: return "out of memory or admission refused";
+    case HMI_ERR_DEVICE: return "CUDA error";
+    case HMI_ERR_DEVICE_TIMEOUT: return "device-side bounded wait or loop gave up";
+    default: return "unknown status";
+    }
+}
+
+int hmi_default_params(hmi_params *p)
+{
+    if (!p) return fail(HMI_ERR_INVALID_ARG);
+    memset(p, 0, sizeof(*p));
+    p->gain_min_q16 = 32768;
+    p->gain_max_q16 = 131072;
+    p->min_area = 50;
+    p->hue_lo = 1472;
+    p->hue_hi = 256;
+    p->click_window = 30;
+    p->gray_tol = 15;
+    p->bg_margin = 2;
+    p->bg_k_num = 5;
+    p->bg_k_den = 2;
+    p->open_iters = 1;
+    p->close_iters = 1;
+    p->click_on_pct = 80;
+    p->click_off_pct = 90;
+    return HMI_OK;
+}
+
+size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p)
+{
+    hmi_params d;
+    hmi_default_params(&d);
+    const hmi_params &pp = p ? *p : d;
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim || !params_valid(pp)) return 0;
+    return make_layout(w, h, pp).total;
+}
+
+hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p)
+{
+    hmi_params d;
+    hmi_default_params(&d);
+    const hmi_params &pp = p ? *p : d;
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim || !params_valid(pp)) {
+        fail(HMI_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    hmi_stream *s = new (std::nothrow) hmi_stream();
+    if (!s) {
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    s->w = w;
+    s->h = h;
+    s->p = pp;
+    s->L = make_layout(w, h, pp);
+    if (cudaGetDevice(&s->dev) != cudaSuccess) {
+        delete s;
+        cuda_fail(cudaErrorNoDevice);
+        return nullptr;
+    }
+    if (cudaMalloc(&s->arena, s->L.total) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete s;
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    uint8_t *a = s->arena;
+    s->d_frame = a + s->L.frame;
+    s->d_mask = a + s->L.mask;
+    s->d_S = reinterpret_cast<uint32_t *>(a + s->L.S);
+    s->d_Q = reinterpret_cast<uint32_t *>(a + s->L.Q);
+    s->d_vmin = a + s->L.vmin;
+    s->d_vmax = a + s->L.vmax;
+    s->st = reinterpret_cast<StreamState *>(a + s->L.st);
+    s->d_ds = reinterpret_cast<DevStream *>(a + s->L.ds);
+    s->d_ptr = reinterpret_cast<hmi_pointer *>(a + s->L.ptr);
+    fill_devstream(s);
+    bool ok = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMemset(s->arena, 0, s->L.total) == cudaSuccess &&
+              cudaMemcpy(s->d_ds, &s->ds, sizeof(DevStream), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (ok) {
+        hmi_stream *one = s;
+        s->self = batch_new(&one, 1);
+        ok = s->self != nullptr;
+    }
+    if (!ok) {
+        (void)cudaGetLastError();
+        if (s->cs) cudaStreamDestroy(s->cs);
+        cudaFree(s->arena);
+        delete s;
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    return s;
+}
+
+void hmi_destroy_stream(hmi_stream *s)
+{
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        if (g_cache && std::find(g_cache->s.begin(), g_cache->s.end(), s) != g_cache->s.end()) {
+            batch_free(g_cache);
+            g_cache = nullptr;
+        }
+    }
+    cudaSetDevice(s->dev);
+    batch_free(s->self);
+    if (s->cs) {
+        cudaStreamSynchronize(s->cs);
+        cudaStreamDestroy(s->cs);
+    }
+    cudaFree(s->arena);
+    delete s;
+}
+
+int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
+{
+    if (!s || !frames || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    const long long npx = (long long)s->w * s->h;
+    const size_t fbytes = (size_t)npx * 3;
+    HMI_CUDA(cudaDeviceSynchronize());   // no tick of this stream may be in flight
+    // reset the learning luma total
+    HMI_CUDA(cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), s->cs));
+    if (is_device_ptr(frames)) {
+        HMI_CUDA(launch_learn_accum(frames, n, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, 1, s->st, s->cs));
+    } else {
+        // host frames: stream through a bounded staging buffer
+        const int per = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (256u << 20) / fbytes));
+        uint8_t *stage = nullptr;
+        if (cudaMalloc(&stage, fbytes * per) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(HMI_ERR_NO_MEMORY);
+        }
+        int status = HMI_OK;
+        for (int i = 0; i < n && status == HMI_OK; i += per) {
+            const int k = std::min(per, n - i);
+            if (cudaMemcpyAsync(stage, frames + (size_t)i * fbytes, fbytes * k, cudaMemcpyHostToDevice, s->cs) != cudaSuccess ||
+                launch_learn_accum(stage, k, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, i == 0, s->st, s->cs) != cudaSuccess ||
+                cudaStreamSynchronize(s->cs) != cudaSuccess)
+                status = cuda_fail(cudaErrorUnknown);
+        }
+        cudaFree(stage);
+        if (status != HMI_OK) return status;
+    }
+    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.lo, 0, (size_t)s->h * s->L.fpitch, s->cs));
+    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.hi, 0, (size_t)s->h * s->L.fpitch, s->cs));
+    HMI_CUDA(launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
+                               s->p.bg_margin, s->w, s->h, s->L.fpitch, s->arena + s->L.lo,
+                               s->arena + s->L.hi, s->st, s->cs));
+    HMI_CUDA(cudaStreamSynchronize(s->cs));
+    s->learned = 1;
+    s->n_learn = n;
+    return HMI_OK;
+}
+
+int hmi_process_frame(hmi_stream *s, const uint8_t *frame, uint8_t *mask_out, hmi_pointer *pointer_out)
+{
+    if (!s || !frame) return fail(HMI_ERR_INVALID_ARG);
+    uint8_t *const masks[1] = {mask_out};
+    return batch_sync(s->self, &frame, masks, pointer_out);
+}
+
+int hmi_process_frame_async(hmi_stream *s, const uint8_t *frame, uint8_t *mask_out,
+                            hmi_pointer *pointer_out, void *cuda_stream)
+{
+    if (!s || !frame) return fail(HMI_ERR_INVALID_ARG);
+    uint8_t *const masks[1] = {mask_out};
+    return batch_async(s->self, &frame, masks, pointer_out, cuda_stream, 0);
+}
+
+hmi_batch *hmi_batch_create(hmi_stream *const *s, int n) { return batch_new(s, n); }
+
+void hmi_batch_destroy(hmi_batch *b) { batch_free(b); }
+
+int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                      hmi_pointer *ptrs)
+{
+    return batch_sync(b, frames, masks, ptrs);
+}
+
+int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                            hmi_pointer *ptrs, void *cuda_stream, int use_graph)
+{
+    return batch_async(b, frames, masks, ptrs, cuda_stream, use_graph);
+}
+
+int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
+                      uint8_t *const *masks, hmi_pointer *ptrs)
+{
+    if (!s || n < 1 || n > kMaxBatch || !frames) return fail(HMI_ERR_INVALID_ARG);
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    if (!g_cache || g_cache->n != n || !std::equal(g_cache->s.begin(), g_cache->s.end(), s)) {
+        batch_free(g_cache);
+        g_cache = batch_new(s, n);
+        if (!g_cache) return g_last_error;
+    }
+    return batch_sync(g_cache, frames, masks, ptrs);
+}
+
+int hmi_batch_profile(hmi_batch *b, int max_ticks)
+{
+    if (!b || max_ticks < 0 || max_ticks > 1000000) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    HMI_CUDA(cudaDeviceSynchronize());
+    for (auto e : b->prof_ev) cudaEventDestroy(e);
+    b->prof_ev.assign(2 * (size_t)max_ticks, nullptr);
+    for (auto &e : b->prof_ev) HMI_CUDA(cudaEventCreate(&e));
+    b->prof_max = max_ticks;
+    b->prof_used = 0;
+    return HMI_OK;
+}
+
+int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms)
+{
+    if (!b || !ticks || !total_ms) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    double tot = 0.0;
+    for (int i = 0; i < b->prof_used; ++i) {
+        HMI_CUDA(cudaEventSynchronize(b->prof_ev[2 * i + 1]));
+        float ms = 0.f;
+        HMI_CUDA(cudaEventElapsedTime(&ms, b->prof_ev[2 * i], b->prof_ev[2 * i + 1]));
+        tot += ms;
+    }
+    *ticks = b->prof_used;
+    *total_ms = tot;
+    return HMI_OK;
+}
+
+int hmi_get_background_stats(const hmi_stream *s, float *mean, float *std)
+{
+    if (!s) return fail(HMI_ERR_INVALID_ARG);
+    if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
+    if (!mean && !std) return HMI_OK;
+    HMI_CUDA(cudaSetDevice(s->dev));
+    const long long count = (long long)s->w * s->h * 3;
+    const size_t bytes = (size_t)count * sizeof(float);
+    float *dm = nullptr, *dd = nullptr;
+    const bool mdev = mean && is_device_ptr(mean), sdev = std && is_device_ptr(std);
+    if (mean && !mdev && cudaMalloc(&dm, bytes) != cudaSuccess) return fail(HMI_ERR_NO_MEMORY);
+    if (std && !sdev && cudaMalloc(&dd, bytes) != cudaSuccess) {
+        cudaFree(dm);
+        return fail(HMI_ERR_NO_MEMORY);
+    }
+    cudaError_t e = launch_stats(s->d_S, s->d_Q, s->n_learn, count, mean ? (mdev ? mean : dm) : nullptr,
+                                 std ? (sdev ? std : dd) : nullptr, s->cs);
+    if (e == cudaSuccess && dm) e = cudaMemcpyAsync(mean, dm, bytes, cudaMemcpyDeviceToHost, s->cs);
+    if (e == cudaSuccess && dd) e = cudaMemcpyAsync(std, dd, bytes, cudaMemcpyDeviceToHost, s->cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+    cudaFree(dm);
+    cudaFree(dd);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return HMI_OK;
+}
+
+int hmi_get_labels(const hmi_stream *s, int32_t *labels)
+{
+    if (!s || !labels) return fail(HMI_ERR_INVALID_ARG);
+    if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());   // the last tick may have run on any stream
+    const size_t bytes = (size_t)s->w * s->h * sizeof(int32_t);
+    const bool dev = is_device_ptr(labels);
+    int32_t *d = labels;
+    if (!dev && cudaMalloc(&d, bytes) != cudaSuccess) return fail(HMI_ERR_NO_MEMORY);
+    cudaError_t e = launch_labels(s->d_ds, s->ds, d, s->cs);
+    if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(labels, d, bytes, cudaMemcpyDeviceToHost, s->cs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
+    if (!dev) cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return HMI_OK;
+}
+
+int hmi_export_background(const hmi_stream *s, uint32_t *S, uint32_t *Q, uint8_t *vmin,
+                          uint8_t *vmax, uint8_t *lo, uint8_t *hi, uint64_t *syref, int *n)
+{
+    if (!s) return fail(HMI_ERR_INVALID_ARG);
+    if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());
+    const size_t cnt = (size_t)s->w * s->h * 3;
+    if (S) HMI_CUDA(cudaMemcpy(S, s->d_S, cnt * 4, cudaMemcpyDefault));
+    if (Q) HMI_CUDA(cudaMemcpy(Q, s->d_Q, cnt * 4, cudaMemcpyDefault));
+    if (vmin) HMI_CUDA(cudaMemcpy(vmin, s->d_vmin, cnt, cudaMemcpyDefault));
+    if (vmax) HMI_CUDA(cudaMemcpy(vmax, s->d_vmax, cnt, cudaMemcpyDefault));
+    if (lo) HMI_CUDA(cudaMemcpy2D(lo, 3 * (size_t)s->w, s->arena + s->L.lo, s->L.fpitch, 3 * (size_t)s->w, s->h, cudaMemcpyDefault));
+    if (hi) HMI_CUDA(cudaMemcpy2D(hi, 3 * (size_t)s->w, s->arena + s->L.hi, s->L.fpitch, 3 * (size_t)s->w, s->h, cudaMemcpyDefault));
+    if (syref) HMI_CUDA(cudaMemcpy(syref, &s->st->syref, sizeof(uint64_t), cudaMemcpyDefault));
+    if (n) *n = s->n_learn;
+    return HMI_OK;
+}
+
+int hmi_import_background(hmi_stream *s, const uint32_t *S, const uint32_t *Q, const uint8_t *vmin,
+                          const uint8_t *vmax, int n, uint64_t syref)
+{
+    if (!s || !S || !Q || !vmin || !vmax || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
+    if (syref > (uint64_t)255 * s->w * s->h) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());
+    const size_t cnt = (size_t)s->w * s->h * 3;
+    HMI_CUDA(cudaMemcpy(s->d_S, S, cnt * 4, cudaMemcpyDefault));
+    HMI_CUDA(cudaMemcpy(s->d_Q, Q, cnt * 4, cudaMemcpyDefault));
+    HMI_CUDA(cudaMemcpy(s->d_vmin, vmin, cnt, cudaMemcpyDefault));
+    HMI_CUDA(cudaMemcpy(s->d_vmax, vmax, cnt, cudaMemcpyDefault));
+    const unsigned long long tot = (unsigned long long)syref * (unsigned long long)n;
+    HMI_CUDA(cudaMemcpy(&s->st->learn_luma, &tot, sizeof(tot), cudaMemcpyHostToDevice));
+    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.lo, 0, (size_t)s->h * s->L.fpitch, s->cs));
+    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.hi, 0, (size_t)s->h * s->L.fpitch, s->cs));
+    HMI_CUDA(launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
+                               s->p.bg_margin, s->w, s->h, s->L.fpitch, s->arena + s->L.lo,
+                               s->arena + s->L.hi, s->st, s->cs));
+    HMI_CUDA(cudaStreamSynchronize(s->cs));
+    s->learned = 1;
+    s->n_learn = n;
+    return HMI_OK;
+}
+
+int hmi_get_last_gain(const hmi_stream *s, uint32_t *gain_q16)
+{
+    if (!s || !gain_q16) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());
+    HMI_CUDA(cudaMemcpy(gain_q16, &s->st->gain, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return HMI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,417 @@
+// hmi_frame.cu -- per-pixel kernels of a tick:
+//   k_luma      frame luma sum per stream; the last CTA turns the sums into the
+//               brightness gains (Sec. 2 "the brightness is also corrected",
+//               Sec. 3.2 luminosity filter)
+//   k_classify  gain, background band test, gray test and hue test, ANDed into
+//               one bit per pixel (Sec. 3.1 (i)-(iii) and the merging step)
+//   k_morph_cc  opening/closing on the bit mask (Sec. 3.1 "erosion and
+//               dilatation"), the 0/1 mask bytes, and the 8-connected
+//               components of each 32x32 block with their statistics (Mouse
+//               module, Sec. 2)
+// All three are pure integer/bit work and bound by HBM bandwidth; nothing here
+// is a dense contraction, so no tensor-core path is used.
+#include "hmi_ccfill.cuh"
+#include "hmi_internal.cuh"
+
+namespace hmi {
+
+// 16-byte global load that keeps the line out of L1 and marks it evict-first
+// in L2 (a read-once stream).
+__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+{
+    return __ldcs(p);
+}
+
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
+{
+    return (w[b >> 2] >> (8 * (b & 3))) & 0xffu;
+}
+
+// Integer BT.601 luma, (77 R + 150 G + 29 B + 128) >> 8.
+__device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b)
+{
+    return (77u * r + 150u * g + 29u * b + 128u) >> 8;
+}
+
+// ---------------------------------------------------------------------------
+// k_luma: one CTA per piece (a contiguous chunk range of one stream).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
+{
+    __shared__ unsigned long long red[kThreads / 32];
+    __shared__ bool is_last;
+    const int tid = threadIdx.x;
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const int s = piece.x;
+        const DevStream &D = b.ds[s];
+        const TickIO io = b.io[s];
+        const int w = D.w, cpr = 2 * D.nwords;
+        unsigned long long acc = 0;
+        for (int u = piece.y + tid; u < piece.z; u += blockDim.x) {
+            const int y = u / cpr, j = u - y * cpr;
+            const int x0 = j * kChunkPx;
+            if (x0 >= w) continue;
+            const uint4 *src = reinterpret_cast<const uint4 *>(io.frame + (long long)y * io.frame_pitch + 3 * x0);
+            uint32_t f[12];
+            uint4 a = __ldg(src), c = __ldg(src + 1), e = __ldg(src + 2);
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+            f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+            f[8] = e.x; f[9] = e.y; f[10] = e.z; f[11] = e.w;
+            const int npx = min(kChunkPx, w - x0);
+            uint32_t sum = 0;
+#pragma unroll
+            for (int k = 0; k < kChunkPx; ++k) {
+                uint32_t v = luma8(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2));
+                sum += (k < npx) ? v : 0u;
+            }
+            acc += sum;
+        }
+        // CTA reduction, one atomic per piece
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+            atomicAdd(&D.st->sy, t);
+        }
+        __syncthreads();
+    }
+    // the last CTA to finish computes every stream's gain
+    __threadfence();
+    if (tid == 0) is_last = (atomicAdd(&b.done[0], 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int s = tid; s < b.n; s += blockDim.x) {
+        const DevStream &D = b.ds[s];
+        StreamState *st = D.st;
+        unsigned long long sy = *(volatile unsigned long long *)&st->sy;
+        unsigned long long syref = st->syref;
+        unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
+        if (g < D.gain_min) g = D.gain_min;
+        if (g > D.gain_max) g = D.gain_max;
+        st->gain = (uint32_t)g;
+        st->sy = 0;
+    }
+    if (tid == 0) b.done[0] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_classify
+// ---------------------------------------------------------------------------
+struct ClassP {
+    uint32_t g;
+    int tol;
+    int A[3][2], B[3][2];
+};
+
+// One pixel: 1 iff it is foreground for the background band (some channel
+// outside [lo, hi]), not gray (max - min >= S) and of skin hue, all on the
+// gain-corrected values c' = min(255, (c g + 2^15) >> 16).
+// The hue test compares N = 512 (t + d) + d against d-scaled interval ends,
+// which is exact for h = base - 256 + floor(N / 2d) without any division.
+__device__ __forceinline__ uint32_t classify_px(uint32_t r0, uint32_t g0, uint32_t b0,
+                                                uint32_t lr, uint32_t lg, uint32_t lb,
+                                                uint32_t hr, uint32_t hg, uint32_t hb,
+                                                const ClassP &P)
+{
+    const int r = (int)min((r0 * P.g + 32768u) >> 16, 255u);
+    const int g = (int)min((g0 * P.g + 32768u) >> 16, 255u);
+    const int b = (int)min((b0 * P.g + 32768u) >> 16, 255u);
+    const bool inband = (r >= (int)lr) & (r <= (int)hr) & (g >= (int)lg) & (g <= (int)hg) &
+                        (b >= (int)lb) & (b <= (int)hb);
+    const int mx = max(r, max(g, b));
+    const int mn = min(r, min(g, b));
+    const int d = mx - mn;
+    int t, a0, b0_, a1, b1;
+    if (r == mx) {
+        t = g - b; a0 = P.A[0][0]; b0_ = P.B[0][0]; a1 = P.A[0][1]; b1 = P.B[0][1];
+    } else if (g == mx) {
+        t = b - r; a0 = P.A[1][0]; b0_ = P.B[1][0]; a1 = P.A[1][1]; b1 = P.B[1][1];
+    } else {
+        t = r - g; a0 = P.A[2][0]; b0_ = P.B[2][0]; a1 = P.A[2][1]; b1 = P.B[2][1];
+    }
+    const int N = 512 * (t + d) + d;
+    const bool skin = (d > 0) & (((N >= d * a0) & (N < d * b0_)) | ((N >= d * a1) & (N < d * b1)));
+    return (uint32_t)((!inband) & (d >= P.tol) & skin);
+}
+
+__global__ void __launch_bounds__(kThreads) k_classify(BatchDev b)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        ClassP P;
+        P.g = D.st->gain;
+        P.tol = D.gray_tol;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            P.A[i][0] = D.hueA[i][0]; P.A[i][1] = D.hueA[i][1];
+            P.B[i][0] = D.hueB[i][0]; P.B[i][1] = D.hueB[i][1];
+        }
+        const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
+        const uint8_t *lo = D.lo, *hi = D.hi;
+        uint32_t *raw = D.raw;
+        // warp-uniform loop so that chunk pairs can combine with a shuffle
+        for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
+            const int u = base + lane;
+            uint32_t bits = 0;
+            int y = 0, j = 0;
+            if (u < piece.z) {
+                y = u / cpr;
+                j = u - y * cpr;
+                const int x0 = j * kChunkPx;
+                if (x0 < w) {
+                    const uint4 *fs = reinterpret_cast<const uint4 *>(io.frame + (long long)y * io.frame_pitch + 3 * x0);
+                    const uint4 *ls = reinterpret_cast<const uint4 *>(lo + (long long)y * fpitch + 3 * x0);
+                    const uint4 *hs = reinterpret_cast<const uint4 *>(hi + (long long)y * fpitch + 3 * x0);
+                    uint32_t f[12], l[12], h[12];
+                    {
+                        uint4 a = ld_stream(fs), c = ld_stream(fs + 1), e = ld_stream(fs + 2);
+                        f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+                        f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+                        f[8] = e.x; f[9] = e.y; f[10] = e.z; f[11] = e.w;
+                    }
+                    {
+                        uint4 a = ld_stream(ls), c = ld_stream(ls + 1), e = ld_stream(ls + 2);
+                        l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
+                        l[4] = c.x; l[5] = c.y; l[6] = c.z; l[7] = c.w;
+                        l[8] = e.x; l[9] = e.y; l[10] = e.z; l[11] = e.w;
+                    }
+                    {
+                        uint4 a = ld_stream(hs), c = ld_stream(hs + 1), e = ld_stream(hs + 2);
+                        h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
+                        h[4] = c.x; h[5] = c.y; h[6] = c.z; h[7] = c.w;
+                        h[8] = e.x; h[9] = e.y; h[10] = e.z; h[11] = e.w;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kChunkPx; ++k) {
+                        const int q = 3 * k;
+                        bits |= classify_px(byte_of(f, q), byte_of(f, q + 1), byte_of(f, q + 2),
+                                            byte_of(l, q), byte_of(l, q + 1), byte_of(l, q + 2),
+                                            byte_of(h, q), byte_of(h, q + 1), byte_of(h, q + 2), P)
+                                << k;
+                    }
+                    const int npx = w - x0;
+                    if (npx < kChunkPx) bits &= (1u << npx) - 1u;
+                }
+            }
+            const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
+            if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_morph_cc: one CTA per tile of 32 rows x kMorphTW words.
+// ---------------------------------------------------------------------------
+constexpr int kMR = kMorphRows + 2 * kMaxHalo;   // buffer rows
+constexpr int kMW = kMorphTW + 2;                // buffer words (one halo word each side)
+
+struct MorphGeo {
+    int y0, k0, HR, R, h, w, nwords;
+    uint32_t lastmask;
+    __device__ uint32_t valid(int r, int k) const
+    {
+        const int y = y0 - HR + r, kw = k0 - 1 + k;
+        if (y < 0 || y >= h || kw < 0 || kw >= nwords) return 0u;
+        return (kw == nwords - 1) ? lastmask : 0xffffffffu;
+    }
+};
+
+__global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
+{
+    __shared__ uint32_t buf[2][kMR][kMW];
+    __shared__ int s_sh;
+    const int tid = threadIdx.x;
+    const unsigned tile = blockIdx.x;
+    if (tid == 0) {
+        int lo = 0, hi = b.n;   // largest s with tile_prefix[s] <= tile
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (b.tile_prefix[mid] <= tile) lo = mid; else hi = mid;
+        }
+        s_sh = lo;
+    }
+    __syncthreads();
+    const int s = s_sh;
+    const DevStream &D = b.ds[s];
+    const TickIO io = b.io[s];
+    const int lt = (int)(tile - b.tile_prefix[s]);
+    const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
+    MorphGeo G;
+    G.HR = 2 * (D.open_iters + D.close_iters);
+    G.R = kMorphRows + 2 * G.HR;
+    G.y0 = ty * kMorphRows;
+    G.k0 = tx * kMorphTW;
+    G.h = D.h;
+    G.w = D.w;
+    G.nwords = D.nwords;
+    G.lastmask = (D.w & 31) ? ((1u << (D.w & 31)) - 1u) : 0xffffffffu;
+    const int ncell = G.R * kMW;
+
+    for (int i = tid; i < ncell; i += blockDim.x) {
+        const int r = i / kMW, k = i - r * kMW;
+        const int y = G.y0 - G.HR + r, kw = G.k0 - 1 + k;
+        buf[0][r][k] = (y >= 0 && y < G.h && kw >= 0 && kw < G.nwords) ? D.raw[(long long)y * G.nwords + kw] : 0u;
+    }
+    __syncthreads();
+
+    // open_iters x (erode, dilate), then close_iters x (dilate, erode);
+    // out-of-image pixels are neutral for each operator
+    const int nops = 2 * (D.open_iters + D.close_iters);
+    int cur = 0;
+    for (int op = 0; op < nops; ++op) {
+        const bool ero = (op < 2 * D.open_iters) ? ((op & 1) == 0) : (((op - 2 * D.open_iters) & 1) == 1);
+        for (int i = tid; i < ncell; i += blockDim.x) {
+            const int r = i / kMW, k = i - r * kMW;
+            uint32_t acc = ero ? 0xffffffffu : 0u;
+#pragma unroll
+            for (int dr = -1; dr <= 1; ++dr) {
+                const int rr = r + dr;
+                uint32_t v[3];
+#pragma unroll
+                for (int dk = -1; dk <= 1; ++dk) {
+                    const int kk = k + dk;
+                    uint32_t x;
+                    if (rr < 0 || rr >= G.R || kk < 0 || kk >= kMW) {
+                        x = ero ? 0xffffffffu : 0u;
+                    } else {
+                        const uint32_t vm = G.valid(rr, kk);
+                        const uint32_t raw = buf[cur][rr][kk];
+                        x = ero ? (raw | ~vm) : (raw & vm);
+                    }
+                    v[dk + 1] = x;
+                }
+                if (ero) {
+                    acc &= v[1] & ((v[1] << 1) | (v[0] >> 31)) & ((v[1] >> 1) | (v[2] << 31));
+                } else {
+                    acc |= v[1] | (v[1] << 1) | (v[0] >> 31) | (v[1] >> 1) | (v[2] << 31);
+                }
+            }
+            buf[cur ^ 1][r][k] = acc;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+
+    // final bits of the tile interior: global bit mask, mask bytes, and a
+    // copy in the other buffer for the component pass
+    uint32_t (*fin)[kMW] = buf[cur ^ 1];
+    for (int i = tid; i < kMorphRows * kMorphTW; i += blockDim.x) {
+        const int r = i / kMorphTW, k = i - r * kMorphTW;
+        const int rb = G.HR + r, kb = 1 + k;
+        const uint32_t v = buf[cur][rb][kb] & G.valid(rb, kb);
+        fin[r][k] = v;
+        const int y = G.y0 + r, kw = G.k0 + k;
+        if (kw < G.nwords) {
+            D.bits[(long long)y * G.nwords + kw] = v;
+            if (io.mask != nullptr && y < G.h) {
+                uint8_t *dst = io.mask + (long long)y * G.w + kw * kWordPx;
+                const int npx = min(kWordPx, G.w - kw * kWordPx);
+                if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+                    uint32_t q[8];
+#pragma unroll
+                    for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((v >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
+                    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                    __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
+                    __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
+                } else {
+                    for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((v >> x) & 1u);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // 8-connected components of each 32x32 block of the tile (one warp each)
+    const int wid = tid >> 5, lane = tid & 31;
+    for (int k = wid; k < kMorphTW; k += blockDim.x >> 5) {
+        const int kw = G.k0 + k;
+        if (kw >= G.nwords) continue;
+        const int blk = ty * G.nwords + kw;
+        uint32_t m = fin[lane][k];
+        Comp *out = D.comp + (long long)blk * kSlots;
+        uint32_t *parent = D.parent + (long long)blk * kSlots;
+        const int xb = kw * kWordPx, yb = G.y0;
+        int ncomp = 0;
+        while (__any_sync(kFull, m != 0u)) {
+            int r0, c0;
+            const uint32_t c = cc_extract_first(m, lane, &r0, &c0);
+            m &= ~c;
+            const uint32_t pc = (uint32_t)__popc(c);
+            const uint32_t area = __reduce_add_sync(kFull, pc);
+            const uint32_t sx = __reduce_add_sync(kFull, pc * (uint32_t)xb + bit_index_sum(c));
+            const uint32_t sy = __reduce_add_sync(kFull, pc * (uint32_t)(yb + lane));
+            const unsigned rows = __ballot_sync(kFull, c != 0u);
+            const uint32_t xmin = __reduce_min_sync(kFull, c ? (uint32_t)(__ffs(c) - 1) : 32u);
+            const uint32_t xmax = __reduce_max_sync(kFull, c ? (uint32_t)(31 - __clz(c)) : 0u);
+            const uint32_t top = __shfl_sync(kFull, c, 0);
+            const uint32_t bot = __shfl_sync(kFull, c, 31);
+            const uint32_t left = __ballot_sync(kFull, c & 1u);
+            const uint32_t right = __ballot_sync(kFull, c >> 31);
+            if (ncomp < kSlots) {
+                uint32_t *o = reinterpret_cast<uint32_t *>(out + ncomp);
+                uint32_t val = 0;
+                switch (lane) {
+                case 0: val = (uint32_t)(yb + r0) * (uint32_t)G.w + (uint32_t)(xb + c0); break;
+                case 1: val = area; break;
+                case 2: val = sx; break;
+                case 3: val = 0; break;
+                case 4: val = sy; break;
+                case 5: val = 0; break;
+                case 6: val = (uint32_t)xb + xmin; break;
+                case 7: val = (uint32_t)(yb + __ffs(rows) - 1); break;
+                case 8: val = (uint32_t)xb + xmax; break;
+                case 9: val = (uint32_t)(yb + 31 - __clz(rows)); break;
+                case 10: val = top; break;
+                case 11: val = bot; break;
+                case 12: val = left; break;
+                case 13: val = right; break;
+                default: val = 0; break;
+                }
+                if (lane < 16) o[lane] = val;
+                if (lane == 0) parent[ncomp] = (uint32_t)ncomp + (uint32_t)blk * kSlots;
+            }
+            ++ncomp;
+        }
+        if (lane == 0) {
+            if (ncomp > kSlots) atomicOr(&D.st->err, kErrSlots);
+            D.count[blk] = (uint32_t)min(ncomp, kSlots);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static int grid_for_pieces(int npieces)
+{
+    return npieces > 0 ? npieces : 1;
+}
+
+cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs)
+{
+    k_luma<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs)
+{
+    k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs)
+{
+    if (b.total_tiles == 0) return cudaSuccess;
+    k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace hmi

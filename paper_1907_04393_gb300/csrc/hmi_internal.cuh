@@ -1,0 +1,133 @@
+// hmi_internal.cuh -- device data structures and launch entry points shared by
+// the CUDA translation units of libhmi.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hmi.h"
+
+namespace hmi {
+
+// ---------------------------------------------------------------------------
+// Geometry constants
+// ---------------------------------------------------------------------------
+constexpr int kChunkPx = 16;       // pixels per classification unit (48 frame bytes)
+constexpr int kWordPx = 32;        // pixels per mask bit word
+constexpr int kBlock = 32;         // connected-component block: 32 rows x 32 px
+constexpr int kSlots = 256;        // max 8-connected components in a 32x32 block
+constexpr int kMorphTW = 8;        // morphology tile width in words (256 px)
+constexpr int kMorphRows = 32;     // morphology tile height (one CC block row)
+constexpr int kMaxHalo = 32;       // 2 * (open_iters + close_iters) <= 32
+constexpr int kMaxDim = 8192;
+constexpr int kMaxBatch = 4096;
+constexpr uint32_t kLoopLimit = 1u << 22;  // bound on every device-side retry loop
+
+// device error flags (StreamState::err / batch error word)
+constexpr uint32_t kErrUnionLoop = 1u;
+constexpr uint32_t kErrFindLoop = 2u;
+constexpr uint32_t kErrSlots = 4u;
+constexpr uint32_t kErrRoot = 8u;
+
+// One 8-connected component of a 32x32 block, later the accumulator of its
+// whole component when it is the root.  64 bytes.
+struct __align__(16) Comp {
+    uint32_t key;                 // smallest linear index y*w + x of its pixels
+    uint32_t area;
+    unsigned long long sx, sy;    // sums of x and y
+    int32_t x0, y0, x1, y1;       // inclusive box
+    uint32_t top, bot, left, right;  // its pixels on the block's 4 borders
+    uint32_t pad[2];
+};
+static_assert(sizeof(Comp) == 64, "Comp layout");
+
+// Mutable per-stream state in device memory.
+struct __align__(16) StreamState {
+    unsigned long long sy;        // luma sum of the frame being processed (0 between frames)
+    unsigned long long syref;     // reference luma of the background
+    unsigned long long best;      // packed (area, ~key) argmax (0 between frames)
+    unsigned long long learn_luma;  // luma total over the learning frames
+    uint32_t gain;                // Q16 gain of the last frame
+    uint32_t err;                 // kErr* flags
+    int32_t click;
+    int32_t hist_count;
+    int32_t hist_head;
+    int32_t frames;               // frames processed since learning
+    hmi_pointer last;             // pointer of the last frame
+};
+
+// Read-only description of a stream as the kernels see it.
+struct DevStream {
+    int w, h;
+    int nwords;                   // ceil(w / 32): bit words per row == CC blocks per block-row
+    int bh;                       // ceil(h / 32): CC block rows
+    int tiles_x;                  // ceil(nwords / kMorphTW)
+    int fpitch;                   // bytes per row of the band (and of the staging frame)
+    int gray_tol;
+    int open_iters, close_iters;
+    uint32_t gain_min, gain_max, min_area;
+    int click_on, click_off, click_window;
+    // hue arc per sector (0: R max, 1: G max, 2: B max) as two half-open
+    // intervals of N = 512 (t + d) + d:  d*A <= N < d*B
+    int hueA[3][2], hueB[3][2];
+    const uint8_t *lo, *hi;       // background band, pitch fpitch, RGB interleaved
+    uint32_t *raw;                // raw AND mask bits, (bh*32) x nwords words
+    uint32_t *bits;               // mask bits after morphology, same layout
+    Comp *comp;                   // bh*nwords*kSlots records
+    uint32_t *parent;             // union-find parent per record
+    uint32_t *count;              // components per CC block
+    StreamState *st;
+    uint32_t *hist;               // click_window areas (ring)
+};
+
+// Per-tick pointers of one stream.
+struct TickIO {
+    const uint8_t *frame;         // frame of this tick
+    long long frame_pitch;        // bytes between rows of `frame`
+    uint8_t *mask;                // h*w mask out (device) or null
+    hmi_pointer *ptr_out;         // pointer out (device) or null
+};
+
+// Everything a tick's kernels need, passed by value.
+struct BatchDev {
+    const DevStream *ds;
+    const TickIO *io;
+    int n;
+    unsigned long long total_chunks;          // sum h * 2 * nwords
+    uint32_t total_tiles;                     // sum bh * tiles_x
+    uint32_t total_blocks;                    // sum bh * nwords
+    const unsigned long long *chunk_prefix;   // n + 1 entries
+    const uint32_t *tile_prefix;              // n + 1
+    const uint32_t *block_prefix;             // n + 1
+    uint32_t *done;                           // last-block counters [4]
+    const int4 *pieces;                       // (stream, chunk begin, chunk end, 0)
+    int npieces;                              // pieces of the per-pixel kernels
+    uint32_t *err;                            // batch error word: OR of the streams' flags
+};
+
+// Threads per CTA of every kernel of a tick.
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_merge(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_resolve(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_pointer(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
+                          cudaStream_t cs);
+
+cudaError_t launch_learn_accum(const uint8_t *frames, int nf, long long npx, uint32_t *S,
+                               uint32_t *Q, uint8_t *vmin, uint8_t *vmax, int first,
+                               StreamState *st, cudaStream_t cs);
+cudaError_t launch_learn_band(const uint32_t *S, const uint32_t *Q, const uint8_t *vmin,
+                              const uint8_t *vmax, int n, int kn, int kd, int delta, int w,
+                              int h, int fpitch, uint8_t *lo, uint8_t *hi, StreamState *st,
+                              cudaStream_t cs);
+cudaError_t launch_stats(const uint32_t *S, const uint32_t *Q, int n, long long count,
+                         float *mean, float *stdv, cudaStream_t cs);
+
+}  // namespace hmi

@@ -1,0 +1,320 @@
+"""Python binding of libhmi.so: the C ABI of include/hmi.h, same names.
+
+Argument marshalling only.  Every step of the path runs in the library's CUDA
+kernels; this module has no compute of its own and no fallback: if the
+library is missing or cannot be loaded, importing the binding raises.
+
+Buffers are passed as raw addresses.  ``_addr`` accepts a numpy array (host
+memory), a torch tensor (host or CUDA memory, via ``data_ptr``) or an int.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HMI_OK = 0
+HMI_ERR_INVALID_ARG = -1
+HMI_ERR_NOT_LEARNED = -2
+HMI_ERR_NO_MEMORY = -3
+HMI_ERR_DEVICE = -4
+HMI_ERR_DEVICE_TIMEOUT = -5
+
+
+class hmi_params(ctypes.Structure):
+    _fields_ = [("gain_min_q16", ctypes.c_uint32), ("gain_max_q16", ctypes.c_uint32),
+                ("min_area", ctypes.c_uint32), ("hue_lo", ctypes.c_uint16),
+                ("hue_hi", ctypes.c_uint16), ("click_window", ctypes.c_uint16),
+                ("gray_tol", ctypes.c_uint8), ("bg_margin", ctypes.c_uint8),
+                ("bg_k_num", ctypes.c_uint8), ("bg_k_den", ctypes.c_uint8),
+                ("open_iters", ctypes.c_uint8), ("close_iters", ctypes.c_uint8),
+                ("click_on_pct", ctypes.c_uint8), ("click_off_pct", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8 * 2)]
+
+
+class hmi_pointer(ctypes.Structure):
+    _fields_ = [("valid", ctypes.c_int32), ("click", ctypes.c_int32),
+                ("x", ctypes.c_float), ("y", ctypes.c_float), ("area", ctypes.c_uint32),
+                ("x0", ctypes.c_int32), ("y0", ctypes.c_int32),
+                ("x1", ctypes.c_int32), ("y1", ctypes.c_int32), ("label", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+POINTER_DTYPE = np.dtype([(k, np.dtype(t._type_)) for k, t in hmi_pointer._fields_])
+assert POINTER_DTYPE.itemsize == ctypes.sizeof(hmi_pointer) == 40
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+
+# name -> (restype, argtypes), one entry per function of include/hmi.h
+SIGNATURES = {
+    "hmi_default_params": (_I, [ctypes.POINTER(hmi_params)]),
+    "hmi_create_stream": (_P, [_I, _I, ctypes.POINTER(hmi_params)]),
+    "hmi_destroy_stream": (None, [_P]),
+    "hmi_learn_background": (_I, [_P, _P, _I]),
+    "hmi_process_frame": (_I, [_P, _P, _P, _P]),
+    "hmi_process_frame_async": (_I, [_P, _P, _P, _P, _P]),
+    "hmi_process_batch": (_I, [_P, _I, _P, _P, _P]),
+    "hmi_batch_create": (_P, [_P, _I]),
+    "hmi_batch_destroy": (None, [_P]),
+    "hmi_batch_process": (_I, [_P, _P, _P, _P]),
+    "hmi_batch_process_async": (_I, [_P, _P, _P, _P, _P, _I]),
+    "hmi_batch_profile": (_I, [_P, _I]),
+    "hmi_batch_profile_read": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "hmi_get_background_stats": (_I, [_P, _P, _P]),
+    "hmi_get_labels": (_I, [_P, _P]),
+    "hmi_export_background": (_I, [_P, _P, _P, _P, _P, _P, _P,
+                                   ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_I)]),
+    "hmi_import_background": (_I, [_P, _P, _P, _P, _P, _I, ctypes.c_uint64]),
+    "hmi_get_last_gain": (_I, [_P, ctypes.POINTER(ctypes.c_uint32)]),
+    "hmi_stream_device_bytes": (ctypes.c_size_t, [_I, _I, ctypes.POINTER(hmi_params)]),
+    "hmi_last_error": (_I, []),
+    "hmi_status_string": (ctypes.c_char_p, [_I]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libhmi.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libhmi.so not found at {_build.LIB}; run the build first")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HmiError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load().hmi_status_string(status).decode()
+        super().__init__(f"{what}: {msg} ({status})")
+
+
+def _check(status: int, what: str) -> int:
+    if status != HMI_OK:
+        raise HmiError(status, what)
+    return status
+
+
+def _addr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "buffers must be contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):          # torch.Tensor
+        assert x.is_contiguous(), "buffers must be contiguous"
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _ptr_array(items) -> ctypes.Array:
+    arr = (ctypes.c_void_p * len(items))()
+    for i, x in enumerate(items):
+        arr[i] = _addr(x)
+    return arr
+
+
+# --------------------------------------------------------------------------- #
+# Same-name wrappers of the C ABI                                             #
+# --------------------------------------------------------------------------- #
+def hmi_default_params(**over) -> hmi_params:
+    p = hmi_params()
+    _check(load().hmi_default_params(ctypes.byref(p)), "hmi_default_params")
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def hmi_create_stream(w: int, h: int, params: hmi_params | None = None) -> int:
+    s = load().hmi_create_stream(w, h, ctypes.byref(params) if params is not None else None)
+    if not s:
+        raise HmiError(load().hmi_last_error(), "hmi_create_stream")
+    return s
+
+
+def hmi_destroy_stream(s: int) -> None:
+    load().hmi_destroy_stream(s)
+
+
+def hmi_learn_background(s: int, frames, n: int) -> None:
+    _check(load().hmi_learn_background(s, _addr(frames), n), "hmi_learn_background")
+
+
+def hmi_process_frame(s: int, frame, mask_out=None, pointer_out: hmi_pointer | None = None) -> None:
+    _check(load().hmi_process_frame(s, _addr(frame), _addr(mask_out),
+                                    ctypes.byref(pointer_out) if pointer_out is not None else None),
+           "hmi_process_frame")
+
+
+def hmi_process_frame_async(s: int, frame, mask_out, pointer_out, cuda_stream: int) -> None:
+    _check(load().hmi_process_frame_async(s, _addr(frame), _addr(mask_out), _addr(pointer_out),
+                                          cuda_stream), "hmi_process_frame_async")
+
+
+def hmi_process_batch(streams, frames, masks=None, ptrs=None) -> None:
+    n = len(streams)
+    sa = (ctypes.c_void_p * n)(*streams)
+    fa = _ptr_array(frames)
+    ma = _ptr_array(masks) if masks is not None else None
+    _check(load().hmi_process_batch(sa, n, fa, ma, _addr(ptrs)), "hmi_process_batch")
+
+
+def hmi_batch_create(streams) -> int:
+    n = len(streams)
+    sa = (ctypes.c_void_p * n)(*streams)
+    b = load().hmi_batch_create(sa, n)
+    if not b:
+        raise HmiError(load().hmi_last_error(), "hmi_batch_create")
+    return b
+
+
+def hmi_batch_destroy(b: int) -> None:
+    load().hmi_batch_destroy(b)
+
+
+def hmi_batch_process(b: int, frames, masks=None, ptrs=None) -> None:
+    fa = _ptr_array(frames)
+    ma = _ptr_array(masks) if masks is not None else None
+    _check(load().hmi_batch_process(b, fa, ma, _addr(ptrs)), "hmi_batch_process")
+
+
+def hmi_batch_process_async(b: int, frames, masks, ptrs, cuda_stream: int, use_graph: bool) -> None:
+    fa = _ptr_array(frames)
+    ma = _ptr_array(masks) if masks is not None else None
+    _check(load().hmi_batch_process_async(b, fa, ma, _addr(ptrs), cuda_stream, int(use_graph)),
+           "hmi_batch_process_async")
+
+
+def hmi_batch_profile(b: int, max_ticks: int) -> None:
+    _check(load().hmi_batch_profile(b, max_ticks), "hmi_batch_profile")
+
+
+def hmi_batch_profile_read(b: int) -> tuple[int, float]:
+    t, ms = ctypes.c_int(), ctypes.c_double()
+    _check(load().hmi_batch_profile_read(b, ctypes.byref(t), ctypes.byref(ms)), "hmi_batch_profile_read")
+    return t.value, ms.value
+
+
+def hmi_get_background_stats(s: int, mean, std) -> None:
+    _check(load().hmi_get_background_stats(s, _addr(mean), _addr(std)), "hmi_get_background_stats")
+
+
+def hmi_get_labels(s: int, labels) -> None:
+    _check(load().hmi_get_labels(s, _addr(labels)), "hmi_get_labels")
+
+
+def hmi_export_background(s: int, S=None, Q=None, vmin=None, vmax=None, lo=None, hi=None):
+    """Returns (syref, n); fills whichever arrays are given."""
+    sy, n = ctypes.c_uint64(), ctypes.c_int()
+    _check(load().hmi_export_background(s, _addr(S), _addr(Q), _addr(vmin), _addr(vmax), _addr(lo),
+                                        _addr(hi), ctypes.byref(sy), ctypes.byref(n)),
+           "hmi_export_background")
+    return sy.value, n.value
+
+
+def hmi_import_background(s: int, S, Q, vmin, vmax, n: int, syref: int) -> None:
+    _check(load().hmi_import_background(s, _addr(S), _addr(Q), _addr(vmin), _addr(vmax), n, syref),
+           "hmi_import_background")
+
+
+def hmi_get_last_gain(s: int) -> int:
+    g = ctypes.c_uint32()
+    _check(load().hmi_get_last_gain(s, ctypes.byref(g)), "hmi_get_last_gain")
+    return g.value
+
+
+def hmi_stream_device_bytes(w: int, h: int, params: hmi_params | None = None) -> int:
+    return load().hmi_stream_device_bytes(w, h, ctypes.byref(params) if params is not None else None)
+
+
+def hmi_last_error() -> int:
+    return load().hmi_last_error()
+
+
+def hmi_status_string(status: int) -> str:
+    return load().hmi_status_string(status).decode()
+
+
+# --------------------------------------------------------------------------- #
+# Convenience object over the same calls                                      #
+# --------------------------------------------------------------------------- #
+class Stream:
+    """One camera stream: ``learn(frames)`` once, then ``process(frame)``."""
+
+    def __init__(self, w: int, h: int, **params):
+        self.w, self.h = int(w), int(h)
+        self.params = hmi_default_params(**params)
+        self.handle = hmi_create_stream(self.w, self.h, self.params)
+
+    def close(self) -> None:
+        if self.handle:
+            hmi_destroy_stream(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def learn(self, frames) -> None:
+        n = frames.shape[0]
+        hmi_learn_background(self.handle, frames, n)
+
+    def process(self, frame, mask: bool = True):
+        """Host round trip: returns (mask uint8 (h, w) or None, pointer dict)."""
+        m = np.empty((self.h, self.w), np.uint8) if mask else None
+        p = hmi_pointer()
+        hmi_process_frame(self.handle, frame, m, p)
+        return m, p.as_dict()
+
+    def labels(self) -> np.ndarray:
+        out = np.empty((self.h, self.w), np.int32)
+        hmi_get_labels(self.handle, out)
+        return out
+
+    def stats(self):
+        mean = np.empty((self.h, self.w, 3), np.float32)
+        std = np.empty((self.h, self.w, 3), np.float32)
+        hmi_get_background_stats(self.handle, mean, std)
+        return mean, std
+
+    def last_gain(self) -> int:
+        return hmi_get_last_gain(self.handle)
+
+    def export(self) -> dict:
+        shp = (self.h, self.w, 3)
+        out = dict(S=np.empty(shp, np.uint32), Q=np.empty(shp, np.uint32),
+                   vmin=np.empty(shp, np.uint8), vmax=np.empty(shp, np.uint8),
+                   lo=np.empty(shp, np.uint8), hi=np.empty(shp, np.uint8))
+        out["syref"], out["n"] = hmi_export_background(self.handle, **out)
+        return out
+
+    def import_background(self, S, Q, vmin, vmax, n: int, syref: int) -> None:
+        c = np.ascontiguousarray
+        hmi_import_background(self.handle, c(S, np.uint32), c(Q, np.uint32), c(vmin, np.uint8),
+                              c(vmax, np.uint8), n, syref)

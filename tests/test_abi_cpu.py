@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function that include/hmi.h declares, and its pure host calls behave."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1907_04393_gb300 import hmi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hmi.h")).read()
+    return sorted(set(re.findall(r"HMI_API[^;(]*?\b(hmi_\w+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = hmi.load()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in hmi.h but not exported"
+    assert set(names) == set(hmi.SIGNATURES), "binding and header disagree"
+
+
+def test_struct_layouts():
+    assert ctypes.sizeof(hmi.hmi_params) == 28
+    assert ctypes.sizeof(hmi.hmi_pointer) == 40
+
+
+def test_defaults_and_status_strings():
+    p = hmi.hmi_default_params()
+    assert (p.gray_tol, p.hue_lo, p.hue_hi, p.bg_margin, p.bg_k_num, p.bg_k_den) == (15, 1472, 256, 2, 5, 2)
+    assert (p.open_iters, p.close_iters, p.gain_min_q16, p.gain_max_q16) == (1, 1, 32768, 131072)
+    assert (p.min_area, p.click_on_pct, p.click_off_pct, p.click_window) == (50, 80, 90, 30)
+    assert hmi.hmi_status_string(0) == "ok"
+    for st in (-1, -2, -3, -4, -5):
+        assert hmi.hmi_status_string(st) not in ("ok", "unknown status")
+    assert hmi.load().hmi_default_params(None) == hmi.HMI_ERR_INVALID_ARG
+    assert hmi.hmi_last_error() == hmi.HMI_ERR_INVALID_ARG
+
+
+def test_device_bytes_accounting():
+    b320 = hmi.hmi_stream_device_bytes(320, 240)
+    b640 = hmi.hmi_stream_device_bytes(640, 480)
+    assert 0 < b320 < b640
+    assert 3.5 < b640 / b320 < 4.5
+    assert hmi.hmi_stream_device_bytes(0, 10) == 0
+    assert hmi.hmi_stream_device_bytes(8193, 10) == 0
+    bad = hmi.hmi_default_params(hue_lo=1536)
+    assert hmi.hmi_stream_device_bytes(32, 32, bad) == 0
+    bad = hmi.hmi_default_params(bg_k_den=0)
+    assert hmi.hmi_stream_device_bytes(32, 32, bad) == 0
+    bad = hmi.hmi_default_params(open_iters=9, close_iters=8)
+    assert hmi.hmi_stream_device_bytes(32, 32, bad) == 0
+
+
+def test_invalid_arguments_fail_on_host():
+    lib = hmi.load()
+    assert lib.hmi_learn_background(None, None, 1) == hmi.HMI_ERR_INVALID_ARG
+    assert lib.hmi_process_frame(None, None, None, None) == hmi.HMI_ERR_INVALID_ARG
+    assert lib.hmi_process_batch(None, 0, None, None, None) == hmi.HMI_ERR_INVALID_ARG
+    assert lib.hmi_create_stream(0, 5, None) is None
+    assert hmi.hmi_last_error() == hmi.HMI_ERR_INVALID_ARG
+    assert lib.hmi_batch_create(None, 1) is None
+
+
+def test_create_without_gpu_reports_an_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert hmi.load().hmi_create_stream(64, 48, None) is None
+    assert hmi.hmi_last_error() in (hmi.HMI_ERR_DEVICE, hmi.HMI_ERR_NO_MEMORY)

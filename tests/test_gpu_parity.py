@@ -1,0 +1,412 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: masks, labels, blob area and box bit-exact; gain exact; background
+mean/std and pointer centroid within 1e-5 relative (FP32; in practice they are
+equal, each being one correctly rounded IEEE operation on exact integers).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1907_04393_gb300 import hmi, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+SKIN = (200, 120, 90)     # hue 70 units, chroma 110: skin for the default arc
+GRAY = (128, 128, 128)
+RNG = np.random.default_rng(1907)
+
+
+def _dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def assert_pointer(pg: dict, po: dict, what=""):
+    for k in ("valid", "click", "area", "x0", "y0", "x1", "y1", "label"):
+        assert pg[k] == po[k], f"{what} pointer.{k}: gpu {pg[k]} oracle {po[k]}"
+    for k in ("x", "y"):
+        assert pg[k] == pytest.approx(po[k], rel=RTOL, abs=1e-6), f"{what} pointer.{k}"
+
+
+def check_frame(g: hmi.Stream, o: oracle.OracleStream, frame: np.ndarray, dev=False, what=""):
+    src = _dev(frame) if dev else frame
+    m_g, p_g = g.process(src)
+    l_g = g.labels()
+    m_o, l_o, p_o, gain_o = o.process(frame)
+    assert g.last_gain() == gain_o, f"{what} gain"
+    if not np.array_equal(m_g, m_o):
+        bad = np.argwhere(m_g != m_o)
+        raise AssertionError(f"{what} mask differs at {len(bad)} px, first {bad[:5].tolist()}")
+    if not np.array_equal(l_g, l_o):
+        bad = np.argwhere(l_g != l_o)
+        raise AssertionError(f"{what} labels differ at {len(bad)} px, first {bad[:5].tolist()}")
+    assert_pointer(p_g, p_o, what)
+    return p_g
+
+
+def pair(w, h, **params):
+    return hmi.Stream(w, h, **params), oracle.OracleStream(w, h, **params)
+
+
+def learn_both(g, o, frames, dev=False):
+    g.learn(_dev(frames) if dev else frames)
+    o.learn(frames)
+
+
+def black_background(g, o, gain=65536):
+    """Background band [0, delta]: every non-black pixel is foreground for the
+    background test; gain pinned to `gain` via the clamp."""
+    shp = (g.h, g.w, 3)
+    z32 = np.zeros(shp, np.uint32)
+    z8 = np.zeros(shp, np.uint8)
+    g.import_background(z32, z32, z8, z8, 1, 0)
+    o.set_background(z32, z32, z8, z8, 1, 0)
+
+
+def pattern_frame(pat: np.ndarray) -> np.ndarray:
+    f = np.empty(pat.shape + (3,), np.uint8)
+    f[...] = GRAY
+    f[pat.astype(bool)] = SKIN
+    return f
+
+
+# --------------------------------------------------------------------------- #
+# Learning: statistics and band                                                #
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("w,h,n", [(320, 240, 30), (37, 29, 5), (1, 1, 3), (100, 3, 1), (33, 65, 17)])
+def test_learned_stats_and_band(w, h, n):
+    frames = RNG.integers(0, 256, size=(n, h, w, 3), dtype=np.uint8)
+    if w == 320:
+        frames = synth.learn_frames(1)
+    g, o = pair(w, h)
+    learn_both(g, o, frames)
+    mean_g, std_g = g.stats()
+    mean_o, std_o = o.stats()
+    np.testing.assert_allclose(mean_g, mean_o, rtol=RTOL)
+    np.testing.assert_allclose(std_g, std_o, rtol=RTOL, atol=1e-6)
+    ex = g.export()
+    assert np.array_equal(ex["S"], o.S) and np.array_equal(ex["Q"], o.Q)
+    assert np.array_equal(ex["vmin"], o.vmin) and np.array_equal(ex["vmax"], o.vmax)
+    assert np.array_equal(ex["lo"], o.lo) and np.array_equal(ex["hi"], o.hi)
+    assert ex["syref"] == o.syref and ex["n"] == n
+    g.close()
+
+
+@pytest.mark.parametrize("kn,kd,delta", [(0, 1, 0), (5, 2, 2), (15, 1, 0), (1, 15, 7), (3, 1, 255)])
+def test_band_parameters(kn, kd, delta):
+    frames = RNG.integers(0, 256, size=(9, 40, 48, 3), dtype=np.uint8)
+    frames[:, :20] = RNG.integers(100, 110, size=(9, 20, 48, 3), dtype=np.uint8)
+    g, o = pair(48, 40, bg_k_num=kn, bg_k_den=kd, bg_margin=delta)
+    learn_both(g, o, frames, dev=True)
+    ex = g.export()
+    assert np.array_equal(ex["lo"], o.lo) and np.array_equal(ex["hi"], o.hi)
+    g.close()
+
+
+# --------------------------------------------------------------------------- #
+# Per-pixel stages on the whole colour cube                                    #
+# --------------------------------------------------------------------------- #
+def _cube():
+    v = np.arange(256, dtype=np.uint8)
+    r, gg, b = np.meshgrid(v, v, v, indexing="ij")
+    return np.stack([r, gg, b], -1).reshape(4096, 4096, 3)
+
+
+@pytest.mark.parametrize("gain,tol,hue_lo,hue_hi", [(65536, 15, 1472, 256), (65536, 0, 100, 900),
+                                                    (50000, 40, 1500, 20), (90000, 1, 0, 1535),
+                                                    (131072, 9, 700, 700)])
+def test_exhaustive_colour_cube(gain, tol, hue_lo, hue_hi):
+    cube = _cube()
+    kw = dict(gain_min_q16=gain, gain_max_q16=gain, gray_tol=tol, hue_lo=hue_lo, hue_hi=hue_hi,
+              open_iters=0, close_iters=0, bg_margin=0)
+    g, o = pair(4096, 4096, **kw)
+    black_background(g, o)
+    m_g, _ = g.process(_dev(cube))
+    assert g.last_gain() == gain
+    corr = oracle.apply_gain(cube, gain)
+    z = np.zeros_like(cube)
+    _, _, _, raw = oracle.fg(corr, z, z, tol, hue_lo, hue_hi)
+    assert np.array_equal(m_g, raw)
+    g.close()
+
+
+# --------------------------------------------------------------------------- #
+# Morphology and components on designed masks                                  #
+# --------------------------------------------------------------------------- #
+SIZES = [(1, 1), (40, 1), (1, 40), (31, 33), (32, 32), (33, 31), (64, 64), (97, 65), (257, 129),
+         (300, 200), (1000, 37), (37, 1000)]
+
+
+@pytest.mark.parametrize("w,h", SIZES)
+@pytest.mark.parametrize("oi,ci", [(0, 0), (1, 1), (2, 0), (0, 3)])
+def test_random_masks(w, h, oi, ci):
+    g, o = pair(w, h, open_iters=oi, close_iters=ci, gain_min_q16=65536, gain_max_q16=65536,
+                min_area=1)
+    black_background(g, o)
+    for p in (0.1, 0.45, 0.6, 0.9):
+        pat = (RNG.random((h, w)) < p).astype(np.uint8)
+        check_frame(g, o, pattern_frame(pat), dev=(w % 16 == 0), what=f"{w}x{h} p={p}")
+    g.close()
+
+
+def _spiral(n):
+    sp = np.zeros((n, n), np.uint8)
+    y, x, dy, dx, L = n // 2, n // 2, 0, 1, 1
+    sp[y, x] = 1
+    while L <= n:
+        for _ in range(2):
+            for _ in range(L):
+                y, x = y + dy, x + dx
+                if 0 <= y < n and 0 <= x < n:
+                    sp[y, x] = 1
+            dy, dx = dx, -dy
+        L += 2
+    return sp
+
+
+def _structured(h, w):
+    yy, xx = np.mgrid[0:h, 0:w]
+    pats = {
+        "empty": np.zeros((h, w), np.uint8),
+        "full": np.ones((h, w), np.uint8),
+        "checker": ((yy + xx) % 2).astype(np.uint8),
+        "grid2": ((yy % 2 == 0) & (xx % 2 == 0)).astype(np.uint8),
+        "diag": ((yy - xx) % 32 == 0).astype(np.uint8),
+        "antidiag": ((yy + xx) % 31 == 0).astype(np.uint8),
+        "hstripes": (yy % 3 == 0).astype(np.uint8),
+        "vstripes": (xx % 5 == 1).astype(np.uint8),
+        "corners": np.zeros((h, w), np.uint8),
+        "blockcorner": (((yy % 32 == 31) & (xx % 32 == 31)) | ((yy % 32 == 0) & (xx % 32 == 0))).astype(np.uint8),
+        "blockcorner2": (((yy % 32 == 31) & (xx % 32 == 0)) | ((yy % 32 == 0) & (xx % 32 == 31))).astype(np.uint8),
+    }
+    c = pats["corners"]
+    c[0, 0] = c[0, w - 1] = c[h - 1, 0] = c[h - 1, w - 1] = 1
+    sp = _spiral(max(h, w))[:h, :w]
+    pats["spiral"] = sp
+    u = np.zeros((h, w), np.uint8)
+    u[3:h - 3, 5] = 1
+    u[3:h - 3, w - 6] = 1
+    u[h - 4, 5:w - 5] = 1
+    pats["ushape"] = u
+    return pats
+
+
+@pytest.mark.parametrize("w,h", [(96, 96), (130, 70), (64, 33)])
+def test_structured_masks(w, h):
+    g, o = pair(w, h, open_iters=0, close_iters=0, gain_min_q16=65536, gain_max_q16=65536,
+                min_area=1)
+    black_background(g, o)
+    for name, pat in _structured(h, w).items():
+        check_frame(g, o, pattern_frame(pat), what=f"{name} {w}x{h}")
+    g.close()
+
+
+def test_ellipse_pointer_exact():
+    w, h = 640, 480
+    g, o = pair(w, h, open_iters=1, close_iters=1, gain_min_q16=65536, gain_max_q16=65536)
+    black_background(g, o)
+    yy, xx = np.mgrid[0:h, 0:w]
+    for cx, cy, a, b in [(320, 240, 50, 70), (100.5, 60.5, 20, 30), (600, 400, 39.5, 60.2)]:
+        pat = ((((xx - cx) / a) ** 2 + ((yy - cy) / b) ** 2) <= 1).astype(np.uint8)
+        p = check_frame(g, o, pattern_frame(pat), what="ellipse")
+        assert p["x"] == cx and p["y"] == cy
+    g.close()
+
+
+# --------------------------------------------------------------------------- #
+# The synthetic workloads                                                      #
+# --------------------------------------------------------------------------- #
+def test_config1_all_frames():
+    g, o = pair(*synth.shape(1))
+    learn_both(g, o, synth.learn_frames(1))
+    for t in range(synth.RUN_FRAMES[1]):
+        check_frame(g, o, synth.run_frame(1, 0, t), dev=(t % 2 == 0), what=f"cfg1 t={t}")
+    g.close()
+
+
+def test_config2_click_sequence():
+    g, o = pair(*synth.shape(2))
+    learn_both(g, o, synth.learn_frames(2), dev=True)
+    clicks = []
+    for t in range(0, 90):
+        p = check_frame(g, o, synth.run_frame(2, 0, t), dev=True, what=f"cfg2 t={t}")
+        clicks.append(p["click"])
+    assert 0 < sum(clicks) < len(clicks)
+    g.close()
+
+
+def test_config3_full_hd_sampled():
+    g, o = pair(*synth.shape(3))
+    learn_both(g, o, synth.learn_frames(3), dev=True)
+    for t in (0, 1, 2, 50, 51, 333, 599):
+        check_frame(g, o, synth.run_frame(3, 0, t), dev=True, what=f"cfg3 t={t}")
+    g.close()
+
+
+def _batch_streams(cfg, idx):
+    gs, os_ = [], []
+    for i in idx:
+        w, h = synth.shape(cfg, i)
+        g, o = pair(w, h)
+        lf = synth.learn_frames(cfg, i)
+        learn_both(g, o, lf, dev=True)
+        gs.append(g)
+        os_.append(o)
+    return gs, os_
+
+
+def _compare_batch(gs, os_, frames, masks_g, ptrs_g, what):
+    for i, (g, o) in enumerate(zip(gs, os_)):
+        m_o, l_o, p_o, _ = o.process(frames[i])
+        m_g = masks_g[i].cpu().numpy() if hasattr(masks_g[i], "cpu") else masks_g[i]
+        assert np.array_equal(m_g, m_o), f"{what} stream {i} mask"
+        assert np.array_equal(g.labels(), l_o), f"{what} stream {i} labels"
+        assert_pointer(ptrs_g[i], p_o, f"{what} stream {i}")
+
+
+def test_batch_config4_sync_async_graph():
+    """64 mixed-resolution streams in one launch per stage; each stream's result
+    equals its result alone (the oracle processes every stream alone)."""
+    n = synth.num_streams(4)
+    gs, os_ = _batch_streams(4, range(n))
+    handles = [g.handle for g in gs]
+    b = hmi.hmi_batch_create(handles)
+    try:
+        for t in range(4):
+            frames = [synth.run_frame(4, i, t) for i in range(n)]
+            mode = ("sync", "async", "graph", "graph")[t]
+            if mode == "sync":
+                masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+                ptrs = np.zeros(n, hmi.POINTER_DTYPE)
+                hmi.hmi_batch_process(b, frames, masks, ptrs)
+                plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(n)]
+            else:
+                dframes = [_dev(f) for f in frames]
+                dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+                dptrs = torch.zeros(n * 40, dtype=torch.uint8, device="cuda")
+                s = torch.cuda.current_stream()
+                hmi.hmi_batch_process_async(b, dframes, dmasks, dptrs.data_ptr(), s.cuda_stream,
+                                            mode == "graph")
+                torch.cuda.synchronize()
+                masks = dmasks
+                arr = dptrs.cpu().numpy().view(hmi.POINTER_DTYPE)
+                plist = [dict(zip(arr.dtype.names, [x.item() for x in arr[i]])) for i in range(n)]
+            _compare_batch(gs, os_, frames, masks, plist, f"cfg4 t={t} {mode}")
+    finally:
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
+
+
+def test_process_batch_cached_plan():
+    idx = [0, 1, 40, 50, 60]
+    gs, os_ = _batch_streams(4, idx)
+    handles = [g.handle for g in gs]
+    for t in range(3):
+        frames = [synth.run_frame(4, i, t) for i in idx]
+        ptrs = np.zeros(len(idx), hmi.POINTER_DTYPE)
+        masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+        hmi.hmi_process_batch(handles, frames, masks, ptrs)
+        plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
+        _compare_batch(gs, os_, frames, masks, plist, f"process_batch t={t}")
+    for g in gs:
+        g.close()
+
+
+# --------------------------------------------------------------------------- #
+# Sizes, placements and error paths                                            #
+# --------------------------------------------------------------------------- #
+@pytest.mark.parametrize("w,h", [(1, 1), (1, 50), (50, 1), (17, 5), (33, 33), (100, 75), (321, 241)])
+def test_ragged_sizes_full_path(w, h):
+    g, o = pair(w, h, min_area=1)
+    bg = RNG.integers(0, 256, size=(h, w, 3), dtype=np.uint8)
+    lf = np.clip(bg[None].astype(int) + RNG.integers(-3, 4, size=(6, h, w, 3)), 0, 255).astype(np.uint8)
+    learn_both(g, o, lf, dev=True)
+    for t in range(4):
+        f = bg.copy()
+        m = RNG.random((h, w)) < 0.3
+        f[m] = SKIN
+        check_frame(g, o, f, dev=(t % 2 == 1), what=f"{w}x{h} t={t}")
+    g.close()
+
+
+def test_maximum_dimensions_properties():
+    for w, h in [(8192, 40), (40, 8192), (8192, 8192)]:
+        g = hmi.Stream(w, h, gain_min_q16=65536, gain_max_q16=65536)
+        z32 = np.zeros((h, w, 3), np.uint32)
+        z8 = np.zeros((h, w, 3), np.uint8)
+        g.import_background(z32, z32, z8, z8, 1, 0)
+        frame = np.empty((h, w, 3), np.uint8)
+        frame[...] = GRAY
+        m, p = g.process(_dev(frame))
+        assert not m.any() and p["valid"] == 0 and p["label"] == -1
+        cx, cy = w // 2, h // 2
+        a, b = min(w, h) // 4, min(w, h) // 5
+        y0, y1, x0, x1 = cy - b - 1, cy + b + 2, cx - a - 1, cx + a + 2
+        yy, xx = np.mgrid[y0:y1, x0:x1]
+        ell = (((xx - cx) / a) ** 2 + ((yy - cy) / b) ** 2) <= 1
+        frame[y0:y1, x0:x1][ell] = SKIN
+        m, p = g.process(_dev(frame))
+        assert (p["x"], p["y"], p["area"]) == (cx, cy, int(ell.sum()))
+        assert (p["x0"], p["x1"], p["y0"], p["y1"]) == (cx - a, cx + a, cy - b, cy + b)
+        assert int(m.sum()) == int(ell.sum())
+        g.close()
+
+
+def test_errors_and_optional_outputs():
+    g = hmi.Stream(64, 48)
+    frame = np.zeros((48, 64, 3), np.uint8)
+    with pytest.raises(hmi.HmiError) as e:
+        g.process(frame)
+    assert e.value.status == hmi.HMI_ERR_NOT_LEARNED
+    with pytest.raises(hmi.HmiError) as e:
+        hmi.hmi_create_stream(64, 48, hmi.hmi_default_params(bg_k_den=0))
+    assert e.value.status == hmi.HMI_ERR_INVALID_ARG
+    with pytest.raises(hmi.HmiError):
+        hmi.hmi_learn_background(g.handle, frame, 0)
+    g.learn(np.stack([frame] * 2))
+    hmi.hmi_process_frame(g.handle, frame, None, None)       # outputs optional
+    m, p = g.process(frame)
+    assert not m.any() and p["valid"] == 0
+    # the same stream cannot appear twice in a batch
+    with pytest.raises(hmi.HmiError):
+        hmi.hmi_batch_create([g.handle, g.handle])
+    g.close()
+
+
+def test_checkpoint_roundtrip():
+    w, h = synth.shape(1)
+    a = hmi.Stream(w, h)
+    a.learn(synth.learn_frames(1))
+    ex = a.export()
+    b = hmi.Stream(w, h)
+    b.import_background(ex["S"], ex["Q"], ex["vmin"], ex["vmax"], ex["n"], ex["syref"])
+    assert np.array_equal(b.export()["lo"], ex["lo"])
+    for t in range(0, 20, 4):
+        f = synth.run_frame(1, 0, t)
+        ma, pa = a.process(f)
+        mb, pb = b.process(f)
+        assert np.array_equal(ma, mb) and pa == pb
+    a.close()
+    b.close()
+
+
+def test_profile_counts_classification_kernel():
+    w, h = synth.shape(3)
+    g = hmi.Stream(w, h)
+    g.learn(_dev(synth.learn_frames(3, 0, 4)))
+    b = hmi.hmi_batch_create([g.handle])
+    f = _dev(synth.run_frame(3, 0, 0))
+    m = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    hmi.hmi_batch_profile(b, 5)
+    s = torch.cuda.current_stream().cuda_stream
+    for i in range(7):
+        hmi.hmi_batch_process_async(b, [f], [m], None, s, i % 2 == 0)
+    ticks, ms = hmi.hmi_batch_profile_read(b)
+    assert ticks == 5 and 0 < ms / ticks < 5.0
+    hmi.hmi_batch_destroy(b)
+    g.close()
