@@ -1,0 +1,468 @@
+"""Throughput benchmark of the hand-isolation path (arXiv 1907.04393) on GB300.
+
+One step = one tick of the 64-stream batch: one frame for each of 64 camera
+streams of mixed resolution (32 x 320x240, 16 x 640x480, 12 x 1280x720,
+4 x 1920x1080; 26.7 Mpx), through every stage of the path (brightness gain,
+background / gray / hue masks, morphology, components, pointer + click),
+replayed from a CUDA graph on the current torch stream.  Inputs are resident
+in HBM in a ring of 4 ticks per stream (320 MB, larger than the 126 MB L2).
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (on
+the host cores, bounded samples of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s & Mpixel/s at 640x480 and 64-stream batch; % HBM peak; p99 frame latency"
+CFG = 4
+RING = 4
+WORKLOAD = ("64-stream batch: 32x320x240 + 16x640x480 + 12x1280x720 + 4x1920x1080 RGB8, "
+            "26.7 Mpx per tick, each stream with its own learned background")
+# algorithmic bytes per pixel of the classification kernel: frame 3 B + band
+# lo/hi 6 B read, 1 bit written
+CLASSIFY_BYTES_PER_PX = 3 + 6 + 1 / 8
+KERNELS_PER_TICK = 6
+PROFILE_FILE = os.path.join(ROOT, "profiles", "k_classify_64stream.txt")
+
+
+# --------------------------------------------------------------------------- #
+# helpers                                                                      #
+# --------------------------------------------------------------------------- #
+def peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("hmi_frame.cu", "hmi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1907_04393_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_px():
+    """DRAM bytes per pixel of k_classify from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    try:
+        kv = {}
+        with open(PROFILE_FILE) as f:
+            for line in f:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_hash") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_px"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [c.strip() for c in line.split(",")]))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = [r for (t, r) in self.rows if t0 - 0.15 <= t <= t1 + 0.15] or [r for _, r in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if len(r) > 8 and num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if len(r) > 8 and num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) > 8 for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        pw = [num(r[3]) for r in rows if len(r) > 8 and num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# --------------------------------------------------------------------------- #
+# CPU oracle workers (spawned processes, no CUDA in them)                      #
+# --------------------------------------------------------------------------- #
+def _oracle_serve(conn, cfg, owned):
+    """Owns `owned` streams: learns them once, then on ("run", t, count)
+    processes `count` stream-frames round robin over its streams (frames of
+    tick t, generated before the clock starts) and returns (frames, px, s)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import oracle
+    from paper_1907_04393_gb300 import synth
+    streams = []
+    for s in owned:
+        o = oracle.OracleStream(*synth.shape(cfg, s))
+        o.learn(synth.learn_frames(cfg, s))
+        streams.append((s, o))
+    conn.send("ready")
+    nxt = 0
+    while True:
+        msg = conn.recv()
+        if msg[0] == "stop":
+            break
+        _, t, count = msg
+        work = []
+        for _ in range(count):
+            s, o = streams[nxt % len(streams)]
+            nxt += 1
+            work.append((o, synth.run_frame(cfg, s, t)))
+        start = time.perf_counter()
+        px = 0
+        for o, fr in work:
+            o.process(fr, want_labels=False)
+            px += o.w * o.h
+        conn.send((len(work), px, time.perf_counter() - start))
+
+
+class OraclePool:
+    """The oracle as it stands (single threaded), one spawned process per core,
+    each owning a fixed share of the workload's streams."""
+
+    def __init__(self, cfg: int, n_streams: int, workers: int):
+        ctx = mp.get_context("spawn")
+        self.owned = [list(range(j, n_streams, workers)) for j in range(workers)]
+        self.owned = [o for o in self.owned if o]
+        self.conns, self.procs = [], []
+        for o in self.owned:
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_serve, args=(b, cfg, o), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    @property
+    def cores(self) -> int:
+        return len(self.procs)
+
+    def run(self, t: int, per_worker: int | None = None) -> dict:
+        """One round: every worker processes per_worker stream-frames (None: all
+        of its streams, i.e. one full tick).  Time = the slowest worker."""
+        for c, o in zip(self.conns, self.owned):
+            c.send(("run", t, len(o) if per_worker is None else per_worker))
+        res = [c.recv() for c in self.conns]
+        return {"frames": sum(r[0] for r in res), "px": sum(r[1] for r in res),
+                "seconds": max(r[2] for r in res)}
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def host_workers(n_streams: int) -> int:
+    return max(1, min(os.cpu_count() or 1, 16, n_streams))
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the CPU oracle on the host cores                              #
+# --------------------------------------------------------------------------- #
+def run_reference(args) -> None:
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from paper_1907_04393_gb300 import synth
+    n = synth.num_streams(CFG)
+    pool = OraclePool(CFG, n, host_workers(n))
+    try:
+        # one step = one stream-frame per core (round robin over the 64 streams)
+        for k in range(max(args.warmup, 1)):
+            pool.run(k, 1)
+        budget, t_start = 150.0, time.time()
+        done, frames, px, secs = 0, 0, 0, 0.0
+        while done < args.steps and (time.time() - t_start) < budget:
+            r = pool.run(args.warmup + done, 1)
+            frames, px, secs, done = frames + r["frames"], px + r["px"], secs + r["seconds"], done + 1
+    finally:
+        pool.close()
+    fps = frames / secs
+    sample = f"{pool.cores} stream-frames per step (one per core, round robin over the 64 streams)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": done, "warmup": args.warmup,
+        "ms_per_step": secs / done * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "mpx_per_s": px / secs / 1e6,
+        "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": f"{sample}; {done} steps"},
+        "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# our arm                                                                      #
+# --------------------------------------------------------------------------- #
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+    from paper_1907_04393_gb300 import hmi, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # CPU baseline first (spawned processes, no CUDA in them)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = OraclePool(CFG, synth.num_streams(CFG), host_workers(synth.num_streams(CFG)))
+        try:
+            pool.run(0)                                   # warm-up tick
+            rs = [pool.run(1 + k) for k in range(args.cpu_ticks)]
+        finally:
+            pool.close()
+        cpu = {"frames": sum(r["frames"] for r in rs), "px": sum(r["px"] for r in rs),
+               "seconds": sum(r["seconds"] for r in rs), "cores": pool.cores}
+
+    hmi.load()
+    n = synth.num_streams(CFG)
+    streams, rings, masks = [], [], []
+    px_per_tick = 0
+    for i in range(n):
+        w, h = synth.shape(CFG, i)
+        st = hmi.Stream(w, h)
+        st.learn(torch.from_numpy(synth.learn_frames(CFG, i)).to(dev))
+        streams.append(st)
+        rings.append([torch.from_numpy(synth.run_frame(CFG, i, t)).to(dev) for t in range(RING)])
+        masks.append(torch.empty((h, w), dtype=torch.uint8, device=dev))
+        px_per_tick += w * h
+    ptrs = torch.zeros(n * 40, dtype=torch.uint8, device=dev)
+    batch = hmi.hmi_batch_create([s.handle for s in streams])
+    cs = torch.cuda.current_stream()
+
+    def tick(k):
+        hmi.hmi_batch_process_async(batch, [rings[i][k % RING] for i in range(n)], masks,
+                                    ptrs.data_ptr(), cs.cuda_stream, True)
+
+    for k in range(args.warmup):
+        tick(k)
+    torch.cuda.synchronize()
+
+    gpu_id = str(local)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    time.sleep(0.3)
+
+    # ---- device-resident timed region ------------------------------------
+    hmi.hmi_batch_profile(batch, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    e0.record(cs)
+    for k in range(args.steps):
+        tick(args.warmup + k)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    barrier()
+    t1 = time.time()
+    ms = e0.elapsed_time(e1)
+    prof_ticks, prof_ms = hmi.hmi_batch_profile_read(batch)
+    hmi.hmi_batch_profile(batch, 0)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.summary(t0, t1)
+    clocks.stop()
+
+    # ---- end to end through the synchronous API with host buffers --------
+    host_frames = []
+    for i in range(n):
+        host_frames.append([r.cpu().pin_memory() for r in rings[i]])
+    host_ptrs = np.zeros(n, hmi.POINTER_DTYPE)
+    e2e_steps = max(3, min(args.steps, args.e2e_steps))
+    for k in range(3):
+        hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], masks, host_ptrs)
+    barrier()
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    for k in range(e2e_steps):
+        hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], masks, host_ptrs)
+    e2e_s = time.perf_counter() - s0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(int(host_frames[i][0].numel()) for i in range(n))
+
+    # ---- single 640x480 stream (the other configuration of the metric) ---
+    single = None
+    if not args.no_single:
+        single = bench_single(hmi, synth, torch, dev, cs, args)
+
+    hmi.hmi_batch_destroy(batch)
+    for s in streams:
+        s.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peak, peak_kind = peaks()
+    frames_total = n * args.steps * world
+    value = frames_total / (ms / 1e3)
+    classify_ms = prof_ms / max(prof_ticks, 1)
+    achieved = CLASSIFY_BYTES_PER_PX * px_per_tick / (classify_ms / 1e3) / 1e9
+    traffic_px = profiled_traffic_per_px()
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "streams_per_gpu": n, "px_per_tick": px_per_tick,
+                   "l2": f"inputs larger than L2: ring of {RING} ticks per stream "
+                         f"({RING * px_per_tick * 3 / 1e6:.0f} MB of frames)",
+                   "launch": "CUDA graph per tick on the torch current stream"},
+        "mpx_per_s": px_per_tick * args.steps * world / (ms / 1e3) / 1e6,
+        "roofline": {"bound": "hbm", "kernel": "k_classify", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": (traffic_px * px_per_tick) if traffic_px else None,
+                     "algorithmic_bytes_per_launch": CLASSIFY_BYTES_PER_PX * px_per_tick,
+                     "launch_ms": classify_ms, "launches_timed": prof_ticks},
+        "e2e": {"value": n * e2e_steps * world / e2e_s, "unit": "frames/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 40,
+                "api": "hmi_batch_process, pinned host frames, pointers read back"},
+        "gpu_launches": KERNELS_PER_TICK * args.steps,
+        "clocks": clk,
+    }
+    if single is not None:
+        line["single_640x480"] = single
+    if cpu is not None:
+        line["cpu_baseline"] = {"value": cpu["frames"] / cpu["seconds"], "unit": "frames/s",
+                                "cores": cpu["cores"], "kind": "oracle",
+                                "sample": f"{cpu['frames']} stream-frames ({args.cpu_ticks} ticks of "
+                                          f"all 64 streams), {cpu['px'] / 1e6:.0f} Mpx",
+                                "mpx_per_s": cpu["px"] / cpu["seconds"] / 1e6}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
+    """640x480 single stream: graph replay throughput, and per-frame latency of
+    the synchronous API with a pinned host frame (host mask, host pointer)."""
+    w, h = synth.shape(2)
+    st = hmi.Stream(w, h)
+    st.learn(torch.from_numpy(synth.learn_frames(2)).to(dev))
+    ring = [torch.from_numpy(synth.run_frame(2, 0, t)).to(dev) for t in range(16)]
+    mask = torch.empty((h, w), dtype=torch.uint8, device=dev)
+    ptr = torch.zeros(40, dtype=torch.uint8, device=dev)
+    b = hmi.hmi_batch_create([st.handle])
+    for k in range(20):
+        hmi.hmi_batch_process_async(b, [ring[k % 16]], [mask], ptr.data_ptr(), cs.cuda_stream, True)
+    torch.cuda.synchronize()
+    steps = max(100, min(args.steps * 4, 4000))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    for k in range(steps):
+        hmi.hmi_batch_process_async(b, [ring[k % 16]], [mask], ptr.data_ptr(), cs.cuda_stream, True)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    host = [r.cpu().pin_memory() for r in ring]
+    hmask = np.empty((h, w), np.uint8)
+    hp = hmi.hmi_pointer()
+    lat = []
+    for k in range(min(steps, 1000)):
+        t = time.perf_counter()
+        hmi.hmi_process_frame(st.handle, host[k % 16], hmask, hp)
+        lat.append((time.perf_counter() - t) * 1e3)
+    hmi.hmi_batch_destroy(b)
+    st.close()
+    lat.sort()
+    return {"frames_per_s": steps / (ms / 1e3), "mpx_per_s": steps * w * h / (ms / 1e3) / 1e6,
+            "ms_per_frame": ms / steps,
+            "e2e_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99) - 1],
+                               "api": "hmi_process_frame, pinned host frame, host mask + pointer"}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--cpu-ticks", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-single", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_set>
 #include <vector>
 
 #include "hmi_internal.cuh"
@@ -193,6 +194,15 @@ struct hmi_batch {
     // profiling of the classification kernel
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
+    // device buffers already validated (skips a pointer-attribute query per
+    // buffer per tick); bounded, cleared when full
+    std::unordered_set<const void *> seen;
+    bool seen_device(const void *p) const { return seen.count(p) != 0; }
+    void remember_device(const void *p)
+    {
+        if (seen.size() >= 65536) seen.clear();
+        seen.insert(p);
+    }
 };
 
 namespace {
@@ -429,7 +439,11 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
         hmi_stream *s = b->s[i];
         const uint8_t *f = frames[i];
         if (!f) return fail(HMI_ERR_INVALID_ARG);
-        const bool dev = is_device_ptr(f);
+        bool dev = b->seen_device(f);
+        if (!dev) {
+            dev = is_device_ptr(f);
+            if (dev) b->remember_device(f);
+        }
         if (async_mode && !dev) return fail(HMI_ERR_INVALID_ARG);
         if (dev && (s->w % 16) == 0 && (reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
             io[i].frame = f;
@@ -443,7 +457,8 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
         uint8_t *m = (masks != nullptr) ? masks[i] : nullptr;
         if (m == nullptr) {
             io[i].mask = nullptr;
-        } else if (is_device_ptr(m)) {
+        } else if (b->seen_device(m) || is_device_ptr(m)) {
+            b->remember_device(m);
             io[i].mask = m;
         } else {
             if (async_mode) return fail(HMI_ERR_INVALID_ARG);

