@@ -192,6 +192,26 @@ HMI_API int hmi_get_last_gain(const hmi_stream *s, uint32_t *gain_q16);
  * (the figure that admission control budgets).  0 on invalid arguments. */
 HMI_API size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p);
 
+/* Brightness gain of one frame without any device allocation.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory, such as a real-time loop in which a cudaMalloc could stall the
+ * device, or a host program that owns all device memory through its own pool.
+ * It returns, in *gain_out (device memory, one uint32), the same clamped Q16
+ * gain round(syref / SY) that hmi_process_frame applies, SY being the frame's
+ * integer luma sum.  frame: device memory, h rows of 3*w bytes.  The work runs
+ * on cuda_stream (NULL = legacy default stream); the result is ready when that
+ * stream reaches this point.
+ * Scratch: a fixed 32 KiB array built into the library, one copy per GPU that
+ * loads it, kept until the process exits.  Frames of more than 4,194,304
+ * sixteen-pixel row chunks (h * ceil(w/16); 8192 x 8192 is the largest square)
+ * and w or h beyond 8192 are rejected with HMI_ERR_INVALID_ARG.  The first
+ * call on a device looks up that device's scratch address, so make it before
+ * any stream capture.  All calls share the scratch: calls that overlap on the
+ * GPU race and must be serialised by the caller.  Calls no allocator. */
+HMI_API int hmi_frame_gain_noalloc(const uint8_t *frame, int w, int h, uint64_t syref,
+                                   uint32_t gain_min_q16, uint32_t gain_max_q16,
+                                   uint32_t *gain_out, void *cuda_stream);
+
 /* Status of the last failed call on this thread, and a text for a status. */
 HMI_API int hmi_last_error(void);
 HMI_API const char *hmi_status_string(int status);

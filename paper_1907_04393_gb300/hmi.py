@@ -73,6 +73,8 @@ SIGNATURES = {
     "hmi_import_background": (_I, [_P, _P, _P, _P, _P, _I, ctypes.c_uint64]),
     "hmi_get_last_gain": (_I, [_P, ctypes.POINTER(ctypes.c_uint32)]),
     "hmi_stream_device_bytes": (ctypes.c_size_t, [_I, _I, ctypes.POINTER(hmi_params)]),
+    "hmi_frame_gain_noalloc": (_I, [_P, _I, _I, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                    _P, _P]),
     "hmi_last_error": (_I, []),
     "hmi_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -249,6 +251,14 @@ def hmi_get_last_gain(s: int) -> int:
 
 def hmi_stream_device_bytes(w: int, h: int, params: hmi_params | None = None) -> int:
     return load().hmi_stream_device_bytes(w, h, ctypes.byref(params) if params is not None else None)
+
+
+def hmi_frame_gain_noalloc(frame, w: int, h: int, syref: int, gain_min_q16: int,
+                           gain_max_q16: int, gain_out, cuda_stream: int) -> None:
+    """Gain of one device frame into gain_out (device uint32) using only the
+    library's built-in scratch: for callers that cannot allocate device memory."""
+    _check(load().hmi_frame_gain_noalloc(_addr(frame), w, h, syref, gain_min_q16, gain_max_q16,
+                                         _addr(gain_out), cuda_stream), "hmi_frame_gain_noalloc")
 
 
 def hmi_last_error() -> int:
