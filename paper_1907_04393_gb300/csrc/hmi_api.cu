@@ -5,8 +5,8 @@
 // tables the tick kernels read (stream descriptors, work pieces, prefix sums),
 // a ring of per-tick pointer slots (pinned host mirror + device copy + event),
 // and optionally one CUDA graph per slot that replays the whole tick: the
-// slot's pointer upload, luma, classification, morphology + block components,
-// merge, resolve and pointer kernels.
+// slot's pointer upload, then the luma, classification, morphology + block
+// components, and per-stream finish (merge, resolve, pointer) kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -99,7 +99,7 @@ struct Arena {
 };
 
 struct Layout {
-    int w, h, nwords, bh, tiles_x, fpitch;
+    int w, h, nwords, bh, tiles_x, strips_x, fpitch;
     size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, bits, comp, parent, count, mask, st,
         hist, ds, ptr, total;
 };
@@ -112,6 +112,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.nwords = (w + 31) / 32;
     L.bh = (h + 31) / 32;
     L.tiles_x = (L.nwords + kMorphTW - 1) / kMorphTW;
+    L.strips_x = (L.nwords + 29) / 30;
     L.fpitch = (int)align_up((size_t)w, 16) * 3;
     L.npx = (size_t)w * h;
     const size_t nblk = (size_t)L.bh * L.nwords;
@@ -220,6 +221,7 @@ void fill_devstream(hmi_stream *s)
     D.nwords = L.nwords;
     D.bh = L.bh;
     D.tiles_x = L.tiles_x;
+    D.strips_x = L.strips_x;
     D.fpitch = L.fpitch;
     D.gray_tol = s->p.gray_tol;
     D.open_iters = s->p.open_iters;
@@ -296,13 +298,16 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     }
     // work tables
     std::vector<unsigned long long> cpre(n + 1, 0);
-    std::vector<uint32_t> tpre(n + 1, 0), bpre(n + 1, 0);
+    std::vector<uint32_t> tpre(n + 1, 0), bpre(n + 1, 0), spre(n + 1, 0);
     std::vector<int4> pieces;
+    int max_halo = 0;
     for (int i = 0; i < n; ++i) {
         const Layout &L = s[i]->L;
         const int chunks = L.h * 2 * L.nwords;
         cpre[i + 1] = cpre[i] + (unsigned long long)chunks;
         tpre[i + 1] = tpre[i] + (uint32_t)(L.bh * L.tiles_x);
+        spre[i + 1] = spre[i] + (uint32_t)(L.bh * L.strips_x);
+        max_halo = std::max(max_halo, 2 * (s[i]->p.open_iters + s[i]->p.close_iters));
         bpre[i + 1] = bpre[i] + (uint32_t)(L.bh * L.nwords);
         for (int c = 0; c < chunks; c += kPieceChunks)
             pieces.push_back(make_int4(i, c, std::min(chunks, c + kPieceChunks), 0));
@@ -312,6 +317,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     const size_t o_c = a.take(sizeof(unsigned long long) * (n + 1));
     const size_t o_t = a.take(sizeof(uint32_t) * (n + 1));
     const size_t o_b = a.take(sizeof(uint32_t) * (n + 1));
+    const size_t o_s = a.take(sizeof(uint32_t) * (n + 1));
     const size_t o_done = a.take(sizeof(uint32_t) * 4);
     const size_t o_p = a.take(sizeof(int4) * pieces.size());
     const size_t o_io = a.take(sizeof(TickIO) * n * kRing);
@@ -338,6 +344,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
          cudaMemcpy(A + o_c, cpre.data(), sizeof(unsigned long long) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(A + o_t, tpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(A + o_b, bpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(A + o_s, spre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
          cudaMemcpy(A + o_p, pieces.data(), sizeof(int4) * pieces.size(), cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
@@ -360,6 +367,9 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     bd.chunk_prefix = reinterpret_cast<const unsigned long long *>(A + o_c);
     bd.tile_prefix = reinterpret_cast<const uint32_t *>(A + o_t);
     bd.block_prefix = reinterpret_cast<const uint32_t *>(A + o_b);
+    bd.strip_prefix = reinterpret_cast<const uint32_t *>(A + o_s);
+    bd.total_strips = spre[n];
+    bd.max_halo = max_halo;
     bd.done = reinterpret_cast<uint32_t *>(A + o_done);
     bd.pieces = reinterpret_cast<const int4 *>(A + o_p);
     bd.npieces = (int)pieces.size();
@@ -385,9 +395,7 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
         return e;
     if ((e = launch_morph_cc(bd, cs)) != cudaSuccess) return e;
-    if ((e = launch_merge(bd, cs)) != cudaSuccess) return e;
-    if ((e = launch_resolve(bd, cs)) != cudaSuccess) return e;
-    return launch_pointer(bd, cs);
+    return launch_finish(bd, cs);
 }
 
 int build_graph(hmi_batch *b, int slot)

@@ -49,70 +49,61 @@ __device__ void unite(uint32_t *parent, const Comp *comp, uint32_t a, uint32_t b
     atomicOr(err, kErrUnionLoop);
 }
 
-// Stream of CC block g (flattened over the batch) and the block's local index.
-__device__ __forceinline__ int block_stream(const BatchDev &b, uint32_t g, uint32_t *local)
+// Unions of block `lb`'s components with those of one neighbour block that
+// touch them across the shared border (8-connected).  dir 0: right,
+// 1: down, 2: down-right corner, 3: down-left corner.
+__device__ void merge_dir(const DevStream &D, uint32_t lb, int dir, uint32_t *err)
 {
-    int lo = 0, hi = b.n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (b.block_prefix[mid] <= g) lo = mid; else hi = mid;
-    }
-    *local = g - b.block_prefix[lo];
-    return lo;
-}
-
-__global__ void __launch_bounds__(kThreads) k_merge(BatchDev b)
-{
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= b.total_blocks) return;
-    uint32_t lb;
-    const DevStream &D = b.ds[block_stream(b, g, &lb)];
-    const uint32_t cnt = D.count[lb];
-    if (cnt == 0) return;
     const int nw = D.nwords;
     const int by = (int)lb / nw, bx = (int)lb - by * nw;
     const bool has_r = bx + 1 < nw, has_d = by + 1 < D.bh, has_l = bx > 0;
-    const uint32_t nb_r = lb + 1, nb_d = lb + nw, nb_dr = lb + nw + 1, nb_dl = lb + nw - 1;
-    const uint32_t c_r = has_r ? D.count[nb_r] : 0u;
-    const uint32_t c_d = has_d ? D.count[nb_d] : 0u;
-    const uint32_t c_dr = (has_d && has_r) ? D.count[nb_dr] : 0u;
-    const uint32_t c_dl = (has_d && has_l) ? D.count[nb_dl] : 0u;
-    uint32_t *err = &D.st->err;
+    uint32_t nb;
+    if (dir == 0) {
+        if (!has_r) return;
+        nb = lb + 1;
+    } else if (dir == 1) {
+        if (!has_d) return;
+        nb = lb + nw;
+    } else if (dir == 2) {
+        if (!(has_d && has_r)) return;
+        nb = lb + nw + 1;
+    } else {
+        if (!(has_d && has_l)) return;
+        nb = lb + nw - 1;
+    }
+    const uint32_t cnt = D.count[lb];
+    const uint32_t cn = D.count[nb];
+    if (cn == 0) return;
     for (uint32_t j = 0; j < cnt; ++j) {
         const uint32_t id = lb * kSlots + j;
         const Comp &A = D.comp[id];
-        const uint32_t ar = A.right, ab = A.bot;
-        if (ar) {
-            for (uint32_t i = 0; i < c_r; ++i) {
-                const uint32_t L = D.comp[nb_r * kSlots + i].left;
-                if (ar & (L | (L << 1) | (L >> 1))) unite(D.parent, D.comp, id, nb_r * kSlots + i, err);
+        const uint32_t edge = (dir == 0) ? A.right : A.bot;
+        if (edge == 0u) continue;
+        if (dir == 2 && !(edge >> 31)) continue;
+        if (dir == 3 && !(edge & 1u)) continue;
+        for (uint32_t i = 0; i < cn; ++i) {
+            const Comp &B = D.comp[nb * kSlots + i];
+            bool touch;
+            if (dir == 0) {
+                const uint32_t L = B.left;
+                touch = (edge & (L | (L << 1) | (L >> 1))) != 0u;
+            } else if (dir == 1) {
+                const uint32_t T = B.top;
+                touch = (edge & (T | (T << 1) | (T >> 1))) != 0u;
+            } else if (dir == 2) {
+                touch = (B.top & 1u) != 0u;
+            } else {
+                touch = (B.top >> 31) != 0u;
             }
-        }
-        if (ab) {
-            for (uint32_t i = 0; i < c_d; ++i) {
-                const uint32_t T = D.comp[nb_d * kSlots + i].top;
-                if (ab & (T | (T << 1) | (T >> 1))) unite(D.parent, D.comp, id, nb_d * kSlots + i, err);
-            }
-            if (ab >> 31) {
-                for (uint32_t i = 0; i < c_dr; ++i)
-                    if (D.comp[nb_dr * kSlots + i].top & 1u) unite(D.parent, D.comp, id, nb_dr * kSlots + i, err);
-            }
-            if (ab & 1u) {
-                for (uint32_t i = 0; i < c_dl; ++i)
-                    if (D.comp[nb_dl * kSlots + i].top >> 31) unite(D.parent, D.comp, id, nb_dl * kSlots + i, err);
-            }
+            if (touch) unite(D.parent, D.comp, id, nb * kSlots + i, err);
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_resolve(BatchDev b)
+// Non-root components of block lb add their statistics into their roots.
+__device__ void resolve_block(const DevStream &D, uint32_t lb, uint32_t *err)
 {
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= b.total_blocks) return;
-    uint32_t lb;
-    const DevStream &D = b.ds[block_stream(b, g, &lb)];
     const uint32_t cnt = D.count[lb];
-    uint32_t *err = &D.st->err;
     for (uint32_t j = 0; j < cnt; ++j) {
         const uint32_t id = lb * kSlots + j;
         const uint32_t r = find_root(D.parent, id, err);
@@ -198,13 +189,52 @@ __device__ void finalize_stream(const DevStream &D, const TickIO &io)
     if (io.ptr_out != nullptr) *io.ptr_out = P;
 }
 
-__global__ void __launch_bounds__(kThreads) k_pointer(BatchDev b)
+// One CTA per stream: the blocks that hold components are compacted into
+// shared memory, then (separated by CTA barriers, no grid-wide wait) their
+// borders are merged, non-roots are added into their roots, the largest root
+// is chosen with a shared 64-bit atomicMax on (area, ~key), and thread 0
+// writes the pointer and steps the click state.
+constexpr int kFinishThreads = 512;
+constexpr int kActCap = 4096;
+
+__global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
 {
-    __shared__ bool is_last;
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < b.total_blocks) {
-        uint32_t lb;
-        const DevStream &D = b.ds[block_stream(b, g, &lb)];
+    __shared__ uint32_t act[kActCap];
+    __shared__ uint32_t nact;
+    __shared__ unsigned long long best;
+    const int tid = threadIdx.x;
+    const DevStream &D = b.ds[blockIdx.x];
+    const TickIO io = b.io[blockIdx.x];
+    uint32_t *err = &D.st->err;
+    const uint32_t nblk = (uint32_t)D.bh * (uint32_t)D.nwords;
+    if (tid == 0) {
+        nact = 0;
+        best = 0;
+    }
+    __syncthreads();
+    for (uint32_t base = 0; base < nblk; base += blockDim.x) {
+        const uint32_t blk = base + tid;
+        const bool a = blk < nblk && D.count[blk] != 0u;
+        const unsigned m = __ballot_sync(kFull, a);
+        uint32_t pos = 0;
+        if ((tid & 31) == 0 && m) pos = atomicAdd(&nact, (uint32_t)__popc(m));
+        pos = __shfl_sync(kFull, pos, 0) + (uint32_t)__popc(m & ((1u << (tid & 31)) - 1u));
+        if (a && pos < kActCap) act[pos] = blk;
+    }
+    __syncthreads();
+    const uint32_t na = nact;
+    const bool fits = na <= (uint32_t)kActCap;
+    const uint32_t nitems = fits ? na : nblk;
+    for (uint32_t it = tid; it < 4 * nitems; it += blockDim.x) {
+        const uint32_t lb = fits ? act[it >> 2] : (it >> 2);
+        if (!fits && D.count[lb] == 0u) continue;
+        merge_dir(D, lb, (int)(it & 3), err);
+    }
+    __syncthreads();
+    for (uint32_t it = tid; it < nitems; it += blockDim.x) resolve_block(D, fits ? act[it] : it, err);
+    __syncthreads();
+    for (uint32_t it = tid; it < nitems; it += blockDim.x) {
+        const uint32_t lb = fits ? act[it] : it;
         const uint32_t cnt = D.count[lb];
         for (uint32_t j = 0; j < cnt; ++j) {
             const uint32_t id = lb * kSlots + j;
@@ -212,21 +242,16 @@ __global__ void __launch_bounds__(kThreads) k_pointer(BatchDev b)
             const Comp &C = D.comp[id];
             const unsigned long long packed = ((unsigned long long)__ldcg(&C.area) << 32) |
                                               (unsigned long long)(0xffffffffu - C.key);
-            atomicMax(&D.st->best, packed);
+            atomicMax(&best, packed);
         }
     }
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(&b.done[1], 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int s = threadIdx.x; s < b.n; s += blockDim.x) {
-        finalize_stream(b.ds[s], b.io[s]);
-        const uint32_t e = b.ds[s].st->err;
+    if (tid == 0) {
+        D.st->best = best;
+        finalize_stream(D, io);
+        const uint32_t e = D.st->err;
         if (e) atomicOr(b.err, e);
     }
-    if (threadIdx.x == 0) b.done[1] = 0;
 }
 
 // Labels of one stream: warp per 32x32 block.
@@ -266,26 +291,9 @@ __global__ void __launch_bounds__(kThreads) k_labels(const DevStream *dsp, int32
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static unsigned blocks_grid(const BatchDev &b)
+cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs)
 {
-    return (b.total_blocks + kThreads - 1) / kThreads;
-}
-
-cudaError_t launch_merge(const BatchDev &b, cudaStream_t cs)
-{
-    k_merge<<<blocks_grid(b), kThreads, 0, cs>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_resolve(const BatchDev &b, cudaStream_t cs)
-{
-    k_resolve<<<blocks_grid(b), kThreads, 0, cs>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pointer(const BatchDev &b, cudaStream_t cs)
-{
-    k_pointer<<<blocks_grid(b), kThreads, 0, cs>>>(b);
+    k_finish<<<b.n, kFinishThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 

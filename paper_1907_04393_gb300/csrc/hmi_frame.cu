@@ -15,11 +15,39 @@
 
 namespace hmi {
 
-// 16-byte global load that keeps the line out of L1 and marks it evict-first
-// in L2 (a read-once stream).
-__device__ __forceinline__ uint4 ld_stream(const uint4 *p)
+// L2 eviction policies: the frame read by k_luma is kept in L2 for k_classify
+// (evict-last); the band and the frame's second read are read-once streams
+// (evict-first).
+__device__ __forceinline__ uint64_t policy_evict_last()
 {
-    return __ldcs(p);
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint4 ld_hint(const uint4 *ptr, uint64_t pol)
+{
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(ptr), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ void load48(const uint8_t *src, uint64_t pol, uint32_t (&w)[12])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(src);
+    const uint4 a = ld_hint(q, pol), b = ld_hint(q + 1, pol), c = ld_hint(q + 2, pol);
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
 }
 
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
@@ -47,17 +75,14 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
         const DevStream &D = b.ds[s];
         const TickIO io = b.io[s];
         const int w = D.w, cpr = 2 * D.nwords;
+        const uint64_t keep = policy_evict_last();
         unsigned long long acc = 0;
         for (int u = piece.y + tid; u < piece.z; u += blockDim.x) {
             const int y = u / cpr, j = u - y * cpr;
             const int x0 = j * kChunkPx;
             if (x0 >= w) continue;
-            const uint4 *src = reinterpret_cast<const uint4 *>(io.frame + (long long)y * io.frame_pitch + 3 * x0);
             uint32_t f[12];
-            uint4 a = __ldg(src), c = __ldg(src + 1), e = __ldg(src + 2);
-            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
-            f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
-            f[8] = e.x; f[9] = e.y; f[10] = e.z; f[11] = e.w;
+            load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f);
             const int npx = min(kChunkPx, w - x0);
             uint32_t sum = 0;
 #pragma unroll
@@ -108,52 +133,61 @@ struct ClassP {
     int A[3][2], B[3][2];
 };
 
-// One pixel: 1 iff it is foreground for the background band (some channel
-// outside [lo, hi]), not gray (max - min >= S) and of skin hue, all on the
-// gain-corrected values c' = min(255, (c g + 2^15) >> 16).
-// The hue test compares N = 512 (t + d) + d against d-scaled interval ends,
-// which is exact for h = base - 256 + floor(N / 2d) without any division.
-__device__ __forceinline__ uint32_t classify_px(uint32_t r0, uint32_t g0, uint32_t b0,
-                                                uint32_t lr, uint32_t lg, uint32_t lb,
-                                                uint32_t hr, uint32_t hg, uint32_t hb,
-                                                const ClassP &P)
+// Gain-corrected channel: c' = min(255, (c g + 2^15) >> 16).
+__device__ __forceinline__ int corr(uint32_t c, uint32_t g)
 {
-    const int r = (int)min((r0 * P.g + 32768u) >> 16, 255u);
-    const int g = (int)min((g0 * P.g + 32768u) >> 16, 255u);
-    const int b = (int)min((b0 * P.g + 32768u) >> 16, 255u);
-    const bool inband = (r >= (int)lr) & (r <= (int)hr) & (g >= (int)lg) & (g <= (int)hg) &
-                        (b >= (int)lb) & (b <= (int)hb);
+    return (int)min((c * g + 32768u) >> 16, 255u);
+}
+
+// Background test of one pixel (Sec. 3.1 (i)): 1 iff some gain-corrected
+// channel lies outside the learned band [lo, hi].
+__device__ __forceinline__ uint32_t outside_band(const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                                 const uint32_t (&h)[12], int k, uint32_t g)
+{
+    const int q = 3 * k;
+    const int r = corr(byte_of(f, q), g), gg = corr(byte_of(f, q + 1), g), b = corr(byte_of(f, q + 2), g);
+    const bool in = (r >= (int)byte_of(l, q)) & (r <= (int)byte_of(h, q)) &
+                    (gg >= (int)byte_of(l, q + 1)) & (gg <= (int)byte_of(h, q + 1)) &
+                    (b >= (int)byte_of(l, q + 2)) & (b <= (int)byte_of(h, q + 2));
+    return in ? 0u : 1u;
+}
+
+// Gray and hue tests of one pixel (Sec. 3.1 (ii), (iii)) on the corrected
+// values: not gray (max - min >= S) and hue inside the arc.  The hue test
+// compares N = 512 (t + d) + d against d-scaled interval ends, which equals
+// testing h = base - 256 + floor(N / 2d) without a division.
+__device__ __forceinline__ uint32_t skin_px(const uint32_t (&f)[12], int k, const ClassP &P)
+{
+    const int q = 3 * k;
+    const int r = corr(byte_of(f, q), P.g), g = corr(byte_of(f, q + 1), P.g), b = corr(byte_of(f, q + 2), P.g);
     const int mx = max(r, max(g, b));
     const int mn = min(r, min(g, b));
     const int d = mx - mn;
-    int t, a0, b0_, a1, b1;
+    int t, a0, b0, a1, b1;
     if (r == mx) {
-        t = g - b; a0 = P.A[0][0]; b0_ = P.B[0][0]; a1 = P.A[0][1]; b1 = P.B[0][1];
+        t = g - b; a0 = P.A[0][0]; b0 = P.B[0][0]; a1 = P.A[0][1]; b1 = P.B[0][1];
     } else if (g == mx) {
-        t = b - r; a0 = P.A[1][0]; b0_ = P.B[1][0]; a1 = P.A[1][1]; b1 = P.B[1][1];
+        t = b - r; a0 = P.A[1][0]; b0 = P.B[1][0]; a1 = P.A[1][1]; b1 = P.B[1][1];
     } else {
-        t = r - g; a0 = P.A[2][0]; b0_ = P.B[2][0]; a1 = P.A[2][1]; b1 = P.B[2][1];
+        t = r - g; a0 = P.A[2][0]; b0 = P.B[2][0]; a1 = P.A[2][1]; b1 = P.B[2][1];
     }
     const int N = 512 * (t + d) + d;
-    const bool skin = (d > 0) & (((N >= d * a0) & (N < d * b0_)) | ((N >= d * a1) & (N < d * b1)));
-    return (uint32_t)((!inband) & (d >= P.tol) & skin);
+    const bool hue = ((N >= d * a0) & (N < d * b0)) | ((N >= d * a1) & (N < d * b1));
+    return (uint32_t)((d > 0) & (d >= P.tol) & hue);
 }
 
-__global__ void __launch_bounds__(kThreads) k_classify(BatchDev b)
+// One thread per 16-pixel chunk: the background test for all 16 pixels first;
+// the gray and hue tests only run when some pixel of the warp's 512 is
+// outside its background band (in practice: warps that overlap the hand).
+__global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
 {
     const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t once = policy_evict_first();
     for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
         const int4 piece = b.pieces[pc];
         const DevStream &D = b.ds[piece.x];
         const TickIO io = b.io[piece.x];
-        ClassP P;
-        P.g = D.st->gain;
-        P.tol = D.gray_tol;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            P.A[i][0] = D.hueA[i][0]; P.A[i][1] = D.hueA[i][1];
-            P.B[i][0] = D.hueB[i][0]; P.B[i][1] = D.hueB[i][1];
-        }
+        const uint32_t g = D.st->gain;
         const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
         const uint8_t *lo = D.lo, *hi = D.hi;
         uint32_t *raw = D.raw;
@@ -161,49 +195,219 @@ __global__ void __launch_bounds__(kThreads) k_classify(BatchDev b)
         for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
             const int u = base + lane;
             uint32_t bits = 0;
-            int y = 0, j = 0;
+            int y = 0, j = 0, x0 = 0;
+            uint32_t f[12];
             if (u < piece.z) {
                 y = u / cpr;
                 j = u - y * cpr;
-                const int x0 = j * kChunkPx;
+                x0 = j * kChunkPx;
                 if (x0 < w) {
-                    const uint4 *fs = reinterpret_cast<const uint4 *>(io.frame + (long long)y * io.frame_pitch + 3 * x0);
-                    const uint4 *ls = reinterpret_cast<const uint4 *>(lo + (long long)y * fpitch + 3 * x0);
-                    const uint4 *hs = reinterpret_cast<const uint4 *>(hi + (long long)y * fpitch + 3 * x0);
-                    uint32_t f[12], l[12], h[12];
-                    {
-                        uint4 a = ld_stream(fs), c = ld_stream(fs + 1), e = ld_stream(fs + 2);
-                        f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
-                        f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
-                        f[8] = e.x; f[9] = e.y; f[10] = e.z; f[11] = e.w;
-                    }
-                    {
-                        uint4 a = ld_stream(ls), c = ld_stream(ls + 1), e = ld_stream(ls + 2);
-                        l[0] = a.x; l[1] = a.y; l[2] = a.z; l[3] = a.w;
-                        l[4] = c.x; l[5] = c.y; l[6] = c.z; l[7] = c.w;
-                        l[8] = e.x; l[9] = e.y; l[10] = e.z; l[11] = e.w;
-                    }
-                    {
-                        uint4 a = ld_stream(hs), c = ld_stream(hs + 1), e = ld_stream(hs + 2);
-                        h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
-                        h[4] = c.x; h[5] = c.y; h[6] = c.z; h[7] = c.w;
-                        h[8] = e.x; h[9] = e.y; h[10] = e.z; h[11] = e.w;
-                    }
+                    uint32_t l[12], h[12];
+                    load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
+                    load48(lo + (long long)y * fpitch + 3 * x0, once, l);
+                    load48(hi + (long long)y * fpitch + 3 * x0, once, h);
 #pragma unroll
-                    for (int k = 0; k < kChunkPx; ++k) {
-                        const int q = 3 * k;
-                        bits |= classify_px(byte_of(f, q), byte_of(f, q + 1), byte_of(f, q + 2),
-                                            byte_of(l, q), byte_of(l, q + 1), byte_of(l, q + 2),
-                                            byte_of(h, q), byte_of(h, q + 1), byte_of(h, q + 2), P)
-                                << k;
-                    }
+                    for (int k = 0; k < kChunkPx; ++k) bits |= outside_band(f, l, h, k, g) << k;
                     const int npx = w - x0;
                     if (npx < kChunkPx) bits &= (1u << npx) - 1u;
+                }
+            }
+            if (__any_sync(kFull, bits != 0u)) {
+                ClassP P;
+                P.g = g;
+                P.tol = D.gray_tol;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    P.A[i][0] = D.hueA[i][0]; P.A[i][1] = D.hueA[i][1];
+                    P.B[i][0] = D.hueB[i][0]; P.B[i][1] = D.hueB[i][1];
+                }
+                if (bits) {
+                    uint32_t sk = 0;
+#pragma unroll
+                    for (int k = 0; k < kChunkPx; ++k) sk |= skin_px(f, k, P) << k;
+                    bits &= sk;
                 }
             }
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
             if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block components: one warp, lane r holds row r of the 32x32 block `blk`
+// (columns xb.., rows yb..).  Components are enumerated in raster order of
+// their first pixel and written to the block's record slots with their area,
+// coordinate sums, box, smallest pixel index and border pixels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void emit_block_components(const DevStream &D, uint32_t m, int lane,
+                                                      int blk, int xb, int yb)
+{
+    Comp *out = D.comp + (long long)blk * kSlots;
+    uint32_t *parent = D.parent + (long long)blk * kSlots;
+    int ncomp = 0;
+    while (__any_sync(kFull, m != 0u)) {
+        int r0, c0;
+        const uint32_t c = cc_extract_first(m, lane, &r0, &c0);
+        m &= ~c;
+        const uint32_t pc = (uint32_t)__popc(c);
+        const uint32_t area = __reduce_add_sync(kFull, pc);
+        const uint32_t sx = __reduce_add_sync(kFull, pc * (uint32_t)xb + bit_index_sum(c));
+        const uint32_t sy = __reduce_add_sync(kFull, pc * (uint32_t)(yb + lane));
+        const unsigned rows = __ballot_sync(kFull, c != 0u);
+        const uint32_t xmin = __reduce_min_sync(kFull, c ? (uint32_t)(__ffs(c) - 1) : 32u);
+        const uint32_t xmax = __reduce_max_sync(kFull, c ? (uint32_t)(31 - __clz(c)) : 0u);
+        const uint32_t top = __shfl_sync(kFull, c, 0);
+        const uint32_t bot = __shfl_sync(kFull, c, 31);
+        const uint32_t left = __ballot_sync(kFull, c & 1u);
+        const uint32_t right = __ballot_sync(kFull, c >> 31);
+        if (ncomp < kSlots) {
+            uint32_t *o = reinterpret_cast<uint32_t *>(out + ncomp);
+            uint32_t val = 0;
+            switch (lane) {
+            case 0: val = (uint32_t)(yb + r0) * (uint32_t)D.w + (uint32_t)(xb + c0); break;
+            case 1: val = area; break;
+            case 2: val = sx; break;
+            case 4: val = sy; break;
+            case 6: val = (uint32_t)xb + xmin; break;
+            case 7: val = (uint32_t)(yb + __ffs(rows) - 1); break;
+            case 8: val = (uint32_t)xb + xmax; break;
+            case 9: val = (uint32_t)(yb + 31 - __clz(rows)); break;
+            case 10: val = top; break;
+            case 11: val = bot; break;
+            case 12: val = left; break;
+            case 13: val = right; break;
+            default: val = 0; break;
+            }
+            if (lane < 16) o[lane] = val;
+            if (lane == 0) parent[ncomp] = (uint32_t)ncomp + (uint32_t)blk * kSlots;
+        }
+        ++ncomp;
+    }
+    if (lane == 0) {
+        if (ncomp > kSlots) atomicOr(&D.st->err, kErrSlots);
+        D.count[blk] = (uint32_t)min(ncomp, kSlots);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_morph_strip: one warp per strip of 32 output rows x 30 words (960 px),
+// lane j = word column (lanes 0 and 31 are the left/right halo words), rows
+// (32 + 2*HR with HR = 2*(open+close) halo rows) held in registers.  Each
+// operator neutralises out-of-image pixels (1 for erosion, 0 for dilation),
+// forms the horizontal 3-pixel AND/OR with the neighbour lanes' words, then
+// the vertical 3-row AND/OR.  Garbage from the strip's own edges moves one
+// pixel per operator and never reaches the interior (HR rows, 32 - HR bits).
+// ---------------------------------------------------------------------------
+constexpr int kStripWords = 30;
+constexpr int kStripWarps = 4;
+
+template <int HR>
+__device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
+                                            uint32_t (*tr)[33], int lane)
+{
+    constexpr int R = kMorphRows + 2 * HR;
+    const int w = D.w, h = D.h, nwords = D.nwords;
+    const int kw = tx * kStripWords - 1 + lane;
+    const bool col_ok = kw >= 0 && kw < nwords;
+    const uint32_t wmask = !col_ok ? 0u : ((kw == nwords - 1 && (w & 31)) ? ((1u << (w & 31)) - 1u) : 0xffffffffu);
+    const int y0 = ty * kMorphRows;
+    const int ybase = y0 - HR;
+    const int rlo = max(0, -ybase), rhi = min(R, h - ybase);   // rows inside the image
+    uint32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ybase + r;
+        v[r] = (col_ok && r >= rlo && r < rhi) ? D.raw[(long long)y * nwords + kw] : 0u;
+    }
+    const int nops = 2 * (D.open_iters + D.close_iters);   // == HR
+    for (int op = 0; op < nops; ++op) {
+        const bool ero = (op < 2 * D.open_iters) ? ((op & 1) == 0) : (((op - 2 * D.open_iters) & 1) == 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
+            v[r] = ero ? (v[r] | ~vm) : (v[r] & vm);
+        }
+        uint32_t prev = 0, cur = 0;
+#pragma unroll
+        for (int r = 0; r <= R; ++r) {
+            uint32_t nxt = cur;
+            if (r < R) {
+                const uint32_t x = v[r];
+                const uint32_t L = __shfl_up_sync(kFull, x, 1);
+                const uint32_t Rt = __shfl_down_sync(kFull, x, 1);
+                nxt = ero ? (x & ((x << 1) | (L >> 31)) & ((x >> 1) | (Rt << 31)))
+                          : (x | (x << 1) | (L >> 31) | (x >> 1) | (Rt << 31));
+            }
+            if (r == 1) {
+                v[0] = ero ? (cur & nxt) : (cur | nxt);
+            } else if (r >= 2) {
+                v[r - 1] = ero ? (prev & cur & nxt) : (prev | cur | nxt);
+            }
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    // interior: global bit mask, mask bytes, transposed copy for components
+    const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
+#pragma unroll
+    for (int i = 0; i < kMorphRows; ++i) {
+        const int r = HR + i, y = y0 + i;
+        const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
+        tr[i][lane] = fin;
+        if (interior) {
+            D.bits[(long long)y * nwords + kw] = fin;
+            if (io.mask != nullptr && y < h) {
+                uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
+                const int npx = min(kWordPx, w - kw * kWordPx);
+                if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+                    uint32_t q[8];
+#pragma unroll
+                    for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
+                    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                    __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
+                    __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
+                } else {
+                    for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    for (int j = 1; j <= kStripWords; ++j) {
+        const int bx = tx * kStripWords - 1 + j;
+        if (bx >= nwords) break;
+        const uint32_t m = tr[lane][j];
+        if (!__any_sync(kFull, m != 0u)) {
+            if (lane == 0) D.count[ty * nwords + bx] = 0u;
+            continue;
+        }
+        emit_block_components(D, m, lane, ty * nwords + bx, bx * kWordPx, y0);
+    }
+}
+
+__global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
+{
+    __shared__ uint32_t tr[kStripWarps][kMorphRows][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t strip = blockIdx.x * kStripWarps + warp;
+    if (strip >= b.total_strips) return;   // warp-uniform
+    int lo = 0, hi = b.n;                   // largest s with strip_prefix[s] <= strip
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (b.strip_prefix[mid] <= strip) lo = mid; else hi = mid;
+    }
+    const DevStream &D = b.ds[lo];
+    const TickIO io = b.io[lo];
+    const int ls = (int)(strip - b.strip_prefix[lo]);
+    const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
+    switch (2 * (D.open_iters + D.close_iters)) {
+    case 0: morph_strip<0>(D, io, ty, tx, tr[warp], lane); break;
+    case 2: morph_strip<2>(D, io, ty, tx, tr[warp], lane); break;
+    case 4: morph_strip<4>(D, io, ty, tx, tr[warp], lane); break;
+    case 6: morph_strip<6>(D, io, ty, tx, tr[warp], lane); break;
+    case 8: morph_strip<8>(D, io, ty, tx, tr[warp], lane); break;
+    default: break;   // wider halos run k_morph_cc instead
     }
 }
 
@@ -334,56 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
     for (int k = wid; k < kMorphTW; k += blockDim.x >> 5) {
         const int kw = G.k0 + k;
         if (kw >= G.nwords) continue;
-        const int blk = ty * G.nwords + kw;
-        uint32_t m = fin[lane][k];
-        Comp *out = D.comp + (long long)blk * kSlots;
-        uint32_t *parent = D.parent + (long long)blk * kSlots;
-        const int xb = kw * kWordPx, yb = G.y0;
-        int ncomp = 0;
-        while (__any_sync(kFull, m != 0u)) {
-            int r0, c0;
-            const uint32_t c = cc_extract_first(m, lane, &r0, &c0);
-            m &= ~c;
-            const uint32_t pc = (uint32_t)__popc(c);
-            const uint32_t area = __reduce_add_sync(kFull, pc);
-            const uint32_t sx = __reduce_add_sync(kFull, pc * (uint32_t)xb + bit_index_sum(c));
-            const uint32_t sy = __reduce_add_sync(kFull, pc * (uint32_t)(yb + lane));
-            const unsigned rows = __ballot_sync(kFull, c != 0u);
-            const uint32_t xmin = __reduce_min_sync(kFull, c ? (uint32_t)(__ffs(c) - 1) : 32u);
-            const uint32_t xmax = __reduce_max_sync(kFull, c ? (uint32_t)(31 - __clz(c)) : 0u);
-            const uint32_t top = __shfl_sync(kFull, c, 0);
-            const uint32_t bot = __shfl_sync(kFull, c, 31);
-            const uint32_t left = __ballot_sync(kFull, c & 1u);
-            const uint32_t right = __ballot_sync(kFull, c >> 31);
-            if (ncomp < kSlots) {
-                uint32_t *o = reinterpret_cast<uint32_t *>(out + ncomp);
-                uint32_t val = 0;
-                switch (lane) {
-                case 0: val = (uint32_t)(yb + r0) * (uint32_t)G.w + (uint32_t)(xb + c0); break;
-                case 1: val = area; break;
-                case 2: val = sx; break;
-                case 3: val = 0; break;
-                case 4: val = sy; break;
-                case 5: val = 0; break;
-                case 6: val = (uint32_t)xb + xmin; break;
-                case 7: val = (uint32_t)(yb + __ffs(rows) - 1); break;
-                case 8: val = (uint32_t)xb + xmax; break;
-                case 9: val = (uint32_t)(yb + 31 - __clz(rows)); break;
-                case 10: val = top; break;
-                case 11: val = bot; break;
-                case 12: val = left; break;
-                case 13: val = right; break;
-                default: val = 0; break;
-                }
-                if (lane < 16) o[lane] = val;
-                if (lane == 0) parent[ncomp] = (uint32_t)ncomp + (uint32_t)blk * kSlots;
-            }
-            ++ncomp;
-        }
-        if (lane == 0) {
-            if (ncomp > kSlots) atomicOr(&D.st->err, kErrSlots);
-            D.count[blk] = (uint32_t)min(ncomp, kSlots);
-        }
+        emit_block_components(D, fin[lane][k], lane, ty * G.nwords + kw, kw * kWordPx, G.y0);
     }
 }
 
@@ -409,8 +564,12 @@ cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs)
 
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs)
 {
-    if (b.total_tiles == 0) return cudaSuccess;
-    k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
+    if (b.max_halo <= kStripMaxHalo) {
+        const unsigned grid = (b.total_strips + kStripWarps - 1) / kStripWarps;
+        k_morph_strip<<<grid, kStripWarps * 32, 0, cs>>>(b);
+    } else {
+        k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
+    }
     return cudaGetLastError();
 }
 

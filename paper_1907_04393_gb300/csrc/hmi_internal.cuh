@@ -19,6 +19,7 @@ constexpr int kSlots = 256;        // max 8-connected components in a 32x32 bloc
 constexpr int kMorphTW = 8;        // morphology tile width in words (256 px)
 constexpr int kMorphRows = 32;     // morphology tile height (one CC block row)
 constexpr int kMaxHalo = 32;       // 2 * (open_iters + close_iters) <= 32
+constexpr int kStripMaxHalo = 8;   // register strips handle halos up to 8 rows
 constexpr int kMaxDim = 8192;
 constexpr int kMaxBatch = 4096;
 constexpr uint32_t kLoopLimit = 1u << 22;  // bound on every device-side retry loop
@@ -62,6 +63,7 @@ struct DevStream {
     int nwords;                   // ceil(w / 32): bit words per row == CC blocks per block-row
     int bh;                       // ceil(h / 32): CC block rows
     int tiles_x;                  // ceil(nwords / kMorphTW)
+    int strips_x;                 // ceil(nwords / 30): register-strip tiles per block-row
     int fpitch;                   // bytes per row of the band (and of the staging frame)
     int gray_tol;
     int open_iters, close_iters;
@@ -98,6 +100,9 @@ struct BatchDev {
     uint32_t total_blocks;                    // sum bh * nwords
     const unsigned long long *chunk_prefix;   // n + 1 entries
     const uint32_t *tile_prefix;              // n + 1
+    const uint32_t *strip_prefix;             // n + 1
+    uint32_t total_strips;                    // sum bh * strips_x
+    int max_halo;                             // largest 2 * (open + close) of the batch
     const uint32_t *block_prefix;             // n + 1
     uint32_t *done;                           // last-block counters [4]
     const int4 *pieces;                       // (stream, chunk begin, chunk end, 0)
@@ -114,9 +119,7 @@ constexpr int kThreads = 256;
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs);
-cudaError_t launch_merge(const BatchDev &b, cudaStream_t cs);
-cudaError_t launch_resolve(const BatchDev &b, cudaStream_t cs);
-cudaError_t launch_pointer(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
                           cudaStream_t cs);
 
