@@ -47,7 +47,7 @@ int cuda_fail(cudaError_t e)
     } while (0)
 
 constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
-constexpr int kPieceChunks = 1024;  // 16-px chunks per CTA piece (16384 px)
+constexpr int kPieceChunks = 512;   // 16-px chunks per CTA piece (8192 px)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

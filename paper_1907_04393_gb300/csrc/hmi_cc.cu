@@ -120,43 +120,28 @@ __device__ void resolve_block(const DevStream &D, uint32_t lb, uint32_t *err)
     }
 }
 
-// Pointer of one stream from its packed argmax, then the click state machine:
-// A_ref = max area of the last click_window valid frames; a valid frame sets
-// the click when 100*area < on*A_ref and clears it when 100*area > off*A_ref
-// (no history yet: no click) and is then appended; an invalid frame changes
-// nothing.
-__device__ void finalize_stream(const DevStream &D, const TickIO &io)
+// Pointer of one stream from its largest component's statistics (has == 0:
+// no foreground), then the click state machine: A_ref = max area of the last
+// click_window valid frames; a valid frame sets the click when
+// 100*area < on*A_ref and clears it when 100*area > off*A_ref (no history yet:
+// no click) and is then appended; an invalid frame changes nothing.
+__device__ void finalize_pointer(const DevStream &D, const TickIO &io, bool has, uint32_t area,
+                                 uint32_t key, unsigned long long sx, unsigned long long sy,
+                                 int x0, int y0, int x1, int y1)
 {
     StreamState *st = D.st;
-    const unsigned long long best = *(volatile unsigned long long *)&st->best;
     hmi_pointer P;
-    if (best == 0ull) {
+    if (!has) {
         P.valid = 0; P.area = 0; P.label = -1;
         P.x0 = P.y0 = P.x1 = P.y1 = -1;
         P.x = -1.0f; P.y = -1.0f;
     } else {
-        const uint32_t area = (uint32_t)(best >> 32);
-        const uint32_t key = 0xffffffffu - (uint32_t)(best & 0xffffffffull);
-        const uint32_t y = key / (uint32_t)D.w, x = key - y * (uint32_t)D.w;
-        const uint32_t blk = (y / kBlock) * (uint32_t)D.nwords + x / kWordPx;
-        const uint32_t cnt = D.count[blk];
-        uint32_t r = 0xffffffffu;
-        for (uint32_t j = 0; j < cnt; ++j)
-            if (D.comp[blk * kSlots + j].key == key) { r = blk * kSlots + j; break; }
-        if (r == 0xffffffffu) {
-            atomicOr(&st->err, kErrRoot);
-            P.valid = 0; P.area = 0; P.label = -1;
-            P.x0 = P.y0 = P.x1 = P.y1 = -1;
-            P.x = -1.0f; P.y = -1.0f;
-        } else {
-            const Comp &C = D.comp[r];
-            P.area = area;
-            P.label = (int32_t)key;
-            P.valid = area >= D.min_area ? 1 : 0;
-            P.x = (float)((double)C.sx / (double)area);
-            P.y = (float)((double)C.sy / (double)area);
-            P.x0 = C.x0; P.y0 = C.y0; P.x1 = C.x1; P.y1 = C.y1;
-        }
+        P.area = area;
+        P.label = (int32_t)key;
+        P.valid = area >= D.min_area ? 1 : 0;
+        P.x = (float)((double)sx / (double)area);
+        P.y = (float)((double)sy / (double)area);
+        P.x0 = x0; P.y0 = y0; P.x1 = x1; P.y1 = y1;
     }
     if (P.valid) {
         const int win = D.click_window;
@@ -189,52 +174,101 @@ __device__ void finalize_stream(const DevStream &D, const TickIO &io)
     if (io.ptr_out != nullptr) *io.ptr_out = P;
 }
 
-// One CTA per stream: the blocks that hold components are compacted into
-// shared memory, then (separated by CTA barriers, no grid-wide wait) their
-// borders are merged, non-roots are added into their roots, the largest root
-// is chosen with a shared 64-bit atomicMax on (area, ~key), and thread 0
-// writes the pointer and steps the click state.
-constexpr int kFinishThreads = 512;
-constexpr int kActCap = 4096;
-
-__global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
+// Pointer from the packed argmax (area, ~key) over the global records.
+__device__ void finalize_stream(const DevStream &D, const TickIO &io, unsigned long long best)
 {
-    __shared__ uint32_t act[kActCap];
-    __shared__ uint32_t nact;
-    __shared__ unsigned long long best;
-    const int tid = threadIdx.x;
-    const DevStream &D = b.ds[blockIdx.x];
-    const TickIO io = b.io[blockIdx.x];
+    if (best == 0ull) {
+        finalize_pointer(D, io, false, 0, 0, 0, 0, 0, 0, 0, 0);
+        return;
+    }
+    const uint32_t area = (uint32_t)(best >> 32);
+    const uint32_t key = 0xffffffffu - (uint32_t)(best & 0xffffffffull);
+    const uint32_t y = key / (uint32_t)D.w, x = key - y * (uint32_t)D.w;
+    const uint32_t blk = (y / kBlock) * (uint32_t)D.nwords + x / kWordPx;
+    const uint32_t cnt = D.count[blk];
+    for (uint32_t j = 0; j < cnt; ++j) {
+        const Comp &C = D.comp[blk * kSlots + j];
+        if (C.key == key) {
+            finalize_pointer(D, io, true, area, key, __ldcg(&C.sx), __ldcg(&C.sy), __ldcg(&C.x0),
+                             __ldcg(&C.y0), __ldcg(&C.x1), __ldcg(&C.y1));
+            return;
+        }
+    }
+    atomicOr(&D.st->err, kErrRoot);
+    finalize_pointer(D, io, false, 0, 0, 0, 0, 0, 0, 0, 0);
+}
+
+// One CTA per stream.  The blocks that hold components are listed in
+// ascending order in shared memory and their component records copied there;
+// the border merge (union-find with atomicCAS on shared parents, larger key
+// hooked under the smaller), the resolve of non-roots into roots, and the
+// argmax on (area, ~key) then all run in shared memory between CTA barriers,
+// with no grid-wide wait.  Final roots are written back to the global parent
+// array for the on-demand labels.  A stream with more than kActCap non-empty
+// blocks or kRecCap components runs the same steps on the global arrays.
+constexpr int kFinishThreads = 512;
+constexpr int kActCap = 2048;
+constexpr int kRecCap = 1024;
+
+struct FinishSmem {
+    Comp rec[kRecCap];
+    uint32_t parent[kRecCap];
+    uint32_t act[kActCap];       // non-empty blocks, ascending
+    uint32_t rbase[kActCap + 1]; // first record of each listed block
+    uint32_t wsum[kFinishThreads / 32];
+    uint32_t nact, nrec, pick;
+    unsigned long long best;
+    bool overflow;
+};
+
+__device__ __forceinline__ uint32_t sm_find(const uint32_t *parent, uint32_t x)
+{
+    for (int it = 0; it < kRecCap + 1; ++it) {
+        const uint32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void sm_unite(uint32_t *parent, const Comp *rec, uint32_t a, uint32_t b)
+{
+    for (int it = 0; it < 4 * kRecCap; ++it) {
+        a = sm_find(parent, a);
+        b = sm_find(parent, b);
+        if (a == b) return;
+        if (rec[a].key < rec[b].key) {
+            const uint32_t t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(parent + a, a, b) == a) return;
+    }
+}
+
+// index of block blk in the ascending list act[0..n), or -1
+__device__ __forceinline__ int act_index(const uint32_t *act, uint32_t n, uint32_t blk)
+{
+    int lo = 0, hi = (int)n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (act[mid] < blk) lo = mid + 1; else hi = mid;
+    }
+    return (lo < (int)n && act[lo] == blk) ? lo : -1;
+}
+
+__device__ void finish_global(const DevStream &D, const TickIO &io, unsigned long long *best)
+{
     uint32_t *err = &D.st->err;
     const uint32_t nblk = (uint32_t)D.bh * (uint32_t)D.nwords;
-    if (tid == 0) {
-        nact = 0;
-        best = 0;
+    for (uint32_t it = threadIdx.x; it < 4 * nblk; it += blockDim.x) {
+        const uint32_t lb = it >> 2;
+        if (D.count[lb] != 0u) merge_dir(D, lb, (int)(it & 3), err);
     }
     __syncthreads();
-    for (uint32_t base = 0; base < nblk; base += blockDim.x) {
-        const uint32_t blk = base + tid;
-        const bool a = blk < nblk && D.count[blk] != 0u;
-        const unsigned m = __ballot_sync(kFull, a);
-        uint32_t pos = 0;
-        if ((tid & 31) == 0 && m) pos = atomicAdd(&nact, (uint32_t)__popc(m));
-        pos = __shfl_sync(kFull, pos, 0) + (uint32_t)__popc(m & ((1u << (tid & 31)) - 1u));
-        if (a && pos < kActCap) act[pos] = blk;
-    }
+    for (uint32_t lb = threadIdx.x; lb < nblk; lb += blockDim.x) resolve_block(D, lb, err);
     __syncthreads();
-    const uint32_t na = nact;
-    const bool fits = na <= (uint32_t)kActCap;
-    const uint32_t nitems = fits ? na : nblk;
-    for (uint32_t it = tid; it < 4 * nitems; it += blockDim.x) {
-        const uint32_t lb = fits ? act[it >> 2] : (it >> 2);
-        if (!fits && D.count[lb] == 0u) continue;
-        merge_dir(D, lb, (int)(it & 3), err);
-    }
-    __syncthreads();
-    for (uint32_t it = tid; it < nitems; it += blockDim.x) resolve_block(D, fits ? act[it] : it, err);
-    __syncthreads();
-    for (uint32_t it = tid; it < nitems; it += blockDim.x) {
-        const uint32_t lb = fits ? act[it] : it;
+    for (uint32_t lb = threadIdx.x; lb < nblk; lb += blockDim.x) {
         const uint32_t cnt = D.count[lb];
         for (uint32_t j = 0; j < cnt; ++j) {
             const uint32_t id = lb * kSlots + j;
@@ -242,13 +276,174 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
             const Comp &C = D.comp[id];
             const unsigned long long packed = ((unsigned long long)__ldcg(&C.area) << 32) |
                                               (unsigned long long)(0xffffffffu - C.key);
-            atomicMax(&best, packed);
+            atomicMax(best, packed);
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0) finalize_stream(D, io, *best);
+}
+
+__global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FinishSmem &S = *reinterpret_cast<FinishSmem *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const DevStream &D = b.ds[blockIdx.x];
+    const TickIO io = b.io[blockIdx.x];
+    const uint32_t nblk = (uint32_t)D.bh * (uint32_t)D.nwords;
     if (tid == 0) {
-        D.st->best = best;
-        finalize_stream(D, io);
+        S.nact = 0;
+        S.nrec = 0;
+        S.best = 0;
+        S.overflow = false;
+    }
+    __syncthreads();
+    // ordered list of non-empty blocks and their record offsets
+    for (uint32_t base = 0; base < nblk; base += blockDim.x) {
+        const uint32_t blk = base + tid;
+        const uint32_t cnt = blk < nblk ? D.count[blk] : 0u;
+        const unsigned m = __ballot_sync(kFull, cnt != 0u);
+        if (lane == 0) S.wsum[wid] = (uint32_t)__popc(m);
+        __syncthreads();
+        uint32_t off = S.nact;
+        for (int i = 0; i < wid; ++i) off += S.wsum[i];
+        const uint32_t pos = off + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        if (cnt != 0u && pos < (uint32_t)kActCap) {
+            S.act[pos] = blk;
+            S.rbase[pos] = cnt;   // counts for now, offsets below
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += S.wsum[i];
+            S.nact += t;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (S.nact > (uint32_t)kActCap) {
+            S.overflow = true;
+        } else {
+            uint32_t acc = 0;
+            for (uint32_t i = 0; i < S.nact; ++i) {
+                const uint32_t c = S.rbase[i];
+                S.rbase[i] = acc;
+                acc += c;
+            }
+            S.rbase[S.nact] = acc;
+            S.nrec = acc;
+            if (acc > (uint32_t)kRecCap) S.overflow = true;
+        }
+    }
+    __syncthreads();
+    if (S.overflow) {
+        finish_global(D, io, &S.best);
+        if (tid == 0) {
+            const uint32_t e = D.st->err;
+            if (e) atomicOr(b.err, e);
+        }
+        return;
+    }
+    const uint32_t na = S.nact, nr = S.nrec;
+    // copy the records
+    for (uint32_t r = tid; r < nr; r += blockDim.x) {
+        int lo = 0, hi = (int)na - 1;   // last i with rbase[i] <= r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.rbase[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t gid = S.act[lo] * kSlots + (r - S.rbase[lo]);
+        const uint4 *src = reinterpret_cast<const uint4 *>(D.comp + gid);
+        uint4 *dst = reinterpret_cast<uint4 *>(S.rec + r);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = src[q];
+        S.parent[r] = r;
+    }
+    __syncthreads();
+    // border merge: item = (listed block, direction)
+    const int nw = D.nwords;
+    for (uint32_t it = tid; it < 4 * na; it += blockDim.x) {
+        const uint32_t i = it >> 2, dir = it & 3;
+        const uint32_t lb = S.act[i];
+        const int by = (int)lb / nw, bx = (int)lb - by * nw;
+        int nbb;
+        if (dir == 0) nbb = (bx + 1 < nw) ? (int)lb + 1 : -1;
+        else if (dir == 1) nbb = (by + 1 < D.bh) ? (int)lb + nw : -1;
+        else if (dir == 2) nbb = (by + 1 < D.bh && bx + 1 < nw) ? (int)lb + nw + 1 : -1;
+        else nbb = (by + 1 < D.bh && bx > 0) ? (int)lb + nw - 1 : -1;
+        if (nbb < 0) continue;
+        const int ni = act_index(S.act, na, (uint32_t)nbb);
+        if (ni < 0) continue;
+        for (uint32_t a = S.rbase[i]; a < S.rbase[i + 1]; ++a) {
+            const uint32_t edge = (dir == 0) ? S.rec[a].right : S.rec[a].bot;
+            if (edge == 0u) continue;
+            if (dir == 2 && !(edge >> 31)) continue;
+            if (dir == 3 && !(edge & 1u)) continue;
+            for (uint32_t c = S.rbase[ni]; c < S.rbase[ni + 1]; ++c) {
+                bool touch;
+                if (dir == 0) {
+                    const uint32_t L = S.rec[c].left;
+                    touch = (edge & (L | (L << 1) | (L >> 1))) != 0u;
+                } else if (dir == 1) {
+                    const uint32_t T = S.rec[c].top;
+                    touch = (edge & (T | (T << 1) | (T >> 1))) != 0u;
+                } else if (dir == 2) {
+                    touch = (S.rec[c].top & 1u) != 0u;
+                } else {
+                    touch = (S.rec[c].top >> 31) != 0u;
+                }
+                if (touch) sm_unite(S.parent, S.rec, a, c);
+            }
+        }
+    }
+    __syncthreads();
+    // resolve: non-roots into roots; final roots back to the global parents
+    for (uint32_t r = tid; r < nr; r += blockDim.x) {
+        const uint32_t root = sm_find(S.parent, r);
+        int lo = 0, hi = (int)na - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.rbase[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        int lo2 = 0, hi2 = (int)na - 1;
+        while (lo2 < hi2) {
+            const int mid = (lo2 + hi2 + 1) >> 1;
+            if (S.rbase[mid] <= root) lo2 = mid; else hi2 = mid - 1;
+        }
+        D.parent[S.act[lo] * kSlots + (r - S.rbase[lo])] = S.act[lo2] * kSlots + (root - S.rbase[lo2]);
+        if (root == r) continue;
+        const Comp &A = S.rec[r];
+        Comp &R = S.rec[root];
+        atomicAdd(&R.area, A.area);
+        atomicAdd(&R.sx, A.sx);
+        atomicAdd(&R.sy, A.sy);
+        atomicMin(&R.x0, A.x0);
+        atomicMin(&R.y0, A.y0);
+        atomicMax(&R.x1, A.x1);
+        atomicMax(&R.y1, A.y1);
+    }
+    __syncthreads();
+    for (uint32_t r = tid; r < nr; r += blockDim.x) {
+        if (S.parent[r] != r) continue;
+        const unsigned long long packed = ((unsigned long long)S.rec[r].area << 32) |
+                                          (unsigned long long)(0xffffffffu - S.rec[r].key);
+        atomicMax(&S.best, packed);
+    }
+    __syncthreads();
+    const unsigned long long best = S.best;
+    for (uint32_t r = tid; r < nr; r += blockDim.x) {
+        if (S.parent[r] == r && best != 0ull &&
+            S.rec[r].key == 0xffffffffu - (uint32_t)(best & 0xffffffffull))
+            S.pick = r;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (best == 0ull) {
+            finalize_pointer(D, io, false, 0, 0, 0, 0, 0, 0, 0, 0);
+        } else {
+            const Comp &C = S.rec[S.pick];
+            finalize_pointer(D, io, true, C.area, C.key, C.sx, C.sy, C.x0, C.y0, C.x1, C.y1);
+        }
         const uint32_t e = D.st->err;
         if (e) atomicOr(b.err, e);
     }
@@ -293,7 +488,17 @@ __global__ void __launch_bounds__(kThreads) k_labels(const DevStream *dsp, int32
 // ---------------------------------------------------------------------------
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs)
 {
-    k_finish<<<b.n, kFinishThreads, 0, cs>>>(b);
+    static bool attr_set[64] = {};   // the shared-memory opt-in is per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FinishSmem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    k_finish<<<b.n, kFinishThreads, sizeof(FinishSmem), cs>>>(b);
     return cudaGetLastError();
 }
 

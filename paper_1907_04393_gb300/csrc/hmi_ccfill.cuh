@@ -46,14 +46,35 @@ __device__ __forceinline__ uint32_t run_fill(uint32_t c, uint32_t m)
     return fill_up(c, m) | fill_down(c, m);
 }
 
+// Propagate the bits of g along the columns (lane r -> r+1 -> ...) through
+// vertical runs of p, and the other way (lane r -> r-1 -> ...); logarithmic
+// fills across lanes with shuffles.  g must be a subset of p.
+__device__ __forceinline__ uint32_t col_fill(uint32_t g, uint32_t p, int lane)
+{
+    uint32_t gd = g, pd = p, gu = g, pu = p;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        uint32_t a = __shfl_up_sync(kFull, gd, s), b = __shfl_up_sync(kFull, pd, s);
+        if (lane < s) a = b = 0u;
+        gd |= pd & a;
+        pd &= b;
+        uint32_t c = __shfl_down_sync(kFull, gu, s), d = __shfl_down_sync(kFull, pu, s);
+        if (lane >= 32 - s) c = d = 0u;
+        gu |= pu & c;
+        pu &= d;
+    }
+    return gd | gu;
+}
+
 // Extract the component of the first remaining pixel in raster order
 // (lowest row, then lowest column) from the per-lane row words m.
 // Returns this lane's row of the component; *seed_row / *seed_col give the
 // seed, which is the component's smallest pixel index inside the block.
-// Grows by whole runs, then by one row up and down (8-connected: the grown
-// set is widened by one column before the vertical step), until stable.
-// Every round that does not stop adds at least one pixel, so the loop ends
-// within 1024 rounds.
+// Each round grows the set by whole horizontal runs, whole vertical runs, and
+// the 8-neighbours in the rows above and below, until a round adds nothing;
+// the fixed point is closed under every 8-neighbour step, so it is the whole
+// component.  A round that does not stop adds at least one pixel, so the loop
+// ends within 1024 rounds (a convex blob takes about three).
 __device__ __forceinline__ uint32_t cc_extract_first(uint32_t m, int lane, int *seed_row,
                                                      int *seed_col)
 {
@@ -66,6 +87,7 @@ __device__ __forceinline__ uint32_t cc_extract_first(uint32_t m, int lane, int *
     uint32_t c = (lane == r0) ? (1u << b0) : 0u;
     for (int it = 0; it < 1100; ++it) {
         c = run_fill(c, m);
+        c = col_fill(c, m, lane);
         uint32_t d = c | (c << 1) | (c >> 1);
         uint32_t up = __shfl_up_sync(kFull, d, 1);
         uint32_t dn = __shfl_down_sync(kFull, d, 1);

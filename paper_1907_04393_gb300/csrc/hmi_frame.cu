@@ -52,7 +52,7 @@ __device__ __forceinline__ void load48(const uint8_t *src, uint64_t pol, uint32_
 
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
 {
-    return (w[b >> 2] >> (8 * (b & 3))) & 0xffu;
+    return __byte_perm(w[b >> 2], 0u, 0x4440u | (uint32_t)(b & 3));
 }
 
 // Integer BT.601 luma, (77 R + 150 G + 29 B + 128) >> 8.
@@ -77,20 +77,32 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
         const int w = D.w, cpr = 2 * D.nwords;
         const uint64_t keep = policy_evict_last();
         unsigned long long acc = 0;
-        for (int u = piece.y + tid; u < piece.z; u += blockDim.x) {
-            const int y = u / cpr, j = u - y * cpr;
-            const int x0 = j * kChunkPx;
-            if (x0 >= w) continue;
-            uint32_t f[12];
-            load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f);
-            const int npx = min(kChunkPx, w - x0);
-            uint32_t sum = 0;
+        // two chunks per thread per round, both loads in flight before the sums
+        for (int u = piece.y + tid; u < piece.z; u += 2 * blockDim.x) {
+            uint32_t f[2][12];
+            int npx[2];
 #pragma unroll
-            for (int k = 0; k < kChunkPx; ++k) {
-                uint32_t v = luma8(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2));
-                sum += (k < npx) ? v : 0u;
+            for (int q = 0; q < 2; ++q) {
+                const int uu = u + q * (int)blockDim.x;
+                npx[q] = 0;
+                if (uu < piece.z) {
+                    const int y = uu / cpr, x0 = (uu - y * cpr) * kChunkPx;
+                    if (x0 < w) {
+                        npx[q] = min(kChunkPx, w - x0);
+                        load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
+                    }
+                }
             }
-            acc += sum;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t sum = 0;
+#pragma unroll
+                for (int k = 0; k < kChunkPx; ++k) {
+                    const uint32_t v = luma8(byte_of(f[q], 3 * k), byte_of(f[q], 3 * k + 1), byte_of(f[q], 3 * k + 2));
+                    sum += (k < npx[q]) ? v : 0u;
+                }
+                acc += sum;
+            }
         }
         // CTA reduction, one atomic per piece
 #pragma unroll
@@ -140,45 +152,71 @@ __device__ __forceinline__ int corr(uint32_t c, uint32_t g)
 }
 
 // Background test of one pixel (Sec. 3.1 (i)): 1 iff some gain-corrected
-// channel lies outside the learned band [lo, hi].
-__device__ __forceinline__ uint32_t outside_band(const uint32_t (&f)[12], const uint32_t (&l)[12],
-                                                 const uint32_t (&h)[12], int k, uint32_t g)
+// channel lies outside the learned band [lo, hi].  Compared in the scaled
+// domain: with Y = min(c g + 2^15, 255 * 2^16 + 2^15),
+//   c' >= lo  <=>  Y >= lo << 16      and      c' <= hi  <=>  Y <= (hi << 16) | 0xffff,
+// where byte permutes place lo / hi straight into bits 16..23.
+template <int K>
+__device__ __forceinline__ bool in_band(const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                        const uint32_t (&h)[12], uint32_t g)
 {
-    const int q = 3 * k;
-    const int r = corr(byte_of(f, q), g), gg = corr(byte_of(f, q + 1), g), b = corr(byte_of(f, q + 2), g);
-    const bool in = (r >= (int)byte_of(l, q)) & (r <= (int)byte_of(h, q)) &
-                    (gg >= (int)byte_of(l, q + 1)) & (gg <= (int)byte_of(h, q + 1)) &
-                    (b >= (int)byte_of(l, q + 2)) & (b <= (int)byte_of(h, q + 2));
-    return in ? 0u : 1u;
+    constexpr int W = K >> 2, B = K & 3;
+    const uint32_t c = __byte_perm(f[W], 0u, 0x4440u | B);
+    const uint32_t y = min(c * g + 32768u, 255u * 65536u + 32768u);
+    const uint32_t lo16 = __byte_perm(l[W], 0u, 0x4044u | (B << 8));
+    const uint32_t hi16 = __byte_perm(h[W], 0x0000ffffu, 0x6054u | (B << 8));
+    return (y >= lo16) & (y <= hi16);
+}
+
+template <int k>
+__device__ __forceinline__ uint32_t outside_band(const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                                 const uint32_t (&h)[12], uint32_t g)
+{
+    const bool in = in_band<3 * k>(f, l, h, g) & in_band<3 * k + 1>(f, l, h, g) &
+                    in_band<3 * k + 2>(f, l, h, g);
+    return in ? 0u : (1u << k);
+}
+
+template <int k>
+__device__ __forceinline__ uint32_t outside_bits(const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                                 const uint32_t (&h)[12], uint32_t g)
+{
+    if constexpr (k == 0) {
+        return outside_band<0>(f, l, h, g);
+    } else {
+        return outside_band<k>(f, l, h, g) | outside_bits<k - 1>(f, l, h, g);
+    }
 }
 
 // Gray and hue tests of one pixel (Sec. 3.1 (ii), (iii)) on the corrected
 // values: not gray (max - min >= S) and hue inside the arc.  The hue test
 // compares N = 512 (t + d) + d against d-scaled interval ends, which equals
 // testing h = base - 256 + floor(N / 2d) without a division.
-__device__ __forceinline__ uint32_t skin_px(const uint32_t (&f)[12], int k, const ClassP &P)
+__device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, const DevStream &D,
+                                         uint32_t gain)
 {
-    const int q = 3 * k;
-    const int r = corr(byte_of(f, q), P.g), g = corr(byte_of(f, q + 1), P.g), b = corr(byte_of(f, q + 2), P.g);
+    const int r = corr(r0, gain), g = corr(g0, gain), b = corr(b0, gain);
     const int mx = max(r, max(g, b));
     const int mn = min(r, min(g, b));
     const int d = mx - mn;
-    int t, a0, b0, a1, b1;
+    int t, sec;
     if (r == mx) {
-        t = g - b; a0 = P.A[0][0]; b0 = P.B[0][0]; a1 = P.A[0][1]; b1 = P.B[0][1];
+        t = g - b; sec = 0;
     } else if (g == mx) {
-        t = b - r; a0 = P.A[1][0]; b0 = P.B[1][0]; a1 = P.A[1][1]; b1 = P.B[1][1];
+        t = b - r; sec = 1;
     } else {
-        t = r - g; a0 = P.A[2][0]; b0 = P.B[2][0]; a1 = P.A[2][1]; b1 = P.B[2][1];
+        t = r - g; sec = 2;
     }
     const int N = 512 * (t + d) + d;
-    const bool hue = ((N >= d * a0) & (N < d * b0)) | ((N >= d * a1) & (N < d * b1));
-    return (uint32_t)((d > 0) & (d >= P.tol) & hue);
+    const bool hue = ((N >= d * D.hueA[sec][0]) & (N < d * D.hueB[sec][0])) |
+                     ((N >= d * D.hueA[sec][1]) & (N < d * D.hueB[sec][1]));
+    return (d > 0) & (d >= D.gray_tol) & hue;
 }
 
-// One thread per 16-pixel chunk: the background test for all 16 pixels first;
-// the gray and hue tests only run when some pixel of the warp's 512 is
-// outside its background band (in practice: warps that overlap the hand).
+// One thread per 16-pixel chunk.  The background test runs on all 16
+// pixels; the gray and hue tests run only on the pixels that are outside
+// their band (camera noise and the hand: a few per thousand), one per lane
+// per round, reading their three bytes again (an L1 hit).
 __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -196,36 +234,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
             const int u = base + lane;
             uint32_t bits = 0;
             int y = 0, j = 0, x0 = 0;
-            uint32_t f[12];
             if (u < piece.z) {
                 y = u / cpr;
                 j = u - y * cpr;
                 x0 = j * kChunkPx;
                 if (x0 < w) {
-                    uint32_t l[12], h[12];
+                    uint32_t f[12], l[12], h[12];
                     load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                     load48(lo + (long long)y * fpitch + 3 * x0, once, l);
                     load48(hi + (long long)y * fpitch + 3 * x0, once, h);
-#pragma unroll
-                    for (int k = 0; k < kChunkPx; ++k) bits |= outside_band(f, l, h, k, g) << k;
+                    bits = outside_bits<kChunkPx - 1>(f, l, h, g);
                     const int npx = w - x0;
                     if (npx < kChunkPx) bits &= (1u << npx) - 1u;
                 }
             }
-            if (__any_sync(kFull, bits != 0u)) {
-                ClassP P;
-                P.g = g;
-                P.tol = D.gray_tol;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    P.A[i][0] = D.hueA[i][0]; P.A[i][1] = D.hueA[i][1];
-                    P.B[i][0] = D.hueB[i][0]; P.B[i][1] = D.hueB[i][1];
-                }
-                if (bits) {
-                    uint32_t sk = 0;
-#pragma unroll
-                    for (int k = 0; k < kChunkPx; ++k) sk |= skin_px(f, k, P) << k;
-                    bits &= sk;
+            uint32_t todo = bits;
+            const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * x0;
+            while (__any_sync(kFull, todo != 0u)) {
+                if (todo) {
+                    const int k = __ffs(todo) - 1;
+                    const uint8_t *px = row + 3 * k;
+                    if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) bits &= ~(1u << k);
+                    todo &= todo - 1u;
                 }
             }
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
