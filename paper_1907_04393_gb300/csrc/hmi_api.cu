@@ -188,6 +188,7 @@ struct hmi_batch {
     int next = 0;
     BatchDev bd{};
     cudaStream_t cs = nullptr;    // stream of the synchronous form and of graph capture
+    int num_sms = 1;
     cudaGraph_t graph_src[kRing] = {};   // kept alive: its event-node handles retarget events
     cudaGraphExec_t graph[kRing] = {};
     cudaGraphNode_t ev_node[kRing][2] = {};
@@ -323,6 +324,8 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     const size_t o_io = a.take(sizeof(TickIO) * n * kRing);
     const size_t o_ptr = a.take(sizeof(hmi_pointer) * n);
     const size_t o_err = a.take(sizeof(uint32_t));
+    const size_t o_ccn = a.take(sizeof(uint32_t));
+    const size_t o_ccl = a.take(sizeof(uint2) * std::max<size_t>(bpre[n], 1));
     bool ok = cudaMalloc(&b->arena, a.off) == cudaSuccess &&
               cudaMallocHost(&b->h_io, sizeof(TickIO) * n * kRing) == cudaSuccess &&
               cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
@@ -374,6 +377,11 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     bd.pieces = reinterpret_cast<const int4 *>(A + o_p);
     bd.npieces = (int)pieces.size();
     bd.err = b->d_err;
+    bd.cc_count = reinterpret_cast<uint32_t *>(A + o_ccn);
+    bd.cc_list = reinterpret_cast<uint2 *>(A + o_ccl);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
+    b->num_sms = sms > 0 ? sms : 1;
     return b;
 }
 
@@ -394,7 +402,7 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;
     if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
         return e;
-    if ((e = launch_morph_cc(bd, cs)) != cudaSuccess) return e;
+    if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
     return launch_finish(bd, cs);
 }
 

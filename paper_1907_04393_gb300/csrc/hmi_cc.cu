@@ -127,7 +127,7 @@ __device__ void resolve_block(const DevStream &D, uint32_t lb, uint32_t *err)
 // no click) and is then appended; an invalid frame changes nothing.
 __device__ void finalize_pointer(const DevStream &D, const TickIO &io, bool has, uint32_t area,
                                  uint32_t key, unsigned long long sx, unsigned long long sy,
-                                 int x0, int y0, int x1, int y1)
+                                 int x0, int y0, int x1, int y1, const uint32_t *hist_copy = nullptr)
 {
     StreamState *st = D.st;
     hmi_pointer P;
@@ -149,8 +149,9 @@ __device__ void finalize_pointer(const DevStream &D, const TickIO &io, bool has,
             st->click = 0;
         } else {
             unsigned long long aref = 0;
+            const uint32_t *hs = hist_copy ? hist_copy : D.hist;
             for (int i = 0; i < st->hist_count; ++i) {
-                const uint32_t a = D.hist[(st->hist_head + i) % win];
+                const uint32_t a = hs[(st->hist_head + i) % win];
                 if (a > aref) aref = a;
             }
             const unsigned long long a100 = 100ull * P.area;
@@ -212,6 +213,7 @@ constexpr int kRecCap = 1024;
 
 struct FinishSmem {
     Comp rec[kRecCap];
+    uint32_t hist[1024];         // click history (click_window <= 1024)
     uint32_t parent[kRecCap];
     uint32_t act[kActCap];       // non-empty blocks, ascending
     uint32_t rbase[kActCap + 1]; // first record of each listed block
@@ -296,7 +298,9 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         S.nrec = 0;
         S.best = 0;
         S.overflow = false;
+        if (blockIdx.x == 0) *b.cc_count = 0u;   // k_block_cc has finished with the list
     }
+    for (int i = tid; i < D.click_window; i += blockDim.x) S.hist[i] = D.hist[i];
     __syncthreads();
     // ordered list of non-empty blocks and their record offsets
     for (uint32_t base = 0; base < nblk; base += blockDim.x) {
@@ -320,19 +324,40 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        if (S.nact > (uint32_t)kActCap) {
-            S.overflow = true;
-        } else {
-            uint32_t acc = 0;
-            for (uint32_t i = 0; i < S.nact; ++i) {
-                const uint32_t c = S.rbase[i];
-                S.rbase[i] = acc;
-                acc += c;
-            }
-            S.rbase[S.nact] = acc;
-            S.nrec = acc;
-            if (acc > (uint32_t)kRecCap) S.overflow = true;
+    if (S.nact > (uint32_t)kActCap) {
+        if (tid == 0) S.overflow = true;
+    } else {
+        // exclusive scan of the listed blocks' counts, kActCap / blockDim per thread
+        constexpr int kPer = kActCap / kFinishThreads;
+        const uint32_t na0 = S.nact;
+        uint32_t v[kPer], run = 0;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t i = (uint32_t)tid * kPer + q;
+            v[q] = i < na0 ? S.rbase[i] : 0u;
+            run += v[q];
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += t;
+        }
+        __syncthreads();
+        if (lane == 31) S.wsum[wid] = incl;
+        __syncthreads();
+        uint32_t off = incl - run;
+        for (int i = 0; i < wid; ++i) off += S.wsum[i];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t i = (uint32_t)tid * kPer + q;
+            if (i < na0) S.rbase[i] = off;
+            off += v[q];
+        }
+        if (tid == kFinishThreads - 1) {
+            S.rbase[na0] = off;
+            S.nrec = off;
+            if (off > (uint32_t)kRecCap) S.overflow = true;
         }
     }
     __syncthreads();
@@ -442,7 +467,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
             finalize_pointer(D, io, false, 0, 0, 0, 0, 0, 0, 0, 0);
         } else {
             const Comp &C = S.rec[S.pick];
-            finalize_pointer(D, io, true, C.area, C.key, C.sx, C.sy, C.x0, C.y0, C.x1, C.y1);
+            finalize_pointer(D, io, true, C.area, C.key, C.sx, C.sy, C.x0, C.y0, C.x1, C.y1, S.hist);
         }
         const uint32_t e = D.st->err;
         if (e) atomicOr(b.err, e);

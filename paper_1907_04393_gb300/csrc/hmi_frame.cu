@@ -10,6 +10,8 @@
 //               module, Sec. 2)
 // All three are pure integer/bit work and bound by HBM bandwidth; nothing here
 // is a dense contraction, so no tensor-core path is used.
+#include <algorithm>
+
 #include "hmi_ccfill.cuh"
 #include "hmi_internal.cuh"
 
@@ -234,12 +236,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
             const int u = base + lane;
             uint32_t bits = 0;
             int y = 0, j = 0, x0 = 0;
+            uint32_t f[12];
             if (u < piece.z) {
                 y = u / cpr;
                 j = u - y * cpr;
                 x0 = j * kChunkPx;
                 if (x0 < w) {
-                    uint32_t f[12], l[12], h[12];
+                    uint32_t l[12], h[12];
                     load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                     load48(lo + (long long)y * fpitch + 3 * x0, once, l);
                     load48(hi + (long long)y * fpitch + 3 * x0, once, h);
@@ -248,14 +251,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
                     if (npx < kChunkPx) bits &= (1u << npx) - 1u;
                 }
             }
-            uint32_t todo = bits;
-            const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * x0;
-            while (__any_sync(kFull, todo != 0u)) {
-                if (todo) {
-                    const int k = __ffs(todo) - 1;
-                    const uint8_t *px = row + 3 * k;
-                    if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) bits &= ~(1u << k);
-                    todo &= todo - 1u;
+            if (__reduce_max_sync(kFull, (uint32_t)__popc(bits)) > 8u) {
+                // dense (the warp crosses the hand): all 16 pixels from registers
+                uint32_t sk = 0;
+#pragma unroll
+                for (int k = 0; k < kChunkPx; ++k)
+                    sk |= (uint32_t)skin_rgb(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2), D, g) << k;
+                bits &= sk;
+            } else {
+                // sparse (camera noise): one pixel per lane per round
+                uint32_t todo = bits;
+                const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * x0;
+                while (__any_sync(kFull, todo != 0u)) {
+                    if (todo) {
+                        const int k = __ffs(todo) - 1;
+                        const uint8_t *px = row + 3 * k;
+                        if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) bits &= ~(1u << k);
+                        todo &= todo - 1u;
+                    }
                 }
             }
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
@@ -334,7 +347,8 @@ constexpr int kStripWarps = 4;
 
 template <int HR>
 __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
-                                            uint32_t (*tr)[33], int lane)
+                                            uint32_t (*tr)[33], int lane, int sidx,
+                                            uint32_t *cc_count, uint2 *cc_list)
 {
     constexpr int R = kMorphRows + 2 * HR;
     const int w = D.w, h = D.h, nwords = D.nwords;
@@ -404,15 +418,20 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
         }
     }
     __syncwarp();
-    for (int j = 1; j <= kStripWords; ++j) {
-        const int bx = tx * kStripWords - 1 + j;
-        if (bx >= nwords) break;
-        const uint32_t m = tr[lane][j];
-        if (!__any_sync(kFull, m != 0u)) {
-            if (lane == 0) D.count[ty * nwords + bx] = 0u;
-            continue;
+    // list the non-empty 32x32 blocks of the strip for k_block_cc; empty ones get count 0
+    const int bx = tx * kStripWords - 1 + lane;
+    const bool own = lane >= 1 && lane <= kStripWords && bx < nwords;
+    uint32_t any = 0;
+#pragma unroll 8
+    for (int i = 0; i < kMorphRows; ++i) any |= tr[i][lane];
+    if (own) {
+        const uint32_t blk = (uint32_t)(ty * nwords + bx);
+        if (any == 0u) {
+            D.count[blk] = 0u;
+        } else {
+            const uint32_t slot = atomicAdd(cc_count, 1u);
+            cc_list[slot] = make_uint2((uint32_t)sidx, blk);
         }
-        emit_block_components(D, m, lane, ty * nwords + bx, bx * kWordPx, y0);
     }
 }
 
@@ -432,12 +451,30 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
     switch (2 * (D.open_iters + D.close_iters)) {
-    case 0: morph_strip<0>(D, io, ty, tx, tr[warp], lane); break;
-    case 2: morph_strip<2>(D, io, ty, tx, tr[warp], lane); break;
-    case 4: morph_strip<4>(D, io, ty, tx, tr[warp], lane); break;
-    case 6: morph_strip<6>(D, io, ty, tx, tr[warp], lane); break;
-    case 8: morph_strip<8>(D, io, ty, tx, tr[warp], lane); break;
+    case 0: morph_strip<0>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
+    case 2: morph_strip<2>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
+    case 4: morph_strip<4>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
+    case 6: morph_strip<6>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
+    case 8: morph_strip<8>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
     default: break;   // wider halos run k_morph_cc instead
+    }
+}
+
+// k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
+// batch): its 8-connected components and their statistics.
+constexpr int kBlockCcWarps = 8;
+
+__global__ void __launch_bounds__(kBlockCcWarps * 32) k_block_cc(BatchDev b)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = *(volatile uint32_t *)b.cc_count;
+    for (uint32_t it = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5); it < n;
+         it += gridDim.x * kBlockCcWarps) {
+        const uint2 e = b.cc_list[it];
+        const DevStream &D = b.ds[e.x];
+        const int by = (int)e.y / D.nwords, bx = (int)e.y - by * D.nwords;
+        const uint32_t m = D.bits[(long long)(by * kBlock + lane) * D.nwords + bx];
+        emit_block_components(D, m, lane, (int)e.y, bx * kWordPx, by * kBlock);
     }
 }
 
@@ -592,11 +629,16 @@ cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs)
     return cudaGetLastError();
 }
 
-cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs)
+cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     if (b.max_halo <= kStripMaxHalo) {
         const unsigned grid = (b.total_strips + kStripWarps - 1) / kStripWarps;
         k_morph_strip<<<grid, kStripWarps * 32, 0, cs>>>(b);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
+                                               (unsigned)num_sms * 8u);
+        k_block_cc<<<g2, kBlockCcWarps * 32, 0, cs>>>(b);
     } else {
         k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
     }

@@ -108,6 +108,8 @@ struct BatchDev {
     const int4 *pieces;                       // (stream, chunk begin, chunk end, 0)
     int npieces;                              // pieces of the per-pixel kernels
     uint32_t *err;                            // batch error word: OR of the streams' flags
+    uint32_t *cc_count;                       // non-empty blocks listed this tick
+    uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
 };
 
 // Threads per CTA of every kernel of a tick.
@@ -118,7 +120,7 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs);
-cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
                           cudaStream_t cs);
