@@ -112,7 +112,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.nwords = (w + 31) / 32;
     L.bh = (h + 31) / 32;
     L.tiles_x = (L.nwords + kMorphTW - 1) / kMorphTW;
-    L.strips_x = (L.nwords + 29) / 30;
+    L.strips_x = (L.nwords + 29) / 30;   // strips of 30 words x 16 rows
     L.fpitch = (int)align_up((size_t)w, 16) * 3;
     L.npx = (size_t)w * h;
     const size_t nblk = (size_t)L.bh * L.nwords;
@@ -307,7 +307,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
         const int chunks = L.h * 2 * L.nwords;
         cpre[i + 1] = cpre[i] + (unsigned long long)chunks;
         tpre[i + 1] = tpre[i] + (uint32_t)(L.bh * L.tiles_x);
-        spre[i + 1] = spre[i] + (uint32_t)(L.bh * L.strips_x);
+        spre[i + 1] = spre[i] + (uint32_t)(((L.h + 15) / 16) * L.strips_x);
         max_halo = std::max(max_halo, 2 * (s[i]->p.open_iters + s[i]->p.close_iters));
         bpre[i + 1] = bpre[i] + (uint32_t)(L.bh * L.nwords);
         for (int c = 0; c < chunks; c += kPieceChunks)
@@ -396,7 +396,7 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     if ((e = cudaMemcpyAsync(const_cast<TickIO *>(bd.io), b->h_io + (size_t)slot * b->n,
                              sizeof(TickIO) * b->n, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
         return e;
-    if ((e = launch_luma(bd, cs)) != cudaSuccess) return e;
+    if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
     if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
         return e;
     if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;

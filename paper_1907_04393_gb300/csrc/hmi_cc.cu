@@ -223,12 +223,16 @@ struct FinishSmem {
     bool overflow;
 };
 
-__device__ __forceinline__ uint32_t sm_find(const uint32_t *parent, uint32_t x)
+// Root of x with path halving (every visited node is re-pointed to its
+// grandparent, always an ancestor, so concurrent unions stay correct).
+__device__ __forceinline__ uint32_t sm_find(uint32_t *parent, uint32_t x)
 {
     for (int it = 0; it < kRecCap + 1; ++it) {
         const uint32_t p = parent[x];
         if (p == x) return x;
-        x = p;
+        const uint32_t gp = parent[p];
+        if (gp != p) parent[x] = gp;
+        x = gp;
     }
     return x;
 }
@@ -422,9 +426,11 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         }
     }
     __syncthreads();
+    for (uint32_t r = tid; r < nr; r += blockDim.x) S.parent[r] = sm_find(S.parent, r);
+    __syncthreads();
     // resolve: non-roots into roots; final roots back to the global parents
     for (uint32_t r = tid; r < nr; r += blockDim.x) {
-        const uint32_t root = sm_find(S.parent, r);
+        const uint32_t root = S.parent[r];
         int lo = 0, hi = (int)na - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;

@@ -71,14 +71,17 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
     __shared__ unsigned long long red[kThreads / 32];
     __shared__ bool is_last;
     const int tid = threadIdx.x;
-    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+    const uint64_t keep = policy_evict_last();
+    // a contiguous range of pieces per CTA: consecutive pieces mostly share a
+    // stream, so partial sums are flushed only when the stream changes
+    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
+    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
+    unsigned long long acc = 0;
+    for (int pc = p0; pc < p1; ++pc) {
         const int4 piece = b.pieces[pc];
-        const int s = piece.x;
-        const DevStream &D = b.ds[s];
-        const TickIO io = b.io[s];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
         const int w = D.w, cpr = 2 * D.nwords;
-        const uint64_t keep = policy_evict_last();
-        unsigned long long acc = 0;
         // two chunks per thread per round, both loads in flight before the sums
         for (int u = piece.y + tid; u < piece.z; u += 2 * blockDim.x) {
             uint32_t f[2][12];
@@ -106,17 +109,20 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
                 acc += sum;
             }
         }
-        // CTA reduction, one atomic per piece
+        const bool flush = (pc + 1 == p1) || (b.pieces[pc + 1].x != piece.x);
+        if (flush) {   // CTA-uniform
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if ((tid & 31) == 0) red[tid >> 5] = acc;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long t = 0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-            atomicAdd(&D.st->sy, t);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long t = 0;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+                atomicAdd(&D.st->sy, t);
+            }
+            __syncthreads();
+            acc = 0;
         }
-        __syncthreads();
     }
     // the last CTA to finish computes every stream's gain
     __threadfence();
@@ -334,7 +340,7 @@ __device__ __forceinline__ void emit_block_components(const DevStream &D, uint32
 }
 
 // ---------------------------------------------------------------------------
-// k_morph_strip: one warp per strip of 32 output rows x 30 words (960 px),
+// k_morph_strip: one warp per strip of 16 output rows x 30 words (960 px),
 // lane j = word column (lanes 0 and 31 are the left/right halo words), rows
 // (32 + 2*HR with HR = 2*(open+close) halo rows) held in registers.  Each
 // operator neutralises out-of-image pixels (1 for erosion, 0 for dilation),
@@ -344,18 +350,18 @@ __device__ __forceinline__ void emit_block_components(const DevStream &D, uint32
 // ---------------------------------------------------------------------------
 constexpr int kStripWords = 30;
 constexpr int kStripWarps = 4;
+constexpr int kStripRows = 16;
 
 template <int HR>
 __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
-                                            uint32_t (*tr)[33], int lane, int sidx,
-                                            uint32_t *cc_count, uint2 *cc_list)
+                                            int lane)
 {
-    constexpr int R = kMorphRows + 2 * HR;
+    constexpr int R = kStripRows + 2 * HR;
     const int w = D.w, h = D.h, nwords = D.nwords;
     const int kw = tx * kStripWords - 1 + lane;
     const bool col_ok = kw >= 0 && kw < nwords;
     const uint32_t wmask = !col_ok ? 0u : ((kw == nwords - 1 && (w & 31)) ? ((1u << (w & 31)) - 1u) : 0xffffffffu);
-    const int y0 = ty * kMorphRows;
+    const int y0 = ty * kStripRows;
     const int ybase = y0 - HR;
     const int rlo = max(0, -ybase), rhi = min(R, h - ybase);   // rows inside the image
     uint32_t v[R];
@@ -364,13 +370,17 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
         const int y = ybase + r;
         v[r] = (col_ok && r >= rlo && r < rhi) ? D.raw[(long long)y * nwords + kw] : 0u;
     }
+    // strips away from every image edge need no neutral out-of-image pixels
+    const bool edge = rlo > 0 || rhi < R || __any_sync(kFull, wmask != 0xffffffffu);
     const int nops = 2 * (D.open_iters + D.close_iters);   // == HR
     for (int op = 0; op < nops; ++op) {
         const bool ero = (op < 2 * D.open_iters) ? ((op & 1) == 0) : (((op - 2 * D.open_iters) & 1) == 1);
+        if (edge) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
-            v[r] = ero ? (v[r] | ~vm) : (v[r] & vm);
+            for (int r = 0; r < R; ++r) {
+                const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
+                v[r] = ero ? (v[r] | ~vm) : (v[r] & vm);
+            }
         }
         uint32_t prev = 0, cur = 0;
 #pragma unroll
@@ -392,52 +402,33 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
             cur = nxt;
         }
     }
-    // interior: global bit mask, mask bytes, transposed copy for components
+    // interior: global bit mask and mask bytes
     const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
+    if (!interior) return;
 #pragma unroll
-    for (int i = 0; i < kMorphRows; ++i) {
+    for (int i = 0; i < kStripRows; ++i) {
         const int r = HR + i, y = y0 + i;
         const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
-        tr[i][lane] = fin;
-        if (interior) {
-            D.bits[(long long)y * nwords + kw] = fin;
-            if (io.mask != nullptr && y < h) {
-                uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
-                const int npx = min(kWordPx, w - kw * kWordPx);
-                if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-                    uint32_t q[8];
+        D.bits[(long long)y * nwords + kw] = fin;
+        if (io.mask != nullptr && y < h) {
+            uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
+            const int npx = min(kWordPx, w - kw * kWordPx);
+            if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+                uint32_t q[8];
 #pragma unroll
-                    for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
-                    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-                    __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
-                    __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
-                } else {
-                    for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
-                }
+                for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
+                __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
+            } else {
+                for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
             }
-        }
-    }
-    __syncwarp();
-    // list the non-empty 32x32 blocks of the strip for k_block_cc; empty ones get count 0
-    const int bx = tx * kStripWords - 1 + lane;
-    const bool own = lane >= 1 && lane <= kStripWords && bx < nwords;
-    uint32_t any = 0;
-#pragma unroll 8
-    for (int i = 0; i < kMorphRows; ++i) any |= tr[i][lane];
-    if (own) {
-        const uint32_t blk = (uint32_t)(ty * nwords + bx);
-        if (any == 0u) {
-            D.count[blk] = 0u;
-        } else {
-            const uint32_t slot = atomicAdd(cc_count, 1u);
-            cc_list[slot] = make_uint2((uint32_t)sidx, blk);
         }
     }
 }
 
 __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
 {
-    __shared__ uint32_t tr[kStripWarps][kMorphRows][33];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t strip = blockIdx.x * kStripWarps + warp;
     if (strip >= b.total_strips) return;   // warp-uniform
@@ -451,31 +442,38 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
     switch (2 * (D.open_iters + D.close_iters)) {
-    case 0: morph_strip<0>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
-    case 2: morph_strip<2>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
-    case 4: morph_strip<4>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
-    case 6: morph_strip<6>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
-    case 8: morph_strip<8>(D, io, ty, tx, tr[warp], lane, lo, b.cc_count, b.cc_list); break;
+    case 0: morph_strip<0>(D, io, ty, tx, lane); break;
+    case 2: morph_strip<2>(D, io, ty, tx, lane); break;
+    case 4: morph_strip<4>(D, io, ty, tx, lane); break;
+    case 6: morph_strip<6>(D, io, ty, tx, lane); break;
+    case 8: morph_strip<8>(D, io, ty, tx, lane); break;
     default: break;   // wider halos run k_morph_cc instead
     }
 }
 
-// k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
-// batch): its 8-connected components and their statistics.
+// k_block_cc: one warp per 32x32 block of every stream: empty blocks get a
+// zero count; the others their 8-connected components and statistics.
 constexpr int kBlockCcWarps = 8;
 
 __global__ void __launch_bounds__(kBlockCcWarps * 32) k_block_cc(BatchDev b)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t n = *(volatile uint32_t *)b.cc_count;
-    for (uint32_t it = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5); it < n;
-         it += gridDim.x * kBlockCcWarps) {
-        const uint2 e = b.cc_list[it];
-        const DevStream &D = b.ds[e.x];
-        const int by = (int)e.y / D.nwords, bx = (int)e.y - by * D.nwords;
-        const uint32_t m = D.bits[(long long)(by * kBlock + lane) * D.nwords + bx];
-        emit_block_components(D, m, lane, (int)e.y, bx * kWordPx, by * kBlock);
+    const uint32_t g = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5);
+    if (g >= b.total_blocks) return;        // warp-uniform
+    int lo = 0, hi = b.n;                   // largest s with block_prefix[s] <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (b.block_prefix[mid] <= g) lo = mid; else hi = mid;
     }
+    const DevStream &D = b.ds[lo];
+    const int blk = (int)(g - b.block_prefix[lo]);
+    const int by = blk / D.nwords, bx = blk - by * D.nwords;
+    const uint32_t m = __ldcg(D.bits + (long long)(by * kBlock + lane) * D.nwords + bx);
+    if (!__any_sync(kFull, m != 0u)) {
+        if (lane == 0) D.count[blk] = 0u;
+        return;
+    }
+    emit_block_components(D, m, lane, blk, bx * kWordPx, by * kBlock);
 }
 
 // ---------------------------------------------------------------------------
@@ -617,9 +615,10 @@ static int grid_for_pieces(int npieces)
     return npieces > 0 ? npieces : 1;
 }
 
-cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs)
+cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    k_luma<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    const int grid = std::max(1, std::min(b.npieces, num_sms * 8));
+    k_luma<<<grid, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
@@ -636,9 +635,8 @@ cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
         k_morph_strip<<<grid, kStripWarps * 32, 0, cs>>>(b);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
-                                               (unsigned)num_sms * 8u);
-        k_block_cc<<<g2, kBlockCcWarps * 32, 0, cs>>>(b);
+        (void)num_sms;
+        k_block_cc<<<(b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps, kBlockCcWarps * 32, 0, cs>>>(b);
     } else {
         k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
     }

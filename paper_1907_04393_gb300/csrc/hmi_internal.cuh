@@ -118,7 +118,7 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
-cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
