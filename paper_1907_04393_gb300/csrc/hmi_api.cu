@@ -100,7 +100,7 @@ struct Arena {
 
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
-    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, bits, comp, parent, count, mask, st,
+    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, bits, comp, parent, count, flag, mask, st,
         hist, ds, ptr, total;
 };
 
@@ -130,6 +130,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.comp = a.take(nblk * kSlots * sizeof(Comp));
     L.parent = a.take(nblk * kSlots * 4);
     L.count = a.take(nblk * 4);
+    L.flag = a.take(nblk * 4);
     L.mask = a.take(L.npx);
     L.st = a.take(sizeof(StreamState));
     L.hist = a.take((size_t)std::max<int>(p.click_window, 1) * 4);
@@ -241,6 +242,7 @@ void fill_devstream(hmi_stream *s)
     D.comp = reinterpret_cast<Comp *>(a + L.comp);
     D.parent = reinterpret_cast<uint32_t *>(a + L.parent);
     D.count = reinterpret_cast<uint32_t *>(a + L.count);
+    D.flag = reinterpret_cast<uint32_t *>(a + L.flag);
     D.st = reinterpret_cast<StreamState *>(a + L.st);
     D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
 }
@@ -301,14 +303,16 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     std::vector<unsigned long long> cpre(n + 1, 0);
     std::vector<uint32_t> tpre(n + 1, 0), bpre(n + 1, 0), spre(n + 1, 0);
     std::vector<int4> pieces;
-    int max_halo = 0;
+    int max_halo = 0, uniform_halo = 2 * (s[0]->p.open_iters + s[0]->p.close_iters);
     for (int i = 0; i < n; ++i) {
         const Layout &L = s[i]->L;
         const int chunks = L.h * 2 * L.nwords;
         cpre[i + 1] = cpre[i] + (unsigned long long)chunks;
         tpre[i + 1] = tpre[i] + (uint32_t)(L.bh * L.tiles_x);
         spre[i + 1] = spre[i] + (uint32_t)(((L.h + 15) / 16) * L.strips_x);
-        max_halo = std::max(max_halo, 2 * (s[i]->p.open_iters + s[i]->p.close_iters));
+        const int halo = 2 * (s[i]->p.open_iters + s[i]->p.close_iters);
+        max_halo = std::max(max_halo, halo);
+        if (halo != uniform_halo) uniform_halo = -1;
         bpre[i + 1] = bpre[i] + (uint32_t)(L.bh * L.nwords);
         for (int c = 0; c < chunks; c += kPieceChunks)
             pieces.push_back(make_int4(i, c, std::min(chunks, c + kPieceChunks), 0));
@@ -373,6 +377,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
     bd.strip_prefix = reinterpret_cast<const uint32_t *>(A + o_s);
     bd.total_strips = spre[n];
     bd.max_halo = max_halo;
+    bd.uniform_halo = uniform_halo;
     bd.done = reinterpret_cast<uint32_t *>(A + o_done);
     bd.pieces = reinterpret_cast<const int4 *>(A + o_p);
     bd.npieces = (int)pieces.size();

@@ -428,30 +428,49 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
     __syncthreads();
     for (uint32_t r = tid; r < nr; r += blockDim.x) S.parent[r] = sm_find(S.parent, r);
     __syncthreads();
-    // resolve: non-roots into roots; final roots back to the global parents
-    for (uint32_t r = tid; r < nr; r += blockDim.x) {
-        const uint32_t root = S.parent[r];
-        int lo = 0, hi = (int)na - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (S.rbase[mid] <= r) lo = mid; else hi = mid - 1;
+    // resolve: non-roots into roots, aggregated per warp and root (a block
+    // record's sums are below 2^23 and at most 32 are combined, so the
+    // per-warp sums fit in 32 bits); final roots back to the global parents
+    for (uint32_t base = 0; base < nr; base += blockDim.x) {
+        const uint32_t r = base + tid;
+        const bool valid = r < nr;
+        const uint32_t root = valid ? S.parent[r] : 0xffffffffu;
+        const bool contrib = valid && root != r;
+        if (valid) {
+            int lo = 0, hi = (int)na - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.rbase[mid] <= r) lo = mid; else hi = mid - 1;
+            }
+            int lo2 = 0, hi2 = (int)na - 1;
+            while (lo2 < hi2) {
+                const int mid = (lo2 + hi2 + 1) >> 1;
+                if (S.rbase[mid] <= root) lo2 = mid; else hi2 = mid - 1;
+            }
+            D.parent[S.act[lo] * kSlots + (r - S.rbase[lo])] = S.act[lo2] * kSlots + (root - S.rbase[lo2]);
         }
-        int lo2 = 0, hi2 = (int)na - 1;
-        while (lo2 < hi2) {
-            const int mid = (lo2 + hi2 + 1) >> 1;
-            if (S.rbase[mid] <= root) lo2 = mid; else hi2 = mid - 1;
+        const uint32_t key = contrib ? root : 0xfffffffeu;
+        const unsigned grp = __match_any_sync(kFull, key);
+        if (contrib) {
+            const Comp &A = S.rec[r];
+            const uint32_t area = __reduce_add_sync(grp, A.area);
+            const uint32_t sx = __reduce_add_sync(grp, (uint32_t)A.sx);
+            const uint32_t sy = __reduce_add_sync(grp, (uint32_t)A.sy);
+            const uint32_t x0 = __reduce_min_sync(grp, (uint32_t)A.x0);
+            const uint32_t y0 = __reduce_min_sync(grp, (uint32_t)A.y0);
+            const uint32_t x1 = __reduce_max_sync(grp, (uint32_t)A.x1);
+            const uint32_t y1 = __reduce_max_sync(grp, (uint32_t)A.y1);
+            if (lane == __ffs(grp) - 1) {
+                Comp &R = S.rec[root];
+                atomicAdd(&R.area, area);
+                atomicAdd(&R.sx, (unsigned long long)sx);
+                atomicAdd(&R.sy, (unsigned long long)sy);
+                atomicMin(&R.x0, (int)x0);
+                atomicMin(&R.y0, (int)y0);
+                atomicMax(&R.x1, (int)x1);
+                atomicMax(&R.y1, (int)y1);
+            }
         }
-        D.parent[S.act[lo] * kSlots + (r - S.rbase[lo])] = S.act[lo2] * kSlots + (root - S.rbase[lo2]);
-        if (root == r) continue;
-        const Comp &A = S.rec[r];
-        Comp &R = S.rec[root];
-        atomicAdd(&R.area, A.area);
-        atomicAdd(&R.sx, A.sx);
-        atomicAdd(&R.sy, A.sy);
-        atomicMin(&R.x0, A.x0);
-        atomicMin(&R.y0, A.y0);
-        atomicMax(&R.x1, A.x1);
-        atomicMax(&R.y1, A.y1);
     }
     __syncthreads();
     for (uint32_t r = tid; r < nr; r += blockDim.x) {

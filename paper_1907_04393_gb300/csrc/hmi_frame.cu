@@ -63,6 +63,35 @@ __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b)
     return (77u * r + 150u * g + 29u * b + 128u) >> 8;
 }
 
+// Sum of luma8 over 16 pixels (48 bytes): each pixel's 3 bytes are gathered
+// into one word with a byte permute, then one 4-way byte dot product with
+// (77, 150, 29, 0) plus 128, shifted per pixel.
+__device__ __forceinline__ uint32_t luma_sum16(const uint32_t (&f)[12])
+{
+    constexpr uint32_t kW = 77u | (150u << 8) | (29u << 16);
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kChunkPx; ++k) {
+        const int b = 3 * k, wi = b >> 2, o = b & 3;
+        // bytes b, b+1, b+2 of the 48 (they span at most two words)
+        const uint32_t lo = f[wi], hi = (wi + 1 < 12) ? f[wi + 1] : 0u;
+        const uint32_t px = __byte_perm(lo, hi, (uint32_t)(o | ((o + 1) << 4) | ((o + 2) << 8) | (0x7 << 12)) & 0x7777u);
+        sum += __dp4a(px & 0x00ffffffu, kW, 128u) >> 8;
+    }
+    return sum;
+}
+
+__device__ __forceinline__ uint32_t luma_sum_n(const uint32_t (&f)[12], int npx)
+{
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kChunkPx; ++k) {
+        const uint32_t v = luma8(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2));
+        sum += (k < npx) ? v : 0u;
+    }
+    return sum;
+}
+
 // ---------------------------------------------------------------------------
 // k_luma: one CTA per piece (a contiguous chunk range of one stream).
 // ---------------------------------------------------------------------------
@@ -99,15 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                uint32_t sum = 0;
-#pragma unroll
-                for (int k = 0; k < kChunkPx; ++k) {
-                    const uint32_t v = luma8(byte_of(f[q], 3 * k), byte_of(f[q], 3 * k + 1), byte_of(f[q], 3 * k + 2));
-                    sum += (k < npx[q]) ? v : 0u;
-                }
-                acc += sum;
-            }
+            for (int q = 0; q < 2; ++q) acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
         }
         const bool flush = (pc + 1 == p1) || (b.pieces[pc + 1].x != piece.x);
         if (flush) {   // CTA-uniform
@@ -354,7 +375,7 @@ constexpr int kStripRows = 16;
 
 template <int HR>
 __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
-                                            int lane)
+                                            int lane, int sidx, uint32_t *cc_count, uint2 *cc_list)
 {
     constexpr int R = kStripRows + 2 * HR;
     const int w = D.w, h = D.h, nwords = D.nwords;
@@ -405,10 +426,12 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
     // interior: global bit mask and mask bytes
     const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
     if (!interior) return;
+    uint32_t any = 0;
 #pragma unroll
     for (int i = 0; i < kStripRows; ++i) {
         const int r = HR + i, y = y0 + i;
         const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
+        any |= fin;
         D.bits[(long long)y * nwords + kw] = fin;
         if (io.mask != nullptr && y < h) {
             uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
@@ -425,8 +448,17 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
             }
         }
     }
+    // the 32x32 block of this word: the upper strip of a block clears its
+    // count; the first strip to find pixels in it lists it for k_block_cc
+    const uint32_t blk = (uint32_t)((y0 / kBlock) * nwords + kw);
+    if ((ty & 1) == 0) D.count[blk] = 0u;
+    if (any != 0u && atomicOr(D.flag + blk, 1u) == 0u) {
+        const uint32_t slot = atomicAdd(cc_count, 1u);
+        cc_list[slot] = make_uint2((uint32_t)sidx, blk);
+    }
 }
 
+template <int HR>
 __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -441,39 +473,27 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     const TickIO io = b.io[lo];
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
-    switch (2 * (D.open_iters + D.close_iters)) {
-    case 0: morph_strip<0>(D, io, ty, tx, lane); break;
-    case 2: morph_strip<2>(D, io, ty, tx, lane); break;
-    case 4: morph_strip<4>(D, io, ty, tx, lane); break;
-    case 6: morph_strip<6>(D, io, ty, tx, lane); break;
-    case 8: morph_strip<8>(D, io, ty, tx, lane); break;
-    default: break;   // wider halos run k_morph_cc instead
-    }
+    morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list);
 }
 
-// k_block_cc: one warp per 32x32 block of every stream: empty blocks get a
-// zero count; the others their 8-connected components and statistics.
+// k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
+// batch): its 8-connected components and their statistics; its flag is
+// cleared for the next tick.
 constexpr int kBlockCcWarps = 8;
 
 __global__ void __launch_bounds__(kBlockCcWarps * 32) k_block_cc(BatchDev b)
 {
     const int lane = threadIdx.x & 31;
-    const uint32_t g = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5);
-    if (g >= b.total_blocks) return;        // warp-uniform
-    int lo = 0, hi = b.n;                   // largest s with block_prefix[s] <= g
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (b.block_prefix[mid] <= g) lo = mid; else hi = mid;
+    const uint32_t n = *(volatile uint32_t *)b.cc_count;
+    for (uint32_t it = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5); it < n;
+         it += gridDim.x * kBlockCcWarps) {
+        const uint2 e = b.cc_list[it];
+        const DevStream &D = b.ds[e.x];
+        const int by = (int)e.y / D.nwords, bx = (int)e.y - by * D.nwords;
+        const uint32_t m = __ldcg(D.bits + (long long)(by * kBlock + lane) * D.nwords + bx);
+        if (lane == 0) D.flag[e.y] = 0u;
+        emit_block_components(D, m, lane, (int)e.y, bx * kWordPx, by * kBlock);
     }
-    const DevStream &D = b.ds[lo];
-    const int blk = (int)(g - b.block_prefix[lo]);
-    const int by = blk / D.nwords, bx = blk - by * D.nwords;
-    const uint32_t m = __ldcg(D.bits + (long long)(by * kBlock + lane) * D.nwords + bx);
-    if (!__any_sync(kFull, m != 0u)) {
-        if (lane == 0) D.count[blk] = 0u;
-        return;
-    }
-    emit_block_components(D, m, lane, blk, bx * kWordPx, by * kBlock);
 }
 
 // ---------------------------------------------------------------------------
@@ -630,13 +650,20 @@ cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs)
 
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    if (b.max_halo <= kStripMaxHalo) {
+    if (b.uniform_halo >= 0 && b.uniform_halo <= kStripMaxHalo) {
         const unsigned grid = (b.total_strips + kStripWarps - 1) / kStripWarps;
-        k_morph_strip<<<grid, kStripWarps * 32, 0, cs>>>(b);
+        switch (b.uniform_halo) {
+        case 0: k_morph_strip<0><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
+        case 2: k_morph_strip<2><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
+        case 4: k_morph_strip<4><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
+        case 6: k_morph_strip<6><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
+        default: k_morph_strip<8><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
+        }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        (void)num_sms;
-        k_block_cc<<<(b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps, kBlockCcWarps * 32, 0, cs>>>(b);
+        const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
+                                               (unsigned)num_sms * 8u);
+        k_block_cc<<<std::max(g2, 1u), kBlockCcWarps * 32, 0, cs>>>(b);
     } else {
         k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
     }

@@ -78,6 +78,7 @@ struct DevStream {
     Comp *comp;                   // bh*nwords*kSlots records
     uint32_t *parent;             // union-find parent per record
     uint32_t *count;              // components per CC block
+    uint32_t *flag;               // per CC block: listed for components this tick
     StreamState *st;
     uint32_t *hist;               // click_window areas (ring)
 };
@@ -103,6 +104,7 @@ struct BatchDev {
     const uint32_t *strip_prefix;             // n + 1
     uint32_t total_strips;                    // sum bh * strips_x
     int max_halo;                             // largest 2 * (open + close) of the batch
+    int uniform_halo;                         // the common 2 * (open + close), or -1
     const uint32_t *block_prefix;             // n + 1
     uint32_t *done;                           // last-block counters [4]
     const int4 *pieces;                       // (stream, chunk begin, chunk end, 0)
