@@ -141,6 +141,15 @@ typedef struct hmi_batch hmi_batch;
 HMI_API hmi_batch *hmi_batch_create(hmi_stream *const *s, int n);
 HMI_API void hmi_batch_destroy(hmi_batch *b);
 
+/* Concurrency of a launch plan.  The streams of a batch are dealt into
+ * `groups` groups of about equal pixel count; each group's kernels form their
+ * own chain, and the chains of a tick overlap (each group's luma pass starts
+ * after the previous group's), so the bandwidth-bound passes of one group run
+ * beside the latency-bound tail of another.  Default: min(4, n).  Changing it
+ * rebuilds the plan (waits for the device).  Results do not depend on it. */
+HMI_API int hmi_batch_set_groups(hmi_batch *b, int groups);
+HMI_API int hmi_batch_get_groups(const hmi_batch *b);
+
 /* Process one frame per stream of the batch.  Synchronous form: buffers may be
  * host or device; frames[i] is the frame of the i-th stream given at creation.
  * masks / ptrs as in hmi_process_batch. */
@@ -155,7 +164,8 @@ HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, 
 
 /* Kernel timing of the batch's classification kernel (the per-pixel HBM pass).
  * hmi_batch_profile(b, max_ticks) starts recording one CUDA-event pair around
- * that kernel for each of the next max_ticks ticks (0 stops).
+ * that kernel for each of the next max_ticks ticks (0 stops); the plan must
+ * have one group (HMI_ERR_INVALID_ARG otherwise), so the launch is timed alone.
  * hmi_batch_profile_read waits for them and returns the number of ticks timed
  * and the sum of their durations in milliseconds. */
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);

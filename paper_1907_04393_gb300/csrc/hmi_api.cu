@@ -174,27 +174,38 @@ struct hmi_stream {
     hmi_batch *self = nullptr;   // one-stream plan used by hmi_process_frame
 };
 
+// One chain of tick kernels over a subset of the batch's streams.
+struct Group {
+    int off = 0, cnt = 0;         // range in the permuted stream order
+    BatchDev bd{};                // io is set per tick slot
+    cudaStream_t cs = nullptr;    // branch stream (also joins graph capture)
+    cudaEvent_t ev_luma = nullptr, ev_done = nullptr;
+};
+
 struct hmi_batch {
     int dev = 0;
     int n = 0;
-    std::vector<hmi_stream *> s;
-    uint8_t *arena = nullptr;     // device tables
-    TickIO *h_io = nullptr;       // pinned mirrors, kRing x n
+    std::vector<hmi_stream *> s;  // user order
+    std::vector<int> pos;         // user index -> permuted position
+    std::vector<Group> groups;
+    uint8_t *arena = nullptr;     // per-batch device buffers
+    uint8_t *plan = nullptr;      // per-plan device tables
+    TickIO *h_io = nullptr;       // pinned mirrors, kRing x n, permuted order
     TickIO *d_io = nullptr;       // device copies, kRing x n
-    hmi_pointer *d_ptrs = nullptr;  // n pointers for the synchronous form
+    hmi_pointer *d_ptrs = nullptr;  // n pointers for the synchronous form, user order
     uint32_t *d_err = nullptr;    // batch error word (device)
     uint32_t *h_err = nullptr;    // pinned
     cudaEvent_t slot_ev[kRing] = {};
     bool slot_used[kRing] = {};
     int next = 0;
-    BatchDev bd{};
-    cudaStream_t cs = nullptr;    // stream of the synchronous form and of graph capture
+    cudaStream_t cs = nullptr;    // origin stream of the synchronous form and of graph capture
+    cudaEvent_t ev_fork = nullptr;
     int num_sms = 1;
     cudaGraph_t graph_src[kRing] = {};   // kept alive: its event-node handles retarget events
     cudaGraphExec_t graph[kRing] = {};
     cudaGraphNode_t ev_node[kRing][2] = {};
     cudaEvent_t dummy_ev[2] = {};
-    // profiling of the classification kernel
+    // profiling of the classification kernel (single-group plans)
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
     // device buffers already validated (skips a pointer-attribute query per
@@ -247,20 +258,40 @@ void fill_devstream(hmi_stream *s)
     D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
 }
 
+void plan_free(hmi_batch *b)
+{
+    for (int i = 0; i < kRing; ++i) {
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+        if (b->graph_src[i]) cudaGraphDestroy(b->graph_src[i]);
+        b->graph[i] = nullptr;
+        b->graph_src[i] = nullptr;
+        b->ev_node[i][0] = b->ev_node[i][1] = nullptr;
+    }
+    for (auto &g : b->groups) {
+        if (g.cs) cudaStreamDestroy(g.cs);
+        if (g.ev_luma) cudaEventDestroy(g.ev_luma);
+        if (g.ev_done) cudaEventDestroy(g.ev_done);
+    }
+    b->groups.clear();
+    if (b->plan) cudaFree(b->plan);
+    b->plan = nullptr;
+}
+
 int batch_free(hmi_batch *b)
 {
     if (!b) return HMI_OK;
     cudaSetDevice(b->dev);
     if (b->cs) cudaStreamSynchronize(b->cs);
-    for (int i = 0; i < kRing; ++i) {
+    for (int i = 0; i < kRing; ++i)
         if (b->slot_ev[i]) cudaEventSynchronize(b->slot_ev[i]);
-        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
-        if (b->graph_src[i]) cudaGraphDestroy(b->graph_src[i]);
+    cudaDeviceSynchronize();
+    plan_free(b);
+    for (int i = 0; i < kRing; ++i)
         if (b->slot_ev[i]) cudaEventDestroy(b->slot_ev[i]);
-    }
     for (auto &e : b->dummy_ev)
         if (e) cudaEventDestroy(e);
     for (auto e : b->prof_ev) cudaEventDestroy(e);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->cs) cudaStreamDestroy(b->cs);
     if (b->arena) cudaFree(b->arena);
     if (b->h_io) cudaFreeHost(b->h_io);
@@ -269,7 +300,130 @@ int batch_free(hmi_batch *b)
     return HMI_OK;
 }
 
-hmi_batch *batch_new(hmi_stream *const *s, int n)
+// Build the launch plan with `ng` stream groups: streams are dealt to groups
+// by pixel count (largest first, to the least-loaded group); each group gets
+// its own descriptor array, prefix tables, work pieces, counters and
+// component list, and its own branch stream.
+int plan_build(hmi_batch *b, int ng)
+{
+    const int n = b->n;
+    ng = std::max(1, std::min(ng, n));
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)b->s[x]->w * b->s[x]->h > (long long)b->s[y]->w * b->s[y]->h;
+    });
+    std::vector<std::vector<int>> members(ng);
+    std::vector<long long> load(ng, 0);
+    for (int i : order) {
+        const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        members[g].push_back(i);
+        load[g] += (long long)b->s[i]->w * b->s[i]->h;
+    }
+    std::vector<int> perm;
+    b->groups.assign(ng, Group());
+    for (int g = 0; g < ng; ++g) {
+        std::sort(members[g].begin(), members[g].end());
+        b->groups[g].off = (int)perm.size();
+        b->groups[g].cnt = (int)members[g].size();
+        for (int i : members[g]) perm.push_back(i);
+    }
+    b->pos.assign(n, 0);
+    for (int p = 0; p < n; ++p) b->pos[perm[p]] = p;
+
+    struct Tables {
+        std::vector<unsigned long long> cpre;
+        std::vector<uint32_t> tpre, bpre, spre;
+        std::vector<int4> pieces;
+        int max_halo = 0, uniform_halo = 0;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl;
+    };
+    std::vector<Tables> T(ng);
+    Arena a;
+    const size_t o_ds = a.take(sizeof(DevStream) * n);
+    for (int g = 0; g < ng; ++g) {
+        Tables &t = T[g];
+        const int m = b->groups[g].cnt;
+        t.cpre.assign(m + 1, 0);
+        t.tpre.assign(m + 1, 0);
+        t.bpre.assign(m + 1, 0);
+        t.spre.assign(m + 1, 0);
+        t.uniform_halo = -2;
+        for (int k = 0; k < m; ++k) {
+            const hmi_stream *st = b->s[perm[b->groups[g].off + k]];
+            const Layout &L = st->L;
+            const int chunks = L.h * 2 * L.nwords;
+            t.cpre[k + 1] = t.cpre[k] + (unsigned long long)chunks;
+            t.tpre[k + 1] = t.tpre[k] + (uint32_t)(L.bh * L.tiles_x);
+            t.spre[k + 1] = t.spre[k] + (uint32_t)(((L.h + 15) / 16) * L.strips_x);
+            t.bpre[k + 1] = t.bpre[k] + (uint32_t)(L.bh * L.nwords);
+            const int halo = 2 * (st->p.open_iters + st->p.close_iters);
+            t.max_halo = std::max(t.max_halo, halo);
+            t.uniform_halo = (t.uniform_halo == -2 || t.uniform_halo == halo) ? halo : -1;
+            for (int c = 0; c < chunks; c += kPieceChunks)
+                t.pieces.push_back(make_int4(k, c, std::min(chunks, c + kPieceChunks), 0));
+        }
+        t.o_c = a.take(sizeof(unsigned long long) * (m + 1));
+        t.o_t = a.take(sizeof(uint32_t) * (m + 1));
+        t.o_b = a.take(sizeof(uint32_t) * (m + 1));
+        t.o_s = a.take(sizeof(uint32_t) * (m + 1));
+        t.o_done = a.take(sizeof(uint32_t) * 4);
+        t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
+        t.o_ccn = a.take(sizeof(uint32_t));
+        t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
+    }
+    if (cudaMalloc(&b->plan, a.off) != cudaSuccess) {
+        (void)cudaGetLastError();
+        b->groups.clear();
+        return fail(HMI_ERR_NO_MEMORY);
+    }
+    uint8_t *A = b->plan;
+    std::vector<DevStream> ds(n);
+    for (int p = 0; p < n; ++p) ds[p] = b->s[perm[p]]->ds;
+    bool ok = cudaMemset(A, 0, a.off) == cudaSuccess &&
+              cudaMemcpy(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    for (int g = 0; ok && g < ng; ++g) {
+        Tables &t = T[g];
+        Group &G = b->groups[g];
+        const int m = G.cnt;
+        ok = cudaMemcpy(A + t.o_c, t.cpre.data(), sizeof(unsigned long long) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(A + t.o_t, t.tpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(A + t.o_b, t.bpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(A + t.o_s, t.spre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(A + t.o_p, t.pieces.data(), sizeof(int4) * t.pieces.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&G.ev_luma, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&G.ev_done, cudaEventDisableTiming) == cudaSuccess;
+        BatchDev &bd = G.bd;
+        bd.ds = reinterpret_cast<const DevStream *>(A + o_ds) + G.off;
+        bd.io = nullptr;
+        bd.n = m;
+        bd.total_chunks = t.cpre[m];
+        bd.total_tiles = t.tpre[m];
+        bd.total_blocks = t.bpre[m];
+        bd.chunk_prefix = reinterpret_cast<const unsigned long long *>(A + t.o_c);
+        bd.tile_prefix = reinterpret_cast<const uint32_t *>(A + t.o_t);
+        bd.block_prefix = reinterpret_cast<const uint32_t *>(A + t.o_b);
+        bd.strip_prefix = reinterpret_cast<const uint32_t *>(A + t.o_s);
+        bd.total_strips = t.spre[m];
+        bd.max_halo = t.max_halo;
+        bd.uniform_halo = t.uniform_halo;
+        bd.done = reinterpret_cast<uint32_t *>(A + t.o_done);
+        bd.pieces = reinterpret_cast<const int4 *>(A + t.o_p);
+        bd.npieces = (int)t.pieces.size();
+        bd.err = b->d_err;
+        bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
+        bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
+    }
+    if (!ok) {
+        (void)cudaGetLastError();
+        plan_free(b);
+        return fail(HMI_ERR_DEVICE);
+    }
+    return HMI_OK;
+}
+
+hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
 {
     if (!s || n < 1 || n > kMaxBatch) {
         fail(HMI_ERR_INVALID_ARG);
@@ -299,41 +453,16 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
         cuda_fail(cudaErrorInvalidDevice);
         return nullptr;
     }
-    // work tables
-    std::vector<unsigned long long> cpre(n + 1, 0);
-    std::vector<uint32_t> tpre(n + 1, 0), bpre(n + 1, 0), spre(n + 1, 0);
-    std::vector<int4> pieces;
-    int max_halo = 0, uniform_halo = 2 * (s[0]->p.open_iters + s[0]->p.close_iters);
-    for (int i = 0; i < n; ++i) {
-        const Layout &L = s[i]->L;
-        const int chunks = L.h * 2 * L.nwords;
-        cpre[i + 1] = cpre[i] + (unsigned long long)chunks;
-        tpre[i + 1] = tpre[i] + (uint32_t)(L.bh * L.tiles_x);
-        spre[i + 1] = spre[i] + (uint32_t)(((L.h + 15) / 16) * L.strips_x);
-        const int halo = 2 * (s[i]->p.open_iters + s[i]->p.close_iters);
-        max_halo = std::max(max_halo, halo);
-        if (halo != uniform_halo) uniform_halo = -1;
-        bpre[i + 1] = bpre[i] + (uint32_t)(L.bh * L.nwords);
-        for (int c = 0; c < chunks; c += kPieceChunks)
-            pieces.push_back(make_int4(i, c, std::min(chunks, c + kPieceChunks), 0));
-    }
     Arena a;
-    const size_t o_ds = a.take(sizeof(DevStream) * n);
-    const size_t o_c = a.take(sizeof(unsigned long long) * (n + 1));
-    const size_t o_t = a.take(sizeof(uint32_t) * (n + 1));
-    const size_t o_b = a.take(sizeof(uint32_t) * (n + 1));
-    const size_t o_s = a.take(sizeof(uint32_t) * (n + 1));
-    const size_t o_done = a.take(sizeof(uint32_t) * 4);
-    const size_t o_p = a.take(sizeof(int4) * pieces.size());
     const size_t o_io = a.take(sizeof(TickIO) * n * kRing);
     const size_t o_ptr = a.take(sizeof(hmi_pointer) * n);
     const size_t o_err = a.take(sizeof(uint32_t));
-    const size_t o_ccn = a.take(sizeof(uint32_t));
-    const size_t o_ccl = a.take(sizeof(uint2) * std::max<size_t>(bpre[n], 1));
     bool ok = cudaMalloc(&b->arena, a.off) == cudaSuccess &&
+              cudaMemset(b->arena, 0, a.off) == cudaSuccess &&
               cudaMallocHost(&b->h_io, sizeof(TickIO) * n * kRing) == cudaSuccess &&
               cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
+              cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kRing; ++i)
         ok = cudaEventCreateWithFlags(&b->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < 2; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
@@ -343,103 +472,98 @@ hmi_batch *batch_new(hmi_stream *const *s, int n)
         fail(HMI_ERR_NO_MEMORY);
         return nullptr;
     }
-    std::vector<DevStream> ds(n);
-    for (int i = 0; i < n; ++i) ds[i] = s[i]->ds;
-    uint8_t *A = b->arena;
-    ok = cudaMemset(A, 0, a.off) == cudaSuccess &&
-         cudaMemcpy(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(A + o_c, cpre.data(), sizeof(unsigned long long) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(A + o_t, tpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(A + o_b, bpre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(A + o_s, spre.data(), sizeof(uint32_t) * (n + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(A + o_p, pieces.data(), sizeof(int4) * pieces.size(), cudaMemcpyHostToDevice) == cudaSuccess;
-    if (!ok) {
-        (void)cudaGetLastError();
-        batch_free(b);
-        fail(HMI_ERR_DEVICE);
-        return nullptr;
-    }
     memset(b->h_io, 0, sizeof(TickIO) * n * kRing);
     *b->h_err = 0;
-    b->d_io = reinterpret_cast<TickIO *>(A + o_io);
-    b->d_ptrs = reinterpret_cast<hmi_pointer *>(A + o_ptr);
-    b->d_err = reinterpret_cast<uint32_t *>(A + o_err);
-    BatchDev &bd = b->bd;
-    bd.ds = reinterpret_cast<const DevStream *>(A + o_ds);
-    bd.io = b->d_io;
-    bd.n = n;
-    bd.total_chunks = cpre[n];
-    bd.total_tiles = tpre[n];
-    bd.total_blocks = bpre[n];
-    bd.chunk_prefix = reinterpret_cast<const unsigned long long *>(A + o_c);
-    bd.tile_prefix = reinterpret_cast<const uint32_t *>(A + o_t);
-    bd.block_prefix = reinterpret_cast<const uint32_t *>(A + o_b);
-    bd.strip_prefix = reinterpret_cast<const uint32_t *>(A + o_s);
-    bd.total_strips = spre[n];
-    bd.max_halo = max_halo;
-    bd.uniform_halo = uniform_halo;
-    bd.done = reinterpret_cast<uint32_t *>(A + o_done);
-    bd.pieces = reinterpret_cast<const int4 *>(A + o_p);
-    bd.npieces = (int)pieces.size();
-    bd.err = b->d_err;
-    bd.cc_count = reinterpret_cast<uint32_t *>(A + o_ccn);
-    bd.cc_list = reinterpret_cast<uint2 *>(A + o_ccl);
+    b->d_io = reinterpret_cast<TickIO *>(b->arena + o_io);
+    b->d_ptrs = reinterpret_cast<hmi_pointer *>(b->arena + o_ptr);
+    b->d_err = reinterpret_cast<uint32_t *>(b->arena + o_err);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
     b->num_sms = sms > 0 ? sms : 1;
+    if (plan_build(b, ngroups) != HMI_OK) {
+        const int st = g_last_error;
+        batch_free(b);
+        fail(st);
+        return nullptr;
+    }
     return b;
 }
 
-// Kernels of one tick on cs with the slot's pointer table; event nodes (or
-// plain event records) bracket the classification kernel.
+// Kernels of one tick with the slot's pointer table.  Each group runs its
+// chain (luma, classify, morphology, block components, finish) on its own
+// branch; group g starts its luma after group g-1's luma, so the HBM-bound
+// passes of later groups overlap the latency-bound tail of earlier ones.
+// With one group, event records (or event nodes) bracket the classify kernel.
 cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1,
                          bool capture)
 {
-    BatchDev bd = b->bd;
-    bd.io = b->d_io + (size_t)slot * b->n;
+    TickIO *dio = b->d_io + (size_t)slot * b->n;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(const_cast<TickIO *>(bd.io), b->h_io + (size_t)slot * b->n,
-                             sizeof(TickIO) * b->n, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(dio, b->h_io + (size_t)slot * b->n, sizeof(TickIO) * b->n,
+                             cudaMemcpyHostToDevice, cs)) != cudaSuccess)
         return e;
-    if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
-    if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
-        return e;
-    if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;
-    if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
-        return e;
-    if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
-    return launch_finish(bd, cs);
+    const int ng = (int)b->groups.size();
+    if (ng == 1) {
+        BatchDev bd = b->groups[0].bd;
+        bd.io = dio;
+        if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
+        if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
+            return e;
+        if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;
+        if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
+            return e;
+        if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
+        return launch_finish(bd, cs);
+    }
+    if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
+    for (int g = 0; g < ng; ++g) {
+        Group &G = b->groups[g];
+        BatchDev bd = G.bd;
+        bd.io = dio + G.off;
+        if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
+        if (g > 0 && (e = cudaStreamWaitEvent(G.cs, b->groups[g - 1].ev_luma, 0)) != cudaSuccess) return e;
+        if ((e = launch_luma(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(G.ev_luma, G.cs)) != cudaSuccess) return e;
+        if ((e = launch_classify(bd, G.cs)) != cudaSuccess) return e;
+        if ((e = launch_morph_cc(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
+        if ((e = launch_finish(bd, G.cs)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;
+    }
+    for (int g = 0; g < ng; ++g)
+        if ((e = cudaStreamWaitEvent(cs, b->groups[g].ev_done, 0)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 int build_graph(hmi_batch *b, int slot)
 {
     cudaGraph_t g = nullptr;
     HMI_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_tick(b, slot, b->cs, b->dummy_ev[0], b->dummy_ev[1], true);
+    const bool one = b->groups.size() == 1;
+    cudaError_t e = enqueue_tick(b, slot, b->cs, one ? b->dummy_ev[0] : nullptr,
+                                 one ? b->dummy_ev[1] : nullptr, true);
     cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_fail(e != cudaSuccess ? e : e2);
     }
-    size_t nn = 0;
-    cudaGraphGetNodes(g, nullptr, &nn);
-    std::vector<cudaGraphNode_t> nodes(nn);
-    cudaGraphGetNodes(g, nodes.data(), &nn);
-    std::vector<cudaGraphNode_t> evn;
-    for (auto nd : nodes) {
-        cudaGraphNodeType t;
-        cudaGraphNodeGetType(nd, &t);
-        if (t == cudaGraphNodeTypeEventRecord) evn.push_back(nd);
-    }
-    for (auto nd : evn) {
-        cudaEvent_t ev;
-        cudaGraphEventRecordNodeGetEvent(nd, &ev);
-        if (ev == b->dummy_ev[0]) b->ev_node[slot][0] = nd;
-        if (ev == b->dummy_ev[1]) b->ev_node[slot][1] = nd;
-    }
-    if (!b->ev_node[slot][0] || !b->ev_node[slot][1]) {
-        cudaGraphDestroy(g);
-        return fail(HMI_ERR_DEVICE);
+    if (one) {
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            cudaGraphNodeGetType(nd, &t);
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            cudaGraphEventRecordNodeGetEvent(nd, &ev);
+            if (ev == b->dummy_ev[0]) b->ev_node[slot][0] = nd;
+            if (ev == b->dummy_ev[1]) b->ev_node[slot][1] = nd;
+        }
+        if (!b->ev_node[slot][0] || !b->ev_node[slot][1]) {
+            cudaGraphDestroy(g);
+            return fail(HMI_ERR_DEVICE);
+        }
     }
     e = cudaGraphInstantiate(&b->graph[slot], g, 0);
     if (e != cudaSuccess) {
@@ -450,14 +574,16 @@ int build_graph(hmi_batch *b, int slot)
     return HMI_OK;
 }
 
-// Fill slot pointers for one tick.  Frames and masks not usable in place are
-// staged through the stream's own buffers; returns which masks need a copy out.
+// Fill slot pointers for one tick (permuted order).  Frames and masks not
+// usable in place are staged through the stream's own buffers; returns which
+// masks need a copy out.
 int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *const *masks,
                  bool async_mode, cudaStream_t cs, std::vector<int> *mask_copy)
 {
     TickIO *io = b->h_io + (size_t)slot * b->n;
     for (int i = 0; i < b->n; ++i) {
         hmi_stream *s = b->s[i];
+        TickIO &t = io[b->pos[i]];
         const uint8_t *f = frames[i];
         if (!f) return fail(HMI_ERR_INVALID_ARG);
         bool dev = b->seen_device(f);
@@ -467,23 +593,27 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
         }
         if (async_mode && !dev) return fail(HMI_ERR_INVALID_ARG);
         if (dev && (s->w % 16) == 0 && (reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
-            io[i].frame = f;
-            io[i].frame_pitch = 3LL * s->w;
+            t.frame = f;
+            t.frame_pitch = 3LL * s->w;
         } else {
-            HMI_CUDA(cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, f, 3 * (size_t)s->w, 3 * (size_t)s->w,
-                                       s->h, cudaMemcpyDefault, cs));
-            io[i].frame = s->d_frame;
-            io[i].frame_pitch = s->L.fpitch;
+            if (3 * (size_t)s->w == (size_t)s->L.fpitch) {
+                HMI_CUDA(cudaMemcpyAsync(s->d_frame, f, 3 * (size_t)s->w * s->h, cudaMemcpyDefault, cs));
+            } else {
+                HMI_CUDA(cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, f, 3 * (size_t)s->w, 3 * (size_t)s->w,
+                                           s->h, cudaMemcpyDefault, cs));
+            }
+            t.frame = s->d_frame;
+            t.frame_pitch = s->L.fpitch;
         }
         uint8_t *m = (masks != nullptr) ? masks[i] : nullptr;
         if (m == nullptr) {
-            io[i].mask = nullptr;
+            t.mask = nullptr;
         } else if (b->seen_device(m) || is_device_ptr(m)) {
             b->remember_device(m);
-            io[i].mask = m;
+            t.mask = m;
         } else {
             if (async_mode) return fail(HMI_ERR_INVALID_ARG);
-            io[i].mask = s->d_mask;
+            t.mask = s->d_mask;
             if (mask_copy) mask_copy->push_back(i);
         }
     }
@@ -504,7 +634,7 @@ int acquire_slot(hmi_batch *b)
 int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool prof = b->prof_used < b->prof_max;
+    const bool prof = b->prof_used < b->prof_max && b->groups.size() == 1;
     if (prof) {
         e0 = b->prof_ev[2 * b->prof_used];
         e1 = b->prof_ev[2 * b->prof_used + 1];
@@ -515,10 +645,12 @@ int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
             int st = build_graph(b, slot);
             if (st != HMI_OK) return st;
         }
-        HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][0],
-                                                      e0 ? e0 : b->dummy_ev[0]));
-        HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][1],
-                                                      e1 ? e1 : b->dummy_ev[1]));
+        if (b->groups.size() == 1) {
+            HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][0],
+                                                          e0 ? e0 : b->dummy_ev[0]));
+            HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][1],
+                                                          e1 ? e1 : b->dummy_ev[1]));
+        }
         HMI_CUDA(cudaGraphLaunch(b->graph[slot], cs));
     } else {
         HMI_CUDA(enqueue_tick(b, slot, cs, e0, e1, false));
@@ -547,7 +679,7 @@ int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks
     int st = prepare_slot(b, slot, frames, masks, false, b->cs, &mcopy);
     if (st != HMI_OK) return st;
     TickIO *io = b->h_io + (size_t)slot * b->n;
-    for (int i = 0; i < b->n; ++i) io[i].ptr_out = b->d_ptrs + i;
+    for (int i = 0; i < b->n; ++i) io[b->pos[i]].ptr_out = b->d_ptrs + i;
     st = run_tick(b, slot, b->cs, false);
     if (st != HMI_OK) return st;
     for (int i : mcopy) {
@@ -578,9 +710,21 @@ int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *mask
     int st = prepare_slot(b, slot, frames, masks, true, cs, nullptr);
     if (st != HMI_OK) return st;
     TickIO *io = b->h_io + (size_t)slot * b->n;
-    for (int i = 0; i < b->n; ++i) io[i].ptr_out = ptrs ? ptrs + i : nullptr;
+    for (int i = 0; i < b->n; ++i) io[b->pos[i]].ptr_out = ptrs ? ptrs + i : nullptr;
     return run_tick(b, slot, cs, use_graph != 0);
 }
+
+int batch_set_groups(hmi_batch *b, int ng)
+{
+    if (!b || ng < 1 || ng > 64) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    HMI_CUDA(cudaDeviceSynchronize());
+    plan_free(b);
+    for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
+    return plan_build(b, ng);
+}
+
+int default_groups(int n) { return std::min(4, n); }
 
 }  // namespace
 
@@ -679,7 +823,7 @@ hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p)
               cudaMemcpy(s->d_ds, &s->ds, sizeof(DevStream), cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) {
         hmi_stream *one = s;
-        s->self = batch_new(&one, 1);
+        s->self = batch_new(&one, 1, 1);
         ok = s->self != nullptr;
     }
     if (!ok) {
@@ -769,7 +913,15 @@ int hmi_process_frame_async(hmi_stream *s, const uint8_t *frame, uint8_t *mask_o
     return batch_async(s->self, &frame, masks, pointer_out, cuda_stream, 0);
 }
 
-hmi_batch *hmi_batch_create(hmi_stream *const *s, int n) { return batch_new(s, n); }
+hmi_batch *hmi_batch_create(hmi_stream *const *s, int n) { return batch_new(s, n, default_groups(n)); }
+
+int hmi_batch_set_groups(hmi_batch *b, int groups) { return batch_set_groups(b, groups); }
+
+int hmi_batch_get_groups(const hmi_batch *b)
+{
+    if (!b) return fail(HMI_ERR_INVALID_ARG);
+    return (int)b->groups.size();
+}
 
 void hmi_batch_destroy(hmi_batch *b) { batch_free(b); }
 
@@ -792,7 +944,7 @@ int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
     std::lock_guard<std::mutex> lk(g_cache_mu);
     if (!g_cache || g_cache->n != n || !std::equal(g_cache->s.begin(), g_cache->s.end(), s)) {
         batch_free(g_cache);
-        g_cache = batch_new(s, n);
+        g_cache = batch_new(s, n, default_groups(n));
         if (!g_cache) return g_last_error;
     }
     return batch_sync(g_cache, frames, masks, ptrs);
@@ -801,6 +953,7 @@ int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
 int hmi_batch_profile(hmi_batch *b, int max_ticks)
 {
     if (!b || max_ticks < 0 || max_ticks > 1000000) return fail(HMI_ERR_INVALID_ARG);
+    if (max_ticks > 0 && b->groups.size() != 1) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
     HMI_CUDA(cudaDeviceSynchronize());
     for (auto e : b->prof_ev) cudaEventDestroy(e);

@@ -64,6 +64,8 @@ SIGNATURES = {
     "hmi_batch_destroy": (None, [_P]),
     "hmi_batch_process": (_I, [_P, _P, _P, _P]),
     "hmi_batch_process_async": (_I, [_P, _P, _P, _P, _P, _I]),
+    "hmi_batch_set_groups": (_I, [_P, _I]),
+    "hmi_batch_get_groups": (_I, [_P]),
     "hmi_batch_profile": (_I, [_P, _I]),
     "hmi_batch_profile_read": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "hmi_get_background_stats": (_I, [_P, _P, _P]),
@@ -209,6 +211,17 @@ def hmi_batch_process_async(b: int, frames, masks, ptrs, cuda_stream: int, use_g
     ma = _ptr_array(masks) if masks is not None else None
     _check(load().hmi_batch_process_async(b, fa, ma, _addr(ptrs), cuda_stream, int(use_graph)),
            "hmi_batch_process_async")
+
+
+def hmi_batch_set_groups(b: int, groups: int) -> None:
+    _check(load().hmi_batch_set_groups(b, groups), "hmi_batch_set_groups")
+
+
+def hmi_batch_get_groups(b: int) -> int:
+    g = load().hmi_batch_get_groups(b)
+    if g < 0:
+        raise HmiError(g, "hmi_batch_get_groups")
+    return g
 
 
 def hmi_batch_profile(b: int, max_ticks: int) -> None:

@@ -303,6 +303,43 @@ def test_batch_config4_sync_async_graph():
             g.close()
 
 
+def test_batch_group_count_does_not_change_results():
+    """The same streams processed with 1, 3 and 5 concurrent groups per tick
+    give identical masks, labels and pointers (and match the oracle)."""
+    idx = [0, 5, 17, 33, 40, 47, 50, 58, 61, 63, 2, 36]
+    frames = {t: [synth.run_frame(4, i, t) for i in idx] for t in range(3)}
+    results = {}
+    for groups in (1, 3, 5):
+        gs, os_ = _batch_streams(4, idx)
+        b = hmi.hmi_batch_create([g.handle for g in gs])
+        hmi.hmi_batch_set_groups(b, groups)
+        assert hmi.hmi_batch_get_groups(b) == groups
+        out = []
+        for t in range(3):
+            dframes = [_dev(f) for f in frames[t]]
+            dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+            dptrs = torch.zeros(len(idx) * 40, dtype=torch.uint8, device="cuda")
+            hmi.hmi_batch_process_async(b, dframes, dmasks, dptrs.data_ptr(),
+                                        torch.cuda.current_stream().cuda_stream, t % 2 == 0)
+            torch.cuda.synchronize()
+            arr = dptrs.cpu().numpy().view(hmi.POINTER_DTYPE)
+            plist = [dict(zip(arr.dtype.names, [x.item() for x in arr[i]])) for i in range(len(idx))]
+            if groups == 3:
+                _compare_batch(gs, os_, frames[t], dmasks, plist, f"groups=3 t={t}")
+            out.append(([m.cpu().numpy() for m in dmasks], [g.labels() for g in gs], plist))
+        results[groups] = out
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
+    for groups in (3, 5):
+        for t in range(3):
+            for a, c in zip(results[1][t][0], results[groups][t][0]):
+                assert np.array_equal(a, c)
+            for a, c in zip(results[1][t][1], results[groups][t][1]):
+                assert np.array_equal(a, c)
+            assert results[1][t][2] == results[groups][t][2]
+
+
 def test_process_batch_cached_plan():
     idx = [0, 1, 40, 50, 60]
     gs, os_ = _batch_streams(4, idx)
