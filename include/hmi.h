@@ -145,7 +145,7 @@ HMI_API void hmi_batch_destroy(hmi_batch *b);
  * `groups` groups of about equal pixel count; each group's kernels form their
  * own chain, and the chains of a tick overlap (each group's luma pass starts
  * after the previous group's), so the bandwidth-bound passes of one group run
- * beside the latency-bound tail of another.  Default: min(4, n).  Changing it
+ * beside the latency-bound tail of another.  Default: min(2, n).  Changing it
  * rebuilds the plan (waits for the device).  Results do not depend on it. */
 HMI_API int hmi_batch_set_groups(hmi_batch *b, int groups);
 HMI_API int hmi_batch_get_groups(const hmi_batch *b);

@@ -336,7 +336,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl;
     };
     std::vector<Tables> T(ng);
     Arena a;
@@ -371,6 +371,8 @@ int plan_build(hmi_batch *b, int ng)
         t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
         t.o_ccn = a.take(sizeof(uint32_t));
         t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
+        t.o_skn = a.take(sizeof(uint32_t));
+        t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
     }
     if (cudaMalloc(&b->plan, a.off) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -414,6 +416,8 @@ int plan_build(hmi_batch *b, int ng)
         bd.err = b->d_err;
         bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
         bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
+        bd.skin_count = reinterpret_cast<uint32_t *>(A + t.o_skn);
+        bd.skin_list = reinterpret_cast<uint2 *>(A + t.o_skl);
     }
     if (!ok) {
         (void)cudaGetLastError();
@@ -509,7 +513,7 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
         if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
         if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
             return e;
-        if ((e = launch_classify(bd, cs)) != cudaSuccess) return e;
+        if ((e = launch_classify(bd, cs, b->num_sms)) != cudaSuccess) return e;
         if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
             return e;
         if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
@@ -524,7 +528,7 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
         if (g > 0 && (e = cudaStreamWaitEvent(G.cs, b->groups[g - 1].ev_luma, 0)) != cudaSuccess) return e;
         if ((e = launch_luma(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_luma, G.cs)) != cudaSuccess) return e;
-        if ((e = launch_classify(bd, G.cs)) != cudaSuccess) return e;
+        if ((e = launch_classify(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = launch_morph_cc(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = launch_finish(bd, G.cs)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;
@@ -724,7 +728,7 @@ int batch_set_groups(hmi_batch *b, int ng)
     return plan_build(b, ng);
 }
 
-int default_groups(int n) { return std::min(4, n); }
+int default_groups(int n) { return std::min(2, n); }
 
 }  // namespace
 

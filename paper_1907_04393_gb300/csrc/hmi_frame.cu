@@ -242,10 +242,12 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
     return (d > 0) & (d >= D.gray_tol) & hue;
 }
 
-// One thread per 16-pixel chunk.  The background test runs on all 16
-// pixels; the gray and hue tests run only on the pixels that are outside
-// their band (camera noise and the hand: a few per thousand), one per lane
-// per round, reading their three bytes again (an L1 hit).
+// One thread per 16-pixel chunk: the background test on all 16 pixels.  The
+// word of out-of-band pixels is stored as the raw mask; chunks that have any
+// are appended (warp-aggregated) to the skin queue, where k_skin runs the gray
+// and hue tests on just those pixels and clears the ones that fail.  Out-of-
+// band pixels are a few percent (the hand, camera noise), so the skin tests
+// run densely instead of stalling whole warps here.
 __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -262,14 +264,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
             const int u = base + lane;
             uint32_t bits = 0;
-            int y = 0, j = 0, x0 = 0;
-            uint32_t f[12];
+            int y = 0, j = 0;
             if (u < piece.z) {
                 y = u / cpr;
                 j = u - y * cpr;
-                x0 = j * kChunkPx;
+                const int x0 = j * kChunkPx;
                 if (x0 < w) {
-                    uint32_t l[12], h[12];
+                    uint32_t f[12], l[12], h[12];
                     load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                     load48(lo + (long long)y * fpitch + 3 * x0, once, l);
                     load48(hi + (long long)y * fpitch + 3 * x0, once, h);
@@ -278,29 +279,60 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
                     if (npx < kChunkPx) bits &= (1u << npx) - 1u;
                 }
             }
-            if (__reduce_max_sync(kFull, (uint32_t)__popc(bits)) > 8u) {
-                // dense (the warp crosses the hand): all 16 pixels from registers
-                uint32_t sk = 0;
-#pragma unroll
-                for (int k = 0; k < kChunkPx; ++k)
-                    sk |= (uint32_t)skin_rgb(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2), D, g) << k;
-                bits &= sk;
-            } else {
-                // sparse (camera noise): one pixel per lane per round
-                uint32_t todo = bits;
-                const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * x0;
-                while (__any_sync(kFull, todo != 0u)) {
-                    if (todo) {
-                        const int k = __ffs(todo) - 1;
-                        const uint8_t *px = row + 3 * k;
-                        if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) bits &= ~(1u << k);
-                        todo &= todo - 1u;
-                    }
-                }
-            }
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
             if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+            const unsigned want = __ballot_sync(kFull, bits != 0u);
+            if (want) {
+                uint32_t slot0 = 0;
+                if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
+                slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
+                if (bits) {
+                    const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                    b.skin_list[slot] = make_uint2(((uint32_t)piece.x << 16) | bits, (uint32_t)u);
+                }
+            }
         }
+    }
+}
+
+// One thread per queued chunk: gray and hue tests on its out-of-band pixels;
+// the pixels that fail are cleared from the raw mask word.
+__global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
+{
+    const uint32_t n = *(volatile uint32_t *)b.skin_count;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        const uint2 e = b.skin_list[it];
+        const int sidx = (int)(e.x >> 16);
+        const uint32_t bits = e.x & 0xffffu;
+        const int u = (int)e.y;
+        const DevStream &D = b.ds[sidx];
+        const TickIO io = b.io[sidx];
+        const uint32_t g = D.st->gain;
+        const int cpr = 2 * D.nwords;
+        const int y = u / cpr, j = u - y * cpr;
+        const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * j * kChunkPx;
+        uint32_t fail = 0;
+        if (__popc(bits) > 4) {
+            uint32_t f[12];
+            const uint4 *q = reinterpret_cast<const uint4 *>(row);
+            const uint4 a = __ldg(q), c = __ldg(q + 1), d = __ldg(q + 2);
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+            f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+            f[8] = d.x; f[9] = d.y; f[10] = d.z; f[11] = d.w;
+#pragma unroll
+            for (int k = 0; k < kChunkPx; ++k) {
+                if (!((bits >> k) & 1u)) continue;
+                if (!skin_rgb(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2), D, g))
+                    fail |= 1u << k;
+            }
+        } else {
+            for (uint32_t todo = bits; todo; todo &= todo - 1u) {
+                const int k = __ffs(todo) - 1;
+                const uint8_t *px = row + 3 * k;
+                if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) fail |= 1u << k;
+            }
+        }
+        if (fail) atomicAnd(D.raw + (long long)y * D.nwords + (j >> 1), ~(fail << (16 * (j & 1))));
     }
 }
 
@@ -642,9 +674,12 @@ cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs)
+cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 

@@ -112,6 +112,8 @@ struct BatchDev {
     uint32_t *err;                            // batch error word: OR of the streams' flags
     uint32_t *cc_count;                       // non-empty blocks listed this tick
     uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
+    uint32_t *skin_count;                     // chunks queued for the skin tests this tick
+    uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
 };
 
 // Threads per CTA of every kernel of a tick.
@@ -121,7 +123,7 @@ constexpr int kThreads = 256;
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
-cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
