@@ -47,7 +47,6 @@ int cuda_fail(cudaError_t e)
     } while (0)
 
 constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
-constexpr int kPieceChunks = 512;   // 16-px chunks per CTA piece (8192 px)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -360,8 +359,18 @@ int plan_build(hmi_batch *b, int ng)
             const int halo = 2 * (st->p.open_iters + st->p.close_iters);
             t.max_halo = std::max(t.max_halo, halo);
             t.uniform_halo = (t.uniform_halo == -2 || t.uniform_halo == halo) ? halo : -1;
-            for (int c = 0; c < chunks; c += kPieceChunks)
-                t.pieces.push_back(make_int4(k, c, std::min(chunks, c + kPieceChunks), 0));
+            // staged pieces of at most kStageChunks chunks: whole rows (up to
+            // 32 per piece), or row segments when a row alone is larger
+            const int cpr = 2 * L.nwords;
+            if (cpr <= kStageChunks) {
+                const int rows = std::max(1, std::min(32, kStageChunks / cpr));
+                for (int y0 = 0; y0 < L.h; y0 += rows)
+                    t.pieces.push_back(make_int4(k, y0, 0, (std::min(rows, L.h - y0) << 16) | cpr));
+            } else {
+                for (int y0 = 0; y0 < L.h; ++y0)
+                    for (int j0 = 0; j0 < cpr; j0 += kStageChunks)
+                        t.pieces.push_back(make_int4(k, y0, j0, (1 << 16) | std::min(kStageChunks, cpr - j0)));
+            }
         }
         t.o_c = a.take(sizeof(unsigned long long) * (m + 1));
         t.o_t = a.take(sizeof(uint32_t) * (m + 1));

@@ -14,6 +14,7 @@
 
 #include "hmi_ccfill.cuh"
 #include "hmi_internal.cuh"
+#include "hmi_stage.cuh"
 
 namespace hmi {
 
@@ -63,6 +64,50 @@ __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b)
     return (77u * r + 150u * g + 29u * b + 128u) >> 8;
 }
 
+// ---------------------------------------------------------------------------
+// Pieces: (stream, first row, first chunk, rows << 16 | chunks) -- at most
+// kStageChunks 16-pixel chunks of whole rows (or a row segment for very wide
+// rows).  A CTA walks a contiguous range of pieces, so consecutive pieces
+// mostly share a stream.  The row segments of the next piece are bulk-copied
+// into the other stage buffer while the current one is processed; each thread
+// handles one chunk of a piece.
+// ---------------------------------------------------------------------------
+struct PieceGeo {
+    int s, y0, j0, rows, cols, vc;   // vc: chunks per row that lie inside the image
+};
+
+__device__ __forceinline__ PieceGeo piece_geo(const int4 pc, const DevStream &D)
+{
+    PieceGeo g;
+    g.s = pc.x;
+    g.y0 = pc.y;
+    g.j0 = pc.z;
+    g.rows = pc.w >> 16;
+    g.cols = pc.w & 0xffff;
+    g.vc = max(0, min(g.cols, (D.w + kChunkPx - 1) / kChunkPx - g.j0));
+    return g;
+}
+
+// Issue (warp 0) the copies of piece `pc` into stage `dst`: for each of the
+// nsrc arrays and each row, 48 * vc bytes from src[k] + (y0 + r) * pitch[k] + 48 * j0.
+template <int NSRC>
+__device__ __forceinline__ void issue_piece(const PieceGeo &g, const uint8_t *const (&src)[NSRC],
+                                            const long long (&pitch)[NSRC], uint8_t *dst,
+                                            uint64_t *bar, uint64_t pol, int lane)
+{
+    const uint32_t rowb = 48u * (uint32_t)g.vc;
+    const uint32_t sb = 48u * (uint32_t)g.cols;   // stage row stride
+    if (lane == 0) mbar_expect_tx(bar, rowb * (uint32_t)g.rows * NSRC);
+    __syncwarp();
+    if (rowb == 0) return;
+    for (int r = lane; r < g.rows; r += 32) {
+#pragma unroll
+        for (int k = 0; k < NSRC; ++k)
+            bulk_g2s(dst + (size_t)k * kStageChunks * 48 + (size_t)r * sb,
+                     src[k] + (long long)(g.y0 + r) * pitch[k] + 48LL * g.j0, rowb, bar, pol);
+    }
+}
+
 // Sum of luma8 over 16 pixels (48 bytes): each pixel's 3 bytes are gathered
 // into one word with a byte permute, then one 4-way byte dot product with
 // (77, 150, 29, 0) plus 128, shifted per pixel.
@@ -73,7 +118,6 @@ __device__ __forceinline__ uint32_t luma_sum16(const uint32_t (&f)[12])
 #pragma unroll
     for (int k = 0; k < kChunkPx; ++k) {
         const int b = 3 * k, wi = b >> 2, o = b & 3;
-        // bytes b, b+1, b+2 of the 48 (they span at most two words)
         const uint32_t lo = f[wi], hi = (wi + 1 < 12) ? f[wi + 1] : 0u;
         const uint32_t px = __byte_perm(lo, hi, (uint32_t)(o | ((o + 1) << 4) | ((o + 2) << 8) | (0x7 << 12)) & 0x7777u);
         sum += __dp4a(px & 0x00ffffffu, kW, 128u) >> 8;
@@ -92,58 +136,92 @@ __device__ __forceinline__ uint32_t luma_sum_n(const uint32_t (&f)[12], int npx)
     return sum;
 }
 
+__device__ __forceinline__ void lds48(const uint8_t *p, uint32_t (&w)[12])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(p);
+    const uint4 a = q[0], b = q[1], c = q[2];
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+}
+
 // ---------------------------------------------------------------------------
-// k_luma: one CTA per piece (a contiguous chunk range of one stream).
+// k_luma: frame luma sums; the last CTA turns them into every stream's gain.
 // ---------------------------------------------------------------------------
+constexpr int kLumaStage = kStageChunks * 48;
+
 __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
 {
+    __shared__ __align__(128) uint8_t stage[2][kLumaStage];
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ unsigned long long red[kThreads / 32];
     __shared__ bool is_last;
-    const int tid = threadIdx.x;
-    const uint64_t keep = policy_evict_last();
-    // a contiguous range of pieces per CTA: consecutive pieces mostly share a
-    // stream, so partial sums are flushed only when the stream changes
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
     const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
+    const uint64_t keep = policy_evict_last();
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int p, int st) {
+        const int4 pc = b.pieces[p];
+        const DevStream &D = b.ds[pc.x];
+        const PieceGeo g = piece_geo(pc, D);
+        const TickIO &io = b.io[pc.x];
+        const uint8_t *const src[1] = {io.frame};
+        const long long pitch[1] = {io.frame_pitch};
+        issue_piece<1>(g, src, pitch, stage[st], &bar[st], keep, lane);
+    };
+    if (wid == 0 && p0 < p1) issue(p0, 0);
+    uint32_t phase = 0, inflight = (p0 < p1) ? 1u : 0u;
+    bool ok = true;
     unsigned long long acc = 0;
-    for (int pc = p0; pc < p1; ++pc) {
-        const int4 piece = b.pieces[pc];
-        const DevStream &D = b.ds[piece.x];
-        const TickIO io = b.io[piece.x];
-        const int w = D.w, cpr = 2 * D.nwords;
-        // two chunks per thread per round, both loads in flight before the sums
-        for (int u = piece.y + tid; u < piece.z; u += 2 * blockDim.x) {
-            uint32_t f[2][12];
-            int npx[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int uu = u + q * (int)blockDim.x;
-                npx[q] = 0;
-                if (uu < piece.z) {
-                    const int y = uu / cpr, x0 = (uu - y * cpr) * kChunkPx;
-                    if (x0 < w) {
-                        npx[q] = min(kChunkPx, w - x0);
-                        load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
+    for (int p = p0; p < p1 && ok; ++p) {
+        const int st = (p - p0) & 1;
+        if (p + 1 < p1) {
+            if (wid == 0) issue(p + 1, st ^ 1);
+            inflight |= 1u << (st ^ 1);
         }
-        const bool flush = (pc + 1 == p1) || (b.pieces[pc + 1].x != piece.x);
+        ok = __syncthreads_and(mbar_wait(&bar[st], (phase >> st) & 1u));
+        if (!ok) break;
+        phase ^= 1u << st;
+        inflight &= ~(1u << st);
+        const int4 pc = b.pieces[p];
+        const DevStream &D = b.ds[pc.x];
+        const PieceGeo g = piece_geo(pc, D);
+        if (tid < g.rows * g.cols) {
+            const int r = tid / g.cols, jj = tid - r * g.cols;
+            const int x0 = (g.j0 + jj) * kChunkPx;
+            if (x0 < D.w) {
+                uint32_t f[12];
+                lds48(stage[st] + r * 48 * g.cols + 48 * jj, f);
+                const int npx = min(kChunkPx, D.w - x0);
+                acc += (npx == kChunkPx) ? luma_sum16(f) : luma_sum_n(f, npx);
+            }
+        }
+        const bool flush = (p + 1 == p1) || (b.pieces[p + 1].x != pc.x);
         if (flush) {   // CTA-uniform
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            if (lane == 0) red[wid] = acc;
             __syncthreads();
             if (tid == 0) {
                 unsigned long long t = 0;
                 for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
                 atomicAdd(&D.st->sy, t);
             }
-            __syncthreads();
             acc = 0;
         }
+        __syncthreads();   // stage st is free for the copies of piece p + 2
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(b.err, kErrStageWait);
+        // let copies still in flight land before the CTA's shared memory goes away
+        for (int st = 0; st < 2; ++st)
+            if ((inflight >> st) & 1u) (void)mbar_wait(&bar[st], (phase >> st) & 1u);
     }
     // the last CTA to finish computes every stream's gain
     __threadfence();
@@ -242,56 +320,94 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
     return (d > 0) & (d >= D.gray_tol) & hue;
 }
 
-// One thread per 16-pixel chunk: the background test on all 16 pixels.  The
-// word of out-of-band pixels is stored as the raw mask; chunks that have any
-// are appended (warp-aggregated) to the skin queue, where k_skin runs the gray
-// and hue tests on just those pixels and clears the ones that fail.  Out-of-
-// band pixels are a few percent (the hand, camera noise), so the skin tests
-// run densely instead of stalling whole warps here.
-__global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
+// One thread per 16-pixel chunk of a staged piece: the background test on all
+// 16 pixels.  The word of out-of-band pixels is stored as the raw mask; chunks
+// that have any are appended (warp-aggregated) to the skin queue, where k_skin
+// runs the gray and hue tests on just those pixels and clears the ones that
+// fail.  Out-of-band pixels are a few percent (the hand, camera noise), so the
+// skin tests run densely instead of stalling whole warps here.
+constexpr int kClassStage = 3 * kStageChunks * 48;   // frame, lo, hi
+constexpr size_t kClassSmem = 2 * (size_t)kClassStage;
+
+__global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev b)
 {
-    const int tid = threadIdx.x, lane = tid & 31;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
+    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
     const uint64_t once = policy_evict_first();
-    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
-        const int4 piece = b.pieces[pc];
-        const DevStream &D = b.ds[piece.x];
-        const TickIO io = b.io[piece.x];
-        const uint32_t g = D.st->gain;
-        const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
-        const uint8_t *lo = D.lo, *hi = D.hi;
-        uint32_t *raw = D.raw;
-        // warp-uniform loop so that chunk pairs can combine with a shuffle
-        for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
-            const int u = base + lane;
-            uint32_t bits = 0;
-            int y = 0, j = 0;
-            if (u < piece.z) {
-                y = u / cpr;
-                j = u - y * cpr;
-                const int x0 = j * kChunkPx;
-                if (x0 < w) {
-                    uint32_t f[12], l[12], h[12];
-                    load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
-                    load48(lo + (long long)y * fpitch + 3 * x0, once, l);
-                    load48(hi + (long long)y * fpitch + 3 * x0, once, h);
-                    bits = outside_bits<kChunkPx - 1>(f, l, h, g);
-                    const int npx = w - x0;
-                    if (npx < kChunkPx) bits &= (1u << npx) - 1u;
-                }
-            }
-            const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
-            if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
-            const unsigned want = __ballot_sync(kFull, bits != 0u);
-            if (want) {
-                uint32_t slot0 = 0;
-                if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
-                slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
-                if (bits) {
-                    const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
-                    b.skin_list[slot] = make_uint2(((uint32_t)piece.x << 16) | bits, (uint32_t)u);
-                }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int p, int st) {
+        const int4 pc = b.pieces[p];
+        const DevStream &D = b.ds[pc.x];
+        const PieceGeo g = piece_geo(pc, D);
+        const TickIO &io = b.io[pc.x];
+        const uint8_t *const src[3] = {io.frame, D.lo, D.hi};
+        const long long pitch[3] = {io.frame_pitch, D.fpitch, D.fpitch};
+        issue_piece<3>(g, src, pitch, smem + (size_t)st * kClassStage, &bar[st], once, lane);
+    };
+    if (wid == 0 && p0 < p1) issue(p0, 0);
+    uint32_t phase = 0, inflight = (p0 < p1) ? 1u : 0u;
+    bool ok = true;
+    for (int p = p0; p < p1 && ok; ++p) {
+        const int st = (p - p0) & 1;
+        if (p + 1 < p1) {
+            if (wid == 0) issue(p + 1, st ^ 1);
+            inflight |= 1u << (st ^ 1);
+        }
+        ok = __syncthreads_and(mbar_wait(&bar[st], (phase >> st) & 1u));
+        if (!ok) break;
+        phase ^= 1u << st;
+        inflight &= ~(1u << st);
+        const int4 pc = b.pieces[p];
+        const DevStream &D = b.ds[pc.x];
+        const PieceGeo g = piece_geo(pc, D);
+        const uint32_t gain = D.st->gain;
+        const uint8_t *sf = smem + (size_t)st * kClassStage;
+        uint32_t bits = 0;
+        int r = 0, jj = 0;
+        const bool mine = tid < g.rows * g.cols;
+        if (mine) {
+            r = tid / g.cols;
+            jj = tid - r * g.cols;
+            const int x0 = (g.j0 + jj) * kChunkPx;
+            if (x0 < D.w) {
+                uint32_t f[12], l[12], h[12];
+                const int off = r * 48 * g.cols + 48 * jj;
+                lds48(sf + off, f);
+                lds48(sf + kStageChunks * 48 + off, l);
+                lds48(sf + 2 * kStageChunks * 48 + off, h);
+                bits = outside_bits<kChunkPx - 1>(f, l, h, gain);
+                const int npx = D.w - x0;
+                if (npx < kChunkPx) bits &= (1u << npx) - 1u;
             }
         }
+        const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
+        const int y = g.y0 + r, j = g.j0 + jj;
+        if (mine && (jj & 1) == 0) D.raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+        const unsigned want = __ballot_sync(kFull, bits != 0u);
+        if (want) {
+            uint32_t slot0 = 0;
+            if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
+            slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
+            if (bits) {
+                const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                b.skin_list[slot] = make_uint2(((uint32_t)pc.x << 16) | bits, (uint32_t)(y * 2 * D.nwords + j));
+            }
+        }
+        __syncthreads();   // stage st is free for the copies of piece p + 2
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(b.err, kErrStageWait);
+        // let copies still in flight land before the CTA's shared memory goes away
+        for (int st = 0; st < 2; ++st)
+            if ((inflight >> st) & 1u) (void)mbar_wait(&bar[st], (phase >> st) & 1u);
     }
 }
 
@@ -662,21 +778,26 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int grid_for_pieces(int npieces)
-{
-    return npieces > 0 ? npieces : 1;
-}
-
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 8));
+    const int grid = std::max(1, std::min(b.npieces, num_sms * 6));
     k_luma<<<grid, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    static bool attr_set[64] = {};   // the shared-memory opt-in is per device
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e0 = cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClassSmem);
+        if (e0 != cudaSuccess) return e0;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    const int grid = std::max(1, std::min(b.npieces, num_sms * 3));
+    k_classify<<<grid, kThreads, kClassSmem, cs>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
