@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         S.nrec = 0;
         S.best = 0;
         S.overflow = false;
-        if (blockIdx.x == 0) {                   // k_skin and k_block_cc are done with their lists
+        if (blockIdx.x == 0) {                   // the skin and block queues are consumed
             *b.cc_count = 0u;
             *b.skin_count = 0u;
         }

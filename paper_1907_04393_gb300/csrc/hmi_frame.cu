@@ -14,7 +14,6 @@
 
 #include "hmi_ccfill.cuh"
 #include "hmi_internal.cuh"
-#include "hmi_stage.cuh"
 
 namespace hmi {
 
@@ -67,46 +66,9 @@ __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b)
 // ---------------------------------------------------------------------------
 // Pieces: (stream, first row, first chunk, rows << 16 | chunks) -- at most
 // kStageChunks 16-pixel chunks of whole rows (or a row segment for very wide
-// rows).  A CTA walks a contiguous range of pieces, so consecutive pieces
-// mostly share a stream.  The row segments of the next piece are bulk-copied
-// into the other stage buffer while the current one is processed; each thread
-// handles one chunk of a piece.
+// rows), so every thread of a CTA handles one chunk of a piece.  A CTA walks a
+// contiguous range of pieces, so consecutive pieces mostly share a stream.
 // ---------------------------------------------------------------------------
-struct PieceGeo {
-    int s, y0, j0, rows, cols, vc;   // vc: chunks per row that lie inside the image
-};
-
-__device__ __forceinline__ PieceGeo piece_geo(const int4 pc, const DevStream &D)
-{
-    PieceGeo g;
-    g.s = pc.x;
-    g.y0 = pc.y;
-    g.j0 = pc.z;
-    g.rows = pc.w >> 16;
-    g.cols = pc.w & 0xffff;
-    g.vc = max(0, min(g.cols, (D.w + kChunkPx - 1) / kChunkPx - g.j0));
-    return g;
-}
-
-// Issue (warp 0) the copies of piece `pc` into stage `dst`: for each of the
-// nsrc arrays and each row, 48 * vc bytes from src[k] + (y0 + r) * pitch[k] + 48 * j0.
-template <int NSRC>
-__device__ __forceinline__ void issue_piece(const PieceGeo &g, const uint8_t *const (&src)[NSRC],
-                                            const long long (&pitch)[NSRC], uint8_t *dst,
-                                            uint64_t *bar, uint64_t pol, int lane)
-{
-    const uint32_t rowb = 48u * (uint32_t)g.vc;
-    const uint32_t sb = 48u * (uint32_t)g.cols;   // stage row stride
-    if (lane == 0) mbar_expect_tx(bar, rowb * (uint32_t)g.rows * NSRC);
-    __syncwarp();
-    if (rowb == 0) return;
-    for (int r = lane; r < g.rows; r += 32) {
-#pragma unroll
-        for (int k = 0; k < NSRC; ++k)
-            bulk_g2s(dst + (size_t)k * kStageChunks * 48 + (size_t)r * sb,
-                     src[k] + (long long)(g.y0 + r) * pitch[k] + 48LL * g.j0, rowb, bar, pol);
-    }
-}
 
 // Sum of luma8 over 16 pixels (48 bytes): each pixel's 3 bytes are gathered
 // into one word with a byte permute, then one 4-way byte dot product with
@@ -136,121 +98,68 @@ __device__ __forceinline__ uint32_t luma_sum_n(const uint32_t (&f)[12], int npx)
     return sum;
 }
 
-__device__ __forceinline__ void lds48(const uint8_t *p, uint32_t (&w)[12])
-{
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
-    const uint4 a = q[0], b = q[1], c = q[2];
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
-}
-
-// ---------------------------------------------------------------------------
-// k_luma: frame luma sums; the last CTA turns them into every stream's gain.
-// ---------------------------------------------------------------------------
-constexpr int kLumaStage = kStageChunks * 48;
-
-__global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
-{
-    __shared__ __align__(128) uint8_t stage[2][kLumaStage];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ unsigned long long red[kThreads / 32];
-    __shared__ bool is_last;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
-    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
-    const uint64_t keep = policy_evict_last();
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int p, int st) {
-        const int4 pc = b.pieces[p];
-        const DevStream &D = b.ds[pc.x];
-        const PieceGeo g = piece_geo(pc, D);
-        const TickIO &io = b.io[pc.x];
-        const uint8_t *const src[1] = {io.frame};
-        const long long pitch[1] = {io.frame_pitch};
-        issue_piece<1>(g, src, pitch, stage[st], &bar[st], keep, lane);
-    };
-    if (wid == 0 && p0 < p1) issue(p0, 0);
-    uint32_t phase = 0, inflight = (p0 < p1) ? 1u : 0u;
-    bool ok = true;
-    unsigned long long acc = 0;
-    for (int p = p0; p < p1 && ok; ++p) {
-        const int st = (p - p0) & 1;
-        if (p + 1 < p1) {
-            if (wid == 0) issue(p + 1, st ^ 1);
-            inflight |= 1u << (st ^ 1);
-        }
-        ok = __syncthreads_and(mbar_wait(&bar[st], (phase >> st) & 1u));
-        if (!ok) break;
-        phase ^= 1u << st;
-        inflight &= ~(1u << st);
-        const int4 pc = b.pieces[p];
-        const DevStream &D = b.ds[pc.x];
-        const PieceGeo g = piece_geo(pc, D);
-        if (tid < g.rows * g.cols) {
-            const int r = tid / g.cols, jj = tid - r * g.cols;
-            const int x0 = (g.j0 + jj) * kChunkPx;
-            if (x0 < D.w) {
-                uint32_t f[12];
-                lds48(stage[st] + r * 48 * g.cols + 48 * jj, f);
-                const int npx = min(kChunkPx, D.w - x0);
-                acc += (npx == kChunkPx) ? luma_sum16(f) : luma_sum_n(f, npx);
-            }
-        }
-        const bool flush = (p + 1 == p1) || (b.pieces[p + 1].x != pc.x);
-        if (flush) {   // CTA-uniform
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if (lane == 0) red[wid] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned long long t = 0;
-                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-                atomicAdd(&D.st->sy, t);
-            }
-            acc = 0;
-        }
-        __syncthreads();   // stage st is free for the copies of piece p + 2
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(b.err, kErrStageWait);
-        // let copies still in flight land before the CTA's shared memory goes away
-        for (int st = 0; st < 2; ++st)
-            if ((inflight >> st) & 1u) (void)mbar_wait(&bar[st], (phase >> st) & 1u);
-    }
-    // the last CTA to finish computes every stream's gain
-    __threadfence();
-    if (tid == 0) is_last = (atomicAdd(&b.done[0], 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int s = tid; s < b.n; s += blockDim.x) {
-        const DevStream &D = b.ds[s];
-        StreamState *st = D.st;
-        unsigned long long sy = *(volatile unsigned long long *)&st->sy;
-        unsigned long long syref = st->syref;
-        unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
-        if (g < D.gain_min) g = D.gain_min;
-        if (g > D.gain_max) g = D.gain_max;
-        st->gain = (uint32_t)g;
-        st->sy = 0;
-    }
-    if (tid == 0) b.done[0] = 0;
-}
-
-// ---------------------------------------------------------------------------
-// k_classify
-// ---------------------------------------------------------------------------
-struct ClassP {
-    uint32_t g;
-    int tol;
-    int A[3][2], B[3][2];
+// Everything a thread needs to address its chunk of a piece.
+struct ChunkRef {
+    int s;                 // stream (index into the batch arrays)
+    int y, j, x0;          // row, chunk within the row, first pixel
+    bool active;           // the thread has a chunk inside the image
+    int npx;               // pixels of the chunk inside the image
+    const uint8_t *frame;  // first byte of the chunk in the frame
+    long long boff;        // byte offset of the chunk in the band arrays
 };
+
+__device__ __forceinline__ ChunkRef chunk_ref(const BatchDev &b, int p, int tid)
+{
+    ChunkRef c;
+    const int4 pc = b.pieces[p];
+    const DevStream &D = b.ds[pc.x];
+    const TickIO &io = b.io[pc.x];
+    const int rows = pc.w >> 16, cols = pc.w & 0xffff;
+    c.s = pc.x;
+    const int r = tid / cols, jj = tid - r * cols;
+    c.y = pc.y + r;
+    c.j = pc.z + jj;
+    c.x0 = c.j * kChunkPx;
+    const int w = D.w;
+    c.active = tid < rows * cols && c.x0 < w;
+    c.npx = min(kChunkPx, w - c.x0);
+    c.frame = io.frame + (long long)c.y * io.frame_pitch + 3LL * c.x0;
+    c.boff = (long long)c.y * D.fpitch + 3LL * c.x0;
+    return c;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident): arrival
+// counter plus generation; the last CTA to arrive opens the next generation.
+// The wait is bounded; false if it gave up.
+__device__ __forceinline__ bool grid_sync(uint32_t *sync, uint32_t nblocks)
+{
+    __shared__ bool ok_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        volatile uint32_t *gen = sync + 1;
+        const uint32_t g = *gen;
+        __threadfence();
+        if (atomicAdd(sync, 1u) == nblocks - 1) {
+            sync[0] = 0u;
+            __threadfence();
+            atomicAdd(sync + 1, 1u);
+        } else {
+            uint32_t it = 0;
+            while (*gen == g) {
+                if (++it > kLoopLimit) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_sh = ok;
+    }
+    __syncthreads();
+    return ok_sh;
+}
 
 // Gain-corrected channel: c' = min(255, (c g + 2^15) >> 16).
 __device__ __forceinline__ int corr(uint32_t c, uint32_t g)
@@ -320,109 +229,127 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
     return (d > 0) & (d >= D.gray_tol) & hue;
 }
 
-// One thread per 16-pixel chunk of a staged piece: the background test on all
-// 16 pixels.  The word of out-of-band pixels is stored as the raw mask; chunks
-// that have any are appended (warp-aggregated) to the skin queue, where k_skin
-// runs the gray and hue tests on just those pixels and clears the ones that
-// fail.  Out-of-band pixels are a few percent (the hand, camera noise), so the
-// skin tests run densely instead of stalling whole warps here.
-constexpr int kClassStage = 3 * kStageChunks * 48;   // frame, lo, hi
-constexpr size_t kClassSmem = 2 * (size_t)kClassStage;
-
-__global__ void __launch_bounds__(kThreads, 3) k_classify(BatchDev b)
+__device__ __forceinline__ uint32_t stream_gain(const DevStream &D)
 {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar[2];
+    const unsigned long long sy = __ldcg(&D.st->sy), syref = D.st->syref;
+    unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
+    if (g < D.gain_min) g = D.gain_min;
+    if (g > D.gain_max) g = D.gain_max;
+    return (uint32_t)g;
+}
+
+// ---------------------------------------------------------------------------
+// k_pixels: the whole per-pixel pass of a tick in one cooperative launch.
+//   A  luma sums (Sec. 2 brightness correction, Sec. 3.2): each CTA sums its
+//      pieces, one atomic per stream segment; frame lines are kept in L2
+//   -- grid barrier: every stream's sum is complete --
+//   B  background test (Sec. 3.1 (i)) on the same pieces in the same order,
+//      so the CTA's frame bytes come back from L2; each CTA derives the gains
+//      of its streams itself; raw mask words; chunks with out-of-band pixels
+//      are queued (warp-aggregated)
+//   -- grid barrier: the queue is complete --
+//   C  gray and hue tests (Sec. 3.1 (ii), (iii)) on the queued chunks only,
+//      clearing the pixels that fail (the AND of the three images)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads, 4) k_pixels(BatchDev b)
+{
+    __shared__ unsigned long long red[kThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
     const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
-    const uint64_t once = policy_evict_first();
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    auto issue = [&](int p, int st) {
-        const int4 pc = b.pieces[p];
-        const DevStream &D = b.ds[pc.x];
-        const PieceGeo g = piece_geo(pc, D);
-        const TickIO &io = b.io[pc.x];
-        const uint8_t *const src[3] = {io.frame, D.lo, D.hi};
-        const long long pitch[3] = {io.frame_pitch, D.fpitch, D.fpitch};
-        issue_piece<3>(g, src, pitch, smem + (size_t)st * kClassStage, &bar[st], once, lane);
-    };
-    if (wid == 0 && p0 < p1) issue(p0, 0);
-    uint32_t phase = 0, inflight = (p0 < p1) ? 1u : 0u;
-    bool ok = true;
-    for (int p = p0; p < p1 && ok; ++p) {
-        const int st = (p - p0) & 1;
-        if (p + 1 < p1) {
-            if (wid == 0) issue(p + 1, st ^ 1);
-            inflight |= 1u << (st ^ 1);
-        }
-        ok = __syncthreads_and(mbar_wait(&bar[st], (phase >> st) & 1u));
-        if (!ok) break;
-        phase ^= 1u << st;
-        inflight &= ~(1u << st);
-        const int4 pc = b.pieces[p];
-        const DevStream &D = b.ds[pc.x];
-        const PieceGeo g = piece_geo(pc, D);
-        const uint32_t gain = D.st->gain;
-        const uint8_t *sf = smem + (size_t)st * kClassStage;
-        uint32_t bits = 0;
-        int r = 0, jj = 0;
-        const bool mine = tid < g.rows * g.cols;
-        if (mine) {
-            r = tid / g.cols;
-            jj = tid - r * g.cols;
-            const int x0 = (g.j0 + jj) * kChunkPx;
-            if (x0 < D.w) {
-                uint32_t f[12], l[12], h[12];
-                const int off = r * 48 * g.cols + 48 * jj;
-                lds48(sf + off, f);
-                lds48(sf + kStageChunks * 48 + off, l);
-                lds48(sf + 2 * kStageChunks * 48 + off, h);
-                bits = outside_bits<kChunkPx - 1>(f, l, h, gain);
-                const int npx = D.w - x0;
-                if (npx < kChunkPx) bits &= (1u << npx) - 1u;
-            }
-        }
-        const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
-        const int y = g.y0 + r, j = g.j0 + jj;
-        if (mine && (jj & 1) == 0) D.raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
-        const unsigned want = __ballot_sync(kFull, bits != 0u);
-        if (want) {
-            uint32_t slot0 = 0;
-            if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
-            slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
-            if (bits) {
-                const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
-                b.skin_list[slot] = make_uint2(((uint32_t)pc.x << 16) | bits, (uint32_t)(y * 2 * D.nwords + j));
-            }
-        }
-        __syncthreads();   // stage st is free for the copies of piece p + 2
-    }
-    if (!ok) {
-        if (tid == 0) atomicOr(b.err, kErrStageWait);
-        // let copies still in flight land before the CTA's shared memory goes away
-        for (int st = 0; st < 2; ++st)
-            if ((inflight >> st) & 1u) (void)mbar_wait(&bar[st], (phase >> st) & 1u);
-    }
-}
 
-// One thread per queued chunk: gray and hue tests on its out-of-band pixels;
-// the pixels that fail are cleared from the raw mask word.
-__global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
-{
+    // ---- A: luma sums ----
+    {
+        const uint64_t keep = policy_evict_last();
+        unsigned long long acc = 0;
+        ChunkRef nxt = (p0 < p1) ? chunk_ref(b, p0, tid) : ChunkRef{};
+        for (int p = p0; p < p1; ++p) {
+            const ChunkRef c = nxt;
+            uint32_t f[12];
+            if (c.active) load48(c.frame, keep, f);
+            if (p + 1 < p1) nxt = chunk_ref(b, p + 1, tid);   // descriptors of the next piece meanwhile
+            if (c.active) acc += (c.npx == kChunkPx) ? luma_sum16(f) : luma_sum_n(f, c.npx);
+            const bool flush = (p + 1 == p1) || (nxt.s != c.s);
+            if (flush) {   // CTA-uniform
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+                if (lane == 0) red[wid] = acc;
+                __syncthreads();
+                if (tid == 0) {
+                    unsigned long long t = 0;
+                    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+                    atomicAdd(&b.ds[c.s].st->sy, t);
+                }
+                __syncthreads();
+                acc = 0;
+            }
+        }
+    }
+    if (!grid_sync(b.gsync, gridDim.x)) {
+        if (tid == 0) atomicOr(b.err, kErrBarrier);
+        return;
+    }
+
+    // ---- B: background test ----
+    {
+        const uint64_t once = policy_evict_first();
+        int gs = -1;
+        uint32_t gain = 0;
+        ChunkRef nxt = (p0 < p1) ? chunk_ref(b, p0, tid) : ChunkRef{};
+        for (int p = p0; p < p1; ++p) {
+            const ChunkRef c = nxt;
+            const DevStream &D = b.ds[c.s];
+            uint32_t f[12], l[12], h[12];
+            if (c.active) {
+                load48(c.frame, once, f);
+                load48(D.lo + c.boff, once, l);
+                load48(D.hi + c.boff, once, h);
+            }
+            if (p + 1 < p1) nxt = chunk_ref(b, p + 1, tid);
+            if (c.s != gs) {
+                gs = c.s;
+                gain = stream_gain(D);
+                if (tid == 0 && (p == 0 || b.pieces[p - 1].x != c.s)) D.st->gain = gain;
+            }
+            uint32_t bits = 0;
+            if (c.active) {
+                bits = outside_bits<kChunkPx - 1>(f, l, h, gain);
+                if (c.npx < kChunkPx) bits &= (1u << c.npx) - 1u;
+            }
+            const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
+            const int4 pc = b.pieces[p];
+            const bool mine = tid < (pc.w >> 16) * (pc.w & 0xffff);
+            if (mine && (tid & 1) == 0) D.raw[(long long)c.y * D.nwords + (c.j >> 1)] = bits | (other << 16);
+            const unsigned want = __ballot_sync(kFull, bits != 0u);
+            if (want) {
+                uint32_t slot0 = 0;
+                if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
+                slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
+                if (bits) {
+                    const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                    b.skin_list[slot] = make_uint2(((uint32_t)c.s << 16) | bits,
+                                                   (uint32_t)(c.y * 2 * D.nwords + c.j));
+                }
+            }
+        }
+    }
+    if (!grid_sync(b.gsync, gridDim.x)) {
+        if (tid == 0) atomicOr(b.err, kErrBarrier);
+        return;
+    }
+    // the sums have been used; the next tick starts from zero
+    if (blockIdx.x == 0)
+        for (int s = tid; s < b.n; s += blockDim.x) b.ds[s].st->sy = 0ull;
+
+    // ---- C: gray and hue tests on the queued chunks ----
     const uint32_t n = *(volatile uint32_t *)b.skin_count;
-    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    for (uint32_t it = blockIdx.x * blockDim.x + tid; it < n; it += gridDim.x * blockDim.x) {
         const uint2 e = b.skin_list[it];
         const int sidx = (int)(e.x >> 16);
         const uint32_t bits = e.x & 0xffffu;
         const int u = (int)e.y;
         const DevStream &D = b.ds[sidx];
-        const TickIO io = b.io[sidx];
+        const TickIO &io = b.io[sidx];
         const uint32_t g = D.st->gain;
         const int cpr = 2 * D.nwords;
         const int y = u / cpr, j = u - y * cpr;
@@ -778,30 +705,38 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
+// Largest co-resident grid of k_pixels on the current device.
+int pixels_max_grid()
 {
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 6));
-    k_luma<<<grid, kThreads, 0, cs>>>(b);
-    return cudaGetLastError();
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pixels, kThreads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    const int g = per_sm * sms;
+    if (dev >= 0 && dev < 64) cache[dev] = g;
+    return g;
 }
 
-cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
+cudaError_t launch_pixels(const BatchDev &b, cudaStream_t cs)
 {
-    static bool attr_set[64] = {};   // the shared-memory opt-in is per device
-    int dev = 0;
-    cudaError_t e0 = cudaGetDevice(&dev);
-    if (e0 != cudaSuccess) return e0;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e0 = cudaFuncSetAttribute(k_classify, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClassSmem);
-        if (e0 != cudaSuccess) return e0;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 3));
-    k_classify<<<grid, kThreads, kClassSmem, cs>>>(b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
-    return cudaGetLastError();
+    const int cap = pixels_max_grid();
+    if (cap <= 0) return cudaErrorInvalidConfiguration;
+    const int grid = std::max(1, std::min(b.npieces, cap));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = cs;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pixels, b);
 }
 
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
