@@ -335,7 +335,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl, o_gs;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl;
     };
     std::vector<Tables> T(ng);
     Arena a;
@@ -380,9 +380,6 @@ int plan_build(hmi_batch *b, int ng)
         t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
         t.o_ccn = a.take(sizeof(uint32_t));
         t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
-        t.o_skn = a.take(sizeof(uint32_t));
-        t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
-        t.o_gs = a.take(sizeof(uint32_t) * 2);
     }
     if (cudaMalloc(&b->plan, a.off) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -426,9 +423,6 @@ int plan_build(hmi_batch *b, int ng)
         bd.err = b->d_err;
         bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
         bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
-        bd.skin_count = reinterpret_cast<uint32_t *>(A + t.o_skn);
-        bd.skin_list = reinterpret_cast<uint2 *>(A + t.o_skl);
-        bd.gsync = reinterpret_cast<uint32_t *>(A + t.o_gs);
     }
     if (!ok) {
         (void)cudaGetLastError();
@@ -504,9 +498,9 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
     return b;
 }
 
-// Kernels of one tick with the slot's pointer table: the per-pixel pass
-// (cooperative), morphology + block components, and the per-stream finish.
-// With one group, event records (or event nodes) bracket the per-pixel pass.
+// Kernels of one tick with the slot's pointer table: luma, classification,
+// morphology + block components, and the per-stream finish.  With one group,
+// event records (or event nodes) bracket the classification kernel.
 cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1,
                          bool capture)
 {
@@ -519,17 +513,18 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     if (ng == 1) {
         BatchDev bd = b->groups[0].bd;
         bd.io = dio;
+        if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
         if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
             return e;
-        if ((e = launch_pixels(bd, cs)) != cudaSuccess) return e;
+        if ((e = launch_classify(bd, cs, b->num_sms)) != cudaSuccess) return e;
         if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
             return e;
         if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
         return launch_finish(bd, cs);
     }
-    // groups: the per-pixel (cooperative) passes run one after another, each
-    // group's tail (morphology, components, finish) overlaps the next group's
-    // per-pixel pass
+    // groups: each group's luma pass starts after the previous group's, so the
+    // bandwidth-bound passes of one group overlap the tail (morphology,
+    // components, finish) of the previous one
     if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
     for (int g = 0; g < ng; ++g) {
         Group &G = b->groups[g];
@@ -537,8 +532,9 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
         bd.io = dio + G.off;
         if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
         if (g > 0 && (e = cudaStreamWaitEvent(G.cs, b->groups[g - 1].ev_luma, 0)) != cudaSuccess) return e;
-        if ((e = launch_pixels(bd, G.cs)) != cudaSuccess) return e;
+        if ((e = launch_luma(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_luma, G.cs)) != cudaSuccess) return e;
+        if ((e = launch_classify(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = launch_morph_cc(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = launch_finish(bd, G.cs)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;

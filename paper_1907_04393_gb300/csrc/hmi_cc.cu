@@ -302,10 +302,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         S.nrec = 0;
         S.best = 0;
         S.overflow = false;
-        if (blockIdx.x == 0) {                   // the skin and block queues are consumed
-            *b.cc_count = 0u;
-            *b.skin_count = 0u;
-        }
+        if (blockIdx.x == 0) *b.cc_count = 0u;   // k_block_cc has consumed the block list
     }
     for (int i = tid; i < D.click_window; i += blockDim.x) S.hist[i] = D.hist[i];
     __syncthreads();

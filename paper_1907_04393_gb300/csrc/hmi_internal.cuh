@@ -30,7 +30,7 @@ constexpr uint32_t kErrUnionLoop = 1u;
 constexpr uint32_t kErrFindLoop = 2u;
 constexpr uint32_t kErrSlots = 4u;
 constexpr uint32_t kErrRoot = 8u;
-constexpr uint32_t kErrBarrier = 16u;
+constexpr uint32_t kErrStageWait = 16u;
 
 // One 8-connected component of a 32x32 block, later the accumulator of its
 // whole component when it is the root.  64 bytes.
@@ -114,9 +114,6 @@ struct BatchDev {
     uint32_t *err;                            // batch error word: OR of the streams' flags
     uint32_t *cc_count;                       // non-empty blocks listed this tick
     uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
-    uint32_t *skin_count;                     // chunks queued for the skin tests this tick
-    uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
-    uint32_t *gsync;                          // grid barrier of k_pixels: count, generation
 };
 
 // Threads per CTA of every kernel of a tick.
@@ -125,7 +122,8 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
-cudaError_t launch_pixels(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
