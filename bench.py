@@ -37,7 +37,7 @@ WORKLOAD = ("64-stream batch: 32x320x240 + 16x640x480 + 12x1280x720 + 4x1920x108
 # algorithmic bytes per pixel of the classification (background test) kernel:
 # frame 3 B + band lo/hi 6 B read, 1 bit written
 CLASSIFY_BYTES_PER_PX = 3 + 6 + 1 / 8
-KERNELS_PER_TICK = 5
+KERNELS_PER_TICK = 6
 PROFILE_FILE = os.path.join(ROOT, "profiles", "k_classify_64stream.txt")
 
 

@@ -47,6 +47,7 @@ int cuda_fail(cudaError_t e)
     } while (0)
 
 constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
+constexpr int kPieceChunks = 512;   // 16-px chunks per CTA piece (8192 px)
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -335,7 +336,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl;
     };
     std::vector<Tables> T(ng);
     Arena a;
@@ -359,18 +360,8 @@ int plan_build(hmi_batch *b, int ng)
             const int halo = 2 * (st->p.open_iters + st->p.close_iters);
             t.max_halo = std::max(t.max_halo, halo);
             t.uniform_halo = (t.uniform_halo == -2 || t.uniform_halo == halo) ? halo : -1;
-            // staged pieces of at most kStageChunks chunks: whole rows (up to
-            // 32 per piece), or row segments when a row alone is larger
-            const int cpr = 2 * L.nwords;
-            if (cpr <= kStageChunks) {
-                const int rows = std::max(1, std::min(32, kStageChunks / cpr));
-                for (int y0 = 0; y0 < L.h; y0 += rows)
-                    t.pieces.push_back(make_int4(k, y0, 0, (std::min(rows, L.h - y0) << 16) | cpr));
-            } else {
-                for (int y0 = 0; y0 < L.h; ++y0)
-                    for (int j0 = 0; j0 < cpr; j0 += kStageChunks)
-                        t.pieces.push_back(make_int4(k, y0, j0, (1 << 16) | std::min(kStageChunks, cpr - j0)));
-            }
+            for (int c = 0; c < chunks; c += kPieceChunks)
+                t.pieces.push_back(make_int4(k, c, std::min(chunks, c + kPieceChunks), 0));
         }
         t.o_c = a.take(sizeof(unsigned long long) * (m + 1));
         t.o_t = a.take(sizeof(uint32_t) * (m + 1));
@@ -380,6 +371,8 @@ int plan_build(hmi_batch *b, int ng)
         t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
         t.o_ccn = a.take(sizeof(uint32_t));
         t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
+        t.o_skn = a.take(sizeof(uint32_t));
+        t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
     }
     if (cudaMalloc(&b->plan, a.off) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -423,6 +416,8 @@ int plan_build(hmi_batch *b, int ng)
         bd.err = b->d_err;
         bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
         bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
+        bd.skin_count = reinterpret_cast<uint32_t *>(A + t.o_skn);
+        bd.skin_list = reinterpret_cast<uint2 *>(A + t.o_skl);
     }
     if (!ok) {
         (void)cudaGetLastError();
@@ -498,9 +493,11 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
     return b;
 }
 
-// Kernels of one tick with the slot's pointer table: luma, classification,
-// morphology + block components, and the per-stream finish.  With one group,
-// event records (or event nodes) bracket the classification kernel.
+// Kernels of one tick with the slot's pointer table.  Each group runs its
+// chain (luma, classify, morphology, block components, finish) on its own
+// branch; group g starts its luma after group g-1's luma, so the HBM-bound
+// passes of later groups overlap the latency-bound tail of earlier ones.
+// With one group, event records (or event nodes) bracket the classify kernel.
 cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1,
                          bool capture)
 {
@@ -522,9 +519,6 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
         if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
         return launch_finish(bd, cs);
     }
-    // groups: each group's luma pass starts after the previous group's, so the
-    // bandwidth-bound passes of one group overlap the tail (morphology,
-    // components, finish) of the previous one
     if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
     for (int g = 0; g < ng; ++g) {
         Group &G = b->groups[g];
@@ -734,7 +728,7 @@ int batch_set_groups(hmi_batch *b, int ng)
     return plan_build(b, ng);
 }
 
-int default_groups(int n) { return std::min(2, n); }  // measured best on the 64-stream mix
+int default_groups(int n) { return std::min(2, n); }
 
 }  // namespace
 

@@ -302,7 +302,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         S.nrec = 0;
         S.best = 0;
         S.overflow = false;
-        if (blockIdx.x == 0) *b.cc_count = 0u;   // k_block_cc has consumed the block list
+        if (blockIdx.x == 0) {                   // k_skin and k_block_cc are done with their lists
+            *b.cc_count = 0u;
+            *b.skin_count = 0u;
+        }
     }
     for (int i = tid; i < D.click_window; i += blockDim.x) S.hist[i] = D.hist[i];
     __syncthreads();

@@ -14,7 +14,6 @@
 
 #include "hmi_ccfill.cuh"
 #include "hmi_internal.cuh"
-#include "hmi_stage.cuh"
 
 namespace hmi {
 
@@ -64,13 +63,6 @@ __device__ __forceinline__ uint32_t luma8(uint32_t r, uint32_t g, uint32_t b)
     return (77u * r + 150u * g + 29u * b + 128u) >> 8;
 }
 
-// ---------------------------------------------------------------------------
-// Pieces: (stream, first row, first chunk, rows << 16 | chunks) -- at most
-// kStageChunks 16-pixel chunks of whole rows (or a row segment for very wide
-// rows), so every thread of a CTA handles one chunk of a piece.  A CTA walks a
-// contiguous range of pieces, so consecutive pieces mostly share a stream.
-// ---------------------------------------------------------------------------
-
 // Sum of luma8 over 16 pixels (48 bytes): each pixel's 3 bytes are gathered
 // into one word with a byte permute, then one 4-way byte dot product with
 // (77, 150, 29, 0) plus 128, shifted per pixel.
@@ -81,6 +73,7 @@ __device__ __forceinline__ uint32_t luma_sum16(const uint32_t (&f)[12])
 #pragma unroll
     for (int k = 0; k < kChunkPx; ++k) {
         const int b = 3 * k, wi = b >> 2, o = b & 3;
+        // bytes b, b+1, b+2 of the 48 (they span at most two words)
         const uint32_t lo = f[wi], hi = (wi + 1 < 12) ? f[wi + 1] : 0u;
         const uint32_t px = __byte_perm(lo, hi, (uint32_t)(o | ((o + 1) << 4) | ((o + 2) << 8) | (0x7 << 12)) & 0x7777u);
         sum += __dp4a(px & 0x00ffffffu, kW, 128u) >> 8;
@@ -99,56 +92,87 @@ __device__ __forceinline__ uint32_t luma_sum_n(const uint32_t (&f)[12], int npx)
     return sum;
 }
 
-struct PieceGeo {
-    int s, y0, j0, rows, cols, vc;   // vc: chunks per row that lie inside the image
-};
-
-__device__ __forceinline__ PieceGeo piece_geo(const int4 pc, const DevStream &D)
+// ---------------------------------------------------------------------------
+// k_luma: one CTA per piece (a contiguous chunk range of one stream).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
 {
-    PieceGeo g;
-    g.s = pc.x;
-    g.y0 = pc.y;
-    g.j0 = pc.z;
-    g.rows = pc.w >> 16;
-    g.cols = pc.w & 0xffff;
-    g.vc = max(0, min(g.cols, (D.w + kChunkPx - 1) / kChunkPx - g.j0));
-    return g;
-}
-
-constexpr int kStageBytes = kStageChunks * 48;   // one array of a stage
-
-// Producer warp: the row segments of piece p (frame, and lo / hi when NSRC is
-// 3) into a stage buffer, completing on `full`.
-template <int NSRC>
-__device__ __forceinline__ void produce_piece(const BatchDev &b, int p, uint8_t *stage, uint64_t *full,
-                                              uint64_t pol, int lane)
-{
-    const int4 pc = b.pieces[p];
-    const DevStream &D = b.ds[pc.x];
-    const TickIO &io = b.io[pc.x];
-    const PieceGeo g = piece_geo(pc, D);
-    const uint8_t *src[3] = {io.frame, D.lo, D.hi};
-    const long long pitch[3] = {io.frame_pitch, D.fpitch, D.fpitch};
-    const uint32_t rowb = 48u * (uint32_t)g.vc, sb = 48u * (uint32_t)g.cols;
-    if (lane == 0) mbar_expect_tx(full, rowb * (uint32_t)g.rows * NSRC);
-    __syncwarp();
-    if (rowb == 0) return;
-    for (int r = lane; r < g.rows; r += 32) {
+    __shared__ unsigned long long red[kThreads / 32];
+    __shared__ bool is_last;
+    const int tid = threadIdx.x;
+    const uint64_t keep = policy_evict_last();
+    // a contiguous range of pieces per CTA: consecutive pieces mostly share a
+    // stream, so partial sums are flushed only when the stream changes
+    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
+    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
+    unsigned long long acc = 0;
+    for (int pc = p0; pc < p1; ++pc) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        const int w = D.w, cpr = 2 * D.nwords;
+        // two chunks per thread per round, both loads in flight before the sums
+        for (int u = piece.y + tid; u < piece.z; u += 2 * blockDim.x) {
+            uint32_t f[2][12];
+            int npx[2];
 #pragma unroll
-        for (int k = 0; k < NSRC; ++k)
-            bulk_g2s(stage + k * kStageBytes + r * sb, src[k] + (long long)(g.y0 + r) * pitch[k] + 48LL * g.j0,
-                     rowb, full, pol);
+            for (int q = 0; q < 2; ++q) {
+                const int uu = u + q * (int)blockDim.x;
+                npx[q] = 0;
+                if (uu < piece.z) {
+                    const int y = uu / cpr, x0 = (uu - y * cpr) * kChunkPx;
+                    if (x0 < w) {
+                        npx[q] = min(kChunkPx, w - x0);
+                        load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
+        }
+        const bool flush = (pc + 1 == p1) || (b.pieces[pc + 1].x != piece.x);
+        if (flush) {   // CTA-uniform
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long t = 0;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+                atomicAdd(&D.st->sy, t);
+            }
+            __syncthreads();
+            acc = 0;
+        }
     }
+    // the last CTA to finish computes every stream's gain
+    __threadfence();
+    if (tid == 0) is_last = (atomicAdd(&b.done[0], 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int s = tid; s < b.n; s += blockDim.x) {
+        const DevStream &D = b.ds[s];
+        StreamState *st = D.st;
+        unsigned long long sy = *(volatile unsigned long long *)&st->sy;
+        unsigned long long syref = st->syref;
+        unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
+        if (g < D.gain_min) g = D.gain_min;
+        if (g > D.gain_max) g = D.gain_max;
+        st->gain = (uint32_t)g;
+        st->sy = 0;
+    }
+    if (tid == 0) b.done[0] = 0;
 }
 
-__device__ __forceinline__ void lds48(const uint8_t *p, uint32_t (&w)[12])
-{
-    const uint4 *q = reinterpret_cast<const uint4 *>(p);
-    const uint4 a = q[0], c = q[1], d = q[2];
-    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-    w[4] = c.x; w[5] = c.y; w[6] = c.z; w[7] = c.w;
-    w[8] = d.x; w[9] = d.y; w[10] = d.z; w[11] = d.w;
-}
+// ---------------------------------------------------------------------------
+// k_classify
+// ---------------------------------------------------------------------------
+struct ClassP {
+    uint32_t g;
+    int tol;
+    int A[3][2], B[3][2];
+};
 
 // Gain-corrected channel: c' = min(255, (c g + 2^15) >> 16).
 __device__ __forceinline__ int corr(uint32_t c, uint32_t g)
@@ -218,206 +242,97 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
     return (d > 0) & (d >= D.gray_tol) & hue;
 }
 
-// ---------------------------------------------------------------------------
-// k_luma: frame luma sums (Sec. 2 brightness correction, Sec. 3.2); the last
-// CTA to finish turns them into every stream's gain.  Warp-specialised: the
-// producer warp keeps kLumaStages pieces in flight, the consumer warps sum.
-// ---------------------------------------------------------------------------
-constexpr int kLumaStages = 4;
-constexpr int kWsThreads = 32 * (kConsumerWarps + 1);
-constexpr size_t kLumaSmem = (size_t)kLumaStages * kStageBytes;
-
-__global__ void __launch_bounds__(kWsThreads) k_luma(BatchDev b)
+// One thread per 16-pixel chunk: the background test on all 16 pixels.  The
+// word of out-of-band pixels is stored as the raw mask; chunks that have any
+// are appended (warp-aggregated) to the skin queue, where k_skin runs the gray
+// and hue tests on just those pixels and clears the ones that fail.  Out-of-
+// band pixels are a few percent (the hand, camera noise), so the skin tests
+// run densely instead of stalling whole warps here.
+__global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
 {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kLumaStages], empty[kLumaStages];
-    __shared__ bool is_last;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
-    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
-    if (tid == 0) {
-        for (int s = 0; s < kLumaStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (wid == kConsumerWarps) {
-        const uint64_t keep = policy_evict_last();
-        for (int p = p0, i = 0; p < p1; ++p, ++i) {
-            const int s = i % kLumaStages;
-            if (!mbar_wait(&empty[s], ((i / kLumaStages) & 1) ^ 1)) {
-                if (lane == 0) atomicOr(b.err, kErrStageWait);
-                break;
-            }
-            produce_piece<1>(b, p, smem + (size_t)s * kStageBytes, &full[s], keep, lane);
-        }
-    } else {
-        unsigned long long acc = 0;
-        int cur = -1;
-        for (int p = p0, i = 0; p < p1; ++p, ++i) {
-            const int s = i % kLumaStages;
-            if (!mbar_wait(&full[s], (i / kLumaStages) & 1)) {
-                if (lane == 0) atomicOr(b.err, kErrStageWait);
-                break;
-            }
-            const int4 pc = b.pieces[p];
-            const DevStream &D = b.ds[pc.x];
-            if (pc.x != cur) {
-                if (cur >= 0) {
-                    const unsigned long long t = __reduce_add_sync(kFull, (uint32_t)acc) +
-                                                 ((unsigned long long)__reduce_add_sync(kFull, (uint32_t)(acc >> 32)) << 32);
-                    if (lane == 0 && t) atomicAdd(&b.ds[cur].st->sy, t);
-                }
-                acc = 0;
-                cur = pc.x;
-            }
-            const PieceGeo g = piece_geo(pc, D);
-            if (tid < g.rows * g.cols) {
-                const int r = tid / g.cols, jj = tid - r * g.cols;
-                const int x0 = (g.j0 + jj) * kChunkPx;
-                if (x0 < D.w) {
-                    uint32_t f[12];
-                    lds48(smem + (size_t)s * kStageBytes + r * 48 * g.cols + 48 * jj, f);
-                    const int npx = min(kChunkPx, D.w - x0);
-                    acc += (npx == kChunkPx) ? luma_sum16(f) : luma_sum_n(f, npx);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint64_t once = policy_evict_first();
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        const uint32_t g = D.st->gain;
+        const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
+        const uint8_t *lo = D.lo, *hi = D.hi;
+        uint32_t *raw = D.raw;
+        // warp-uniform loop so that chunk pairs can combine with a shuffle
+        for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
+            const int u = base + lane;
+            uint32_t bits = 0;
+            int y = 0, j = 0;
+            if (u < piece.z) {
+                y = u / cpr;
+                j = u - y * cpr;
+                const int x0 = j * kChunkPx;
+                if (x0 < w) {
+                    uint32_t f[12], l[12], h[12];
+                    load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
+                    load48(lo + (long long)y * fpitch + 3 * x0, once, l);
+                    load48(hi + (long long)y * fpitch + 3 * x0, once, h);
+                    bits = outside_bits<kChunkPx - 1>(f, l, h, g);
+                    const int npx = w - x0;
+                    if (npx < kChunkPx) bits &= (1u << npx) - 1u;
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-        }
-        if (cur >= 0) {
-            const unsigned long long t = __reduce_add_sync(kFull, (uint32_t)acc) +
-                                         ((unsigned long long)__reduce_add_sync(kFull, (uint32_t)(acc >> 32)) << 32);
-            if (lane == 0 && t) atomicAdd(&b.ds[cur].st->sy, t);
+            const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
+            if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+            const unsigned want = __ballot_sync(kFull, bits != 0u);
+            if (want) {
+                uint32_t slot0 = 0;
+                if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
+                slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
+                if (bits) {
+                    const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
+                    b.skin_list[slot] = make_uint2(((uint32_t)piece.x << 16) | bits, (uint32_t)u);
+                }
+            }
         }
     }
-    // the last CTA to finish computes every stream's gain
-    __syncthreads();
-    __threadfence();
-    if (tid == 0) is_last = (atomicAdd(&b.done[0], 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int s = tid; s < b.n; s += blockDim.x) {
-        const DevStream &D = b.ds[s];
-        StreamState *st = D.st;
-        const unsigned long long sy = *(volatile unsigned long long *)&st->sy;
-        const unsigned long long syref = st->syref;
-        unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
-        if (g < D.gain_min) g = D.gain_min;
-        if (g > D.gain_max) g = D.gain_max;
-        st->gain = (uint32_t)g;
-        st->sy = 0;
-    }
-    if (tid == 0) b.done[0] = 0;
 }
 
-// ---------------------------------------------------------------------------
-// k_classify: background, gray and hue tests and their AND (Sec. 3.1 (i)-(iii)
-// and the merging step).  Warp-specialised like k_luma, with the frame and
-// the band lo / hi staged.  Each consumer thread runs the background test on
-// its 16-pixel chunk; the pixels outside their band (the hand, camera noise:
-// a few percent) are then listed per warp and given the gray and hue tests
-// densely, one pixel per lane, reading their bytes from the stage buffer.
-// ---------------------------------------------------------------------------
-constexpr int kClassStages = 2;
-constexpr size_t kClassStageBytes = 3 * (size_t)kStageBytes;
-struct ClassAux {
-    uint16_t list[kConsumerWarps][32 * kChunkPx];   // (lane << 4) | pixel
-    uint32_t fail[kConsumerWarps][32];
-};
-constexpr size_t kClassSmem = kClassStages * kClassStageBytes + sizeof(ClassAux);
-
-__global__ void __launch_bounds__(kWsThreads) k_classify(BatchDev b)
+// One thread per queued chunk: gray and hue tests on its out-of-band pixels;
+// the pixels that fail are cleared from the raw mask word.
+__global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
 {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t full[kClassStages], empty[kClassStages];
-    ClassAux &X = *reinterpret_cast<ClassAux *>(smem + kClassStages * kClassStageBytes);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
-    const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
-    if (tid == 0) {
-        for (int s = 0; s < kClassStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (wid == kConsumerWarps) {
-        const uint64_t once = policy_evict_first();
-        for (int p = p0, i = 0; p < p1; ++p, ++i) {
-            const int s = i % kClassStages;
-            if (!mbar_wait(&empty[s], ((i / kClassStages) & 1) ^ 1)) {
-                if (lane == 0) atomicOr(b.err, kErrStageWait);
-                break;
-            }
-            produce_piece<3>(b, p, smem + (size_t)s * kClassStageBytes, &full[s], once, lane);
-        }
-        return;
-    }
-    int cur = -1;
-    uint32_t gain = 0;
-    for (int p = p0, i = 0; p < p1; ++p, ++i) {
-        const int s = i % kClassStages;
-        if (!mbar_wait(&full[s], (i / kClassStages) & 1)) {
-            if (lane == 0) atomicOr(b.err, kErrStageWait);
-            break;
-        }
-        const uint8_t *sf = smem + (size_t)s * kClassStageBytes;
-        const int4 pc = b.pieces[p];
-        const DevStream &D = b.ds[pc.x];
-        if (pc.x != cur) {
-            cur = pc.x;
-            gain = D.st->gain;
-        }
-        const PieceGeo g = piece_geo(pc, D);
-        const bool mine = tid < g.rows * g.cols;
-        const int r = mine ? tid / g.cols : 0, jj = mine ? tid - r * g.cols : 0;
-        const int x0 = (g.j0 + jj) * kChunkPx;
-        const int off = r * 48 * g.cols + 48 * jj;
-        uint32_t bits = 0;
-        if (mine && x0 < D.w) {
-            uint32_t f[12], l[12], h[12];
-            lds48(sf + off, f);
-            lds48(sf + kStageBytes + off, l);
-            lds48(sf + 2 * kStageBytes + off, h);
-            bits = outside_bits<kChunkPx - 1>(f, l, h, gain);
-            const int npx = D.w - x0;
-            if (npx < kChunkPx) bits &= (1u << npx) - 1u;
-        }
-        // gray and hue tests on the warp's out-of-band pixels, densely
-        const uint32_t cnt = (uint32_t)__popc(bits);
-        uint32_t incl = cnt;
+    const uint32_t n = *(volatile uint32_t *)b.skin_count;
+    for (uint32_t it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        const uint2 e = b.skin_list[it];
+        const int sidx = (int)(e.x >> 16);
+        const uint32_t bits = e.x & 0xffffu;
+        const int u = (int)e.y;
+        const DevStream &D = b.ds[sidx];
+        const TickIO io = b.io[sidx];
+        const uint32_t g = D.st->gain;
+        const int cpr = 2 * D.nwords;
+        const int y = u / cpr, j = u - y * cpr;
+        const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * j * kChunkPx;
+        uint32_t fail = 0;
+        if (__popc(bits) > 4) {
+            uint32_t f[12];
+            const uint4 *q = reinterpret_cast<const uint4 *>(row);
+            const uint4 a = __ldg(q), c = __ldg(q + 1), d = __ldg(q + 2);
+            f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+            f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+            f[8] = d.x; f[9] = d.y; f[10] = d.z; f[11] = d.w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(kFull, incl, 31);
-        if (total) {
-            uint32_t pos = incl - cnt;
-            for (uint32_t t = bits; t; t &= t - 1u) X.list[wid][pos++] = (uint16_t)((lane << 4) | (__ffs(t) - 1));
-            X.fail[wid][lane] = 0u;
-            __syncwarp();
-            for (uint32_t e = lane; e < total; e += 32) {
-                const uint32_t v = X.list[wid][e];
-                const int owner = (int)(v >> 4), k = (int)(v & 15u);
-                const int c = wid * 32 + owner;
-                const int ro = c / g.cols, jo = c - ro * g.cols;
-                const uint8_t *px = sf + ro * 48 * g.cols + 48 * jo + 3 * k;
-                if (!skin_rgb(px[0], px[1], px[2], D, gain)) atomicOr(&X.fail[wid][owner], 1u << k);
+            for (int k = 0; k < kChunkPx; ++k) {
+                if (!((bits >> k) & 1u)) continue;
+                if (!skin_rgb(byte_of(f, 3 * k), byte_of(f, 3 * k + 1), byte_of(f, 3 * k + 2), D, g))
+                    fail |= 1u << k;
             }
-            __syncwarp();
-            bits &= ~X.fail[wid][lane];
+        } else {
+            for (uint32_t todo = bits; todo; todo &= todo - 1u) {
+                const int k = __ffs(todo) - 1;
+                const uint8_t *px = row + 3 * k;
+                if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) fail |= 1u << k;
+            }
         }
-        const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
-        if (mine && (jj & 1) == 0)
-            D.raw[(long long)(g.y0 + r) * D.nwords + ((g.j0 + jj) >> 1)] = bits | (other << 16);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
+        if (fail) atomicAnd(D.raw + (long long)y * D.nwords + (j >> 1), ~(fail << (16 * (j & 1))));
     }
 }
 
@@ -747,35 +662,24 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <typename K>
-static cudaError_t set_smem(K kernel, size_t bytes, bool (&done)[64])
+static int grid_for_pieces(int npieces)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
-    return e;
+    return npieces > 0 ? npieces : 1;
 }
 
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    static bool done[64] = {};   // the shared-memory opt-in is per device
-    cudaError_t e = set_smem(k_luma, kLumaSmem, done);
-    if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 4));
-    k_luma<<<grid, kWsThreads, kLumaSmem, cs>>>(b);
+    const int grid = std::max(1, std::min(b.npieces, num_sms * 8));
+    k_luma<<<grid, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    static bool done[64] = {};
-    cudaError_t e = set_smem(k_classify, kClassSmem, done);
+    k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 2));
-    k_classify<<<grid, kWsThreads, kClassSmem, cs>>>(b);
+    k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,6 @@ namespace hmi {
 // Geometry constants
 // ---------------------------------------------------------------------------
 constexpr int kChunkPx = 16;       // pixels per classification unit (48 frame bytes)
-constexpr int kStageChunks = 256;  // chunks per staged piece (one per thread)
 constexpr int kWordPx = 32;        // pixels per mask bit word
 constexpr int kBlock = 32;         // connected-component block: 32 rows x 32 px
 constexpr int kSlots = 256;        // max 8-connected components in a 32x32 block
@@ -30,7 +29,6 @@ constexpr uint32_t kErrUnionLoop = 1u;
 constexpr uint32_t kErrFindLoop = 2u;
 constexpr uint32_t kErrSlots = 4u;
 constexpr uint32_t kErrRoot = 8u;
-constexpr uint32_t kErrStageWait = 16u;
 
 // One 8-connected component of a 32x32 block, later the accumulator of its
 // whole component when it is the root.  64 bytes.
@@ -109,11 +107,13 @@ struct BatchDev {
     int uniform_halo;                         // the common 2 * (open + close), or -1
     const uint32_t *block_prefix;             // n + 1
     uint32_t *done;                           // last-block counters [4]
-    const int4 *pieces;                       // (stream, row, chunk, rows << 16 | chunks)
+    const int4 *pieces;                       // (stream, chunk begin, chunk end, 0)
     int npieces;                              // pieces of the per-pixel kernels
     uint32_t *err;                            // batch error word: OR of the streams' flags
     uint32_t *cc_count;                       // non-empty blocks listed this tick
     uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
+    uint32_t *skin_count;                     // chunks queued for the skin tests this tick
+    uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
 };
 
 // Threads per CTA of every kernel of a tick.
