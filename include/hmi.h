@@ -202,6 +202,52 @@ HMI_API int hmi_get_last_gain(const hmi_stream *s, uint32_t *gain_q16);
  * (the figure that admission control budgets).  0 on invalid arguments. */
 HMI_API size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p);
 
+/* ---------------------------------------------------------------------------
+ * Serving: many camera streams that come and go, frames arriving on their own
+ * clocks.  A server admits a stream only while the device memory of all its
+ * streams stays within a budget, keeps every admitted stream's state resident,
+ * and runs a dispatcher thread that continuously batches: whenever frames are
+ * pending it runs one tick over all admitted streams, taking at most one
+ * frame (the oldest) per stream, so each stream's frames stay in order.
+ * Results carry the submit and completion times (hmi_server_now_ns clock).
+ * All calls are thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct hmi_server hmi_server;
+
+typedef struct {
+    int32_t stream_id;   /* as returned by hmi_server_admit */
+    int32_t status;      /* HMI_OK or the tick's error status */
+    uint64_t tag;        /* the caller's tag from hmi_server_submit */
+    uint64_t submit_ns;  /* when hmi_server_submit accepted the frame */
+    uint64_t done_ns;    /* when the result became available */
+    hmi_pointer pointer; /* the frame's pointer (Mouse module output) */
+} hmi_server_result;
+
+/* device_budget_bytes: cap on the sum of hmi_stream_device_bytes of admitted
+ * streams; max_queue: frames a stream may have pending (1..64). */
+HMI_API hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue);
+HMI_API void hmi_server_destroy(hmi_server *srv);
+/* Create a stream and learn its background from n host frames.
+ * HMI_ERR_NO_MEMORY when it would exceed the budget (admission refused). */
+HMI_API int hmi_server_admit(hmi_server *srv, int w, int h, const hmi_params *p,
+                             const uint8_t *learn_frames, int n, int *stream_id);
+/* Retire a stream once its pending frames have been processed. */
+HMI_API int hmi_server_release(hmi_server *srv, int stream_id);
+/* Queue one host frame (h*w*3 bytes, copied before return).  HMI_ERR_NO_MEMORY
+ * when the stream already has max_queue frames pending. */
+HMI_API int hmi_server_submit(hmi_server *srv, int stream_id, const uint8_t *frame, uint64_t tag);
+/* Same, without the copy: the server reads `frame` when the stream's tick
+ * runs, so the caller keeps it valid and unchanged until the frame's result
+ * has been returned by hmi_server_poll (pinned host memory is fastest). */
+HMI_API int hmi_server_submit_ref(hmi_server *srv, int stream_id, const uint8_t *frame, uint64_t tag);
+/* Up to max_results finished frames (waiting at most wait_us for the first);
+ * returns how many were written, or a negative status. */
+HMI_API int hmi_server_poll(hmi_server *srv, hmi_server_result *out, int max_results, int wait_us);
+/* Device bytes admitted, ticks run and frames processed so far. */
+HMI_API int hmi_server_stats(hmi_server *srv, size_t *bytes_admitted, uint64_t *ticks,
+                             uint64_t *frames);
+HMI_API uint64_t hmi_server_now_ns(void);
+
 /* Brightness gain of one frame without any device allocation.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate
  * device memory, such as a real-time loop in which a cudaMalloc could stall the

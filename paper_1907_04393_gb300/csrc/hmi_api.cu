@@ -10,6 +10,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -170,6 +175,7 @@ struct hmi_stream {
     hmi_pointer *d_ptr = nullptr;
     int learned = 0;
     int n_learn = 0;
+    bool used = false;           // has been given frames (learning must wait for its work)
     cudaStream_t cs = nullptr;
     hmi_batch *self = nullptr;   // one-stream plan used by hmi_process_frame
 };
@@ -587,6 +593,7 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
     TickIO *io = b->h_io + (size_t)slot * b->n;
     for (int i = 0; i < b->n; ++i) {
         hmi_stream *s = b->s[i];
+        s->used = true;
         TickIO &t = io[b->pos[i]];
         const uint8_t *f = frames[i];
         if (!f) return fail(HMI_ERR_INVALID_ARG);
@@ -730,6 +737,382 @@ int batch_set_groups(hmi_batch *b, int ng)
 
 int default_groups(int n) { return std::min(2, n); }
 
+
+// ===========================================================================
+// Server: admission by device-memory budget, resident streams, continuous
+// batching by a dispatcher thread (one tick over all admitted streams per
+// round, streams without a pending frame marked inactive by a null frame).
+// ===========================================================================
+struct SrvFrame {
+    const uint8_t *host = nullptr;   // pinned copy, or the caller's buffer
+    size_t bytes = 0;
+    uint64_t tag = 0, submit_ns = 0;
+    bool owned = false;              // host is a pooled copy to give back
+};
+
+struct SrvStream {
+    hmi_stream *s = nullptr;
+    size_t bytes = 0;
+    bool releasing = false;
+    std::deque<SrvFrame> q;
+};
+
+uint64_t now_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+struct hmi_server {
+    int dev = 0;
+    size_t budget = 0, used = 0;
+    int max_queue = 8;
+    std::mutex mu;
+    std::condition_variable work_cv, done_cv;
+    std::map<int, SrvStream> streams;
+    int next_id = 1;
+    std::deque<hmi_server_result> done;
+    std::map<size_t, std::vector<uint8_t *>> pool;   // free pinned buffers by size
+    bool stop = false, dirty = false;
+    std::thread worker;
+    // dispatcher-only state
+    hmi_batch *plan = nullptr;
+    std::vector<int> plan_ids;
+    cudaStream_t cs = nullptr;
+    hmi_pointer *h_ptrs = nullptr, *d_ptrs = nullptr;
+    int ptr_cap = 0;
+    uint64_t ticks = 0, frames = 0;
+};
+
+namespace {
+
+uint8_t *pool_get(hmi_server *v, size_t bytes)
+{
+    auto &fl = v->pool[bytes];
+    if (!fl.empty()) {
+        uint8_t *p = fl.back();
+        fl.pop_back();
+        return p;
+    }
+    uint8_t *p = nullptr;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+// One dispatcher round; returns false when there was nothing to do.
+bool server_round(hmi_server *v)
+{
+    std::vector<SrvFrame> take;
+    std::vector<hmi_stream *> dead;
+    {
+        std::unique_lock<std::mutex> lk(v->mu);
+        // retire released streams whose queues are empty
+        for (auto it = v->streams.begin(); it != v->streams.end();) {
+            if (it->second.releasing && it->second.q.empty()) {
+                dead.push_back(it->second.s);
+                v->used -= it->second.bytes;
+                it = v->streams.erase(it);
+                v->dirty = true;
+            } else {
+                ++it;
+            }
+        }
+        if (v->dirty) {
+            batch_free(v->plan);
+            v->plan = nullptr;
+            v->plan_ids.clear();
+            std::vector<hmi_stream *> ss;
+            for (auto &kv : v->streams) {
+                v->plan_ids.push_back(kv.first);
+                ss.push_back(kv.second.s);
+            }
+            if (!ss.empty()) v->plan = batch_new(ss.data(), (int)ss.size(), 1);
+            v->dirty = false;
+        }
+        take.resize(v->plan_ids.size());
+        bool any = false;
+        for (size_t i = 0; i < v->plan_ids.size(); ++i) {
+            auto &st = v->streams[v->plan_ids[i]];
+            if (!st.q.empty()) {
+                take[i] = st.q.front();
+                st.q.pop_front();
+                any = true;
+            }
+        }
+        if (!any) {
+            for (auto *d : dead) hmi_destroy_stream(d);
+            return false;
+        }
+    }
+    for (auto *d : dead) hmi_destroy_stream(d);
+    hmi_batch *b = v->plan;
+    const int n = b ? b->n : 0;
+    int status = b ? HMI_OK : HMI_ERR_NO_MEMORY;
+    if (status == HMI_OK && v->ptr_cap < n) {
+        cudaFreeHost(v->h_ptrs);
+        cudaFree(v->d_ptrs);
+        v->h_ptrs = nullptr;
+        v->d_ptrs = nullptr;
+        v->ptr_cap = 0;
+        if (cudaMallocHost(&v->h_ptrs, sizeof(hmi_pointer) * n) == cudaSuccess &&
+            cudaMalloc(&v->d_ptrs, sizeof(hmi_pointer) * n) == cudaSuccess)
+            v->ptr_cap = n;
+        else
+            status = HMI_ERR_NO_MEMORY;
+    }
+    if (status == HMI_OK) {
+        const int slot = acquire_slot(b);
+        TickIO *io = b->h_io + (size_t)slot * n;
+        for (int i = 0; i < n; ++i) {
+            hmi_stream *s = b->s[i];
+            TickIO &t = io[b->pos[i]];
+            t.mask = nullptr;
+            t.ptr_out = v->d_ptrs + i;
+            if (take[i].host) {
+                s->used = true;
+                if (3 * (size_t)s->w == (size_t)s->L.fpitch)
+                    cudaMemcpyAsync(s->d_frame, take[i].host, take[i].bytes, cudaMemcpyHostToDevice, v->cs);
+                else
+                    cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, take[i].host, 3 * (size_t)s->w,
+                                      3 * (size_t)s->w, s->h, cudaMemcpyHostToDevice, v->cs);
+                t.frame = s->d_frame;
+                t.frame_pitch = s->L.fpitch;
+            } else {
+                t.frame = nullptr;
+                t.frame_pitch = 0;
+            }
+        }
+        status = run_tick(b, slot, v->cs, false);
+        if (status == HMI_OK &&
+            (cudaMemcpyAsync(v->h_ptrs, v->d_ptrs, sizeof(hmi_pointer) * n, cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
+             cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
+             cudaStreamSynchronize(v->cs) != cudaSuccess)) {
+            (void)cudaGetLastError();
+            status = HMI_ERR_DEVICE;
+        }
+        if (status == HMI_OK && *b->h_err) {
+            *b->h_err = 0;
+            cudaMemset(b->d_err, 0, sizeof(uint32_t));
+            status = HMI_ERR_DEVICE_TIMEOUT;
+        }
+    }
+    const uint64_t t_done = now_ns();
+    std::unique_lock<std::mutex> lk(v->mu);
+    v->ticks += 1;
+    for (int i = 0; i < (int)take.size(); ++i) {
+        if (!take[i].host) continue;
+        hmi_server_result r;
+        memset(&r, 0, sizeof(r));
+        r.stream_id = v->plan_ids[i];
+        r.status = status;
+        r.tag = take[i].tag;
+        r.submit_ns = take[i].submit_ns;
+        r.done_ns = t_done;
+        if (status == HMI_OK) r.pointer = v->h_ptrs[i];
+        v->done.push_back(r);
+        if (take[i].owned) v->pool[take[i].bytes].push_back(const_cast<uint8_t *>(take[i].host));
+        v->frames += 1;
+    }
+    lk.unlock();
+    v->done_cv.notify_all();
+    return true;
+}
+
+void server_loop(hmi_server *v)
+{
+    cudaSetDevice(v->dev);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(v->mu);
+            if (v->stop) break;
+        }
+        if (!server_round(v)) {
+            std::unique_lock<std::mutex> lk(v->mu);
+            if (v->stop) break;
+            v->work_cv.wait_for(lk, std::chrono::microseconds(500));
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t hmi_server_now_ns(void) { return now_ns(); }
+
+hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue)
+{
+    if (max_queue < 1 || max_queue > 64) {
+        fail(HMI_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    hmi_server *v = new (std::nothrow) hmi_server();
+    if (!v) {
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    v->budget = device_budget_bytes;
+    v->max_queue = max_queue;
+    if (cudaGetDevice(&v->dev) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&v->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete v;
+        fail(HMI_ERR_DEVICE);
+        return nullptr;
+    }
+    v->worker = std::thread(server_loop, v);
+    return v;
+}
+
+void hmi_server_destroy(hmi_server *v)
+{
+    if (!v) return;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->stop = true;
+    }
+    v->work_cv.notify_all();
+    if (v->worker.joinable()) v->worker.join();
+    cudaSetDevice(v->dev);
+    batch_free(v->plan);
+    for (auto &kv : v->streams) {
+        for (auto &f : kv.second.q)
+            if (f.owned) cudaFreeHost(const_cast<uint8_t *>(f.host));
+        hmi_destroy_stream(kv.second.s);
+    }
+    for (auto &kv : v->pool)
+        for (auto *p : kv.second) cudaFreeHost(p);
+    cudaFreeHost(v->h_ptrs);
+    cudaFree(v->d_ptrs);
+    if (v->cs) cudaStreamDestroy(v->cs);
+    delete v;
+}
+
+int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uint8_t *learn_frames,
+                     int n, int *stream_id)
+{
+    if (!v || !learn_frames || !stream_id || n < 1) return fail(HMI_ERR_INVALID_ARG);
+    const size_t bytes = hmi_stream_device_bytes(w, h, p);
+    if (bytes == 0) return fail(HMI_ERR_INVALID_ARG);
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        if (v->used + bytes > v->budget) return fail(HMI_ERR_NO_MEMORY);
+        v->used += bytes;   // reserved while the stream is set up
+    }
+    HMI_CUDA(cudaSetDevice(v->dev));
+    hmi_stream *s = hmi_create_stream(w, h, p);
+    int st = s ? hmi_learn_background(s, learn_frames, n) : g_last_error;
+    if (st != HMI_OK) {
+        if (s) hmi_destroy_stream(s);
+        std::lock_guard<std::mutex> lk(v->mu);
+        v->used -= bytes;
+        return fail(st);
+    }
+    std::lock_guard<std::mutex> lk(v->mu);
+    const int id = v->next_id++;
+    SrvStream &ss = v->streams[id];
+    ss.s = s;
+    ss.bytes = bytes;
+    v->dirty = true;
+    *stream_id = id;
+    return HMI_OK;
+}
+
+int hmi_server_release(hmi_server *v, int stream_id)
+{
+    if (!v) return fail(HMI_ERR_INVALID_ARG);
+    std::lock_guard<std::mutex> lk(v->mu);
+    auto it = v->streams.find(stream_id);
+    if (it == v->streams.end() || it->second.releasing) return fail(HMI_ERR_INVALID_ARG);
+    it->second.releasing = true;
+    v->work_cv.notify_all();
+    return HMI_OK;
+}
+
+static int server_enqueue(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag, bool copy)
+{
+    if (!v || !frame) return fail(HMI_ERR_INVALID_ARG);
+    size_t bytes;
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        auto it = v->streams.find(stream_id);
+        if (it == v->streams.end() || it->second.releasing) return fail(HMI_ERR_INVALID_ARG);
+        if ((int)it->second.q.size() >= v->max_queue) return fail(HMI_ERR_NO_MEMORY);
+        bytes = 3 * (size_t)it->second.s->w * it->second.s->h;
+    }
+    SrvFrame f;
+    f.bytes = bytes;
+    f.tag = tag;
+    f.submit_ns = now_ns();
+    f.owned = copy;
+    if (copy) {
+        uint8_t *buf;
+        {
+            std::lock_guard<std::mutex> lk(v->mu);
+            buf = pool_get(v, bytes);
+        }
+        if (!buf) return fail(HMI_ERR_NO_MEMORY);
+        memcpy(buf, frame, bytes);
+        f.host = buf;
+    } else {
+        f.host = frame;
+    }
+    {
+        std::lock_guard<std::mutex> lk(v->mu);
+        auto it = v->streams.find(stream_id);
+        if (it == v->streams.end() || it->second.releasing) {
+            if (copy) v->pool[bytes].push_back(const_cast<uint8_t *>(f.host));
+            return fail(HMI_ERR_INVALID_ARG);
+        }
+        it->second.q.push_back(f);
+    }
+    v->work_cv.notify_all();
+    return HMI_OK;
+}
+
+int hmi_server_submit(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag)
+{
+    return server_enqueue(v, stream_id, frame, tag, true);
+}
+
+int hmi_server_submit_ref(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag)
+{
+    return server_enqueue(v, stream_id, frame, tag, false);
+}
+
+int hmi_server_poll(hmi_server *v, hmi_server_result *out, int max_results, int wait_us)
+{
+    if (!v || !out || max_results < 1) return fail(HMI_ERR_INVALID_ARG);
+    std::unique_lock<std::mutex> lk(v->mu);
+    if (v->done.empty() && wait_us > 0)
+        v->done_cv.wait_for(lk, std::chrono::microseconds(wait_us), [&] { return !v->done.empty(); });
+    int k = 0;
+    while (k < max_results && !v->done.empty()) {
+        out[k++] = v->done.front();
+        v->done.pop_front();
+    }
+    return k;
+}
+
+int hmi_server_stats(hmi_server *v, size_t *bytes_admitted, uint64_t *ticks, uint64_t *frames)
+{
+    if (!v) return fail(HMI_ERR_INVALID_ARG);
+    std::lock_guard<std::mutex> lk(v->mu);
+    if (bytes_admitted) *bytes_admitted = v->used;
+    if (ticks) *ticks = v->ticks;
+    if (frames) *frames = v->frames;
+    return HMI_OK;
+}
+
+}  // extern "C"
+
+namespace {
 }  // namespace
 
 // ===========================================================================
@@ -867,7 +1250,7 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
     HMI_CUDA(cudaSetDevice(s->dev));
     const long long npx = (long long)s->w * s->h;
     const size_t fbytes = (size_t)npx * 3;
-    HMI_CUDA(cudaDeviceSynchronize());   // no tick of this stream may be in flight
+    if (s->used) HMI_CUDA(cudaDeviceSynchronize());   // no tick of this stream may be in flight
     // reset the learning luma total
     HMI_CUDA(cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), s->cs));
     if (is_device_ptr(frames)) {
@@ -875,8 +1258,8 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
     } else {
         // host frames: stream through a bounded staging buffer
         const int per = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (256u << 20) / fbytes));
-        uint8_t *stage = nullptr;
-        if (cudaMalloc(&stage, fbytes * per) != cudaSuccess) {
+        uint8_t *stage = nullptr;   // stream-ordered: no device-wide synchronisation
+        if (cudaMallocAsync(reinterpret_cast<void **>(&stage), fbytes * per, s->cs) != cudaSuccess) {
             (void)cudaGetLastError();
             return fail(HMI_ERR_NO_MEMORY);
         }
@@ -888,7 +1271,7 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
                 cudaStreamSynchronize(s->cs) != cudaSuccess)
                 status = cuda_fail(cudaErrorUnknown);
         }
-        cudaFree(stage);
+        cudaFreeAsync(stage, s->cs);
         if (status != HMI_OK) return status;
     }
     HMI_CUDA(cudaMemsetAsync(s->arena + s->L.lo, 0, (size_t)s->h * s->L.fpitch, s->cs));

@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
             *b.skin_count = 0u;
         }
     }
+    if (io.frame == nullptr) return;             // no frame this tick: pointer and click unchanged
     for (int i = tid; i < D.click_window; i += blockDim.x) S.hist[i] = D.hist[i];
     __syncthreads();
     // ordered list of non-empty blocks and their record offsets

@@ -111,8 +111,9 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
         const DevStream &D = b.ds[piece.x];
         const TickIO io = b.io[piece.x];
         const int w = D.w, cpr = 2 * D.nwords;
-        // two chunks per thread per round, both loads in flight before the sums
-        for (int u = piece.y + tid; u < piece.z; u += 2 * blockDim.x) {
+        // two chunks per thread per round, both loads in flight before the sums;
+        // a stream without a frame this tick (null frame) is skipped
+        for (int u = piece.y + tid; io.frame != nullptr && u < piece.z; u += 2 * blockDim.x) {
             uint32_t f[2][12];
             int npx[2];
 #pragma unroll
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
     if (!is_last) return;
     __threadfence();
     for (int s = tid; s < b.n; s += blockDim.x) {
+        if (b.io[s].frame == nullptr) continue;
         const DevStream &D = b.ds[s];
         StreamState *st = D.st;
         unsigned long long sy = *(volatile unsigned long long *)&st->sy;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         const int4 piece = b.pieces[pc];
         const DevStream &D = b.ds[piece.x];
         const TickIO io = b.io[piece.x];
+        if (io.frame == nullptr) continue;   // no frame for this stream this tick
         const uint32_t g = D.st->gain;
         const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
         const uint8_t *lo = D.lo, *hi = D.hi;
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     }
     const DevStream &D = b.ds[lo];
     const TickIO io = b.io[lo];
+    if (io.frame == nullptr) return;       // no frame for this stream this tick
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
     morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list);
@@ -563,6 +567,7 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
     const int s = s_sh;
     const DevStream &D = b.ds[s];
     const TickIO io = b.io[s];
+    if (io.frame == nullptr) return;       // CTA-uniform: no frame this tick
     const int lt = (int)(tile - b.tile_prefix[s]);
     const int ty = lt / D.tiles_x, tx = lt - ty * D.tiles_x;
     MorphGeo G;

@@ -45,6 +45,12 @@ class hmi_pointer(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hmi_server_result(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_uint64),
+                ("submit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64),
+                ("pointer", hmi_pointer)]
+
+
 POINTER_DTYPE = np.dtype([(k, np.dtype(t._type_)) for k, t in hmi_pointer._fields_])
 assert POINTER_DTYPE.itemsize == ctypes.sizeof(hmi_pointer) == 40
 
@@ -77,6 +83,16 @@ SIGNATURES = {
     "hmi_stream_device_bytes": (ctypes.c_size_t, [_I, _I, ctypes.POINTER(hmi_params)]),
     "hmi_frame_gain_noalloc": (_I, [_P, _I, _I, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                     _P, _P]),
+    "hmi_server_create": (_P, [ctypes.c_size_t, _I]),
+    "hmi_server_destroy": (None, [_P]),
+    "hmi_server_admit": (_I, [_P, _I, _I, ctypes.POINTER(hmi_params), _P, _I, ctypes.POINTER(_I)]),
+    "hmi_server_release": (_I, [_P, _I]),
+    "hmi_server_submit": (_I, [_P, _I, _P, ctypes.c_uint64]),
+    "hmi_server_submit_ref": (_I, [_P, _I, _P, ctypes.c_uint64]),
+    "hmi_server_poll": (_I, [_P, ctypes.POINTER(hmi_server_result), _I, _I]),
+    "hmi_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64),
+                              ctypes.POINTER(ctypes.c_uint64)]),
+    "hmi_server_now_ns": (ctypes.c_uint64, []),
     "hmi_last_error": (_I, []),
     "hmi_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -272,6 +288,56 @@ def hmi_frame_gain_noalloc(frame, w: int, h: int, syref: int, gain_min_q16: int,
     library's built-in scratch: for callers that cannot allocate device memory."""
     _check(load().hmi_frame_gain_noalloc(_addr(frame), w, h, syref, gain_min_q16, gain_max_q16,
                                          _addr(gain_out), cuda_stream), "hmi_frame_gain_noalloc")
+
+
+def hmi_server_create(device_budget_bytes: int, max_queue: int = 8) -> int:
+    v = load().hmi_server_create(device_budget_bytes, max_queue)
+    if not v:
+        raise HmiError(load().hmi_last_error(), "hmi_server_create")
+    return v
+
+
+def hmi_server_destroy(v: int) -> None:
+    load().hmi_server_destroy(v)
+
+
+def hmi_server_admit(v: int, w: int, h: int, params: hmi_params | None, learn_frames, n: int) -> int:
+    """Returns the stream id; raises HmiError(HMI_ERR_NO_MEMORY) when refused."""
+    sid = ctypes.c_int()
+    _check(load().hmi_server_admit(v, w, h, ctypes.byref(params) if params is not None else None,
+                                   _addr(learn_frames), n, ctypes.byref(sid)), "hmi_server_admit")
+    return sid.value
+
+
+def hmi_server_release(v: int, stream_id: int) -> None:
+    _check(load().hmi_server_release(v, stream_id), "hmi_server_release")
+
+
+def hmi_server_submit(v: int, stream_id: int, frame, tag: int) -> int:
+    """Returns the status (HMI_ERR_NO_MEMORY when the stream's queue is full)."""
+    return load().hmi_server_submit(v, stream_id, _addr(frame), tag)
+
+
+def hmi_server_submit_ref(v: int, stream_id: int, frame, tag: int) -> int:
+    """By reference: `frame` must stay valid until its result is polled."""
+    return load().hmi_server_submit_ref(v, stream_id, _addr(frame), tag)
+
+
+def hmi_server_poll(v: int, buf: "ctypes.Array", wait_us: int) -> int:
+    n = load().hmi_server_poll(v, buf, len(buf), wait_us)
+    if n < 0:
+        raise HmiError(n, "hmi_server_poll")
+    return n
+
+
+def hmi_server_stats(v: int) -> tuple[int, int, int]:
+    b, t, f = ctypes.c_size_t(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().hmi_server_stats(v, ctypes.byref(b), ctypes.byref(t), ctypes.byref(f)), "hmi_server_stats")
+    return b.value, t.value, f.value
+
+
+def hmi_server_now_ns() -> int:
+    return load().hmi_server_now_ns()
 
 
 def hmi_last_error() -> int:
