@@ -21,6 +21,9 @@
  *     memory (pageable or pinned) or in device memory of the stream's GPU;
  *     the library tells them apart with cudaPointerGetAttributes.  The library
  *     owns all per-stream device state.
+ *   - Host frames are copied to the device (pinned host memory copies
+ *     fastest); device frames whose width is a multiple of 16 and whose
+ *     address is 16-byte aligned are read in place.
  *   - Synchronous calls return when results are in the caller's buffers.
  *     The *_async calls only enqueue work on the given CUDA stream
  *     (a cudaStream_t passed as void*, NULL = the legacy default stream) and
@@ -52,6 +55,9 @@ extern "C" {
 #define HMI_ERR_NO_MEMORY (-3)      /* device or host allocation failed, or admission refused */
 #define HMI_ERR_DEVICE (-4)         /* a CUDA call failed */
 #define HMI_ERR_DEVICE_TIMEOUT (-5) /* a bounded device-side wait/loop gave up */
+#define HMI_LEARNING 1              /* server result only: the frame was taken as one of the
+                                     * stream's background-learning frames (not an error;
+                                     * its pointer is the empty pointer) */
 
 /* Opaque per-camera stream: geometry, parameters, learned background model,
  * click state and device work buffers.  Created by hmi_create_stream. */
@@ -216,7 +222,7 @@ typedef struct hmi_server hmi_server;
 
 typedef struct {
     int32_t stream_id;   /* as returned by hmi_server_admit */
-    int32_t status;      /* HMI_OK or the tick's error status */
+    int32_t status;      /* HMI_OK, HMI_LEARNING or the tick's error status */
     uint64_t tag;        /* the caller's tag from hmi_server_submit */
     uint64_t submit_ns;  /* when hmi_server_submit accepted the frame */
     uint64_t done_ns;    /* when the result became available */
@@ -227,8 +233,15 @@ typedef struct {
  * streams; max_queue: frames a stream may have pending (1..64). */
 HMI_API hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue);
 HMI_API void hmi_server_destroy(hmi_server *srv);
-/* Create a stream and learn its background from n host frames.
- * HMI_ERR_NO_MEMORY when it would exceed the budget (admission refused). */
+/* Create a stream (Sec. 2, initialisation) and reserve its device bytes in
+ * the budget; HMI_ERR_NO_MEMORY when they would exceed it (admission refused).
+ * With learn_frames non-NULL the background is learned now from n contiguous
+ * host frames (h*w*3 bytes each).  With learn_frames NULL the stream learns
+ * online: the first n frames submitted to it are the user-free learning frames
+ * (Sec. 2: the FIZI module learns the background without the user), each
+ * accumulated by the dispatcher as it arrives and returned with status
+ * HMI_LEARNING; the band is formed after the n-th, and later frames are
+ * processed.  n: 1..65535. */
 HMI_API int hmi_server_admit(hmi_server *srv, int w, int h, const hmi_params *p,
                              const uint8_t *learn_frames, int n, int *stream_id);
 /* Retire a stream once its pending frames have been processed. */
@@ -247,6 +260,21 @@ HMI_API int hmi_server_poll(hmi_server *srv, hmi_server_result *out, int max_res
 HMI_API int hmi_server_stats(hmi_server *srv, size_t *bytes_admitted, uint64_t *ticks,
                              uint64_t *frames);
 HMI_API uint64_t hmi_server_now_ns(void);
+
+/* Per-round record of the dispatcher (the server's own timing trace). */
+typedef struct {
+    uint64_t start_ns;     /* round start: frames taken from the queues */
+    uint64_t issued_ns;    /* every copy and kernel of the round issued */
+    uint64_t done_ns;      /* device work finished and results posted */
+    int32_t frames;        /* frames processed by the round's tick */
+    int32_t learning;      /* learning frames accumulated in the round */
+    int32_t streams;       /* streams in the plan */
+    int32_t replanned;     /* 1 if the plan was re-made at the round's start */
+} hmi_server_round;
+
+/* Copy up to max_rounds of the most recent rounds (oldest first; the server
+ * keeps the last 16384) into out; returns how many were written. */
+HMI_API int hmi_server_rounds(hmi_server *srv, hmi_server_round *out, int max_rounds);
 
 /* Brightness gain of one frame without any device allocation.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate

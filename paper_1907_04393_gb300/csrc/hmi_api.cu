@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -145,6 +146,44 @@ Layout make_layout(int w, int h, const hmi_params &p)
     return L;
 }
 
+// Stream state comes from a stream-ordered memory pool owned by the library
+// (one per device, memory kept while any stream lives), so that creating and
+// destroying streams, as a server admitting and retiring cameras does, needs
+// neither the driver's allocator nor a device-wide synchronisation of its own.
+struct ArenaPools {
+    std::mutex mu;
+    cudaMemPool_t pool[64] = {};
+    int state[64] = {};              // 0 unknown, 1 pool, 2 no pool support
+    std::atomic<int> live[64] = {};
+};
+ArenaPools g_pools;
+
+cudaMemPool_t arena_pool(int dev)
+{
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pools.mu);
+    if (g_pools.state[dev] == 0) {
+        int ok = 0;
+        cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, dev);
+        cudaMemPoolProps pr;
+        memset(&pr, 0, sizeof(pr));
+        pr.allocType = cudaMemAllocationTypePinned;
+        pr.location.type = cudaMemLocationTypeDevice;
+        pr.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (ok && cudaMemPoolCreate(&pool, &pr) == cudaSuccess) {
+            uint64_t keep = ~0ull;   // released only when the last stream goes
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pools.pool[dev] = pool;
+            g_pools.state[dev] = 1;
+        } else {
+            (void)cudaGetLastError();
+            g_pools.state[dev] = 2;
+        }
+    }
+    return g_pools.pool[dev];
+}
+
 bool is_device_ptr(const void *p)
 {
     if (p == nullptr) return false;
@@ -175,9 +214,10 @@ struct hmi_stream {
     hmi_pointer *d_ptr = nullptr;
     int learned = 0;
     int n_learn = 0;
+    bool pooled = false;         // arena from the library's memory pool
     bool used = false;           // has been given frames (learning must wait for its work)
     cudaStream_t cs = nullptr;
-    hmi_batch *self = nullptr;   // one-stream plan used by hmi_process_frame
+    hmi_batch *self = nullptr;   // one-stream plan of hmi_process_frame, made on first use
 };
 
 // One chain of tick kernels over a subset of the batch's streams.
@@ -191,6 +231,8 @@ struct Group {
 struct hmi_batch {
     int dev = 0;
     int n = 0;
+    int cap = 0;                  // streams the per-batch buffers hold
+    size_t plan_cap = 0;          // bytes of the plan table buffer
     std::vector<hmi_stream *> s;  // user order
     std::vector<int> pos;         // user index -> permuted position
     std::vector<Group> groups;
@@ -264,7 +306,7 @@ void fill_devstream(hmi_stream *s)
     D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
 }
 
-void plan_free(hmi_batch *b)
+void plan_free_graphs(hmi_batch *b)
 {
     for (int i = 0; i < kRing; ++i) {
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
@@ -273,14 +315,25 @@ void plan_free(hmi_batch *b)
         b->graph_src[i] = nullptr;
         b->ev_node[i][0] = b->ev_node[i][1] = nullptr;
     }
-    for (auto &g : b->groups) {
-        if (g.cs) cudaStreamDestroy(g.cs);
-        if (g.ev_luma) cudaEventDestroy(g.ev_luma);
-        if (g.ev_done) cudaEventDestroy(g.ev_done);
-    }
+}
+
+void group_destroy(Group &g)
+{
+    if (g.cs) cudaStreamDestroy(g.cs);
+    if (g.ev_luma) cudaEventDestroy(g.ev_luma);
+    if (g.ev_done) cudaEventDestroy(g.ev_done);
+    g.cs = nullptr;
+    g.ev_luma = g.ev_done = nullptr;
+}
+
+void plan_free(hmi_batch *b)
+{
+    plan_free_graphs(b);
+    for (auto &g : b->groups) group_destroy(g);
     b->groups.clear();
     if (b->plan) cudaFree(b->plan);
     b->plan = nullptr;
+    b->plan_cap = 0;
 }
 
 int batch_free(hmi_batch *b)
@@ -327,7 +380,18 @@ int plan_build(hmi_batch *b, int ng)
         load[g] += (long long)b->s[i]->w * b->s[i]->h;
     }
     std::vector<int> perm;
+    // branch streams and events of an earlier plan are reused
+    std::vector<Group> old = std::move(b->groups);
     b->groups.assign(ng, Group());
+    for (int g = 0; g < (int)old.size(); ++g) {
+        if (g < ng) {
+            b->groups[g].cs = old[g].cs;
+            b->groups[g].ev_luma = old[g].ev_luma;
+            b->groups[g].ev_done = old[g].ev_done;
+        } else {
+            group_destroy(old[g]);
+        }
+    }
     for (int g = 0; g < ng; ++g) {
         std::sort(members[g].begin(), members[g].end());
         b->groups[g].off = (int)perm.size();
@@ -380,28 +444,39 @@ int plan_build(hmi_batch *b, int ng)
         t.o_skn = a.take(sizeof(uint32_t));
         t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
     }
-    if (cudaMalloc(&b->plan, a.off) != cudaSuccess) {
-        (void)cudaGetLastError();
-        b->groups.clear();
-        return fail(HMI_ERR_NO_MEMORY);
+    if (a.off > b->plan_cap) {   // grow the table buffer; a smaller plan reuses it
+        if (b->plan) cudaFree(b->plan);
+        b->plan = nullptr;
+        b->plan_cap = 0;
+        const size_t want = std::max(a.off, b->plan_cap + b->plan_cap / 2);
+        if (cudaMalloc(&b->plan, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            for (auto &g : b->groups) group_destroy(g);
+            b->groups.clear();
+            return fail(HMI_ERR_NO_MEMORY);
+        }
+        b->plan_cap = want;
     }
+    // Tables go up in stream order on the batch's own stream, from host
+    // vectors that live until the synchronisation at the end.
     uint8_t *A = b->plan;
+    cudaStream_t up = b->cs;
     std::vector<DevStream> ds(n);
     for (int p = 0; p < n; ++p) ds[p] = b->s[perm[p]]->ds;
-    bool ok = cudaMemset(A, 0, a.off) == cudaSuccess &&
-              cudaMemcpy(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+    bool ok = cudaMemsetAsync(A, 0, a.off, up) == cudaSuccess &&
+              cudaMemcpyAsync(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice, up) == cudaSuccess;
     for (int g = 0; ok && g < ng; ++g) {
         Tables &t = T[g];
         Group &G = b->groups[g];
         const int m = G.cnt;
-        ok = cudaMemcpy(A + t.o_c, t.cpre.data(), sizeof(unsigned long long) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(A + t.o_t, t.tpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(A + t.o_b, t.bpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(A + t.o_s, t.spre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaMemcpy(A + t.o_p, t.pieces.data(), sizeof(int4) * t.pieces.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&G.ev_luma, cudaEventDisableTiming) == cudaSuccess &&
-             cudaEventCreateWithFlags(&G.ev_done, cudaEventDisableTiming) == cudaSuccess;
+        ok = cudaMemcpyAsync(A + t.o_c, t.cpre.data(), sizeof(unsigned long long) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             cudaMemcpyAsync(A + t.o_t, t.tpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             cudaMemcpyAsync(A + t.o_b, t.bpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             cudaMemcpyAsync(A + t.o_s, t.spre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             cudaMemcpyAsync(A + t.o_p, t.pieces.data(), sizeof(int4) * t.pieces.size(), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             (G.cs || cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) == cudaSuccess) &&
+             (G.ev_luma || cudaEventCreateWithFlags(&G.ev_luma, cudaEventDisableTiming) == cudaSuccess) &&
+             (G.ev_done || cudaEventCreateWithFlags(&G.ev_done, cudaEventDisableTiming) == cudaSuccess);
         BatchDev &bd = G.bd;
         bd.ds = reinterpret_cast<const DevStream *>(A + o_ds) + G.off;
         bd.io = nullptr;
@@ -425,6 +500,7 @@ int plan_build(hmi_batch *b, int ng)
         bd.skin_count = reinterpret_cast<uint32_t *>(A + t.o_skn);
         bd.skin_list = reinterpret_cast<uint2 *>(A + t.o_skl);
     }
+    ok = ok && cudaStreamSynchronize(up) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         plan_free(b);
@@ -433,22 +509,48 @@ int plan_build(hmi_batch *b, int ng)
     return HMI_OK;
 }
 
+bool streams_ok(hmi_stream *const *s, int n)
+{
+    if (!s || n < 1 || n > kMaxBatch) return false;
+    for (int i = 0; i < n; ++i) {
+        if (!s[i] || s[i]->dev != s[0]->dev) return false;
+        for (int j = 0; j < i; ++j)
+            if (s[j] == s[i]) return false;
+    }
+    return true;
+}
+
+// Per-batch buffers for `cap` streams: kRing tick tables (device and pinned
+// mirror), the pointers of the synchronous form and the error word.
+bool batch_alloc_io(hmi_batch *b, int cap)
+{
+    if (b->arena) cudaFree(b->arena);
+    if (b->h_io) cudaFreeHost(b->h_io);
+    b->arena = nullptr;
+    b->h_io = nullptr;
+    b->cap = 0;
+    Arena a;
+    const size_t o_io = a.take(sizeof(TickIO) * cap * kRing);
+    const size_t o_ptr = a.take(sizeof(hmi_pointer) * cap);
+    const size_t o_err = a.take(sizeof(uint32_t));
+    if (cudaMalloc(&b->arena, a.off) != cudaSuccess || cudaMemset(b->arena, 0, a.off) != cudaSuccess ||
+        cudaMallocHost(&b->h_io, sizeof(TickIO) * cap * kRing) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    memset(b->h_io, 0, sizeof(TickIO) * cap * kRing);
+    b->d_io = reinterpret_cast<TickIO *>(b->arena + o_io);
+    b->d_ptrs = reinterpret_cast<hmi_pointer *>(b->arena + o_ptr);
+    b->d_err = reinterpret_cast<uint32_t *>(b->arena + o_err);
+    b->cap = cap;
+    return true;
+}
+
 hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
 {
-    if (!s || n < 1 || n > kMaxBatch) {
+    if (!streams_ok(s, n)) {
         fail(HMI_ERR_INVALID_ARG);
         return nullptr;
-    }
-    for (int i = 0; i < n; ++i) {
-        if (!s[i] || s[i]->dev != s[0]->dev) {
-            fail(HMI_ERR_INVALID_ARG);
-            return nullptr;
-        }
-        for (int j = 0; j < i; ++j)
-            if (s[j] == s[i]) {
-                fail(HMI_ERR_INVALID_ARG);
-                return nullptr;
-            }
     }
     hmi_batch *b = new (std::nothrow) hmi_batch();
     if (!b) {
@@ -463,13 +565,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
         cuda_fail(cudaErrorInvalidDevice);
         return nullptr;
     }
-    Arena a;
-    const size_t o_io = a.take(sizeof(TickIO) * n * kRing);
-    const size_t o_ptr = a.take(sizeof(hmi_pointer) * n);
-    const size_t o_err = a.take(sizeof(uint32_t));
-    bool ok = cudaMalloc(&b->arena, a.off) == cudaSuccess &&
-              cudaMemset(b->arena, 0, a.off) == cudaSuccess &&
-              cudaMallocHost(&b->h_io, sizeof(TickIO) * n * kRing) == cudaSuccess &&
+    bool ok = batch_alloc_io(b, n) &&
               cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
@@ -482,11 +578,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
         fail(HMI_ERR_NO_MEMORY);
         return nullptr;
     }
-    memset(b->h_io, 0, sizeof(TickIO) * n * kRing);
     *b->h_err = 0;
-    b->d_io = reinterpret_cast<TickIO *>(b->arena + o_io);
-    b->d_ptrs = reinterpret_cast<hmi_pointer *>(b->arena + o_ptr);
-    b->d_err = reinterpret_cast<uint32_t *>(b->arena + o_err);
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->dev);
     b->num_sms = sms > 0 ? sms : 1;
@@ -737,6 +829,147 @@ int batch_set_groups(hmi_batch *b, int ng)
 
 int default_groups(int n) { return std::min(2, n); }
 
+// Give a stream's arena back (stream-ordered for pooled arenas) and destroy
+// its CUDA stream; the pool is trimmed when the device's last stream goes.
+void release_arena(hmi_stream *s)
+{
+    if (s->arena) {
+        if (s->pooled) {
+            cudaFreeAsync(s->arena, s->cs);
+            cudaStreamSynchronize(s->cs);
+            if (--g_pools.live[s->dev] == 0) cudaMemPoolTrimTo(g_pools.pool[s->dev], 0);
+        } else {
+            cudaFree(s->arena);
+        }
+        s->arena = nullptr;
+    }
+    if (s->cs) {
+        cudaStreamSynchronize(s->cs);
+        cudaStreamDestroy(s->cs);
+        s->cs = nullptr;
+    }
+}
+
+// A stream whose device state is allocated and initialised in the order of
+// CUDA stream `order` (no host synchronisation: usable by work enqueued on
+// `order`, and by any work once `order` has been synchronised), or, with
+// order NULL, on its own CUDA stream and synchronised before returning.
+hmi_stream *create_stream_on(int w, int h, const hmi_params *p, cudaStream_t order)
+{
+    hmi_params d;
+    hmi_default_params(&d);
+    const hmi_params &pp = p ? *p : d;
+    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim || !params_valid(pp)) {
+        fail(HMI_ERR_INVALID_ARG);
+        return nullptr;
+    }
+    hmi_stream *s = new (std::nothrow) hmi_stream();
+    if (!s) {
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    s->w = w;
+    s->h = h;
+    s->p = pp;
+    s->L = make_layout(w, h, pp);
+    if (cudaGetDevice(&s->dev) != cudaSuccess) {
+        delete s;
+        cuda_fail(cudaErrorNoDevice);
+        return nullptr;
+    }
+    if (cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete s;
+        fail(HMI_ERR_DEVICE);
+        return nullptr;
+    }
+    cudaStream_t cs = order ? order : s->cs;
+    cudaMemPool_t pool = arena_pool(s->dev);
+    cudaError_t ae = pool ? cudaMallocFromPoolAsync(reinterpret_cast<void **>(&s->arena), s->L.total, pool, cs)
+                          : cudaMalloc(&s->arena, s->L.total);
+    if (ae != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaStreamDestroy(s->cs);
+        delete s;
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    s->pooled = pool != nullptr;
+    if (s->pooled) g_pools.live[s->dev]++;
+    uint8_t *a = s->arena;
+    s->d_frame = a + s->L.frame;
+    s->d_mask = a + s->L.mask;
+    s->d_S = reinterpret_cast<uint32_t *>(a + s->L.S);
+    s->d_Q = reinterpret_cast<uint32_t *>(a + s->L.Q);
+    s->d_vmin = a + s->L.vmin;
+    s->d_vmax = a + s->L.vmax;
+    s->st = reinterpret_cast<StreamState *>(a + s->L.st);
+    s->d_ds = reinterpret_cast<DevStream *>(a + s->L.ds);
+    s->d_ptr = reinterpret_cast<hmi_pointer *>(a + s->L.ptr);
+    fill_devstream(s);
+    bool ok = cudaMemsetAsync(s->arena, 0, s->L.total, cs) == cudaSuccess &&
+              cudaMemcpyAsync(s->d_ds, &s->ds, sizeof(DevStream), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+              (order != nullptr || cudaStreamSynchronize(cs) == cudaSuccess);
+    if (!ok) {
+        (void)cudaGetLastError();
+        if (order) cudaStreamSynchronize(order);
+        release_arena(s);
+        delete s;
+        fail(HMI_ERR_NO_MEMORY);
+        return nullptr;
+    }
+    return s;
+}
+
+hmi_batch *self_plan(hmi_stream *s)
+{
+    if (!s->self) {
+        hmi_stream *one = s;
+        if (cudaSetDevice(s->dev) != cudaSuccess) {
+            cuda_fail(cudaErrorInvalidDevice);
+            return nullptr;
+        }
+        s->self = batch_new(&one, 1, 1);
+    }
+    return s->self;
+}
+
+// Re-plan an idle batch (no tick in flight) over another set of streams,
+// reusing its buffers, branch streams and events where they are large enough,
+// so that a plan can follow streams joining and leaving without allocating on
+// every change.  The batch's error word is cleared.
+int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
+{
+    if (!b || !streams_ok(s, n) || s[0]->dev != b->dev) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    plan_free_graphs(b);
+    if (n > b->cap && !batch_alloc_io(b, std::min(kMaxBatch, std::max(n, 2 * b->cap)))) {
+        plan_free(b);
+        return fail(HMI_ERR_NO_MEMORY);
+    }
+    b->n = n;
+    b->s.assign(s, s + n);
+    for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
+    b->next = 0;
+    b->seen.clear();
+    HMI_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), b->cs));
+    return plan_build(b, ngroups);
+}
+
+// Band of a stream from its learned sums after n frames (Sec. 3.1 (i)), in
+// the padded row layout; the padding bytes are zeroed first.
+cudaError_t enqueue_band(hmi_stream *s, int n, cudaStream_t cs)
+{
+    const size_t bytes = (size_t)s->h * s->L.fpitch;
+    cudaError_t e = cudaMemsetAsync(s->arena + s->L.lo, 0, bytes, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + s->L.hi, 0, bytes, cs);
+    if (e == cudaSuccess)
+        e = launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
+                              s->p.bg_margin, s->w, s->h, s->L.fpitch, s->arena + s->L.lo,
+                              s->arena + s->L.hi, s->st, cs);
+    return e;
+}
+
 
 // ===========================================================================
 // Server: admission by device-memory budget, resident streams, continuous
@@ -751,11 +984,32 @@ struct SrvFrame {
 };
 
 struct SrvStream {
-    hmi_stream *s = nullptr;
+    hmi_stream *s = nullptr;         // null until the dispatcher has created it
+    int w = 0, h = 0;
+    hmi_params p{};
     size_t bytes = 0;
+    bool pending = false;            // admitted, creation left to the dispatcher
+    bool failed = false;             // creation failed: queued frames are returned as errors
     bool releasing = false;
+    int learn_n = 0, learn_done = 0;   // online learning: frames wanted / taken
     std::deque<SrvFrame> q;
 };
+
+struct SrvTake {
+    SrvFrame f;
+    SrvStream *ss = nullptr;
+    bool learning = false;
+};
+
+hmi_pointer empty_pointer()
+{
+    hmi_pointer p;
+    memset(&p, 0, sizeof(p));
+    p.x = p.y = -1.0f;
+    p.x0 = p.y0 = p.x1 = p.y1 = -1;
+    p.label = -1;
+    return p;
+}
 
 uint64_t now_ns()
 {
@@ -785,6 +1039,8 @@ struct hmi_server {
     hmi_pointer *h_ptrs = nullptr, *d_ptrs = nullptr;
     int ptr_cap = 0;
     uint64_t ticks = 0, frames = 0;
+    std::vector<hmi_server_round> rounds;   // ring of kRoundLog records (under mu)
+    uint64_t rounds_written = 0;
 };
 
 namespace {
@@ -806,51 +1062,114 @@ uint8_t *pool_get(hmi_server *v, size_t bytes)
 }
 
 // One dispatcher round; returns false when there was nothing to do.
+constexpr int kRoundLog = 16384;
+
 bool server_round(hmi_server *v)
 {
-    std::vector<SrvFrame> take;
+    std::vector<SrvTake> take;
     std::vector<hmi_stream *> dead;
+    std::vector<int> replan_ids;
+    std::vector<hmi_stream *> replan_s;
+    hmi_server_round rec;
+    memset(&rec, 0, sizeof(rec));
+    rec.start_ns = now_ns();
+    std::vector<SrvStream *> creates;
     {
         std::unique_lock<std::mutex> lk(v->mu);
-        // retire released streams whose queues are empty
+        // retire released streams whose queues are empty, and streams whose
+        // creation failed (their frames come back with the error)
+        bool posted = false;
         for (auto it = v->streams.begin(); it != v->streams.end();) {
-            if (it->second.releasing && it->second.q.empty()) {
-                dead.push_back(it->second.s);
-                v->used -= it->second.bytes;
+            SrvStream &ss = it->second;
+            if (ss.failed) {
+                for (const SrvFrame &f : ss.q) {
+                    hmi_server_result r;
+                    memset(&r, 0, sizeof(r));
+                    r.stream_id = it->first;
+                    r.status = HMI_ERR_NO_MEMORY;
+                    r.tag = f.tag;
+                    r.submit_ns = f.submit_ns;
+                    r.done_ns = now_ns();
+                    r.pointer = empty_pointer();
+                    v->done.push_back(r);
+                    if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
+                    posted = true;
+                }
+                ss.q.clear();
+            }
+            if ((ss.releasing || ss.failed) && ss.q.empty() && !ss.pending) {
+                if (ss.s) dead.push_back(ss.s);
+                v->used -= ss.bytes;
                 it = v->streams.erase(it);
                 v->dirty = true;
             } else {
+                if (ss.pending) {
+                    creates.push_back(&ss);
+                    ss.pending = false;
+                }
                 ++it;
             }
         }
+        if (posted) v->done_cv.notify_all();
+    }
+    if (!creates.empty()) {
+        // device state of newly admitted streams, in the order of this
+        // thread's CUDA stream (all later work on them runs on it too)
+        std::vector<hmi_stream *> made(creates.size());
+        for (size_t k = 0; k < creates.size(); ++k)
+            made[k] = create_stream_on(creates[k]->w, creates[k]->h, &creates[k]->p, v->cs);
+        std::unique_lock<std::mutex> lk(v->mu);
+        for (size_t k = 0; k < creates.size(); ++k) {
+            creates[k]->s = made[k];
+            creates[k]->failed = made[k] == nullptr;
+        }
+        v->dirty = true;
+    }
+    {
+        std::unique_lock<std::mutex> lk(v->mu);
         if (v->dirty) {
-            batch_free(v->plan);
-            v->plan = nullptr;
-            v->plan_ids.clear();
-            std::vector<hmi_stream *> ss;
+            rec.replanned = 1;
+            replan_ids.clear();
             for (auto &kv : v->streams) {
-                v->plan_ids.push_back(kv.first);
-                ss.push_back(kv.second.s);
+                if (!kv.second.s) continue;
+                replan_ids.push_back(kv.first);
+                replan_s.push_back(kv.second.s);
             }
-            if (!ss.empty()) v->plan = batch_new(ss.data(), (int)ss.size(), 1);
             v->dirty = false;
         }
+    }
+    if (rec.replanned) {
+        // Re-made in place with the lock released (no tick is in flight
+        // between rounds, and only this thread erases streams), so that
+        // admissions and submissions are not held up by it.
+        v->plan_ids = replan_ids;
+        if (!replan_s.empty()) {
+            if (!v->plan)
+                v->plan = batch_new(replan_s.data(), (int)replan_s.size(), 1);
+            else if (batch_replan(v->plan, replan_s.data(), (int)replan_s.size(), 1) != HMI_OK) {
+                batch_free(v->plan);
+                v->plan = nullptr;
+            }
+        }
+    }
+    for (auto *d : dead) hmi_destroy_stream(d);   // no plan refers to them now
+    {
+        std::unique_lock<std::mutex> lk(v->mu);
         take.resize(v->plan_ids.size());
         bool any = false;
         for (size_t i = 0; i < v->plan_ids.size(); ++i) {
-            auto &st = v->streams[v->plan_ids[i]];
+            auto it = v->streams.find(v->plan_ids[i]);
+            if (it == v->streams.end()) continue;   // cannot happen: only this thread erases
+            SrvStream &st = it->second;
+            take[i].ss = &st;   // map nodes stay put
             if (!st.q.empty()) {
-                take[i] = st.q.front();
+                take[i].f = st.q.front();
                 st.q.pop_front();
                 any = true;
             }
         }
-        if (!any) {
-            for (auto *d : dead) hmi_destroy_stream(d);
-            return false;
-        }
+        if (!any) return rec.replanned != 0;
     }
-    for (auto *d : dead) hmi_destroy_stream(d);
     hmi_batch *b = v->plan;
     const int n = b ? b->n : 0;
     int status = b ? HMI_OK : HMI_ERR_NO_MEMORY;
@@ -866,7 +1185,53 @@ bool server_round(hmi_server *v)
         else
             status = HMI_ERR_NO_MEMORY;
     }
-    if (status == HMI_OK) {
+    // All of the round's host-to-device copies go first, back to back on the
+    // copy engine: a learning frame densely into its stream's frame buffer, a
+    // frame to process at the buffer's pitch.  Then the learning kernels (the
+    // band is formed after a stream's last learning frame), then one tick over
+    // the plan, in which learning streams are inactive (null frame).
+    bool any_active = false;
+    for (int i = 0; i < n && status == HMI_OK; ++i) {
+        const SrvFrame &f = take[i].f;
+        if (!f.host) continue;
+        SrvStream *ss = take[i].ss;
+        hmi_stream *s = ss->s;
+        take[i].learning = ss->learn_done < ss->learn_n;
+        any_active = any_active || !take[i].learning;
+        cudaError_t e;
+        if (take[i].learning || 3 * (size_t)s->w == (size_t)s->L.fpitch)
+            e = cudaMemcpyAsync(s->d_frame, f.host, f.bytes, cudaMemcpyHostToDevice, v->cs);
+        else
+            e = cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, f.host, 3 * (size_t)s->w, 3 * (size_t)s->w, s->h,
+                                  cudaMemcpyHostToDevice, v->cs);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            status = HMI_ERR_DEVICE;
+        }
+    }
+    for (int i = 0; i < n && status == HMI_OK; ++i) {
+        if (!take[i].f.host || !take[i].learning) continue;
+        SrvStream *ss = take[i].ss;
+        hmi_stream *s = ss->s;
+        cudaError_t e = cudaSuccess;
+        if (ss->learn_done == 0)
+            e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
+        if (e == cudaSuccess)
+            e = launch_learn_accum(s->d_frame, 1, (long long)s->w * s->h, s->d_S, s->d_Q, s->d_vmin,
+                                   s->d_vmax, ss->learn_done == 0, s->st, v->cs);
+        if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            status = HMI_ERR_DEVICE;
+            break;
+        }
+        if (++ss->learn_done == ss->learn_n) {
+            s->learned = 1;
+            s->n_learn = ss->learn_n;
+        }
+        rec.learning += 1;
+    }
+    if (status == HMI_OK && any_active) {
         const int slot = acquire_slot(b);
         TickIO *io = b->h_io + (size_t)slot * n;
         for (int i = 0; i < n; ++i) {
@@ -874,13 +1239,8 @@ bool server_round(hmi_server *v)
             TickIO &t = io[b->pos[i]];
             t.mask = nullptr;
             t.ptr_out = v->d_ptrs + i;
-            if (take[i].host) {
+            if (take[i].f.host && !take[i].learning) {
                 s->used = true;
-                if (3 * (size_t)s->w == (size_t)s->L.fpitch)
-                    cudaMemcpyAsync(s->d_frame, take[i].host, take[i].bytes, cudaMemcpyHostToDevice, v->cs);
-                else
-                    cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, take[i].host, 3 * (size_t)s->w,
-                                      3 * (size_t)s->w, s->h, cudaMemcpyHostToDevice, v->cs);
                 t.frame = s->d_frame;
                 t.frame_pitch = s->L.fpitch;
             } else {
@@ -891,34 +1251,50 @@ bool server_round(hmi_server *v)
         status = run_tick(b, slot, v->cs, false);
         if (status == HMI_OK &&
             (cudaMemcpyAsync(v->h_ptrs, v->d_ptrs, sizeof(hmi_pointer) * n, cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
-             cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
-             cudaStreamSynchronize(v->cs) != cudaSuccess)) {
+             cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess)) {
             (void)cudaGetLastError();
             status = HMI_ERR_DEVICE;
         }
-        if (status == HMI_OK && *b->h_err) {
-            *b->h_err = 0;
-            cudaMemset(b->d_err, 0, sizeof(uint32_t));
-            status = HMI_ERR_DEVICE_TIMEOUT;
-        }
+    }
+    rec.issued_ns = now_ns();
+    if (status == HMI_OK && cudaStreamSynchronize(v->cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        status = HMI_ERR_DEVICE;
+    }
+    if (status == HMI_OK && any_active && *b->h_err) {
+        *b->h_err = 0;
+        cudaMemset(b->d_err, 0, sizeof(uint32_t));
+        status = HMI_ERR_DEVICE_TIMEOUT;
     }
     const uint64_t t_done = now_ns();
+    rec.done_ns = t_done;
+    rec.streams = n;
     std::unique_lock<std::mutex> lk(v->mu);
     v->ticks += 1;
     for (int i = 0; i < (int)take.size(); ++i) {
-        if (!take[i].host) continue;
+        const SrvFrame &f = take[i].f;
+        if (!f.host) continue;
         hmi_server_result r;
         memset(&r, 0, sizeof(r));
         r.stream_id = v->plan_ids[i];
         r.status = status;
-        r.tag = take[i].tag;
-        r.submit_ns = take[i].submit_ns;
+        r.tag = f.tag;
+        r.submit_ns = f.submit_ns;
         r.done_ns = t_done;
-        if (status == HMI_OK) r.pointer = v->h_ptrs[i];
+        if (status == HMI_OK && take[i].learning) {
+            r.status = HMI_LEARNING;
+            r.pointer = empty_pointer();
+        } else if (status == HMI_OK) {
+            r.pointer = v->h_ptrs[i];
+        }
         v->done.push_back(r);
-        if (take[i].owned) v->pool[take[i].bytes].push_back(const_cast<uint8_t *>(take[i].host));
+        if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
         v->frames += 1;
+        if (!take[i].learning) rec.frames += 1;
     }
+    if (v->rounds.size() < (size_t)kRoundLog) v->rounds.push_back(rec);
+    else v->rounds[v->rounds_written % kRoundLog] = rec;
+    v->rounds_written += 1;
     lk.unlock();
     v->done_cv.notify_all();
     return true;
@@ -997,7 +1373,7 @@ void hmi_server_destroy(hmi_server *v)
 int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uint8_t *learn_frames,
                      int n, int *stream_id)
 {
-    if (!v || !learn_frames || !stream_id || n < 1) return fail(HMI_ERR_INVALID_ARG);
+    if (!v || !stream_id || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
     const size_t bytes = hmi_stream_device_bytes(w, h, p);
     if (bytes == 0) return fail(HMI_ERR_INVALID_ARG);
     {
@@ -1005,9 +1381,27 @@ int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uin
         if (v->used + bytes > v->budget) return fail(HMI_ERR_NO_MEMORY);
         v->used += bytes;   // reserved while the stream is set up
     }
+    if (!learn_frames) {
+        // online learning: a reservation only; the dispatcher creates the
+        // stream at its next round, and frames may be queued meanwhile
+        std::lock_guard<std::mutex> lk(v->mu);
+        const int id = v->next_id++;
+        SrvStream &ss = v->streams[id];
+        ss.w = w;
+        ss.h = h;
+        if (p) ss.p = *p;
+        else hmi_default_params(&ss.p);
+        ss.bytes = bytes;
+        ss.pending = true;
+        ss.learn_n = n;
+        *stream_id = id;
+        v->work_cv.notify_all();
+        return HMI_OK;
+    }
     HMI_CUDA(cudaSetDevice(v->dev));
     hmi_stream *s = hmi_create_stream(w, h, p);
-    int st = s ? hmi_learn_background(s, learn_frames, n) : g_last_error;
+    int st = s ? HMI_OK : g_last_error;
+    if (s) st = hmi_learn_background(s, learn_frames, n);
     if (st != HMI_OK) {
         if (s) hmi_destroy_stream(s);
         std::lock_guard<std::mutex> lk(v->mu);
@@ -1018,6 +1412,9 @@ int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uin
     const int id = v->next_id++;
     SrvStream &ss = v->streams[id];
     ss.s = s;
+    ss.w = w;
+    ss.h = h;
+    ss.p = s->p;
     ss.bytes = bytes;
     v->dirty = true;
     *stream_id = id;
@@ -1044,7 +1441,7 @@ static int server_enqueue(hmi_server *v, int stream_id, const uint8_t *frame, ui
         auto it = v->streams.find(stream_id);
         if (it == v->streams.end() || it->second.releasing) return fail(HMI_ERR_INVALID_ARG);
         if ((int)it->second.q.size() >= v->max_queue) return fail(HMI_ERR_NO_MEMORY);
-        bytes = 3 * (size_t)it->second.s->w * it->second.s->h;
+        bytes = 3 * (size_t)it->second.w * it->second.h;
     }
     SrvFrame f;
     f.bytes = bytes;
@@ -1100,6 +1497,19 @@ int hmi_server_poll(hmi_server *v, hmi_server_result *out, int max_results, int 
     return k;
 }
 
+int hmi_server_rounds(hmi_server *v, hmi_server_round *out, int max_rounds)
+{
+    if (!v || !out || max_rounds < 1) return fail(HMI_ERR_INVALID_ARG);
+    std::lock_guard<std::mutex> lk(v->mu);
+    const uint64_t have = std::min<uint64_t>(v->rounds_written, v->rounds.size());
+    const uint64_t k = std::min<uint64_t>(have, (uint64_t)max_rounds);
+    for (uint64_t i = 0; i < k; ++i) {
+        const uint64_t r = v->rounds_written - k + i;   // oldest of the last k first
+        out[i] = v->rounds[r % kRoundLog];
+    }
+    return (int)k;
+}
+
 int hmi_server_stats(hmi_server *v, size_t *bytes_admitted, uint64_t *ticks, uint64_t *frames)
 {
     if (!v) return fail(HMI_ERR_INVALID_ARG);
@@ -1111,9 +1521,6 @@ int hmi_server_stats(hmi_server *v, size_t *bytes_admitted, uint64_t *ticks, uin
 }
 
 }  // extern "C"
-
-namespace {
-}  // namespace
 
 // ===========================================================================
 // C ABI
@@ -1167,61 +1574,7 @@ size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p)
 
 hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p)
 {
-    hmi_params d;
-    hmi_default_params(&d);
-    const hmi_params &pp = p ? *p : d;
-    if (w < 1 || h < 1 || w > kMaxDim || h > kMaxDim || !params_valid(pp)) {
-        fail(HMI_ERR_INVALID_ARG);
-        return nullptr;
-    }
-    hmi_stream *s = new (std::nothrow) hmi_stream();
-    if (!s) {
-        fail(HMI_ERR_NO_MEMORY);
-        return nullptr;
-    }
-    s->w = w;
-    s->h = h;
-    s->p = pp;
-    s->L = make_layout(w, h, pp);
-    if (cudaGetDevice(&s->dev) != cudaSuccess) {
-        delete s;
-        cuda_fail(cudaErrorNoDevice);
-        return nullptr;
-    }
-    if (cudaMalloc(&s->arena, s->L.total) != cudaSuccess) {
-        (void)cudaGetLastError();
-        delete s;
-        fail(HMI_ERR_NO_MEMORY);
-        return nullptr;
-    }
-    uint8_t *a = s->arena;
-    s->d_frame = a + s->L.frame;
-    s->d_mask = a + s->L.mask;
-    s->d_S = reinterpret_cast<uint32_t *>(a + s->L.S);
-    s->d_Q = reinterpret_cast<uint32_t *>(a + s->L.Q);
-    s->d_vmin = a + s->L.vmin;
-    s->d_vmax = a + s->L.vmax;
-    s->st = reinterpret_cast<StreamState *>(a + s->L.st);
-    s->d_ds = reinterpret_cast<DevStream *>(a + s->L.ds);
-    s->d_ptr = reinterpret_cast<hmi_pointer *>(a + s->L.ptr);
-    fill_devstream(s);
-    bool ok = cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMemset(s->arena, 0, s->L.total) == cudaSuccess &&
-              cudaMemcpy(s->d_ds, &s->ds, sizeof(DevStream), cudaMemcpyHostToDevice) == cudaSuccess;
-    if (ok) {
-        hmi_stream *one = s;
-        s->self = batch_new(&one, 1, 1);
-        ok = s->self != nullptr;
-    }
-    if (!ok) {
-        (void)cudaGetLastError();
-        if (s->cs) cudaStreamDestroy(s->cs);
-        cudaFree(s->arena);
-        delete s;
-        fail(HMI_ERR_NO_MEMORY);
-        return nullptr;
-    }
-    return s;
+    return create_stream_on(w, h, p, nullptr);
 }
 
 void hmi_destroy_stream(hmi_stream *s)
@@ -1236,11 +1589,8 @@ void hmi_destroy_stream(hmi_stream *s)
     }
     cudaSetDevice(s->dev);
     batch_free(s->self);
-    if (s->cs) {
-        cudaStreamSynchronize(s->cs);
-        cudaStreamDestroy(s->cs);
-    }
-    cudaFree(s->arena);
+    cudaDeviceSynchronize();   // no work of any stream may still use the state
+    release_arena(s);
     delete s;
 }
 
@@ -1274,11 +1624,7 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
         cudaFreeAsync(stage, s->cs);
         if (status != HMI_OK) return status;
     }
-    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.lo, 0, (size_t)s->h * s->L.fpitch, s->cs));
-    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.hi, 0, (size_t)s->h * s->L.fpitch, s->cs));
-    HMI_CUDA(launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
-                               s->p.bg_margin, s->w, s->h, s->L.fpitch, s->arena + s->L.lo,
-                               s->arena + s->L.hi, s->st, s->cs));
+    HMI_CUDA(enqueue_band(s, n, s->cs));
     HMI_CUDA(cudaStreamSynchronize(s->cs));
     s->learned = 1;
     s->n_learn = n;
@@ -1289,6 +1635,7 @@ int hmi_process_frame(hmi_stream *s, const uint8_t *frame, uint8_t *mask_out, hm
 {
     if (!s || !frame) return fail(HMI_ERR_INVALID_ARG);
     uint8_t *const masks[1] = {mask_out};
+    if (!self_plan(s)) return g_last_error;
     return batch_sync(s->self, &frame, masks, pointer_out);
 }
 
@@ -1297,6 +1644,7 @@ int hmi_process_frame_async(hmi_stream *s, const uint8_t *frame, uint8_t *mask_o
 {
     if (!s || !frame) return fail(HMI_ERR_INVALID_ARG);
     uint8_t *const masks[1] = {mask_out};
+    if (!self_plan(s)) return g_last_error;
     return batch_async(s->self, &frame, masks, pointer_out, cuda_stream, 0);
 }
 
@@ -1444,11 +1792,7 @@ int hmi_import_background(hmi_stream *s, const uint32_t *S, const uint32_t *Q, c
     HMI_CUDA(cudaMemcpy(s->d_vmax, vmax, cnt, cudaMemcpyDefault));
     const unsigned long long tot = (unsigned long long)syref * (unsigned long long)n;
     HMI_CUDA(cudaMemcpy(&s->st->learn_luma, &tot, sizeof(tot), cudaMemcpyHostToDevice));
-    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.lo, 0, (size_t)s->h * s->L.fpitch, s->cs));
-    HMI_CUDA(cudaMemsetAsync(s->arena + s->L.hi, 0, (size_t)s->h * s->L.fpitch, s->cs));
-    HMI_CUDA(launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
-                               s->p.bg_margin, s->w, s->h, s->L.fpitch, s->arena + s->L.lo,
-                               s->arena + s->L.hi, s->st, s->cs));
+    HMI_CUDA(enqueue_band(s, n, s->cs));
     HMI_CUDA(cudaStreamSynchronize(s->cs));
     s->learned = 1;
     s->n_learn = n;

@@ -3,6 +3,7 @@
 // in the initialisation step; Sec. 3.3: Gaussian background models).
 //   k_learn_accum  exact per pixel-channel sums S = sum v, Q = sum v^2 and the
 //                  min / max over a chunk of frames, plus the frames' luma total
+//                  (k_learn_accum4: the same, four pixels per thread, vectorised)
 //   k_learn_band   band [lo, hi] = [min(vmin, L_k) - delta, max(vmax, H_k) + delta]
 //                  clamped to bytes, with L_k / H_k the exact integer edges of
 //                  mu -/+ k sigma; written in the padded row layout the
@@ -59,6 +60,81 @@ __global__ void __launch_bounds__(kThreads) k_learn_accum(const uint8_t *__restr
     }
 }
 
+// Same sums, four pixels (twelve channel values) per thread: the frame bytes,
+// min and max as three 32-bit words each (byte-wise min / max on packed
+// bytes), S and Q as three 128-bit words each.  Needs npx % 4 == 0, frames
+// 4-byte aligned and S, Q 16-byte aligned.
+__global__ void __launch_bounds__(kThreads) k_learn_accum4(const uint8_t *__restrict__ frames,
+                                                           int nf, long long npx,
+                                                           uint32_t *S, uint32_t *Q,
+                                                           uint8_t *vmin, uint8_t *vmax,
+                                                           int first, StreamState *st)
+{
+    __shared__ unsigned long long red[kThreads / 32];
+    const long long quad = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long luma = 0;
+    if (quad < npx / 4) {
+        uint4 *S4 = reinterpret_cast<uint4 *>(S) + 3 * quad;
+        uint4 *Q4 = reinterpret_cast<uint4 *>(Q) + 3 * quad;
+        uint32_t *mn4 = reinterpret_cast<uint32_t *>(vmin) + 3 * quad;
+        uint32_t *mx4 = reinterpret_cast<uint32_t *>(vmax) + 3 * quad;
+        uint32_t s[12], q[12], mn[3], mx[3];
+        if (first) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s[k] = q[k] = 0u;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                mn[k] = 0xffffffffu;
+                mx[k] = 0u;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint4 a = S4[k], b = Q4[k];
+                s[4 * k] = a.x; s[4 * k + 1] = a.y; s[4 * k + 2] = a.z; s[4 * k + 3] = a.w;
+                q[4 * k] = b.x; q[4 * k + 1] = b.y; q[4 * k + 2] = b.z; q[4 * k + 3] = b.w;
+                mn[k] = mn4[k];
+                mx[k] = mx4[k];
+            }
+        }
+        for (int i = 0; i < nf; ++i) {
+            const uint32_t *f = reinterpret_cast<const uint32_t *>(frames + (long long)i * npx * 3) + 3 * quad;
+            uint32_t wv[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                wv[k] = __ldg(f + k);
+                mn[k] = __vminu4(mn[k], wv[k]);
+                mx[k] = __vmaxu4(mx[k], wv[k]);
+            }
+            uint32_t v[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                v[k] = (wv[k >> 2] >> (8 * (k & 3))) & 0xffu;
+                s[k] += v[k];
+                q[k] += v[k] * v[k];
+            }
+#pragma unroll
+            for (int px = 0; px < 4; ++px)
+                luma += (77u * v[3 * px] + 150u * v[3 * px + 1] + 29u * v[3 * px + 2] + 128u) >> 8;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            S4[k] = make_uint4(s[4 * k], s[4 * k + 1], s[4 * k + 2], s[4 * k + 3]);
+            Q4[k] = make_uint4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+            mn4[k] = mn[k];
+            mx4[k] = mx[k];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) luma += __shfl_xor_sync(0xffffffffu, luma, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = luma;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        if (t) atomicAdd(&st->learn_luma, t);
+    }
+}
+
 // Band edge predicate P(L): n L <= S and kd^2 (S - n L)^2 >= kn^2 D (low side).
 __device__ __forceinline__ bool low_ok(long long L, long long s, long long n, long long kd2,
                                        long long knD)
@@ -98,16 +174,19 @@ __global__ void __launch_bounds__(kThreads) k_learn_band(const uint32_t *S, cons
     const long long kd2 = (long long)kd * kd, knD = (long long)kn * kn * D;
     // L' = max(L_k, -1) and H' = min(H_k, 256) give the same clamped band as
     // the unbounded edges; the predicates are monotone, so start from a
-    // floating estimate and step to the exact edge.
-    const double ksig = (double)kn / (double)kd * sqrt((double)D) / (double)n;
-    const double mu = (double)s / (double)n;
+    // floating estimate and step to the exact edge.  The estimate is FP32
+    // (FP64 is slow on this part) and lands within a step of the edge, so the
+    // predicates are only evaluated next to it, where kd^2 gap^2 stays near
+    // kn^2 D, below 2^63 for n <= 65535 and 8-bit k.
+    const float ksig = (float)kn / (float)kd * sqrtf(__ll2float_rn(D)) / (float)n;
+    const float mu = __ll2float_rn(s) / (float)n;
     const long long lmax = s / nn;   // largest L with n L <= S
-    long long L = (long long)floor(mu - ksig);
+    long long L = (long long)floorf(mu - ksig);
     L = max(-1ll, min(L, lmax));
     while (L + 1 <= lmax && low_ok(L + 1, s, nn, kd2, knD)) ++L;
     while (L > -1 && !low_ok(L, s, nn, kd2, knD)) --L;
     const long long hmin = (s + nn - 1) / nn;   // smallest H with n H >= S
-    long long H = (long long)ceil(mu + ksig);
+    long long H = (long long)ceilf(mu + ksig);
     H = min(256ll, max(H, hmin));
     while (H - 1 >= hmin && high_ok(H - 1, s, nn, kd2, knD)) --H;
     while (H < 256 && !high_ok(H, s, nn, kd2, knD)) ++H;
@@ -138,8 +217,18 @@ cudaError_t launch_learn_accum(const uint8_t *frames, int nf, long long npx, uin
                                uint32_t *Q, uint8_t *vmin, uint8_t *vmax, int first,
                                StreamState *st, cudaStream_t cs)
 {
-    const unsigned grid = (unsigned)((npx + kThreads - 1) / kThreads);
-    k_learn_accum<<<grid, kThreads, 0, cs>>>(frames, nf, npx, S, Q, vmin, vmax, first, st);
+    const bool vec = (npx % 4) == 0 && (reinterpret_cast<uintptr_t>(frames) & 3u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(S) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(Q) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(vmin) & 3u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(vmax) & 3u) == 0;
+    if (vec) {
+        const unsigned grid = (unsigned)((npx / 4 + kThreads - 1) / kThreads);
+        k_learn_accum4<<<grid, kThreads, 0, cs>>>(frames, nf, npx, S, Q, vmin, vmax, first, st);
+    } else {
+        const unsigned grid = (unsigned)((npx + kThreads - 1) / kThreads);
+        k_learn_accum<<<grid, kThreads, 0, cs>>>(frames, nf, npx, S, Q, vmin, vmax, first, st);
+    }
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ HMI_ERR_NOT_LEARNED = -2
 HMI_ERR_NO_MEMORY = -3
 HMI_ERR_DEVICE = -4
 HMI_ERR_DEVICE_TIMEOUT = -5
+HMI_LEARNING = 1          # server results only: a background-learning frame
 
 
 class hmi_params(ctypes.Structure):
@@ -49,6 +50,13 @@ class hmi_server_result(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_int32), ("status", ctypes.c_int32), ("tag", ctypes.c_uint64),
                 ("submit_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64),
                 ("pointer", hmi_pointer)]
+
+
+class hmi_server_round(ctypes.Structure):
+    _fields_ = [("start_ns", ctypes.c_uint64), ("issued_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("frames", ctypes.c_int32),
+                ("learning", ctypes.c_int32), ("streams", ctypes.c_int32),
+                ("replanned", ctypes.c_int32)]
 
 
 POINTER_DTYPE = np.dtype([(k, np.dtype(t._type_)) for k, t in hmi_pointer._fields_])
@@ -93,6 +101,7 @@ SIGNATURES = {
     "hmi_server_stats": (_I, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_uint64),
                               ctypes.POINTER(ctypes.c_uint64)]),
     "hmi_server_now_ns": (ctypes.c_uint64, []),
+    "hmi_server_rounds": (_I, [_P, ctypes.POINTER(hmi_server_round), _I]),
     "hmi_last_error": (_I, []),
     "hmi_status_string": (ctypes.c_char_p, [_I]),
 }
@@ -302,7 +311,9 @@ def hmi_server_destroy(v: int) -> None:
 
 
 def hmi_server_admit(v: int, w: int, h: int, params: hmi_params | None, learn_frames, n: int) -> int:
-    """Returns the stream id; raises HmiError(HMI_ERR_NO_MEMORY) when refused."""
+    """Returns the stream id; raises HmiError(HMI_ERR_NO_MEMORY) when refused.
+    learn_frames None: the stream's first n submitted frames are its learning
+    frames (their results carry status HMI_LEARNING)."""
     sid = ctypes.c_int()
     _check(load().hmi_server_admit(v, w, h, ctypes.byref(params) if params is not None else None,
                                    _addr(learn_frames), n, ctypes.byref(sid)), "hmi_server_admit")
@@ -338,6 +349,16 @@ def hmi_server_stats(v: int) -> tuple[int, int, int]:
 
 def hmi_server_now_ns() -> int:
     return load().hmi_server_now_ns()
+
+
+def hmi_server_rounds(v: int, max_rounds: int = 16384) -> np.ndarray:
+    """The dispatcher's most recent rounds (oldest first) as a structured array."""
+    buf = (hmi_server_round * max_rounds)()
+    n = load().hmi_server_rounds(v, buf, max_rounds)
+    if n < 0:
+        raise HmiError(n, "hmi_server_rounds")
+    dt = np.dtype([(k, np.dtype(t._type_)) for k, t in hmi_server_round._fields_])
+    return np.frombuffer(bytes(buf)[: n * ctypes.sizeof(hmi_server_round)], dtype=dt).copy()
 
 
 def hmi_last_error() -> int:

@@ -1,21 +1,35 @@
 """Replay of camera arrival traces against the continuous-batching server.
 
-The workload: many camera streams of the 256-stream resolution mix, each
-sending frames at 30 fps with exponential inter-arrival times, optionally
-joining (Poisson arrivals) and leaving (exponential lifetimes) while the trace
-runs, with admission limited by the server's device-memory budget (a refused
-stream retries every 100 ms).  The trace is replayed in wall-clock time; the
-latency of a frame is its completion time minus its scheduled arrival time.
+The workload: camera streams of the 256-stream resolution mix (128 at
+320x240, 64 at 640x480, 48 at 1280x720, 16 at 1920x1080), each sending frames
+at 30 fps with exponential inter-arrival times, joining (Poisson arrivals) and
+leaving (exponential lifetimes) while the trace runs, with admission limited
+by the server's device-memory budget (a refused stream retries every 100 ms,
+and its frames are lost until it is admitted).  A stream's first n_learn
+frames are its user-free learning frames (Sec. 2: the background is learned
+without the user); the server accumulates them online as they arrive.  The
+trace is replayed in wall-clock time; the latency of a frame is its completion
+time minus its scheduled arrival time, so a submitter running late counts
+against the server, never for it.
 
-Two ways to serve the same trace are provided: ``run_served`` (the library's
-server: resident streams, one tick over every stream with a pending frame) and
-``run_plain`` (one synchronous ``hmi_process_frame`` call per frame, in
-arrival order, from one worker thread).  This module drives the C ABI only; it
-holds none of the method's arithmetic.
+Two ways to serve the same trace:
+  * ``run_served``: the library's server (resident streams, one tick over
+    every stream with a pending frame, online learning);
+  * ``run_plain``: one synchronous ``hmi_process_frame`` call per frame, in
+    arrival order, from one worker thread, with every stream created and
+    learned before the trace starts (its learning frames are skipped, so the
+    plain form does no learning work while it is timed).
+
+Frames come from a bank of pinned host buffers per generator stream: a ring of
+``LEARN_RING`` distinct learning frames, cycled through the n_learn learning
+frames, and a ring of run frames.  This module drives the C ABI only; it holds
+none of the method's arithmetic.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
+import gc
 import heapq
 import threading
 import time
@@ -27,12 +41,16 @@ from . import hmi, synth
 
 CFG = 5
 FPS = 30.0
+N_LEARN = 30
+LEARN_RING = 8
+RETRY_S = 0.1
+SLO_MS = 5.0
 
 
 @dataclass
 class StreamPlan:
     idx: int          # trace-wide stream number
-    src: int          # generator stream of configuration 5 (idx mod 256)
+    src: int          # generator stream of the 256-stream mix (idx mod 256)
     w: int
     h: int
     start: float      # seconds from trace start
@@ -44,6 +62,10 @@ class StreamPlan:
 class Trace:
     duration: float
     streams: list
+
+    @property
+    def frames(self) -> int:
+        return int(sum(len(sp.arrivals) for sp in self.streams))
 
 
 def make_trace(duration: float, n_streams: int = 256, rate_scale: float = 1.0, churn: bool = True,
@@ -76,134 +98,259 @@ def make_trace(duration: float, n_streams: int = 256, rate_scale: float = 1.0, c
 
 
 class FrameBank:
-    """Learning frames and a small ring of run frames per generator stream,
-    generated once (pinned host memory, so by-reference submits copy fast)."""
+    """Pinned host frames per generator stream: LEARN_RING learning frames and
+    `run_ring` run frames, generated once."""
 
-    def __init__(self, srcs, n_learn: int, ring: int = 2):
+    def __init__(self, srcs, learn_ring: int = LEARN_RING, run_ring: int = 2):
         import torch
-        self.learn, self.ring = {}, {}
+        self.learn, self.run, self.addr = {}, {}, {}
         for s in sorted(set(srcs)):
-            self.learn[s] = synth.learn_frames(CFG, s, n_learn)
-            frames = []
-            for t in range(ring):
-                f = torch.from_numpy(synth.run_frame(CFG, s, t)).pin_memory()
-                frames.append(f)
-            self.ring[s] = frames
+            lf = synth.learn_frames(CFG, s, learn_ring)
+            self.learn[s] = [torch.from_numpy(np.ascontiguousarray(f)).pin_memory() for f in lf]
+            self.run[s] = [torch.from_numpy(synth.run_frame(CFG, s, t)).pin_memory()
+                           for t in range(run_ring)]
+            self.addr[s] = ([f.data_ptr() for f in self.learn[s]], [f.data_ptr() for f in self.run[s]])
+
+    def frame_addr(self, src: int, k: int, n_learn: int) -> int:
+        """Address of the k-th frame a stream of generator stream `src` sends."""
+        la, ra = self.addr[src]
+        return la[k % len(la)] if k < n_learn else ra[(k - n_learn) % len(ra)]
+
+    def learn_block(self, src: int, n_learn: int) -> np.ndarray:
+        """The n_learn learning frames, contiguous (for up-front learning)."""
+        ring = self.learn[src]
+        return np.stack([ring[k % len(ring)].numpy() for k in range(n_learn)])
 
 
-def _stats(lat_ms, wall_s, nframes, dropped):
-    lat = np.sort(np.asarray(lat_ms)) if lat_ms else np.zeros(1)
-    return {"frames": int(nframes), "dropped": int(dropped), "wall_s": wall_s,
-            "frames_per_s": nframes / wall_s if wall_s > 0 else 0.0,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+RESULT_DTYPE = np.dtype([("stream_id", np.int32), ("status", np.int32), ("tag", np.uint64),
+                         ("submit_ns", np.uint64), ("done_ns", np.uint64),
+                         ("pointer", hmi.POINTER_DTYPE)])
+assert RESULT_DTYPE.itemsize == ctypes.sizeof(hmi.hmi_server_result)
+
+
+@contextlib.contextmanager
+def _no_gc_pauses():
+    """The replay is a load generator: a cyclic-GC pass over the interpreter's
+    objects would stall it for tens of ms and show up as server latency."""
+    gc.collect()
+    was = gc.isenabled()
+    gc.disable()
+    try:
+        yield
+    finally:
+        if was:
+            gc.enable()
+
+
+def _latency_stats(lat_ms) -> dict:
+    lat = np.sort(np.asarray(lat_ms, dtype=np.float64)) if len(lat_ms) else np.zeros(1)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "max_ms": float(lat[-1])}
 
 
-def _events(trace: Trace):
-    ev = []
-    for sp in trace.streams:
-        ev.append((sp.start, 0, sp.idx, -1))           # start (admission attempt)
-        for n, t in enumerate(sp.arrivals):
-            ev.append((float(t), 1, sp.idx, n))        # frame arrival
-        ev.append((sp.end, 2, sp.idx, -1))             # end
-    heapq.heapify(ev)
-    return ev
+def _arrivals(trace: Trace):
+    """All frame arrivals sorted by time: (t, stream idx, frame number)."""
+    t = np.concatenate([sp.arrivals for sp in trace.streams] + [np.zeros(0)])
+    idx = np.concatenate([np.full(len(sp.arrivals), sp.idx) for sp in trace.streams] + [np.zeros(0, int)])
+    num = np.concatenate([np.arange(len(sp.arrivals)) for sp in trace.streams] + [np.zeros(0, int)])
+    o = np.argsort(t, kind="stable")
+    return t[o].tolist(), idx[o].astype(int).tolist(), num[o].astype(int).tolist()
 
 
-def run_served(trace: Trace, bank: FrameBank, budget_bytes: int, n_learn: int,
+def run_served(trace: Trace, bank: FrameBank, budget_bytes: int, n_learn: int = N_LEARN,
                max_queue: int = 8) -> dict:
+    with _no_gc_pauses():
+        return _run_served(trace, bank, budget_bytes, n_learn, max_queue)
+
+
+def _run_served(trace: Trace, bank: FrameBank, budget_bytes: int, n_learn: int,
+                max_queue: int) -> dict:
+    lib = hmi.load()
     srv = hmi.hmi_server_create(budget_bytes, max_queue)
     plans = {sp.idx: sp for sp in trace.streams}
-    sid, arrival = {}, {}
-    lat, got = [], [0]
-    refused = [0]
+    sid = {}
+    arrival = {}                    # tag -> scheduled arrival (ns), outstanding
+    lat, lat_at, counts = [], [], {"learn": 0, "errors": 0}
     stop = threading.Event()
-    buf = (hmi.hmi_server_result * 256)()
+    buf = (hmi.hmi_server_result * 1024)()
+    view = np.frombuffer(buf, dtype=RESULT_DTYPE)
 
     def poller():
-        while not stop.is_set() or got[0] < len(arrival):
-            n = hmi.hmi_server_poll(srv, buf, 200)
-            for k in range(n):
-                r = buf[k]
-                a = arrival.pop(r.tag, None)
-                if a is not None:
-                    lat.append((r.done_ns - a) / 1e6)
-            if stop.is_set() and not arrival:
-                break
+        deadline = None
+        while True:
+            n = lib.hmi_server_poll(srv, buf, len(buf), 2000)
+            if n > 0:
+                for tg, st, dn in zip(view["tag"][:n].tolist(), view["status"][:n].tolist(),
+                                      view["done_ns"][:n].tolist()):
+                    a = arrival.pop(tg, None)
+                    if a is None:
+                        continue
+                    if st == hmi.HMI_OK:
+                        lat.append((dn - a) * 1e-6)
+                        lat_at.append(a)
+                    elif st == hmi.HMI_LEARNING:
+                        counts["learn"] += 1
+                    else:
+                        counts["errors"] += 1
+            if stop.is_set():
+                if not arrival:
+                    break
+                deadline = deadline or time.monotonic() + 30.0
+                if time.monotonic() > deadline:
+                    break
 
-    ev = _events(trace)
-    pending_retry = []
+    # stream starts / ends and retries, merged with the sorted frame arrivals
+    ctl = []
+    for sp in trace.streams:
+        ctl.append((sp.start, 0, sp.idx))
+        ctl.append((sp.end, 2, sp.idx))
+    heapq.heapify(ctl)
+    at, ai, _ = _arrivals(trace)
     th = threading.Thread(target=poller, daemon=True)
     th.start()
-    t0 = hmi.hmi_server_now_ns()
-    dropped, tag = 0, 0
-    while ev or pending_retry:
-        if pending_retry and (not ev or pending_retry[0][0] <= ev[0][0]):
-            item = heapq.heappop(pending_retry)
+    now = lib.hmi_server_now_ns
+    submit = lib.hmi_server_submit_ref
+    refused = lost = dropped = admitted = 0
+    drop_t, lag = [], []
+    sent = {}                       # frames each admitted stream has been sent
+    tag, j, na = 0, 0, len(at)
+    t0 = now()
+    while j < na or ctl:
+        if ctl and (j >= na or ctl[0][0] <= at[j]):
+            t, kind, idx = heapq.heappop(ctl)
         else:
-            item = heapq.heappop(ev)
-        t, kind, idx, n = item
-        delay = t0 + int(t * 1e9) - hmi.hmi_server_now_ns()
-        if delay > 0:
-            time.sleep(delay / 1e9)
-        sp = plans[idx]
-        if kind == 0:
+            t, kind, idx = at[j], 1, ai[j]
+            j += 1
+        due = t0 + int(t * 1e9)
+        delay = due - now()
+        if delay > 150_000:
+            time.sleep((delay - 100_000) * 1e-9)
+        if kind == 1:
+            s = sid.get(idx)
+            if s is None:
+                lost += 1                     # stream not (yet) admitted
+                continue
+            k = sent[idx]
+            sent[idx] = k + 1
+            tag += 1
+            arrival[tag] = due
+            lag.append(now() - due)
+            if submit(srv, s, bank.frame_addr(plans[idx].src, k, n_learn), tag) != hmi.HMI_OK:
+                arrival.pop(tag, None)
+                dropped += 1                  # the stream's queue is full
+                drop_t.append(t)
+        elif kind == 0:
+            sp = plans[idx]
             try:
-                sid[idx] = hmi.hmi_server_admit(srv, sp.w, sp.h, None, bank.learn[sp.src], n_learn)
+                sid[idx] = hmi.hmi_server_admit(srv, sp.w, sp.h, None, None, n_learn)
+                sent[idx] = 0                 # the camera's first frames are user-free
+                admitted += 1
             except hmi.HmiError as e:
                 if e.status != hmi.HMI_ERR_NO_MEMORY:
                     raise
-                refused[0] += 1
-                if t + 0.1 < sp.end:
-                    heapq.heappush(pending_retry, (t + 0.1, 0, idx, -1))
-        elif kind == 1:
-            if idx not in sid:
-                dropped += 1
-                continue
-            tag += 1
-            arrival[tag] = t0 + int(t * 1e9)
-            frame = bank.ring[sp.src][n % len(bank.ring[sp.src])]
-            if hmi.hmi_server_submit_ref(srv, sid[idx], frame, tag) != hmi.HMI_OK:
-                arrival.pop(tag, None)
-                dropped += 1
-            else:
-                got[0] += 1
-        else:
-            if idx in sid:
-                hmi.hmi_server_release(srv, sid.pop(idx))
+                refused += 1
+                if t + RETRY_S < sp.end:
+                    heapq.heappush(ctl, (t + RETRY_S, 0, idx))
+        elif idx in sid:
+            hmi.hmi_server_release(srv, sid.pop(idx))
+    t_end = now()
     stop.set()
-    th.join(timeout=30)
-    wall = (hmi.hmi_server_now_ns() - t0) / 1e9
+    th.join(timeout=60)
+    wall = (t_end - t0) * 1e-9
     _, ticks, frames = hmi.hmi_server_stats(srv)
+    rounds = hmi.hmi_server_rounds(srv)
     hmi.hmi_server_destroy(srv)
-    out = _stats(lat, wall, len(lat), dropped)
-    out.update({"ticks": ticks, "frames_per_tick": frames / max(ticks, 1),
-                "admission_refusals": refused[0]})
+    out = {"frames": len(lat), "frames_per_s": len(lat) / wall, "wall_s": wall,
+           "learning_frames": counts["learn"], "errors": counts["errors"],
+           "dropped_queue_full": dropped, "lost_not_admitted": lost,
+           "streams_admitted": admitted, "admission_refusals": refused,
+           "ticks": ticks, "frames_per_tick": frames / max(ticks, 1),
+           "offered_frames_per_s": trace.frames / trace.duration}
+    out.update(_latency_stats(lat))
+    # the start (all streams admitted and learning at once) against the rest
+    warm = t0 + int(1e9)
+    steady = [x for x, a in zip(lat, lat_at) if a >= warm]
+    out["after_first_s"] = {"p99_ms": _latency_stats(steady)["p99_ms"] if steady else None,
+                            "dropped_queue_full": sum(1 for x in drop_t if x >= 1.0)}
+    out["submit_lag_ms_p99"] = float(np.percentile(np.asarray(lag, np.float64), 99)) * 1e-6 if lag else 0.0
+    if len(rounds):
+        busy = (rounds["done_ns"] - rounds["start_ns"]).astype(np.float64) * 1e-6
+        out["round_ms"] = {"p50": float(np.percentile(busy, 50)), "p99": float(np.percentile(busy, 99)),
+                           "of_last": int(len(rounds))}
     return out
 
 
-def run_plain(trace: Trace, bank: FrameBank, n_learn: int) -> dict:
-    """One hmi_process_frame per frame, in arrival order, one worker thread."""
+def run_plain(trace: Trace, bank: FrameBank, n_learn: int = N_LEARN, max_backlog_s: float = 1.0) -> dict:
+    """One synchronous hmi_process_frame per frame, in arrival order, from one
+    thread; streams are created and learned before the trace starts.  A replay
+    that falls more than max_backlog_s behind the trace stops there
+    ("saturated"): its latency only grows from then on."""
+    with _no_gc_pauses():
+        return _run_plain(trace, bank, n_learn, max_backlog_s)
+
+
+def _run_plain(trace: Trace, bank: FrameBank, n_learn: int, max_backlog_s: float) -> dict:
+    lib = hmi.load()
     streams = {}
     for sp in trace.streams:
         s = hmi.Stream(sp.w, sp.h)
-        s.learn(bank.learn[sp.src])
+        s.learn(bank.learn_block(sp.src, n_learn))
         streams[sp.idx] = s
-    arr = [(float(t), sp.idx, n) for sp in trace.streams for n, t in enumerate(sp.arrivals)]
-    arr.sort()
+    handle = {k: s.handle for k, s in streams.items()}
+    src = {sp.idx: sp.src for sp in trace.streams}
+    at, ai, an = _arrivals(trace)
     lat = []
     ptr = hmi.hmi_pointer()
-    t0 = hmi.hmi_server_now_ns()
-    for t, idx, n in arr:
+    pref = ctypes.byref(ptr)
+    now = lib.hmi_server_now_ns
+    proc = lib.hmi_process_frame
+    errors, saturated = 0, False
+    limit = int(max_backlog_s * 1e9)
+    t0 = now()
+    for t, idx, n in zip(at, ai, an):
+        if n < n_learn:
+            continue                          # learned up front
         due = t0 + int(t * 1e9)
-        delay = due - hmi.hmi_server_now_ns()
-        if delay > 0:
-            time.sleep(delay / 1e9)
-        sp_src = trace.streams[idx].src
-        frame = bank.ring[sp_src][n % len(bank.ring[sp_src])]
-        hmi.hmi_process_frame(streams[idx].handle, frame, None, ptr)
-        lat.append((hmi.hmi_server_now_ns() - due) / 1e6)
-    wall = (hmi.hmi_server_now_ns() - t0) / 1e9
+        delay = due - now()
+        if delay > 150_000:
+            time.sleep((delay - 100_000) * 1e-9)
+        elif -delay > limit:
+            saturated = True
+            break
+        if proc(handle[idx], bank.frame_addr(src[idx], n, n_learn), None, pref) != hmi.HMI_OK:
+            errors += 1
+        lat.append((now() - due) * 1e-6)
+    wall = (now() - t0) * 1e-9
     for s in streams.values():
         s.close()
-    return _stats(lat, wall, len(lat), 0)
+    out = {"frames": len(lat), "frames_per_s": len(lat) / wall, "wall_s": wall, "errors": errors,
+           "offered_frames_per_s": trace.frames / trace.duration, "saturated": saturated}
+    out.update(_latency_stats(lat))
+    return out
+
+
+DROP_BUDGET = 0.01
+
+
+def meets_slo(r: dict) -> bool:
+    """p99 within SLO_MS, no errors, and at most DROP_BUDGET of the offered
+    frames refused because a stream's queue was full."""
+    offered = r["offered_frames_per_s"] * r["wall_s"]
+    return (not r.get("saturated", False) and r["p99_ms"] <= SLO_MS and r.get("errors", 0) == 0 and
+            r.get("dropped_queue_full", 0) <= DROP_BUDGET * offered)
+
+
+def sweep(bank: FrameBank, rates, duration: float, n_learn: int = N_LEARN, seed: int = 1907043935):
+    """Served and plain forms over the same traces at each arrival-rate scale
+    (no memory limit on admission, so that only the serving form differs)."""
+    rows = []
+    for r in rates:
+        tr = make_trace(duration, rate_scale=r, seed=seed + int(r * 1000))
+        srv = run_served(tr, bank, 1 << 50, n_learn)
+        pln = run_plain(tr, bank, n_learn)
+        rows.append({"rate_scale": r, "served": srv, "plain": pln})
+    best = {}
+    for arm in ("served", "plain"):
+        ok = [row[arm]["frames_per_s"] for row in rows if meets_slo(row[arm])]
+        best[arm] = max(ok) if ok else 0.0
+    return rows, best

@@ -28,6 +28,8 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_params) == 28
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
+    assert ctypes.sizeof(hmi.hmi_server_result) == 72
+    assert ctypes.sizeof(hmi.hmi_server_round) == 40
 
 
 def test_defaults_and_status_strings():
@@ -73,3 +75,13 @@ def test_create_without_gpu_reports_an_error():
         pytest.skip("a GPU is present")
     assert hmi.load().hmi_create_stream(64, 48, None) is None
     assert hmi.hmi_last_error() in (hmi.HMI_ERR_DEVICE, hmi.HMI_ERR_NO_MEMORY)
+
+
+def test_status_constants_match_header():
+    import re
+    text = open(os.path.join(ROOT, "include", "hmi.h")).read()
+    found = dict((k, int(v)) for k, v in re.findall(r"#define (HMI_[A-Z_]+) \(?(-?\d+)\)?", text))
+    names = [k for k in dir(hmi) if re.fullmatch(r"HMI_(OK|ERR_[A-Z_]+|LEARNING)", k)]
+    assert found and set(found) == set(names)
+    for k in names:
+        assert getattr(hmi, k) == found[k], k

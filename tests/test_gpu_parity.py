@@ -303,6 +303,41 @@ def test_batch_config4_sync_async_graph():
             g.close()
 
 
+def _pinned(a: np.ndarray, offset: int = 0):
+    """A page-locked host copy of `a`, starting `offset` bytes into its buffer."""
+    buf = torch.empty(a.nbytes + 64, dtype=torch.uint8).pin_memory()
+    base = (-buf.data_ptr()) % 16 + offset
+    view = buf[base:base + a.nbytes]
+    view.numpy()[:] = a.reshape(-1)
+    return view
+
+
+def test_batch_pinned_host_frames():
+    """Frames in page-locked host memory, aligned and misaligned, through the
+    synchronous batch form; an asynchronous call with a host frame is refused;
+    every result equals the oracle's."""
+    idx = [0, 20, 33, 50, 61, 63]
+    gs, os_ = _batch_streams(4, idx)
+    b = hmi.hmi_batch_create([g.handle for g in gs])
+    try:
+        for t in range(2):
+            frames = [synth.run_frame(4, i, t) for i in idx]
+            pins = [_pinned(f, offset=(1 if (k == 2 and t == 1) else 0)) for k, f in enumerate(frames)]
+            masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+            ptrs = np.zeros(len(idx), hmi.POINTER_DTYPE)
+            hmi.hmi_batch_process(b, pins, masks, ptrs)
+            plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
+            _compare_batch(gs, os_, frames, masks, plist, f"pinned t={t}")
+        dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+        with pytest.raises(hmi.HmiError) as e:
+            hmi.hmi_batch_process_async(b, pins, dmasks, None, torch.cuda.current_stream().cuda_stream, False)
+        assert e.value.status == hmi.HMI_ERR_INVALID_ARG
+    finally:
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
+
+
 def test_batch_group_count_does_not_change_results():
     """The same streams processed with 1, 3 and 5 concurrent groups per tick
     give identical masks, labels and pointers (and match the oracle)."""

@@ -82,8 +82,63 @@ def test_served_results_equal_alone_and_in_order():
 
 
 def test_trace_replay_small():
-    tr = serve.make_trace(1.0, n_streams=16, rate_scale=1.0, churn=True, lifetime_mean=2.0)
-    bank = serve.FrameBank([sp.src for sp in tr.streams], n_learn=3)
-    budget = 12 * hmi.hmi_stream_device_bytes(640, 480)
+    """A 1.5 s trace of 16 churning streams under a budget below their demand:
+    refusals happen, learning frames come back as such, nothing errs, and the
+    plain form serves the same frames."""
+    tr = serve.make_trace(1.5, n_streams=16, rate_scale=1.0, churn=True, lifetime_mean=2.0)
+    bank = serve.FrameBank([sp.src for sp in tr.streams], learn_ring=3, run_ring=2)
+    assert all(sp.w == 320 for sp in tr.streams)
+    budget = 10 * hmi.hmi_stream_device_bytes(320, 240)
     out = serve.run_served(tr, bank, budget, 3)
-    assert out["frames"] > 0 and out["p99_ms"] < 1000
+    assert out["errors"] == 0 and out["admission_refusals"] > 0 and out["lost_not_admitted"] > 0
+    assert out["frames"] > 0 and 0 < out["learning_frames"] <= 3 * out["streams_admitted"]
+    assert out["p99_ms"] < 1000
+    pl = serve.run_plain(tr, bank, 3)
+    assert pl["errors"] == 0 and pl["frames"] > 0
+
+
+def test_online_learning_equals_learned_up_front():
+    """Streams admitted without learning frames take their first n submitted
+    frames as the user-free learning frames (status HMI_LEARNING, empty
+    pointer) while another stream is processed in the same ticks; their later
+    results equal those of streams learned from the same frames up front."""
+    srcs = [3, 70, 150, 250]
+    n_learn, nframes = 6, 5
+    learn = {s: synth.learn_frames(5, s, n_learn) for s in srcs}
+    frames = {s: [synth.run_frame(5, s, t) for t in range(nframes)] for s in srcs}
+    alone = {}
+    for s in srcs:
+        st = hmi.Stream(*synth.shape(5, s))
+        st.learn(learn[s])
+        alone[s] = [st.process(f, mask=False)[1] for f in frames[s]]
+        st.close()
+    srv = hmi.hmi_server_create(1 << 34, 16)
+    busy = srcs[0]            # learned up front, busy while the others learn
+    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), None,
+                                   learn[s] if s == busy else None, n_learn) for s in srcs}
+    seq = {s: ([] if s == busy else list(learn[s])) + frames[s] for s in srcs}
+    tag_of, tag = {}, 0
+    for k in range(max(len(v) for v in seq.values())):
+        for s in srcs:
+            if k < len(seq[s]):
+                tag += 1
+                tag_of[tag] = (s, k)
+                assert hmi.hmi_server_submit(srv, ids[s], np.ascontiguousarray(seq[s][k]), tag) == hmi.HMI_OK
+    got = {}
+    buf = (hmi.hmi_server_result * 64)()
+    while len(got) < tag:
+        n = hmi.hmi_server_poll(srv, buf, 2_000_000)
+        assert n > 0, "server stalled"
+        for i in range(n):
+            r = buf[i]
+            got[tag_of[r.tag]] = (r.status, r.pointer.as_dict())
+    empty = {"valid": 0, "click": 0, "x": -1.0, "y": -1.0, "area": 0,
+             "x0": -1, "y0": -1, "x1": -1, "y1": -1, "label": -1}
+    for s in srcs:
+        skip = 0 if s == busy else n_learn
+        for k in range(skip):
+            assert got[(s, k)] == (hmi.HMI_LEARNING, empty), (s, k)
+        for t in range(nframes):
+            st, p = got[(s, skip + t)]
+            assert st == hmi.HMI_OK and p == alone[s][t], (s, t)
+    hmi.hmi_server_destroy(srv)
