@@ -168,13 +168,20 @@ HMI_API int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_
 HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                             hmi_pointer *ptrs, void *cuda_stream, int use_graph);
 
-/* Kernel timing of the batch's classification kernel (the per-pixel HBM pass).
- * hmi_batch_profile(b, max_ticks) starts recording one CUDA-event pair around
- * that kernel for each of the next max_ticks ticks (0 stops); the plan must
- * have one group (HMI_ERR_INVALID_ARG otherwise), so the launch is timed alone.
- * hmi_batch_profile_read waits for them and returns the number of ticks timed
- * and the sum of their durations in milliseconds. */
+/* Kernel timing of a batch's ticks.  A tick runs HMI_TICK_KERNELS kernels in
+ * this order: 0 luma sums and gains, 1 background band test (the per-pixel
+ * HBM pass), 2 gray and hue tests of out-of-band pixels, 3 morphology, 4
+ * block components, 5 merge and pointer.  hmi_batch_profile(b, max_ticks)
+ * starts recording CUDA events between the kernels for each of the next
+ * max_ticks ticks (0 stops); the plan must have one group
+ * (HMI_ERR_INVALID_ARG otherwise), so that every launch is timed alone.
+ * hmi_batch_profile_kernels waits for them and gives the number of ticks timed
+ * and, for the first n_kernels kernels (1..HMI_TICK_KERNELS), the sum of their
+ * durations in milliseconds; hmi_batch_profile_read gives that sum for kernel
+ * 1 alone. */
+#define HMI_TICK_KERNELS 6
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
+HMI_API int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels);
 HMI_API int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms);
 
 /* FP32 mean and standard deviation of the learned background per pixel and

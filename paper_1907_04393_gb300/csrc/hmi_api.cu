@@ -249,10 +249,14 @@ struct hmi_batch {
     cudaStream_t cs = nullptr;    // origin stream of the synchronous form and of graph capture
     cudaEvent_t ev_fork = nullptr;
     int num_sms = 1;
-    cudaGraph_t graph_src[kRing] = {};   // kept alive: its event-node handles retarget events
-    cudaGraphExec_t graph[kRing] = {};
-    cudaGraphNode_t ev_node[kRing][2] = {};
-    cudaEvent_t dummy_ev[2] = {};
+    cudaGraphExec_t graph[kRing] = {};     // plain tick graphs
+    // profiling tick graphs (single group): an event-record node before the
+    // first kernel and after each, retargeted to the tick's events at launch;
+    // the source graph is kept alive for its node handles
+    cudaGraph_t pgraph_src[kRing] = {};
+    cudaGraphExec_t pgraph[kRing] = {};
+    cudaGraphNode_t ev_node[kRing][kTickKernels + 1] = {};
+    cudaEvent_t dummy_ev[kTickKernels + 1] = {};
     // profiling of the classification kernel (single-group plans)
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
@@ -284,6 +288,7 @@ void fill_devstream(hmi_stream *s)
     D.tiles_x = L.tiles_x;
     D.strips_x = L.strips_x;
     D.fpitch = L.fpitch;
+    D.cpr_magic = (uint32_t)(((1ull << 32) + 2ull * L.nwords - 1) / (2ull * L.nwords));
     D.gray_tol = s->p.gray_tol;
     D.open_iters = s->p.open_iters;
     D.close_iters = s->p.close_iters;
@@ -310,10 +315,11 @@ void plan_free_graphs(hmi_batch *b)
 {
     for (int i = 0; i < kRing; ++i) {
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
-        if (b->graph_src[i]) cudaGraphDestroy(b->graph_src[i]);
-        b->graph[i] = nullptr;
-        b->graph_src[i] = nullptr;
-        b->ev_node[i][0] = b->ev_node[i][1] = nullptr;
+        if (b->pgraph[i]) cudaGraphExecDestroy(b->pgraph[i]);
+        if (b->pgraph_src[i]) cudaGraphDestroy(b->pgraph_src[i]);
+        b->graph[i] = b->pgraph[i] = nullptr;
+        b->pgraph_src[i] = nullptr;
+        for (auto &nd : b->ev_node[i]) nd = nullptr;
     }
 }
 
@@ -571,7 +577,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
               cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kRing; ++i)
         ok = cudaEventCreateWithFlags(&b->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
-    for (int i = 0; ok && i < 2; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
+    for (int i = 0; ok && i <= kTickKernels; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
     if (!ok) {
         (void)cudaGetLastError();
         batch_free(b);
@@ -596,8 +602,7 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
 // branch; group g starts its luma after group g-1's luma, so the HBM-bound
 // passes of later groups overlap the latency-bound tail of earlier ones.
 // With one group, event records (or event nodes) bracket the classify kernel.
-cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0, cudaEvent_t e1,
-                         bool capture)
+cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEvent_t *ev, bool capture)
 {
     TickIO *dio = b->d_io + (size_t)slot * b->n;
     cudaError_t e;
@@ -608,14 +613,13 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     if (ng == 1) {
         BatchDev bd = b->groups[0].bd;
         bd.io = dio;
-        if ((e = launch_luma(bd, cs, b->num_sms)) != cudaSuccess) return e;
-        if (e0 && (e = cudaEventRecordWithFlags(e0, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
-            return e;
-        if ((e = launch_classify(bd, cs, b->num_sms)) != cudaSuccess) return e;
-        if (e1 && (e = cudaEventRecordWithFlags(e1, cs, capture ? cudaEventRecordExternal : 0)) != cudaSuccess)
-            return e;
-        if ((e = launch_morph_cc(bd, cs, b->num_sms)) != cudaSuccess) return e;
-        return launch_finish(bd, cs);
+        const unsigned flags = capture ? cudaEventRecordExternal : 0;
+        if (ev && (e = cudaEventRecordWithFlags(ev[0], cs, flags)) != cudaSuccess) return e;
+        for (int k = 0; k < kTickKernels; ++k) {
+            if ((e = launch_tick_kernel(k, bd, cs, b->num_sms)) != cudaSuccess) return e;
+            if (ev && (e = cudaEventRecordWithFlags(ev[k + 1], cs, flags)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
     for (int g = 0; g < ng; ++g) {
@@ -624,11 +628,10 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
         bd.io = dio + G.off;
         if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
         if (g > 0 && (e = cudaStreamWaitEvent(G.cs, b->groups[g - 1].ev_luma, 0)) != cudaSuccess) return e;
-        if ((e = launch_luma(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
+        if ((e = launch_tick_kernel(0, bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_luma, G.cs)) != cudaSuccess) return e;
-        if ((e = launch_classify(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
-        if ((e = launch_morph_cc(bd, G.cs, b->num_sms)) != cudaSuccess) return e;
-        if ((e = launch_finish(bd, G.cs)) != cudaSuccess) return e;
+        for (int k = 1; k < kTickKernels; ++k)
+            if ((e = launch_tick_kernel(k, bd, G.cs, b->num_sms)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;
     }
     for (int g = 0; g < ng; ++g)
@@ -636,19 +639,19 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, cudaEvent_t e0
     return cudaSuccess;
 }
 
-int build_graph(hmi_batch *b, int slot)
+// Capture one tick into a graph: the plain form, or (profiling, single group)
+// the form with event-record nodes around each kernel.
+int build_graph(hmi_batch *b, int slot, bool profiling)
 {
     cudaGraph_t g = nullptr;
     HMI_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-    const bool one = b->groups.size() == 1;
-    cudaError_t e = enqueue_tick(b, slot, b->cs, one ? b->dummy_ev[0] : nullptr,
-                                 one ? b->dummy_ev[1] : nullptr, true);
+    cudaError_t e = enqueue_tick(b, slot, b->cs, profiling ? b->dummy_ev : nullptr, true);
     cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return cuda_fail(e != cudaSuccess ? e : e2);
     }
-    if (one) {
+    if (profiling) {
         size_t nn = 0;
         cudaGraphGetNodes(g, nullptr, &nn);
         std::vector<cudaGraphNode_t> nodes(nn);
@@ -659,20 +662,28 @@ int build_graph(hmi_batch *b, int slot)
             if (t != cudaGraphNodeTypeEventRecord) continue;
             cudaEvent_t ev;
             cudaGraphEventRecordNodeGetEvent(nd, &ev);
-            if (ev == b->dummy_ev[0]) b->ev_node[slot][0] = nd;
-            if (ev == b->dummy_ev[1]) b->ev_node[slot][1] = nd;
+            for (int k = 0; k <= kTickKernels; ++k)
+                if (ev == b->dummy_ev[k]) b->ev_node[slot][k] = nd;
         }
-        if (!b->ev_node[slot][0] || !b->ev_node[slot][1]) {
-            cudaGraphDestroy(g);
-            return fail(HMI_ERR_DEVICE);
-        }
+        for (int k = 0; k <= kTickKernels; ++k)
+            if (!b->ev_node[slot][k]) {
+                cudaGraphDestroy(g);
+                return fail(HMI_ERR_DEVICE);
+            }
     }
-    e = cudaGraphInstantiate(&b->graph[slot], g, 0);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return cuda_fail(e);
     }
-    b->graph_src[slot] = g;
+    if (profiling) {
+        b->pgraph[slot] = x;
+        b->pgraph_src[slot] = g;
+    } else {
+        b->graph[slot] = x;
+        cudaGraphDestroy(g);
+    }
     return HMI_OK;
 }
 
@@ -736,27 +747,27 @@ int acquire_slot(hmi_batch *b)
 
 int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
 {
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    const bool prof = b->prof_used < b->prof_max && b->groups.size() == 1;
-    if (prof) {
-        e0 = b->prof_ev[2 * b->prof_used];
-        e1 = b->prof_ev[2 * b->prof_used + 1];
+    const cudaEvent_t *ev = nullptr;
+    if (b->prof_used < b->prof_max && b->groups.size() == 1) {
+        ev = b->prof_ev.data() + (size_t)(kTickKernels + 1) * b->prof_used;
         b->prof_used++;
     }
-    if (use_graph) {
-        if (!b->graph[slot]) {
-            int st = build_graph(b, slot);
+    if (use_graph && ev) {
+        if (!b->pgraph[slot]) {
+            int st = build_graph(b, slot, true);
             if (st != HMI_OK) return st;
         }
-        if (b->groups.size() == 1) {
-            HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][0],
-                                                          e0 ? e0 : b->dummy_ev[0]));
-            HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->graph[slot], b->ev_node[slot][1],
-                                                          e1 ? e1 : b->dummy_ev[1]));
+        for (int k = 0; k <= kTickKernels; ++k)
+            HMI_CUDA(cudaGraphExecEventRecordNodeSetEvent(b->pgraph[slot], b->ev_node[slot][k], ev[k]));
+        HMI_CUDA(cudaGraphLaunch(b->pgraph[slot], cs));
+    } else if (use_graph) {
+        if (!b->graph[slot]) {
+            int st = build_graph(b, slot, false);
+            if (st != HMI_OK) return st;
         }
         HMI_CUDA(cudaGraphLaunch(b->graph[slot], cs));
     } else {
-        HMI_CUDA(enqueue_tick(b, slot, cs, e0, e1, false));
+        HMI_CUDA(enqueue_tick(b, slot, cs, ev, false));
     }
     HMI_CUDA(cudaEventRecord(b->slot_ev[slot], cs));
     b->slot_used[slot] = true;
@@ -1692,26 +1703,38 @@ int hmi_batch_profile(hmi_batch *b, int max_ticks)
     HMI_CUDA(cudaSetDevice(b->dev));
     HMI_CUDA(cudaDeviceSynchronize());
     for (auto e : b->prof_ev) cudaEventDestroy(e);
-    b->prof_ev.assign(2 * (size_t)max_ticks, nullptr);
+    b->prof_ev.assign((size_t)(kTickKernels + 1) * max_ticks, nullptr);
     for (auto &e : b->prof_ev) HMI_CUDA(cudaEventCreate(&e));
     b->prof_max = max_ticks;
     b->prof_used = 0;
     return HMI_OK;
 }
 
+int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels)
+{
+    if (!b || !ticks || !ms || n_kernels < 1 || n_kernels > HMI_TICK_KERNELS) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    for (int k = 0; k < n_kernels; ++k) ms[k] = 0.0;
+    for (int i = 0; i < b->prof_used; ++i) {
+        const cudaEvent_t *ev = b->prof_ev.data() + (size_t)(kTickKernels + 1) * i;
+        HMI_CUDA(cudaEventSynchronize(ev[kTickKernels]));
+        for (int k = 0; k < n_kernels; ++k) {
+            float t = 0.f;
+            HMI_CUDA(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            ms[k] += t;
+        }
+    }
+    *ticks = b->prof_used;
+    return HMI_OK;
+}
+
 int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms)
 {
     if (!b || !ticks || !total_ms) return fail(HMI_ERR_INVALID_ARG);
-    HMI_CUDA(cudaSetDevice(b->dev));
-    double tot = 0.0;
-    for (int i = 0; i < b->prof_used; ++i) {
-        HMI_CUDA(cudaEventSynchronize(b->prof_ev[2 * i + 1]));
-        float ms = 0.f;
-        HMI_CUDA(cudaEventElapsedTime(&ms, b->prof_ev[2 * i], b->prof_ev[2 * i + 1]));
-        tot += ms;
-    }
-    *ticks = b->prof_used;
-    *total_ms = tot;
+    double ms[HMI_TICK_KERNELS];
+    const int st = hmi_batch_profile_kernels(b, ticks, ms, HMI_TICK_KERNELS);
+    if (st != HMI_OK) return st;
+    *total_ms = ms[1];
     return HMI_OK;
 }
 

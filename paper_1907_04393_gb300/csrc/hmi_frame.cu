@@ -93,35 +93,46 @@ __device__ __forceinline__ uint32_t luma_sum_n(const uint32_t (&f)[12], int npx)
 }
 
 // ---------------------------------------------------------------------------
-// k_luma: one CTA per piece (a contiguous chunk range of one stream).
+// k_luma: one resident wave of CTAs, each over a contiguous range of pieces.
+// Consecutive pieces of one stream are walked as a single chunk range, with
+// kLumaChunks chunks per thread in flight before the sums; the partial sum is
+// flushed (one atomic per CTA) when the stream changes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
+constexpr int kLumaChunks = 2;
+
+__global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
 {
     __shared__ unsigned long long red[kThreads / 32];
     __shared__ bool is_last;
     const int tid = threadIdx.x;
     const uint64_t keep = policy_evict_last();
-    // a contiguous range of pieces per CTA: consecutive pieces mostly share a
-    // stream, so partial sums are flushed only when the stream changes
     const int p0 = (int)(((long long)b.npieces * blockIdx.x) / gridDim.x);
     const int p1 = (int)(((long long)b.npieces * (blockIdx.x + 1)) / gridDim.x);
-    unsigned long long acc = 0;
-    for (int pc = p0; pc < p1; ++pc) {
-        const int4 piece = b.pieces[pc];
-        const DevStream &D = b.ds[piece.x];
-        const TickIO io = b.io[piece.x];
+    for (int pc = p0; pc < p1;) {
+        const int4 first = b.pieces[pc];
+        int c1 = first.z, pn = pc + 1;
+        while (pn < p1) {
+            const int4 nx = b.pieces[pn];
+            if (nx.x != first.x || nx.y != c1) break;
+            c1 = nx.z;
+            ++pn;
+        }
+        pc = pn;
+        const DevStream &D = b.ds[first.x];
+        const TickIO io = b.io[first.x];
+        if (io.frame == nullptr) continue;   // no frame for this stream this tick (CTA-uniform)
         const int w = D.w, cpr = 2 * D.nwords;
-        // two chunks per thread per round, both loads in flight before the sums;
-        // a stream without a frame this tick (null frame) is skipped
-        for (int u = piece.y + tid; io.frame != nullptr && u < piece.z; u += 2 * blockDim.x) {
-            uint32_t f[2][12];
-            int npx[2];
+        const uint32_t magic = D.cpr_magic;
+        unsigned long long acc = 0;
+        for (int u = first.y + tid; u < c1; u += kLumaChunks * blockDim.x) {
+            uint32_t f[kLumaChunks][12];
+            int npx[kLumaChunks];
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < kLumaChunks; ++q) {
                 const int uu = u + q * (int)blockDim.x;
                 npx[q] = 0;
-                if (uu < piece.z) {
-                    const int y = uu / cpr, x0 = (uu - y * cpr) * kChunkPx;
+                if (uu < c1) {
+                    const int y = chunk_row((uint32_t)uu, magic), x0 = (uu - y * cpr) * kChunkPx;
                     if (x0 < w) {
                         npx[q] = min(kChunkPx, w - x0);
                         load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
@@ -129,22 +140,19 @@ __global__ void __launch_bounds__(kThreads) k_luma(BatchDev b)
                 }
             }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
+            for (int q = 0; q < kLumaChunks; ++q)
+                acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
         }
-        const bool flush = (pc + 1 == p1) || (b.pieces[pc + 1].x != piece.x);
-        if (flush) {   // CTA-uniform
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-            if ((tid & 31) == 0) red[tid >> 5] = acc;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned long long t = 0;
-                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-                atomicAdd(&D.st->sy, t);
-            }
-            __syncthreads();
-            acc = 0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+            atomicAdd(&D.st->sy, t);
         }
+        __syncthreads();
     }
     // the last CTA to finish computes every stream's gain
     __threadfence();
@@ -269,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
             uint32_t bits = 0;
             int y = 0, j = 0;
             if (u < piece.z) {
-                y = u / cpr;
+                y = chunk_row((uint32_t)u, D.cpr_magic);
                 j = u - y * cpr;
                 const int x0 = j * kChunkPx;
                 if (x0 < w) {
@@ -312,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
         const TickIO io = b.io[sidx];
         const uint32_t g = D.st->gain;
         const int cpr = 2 * D.nwords;
-        const int y = u / cpr, j = u - y * cpr;
+        const int y = chunk_row((uint32_t)u, D.cpr_magic), j = u - y * cpr;
         const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * j * kChunkPx;
         uint32_t fail = 0;
         if (__popc(bits) > 4) {
@@ -672,25 +680,54 @@ static int grid_for_pieces(int npieces)
     return npieces > 0 ? npieces : 1;
 }
 
+// CTAs of `kernel` that fit on one SM at once (queried once per device).
+template <typename K>
+static int resident_ctas(K kernel, int threads, int *cache)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            n = 1;
+        }
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    const int grid = std::max(1, std::min(b.npieces, num_sms * 8));
+    static int per_sm[64];
+    const int grid = std::max(1, std::min(b.npieces, num_sms * resident_ctas(k_luma, kThreads, per_sm)));
     k_luma<<<grid, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
+    (void)num_sms;
     k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
     k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
-cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
+static bool strip_path(const BatchDev &b)
 {
-    if (b.uniform_halo >= 0 && b.uniform_halo <= kStripMaxHalo) {
+    return b.uniform_halo >= 0 && b.uniform_halo <= kStripMaxHalo;
+}
+
+cudaError_t launch_morph(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    (void)num_sms;
+    if (strip_path(b)) {
         const unsigned grid = (b.total_strips + kStripWarps - 1) / kStripWarps;
         switch (b.uniform_halo) {
         case 0: k_morph_strip<0><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
@@ -699,15 +736,31 @@ cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
         case 6: k_morph_strip<6><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
         default: k_morph_strip<8><<<grid, kStripWarps * 32, 0, cs>>>(b); break;
         }
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
-                                               (unsigned)num_sms * 8u);
-        k_block_cc<<<std::max(g2, 1u), kBlockCcWarps * 32, 0, cs>>>(b);
     } else {
         k_morph_cc<<<b.total_tiles, kThreads, 0, cs>>>(b);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    if (!strip_path(b)) return cudaSuccess;   // k_morph_cc labels its blocks itself
+    const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
+                                           (unsigned)num_sms * 8u);
+    k_block_cc<<<std::max(g2, 1u), kBlockCcWarps * 32, 0, cs>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    switch (k) {
+    case 0: return launch_luma(b, cs, num_sms);
+    case 1: return launch_classify(b, cs, num_sms);
+    case 2: return launch_skin(b, cs, num_sms);
+    case 3: return launch_morph(b, cs, num_sms);
+    case 4: return launch_block_cc(b, cs, num_sms);
+    default: return launch_finish(b, cs);
+    }
 }
 
 }  // namespace hmi

@@ -65,6 +65,7 @@ struct DevStream {
     int tiles_x;                  // ceil(nwords / kMorphTW)
     int strips_x;                 // ceil(nwords / 30): register-strip tiles per block-row
     int fpitch;                   // bytes per row of the band (and of the staging frame)
+    uint32_t cpr_magic;           // ceil(2^32 / (2 * nwords)): row of chunk u = umulhi(u, magic)
     int gray_tol;
     int open_iters, close_iters;
     uint32_t gain_min, gain_max, min_area;
@@ -82,6 +83,15 @@ struct DevStream {
     StreamState *st;
     uint32_t *hist;               // click_window areas (ring)
 };
+
+// Row of chunk u of a stream with cpr chunks per row: with m = ceil(2^32 / cpr)
+// = (2^32 + e) / cpr, 0 <= e < cpr, u m / 2^32 = u / cpr + u e / (cpr 2^32),
+// and the second term stays below 1 / cpr whenever u cpr < 2^32, so the high
+// word of u m is floor(u / cpr).  Here u < h cpr and cpr <= 512, h <= 8192.
+__device__ __forceinline__ int chunk_row(uint32_t u, uint32_t magic)
+{
+    return (int)__umulhi(u, magic);
+}
 
 // Per-tick pointers of one stream.
 struct TickIO {
@@ -122,10 +132,18 @@ constexpr int kThreads = 256;
 // ---------------------------------------------------------------------------
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
+// The kernels of one tick, in order: 0 luma (and gains), 1 classify (band
+// test), 2 skin (gray and hue tests), 3 morphology, 4 block components (none
+// on the generic morphology path, which labels its blocks itself), 5 finish.
+constexpr int kTickKernels = 6;
+static_assert(kTickKernels == HMI_TICK_KERNELS, "tick kernel count");
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms);
-cudaError_t launch_morph_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_morph(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
+cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,
                           cudaStream_t cs);
 

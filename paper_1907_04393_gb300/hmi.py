@@ -23,6 +23,7 @@ HMI_ERR_NO_MEMORY = -3
 HMI_ERR_DEVICE = -4
 HMI_ERR_DEVICE_TIMEOUT = -5
 HMI_LEARNING = 1          # server results only: a background-learning frame
+HMI_TICK_KERNELS = 6
 
 
 class hmi_params(ctypes.Structure):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "hmi_batch_get_groups": (_I, [_P]),
     "hmi_batch_profile": (_I, [_P, _I]),
     "hmi_batch_profile_read": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "hmi_batch_profile_kernels": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I]),
     "hmi_get_background_stats": (_I, [_P, _P, _P]),
     "hmi_get_labels": (_I, [_P, _P]),
     "hmi_export_background": (_I, [_P, _P, _P, _P, _P, _P, _P,
@@ -251,6 +253,18 @@ def hmi_batch_get_groups(b: int) -> int:
 
 def hmi_batch_profile(b: int, max_ticks: int) -> None:
     _check(load().hmi_batch_profile(b, max_ticks), "hmi_batch_profile")
+
+
+TICK_KERNELS = ("luma", "classify", "skin", "morphology", "block_components", "finish")
+
+
+def hmi_batch_profile_kernels(b: int) -> tuple[int, dict]:
+    """(ticks timed, {kernel name: summed milliseconds}) in tick order."""
+    t = ctypes.c_int()
+    ms = (ctypes.c_double * len(TICK_KERNELS))()
+    _check(load().hmi_batch_profile_kernels(b, ctypes.byref(t), ms, len(TICK_KERNELS)),
+           "hmi_batch_profile_kernels")
+    return t.value, dict(zip(TICK_KERNELS, list(ms)))
 
 
 def hmi_batch_profile_read(b: int) -> tuple[int, float]:

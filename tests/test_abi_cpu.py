@@ -81,7 +81,7 @@ def test_status_constants_match_header():
     import re
     text = open(os.path.join(ROOT, "include", "hmi.h")).read()
     found = dict((k, int(v)) for k, v in re.findall(r"#define (HMI_[A-Z_]+) \(?(-?\d+)\)?", text))
-    names = [k for k in dir(hmi) if re.fullmatch(r"HMI_(OK|ERR_[A-Z_]+|LEARNING)", k)]
+    names = [k for k in dir(hmi) if re.fullmatch(r"HMI_(OK|ERR_[A-Z_]+|LEARNING|TICK_KERNELS)", k)]
     assert found and set(found) == set(names)
     for k in names:
         assert getattr(hmi, k) == found[k], k

@@ -481,5 +481,8 @@ def test_profile_counts_classification_kernel():
         hmi.hmi_batch_process_async(b, [f], [m], None, s, i % 2 == 0)
     ticks, ms = hmi.hmi_batch_profile_read(b)
     assert ticks == 5 and 0 < ms / ticks < 5.0
+    t2, per = hmi.hmi_batch_profile_kernels(b)
+    assert t2 == 5 and per["classify"] == pytest.approx(ms)
+    assert all(v > 0 for k, v in per.items() if k != "block_components")
     hmi.hmi_batch_destroy(b)
     g.close()
