@@ -293,7 +293,11 @@ def run_ours(args) -> None:
         px_per_tick += w * h
     ptrs = torch.zeros(n * 40, dtype=torch.uint8, device=dev)
     batch = hmi.hmi_batch_create([s.handle for s in streams])
-    if args.groups:
+    default_groups = hmi.hmi_batch_get_groups(batch)
+    pipelined = args.mode == "pipelined"
+    if pipelined:
+        hmi.hmi_batch_set_groups(batch, 1)      # pipelined ticks run as one chain
+    elif args.groups:
         hmi.hmi_batch_set_groups(batch, args.groups)
     cs = torch.cuda.current_stream()
 
@@ -301,8 +305,20 @@ def run_ours(args) -> None:
         hmi.hmi_batch_process_async(batch, [rings[i][k % RING] for i in range(n)], masks,
                                     ptrs.data_ptr(), cs.cuda_stream, True)
 
+    def tick_main(k):
+        if pipelined:
+            hmi.hmi_batch_process_pipelined(batch, [rings[i][k % RING] for i in range(n)], masks,
+                                            ptrs.data_ptr(), cs.cuda_stream, True)
+        else:
+            tick(k)
+
+    def finish_main():
+        if pipelined:
+            hmi.hmi_batch_flush(batch, cs.cuda_stream)   # the last tick's second stage
+
     for k in range(args.warmup):
-        tick(k)
+        tick_main(k)
+    finish_main()
     torch.cuda.synchronize()
 
     gpu_id = str(local)
@@ -321,7 +337,8 @@ def run_ours(args) -> None:
     t0 = time.time()
     e0.record(cs)
     for k in range(args.steps):
-        tick(args.warmup + k)
+        tick_main(args.warmup + k)
+    finish_main()
     e1.record(cs)
     torch.cuda.synchronize()
     barrier()
@@ -333,6 +350,21 @@ def run_ours(args) -> None:
         ms = float(t.item())
     clk = clocks.summary(t0, t1)
     clocks.stop()
+
+    # ---- plain (unpipelined) ticks with the library's default groups ------
+    plain_steps = max(10, min(args.steps, 2000))
+    hmi.hmi_batch_set_groups(batch, args.groups or default_groups)
+    plain_groups = hmi.hmi_batch_get_groups(batch)
+    for k in range(args.warmup):
+        tick(k)
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(cs)
+    for k in range(plain_steps):
+        tick(args.warmup + k)
+    q1.record(cs)
+    torch.cuda.synchronize()
+    plain_ms = q0.elapsed_time(q1) / plain_steps
 
     # ---- roofline pass: the same ticks with one chain, so that each
     # classification launch is timed alone with events on its stream -------
@@ -352,7 +384,7 @@ def run_ours(args) -> None:
     prof_ticks, per_kernel = hmi.hmi_batch_profile_kernels(batch)
     prof_ms = per_kernel["classify"]
     hmi.hmi_batch_profile(batch, 0)
-    hmi.hmi_batch_set_groups(batch, groups)
+    hmi.hmi_batch_set_groups(batch, plain_groups)
 
     # ---- end to end through the synchronous API with host buffers --------
     host_frames = []
@@ -409,8 +441,15 @@ def run_ours(args) -> None:
         "config": {"workload": WORKLOAD, "streams_per_gpu": n, "px_per_tick": px_per_tick,
                    "l2": f"inputs larger than L2: ring of {RING} ticks per stream "
                          f"({RING * px_per_tick * 3 / 1e6:.0f} MB of frames)",
-                   "launch": f"CUDA graph per tick on the torch current stream, {groups} "
-                             "overlapping stream groups"},
+                   "launch": ("pipelined ticks: one CUDA graph per tick on the torch current stream "
+                              "runs stage 1 (gains, band test) of tick k beside stage 2 (gray/hue, "
+                              "morphology, components, pointer) of tick k-1; one flush ends the timed "
+                              "region" if pipelined else
+                              f"CUDA graph per tick on the torch current stream, {groups} overlapping "
+                              "stream groups")},
+        "plain_ticks": {"ms_per_step": plain_ms, "frames_per_s": n * world / (plain_ms / 1e3),
+                        "groups": plain_groups, "steps": plain_steps,
+                        "launch": "hmi_batch_process_async, one CUDA graph per tick"},
         "mpx_per_s": px_per_tick * args.steps * world / (ms / 1e3) / 1e6,
         "roofline": {"bound": "hbm", "kernel": "k_classify", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -528,6 +567,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",
+                    help="ticks of the timed region: pipelined (stage overlap) or plain")
     ap.add_argument("--groups", type=int, default=0,
                     help="concurrent stream groups per tick (0: the library default)")
     ap.add_argument("--serve-seconds", type=float, default=60.0)

@@ -168,6 +168,23 @@ HMI_API int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_
 HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                             hmi_pointer *ptrs, void *cuda_stream, int use_graph);
 
+/* Pipelined ticks, for plans with one group (HMI_ERR_INVALID_ARG otherwise;
+ * see hmi_batch_set_groups).  A tick runs in two stages: stage 1 computes the
+ * gains and the background band test (bandwidth-bound), stage 2 the gray and
+ * hue tests, morphology, components and pointer (latency-bound).  Each call
+ * enqueues stage 1 of its own frames and, beside it on the device, stage 2 of
+ * the previous pipelined call's frames, so the two overlap.  Buffers as in
+ * hmi_batch_process_async.  The results of a call (its masks and ptrs) are
+ * complete once cuda_stream has passed the NEXT pipelined call on the batch,
+ * or hmi_batch_flush; its frames must stay valid and unchanged until then.
+ * Every other processing call on the batch flushes first.  Results equal
+ * those of hmi_batch_process_async on the same frames. */
+HMI_API int hmi_batch_process_pipelined(hmi_batch *b, const uint8_t *const *frames,
+                                        uint8_t *const *masks, hmi_pointer *ptrs,
+                                        void *cuda_stream, int use_graph);
+/* Enqueue the pending stage 2 (if any) on cuda_stream. */
+HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
+
 /* Kernel timing of a batch's ticks.  A tick runs HMI_TICK_KERNELS kernels in
  * this order: 0 luma sums and gains, 1 background band test (the per-pixel
  * HBM pass), 2 gray and hue tests of out-of-band pixels, 3 morphology, 4

@@ -106,7 +106,7 @@ struct Arena {
 
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
-    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, bits, comp, parent, count, flag, mask, st,
+    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, raw2, bits, comp, parent, count, flag, mask, st,
         hist, ds, ptr, total;
 };
 
@@ -132,6 +132,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.vmin = a.take(L.npx * 3);
     L.vmax = a.take(L.npx * 3);
     L.raw = a.take(bitrows);
+    L.raw2 = a.take(bitrows);   // second tick parity (pipelined ticks)
     L.bits = a.take(bitrows);
     L.comp = a.take(nblk * kSlots * sizeof(Comp));
     L.parent = a.take(nblk * kSlots * 4);
@@ -223,7 +224,9 @@ struct hmi_stream {
 // One chain of tick kernels over a subset of the batch's streams.
 struct Group {
     int off = 0, cnt = 0;         // range in the permuted stream order
-    BatchDev bd{};                // io is set per tick slot
+    BatchDev bd{};                // io, parity and skin queue are set per tick slot
+    uint32_t *skin_count_p[2] = {};   // skin queue of each tick parity
+    uint2 *skin_list_p[2] = {};
     cudaStream_t cs = nullptr;    // branch stream (also joins graph capture)
     cudaEvent_t ev_luma = nullptr, ev_done = nullptr;
 };
@@ -257,6 +260,12 @@ struct hmi_batch {
     cudaGraphExec_t pgraph[kRing] = {};
     cudaGraphNode_t ev_node[kRing][kTickKernels + 1] = {};
     cudaEvent_t dummy_ev[kTickKernels + 1] = {};
+    // pipelined ticks (single group): the slot whose second stage is still to
+    // run (-1: none), an event at the end of the last pipelined call, and the
+    // graphs of "stage 1 of slot s beside stage 2 of slot s - 1"
+    int pending = -1;
+    cudaEvent_t pipe_ev = nullptr;
+    cudaGraphExec_t pipe_graph[kRing] = {};
     // profiling of the classification kernel (single-group plans)
     std::vector<cudaEvent_t> prof_ev;
     int prof_max = 0, prof_used = 0;
@@ -301,7 +310,8 @@ void fill_devstream(hmi_stream *s)
     hue_intervals(s->p.hue_lo, s->p.hue_hi, D.hueA, D.hueB);
     D.lo = a + L.lo;
     D.hi = a + L.hi;
-    D.raw = reinterpret_cast<uint32_t *>(a + L.raw);
+    D.raw[0] = reinterpret_cast<uint32_t *>(a + L.raw);
+    D.raw[1] = reinterpret_cast<uint32_t *>(a + L.raw2);
     D.bits = reinterpret_cast<uint32_t *>(a + L.bits);
     D.comp = reinterpret_cast<Comp *>(a + L.comp);
     D.parent = reinterpret_cast<uint32_t *>(a + L.parent);
@@ -316,6 +326,8 @@ void plan_free_graphs(hmi_batch *b)
     for (int i = 0; i < kRing; ++i) {
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
         if (b->pgraph[i]) cudaGraphExecDestroy(b->pgraph[i]);
+        if (b->pipe_graph[i]) cudaGraphExecDestroy(b->pipe_graph[i]);
+        b->pipe_graph[i] = nullptr;
         if (b->pgraph_src[i]) cudaGraphDestroy(b->pgraph_src[i]);
         b->graph[i] = b->pgraph[i] = nullptr;
         b->pgraph_src[i] = nullptr;
@@ -342,10 +354,13 @@ void plan_free(hmi_batch *b)
     b->plan_cap = 0;
 }
 
+int flush_pending(hmi_batch *b, cudaStream_t cs);
+
 int batch_free(hmi_batch *b)
 {
     if (!b) return HMI_OK;
     cudaSetDevice(b->dev);
+    if (b->cs && b->pending >= 0) flush_pending(b, b->cs);
     if (b->cs) cudaStreamSynchronize(b->cs);
     for (int i = 0; i < kRing; ++i)
         if (b->slot_ev[i]) cudaEventSynchronize(b->slot_ev[i]);
@@ -357,6 +372,7 @@ int batch_free(hmi_batch *b)
         if (e) cudaEventDestroy(e);
     for (auto e : b->prof_ev) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->pipe_ev) cudaEventDestroy(b->pipe_ev);
     if (b->cs) cudaStreamDestroy(b->cs);
     if (b->arena) cudaFree(b->arena);
     if (b->h_io) cudaFreeHost(b->h_io);
@@ -412,7 +428,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl, o_skn2, o_skl2;
     };
     std::vector<Tables> T(ng);
     Arena a;
@@ -449,6 +465,8 @@ int plan_build(hmi_batch *b, int ng)
         t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
         t.o_skn = a.take(sizeof(uint32_t));
         t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
+        t.o_skn2 = a.take(sizeof(uint32_t));
+        t.o_skl2 = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
     }
     if (a.off > b->plan_cap) {   // grow the table buffer; a smaller plan reuses it
         if (b->plan) cudaFree(b->plan);
@@ -503,8 +521,13 @@ int plan_build(hmi_batch *b, int ng)
         bd.err = b->d_err;
         bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
         bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
-        bd.skin_count = reinterpret_cast<uint32_t *>(A + t.o_skn);
-        bd.skin_list = reinterpret_cast<uint2 *>(A + t.o_skl);
+        G.skin_count_p[0] = reinterpret_cast<uint32_t *>(A + t.o_skn);
+        G.skin_list_p[0] = reinterpret_cast<uint2 *>(A + t.o_skl);
+        G.skin_count_p[1] = reinterpret_cast<uint32_t *>(A + t.o_skn2);
+        G.skin_list_p[1] = reinterpret_cast<uint2 *>(A + t.o_skl2);
+        bd.skin_count = G.skin_count_p[0];
+        bd.skin_list = G.skin_list_p[0];
+        bd.parity = 0;
     }
     ok = ok && cudaStreamSynchronize(up) == cudaSuccess;
     if (!ok) {
@@ -574,7 +597,8 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
     bool ok = batch_alloc_io(b, n) &&
               cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b->pipe_ev, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kRing; ++i)
         ok = cudaEventCreateWithFlags(&b->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i <= kTickKernels; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
@@ -602,30 +626,56 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
 // branch; group g starts its luma after group g-1's luma, so the HBM-bound
 // passes of later groups overlap the latency-bound tail of earlier ones.
 // With one group, event records (or event nodes) bracket the classify kernel.
+// Launch parameters of group G for the tick in `slot`: its pointer table, and
+// the tick parity (slot & 1, the ring being even) that picks the raw bits, the
+// gains and the skin queue, so that consecutive ticks never share them.
+BatchDev tick_dev(const hmi_batch *b, const Group &G, int slot)
+{
+    static_assert(kRing % 2 == 0, "slot parity must alternate");
+    BatchDev bd = G.bd;
+    bd.io = b->d_io + (size_t)slot * b->n + G.off;
+    bd.parity = slot & 1;
+    bd.skin_count = G.skin_count_p[bd.parity];
+    bd.skin_list = G.skin_list_p[bd.parity];
+    return bd;
+}
+
+cudaError_t upload_io(hmi_batch *b, int slot, cudaStream_t cs)
+{
+    return cudaMemcpyAsync(b->d_io + (size_t)slot * b->n, b->h_io + (size_t)slot * b->n,
+                           sizeof(TickIO) * b->n, cudaMemcpyHostToDevice, cs);
+}
+
+// Tick kernels k0 .. k1 - 1 of a single-group plan, with an event after each
+// (and one before the first) when ev is given.
+cudaError_t enqueue_kernels(hmi_batch *b, int slot, cudaStream_t cs, int k0, int k1, const cudaEvent_t *ev,
+                            bool capture)
+{
+    const BatchDev bd = tick_dev(b, b->groups[0], slot);
+    const unsigned flags = capture ? cudaEventRecordExternal : 0;
+    cudaError_t e;
+    if (ev && (e = cudaEventRecordWithFlags(ev[k0], cs, flags)) != cudaSuccess) return e;
+    for (int k = k0; k < k1; ++k) {
+        if ((e = launch_tick_kernel(k, bd, cs, b->num_sms)) != cudaSuccess) return e;
+        if (ev && (e = cudaEventRecordWithFlags(ev[k + 1], cs, flags)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Stage 1 of a tick: luma and gains, then the band test (kernels 0, 1).
+// Stage 2: gray and hue tests, morphology, block components, finish (2 .. 5).
+constexpr int kStage2 = 2;
+
 cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEvent_t *ev, bool capture)
 {
-    TickIO *dio = b->d_io + (size_t)slot * b->n;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(dio, b->h_io + (size_t)slot * b->n, sizeof(TickIO) * b->n,
-                             cudaMemcpyHostToDevice, cs)) != cudaSuccess)
-        return e;
+    if ((e = upload_io(b, slot, cs)) != cudaSuccess) return e;
     const int ng = (int)b->groups.size();
-    if (ng == 1) {
-        BatchDev bd = b->groups[0].bd;
-        bd.io = dio;
-        const unsigned flags = capture ? cudaEventRecordExternal : 0;
-        if (ev && (e = cudaEventRecordWithFlags(ev[0], cs, flags)) != cudaSuccess) return e;
-        for (int k = 0; k < kTickKernels; ++k) {
-            if ((e = launch_tick_kernel(k, bd, cs, b->num_sms)) != cudaSuccess) return e;
-            if (ev && (e = cudaEventRecordWithFlags(ev[k + 1], cs, flags)) != cudaSuccess) return e;
-        }
-        return cudaSuccess;
-    }
+    if (ng == 1) return enqueue_kernels(b, slot, cs, 0, kTickKernels, ev, capture);
     if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
     for (int g = 0; g < ng; ++g) {
         Group &G = b->groups[g];
-        BatchDev bd = G.bd;
-        bd.io = dio + G.off;
+        const BatchDev bd = tick_dev(b, G, slot);
         if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
         if (g > 0 && (e = cudaStreamWaitEvent(G.cs, b->groups[g - 1].ev_luma, 0)) != cudaSuccess) return e;
         if ((e = launch_tick_kernel(0, bd, G.cs, b->num_sms)) != cudaSuccess) return e;
@@ -637,6 +687,56 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
     for (int g = 0; g < ng; ++g)
         if ((e = cudaStreamWaitEvent(cs, b->groups[g].ev_done, 0)) != cudaSuccess) return e;
     return cudaSuccess;
+}
+
+// Pipelined tick (single group): stage 1 of `slot` on cs, and beside it, on
+// the group's branch stream, stage 2 of `prev` (if >= 0); cs then waits for
+// both.  The two touch disjoint per-tick state (their parities differ).
+cudaError_t enqueue_pipelined(hmi_batch *b, int slot, int prev, cudaStream_t cs)
+{
+    cudaError_t e;
+    Group &G = b->groups[0];
+    if (prev >= 0) {
+        if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = enqueue_kernels(b, prev, G.cs, kStage2, kTickKernels, nullptr, false)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;
+    }
+    if ((e = upload_io(b, slot, cs)) != cudaSuccess) return e;
+    if ((e = enqueue_kernels(b, slot, cs, 0, kStage2, nullptr, false)) != cudaSuccess) return e;
+    if (prev >= 0 && (e = cudaStreamWaitEvent(cs, G.ev_done, 0)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+int build_pipe_graph(hmi_batch *b, int slot)
+{
+    cudaGraph_t g = nullptr;
+    HMI_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_pipelined(b, slot, (slot + kRing - 1) % kRing, b->cs);
+    cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e != cudaSuccess ? e : e2);
+    }
+    e = cudaGraphInstantiate(&b->pipe_graph[slot], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->pipe_graph[slot] = nullptr;
+        return cuda_fail(e);
+    }
+    return HMI_OK;
+}
+
+// Run the second stage of the pending pipelined tick on cs.
+int flush_pending(hmi_batch *b, cudaStream_t cs)
+{
+    if (b->pending < 0) return HMI_OK;
+    const int prev = b->pending;
+    b->pending = -1;
+    HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
+    HMI_CUDA(enqueue_kernels(b, prev, cs, kStage2, kTickKernels, nullptr, false));
+    HMI_CUDA(cudaEventRecord(b->slot_ev[prev], cs));
+    return HMI_OK;
 }
 
 // Capture one tick into a graph: the plain form, or (profiling, single group)
@@ -787,6 +887,8 @@ int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks
     if (!b || !frames) return fail(HMI_ERR_INVALID_ARG);
     if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
     HMI_CUDA(cudaSetDevice(b->dev));
+    int st0 = flush_pending(b, b->cs);
+    if (st0 != HMI_OK) return st0;
     int slot = acquire_slot(b);
     if (slot < 0) return slot;
     std::vector<int> mcopy;
@@ -819,19 +921,56 @@ int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *mask
     if (ptrs && !is_device_ptr(ptrs)) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int st = flush_pending(b, cs);
+    if (st != HMI_OK) return st;
     int slot = acquire_slot(b);
     if (slot < 0) return slot;
-    int st = prepare_slot(b, slot, frames, masks, true, cs, nullptr);
+    st = prepare_slot(b, slot, frames, masks, true, cs, nullptr);
     if (st != HMI_OK) return st;
     TickIO *io = b->h_io + (size_t)slot * b->n;
     for (int i = 0; i < b->n; ++i) io[b->pos[i]].ptr_out = ptrs ? ptrs + i : nullptr;
     return run_tick(b, slot, cs, use_graph != 0);
 }
 
+int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                    hmi_pointer *ptrs, void *cuda_stream, int use_graph)
+{
+    if (!b || !frames || b->groups.size() != 1) return fail(HMI_ERR_INVALID_ARG);
+    if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
+    if (ptrs && !is_device_ptr(ptrs)) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const int slot = acquire_slot(b);
+    if (slot < 0) return slot;
+    int st = prepare_slot(b, slot, frames, masks, true, cs, nullptr);
+    if (st != HMI_OK) return st;
+    TickIO *io = b->h_io + (size_t)slot * b->n;
+    for (int i = 0; i < b->n; ++i) io[b->pos[i]].ptr_out = ptrs ? ptrs + i : nullptr;
+    const int prev = b->pending;
+    if (prev >= 0) HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
+    if (use_graph && prev == (slot + kRing - 1) % kRing) {
+        if (!b->pipe_graph[slot]) {
+            st = build_pipe_graph(b, slot);
+            if (st != HMI_OK) return st;
+        }
+        HMI_CUDA(cudaGraphLaunch(b->pipe_graph[slot], cs));
+    } else {
+        HMI_CUDA(enqueue_pipelined(b, slot, prev, cs));
+    }
+    HMI_CUDA(cudaEventRecord(b->slot_ev[slot], cs));
+    b->slot_used[slot] = true;
+    if (prev >= 0) HMI_CUDA(cudaEventRecord(b->slot_ev[prev], cs));
+    HMI_CUDA(cudaEventRecord(b->pipe_ev, cs));
+    b->pending = slot;
+    return HMI_OK;
+}
+
 int batch_set_groups(hmi_batch *b, int ng)
 {
     if (!b || ng < 1 || ng > 64) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
+    const int st = flush_pending(b, b->cs);
+    if (st != HMI_OK) return st;
     HMI_CUDA(cudaDeviceSynchronize());
     plan_free(b);
     for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
@@ -1683,6 +1822,19 @@ int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t 
     return batch_async(b, frames, masks, ptrs, cuda_stream, use_graph);
 }
 
+int hmi_batch_process_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+                                hmi_pointer *ptrs, void *cuda_stream, int use_graph)
+{
+    return batch_pipelined(b, frames, masks, ptrs, cuda_stream, use_graph);
+}
+
+int hmi_batch_flush(hmi_batch *b, void *cuda_stream)
+{
+    if (!b) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    return flush_pending(b, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
 int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
                       uint8_t *const *masks, hmi_pointer *ptrs)
 {
@@ -1701,6 +1853,8 @@ int hmi_batch_profile(hmi_batch *b, int max_ticks)
     if (!b || max_ticks < 0 || max_ticks > 1000000) return fail(HMI_ERR_INVALID_ARG);
     if (max_ticks > 0 && b->groups.size() != 1) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
+    const int fs = flush_pending(b, b->cs);
+    if (fs != HMI_OK) return fs;
     HMI_CUDA(cudaDeviceSynchronize());
     for (auto e : b->prof_ev) cudaEventDestroy(e);
     b->prof_ev.assign((size_t)(kTickKernels + 1) * max_ticks, nullptr);

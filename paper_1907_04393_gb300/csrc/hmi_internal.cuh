@@ -49,6 +49,7 @@ struct __align__(16) StreamState {
     unsigned long long best;      // packed (area, ~key) argmax (0 between frames)
     unsigned long long learn_luma;  // luma total over the learning frames
     uint32_t gain;                // Q16 gain of the last frame
+    uint32_t gain_p[2];           // Q16 gain of the frame of each tick parity
     uint32_t err;                 // kErr* flags
     int32_t click;
     int32_t hist_count;
@@ -74,7 +75,7 @@ struct DevStream {
     // intervals of N = 512 (t + d) + d:  d*A <= N < d*B
     int hueA[3][2], hueB[3][2];
     const uint8_t *lo, *hi;       // background band, pitch fpitch, RGB interleaved
-    uint32_t *raw;                // raw AND mask bits, (bh*32) x nwords words
+    uint32_t *raw[2];             // raw AND mask bits, (bh*32) x nwords words, by tick parity
     uint32_t *bits;               // mask bits after morphology, same layout
     Comp *comp;                   // bh*nwords*kSlots records
     uint32_t *parent;             // union-find parent per record
@@ -124,6 +125,8 @@ struct BatchDev {
     uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
     uint32_t *skin_count;                     // chunks queued for the skin tests this tick
     uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
+    int parity;                               // tick parity: selects raw[], gain_p[] and the skin
+                                              // queue, so that two ticks can be in flight
 };
 
 // Threads per CTA of every kernel of a tick.

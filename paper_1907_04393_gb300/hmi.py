@@ -81,6 +81,8 @@ SIGNATURES = {
     "hmi_batch_process_async": (_I, [_P, _P, _P, _P, _P, _I]),
     "hmi_batch_set_groups": (_I, [_P, _I]),
     "hmi_batch_get_groups": (_I, [_P]),
+    "hmi_batch_process_pipelined": (_I, [_P, _P, _P, _P, _P, _I]),
+    "hmi_batch_flush": (_I, [_P, _P]),
     "hmi_batch_profile": (_I, [_P, _I]),
     "hmi_batch_profile_read": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "hmi_batch_profile_kernels": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I]),
@@ -238,6 +240,19 @@ def hmi_batch_process_async(b: int, frames, masks, ptrs, cuda_stream: int, use_g
     ma = _ptr_array(masks) if masks is not None else None
     _check(load().hmi_batch_process_async(b, fa, ma, _addr(ptrs), cuda_stream, int(use_graph)),
            "hmi_batch_process_async")
+
+
+def hmi_batch_process_pipelined(b: int, frames, masks, ptrs, cuda_stream: int, use_graph: bool) -> None:
+    """Stage 1 of these frames beside stage 2 of the previous call's frames;
+    this call's results are complete after the next call or hmi_batch_flush."""
+    fa = _ptr_array(frames)
+    ma = _ptr_array(masks) if masks is not None else None
+    _check(load().hmi_batch_process_pipelined(b, fa, ma, _addr(ptrs), cuda_stream, int(use_graph)),
+           "hmi_batch_process_pipelined")
+
+
+def hmi_batch_flush(b: int, cuda_stream: int) -> None:
+    _check(load().hmi_batch_flush(b, cuda_stream), "hmi_batch_flush")
 
 
 def hmi_batch_set_groups(b: int, groups: int) -> None:

@@ -486,3 +486,51 @@ def test_profile_counts_classification_kernel():
     assert all(v > 0 for k, v in per.items() if k != "block_components")
     hmi.hmi_batch_destroy(b)
     g.close()
+
+
+def test_pipelined_ticks_equal_async_ticks():
+    """Two identically learned sets of streams: one processed tick by tick with
+    hmi_batch_process_async, the other with pipelined calls (stage 1 of a tick
+    beside stage 2 of the one before, graph and direct launches, an ordinary
+    call in between, a final flush).  Every tick's masks and pointers agree,
+    and a multi-group plan refuses pipelining."""
+    idx = [0, 7, 20, 33, 41, 50, 58, 63]
+    T = 7
+    frames = [[_dev(synth.run_frame(4, i, t)) for i in idx] for t in range(T)]
+    ga, _ = _batch_streams(4, idx)
+    gb, _ = _batch_streams(4, idx)
+    ba = hmi.hmi_batch_create([g.handle for g in ga])
+    bb = hmi.hmi_batch_create([g.handle for g in gb])
+    hmi.hmi_batch_set_groups(ba, 1)
+    hmi.hmi_batch_set_groups(bb, 1)
+    s = torch.cuda.current_stream().cuda_stream
+
+    def outs(gs):
+        return ([torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs],
+                torch.zeros(len(gs) * 40, dtype=torch.uint8, device="cuda"))
+
+    ref, got = [], []
+    for t in range(T):
+        m, p = outs(ga)
+        hmi.hmi_batch_process_async(ba, frames[t], m, p.data_ptr(), s, True)
+        ref.append((m, p))
+        m, p = outs(gb)
+        if t == 4:   # an ordinary call flushes the pending tick first
+            hmi.hmi_batch_process_async(bb, frames[t], m, p.data_ptr(), s, False)
+        else:
+            hmi.hmi_batch_process_pipelined(bb, frames[t], m, p.data_ptr(), s, t % 3 != 0)
+        got.append((m, p))
+    hmi.hmi_batch_flush(bb, s)
+    torch.cuda.synchronize()
+    for t in range(T):
+        for k in range(len(idx)):
+            assert torch.equal(ref[t][0][k], got[t][0][k]), (t, k)
+        assert torch.equal(ref[t][1], got[t][1]), t
+    hmi.hmi_batch_set_groups(bb, 2)
+    with pytest.raises(hmi.HmiError) as e:
+        hmi.hmi_batch_process_pipelined(bb, frames[0], None, None, s, False)
+    assert e.value.status == hmi.HMI_ERR_INVALID_ARG
+    for b in (ba, bb):
+        hmi.hmi_batch_destroy(b)
+    for g in ga + gb:
+        g.close()
