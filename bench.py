@@ -316,6 +316,15 @@ def run_ours(args) -> None:
         if pipelined:
             hmi.hmi_batch_flush(batch, cs.cuda_stream)   # the last tick's second stage
 
+    # launch shape: searched by the library's autotuner (untimed), or the default
+    tuned = None
+    if not args.no_autotune:
+        from paper_1907_04393_gb300 import autotune
+        shapes = [synth.shape(CFG, i) for i in range(n)]
+        tuned = autotune.tune(batch, shapes, [rings[i][0] for i in range(n)],
+                              torch.cuda.get_device_name(dev), pipelined, ticks=50, cache_path=None)
+    shape_used = hmi.hmi_batch_get_tuning(batch)
+
     for k in range(args.warmup):
         tick_main(k)
     finish_main()
@@ -447,6 +456,9 @@ def run_ours(args) -> None:
                               "region" if pipelined else
                               f"CUDA graph per tick on the torch current stream, {groups} overlapping "
                               "stream groups")},
+        "tuning": {"shape": shape_used,
+                   "autotuned": tuned is not None,
+                   "search_tick_us": None if tuned is None else tuned["tick_us"]},
         "plain_ticks": {"ms_per_step": plain_ms, "frames_per_s": n * world / (plain_ms / 1e3),
                         "groups": plain_groups, "steps": plain_steps,
                         "launch": "hmi_batch_process_async, one CUDA graph per tick"},
@@ -567,6 +579,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",
                     help="ticks of the timed region: pipelined (stage overlap) or plain")
     ap.add_argument("--groups", type=int, default=0,

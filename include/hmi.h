@@ -168,6 +168,38 @@ HMI_API int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_
 HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                             hmi_pointer *ptrs, void *cuda_stream, int use_graph);
 
+/* Launch shape of a batch's ticks.  piece_chunks: 16-pixel chunks per CTA
+ * work piece of the per-pixel kernels (the tile; a multiple of 32 in
+ * 32..65536, default 512); luma_ctas_per_sm: CTAs per SM of the luma pass
+ * (0 = as many as fit, else 1..32); skin_ctas_per_sm, cc_ctas_per_sm: grid
+ * of the gray/hue pass and of the block-component pass, in CTAs per SM
+ * (1..32, default 8); groups: stream groups of plain ticks (0 = min(2, n),
+ * else 1..64).  Results never depend on the tuning. */
+typedef struct {
+    int32_t piece_chunks;
+    int32_t luma_ctas_per_sm;
+    int32_t skin_ctas_per_sm;
+    int32_t cc_ctas_per_sm;
+    int32_t groups;
+} hmi_tuning;
+
+/* Replace the batch's launch shape (re-makes the plan; waits for the device).
+ * HMI_ERR_INVALID_ARG for values out of range. */
+HMI_API int hmi_batch_set_tuning(hmi_batch *b, const hmi_tuning *t);
+HMI_API int hmi_batch_get_tuning(const hmi_batch *b, hmi_tuning *t);
+
+/* Search the launch shape (Sec. 3.3: the GPU computation is autotuned):
+ * time `ticks` ticks (2..10000) of frames (device memory, one per stream) for
+ * each candidate, changing one parameter at a time (piece size, then the
+ * luma, skin and block-component grids, then the group count for plain
+ * ticks), keep the fastest, apply it and return it in *best with its time per
+ * tick in microseconds (either may be NULL).  pipelined != 0 times pipelined
+ * ticks (one group), else plain graph ticks.  The streams' click state and
+ * pointer history are restored afterwards; their last labels are those of the
+ * last tuning tick. */
+HMI_API int hmi_batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, int pipelined,
+                               hmi_tuning *best, double *best_tick_us);
+
 /* Pipelined ticks, for plans with one group (HMI_ERR_INVALID_ARG otherwise;
  * see hmi_batch_set_groups).  A tick runs in two stages: stage 1 computes the
  * gains and the background band test (bandwidth-bound), stage 2 the gray and

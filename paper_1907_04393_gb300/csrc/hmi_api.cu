@@ -53,7 +53,10 @@ int cuda_fail(cudaError_t e)
     } while (0)
 
 constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
-constexpr int kPieceChunks = 512;   // 16-px chunks per CTA piece (8192 px)
+// Default launch shape (hmi_tuning): 16-px chunks per CTA piece of the
+// per-pixel kernels (512 = 8192 px), luma CTAs per SM (0 = as many as fit),
+// skin-test and block-component CTAs per SM, stream groups (0 = min(2, n)).
+constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -234,6 +237,7 @@ struct Group {
 struct hmi_batch {
     int dev = 0;
     int n = 0;
+    hmi_tuning tune{};            // launch shape of the plan
     int cap = 0;                  // streams the per-batch buffers hold
     size_t plan_cap = 0;          // bytes of the plan table buffer
     std::vector<hmi_stream *> s;  // user order
@@ -452,8 +456,8 @@ int plan_build(hmi_batch *b, int ng)
             const int halo = 2 * (st->p.open_iters + st->p.close_iters);
             t.max_halo = std::max(t.max_halo, halo);
             t.uniform_halo = (t.uniform_halo == -2 || t.uniform_halo == halo) ? halo : -1;
-            for (int c = 0; c < chunks; c += kPieceChunks)
-                t.pieces.push_back(make_int4(k, c, std::min(chunks, c + kPieceChunks), 0));
+            for (int c = 0; c < chunks; c += b->tune.piece_chunks)
+                t.pieces.push_back(make_int4(k, c, std::min(chunks, c + b->tune.piece_chunks), 0));
         }
         t.o_c = a.take(sizeof(unsigned long long) * (m + 1));
         t.o_t = a.take(sizeof(uint32_t) * (m + 1));
@@ -528,6 +532,9 @@ int plan_build(hmi_batch *b, int ng)
         bd.skin_count = G.skin_count_p[0];
         bd.skin_list = G.skin_list_p[0];
         bd.parity = 0;
+        bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
+        bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
+        bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
     }
     ok = ok && cudaStreamSynchronize(up) == cudaSuccess;
     if (!ok) {
@@ -589,6 +596,8 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
     b->dev = s[0]->dev;
     b->n = n;
     b->s.assign(s, s + n);
+    b->tune = kDefaultTuning;
+    b->tune.groups = ngroups;
     if (cudaSetDevice(b->dev) != cudaSuccess) {
         delete b;
         cuda_fail(cudaErrorInvalidDevice);
@@ -965,19 +974,141 @@ int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *
     return HMI_OK;
 }
 
-int batch_set_groups(hmi_batch *b, int ng)
+int default_groups(int n) { return std::min(2, n); }
+
+bool tuning_ok(const hmi_tuning &t)
 {
-    if (!b || ng < 1 || ng > 64) return fail(HMI_ERR_INVALID_ARG);
+    return t.piece_chunks >= 32 && t.piece_chunks <= 65536 && t.piece_chunks % 32 == 0 &&
+           t.luma_ctas_per_sm >= 0 && t.luma_ctas_per_sm <= 32 && t.skin_ctas_per_sm >= 1 &&
+           t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
+           t.groups >= 0 && t.groups <= 64;
+}
+
+// Apply a launch shape: the plan is re-made with the device idle.
+int batch_retune(hmi_batch *b, const hmi_tuning &t)
+{
+    if (!b || !tuning_ok(t)) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
     const int st = flush_pending(b, b->cs);
     if (st != HMI_OK) return st;
     HMI_CUDA(cudaDeviceSynchronize());
     plan_free(b);
     for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
-    return plan_build(b, ng);
+    b->tune = t;
+    return plan_build(b, t.groups > 0 ? t.groups : default_groups(b->n));
 }
 
-int default_groups(int n) { return std::min(2, n); }
+// Microseconds per tick of `ticks` ticks of `frames` with the current plan
+// (pipelined or plain graph ticks on the batch's own stream, masks and
+// pointers not written), after three untimed ticks.
+int time_ticks(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined, double *us)
+{
+    auto one = [&]() {
+        return pipelined ? batch_pipelined(b, frames, nullptr, nullptr, b->cs, 1)
+                         : batch_async(b, frames, nullptr, nullptr, b->cs, 1);
+    };
+    for (int i = 0; i < 3; ++i) {
+        const int st = one();
+        if (st != HMI_OK) return st;
+    }
+    int st = flush_pending(b, b->cs);
+    if (st != HMI_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(cudaErrorMemoryAllocation);
+    }
+    cudaEventRecord(e0, b->cs);
+    for (int i = 0; i < ticks && st == HMI_OK; ++i) st = one();
+    if (st == HMI_OK) st = flush_pending(b, b->cs);
+    cudaEventRecord(e1, b->cs);
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HMI_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e);
+    *us = 1e3 * ms / ticks;
+    return HMI_OK;
+}
+
+int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined,
+                   hmi_tuning *best_out, double *best_us_out)
+{
+    if (!b || !frames || ticks < 2 || ticks > 10000) return fail(HMI_ERR_INVALID_ARG);
+    if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(b->dev));
+    int st = flush_pending(b, b->cs);
+    if (st != HMI_OK) return st;
+    HMI_CUDA(cudaDeviceSynchronize());
+    // the streams' click state and pointer history, put back afterwards
+    std::vector<std::pair<void *, size_t>> keep;
+    for (hmi_stream *s : b->s) {
+        keep.emplace_back(s->st, sizeof(StreamState));
+        keep.emplace_back(s->ds.hist, sizeof(uint32_t) * std::max<int>(s->p.click_window, 1));
+    }
+    size_t total = 0;
+    for (auto &k : keep) total += k.second;
+    uint8_t *save = nullptr;
+    HMI_CUDA(cudaMalloc(&save, total));
+    size_t off = 0;
+    for (auto &k : keep) {
+        cudaMemcpyAsync(save + off, k.first, k.second, cudaMemcpyDeviceToDevice, b->cs);
+        off += k.second;
+    }
+    const hmi_tuning start = b->tune;
+    hmi_tuning cur = start;
+    if (pipelined) cur.groups = 1;
+    double cur_us = 0.0;
+    st = batch_retune(b, cur);
+    if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &cur_us);
+    // one parameter at a time, each over its candidate values
+    struct Axis {
+        int32_t hmi_tuning::*field;
+        std::vector<int32_t> values;
+    };
+    std::vector<Axis> axes = {{&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
+                              {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
+                              {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},
+                              {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}}};
+    if (!pipelined) axes.push_back({&hmi_tuning::groups, {1, 2, 3}});
+    for (const Axis &ax : axes) {
+        for (int32_t v : ax.values) {
+            if (st != HMI_OK || cur.*ax.field == v) continue;
+            hmi_tuning cand = cur;
+            cand.*ax.field = v;
+            double us = 0.0;
+            st = batch_retune(b, cand);
+            if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &us);
+            if (st == HMI_OK && us < cur_us) {
+                cur = cand;
+                cur_us = us;
+            }
+        }
+    }
+    const int st_apply = batch_retune(b, st == HMI_OK ? cur : start);
+    cudaDeviceSynchronize();
+    off = 0;
+    for (auto &k : keep) {
+        cudaMemcpy(k.first, save + off, k.second, cudaMemcpyDeviceToDevice);
+        off += k.second;
+    }
+    cudaFree(save);
+    if (st != HMI_OK) return st;
+    if (st_apply != HMI_OK) return st_apply;
+    if (best_out) *best_out = cur;
+    if (best_us_out) *best_us_out = cur_us;
+    return HMI_OK;
+}
+
+int batch_set_groups(hmi_batch *b, int ng)
+{
+    if (!b || ng < 1 || ng > 64) return fail(HMI_ERR_INVALID_ARG);
+    hmi_tuning t = b->tune;
+    t.groups = ng;
+    return batch_retune(b, t);
+}
 
 // Give a stream's arena back (stream-ordered for pooled arenas) and destroy
 // its CUDA stream; the pool is trimmed when the device's last stream goes.
@@ -1102,6 +1233,7 @@ int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
     for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
     b->next = 0;
     b->seen.clear();
+    b->tune.groups = ngroups;
     HMI_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), b->cs));
     return plan_build(b, ngroups);
 }
@@ -1806,6 +1938,26 @@ int hmi_batch_get_groups(const hmi_batch *b)
 {
     if (!b) return fail(HMI_ERR_INVALID_ARG);
     return (int)b->groups.size();
+}
+
+int hmi_batch_set_tuning(hmi_batch *b, const hmi_tuning *t)
+{
+    if (!b || !t) return fail(HMI_ERR_INVALID_ARG);
+    return batch_retune(b, *t);
+}
+
+int hmi_batch_get_tuning(const hmi_batch *b, hmi_tuning *t)
+{
+    if (!b || !t) return fail(HMI_ERR_INVALID_ARG);
+    *t = b->tune;
+    if (t->groups == 0) t->groups = (int32_t)b->groups.size();
+    return HMI_OK;
+}
+
+int hmi_batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, int pipelined,
+                       hmi_tuning *best, double *best_tick_us)
+{
+    return batch_autotune(b, frames, ticks, pipelined != 0, best, best_tick_us);
 }
 
 void hmi_batch_destroy(hmi_batch *b) { batch_free(b); }

@@ -703,7 +703,9 @@ static int resident_ctas(K kernel, int threads, int *cache)
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     static int per_sm[64];
-    const int grid = std::max(1, std::min(b.npieces, num_sms * resident_ctas(k_luma, kThreads, per_sm)));
+    const int fit = resident_ctas(k_luma, kThreads, per_sm);
+    const int per = b.luma_ctas_per_sm > 0 ? std::min(b.luma_ctas_per_sm, fit) : fit;
+    const int grid = std::max(1, std::min(b.npieces, num_sms * per));
     k_luma<<<grid, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
@@ -717,7 +719,7 @@ cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 
 cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    k_skin<<<num_sms * 8, kThreads, 0, cs>>>(b);
+    k_skin<<<num_sms * std::max(1, b.skin_ctas_per_sm), kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 
@@ -748,7 +750,7 @@ cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     if (!strip_path(b)) return cudaSuccess;   // k_morph_cc labels its blocks itself
     const unsigned g2 = std::min<unsigned>((b.total_blocks + kBlockCcWarps - 1) / kBlockCcWarps,
-                                           (unsigned)num_sms * 8u);
+                                           (unsigned)num_sms * (unsigned)std::max(1, b.cc_ctas_per_sm));
     k_block_cc<<<std::max(g2, 1u), kBlockCcWarps * 32, 0, cs>>>(b);
     return cudaGetLastError();
 }

@@ -127,6 +127,10 @@ struct BatchDev {
     uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
     int parity;                               // tick parity: selects raw[], gain_p[] and the skin
                                               // queue, so that two ticks can be in flight
+    // launch shape (host side; chosen by the plan's tuning)
+    int luma_ctas_per_sm;                     // 0: as many as fit
+    int skin_ctas_per_sm;
+    int cc_ctas_per_sm;
 };
 
 // Threads per CTA of every kernel of a tick.

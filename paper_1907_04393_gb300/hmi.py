@@ -53,6 +53,15 @@ class hmi_server_result(ctypes.Structure):
                 ("pointer", hmi_pointer)]
 
 
+class hmi_tuning(ctypes.Structure):
+    _fields_ = [("piece_chunks", ctypes.c_int32), ("luma_ctas_per_sm", ctypes.c_int32),
+                ("skin_ctas_per_sm", ctypes.c_int32), ("cc_ctas_per_sm", ctypes.c_int32),
+                ("groups", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class hmi_server_round(ctypes.Structure):
     _fields_ = [("start_ns", ctypes.c_uint64), ("issued_ns", ctypes.c_uint64),
                 ("done_ns", ctypes.c_uint64), ("frames", ctypes.c_int32),
@@ -81,6 +90,9 @@ SIGNATURES = {
     "hmi_batch_process_async": (_I, [_P, _P, _P, _P, _P, _I]),
     "hmi_batch_set_groups": (_I, [_P, _I]),
     "hmi_batch_get_groups": (_I, [_P]),
+    "hmi_batch_set_tuning": (_I, [_P, ctypes.POINTER(hmi_tuning)]),
+    "hmi_batch_get_tuning": (_I, [_P, ctypes.POINTER(hmi_tuning)]),
+    "hmi_batch_autotune": (_I, [_P, _P, _I, _I, ctypes.POINTER(hmi_tuning), ctypes.POINTER(ctypes.c_double)]),
     "hmi_batch_process_pipelined": (_I, [_P, _P, _P, _P, _P, _I]),
     "hmi_batch_flush": (_I, [_P, _P]),
     "hmi_batch_profile": (_I, [_P, _I]),
@@ -240,6 +252,25 @@ def hmi_batch_process_async(b: int, frames, masks, ptrs, cuda_stream: int, use_g
     ma = _ptr_array(masks) if masks is not None else None
     _check(load().hmi_batch_process_async(b, fa, ma, _addr(ptrs), cuda_stream, int(use_graph)),
            "hmi_batch_process_async")
+
+
+def hmi_batch_set_tuning(b: int, tuning) -> None:
+    t = tuning if isinstance(tuning, hmi_tuning) else hmi_tuning(**tuning)
+    _check(load().hmi_batch_set_tuning(b, ctypes.byref(t)), "hmi_batch_set_tuning")
+
+
+def hmi_batch_get_tuning(b: int) -> dict:
+    t = hmi_tuning()
+    _check(load().hmi_batch_get_tuning(b, ctypes.byref(t)), "hmi_batch_get_tuning")
+    return t.as_dict()
+
+
+def hmi_batch_autotune(b: int, frames, ticks: int = 50, pipelined: bool = True) -> tuple[dict, float]:
+    """Search and apply the batch's launch shape; (tuning, microseconds per tick)."""
+    t, us = hmi_tuning(), ctypes.c_double()
+    _check(load().hmi_batch_autotune(b, _ptr_array(frames), ticks, int(pipelined), ctypes.byref(t),
+                                     ctypes.byref(us)), "hmi_batch_autotune")
+    return t.as_dict(), us.value
 
 
 def hmi_batch_process_pipelined(b: int, frames, masks, ptrs, cuda_stream: int, use_graph: bool) -> None:

@@ -30,6 +30,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 40
+    assert ctypes.sizeof(hmi.hmi_tuning) == 20
 
 
 def test_defaults_and_status_strings():
@@ -85,3 +86,27 @@ def test_status_constants_match_header():
     assert found and set(found) == set(names)
     for k in names:
         assert getattr(hmi, k) == found[k], k
+
+
+def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
+    """The cache module stores a searched launch shape under its key and applies
+    it on the next call without searching (library calls faked on the CPU)."""
+    from paper_1907_04393_gb300 import autotune
+    calls = {"search": 0, "set": []}
+
+    def fake_search(b, frames, ticks, pipelined):
+        calls["search"] += 1
+        return {"piece_chunks": 256, "luma_ctas_per_sm": 0, "skin_ctas_per_sm": 8,
+                "cc_ctas_per_sm": 4, "groups": 1}, 99.5
+
+    monkeypatch.setattr(hmi, "hmi_batch_autotune", fake_search)
+    monkeypatch.setattr(hmi, "hmi_batch_set_tuning", lambda b, t: calls["set"].append(dict(t)))
+    path = str(tmp_path / "cache.json")
+    shapes = [(640, 480), (320, 240), (320, 240)]
+    a = autotune.tune(1, shapes, None, "GB300", True, cache_path=path)
+    assert not a["cached"] and calls["search"] == 1
+    b = autotune.tune(1, list(reversed(shapes)), None, "GB300", True, cache_path=path)
+    assert b["cached"] and calls["search"] == 1 and calls["set"][-1]["cc_ctas_per_sm"] == 4
+    c = autotune.tune(1, shapes, None, "GB300", False, cache_path=path)
+    assert not c["cached"] and calls["search"] == 2
+    assert a["key"] != c["key"] and autotune.key("GB300", shapes, True) == a["key"]

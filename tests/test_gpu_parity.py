@@ -534,3 +534,66 @@ def test_pipelined_ticks_equal_async_ticks():
         hmi.hmi_batch_destroy(b)
     for g in ga + gb:
         g.close()
+
+
+def test_tuning_does_not_change_results():
+    """A batch under an unusual launch shape (small pieces, two luma CTAs per
+    SM, small skin grid, large block-component grid, three groups) matches
+    the oracle; out-of-range shapes are refused."""
+    idx = [1, 9, 18, 30, 39, 47, 55, 62]
+    gs, os_ = _batch_streams(4, idx)
+    b = hmi.hmi_batch_create([g.handle for g in gs])
+    try:
+        hmi.hmi_batch_set_tuning(b, {"piece_chunks": 128, "luma_ctas_per_sm": 2, "skin_ctas_per_sm": 4,
+                                     "cc_ctas_per_sm": 16, "groups": 3})
+        assert hmi.hmi_batch_get_tuning(b)["piece_chunks"] == 128
+        assert hmi.hmi_batch_get_groups(b) == 3
+        for t in range(2):
+            frames = [synth.run_frame(4, i, t) for i in idx]
+            masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+            ptrs = np.zeros(len(idx), hmi.POINTER_DTYPE)
+            hmi.hmi_batch_process(b, frames, masks, ptrs)
+            plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
+            _compare_batch(gs, os_, frames, masks, plist, f"tuned t={t}")
+        for bad in ({"piece_chunks": 100}, {"piece_chunks": 0}, {"skin_ctas_per_sm": 0},
+                    {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65}):
+            t = dict(hmi.hmi_batch_get_tuning(b), **bad)
+            with pytest.raises(hmi.HmiError) as e:
+                hmi.hmi_batch_set_tuning(b, t)
+            assert e.value.status == hmi.HMI_ERR_INVALID_ARG
+    finally:
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
+
+
+def test_autotune_keeps_stream_state():
+    """Autotuning a batch between ticks leaves its streams' later results as
+    if it had not run (click state and pointer history are restored), and
+    returns a valid launch shape that is then in force."""
+    idx = [2, 17, 35, 52, 60]
+    T = 6
+    frames = [[_dev(synth.run_frame(4, i, t)) for i in idx] for t in range(T + 1)]
+    ga, _ = _batch_streams(4, idx)
+    gb, _ = _batch_streams(4, idx)
+    ba = hmi.hmi_batch_create([g.handle for g in ga])
+    bb = hmi.hmi_batch_create([g.handle for g in gb])
+    s = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name, b in (("a", ba), ("b", bb)):
+        res = []
+        for t in range(T):
+            if name == "b" and t == 3:
+                tuning, us = hmi.hmi_batch_autotune(b, frames[T], 4, t % 2 == 0)
+                assert us > 0 and hmi.hmi_batch_get_tuning(b)["piece_chunks"] == tuning["piece_chunks"]
+            p = torch.zeros(len(idx) * 40, dtype=torch.uint8, device="cuda")
+            hmi.hmi_batch_process_async(b, frames[t], None, p.data_ptr(), s, False)
+            res.append(p)
+        torch.cuda.synchronize()
+        out[name] = [r.cpu().numpy().view(hmi.POINTER_DTYPE) for r in res]
+    for t in range(T):
+        assert np.array_equal(out["a"][t], out["b"][t]), t
+    for b in (ba, bb):
+        hmi.hmi_batch_destroy(b)
+    for g in ga + gb:
+        g.close()
