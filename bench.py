@@ -54,10 +54,15 @@ def peaks() -> tuple[float, str]:
 
 
 def kernel_source_hash() -> str:
+    """Hash of the per-pixel kernels' code (comments and blank lines left out,
+    so that a comment edit does not orphan the committed counters)."""
     h = hashlib.sha256()
     for f in ("hmi_frame.cu", "hmi_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1907_04393_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1907_04393_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
@@ -207,6 +212,23 @@ class OraclePool:
             p.join(timeout=10)
 
 
+def max_over_ranks(x: float, dev) -> float:
+    """The slowest rank's time (every rank gets it); x itself with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time (weak scaling: each rank runs the same workload)."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def host_workers(n_streams: int) -> int:
     return max(1, min(os.cpu_count() or 1, 16, n_streams))
 
@@ -352,11 +374,7 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     barrier()
     t1 = time.time()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     clk = clocks.summary(t0, t1)
     clocks.stop()
 
@@ -408,11 +426,7 @@ def run_ours(args) -> None:
     s0 = time.perf_counter()
     for k in range(e2e_steps):
         hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], masks, host_ptrs)
-    e2e_s = time.perf_counter() - s0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - s0, dev)
     h2d = sum(int(host_frames[i][0].numel()) for i in range(n))
 
     # ---- single 640x480 stream (the other configuration of the metric) ---
@@ -437,8 +451,7 @@ def run_ours(args) -> None:
             dist.destroy_process_group()
         return
     peak, peak_kind = peaks()
-    frames_total = n * args.steps * world
-    value = frames_total / (ms / 1e3)
+    value = whole_job_rate(n * args.steps, world, ms)
     classify_ms = prof_ms / max(prof_ticks, 1)
     achieved = CLASSIFY_BYTES_PER_PX * px_per_tick / (classify_ms / 1e3) / 1e9
     traffic_px = profiled_traffic_per_px()
@@ -532,15 +545,20 @@ def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
 
 
 def bench_serving(hmi, args) -> dict:
-    """The 256-stream serving workload: the arrival trace replayed in wall
-    time against the server with a device budget below the streams' demand,
-    then a sweep of arrival rates on shorter traces, served against plain
-    per-frame calls, for the highest frames/s at p99 <= 5 ms."""
+    """The 256-stream serving workload: a sweep of arrival rates on short
+    traces, served against plain per-frame calls, for the highest frames/s at
+    p99 <= 5 ms; then the full-length arrival trace replayed in wall time
+    against the server with a device budget below the streams' demand."""
     from paper_1907_04393_gb300 import serve, synth
     n_src = synth.num_streams(serve.CFG)
     bank = serve.FrameBank(range(n_src))
     demand = sum(hmi.hmi_stream_device_bytes(*synth.shape(serve.CFG, i)) for i in range(n_src))
     budget = int(demand * args.serve_budget)
+    # the rate sweep first, on fresh servers; then the full-length trace
+    rates = [float(x) for x in args.sweep_rates.split(",") if x]
+    sweep = None
+    if rates and args.sweep_seconds > 0:
+        sweep = serve.sweep(bank, rates, args.sweep_seconds)
     tr = serve.make_trace(args.serve_seconds)
     main_run = serve.run_served(tr, bank, budget)
     out = {"workload": "256 streams (128x320x240, 64x640x480, 48x1280x720, 16x1920x1080 RGB8), "
@@ -551,9 +569,8 @@ def bench_serving(hmi, args) -> dict:
            "latency": "completion (result available on the host) minus scheduled arrival; "
                       "pinned host frames, H2D copy inside",
            **main_run}
-    rates = [float(x) for x in args.sweep_rates.split(",") if x]
-    if rates and args.sweep_seconds > 0:
-        rows, best = serve.sweep(bank, rates, args.sweep_seconds)
+    if sweep is not None:
+        rows, best = sweep
         keep = ("frames_per_s", "offered_frames_per_s", "p50_ms", "p99_ms", "max_ms",
                 "dropped_queue_full", "errors", "frames_per_tick", "round_ms", "saturated",
                 "after_first_s", "submit_lag_ms_p99")
@@ -565,6 +582,7 @@ def bench_serving(hmi, args) -> dict:
         out["slo"] = f"p99 <= {serve.SLO_MS} ms, no errors, <= {serve.DROP_BUDGET:.0%} of offered frames dropped"
         out["plain_form"] = "one synchronous hmi_process_frame per frame in arrival order, one thread, " \
                             "streams learned before the trace (no learning work timed)"
+        out["order"] = "sweep first, then the full-length trace"
     return out
 
 

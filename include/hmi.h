@@ -317,15 +317,22 @@ HMI_API int hmi_server_stats(hmi_server *srv, size_t *bytes_admitted, uint64_t *
                              uint64_t *frames);
 HMI_API uint64_t hmi_server_now_ns(void);
 
-/* Per-round record of the dispatcher (the server's own timing trace). */
+/* Per-round record of the dispatcher (the server's own timing trace).  A
+ * round first creates newly admitted streams, retires released ones and
+ * re-makes the plan when they changed (setup), then takes at most one
+ * pending frame per stream and processes them; rounds that only did setup
+ * are recorded too (frames = learning = 0). */
 typedef struct {
-    uint64_t start_ns;     /* round start: frames taken from the queues */
+    uint64_t start_ns;     /* round start */
+    uint64_t setup_ns;     /* setup finished, frames taken from the queues */
     uint64_t issued_ns;    /* every copy and kernel of the round issued */
     uint64_t done_ns;      /* device work finished and results posted */
     int32_t frames;        /* frames processed by the round's tick */
     int32_t learning;      /* learning frames accumulated in the round */
     int32_t streams;       /* streams in the plan */
-    int32_t replanned;     /* 1 if the plan was re-made at the round's start */
+    int32_t replanned;     /* 1 if the plan was re-made in the setup */
+    int32_t created;       /* streams created in the setup */
+    int32_t retired;       /* streams retired in the setup */
 } hmi_server_round;
 
 /* Copy up to max_rounds of the most recent rounds (oldest first; the server

@@ -1346,6 +1346,13 @@ uint8_t *pool_get(hmi_server *v, size_t bytes)
 // One dispatcher round; returns false when there was nothing to do.
 constexpr int kRoundLog = 16384;
 
+void log_round(hmi_server *v, const hmi_server_round &rec)   // under v->mu
+{
+    if (v->rounds.size() < (size_t)kRoundLog) v->rounds.push_back(rec);
+    else v->rounds[v->rounds_written % kRoundLog] = rec;
+    v->rounds_written += 1;
+}
+
 bool server_round(hmi_server *v)
 {
     std::vector<SrvTake> take;
@@ -1394,6 +1401,8 @@ bool server_round(hmi_server *v)
         }
         if (posted) v->done_cv.notify_all();
     }
+    rec.created = (int32_t)creates.size();
+    rec.retired = (int32_t)dead.size();
     if (!creates.empty()) {
         // device state of newly admitted streams, in the order of this
         // thread's CUDA stream (all later work on them runs on it too)
@@ -1450,7 +1459,15 @@ bool server_round(hmi_server *v)
                 any = true;
             }
         }
-        if (!any) return rec.replanned != 0;
+        rec.setup_ns = now_ns();
+        if (!any) {
+            if (rec.replanned || rec.created || rec.retired) {
+                rec.issued_ns = rec.done_ns = rec.setup_ns;
+                rec.streams = (int32_t)v->plan_ids.size();
+                log_round(v, rec);
+            }
+            return rec.replanned != 0;
+        }
     }
     hmi_batch *b = v->plan;
     const int n = b ? b->n : 0;
@@ -1574,9 +1591,7 @@ bool server_round(hmi_server *v)
         v->frames += 1;
         if (!take[i].learning) rec.frames += 1;
     }
-    if (v->rounds.size() < (size_t)kRoundLog) v->rounds.push_back(rec);
-    else v->rounds[v->rounds_written % kRoundLog] = rec;
-    v->rounds_written += 1;
+    log_round(v, rec);
     lk.unlock();
     v->done_cv.notify_all();
     return true;

@@ -1,13 +1,12 @@
 // hmi_cc.cu -- connected components across 32x32 blocks and the pointer
 // (Mouse module, Sec. 2: the binary image's hand zone becomes a pointer with a
 // position and a click state).
-//   k_merge    union-find over the block components that touch across block
-//              borders (8-connected); the root of every set is its component
-//              with the smallest key (smallest pixel index), by hooking the
-//              root with the larger key under the one with the smaller key
-//   k_resolve  adds every non-root's statistics into its root
-//   k_pointer  largest root (ties: smaller label) per stream, then the last
-//              CTA writes every stream's pointer and steps its click state
+//   k_finish   one CTA per stream: union-find over the block components that
+//              touch across block borders (8-connected), the root of every set
+//              being its component with the smallest key (smallest pixel
+//              index: the larger-key root is hooked under the smaller), the
+//              statistics of non-roots added into their roots, the largest
+//              root (ties: smaller label), the pointer and the click state
 //   k_labels   per-pixel labels on demand (label = root key), same component
 //              enumeration as the tick's block pass
 // Every retry loop is bounded; overruns set an error flag in the stream state.

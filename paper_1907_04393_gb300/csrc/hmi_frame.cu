@@ -1,15 +1,19 @@
 // hmi_frame.cu -- per-pixel kernels of a tick:
-//   k_luma      frame luma sum per stream; the last CTA turns the sums into the
-//               brightness gains (Sec. 2 "the brightness is also corrected",
-//               Sec. 3.2 luminosity filter)
-//   k_classify  gain, background band test, gray test and hue test, ANDed into
-//               one bit per pixel (Sec. 3.1 (i)-(iii) and the merging step)
-//   k_morph_cc  opening/closing on the bit mask (Sec. 3.1 "erosion and
-//               dilatation"), the 0/1 mask bytes, and the 8-connected
-//               components of each 32x32 block with their statistics (Mouse
-//               module, Sec. 2)
-// All three are pure integer/bit work and bound by HBM bandwidth; nothing here
-// is a dense contraction, so no tensor-core path is used.
+//   k_luma        frame luma sum per stream; the last CTA turns the sums into the
+//                 brightness gains (Sec. 2 "the brightness is also corrected",
+//                 Sec. 3.2 luminosity filter)
+//   k_classify    gain and background band test (Sec. 3.1 (i)) of every pixel,
+//                 one bit per pixel; chunks with out-of-band pixels are queued
+//   k_skin        gray and hue tests (Sec. 3.1 (ii), (iii)) of the queued
+//                 pixels, clearing those that fail (the AND of the merging step)
+//   k_morph_strip opening/closing on the bit mask (Sec. 3.1 "erosion and
+//                 dilatation") in registers, the 0/1 mask bytes, and the list
+//                 of 32x32 blocks holding foreground
+//   k_block_cc    8-connected components of each listed block with their
+//                 statistics (Mouse module, Sec. 2)
+//   k_morph_cc    generic form of the last two for mixed morphology settings
+// All are integer/bit work, bound by HBM bandwidth, issue rate or latency;
+// nothing here is a dense contraction, so no tensor-core path is used.
 #include <algorithm>
 
 #include "hmi_ccfill.cuh"

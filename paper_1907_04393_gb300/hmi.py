@@ -63,10 +63,11 @@ class hmi_tuning(ctypes.Structure):
 
 
 class hmi_server_round(ctypes.Structure):
-    _fields_ = [("start_ns", ctypes.c_uint64), ("issued_ns", ctypes.c_uint64),
-                ("done_ns", ctypes.c_uint64), ("frames", ctypes.c_int32),
-                ("learning", ctypes.c_int32), ("streams", ctypes.c_int32),
-                ("replanned", ctypes.c_int32)]
+    _fields_ = [("start_ns", ctypes.c_uint64), ("setup_ns", ctypes.c_uint64),
+                ("issued_ns", ctypes.c_uint64), ("done_ns", ctypes.c_uint64),
+                ("frames", ctypes.c_int32), ("learning", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("replanned", ctypes.c_int32),
+                ("created", ctypes.c_int32), ("retired", ctypes.c_int32)]
 
 
 POINTER_DTYPE = np.dtype([(k, np.dtype(t._type_)) for k, t in hmi_pointer._fields_])

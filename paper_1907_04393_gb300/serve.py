@@ -275,8 +275,13 @@ def _run_served(trace: Trace, bank: FrameBank, budget_bytes: int, n_learn: int,
     out["submit_lag_ms_p99"] = float(np.percentile(np.asarray(lag, np.float64), 99)) * 1e-6 if lag else 0.0
     if len(rounds):
         busy = (rounds["done_ns"] - rounds["start_ns"]).astype(np.float64) * 1e-6
+        setup = (rounds["setup_ns"] - rounds["start_ns"]).astype(np.float64) * 1e-6
+        changed = (rounds["created"] > 0) | (rounds["retired"] > 0) | (rounds["replanned"] > 0)
         out["round_ms"] = {"p50": float(np.percentile(busy, 50)), "p99": float(np.percentile(busy, 99)),
-                           "of_last": int(len(rounds))}
+                           "max": float(busy.max()), "of_last": int(len(rounds)),
+                           "setup_rounds": int(changed.sum()),
+                           "setup_max": float(setup.max()),
+                           "setup_p99_of_setup_rounds": float(np.percentile(setup[changed], 99)) if changed.any() else 0.0}
     return out
 
 

@@ -29,7 +29,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_params) == 28
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
-    assert ctypes.sizeof(hmi.hmi_server_round) == 40
+    assert ctypes.sizeof(hmi.hmi_server_round) == 56
     assert ctypes.sizeof(hmi.hmi_tuning) == 20
 
 
