@@ -174,13 +174,16 @@ HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, 
  * (0 = as many as fit, else 1..32); skin_ctas_per_sm, cc_ctas_per_sm: grid
  * of the gray/hue pass and of the block-component pass, in CTAs per SM
  * (1..32, default 8); groups: stream groups of plain ticks (0 = min(2, n),
- * else 1..64).  Results never depend on the tuning. */
+ * else 1..64); pipeline_depth: stages of a pipelined tick (2 or 3, see
+ * hmi_batch_process_pipelined; default 2).  Results never depend on the
+ * tuning. */
 typedef struct {
     int32_t piece_chunks;
     int32_t luma_ctas_per_sm;
     int32_t skin_ctas_per_sm;
     int32_t cc_ctas_per_sm;
     int32_t groups;
+    int32_t pipeline_depth;
 } hmi_tuning;
 
 /* Replace the batch's launch shape (re-makes the plan; waits for the device).
@@ -191,8 +194,8 @@ HMI_API int hmi_batch_get_tuning(const hmi_batch *b, hmi_tuning *t);
 /* Search the launch shape (Sec. 3.3: the GPU computation is autotuned):
  * time `ticks` ticks (2..10000) of frames (device memory, one per stream) for
  * each candidate, changing one parameter at a time (piece size, then the
- * luma, skin and block-component grids, then the group count for plain
- * ticks), keep the fastest, apply it and return it in *best with its time per
+ * luma, skin and block-component grids, then the pipeline depth for pipelined
+ * ticks or the group count for plain ticks), keep the fastest, apply it and return it in *best with its time per
  * tick in microseconds (either may be NULL).  pipelined != 0 times pipelined
  * ticks (one group), else plain graph ticks.  The streams' click state and
  * pointer history are restored afterwards; their last labels are those of the
@@ -201,16 +204,18 @@ HMI_API int hmi_batch_autotune(hmi_batch *b, const uint8_t *const *frames, int t
                                hmi_tuning *best, double *best_tick_us);
 
 /* Pipelined ticks, for plans with one group (HMI_ERR_INVALID_ARG otherwise;
- * see hmi_batch_set_groups).  A tick runs in two stages: stage 1 computes the
- * gains and the background band test (bandwidth-bound), stage 2 the gray and
- * hue tests, morphology, components and pointer (latency-bound).  Each call
- * enqueues stage 1 of its own frames and, beside it on the device, stage 2 of
- * the previous pipelined call's frames, so the two overlap.  Buffers as in
- * hmi_batch_process_async.  The results of a call (its masks and ptrs) are
- * complete once cuda_stream has passed the NEXT pipelined call on the batch,
- * or hmi_batch_flush; its frames must stay valid and unchanged until then.
- * Every other processing call on the batch flushes first.  Results equal
- * those of hmi_batch_process_async on the same frames. */
+ * see hmi_batch_set_groups).  A tick is split into D stages (D = the tuning's
+ * pipeline_depth): with D = 2, {gains, background band test} (bandwidth-
+ * bound) and {gray and hue tests, morphology, components, pointer} (latency-
+ * bound); with D = 3, {gains}, {band test} and the same last stage.  Each call
+ * enqueues the first stage of its own frames and, beside it on the device,
+ * stage j of the frames of the call j calls earlier, so D ticks overlap.
+ * Buffers as in hmi_batch_process_async.  The results of a call (its masks
+ * and ptrs) are complete once cuda_stream has passed the (D-1)-th pipelined
+ * call after it on the batch, or hmi_batch_flush; its frames must stay valid
+ * and unchanged until then.  Every other processing call on the batch (and
+ * any change of its tuning) flushes first.  Results equal those of
+ * hmi_batch_process_async on the same frames. */
 HMI_API int hmi_batch_process_pipelined(hmi_batch *b, const uint8_t *const *frames,
                                         uint8_t *const *masks, hmi_pointer *ptrs,
                                         void *cuda_stream, int use_graph);

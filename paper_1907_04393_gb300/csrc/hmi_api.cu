@@ -52,11 +52,12 @@ int cuda_fail(cudaError_t e)
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
 
-constexpr int kRing = 8;          // per-tick pointer slots of a launch plan
+constexpr int kRing = 12;         // per-tick pointer slots of a launch plan (a multiple of kPhases)
 // Default launch shape (hmi_tuning): 16-px chunks per CTA piece of the
 // per-pixel kernels (512 = 8192 px), luma CTAs per SM (0 = as many as fit),
-// skin-test and block-component CTAs per SM, stream groups (0 = min(2, n)).
-constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0};
+// skin-test and block-component CTAs per SM, stream groups (0 = min(2, n)),
+// stages of a pipelined tick.
+constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -109,8 +110,8 @@ struct Arena {
 
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
-    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw, raw2, bits, comp, parent, count, flag, mask, st,
-        hist, ds, ptr, total;
+    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits, comp, parent, count, flag, mask,
+        st, hist, ds, ptr, total;
 };
 
 Layout make_layout(int w, int h, const hmi_params &p)
@@ -134,8 +135,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.Q = a.take(L.npx * 3 * 4);
     L.vmin = a.take(L.npx * 3);
     L.vmax = a.take(L.npx * 3);
-    L.raw = a.take(bitrows);
-    L.raw2 = a.take(bitrows);   // second tick parity (pipelined ticks)
+    for (int k = 0; k < kPhases; ++k) L.raw[k] = a.take(bitrows);   // one per tick phase
     L.bits = a.take(bitrows);
     L.comp = a.take(nblk * kSlots * sizeof(Comp));
     L.parent = a.take(nblk * kSlots * 4);
@@ -227,9 +227,9 @@ struct hmi_stream {
 // One chain of tick kernels over a subset of the batch's streams.
 struct Group {
     int off = 0, cnt = 0;         // range in the permuted stream order
-    BatchDev bd{};                // io, parity and skin queue are set per tick slot
-    uint32_t *skin_count_p[2] = {};   // skin queue of each tick parity
-    uint2 *skin_list_p[2] = {};
+    BatchDev bd{};                // io, phase and skin queue are set per tick slot
+    uint32_t *skin_count_p[kPhases] = {};   // skin queue of each tick phase
+    uint2 *skin_list_p[kPhases] = {};
     cudaStream_t cs = nullptr;    // branch stream (also joins graph capture)
     cudaEvent_t ev_luma = nullptr, ev_done = nullptr;
 };
@@ -264,11 +264,17 @@ struct hmi_batch {
     cudaGraphExec_t pgraph[kRing] = {};
     cudaGraphNode_t ev_node[kRing][kTickKernels + 1] = {};
     cudaEvent_t dummy_ev[kTickKernels + 1] = {};
-    // pipelined ticks (single group): the slot whose second stage is still to
-    // run (-1: none), an event at the end of the last pipelined call, and the
-    // graphs of "stage 1 of slot s beside stage 2 of slot s - 1"
-    int pending = -1;
+    // pipelined ticks (single group): slots of the ticks still in flight,
+    // newest first (pend[j] has run stages 0 .. j and runs stage j + 1 next),
+    // the depth they were started with, an event at the end of the last
+    // pipelined call, a second branch stream and the branches' end events,
+    // and per slot the graph of a full pipelined call
+    int npend = 0;
+    int pend[kPhases - 1] = {};
+    int pend_depth = 0;
     cudaEvent_t pipe_ev = nullptr;
+    cudaStream_t cs2 = nullptr;
+    cudaEvent_t side_done[kPhases - 1] = {};
     cudaGraphExec_t pipe_graph[kRing] = {};
     // profiling of the classification kernel (single-group plans)
     std::vector<cudaEvent_t> prof_ev;
@@ -314,8 +320,7 @@ void fill_devstream(hmi_stream *s)
     hue_intervals(s->p.hue_lo, s->p.hue_hi, D.hueA, D.hueB);
     D.lo = a + L.lo;
     D.hi = a + L.hi;
-    D.raw[0] = reinterpret_cast<uint32_t *>(a + L.raw);
-    D.raw[1] = reinterpret_cast<uint32_t *>(a + L.raw2);
+    for (int k = 0; k < kPhases; ++k) D.raw[k] = reinterpret_cast<uint32_t *>(a + L.raw[k]);
     D.bits = reinterpret_cast<uint32_t *>(a + L.bits);
     D.comp = reinterpret_cast<Comp *>(a + L.comp);
     D.parent = reinterpret_cast<uint32_t *>(a + L.parent);
@@ -364,7 +369,7 @@ int batch_free(hmi_batch *b)
 {
     if (!b) return HMI_OK;
     cudaSetDevice(b->dev);
-    if (b->cs && b->pending >= 0) flush_pending(b, b->cs);
+    if (b->cs && b->npend > 0) flush_pending(b, b->cs);
     if (b->cs) cudaStreamSynchronize(b->cs);
     for (int i = 0; i < kRing; ++i)
         if (b->slot_ev[i]) cudaEventSynchronize(b->slot_ev[i]);
@@ -377,6 +382,9 @@ int batch_free(hmi_batch *b)
     for (auto e : b->prof_ev) cudaEventDestroy(e);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->pipe_ev) cudaEventDestroy(b->pipe_ev);
+    for (auto e : b->side_done)
+        if (e) cudaEventDestroy(e);
+    if (b->cs2) cudaStreamDestroy(b->cs2);
     if (b->cs) cudaStreamDestroy(b->cs);
     if (b->arena) cudaFree(b->arena);
     if (b->h_io) cudaFreeHost(b->h_io);
@@ -432,7 +440,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn, o_skl, o_skn2, o_skl2;
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn[kPhases], o_skl[kPhases];
     };
     std::vector<Tables> T(ng);
     Arena a;
@@ -467,10 +475,10 @@ int plan_build(hmi_batch *b, int ng)
         t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
         t.o_ccn = a.take(sizeof(uint32_t));
         t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
-        t.o_skn = a.take(sizeof(uint32_t));
-        t.o_skl = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
-        t.o_skn2 = a.take(sizeof(uint32_t));
-        t.o_skl2 = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
+        for (int k = 0; k < kPhases; ++k) {
+            t.o_skn[k] = a.take(sizeof(uint32_t));
+            t.o_skl[k] = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
+        }
     }
     if (a.off > b->plan_cap) {   // grow the table buffer; a smaller plan reuses it
         if (b->plan) cudaFree(b->plan);
@@ -525,13 +533,13 @@ int plan_build(hmi_batch *b, int ng)
         bd.err = b->d_err;
         bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
         bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
-        G.skin_count_p[0] = reinterpret_cast<uint32_t *>(A + t.o_skn);
-        G.skin_list_p[0] = reinterpret_cast<uint2 *>(A + t.o_skl);
-        G.skin_count_p[1] = reinterpret_cast<uint32_t *>(A + t.o_skn2);
-        G.skin_list_p[1] = reinterpret_cast<uint2 *>(A + t.o_skl2);
+        for (int k = 0; k < kPhases; ++k) {
+            G.skin_count_p[k] = reinterpret_cast<uint32_t *>(A + t.o_skn[k]);
+            G.skin_list_p[k] = reinterpret_cast<uint2 *>(A + t.o_skl[k]);
+        }
         bd.skin_count = G.skin_count_p[0];
         bd.skin_list = G.skin_list_p[0];
-        bd.parity = 0;
+        bd.phase = 0;
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
         bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
         bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
@@ -607,7 +615,10 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
               cudaMallocHost(&b->h_err, sizeof(uint32_t)) == cudaSuccess &&
               cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b->pipe_ev, cudaEventDisableTiming) == cudaSuccess;
+              cudaEventCreateWithFlags(&b->pipe_ev, cudaEventDisableTiming) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&b->cs2, cudaStreamNonBlocking) == cudaSuccess;
+    for (auto &e : b->side_done)
+        ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i < kRing; ++i)
         ok = cudaEventCreateWithFlags(&b->slot_ev[i], cudaEventDisableTiming) == cudaSuccess;
     for (int i = 0; ok && i <= kTickKernels; ++i) ok = cudaEventCreate(&b->dummy_ev[i]) == cudaSuccess;
@@ -636,16 +647,17 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
 // passes of later groups overlap the latency-bound tail of earlier ones.
 // With one group, event records (or event nodes) bracket the classify kernel.
 // Launch parameters of group G for the tick in `slot`: its pointer table, and
-// the tick parity (slot & 1, the ring being even) that picks the raw bits, the
-// gains and the skin queue, so that consecutive ticks never share them.
+// the tick phase (slot mod kPhases; slots are taken in turn and the ring is a
+// multiple of kPhases) that picks the raw bits, the gains and the skin queue,
+// so that up to kPhases consecutive ticks never share them.
 BatchDev tick_dev(const hmi_batch *b, const Group &G, int slot)
 {
-    static_assert(kRing % 2 == 0, "slot parity must alternate");
+    static_assert(kRing % kPhases == 0, "consecutive slots must have distinct phases");
     BatchDev bd = G.bd;
     bd.io = b->d_io + (size_t)slot * b->n + G.off;
-    bd.parity = slot & 1;
-    bd.skin_count = G.skin_count_p[bd.parity];
-    bd.skin_list = G.skin_list_p[bd.parity];
+    bd.phase = slot % kPhases;
+    bd.skin_count = G.skin_count_p[bd.phase];
+    bd.skin_list = G.skin_list_p[bd.phase];
     return bd;
 }
 
@@ -671,10 +683,6 @@ cudaError_t enqueue_kernels(hmi_batch *b, int slot, cudaStream_t cs, int k0, int
     return cudaSuccess;
 }
 
-// Stage 1 of a tick: luma and gains, then the band test (kernels 0, 1).
-// Stage 2: gray and hue tests, morphology, block components, finish (2 .. 5).
-constexpr int kStage2 = 2;
-
 cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEvent_t *ev, bool capture)
 {
     cudaError_t e;
@@ -698,30 +706,57 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
     return cudaSuccess;
 }
 
-// Pipelined tick (single group): stage 1 of `slot` on cs, and beside it, on
-// the group's branch stream, stage 2 of `prev` (if >= 0); cs then waits for
-// both.  The two touch disjoint per-tick state (their parities differ).
-cudaError_t enqueue_pipelined(hmi_batch *b, int slot, int prev, cudaStream_t cs)
+// Stages of a pipelined tick: the first kernel of each of its `depth` stages,
+// then kTickKernels.  Depth 2: {luma, band test} {gray/hue, morphology,
+// blocks, finish}; depth 3: {luma} {band test} {gray/hue .. finish}.  The
+// first stages are bandwidth-bound, the last is latency-bound.
+void stage_bounds(int depth, int *first)
 {
+    if (depth >= 3) {
+        first[0] = 0;
+        first[1] = 1;
+        first[2] = 2;
+        first[3] = kTickKernels;
+    } else {
+        first[0] = 0;
+        first[1] = 2;
+        first[2] = kTickKernels;
+    }
+}
+
+// One pipelined call (single group): stage 0 of `slot` on cs and, beside it,
+// stage j + 1 of the in-flight tick pend[j] on branch stream j; cs then waits
+// for the branches.  Concurrent stages belong to consecutive ticks, whose
+// phases differ, so they touch disjoint per-tick state.
+cudaError_t enqueue_pipelined(hmi_batch *b, int slot, const int *pend, int npend, int depth, cudaStream_t cs)
+{
+    int first[kPhases + 1];
+    stage_bounds(depth, first);
+    cudaStream_t side[kPhases - 1] = {b->groups[0].cs, b->cs2};
     cudaError_t e;
-    Group &G = b->groups[0];
-    if (prev >= 0) {
-        if ((e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(G.cs, b->ev_fork, 0)) != cudaSuccess) return e;
-        if ((e = enqueue_kernels(b, prev, G.cs, kStage2, kTickKernels, nullptr, false)) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(G.ev_done, G.cs)) != cudaSuccess) return e;
+    if (npend > 0 && (e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
+    for (int j = 0; j < npend; ++j) {
+        if ((e = cudaStreamWaitEvent(side[j], b->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = enqueue_kernels(b, pend[j], side[j], first[j + 1], first[j + 2], nullptr, false)) != cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(b->side_done[j], side[j])) != cudaSuccess) return e;
     }
     if ((e = upload_io(b, slot, cs)) != cudaSuccess) return e;
-    if ((e = enqueue_kernels(b, slot, cs, 0, kStage2, nullptr, false)) != cudaSuccess) return e;
-    if (prev >= 0 && (e = cudaStreamWaitEvent(cs, G.ev_done, 0)) != cudaSuccess) return e;
+    if ((e = enqueue_kernels(b, slot, cs, first[0], first[1], nullptr, false)) != cudaSuccess) return e;
+    for (int j = 0; j < npend; ++j)
+        if ((e = cudaStreamWaitEvent(cs, b->side_done[j], 0)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
-int build_pipe_graph(hmi_batch *b, int slot)
+// Graph of a full pipelined call in `slot` (every earlier stage in flight:
+// the ticks of the depth - 1 slots before it).
+int build_pipe_graph(hmi_batch *b, int slot, int depth)
 {
+    int pend[kPhases - 1];
+    for (int j = 0; j + 1 < depth; ++j) pend[j] = (slot + kRing - 1 - j) % kRing;
     cudaGraph_t g = nullptr;
     HMI_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_pipelined(b, slot, (slot + kRing - 1) % kRing, b->cs);
+    cudaError_t e = enqueue_pipelined(b, slot, pend, depth - 1, depth, b->cs);
     cudaError_t e2 = cudaStreamEndCapture(b->cs, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -736,15 +771,20 @@ int build_pipe_graph(hmi_batch *b, int slot)
     return HMI_OK;
 }
 
-// Run the second stage of the pending pipelined tick on cs.
+// Run the remaining stages of the in-flight pipelined ticks on cs, oldest
+// first.
 int flush_pending(hmi_batch *b, cudaStream_t cs)
 {
-    if (b->pending < 0) return HMI_OK;
-    const int prev = b->pending;
-    b->pending = -1;
+    if (b->npend == 0) return HMI_OK;
+    int first[kPhases + 1];
+    stage_bounds(b->pend_depth, first);
+    const int npend = b->npend;
+    b->npend = 0;
     HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
-    HMI_CUDA(enqueue_kernels(b, prev, cs, kStage2, kTickKernels, nullptr, false));
-    HMI_CUDA(cudaEventRecord(b->slot_ev[prev], cs));
+    for (int j = npend - 1; j >= 0; --j) {
+        HMI_CUDA(enqueue_kernels(b, b->pend[j], cs, first[j + 1], kTickKernels, nullptr, false));
+        HMI_CUDA(cudaEventRecord(b->slot_ev[b->pend[j]], cs));
+    }
     return HMI_OK;
 }
 
@@ -955,22 +995,33 @@ int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *
     if (st != HMI_OK) return st;
     TickIO *io = b->h_io + (size_t)slot * b->n;
     for (int i = 0; i < b->n; ++i) io[b->pos[i]].ptr_out = ptrs ? ptrs + i : nullptr;
-    const int prev = b->pending;
-    if (prev >= 0) HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
-    if (use_graph && prev == (slot + kRing - 1) % kRing) {
+    const int depth = b->tune.pipeline_depth;
+    const int npend = b->npend;
+    int pend[kPhases - 1];
+    for (int j = 0; j < npend; ++j) pend[j] = b->pend[j];
+    bool full = npend == depth - 1;
+    for (int j = 0; j < npend; ++j) full = full && pend[j] == (slot + kRing - 1 - j) % kRing;
+    if (npend > 0) HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
+    if (use_graph && full) {
         if (!b->pipe_graph[slot]) {
-            st = build_pipe_graph(b, slot);
+            st = build_pipe_graph(b, slot, depth);
             if (st != HMI_OK) return st;
         }
         HMI_CUDA(cudaGraphLaunch(b->pipe_graph[slot], cs));
     } else {
-        HMI_CUDA(enqueue_pipelined(b, slot, prev, cs));
+        HMI_CUDA(enqueue_pipelined(b, slot, pend, npend, depth, cs));
     }
     HMI_CUDA(cudaEventRecord(b->slot_ev[slot], cs));
     b->slot_used[slot] = true;
-    if (prev >= 0) HMI_CUDA(cudaEventRecord(b->slot_ev[prev], cs));
+    for (int j = 0; j < npend; ++j) HMI_CUDA(cudaEventRecord(b->slot_ev[pend[j]], cs));
     HMI_CUDA(cudaEventRecord(b->pipe_ev, cs));
-    b->pending = slot;
+    // pend[j] has now run stage j + 1; it stays in flight while stages remain
+    b->pend[0] = slot;
+    int k = 1;
+    for (int j = 0; j < npend && k < depth - 1; ++j)
+        if (j + 2 < depth) b->pend[k++] = pend[j];
+    b->npend = std::min(k, depth - 1);
+    b->pend_depth = depth;
     return HMI_OK;
 }
 
@@ -981,7 +1032,7 @@ bool tuning_ok(const hmi_tuning &t)
     return t.piece_chunks >= 32 && t.piece_chunks <= 65536 && t.piece_chunks % 32 == 0 &&
            t.luma_ctas_per_sm >= 0 && t.luma_ctas_per_sm <= 32 && t.skin_ctas_per_sm >= 1 &&
            t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
-           t.groups >= 0 && t.groups <= 64;
+           t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases;
 }
 
 // Apply a launch shape: the plan is re-made with the device idle.
@@ -1072,7 +1123,8 @@ int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool p
                               {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
                               {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},
                               {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}}};
-    if (!pipelined) axes.push_back({&hmi_tuning::groups, {1, 2, 3}});
+    if (pipelined) axes.push_back({&hmi_tuning::pipeline_depth, {2, 3}});
+    else axes.push_back({&hmi_tuning::groups, {1, 2, 3}});
     for (const Axis &ax : axes) {
         for (int32_t v : ax.values) {
             if (st != HMI_OK || cur.*ax.field == v) continue;

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
         if (g < D.gain_min) g = D.gain_min;
         if (g > D.gain_max) g = D.gain_max;
         st->gain = (uint32_t)g;
-        st->gain_p[b.parity] = (uint32_t)g;
+        st->gain_p[b.phase] = (uint32_t)g;
         st->sy = 0;
     }
     if (tid == 0) b.done[0] = 0;
@@ -272,10 +272,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         const DevStream &D = b.ds[piece.x];
         const TickIO io = b.io[piece.x];
         if (io.frame == nullptr) continue;   // no frame for this stream this tick
-        const uint32_t g = D.st->gain_p[b.parity];
+        const uint32_t g = D.st->gain_p[b.phase];
         const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
         const uint8_t *lo = D.lo, *hi = D.hi;
-        uint32_t *raw = D.raw[b.parity];
+        uint32_t *raw = D.raw[b.phase];
         // warp-uniform loop so that chunk pairs can combine with a shuffle
         for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
             const int u = base + lane;
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
         const int u = (int)e.y;
         const DevStream &D = b.ds[sidx];
         const TickIO io = b.io[sidx];
-        const uint32_t g = D.st->gain_p[b.parity];
+        const uint32_t g = D.st->gain_p[b.phase];
         const int cpr = 2 * D.nwords;
         const int y = chunk_row((uint32_t)u, D.cpr_magic), j = u - y * cpr;
         const uint8_t *row = io.frame + (long long)y * io.frame_pitch + 3 * j * kChunkPx;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
                 if (!skin_rgb(__ldg(px), __ldg(px + 1), __ldg(px + 2), D, g)) fail |= 1u << k;
             }
         }
-        if (fail) atomicAnd(D.raw[b.parity] + (long long)y * D.nwords + (j >> 1), ~(fail << (16 * (j & 1))));
+        if (fail) atomicAnd(D.raw[b.phase] + (long long)y * D.nwords + (j >> 1), ~(fail << (16 * (j & 1))));
     }
 }
 
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     if (io.frame == nullptr) return;       // no frame for this stream this tick
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
-    morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, D.raw[b.parity]);
+    morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, D.raw[b.phase]);
 }
 
 // k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
@@ -598,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) k_morph_cc(BatchDev b)
     for (int i = tid; i < ncell; i += blockDim.x) {
         const int r = i / kMW, k = i - r * kMW;
         const int y = G.y0 - G.HR + r, kw = G.k0 - 1 + k;
-        buf[0][r][k] = (y >= 0 && y < G.h && kw >= 0 && kw < G.nwords) ? D.raw[b.parity][(long long)y * G.nwords + kw] : 0u;
+        buf[0][r][k] = (y >= 0 && y < G.h && kw >= 0 && kw < G.nwords) ? D.raw[b.phase][(long long)y * G.nwords + kw] : 0u;
     }
     __syncthreads();
 

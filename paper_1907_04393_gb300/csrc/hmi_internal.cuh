@@ -49,7 +49,7 @@ struct __align__(16) StreamState {
     unsigned long long best;      // packed (area, ~key) argmax (0 between frames)
     unsigned long long learn_luma;  // luma total over the learning frames
     uint32_t gain;                // Q16 gain of the last frame
-    uint32_t gain_p[2];           // Q16 gain of the frame of each tick parity
+    uint32_t gain_p[3];           // Q16 gain of the frame of each tick phase (kPhases)
     uint32_t err;                 // kErr* flags
     int32_t click;
     int32_t hist_count;
@@ -75,7 +75,7 @@ struct DevStream {
     // intervals of N = 512 (t + d) + d:  d*A <= N < d*B
     int hueA[3][2], hueB[3][2];
     const uint8_t *lo, *hi;       // background band, pitch fpitch, RGB interleaved
-    uint32_t *raw[2];             // raw AND mask bits, (bh*32) x nwords words, by tick parity
+    uint32_t *raw[3];             // raw AND mask bits, (bh*32) x nwords words, by tick phase
     uint32_t *bits;               // mask bits after morphology, same layout
     Comp *comp;                   // bh*nwords*kSlots records
     uint32_t *parent;             // union-find parent per record
@@ -125,13 +125,18 @@ struct BatchDev {
     uint2 *cc_list;                           // (stream, block) of each, total_blocks slots
     uint32_t *skin_count;                     // chunks queued for the skin tests this tick
     uint2 *skin_list;                         // ((stream << 16) | bits, chunk), total_chunks slots
-    int parity;                               // tick parity: selects raw[], gain_p[] and the skin
-                                              // queue, so that two ticks can be in flight
+    int phase;                                // tick phase (slot mod kPhases): selects raw[],
+                                              // gain_p[] and the skin queue, so that up to
+                                              // kPhases consecutive ticks can be in flight
     // launch shape (host side; chosen by the plan's tuning)
     int luma_ctas_per_sm;                     // 0: as many as fit
     int skin_ctas_per_sm;
     int cc_ctas_per_sm;
 };
+
+// Consecutive ticks in flight at once at most (pipelined ticks), and so the
+// number of copies of the per-tick state they would otherwise share.
+constexpr int kPhases = 3;
 
 // Threads per CTA of every kernel of a tick.
 constexpr int kThreads = 256;

@@ -56,7 +56,7 @@ class hmi_server_result(ctypes.Structure):
 class hmi_tuning(ctypes.Structure):
     _fields_ = [("piece_chunks", ctypes.c_int32), ("luma_ctas_per_sm", ctypes.c_int32),
                 ("skin_ctas_per_sm", ctypes.c_int32), ("cc_ctas_per_sm", ctypes.c_int32),
-                ("groups", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("pipeline_depth", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

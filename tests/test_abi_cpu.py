@@ -30,7 +30,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 56
-    assert ctypes.sizeof(hmi.hmi_tuning) == 20
+    assert ctypes.sizeof(hmi.hmi_tuning) == 24
 
 
 def test_defaults_and_status_strings():
@@ -97,7 +97,7 @@ def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
     def fake_search(b, frames, ticks, pipelined):
         calls["search"] += 1
         return {"piece_chunks": 256, "luma_ctas_per_sm": 0, "skin_ctas_per_sm": 8,
-                "cc_ctas_per_sm": 4, "groups": 1}, 99.5
+                "cc_ctas_per_sm": 4, "groups": 1, "pipeline_depth": 3}, 99.5
 
     monkeypatch.setattr(hmi, "hmi_batch_autotune", fake_search)
     monkeypatch.setattr(hmi, "hmi_batch_set_tuning", lambda b, t: calls["set"].append(dict(t)))

@@ -488,21 +488,22 @@ def test_profile_counts_classification_kernel():
     g.close()
 
 
-def test_pipelined_ticks_equal_async_ticks():
+@pytest.mark.parametrize("depth", [2, 3])
+def test_pipelined_ticks_equal_async_ticks(depth):
     """Two identically learned sets of streams: one processed tick by tick with
-    hmi_batch_process_async, the other with pipelined calls (stage 1 of a tick
-    beside stage 2 of the one before, graph and direct launches, an ordinary
+    hmi_batch_process_async, the other with pipelined calls (depth stages of
+    consecutive ticks side by side, graph and direct launches, an ordinary
     call in between, a final flush).  Every tick's masks and pointers agree,
     and a multi-group plan refuses pipelining."""
     idx = [0, 7, 20, 33, 41, 50, 58, 63]
-    T = 7
+    T = 9
     frames = [[_dev(synth.run_frame(4, i, t)) for i in idx] for t in range(T)]
     ga, _ = _batch_streams(4, idx)
     gb, _ = _batch_streams(4, idx)
     ba = hmi.hmi_batch_create([g.handle for g in ga])
     bb = hmi.hmi_batch_create([g.handle for g in gb])
     hmi.hmi_batch_set_groups(ba, 1)
-    hmi.hmi_batch_set_groups(bb, 1)
+    hmi.hmi_batch_set_tuning(bb, dict(hmi.hmi_batch_get_tuning(bb), groups=1, pipeline_depth=depth))
     s = torch.cuda.current_stream().cuda_stream
 
     def outs(gs):
@@ -515,7 +516,7 @@ def test_pipelined_ticks_equal_async_ticks():
         hmi.hmi_batch_process_async(ba, frames[t], m, p.data_ptr(), s, True)
         ref.append((m, p))
         m, p = outs(gb)
-        if t == 4:   # an ordinary call flushes the pending tick first
+        if t == 5:   # an ordinary call flushes the ticks in flight first
             hmi.hmi_batch_process_async(bb, frames[t], m, p.data_ptr(), s, False)
         else:
             hmi.hmi_batch_process_pipelined(bb, frames[t], m, p.data_ptr(), s, t % 3 != 0)
@@ -545,7 +546,7 @@ def test_tuning_does_not_change_results():
     b = hmi.hmi_batch_create([g.handle for g in gs])
     try:
         hmi.hmi_batch_set_tuning(b, {"piece_chunks": 128, "luma_ctas_per_sm": 2, "skin_ctas_per_sm": 4,
-                                     "cc_ctas_per_sm": 16, "groups": 3})
+                                     "cc_ctas_per_sm": 16, "groups": 3, "pipeline_depth": 3})
         assert hmi.hmi_batch_get_tuning(b)["piece_chunks"] == 128
         assert hmi.hmi_batch_get_groups(b) == 3
         for t in range(2):
@@ -556,7 +557,8 @@ def test_tuning_does_not_change_results():
             plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
             _compare_batch(gs, os_, frames, masks, plist, f"tuned t={t}")
         for bad in ({"piece_chunks": 100}, {"piece_chunks": 0}, {"skin_ctas_per_sm": 0},
-                    {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65}):
+                    {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65},
+                    {"pipeline_depth": 1}, {"pipeline_depth": 4}):
             t = dict(hmi.hmi_batch_get_tuning(b), **bad)
             with pytest.raises(hmi.HmiError) as e:
                 hmi.hmi_batch_set_tuning(b, t)
