@@ -85,6 +85,10 @@ def _load():
             "orc_label": (_I, [_P, _I, _I, _P]),
             "orc_pointer_from_labels": (None, [_P, _I, _I, _U32, _P]),
             "orc_click_update": (None, [_P, _P, _P, _I, _I, _I, _P]),
+            "orc_relearn_reset": (None, [_SZ, _P, _P, _P, _P, _P]),
+            "orc_relearn_accumulate": (None, [_P, _P, _P, _SZ, _P, _P, _P, _P, _P]),
+            "orc_relearn_apply": (None, [_P, _P, _P, _P, _P, _SZ, _I, _I, _I, _I, _P, _P]),
+            "orc_relearn_in_window": (_I, [ctypes.c_longlong, _I, _I]),
             "orc_process_frame": (None, [_P, _I, _I, _P, _P, _U64, _I, _I, _I, _I, _I,
                                          _U32, _U32, _U32, _I, _I, _I, _P, _P, _P,
                                          _P, _P, _P, _P]),
@@ -114,7 +118,8 @@ def _u8(a) -> np.ndarray:
 DEFAULTS = dict(gray_tol=15, hue_lo=1472, hue_hi=256, bg_margin=2, bg_k_num=5,
                 bg_k_den=2, open_iters=1, close_iters=1, gain_min_q16=32768,
                 gain_max_q16=131072, min_area=50, click_on_pct=80,
-                click_off_pct=90, click_window=30)
+                click_off_pct=90, click_window=30,
+                relearn_frames=0, relearn_min=0, relearn_period=0)
 
 
 def params(**over) -> dict:
@@ -278,6 +283,33 @@ class ClickState:
         return p.as_dict()
 
 
+class Relearn:
+    """Re-learning sums of one stream (orc_relearn_*), shaped (H, W, 3) / (H, W)."""
+
+    def __init__(self, h: int, w: int):
+        self.S = np.empty((h, w, 3), np.uint32)
+        self.Q = np.empty((h, w, 3), np.uint32)
+        self.vmin = np.empty((h, w, 3), np.uint8)
+        self.vmax = np.empty((h, w, 3), np.uint8)
+        self.cnt = np.empty((h, w), np.uint8)
+        _load().orc_relearn_reset(h * w, _ptr(self.S), _ptr(self.Q), _ptr(self.vmin),
+                                  _ptr(self.vmax), _ptr(self.cnt))
+
+    def accumulate(self, c, lo, hi) -> None:
+        _load().orc_relearn_accumulate(_ptr(c), _ptr(lo), _ptr(hi), self.cnt.size, _ptr(self.S),
+                                       _ptr(self.Q), _ptr(self.vmin), _ptr(self.vmax),
+                                       _ptr(self.cnt))
+
+    def apply(self, min_cnt: int, kn: int, kd: int, delta: int, lo, hi) -> None:
+        _load().orc_relearn_apply(_ptr(self.S), _ptr(self.Q), _ptr(self.vmin), _ptr(self.vmax),
+                                  _ptr(self.cnt), self.cnt.size, min_cnt, kn, kd, delta,
+                                  _ptr(lo), _ptr(hi))
+
+
+def relearn_in_window(f: int, period: int, frames: int) -> bool:
+    return bool(_load().orc_relearn_in_window(f, period, frames))
+
+
 class OracleStream:
     """The whole path for one camera stream: learn once, then process frames."""
 
@@ -298,6 +330,11 @@ class OracleStream:
                                       self.p["bg_k_den"], self.p["bg_margin"])
         self.syref = ref_luma(frames)
         self.learned = True
+        self._reset_relearn()
+
+    def _reset_relearn(self) -> None:
+        self.frames = 0
+        self.relearn = Relearn(self.h, self.w) if self.p["relearn_frames"] > 0 else None
 
     def set_background(self, S, Q, vmin, vmax, n: int, syref: int) -> None:
         """Install learned sums directly (the state learning would leave)."""
@@ -310,6 +347,7 @@ class OracleStream:
         self.syref = int(syref)
         self.click = ClickState(self.p["click_window"])
         self.learned = True
+        self._reset_relearn()
 
     def stats(self):
         return learn_meanstd(self.S, self.Q, self.n)
@@ -332,4 +370,12 @@ class OracleStream:
             p["click_off_pct"], c.window, ctypes.byref(c.click), _ptr(c.hist),
             ctypes.byref(c.count), _ptr(mask), _ptr(labels), ctypes.byref(ptr),
             ctypes.byref(g))
+        # re-learning (Sec. 3.3), after this frame's classification
+        self.frames += 1
+        if self.relearn is not None and relearn_in_window(self.frames, p["relearn_period"],
+                                                           p["relearn_frames"]):
+            self.relearn.accumulate(apply_gain(frame, g.value), self.lo, self.hi)
+            if self.frames % p["relearn_period"] == 0:
+                self.relearn.apply(p["relearn_min"], p["bg_k_num"], p["bg_k_den"], p["bg_margin"],
+                                   self.lo, self.hi)
         return mask, labels, ptr.as_dict(), g.value

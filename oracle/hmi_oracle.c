@@ -142,6 +142,78 @@ void orc_learn_band(const uint32_t *S, const uint32_t *Q,
 }
 
 /* ======================================================================== */
+/* Re-learning, Sec. 3.3: dealing with the evolution of the luminosity, the  */
+/* learning is sometimes re-initiated partly.                                 */
+/* Reading: with a period of P frames and a window of the last R of them,     */
+/* every frame of a window adds the gain-corrected values of the pixels that  */
+/* its background test classified as background (all three channels inside  */
+/* the current band) to per-pixel re-learning sums S', Q', min', max' and a   */
+/* count; after the window's last frame, every pixel counted at least         */
+/* `min_cnt` times gets the band of those sums with n = its count (the same  */
+/* formula as the initial band), the others keep theirs, and all sums are     */
+/* reset.  Frames are counted from 1 after learning; frame f belongs to a     */
+/* window iff (f - 1) mod P >= P - R, and ends it iff f mod P == 0.           */
+/* ======================================================================== */
+
+void orc_relearn_reset(size_t npx, uint32_t *S2, uint32_t *Q2, uint8_t *vmin2, uint8_t *vmax2,
+                       uint8_t *cnt)
+{
+    for (size_t j = 0; j < npx * 3; ++j) {
+        S2[j] = 0;
+        Q2[j] = 0;
+        vmin2[j] = 255;
+        vmax2[j] = 0;
+    }
+    for (size_t p = 0; p < npx; ++p) cnt[p] = 0;
+}
+
+/* c: gain-corrected frame (npx x 3). */
+void orc_relearn_accumulate(const uint8_t *c, const uint8_t *lo, const uint8_t *hi, size_t npx,
+                            uint32_t *S2, uint32_t *Q2, uint8_t *vmin2, uint8_t *vmax2,
+                            uint8_t *cnt)
+{
+    for (size_t p = 0; p < npx; ++p) {
+        int background = 1;
+        for (int k = 0; k < 3; ++k)
+            if (c[3 * p + k] < lo[3 * p + k] || c[3 * p + k] > hi[3 * p + k]) background = 0;
+        if (!background) continue;
+        cnt[p] += 1;
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t v = c[3 * p + k];
+            S2[3 * p + k] += v;
+            Q2[3 * p + k] += v * v;
+            if (v < vmin2[3 * p + k]) vmin2[3 * p + k] = (uint8_t)v;
+            if (v > vmax2[3 * p + k]) vmax2[3 * p + k] = (uint8_t)v;
+        }
+    }
+}
+
+void orc_relearn_apply(uint32_t *S2, uint32_t *Q2, uint8_t *vmin2, uint8_t *vmax2, uint8_t *cnt,
+                       size_t npx, int min_cnt, int kn, int kd, int delta, uint8_t *lo, uint8_t *hi)
+{
+    for (size_t p = 0; p < npx; ++p) {
+        const int n = cnt[p];
+        if (n >= min_cnt && n > 0) {
+            for (int k = 0; k < 3; ++k) {
+                const size_t j = 3 * p + k;
+                int64_t L = orc_band_low(S2[j], Q2[j], n, kn, kd);
+                int64_t H = orc_band_high(S2[j], Q2[j], n, kn, kd);
+                int64_t a = (L < vmin2[j] ? L : vmin2[j]) - delta;
+                int64_t b = (H > vmax2[j] ? H : vmax2[j]) + delta;
+                lo[j] = (uint8_t)(a < 0 ? 0 : (a > 255 ? 255 : a));
+                hi[j] = (uint8_t)(b < 0 ? 0 : (b > 255 ? 255 : b));
+            }
+        }
+    }
+    orc_relearn_reset(npx, S2, Q2, vmin2, vmax2, cnt);
+}
+
+int orc_relearn_in_window(long long f, int period, int frames)
+{
+    return period > 0 && frames > 0 && (int)((f - 1) % period) >= period - frames;
+}
+
+/* ======================================================================== */
 /* Step 1 -- brightness correction (Sec. 2 "The brightness is also corrected"; */
 /* Sec. 3.2 "a filter ... to modify the Luminosity component").               */
 /* Reading: the frame is rescaled so that its total luma equals the mean      */

@@ -461,3 +461,100 @@ def test_click_follows_open_closed_config2():
         _, _, p, _ = o.process(synth.run_frame(2, 0, t))
         agree += p["click"] == (0 if synth.truth(2, 0, t)[1] else 1)
     assert agree >= 0.8 * len(ts)
+
+
+# --------------------------------------------------------------------------- #
+# Re-learning (Sec. 3.3: the learning is re-initiated partly)                 #
+# --------------------------------------------------------------------------- #
+FIXED_GAIN = dict(gain_min_q16=65536, gain_max_q16=65536)   # c' = c: no brightness term
+
+
+def test_relearn_windows_are_the_last_frames_of_each_period():
+    got = [f for f in range(1, 31) if oracle.relearn_in_window(f, 10, 3)]
+    assert got == [8, 9, 10, 18, 19, 20, 28, 29, 30]
+    assert not any(oracle.relearn_in_window(f, 10, 0) for f in range(1, 31))
+    assert not any(oracle.relearn_in_window(f, 0, 3) for f in range(1, 31))
+    assert all(oracle.relearn_in_window(f, 4, 4) for f in range(1, 13))
+
+
+def _flat(v, h=6, w=8):
+    return np.full((h, w, 3), v, np.uint8)
+
+
+def test_relearned_band_closed_form():
+    """Constant background B learned (sigma 0: band [B - d, B + d]); a window of
+    R frames at B + 1 (inside the band) re-forms every band to [B + 1 - d, B + 1 + d]:
+    S' = R (B + 1), Q' = R (B + 1)^2, n = R gives mu = B + 1, sigma = 0."""
+    B, d, R = 100, 2, 3
+    o = oracle.OracleStream(8, 6, relearn_frames=R, relearn_min=R, relearn_period=5,
+                            bg_margin=d, **FIXED_GAIN)
+    o.learn(np.stack([_flat(B)] * 4))
+    assert (o.lo == B - d).all() and (o.hi == B + d).all()
+    for f in range(1, 6):
+        o.process(_flat(B + 1))
+        if f < 5:
+            assert (o.lo == B - d).all() and (o.hi == B + d).all(), f
+    assert (o.lo == B + 1 - d).all() and (o.hi == B + 1 + d).all()
+    assert (o.relearn.cnt == 0).all() and (o.relearn.S == 0).all()   # reset after the window
+
+
+def test_relearn_keeps_bands_of_pixels_seen_as_foreground():
+    """A pixel outside its band in the window frames is never counted and keeps
+    its band; a pixel counted fewer than relearn_min times keeps it too."""
+    B, d = 80, 2
+    o = oracle.OracleStream(8, 6, relearn_frames=4, relearn_min=3, relearn_period=4,
+                            bg_margin=d, **FIXED_GAIN)
+    o.learn(np.stack([_flat(B)] * 3))
+    frames = []
+    for t in range(4):
+        f = _flat(B + 1)
+        f[2, 3] = B + 50                        # always outside: count 0
+        if t >= 2:
+            f[4, 5] = B + 50                    # background in 2 of 4 frames only
+        frames.append(f)
+    for f in frames:
+        o.process(f)
+    assert o.lo[2, 3, 0] == B - d and o.hi[2, 3, 0] == B + d
+    assert o.lo[4, 5, 0] == B - d and o.hi[4, 5, 0] == B + d
+    assert o.lo[0, 0, 0] == B + 1 - d and o.hi[0, 0, 0] == B + 1 + d
+
+
+def test_relearn_windows_do_not_accumulate_across_windows():
+    B, d = 60, 2
+    o = oracle.OracleStream(8, 6, relearn_frames=2, relearn_min=2, relearn_period=2,
+                            bg_margin=d, **FIXED_GAIN)
+    o.learn(np.stack([_flat(B)] * 3))
+    for v in (B + 1, B + 1, B + 2, B + 2):
+        o.process(_flat(v))
+    # second window alone: mu = B + 2, sigma 0
+    assert (o.lo == B + 2 - d).all() and (o.hi == B + 2 + d).all()
+
+
+def test_relearning_tracks_a_drifting_background():
+    """The background drifts by +1 level every 2 frames.  Without re-learning
+    it leaves the learned band (d = 2) after a few frames and every pixel is
+    classified foreground; with a window of 2 every 4 frames the band follows."""
+    B, d = 90, 2
+    def run(**rl):
+        o = oracle.OracleStream(8, 6, bg_margin=d, **FIXED_GAIN, **rl)
+        o.learn(np.stack([_flat(B)] * 4))
+        outside = []
+        for t in range(40):
+            f = _flat(B + t // 2)
+            outside.append(bool(((f < o.lo) | (f > o.hi)).any()))
+            o.process(f)
+        return outside
+    assert any(run())
+    assert not any(run(relearn_frames=2, relearn_min=1, relearn_period=4))
+
+
+def test_relearning_off_changes_nothing():
+    frames = [synth.run_frame(1, 0, t) for t in range(3)]
+    lf = synth.learn_frames(1, 0, 8)
+    a = oracle.OracleStream(320, 240)
+    b = oracle.OracleStream(320, 240, relearn_frames=0, relearn_min=0, relearn_period=50)
+    a.learn(lf)
+    b.learn(lf)
+    for f in frames:
+        ra, rb = a.process(f), b.process(f)
+        assert np.array_equal(ra[0], rb[0]) and ra[2] == rb[2]
