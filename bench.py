@@ -429,6 +429,13 @@ def run_ours(args) -> None:
     e2e_s = max_over_ranks(time.perf_counter() - s0, dev)
     h2d = sum(int(host_frames[i][0].numel()) for i in range(n))
 
+    # ---- re-learning on every stream: its cost on the same workload -------
+    relearn = None
+    if not args.no_relearn:
+        relearn = bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape_used, args)
+        if args.relearn_eval:
+            relearn["quality"] = bench_relearn_quality(hmi, synth, torch, dev, args.relearn_eval)
+
     # ---- single 640x480 stream (the other configuration of the metric) ---
     single = None
     if not args.no_single:
@@ -493,6 +500,8 @@ def run_ours(args) -> None:
     }
     if single is not None:
         line["single_640x480"] = single
+    if relearn is not None:
+        line["relearning"] = relearn
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:
@@ -504,6 +513,82 @@ def run_ours(args) -> None:
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+RELEARN_BENCH = dict(relearn_frames=30, relearn_min=20, relearn_period=300)
+
+
+def bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
+    """The 64-stream batch again, every stream re-learning (a window of 30
+    frames every 300): pipelined ticks over whole periods, with the same launch
+    shape; the cost is the window ticks' re-learning sums and bands."""
+    n = len(rings)
+    p = hmi.hmi_default_params(**RELEARN_BENCH)
+    streams = []
+    for i in range(n):
+        w, h = synth.shape(CFG, i)
+        st = hmi.Stream(w, h, **RELEARN_BENCH)
+        st.learn(torch.from_numpy(synth.learn_frames(CFG, i)).to(dev))
+        streams.append(st)
+    b = hmi.hmi_batch_create([s.handle for s in streams])
+    hmi.hmi_batch_set_tuning(b, dict(shape, groups=1))
+    masks = [torch.empty((s.h, s.w), dtype=torch.uint8, device=dev) for s in streams]
+    ptrs = torch.zeros(n * 40, dtype=torch.uint8, device=dev)
+    steps = 4 * p.relearn_period
+    for k in range(p.relearn_period):
+        hmi.hmi_batch_process_pipelined(b, [rings[i][k % RING] for i in range(n)], masks, ptrs.data_ptr(),
+                                        cs.cuda_stream, True)
+    hmi.hmi_batch_flush(b, cs.cuda_stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    for k in range(steps):
+        hmi.hmi_batch_process_pipelined(b, [rings[i][k % RING] for i in range(n)], masks, ptrs.data_ptr(),
+                                        cs.cuda_stream, True)
+    hmi.hmi_batch_flush(b, cs.cuda_stream)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # one period of plain ticks with every kernel timed alone
+    hmi.hmi_batch_profile(b, p.relearn_period)
+    for k in range(p.relearn_period):
+        hmi.hmi_batch_process_async(b, [rings[i][k % RING] for i in range(n)], masks, ptrs.data_ptr(),
+                                    cs.cuda_stream, True)
+    ticks, per = hmi.hmi_batch_profile_kernels(b)
+    hmi.hmi_batch_profile(b, 0)
+    hmi.hmi_batch_destroy(b)
+    for s in streams:
+        s.close()
+    return {"params": RELEARN_BENCH, "ms_per_step": ms, "frames_per_s": n / (ms / 1e3),
+            "steps": steps, "launch": "pipelined ticks, the main run's launch shape, one group",
+            "per_period_ms": {k: round(v, 3) for k, v in per.items()}, "period_ticks": ticks,
+            "sums_ms_per_window_tick": per["relearn"] / p.relearn_frames,
+            "band_reform_ms_per_window_end": per["relearn_band"]}
+
+
+def bench_relearn_quality(hmi, synth, torch, dev, frames: int) -> dict:
+    """1920x1080 drifting scene (the third single-stream workload: gradient
+    drift of one level per 50 frames, brightness flicker): share of pixels the
+    background test puts outside the band, with and without re-learning."""
+    import numpy as np
+    w, h = synth.shape(3)
+    lf = torch.from_numpy(synth.learn_frames(3, 0)).to(dev)
+    out = {"frames": frames, "params": RELEARN_BENCH}
+    for name, over in (("off", {}), ("on", RELEARN_BENCH)):
+        st = hmi.Stream(w, h, **over)
+        st.learn(lf)
+        series = []
+        for t in range(frames):
+            f = synth.run_frame(3, 0, t)
+            st.process(torch.from_numpy(f).to(dev), mask=False)
+            if (t + 1) % 100 == 0:
+                lo, hi = st.band()
+                g = st.last_gain()
+                c = np.minimum(255, (f.astype(np.uint32) * g + 32768) >> 16)
+                series.append(round(float(((c < lo) | (c > hi)).any(axis=2).mean()), 4))
+        st.close()
+        out[f"out_of_band_share_every_100_frames_{name}"] = series
+    return out
 
 
 def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
@@ -597,6 +682,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-relearn", action="store_true", help="skip the re-learning cost run")
+    ap.add_argument("--relearn-eval", type=int, default=0,
+                    help="frames of the 1080p drifting scene to evaluate re-learning on (0: skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",
                     help="ticks of the timed region: pipelined (stage overlap) or plain")

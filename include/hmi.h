@@ -81,7 +81,18 @@ typedef struct {
     uint8_t close_iters;    /* [1]      closings (dilate, erode) to connect zones; open+close <= 16 */
     uint8_t click_on_pct;   /* [80]     click when 100*area < on_pct * reference area */
     uint8_t click_off_pct;  /* [90]     release when 100*area > off_pct * reference area */
-    uint8_t reserved[2];    /* must be zero */
+    /* Re-learning (Sec. 3.3: the learning is re-initiated partly as the
+     * luminosity evolves).  Off when relearn_frames is 0.  Otherwise the last
+     * relearn_frames frames of every relearn_period frames (counted from 1
+     * after learning) add the gain-corrected values of their background
+     * pixels to per-pixel sums; after the window each pixel counted at least
+     * relearn_min times gets the band of those sums (the learning formula,
+     * n = its count) and the sums restart.  1 <= relearn_min <= relearn_frames
+     * <= relearn_period. */
+    uint8_t relearn_frames; /* [0]      frames of a re-learning window (0: off) */
+    uint8_t relearn_min;    /* [0]      background frames a pixel needs in a window */
+    uint16_t relearn_period;/* [0]      frames from one window's end to the next */
+    uint16_t reserved;      /* must be zero */
 } hmi_params;
 
 /* The Mouse module's pointer (Sec. 2): position of the hand zone and its
@@ -205,9 +216,10 @@ HMI_API int hmi_batch_autotune(hmi_batch *b, const uint8_t *const *frames, int t
 
 /* Pipelined ticks, for plans with one group (HMI_ERR_INVALID_ARG otherwise;
  * see hmi_batch_set_groups).  A tick is split into D stages (D = the tuning's
- * pipeline_depth): with D = 2, {gains, background band test} (bandwidth-
- * bound) and {gray and hue tests, morphology, components, pointer} (latency-
- * bound); with D = 3, {gains}, {band test} and the same last stage.  Each call
+ * pipeline_depth): with D = 2, {gains, background band test, re-learning}
+ * (bandwidth-bound) and {gray and hue tests, morphology, components, pointer}
+ * (latency-bound); with D = 3, {gains}, {band test, re-learning} and the same
+ * last stage.  Each call
  * enqueues the first stage of its own frames and, beside it on the device,
  * stage j of the frames of the call j calls earlier, so D ticks overlap.
  * Buffers as in hmi_batch_process_async.  The results of a call (its masks
@@ -224,8 +236,10 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
 
 /* Kernel timing of a batch's ticks.  A tick runs HMI_TICK_KERNELS kernels in
  * this order: 0 luma sums and gains, 1 background band test (the per-pixel
- * HBM pass), 2 gray and hue tests of out-of-band pixels, 3 morphology, 4
- * block components, 5 merge and pointer.  hmi_batch_profile(b, max_ticks)
+ * HBM pass), 2 re-learning sums and 3 re-learned bands (launched only when a
+ * stream of the batch re-learns; they act on streams inside a window), 4 gray
+ * and hue tests of out-of-band pixels, 5 morphology, 6 block components, 7
+ * merge and pointer.  hmi_batch_profile(b, max_ticks)
  * starts recording CUDA events between the kernels for each of the next
  * max_ticks ticks (0 stops); the plan must have one group
  * (HMI_ERR_INVALID_ARG otherwise), so that every launch is timed alone.
@@ -233,7 +247,7 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
  * and, for the first n_kernels kernels (1..HMI_TICK_KERNELS), the sum of their
  * durations in milliseconds; hmi_batch_profile_read gives that sum for kernel
  * 1 alone. */
-#define HMI_TICK_KERNELS 6
+#define HMI_TICK_KERNELS 8
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
 HMI_API int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels);
 HMI_API int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms);
@@ -247,6 +261,11 @@ HMI_API int hmi_get_background_stats(const hmi_stream *s, float *mean, float *st
  * background, else the smallest linear index of the pixel's 8-connected
  * component (Mouse module, Sec. 2).  Computed on demand from the last mask. */
 HMI_API int hmi_get_labels(const hmi_stream *s, int32_t *labels);
+
+/* The background band in use (Sec. 3.1 (i)): lo and hi are h*w*3 bytes each
+ * (host or device; pixel-major RGB), the learned band or, with re-learning,
+ * the band as last re-formed.  HMI_ERR_NOT_LEARNED before learning. */
+HMI_API int hmi_get_band(const hmi_stream *s, uint8_t *lo, uint8_t *hi);
 
 /* Checkpoint of the learned model.  Export copies (each pointer may be NULL;
  * host or device) the per pixel-channel sums S, Q (uint32, h*w*3), min/max

@@ -68,7 +68,10 @@ bool params_valid(const hmi_params &p)
     if (p.open_iters + p.close_iters > 16) return false;
     if (p.gain_min_q16 > p.gain_max_q16 || p.gain_max_q16 > (1u << 24)) return false;
     if (p.click_window > 1024) return false;
-    if (p.reserved[0] || p.reserved[1]) return false;
+    if (p.reserved) return false;
+    if (p.relearn_frames > 0 &&
+        (p.relearn_min < 1 || p.relearn_min > p.relearn_frames || p.relearn_period < p.relearn_frames))
+        return false;
     return true;
 }
 
@@ -112,6 +115,9 @@ struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
     size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits, comp, parent, count, flag, mask,
         st, hist, ds, ptr, total;
+    // re-learning sums (only with re-learning on): rows of rpitch pixels
+    int rpitch;
+    size_t rS, rQ, rmin, rmax, rcnt, rpx;
 };
 
 Layout make_layout(int w, int h, const hmi_params &p)
@@ -146,6 +152,16 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.hist = a.take((size_t)std::max<int>(p.click_window, 1) * 4);
     L.ds = a.take(sizeof(DevStream));
     L.ptr = a.take(sizeof(hmi_pointer));
+    L.rpitch = (int)align_up((size_t)w, 16);
+    L.rpx = p.relearn_frames > 0 ? (size_t)h * L.rpitch : 0;
+    L.rS = L.rQ = L.rmin = L.rmax = L.rcnt = 0;
+    if (L.rpx) {
+        L.rS = a.take(L.rpx * 3 * 2);
+        L.rQ = a.take(L.rpx * 3 * 4);
+        L.rmin = a.take(L.rpx * 3);
+        L.rmax = a.take(L.rpx * 3);
+        L.rcnt = a.take(L.rpx);
+    }
     L.total = a.off;
     return L;
 }
@@ -328,6 +344,18 @@ void fill_devstream(hmi_stream *s)
     D.flag = reinterpret_cast<uint32_t *>(a + L.flag);
     D.st = reinterpret_cast<StreamState *>(a + L.st);
     D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
+    D.bg_kn = s->p.bg_k_num;
+    D.bg_kd = s->p.bg_k_den;
+    D.bg_delta = s->p.bg_margin;
+    D.relearn_frames = L.rpx ? s->p.relearn_frames : 0;
+    D.relearn_min = s->p.relearn_min;
+    D.relearn_period = s->p.relearn_period;
+    D.rpitch = L.rpitch;
+    D.rS = L.rpx ? reinterpret_cast<uint16_t *>(a + L.rS) : nullptr;
+    D.rQ = L.rpx ? reinterpret_cast<uint32_t *>(a + L.rQ) : nullptr;
+    D.rmin = L.rpx ? a + L.rmin : nullptr;
+    D.rmax = L.rpx ? a + L.rmax : nullptr;
+    D.rcnt = L.rpx ? a + L.rcnt : nullptr;
 }
 
 void plan_free_graphs(hmi_batch *b)
@@ -540,6 +568,9 @@ int plan_build(hmi_batch *b, int ng)
         bd.skin_count = G.skin_count_p[0];
         bd.skin_list = G.skin_list_p[0];
         bd.phase = 0;
+        bd.relearn = 0;
+        for (int k = 0; k < m; ++k)
+            if (b->s[perm[G.off + k]]->L.rpx) bd.relearn = 1;
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
         bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
         bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
@@ -707,19 +738,21 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
 }
 
 // Stages of a pipelined tick: the first kernel of each of its `depth` stages,
-// then kTickKernels.  Depth 2: {luma, band test} {gray/hue, morphology,
-// blocks, finish}; depth 3: {luma} {band test} {gray/hue .. finish}.  The
-// first stages are bandwidth-bound, the last is latency-bound.
+// then kTickKernels.  Depth 2: {luma, band test, re-learning} {gray/hue,
+// morphology, blocks, finish}; depth 3: {luma} {band test, re-learning}
+// {gray/hue .. finish}.  The first stages are bandwidth-bound, the last is
+// latency-bound; the band is only read and re-formed in the middle stage.
 void stage_bounds(int depth, int *first)
 {
+    constexpr int kTail = 4;   // first kernel of the latency-bound tail (gray/hue tests)
     if (depth >= 3) {
         first[0] = 0;
         first[1] = 1;
-        first[2] = 2;
+        first[2] = kTail;
         first[3] = kTickKernels;
     } else {
         first[0] = 0;
-        first[1] = 2;
+        first[1] = kTail;
         first[2] = kTickKernels;
     }
 }
@@ -1295,7 +1328,16 @@ int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
 cudaError_t enqueue_band(hmi_stream *s, int n, cudaStream_t cs)
 {
     const size_t bytes = (size_t)s->h * s->L.fpitch;
-    cudaError_t e = cudaMemsetAsync(s->arena + s->L.lo, 0, bytes, cs);
+    cudaError_t e = cudaSuccess;
+    if (s->L.rpx) {   // the re-learning sums restart with the learned band
+        const Layout &L = s->L;
+        e = cudaMemsetAsync(s->arena + L.rS, 0, L.rpx * 3 * 2, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + L.rQ, 0, L.rpx * 3 * 4, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + L.rmin, 0xff, L.rpx * 3, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + L.rmax, 0, L.rpx * 3, cs);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + L.rcnt, 0, L.rpx, cs);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + s->L.lo, 0, bytes, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->arena + s->L.hi, 0, bytes, cs);
     if (e == cudaSuccess)
         e = launch_learn_band(s->d_S, s->d_Q, s->d_vmin, s->d_vmax, n, s->p.bg_k_num, s->p.bg_k_den,
@@ -2152,6 +2194,18 @@ int hmi_get_labels(const hmi_stream *s, int32_t *labels)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (!dev) cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e);
+    return HMI_OK;
+}
+
+int hmi_get_band(const hmi_stream *s, uint8_t *lo, uint8_t *hi)
+{
+    if (!s || !lo || !hi) return fail(HMI_ERR_INVALID_ARG);
+    if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());   // the last tick may have run on any stream
+    const size_t row = 3 * (size_t)s->w;
+    HMI_CUDA(cudaMemcpy2D(lo, row, s->arena + s->L.lo, s->L.fpitch, row, s->h, cudaMemcpyDefault));
+    HMI_CUDA(cudaMemcpy2D(hi, row, s->arena + s->L.hi, s->L.fpitch, row, s->h, cudaMemcpyDefault));
     return HMI_OK;
 }
 

@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
         st->gain = (uint32_t)g;
         st->gain_p[b.phase] = (uint32_t)g;
         st->sy = 0;
+        st->lframes += 1;
+        st->lframe_p[b.phase] = st->lframes;   // read by later kernels of this tick only
     }
     if (tid == 0) b.done[0] = 0;
 }
@@ -349,6 +351,124 @@ __global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
             }
         }
         if (fail) atomicAnd(D.raw[b.phase] + (long long)y * D.nwords + (j >> 1), ~(fail << (16 * (j & 1))));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_relearn: re-learning sums (Sec. 3.3, the learning is re-initiated partly).
+// In a window frame of a stream, every background pixel (all three gain-
+// corrected channels inside the band: the test of k_classify) adds its
+// corrected values to the stream's sums.  One thread per 16-px chunk, four
+// pixels (12 values) at a time: value sums as 3 x 8 B (uint16), squares as
+// 3 x 16 B, min and max as 3 x 4 B each, counts as 4 B.
+// ---------------------------------------------------------------------------
+template <int P>
+__device__ __forceinline__ bool px_in_band(const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                           const uint32_t (&h)[12], uint32_t g)
+{
+    return in_band<3 * P>(f, l, h, g) & in_band<3 * P + 1>(f, l, h, g) & in_band<3 * P + 2>(f, l, h, g);
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t corrected(const uint32_t (&f)[12], uint32_t g)
+{
+    return (uint32_t)corr(__byte_perm(f[K >> 2], 0u, 0x4440u | (K & 3)), g);
+}
+
+// One value (index k of the group's 12) of a background pixel into the sums.
+template <int KK, int k>
+__device__ __forceinline__ void relearn_value(const uint32_t (&f)[12], uint32_t g, bool in,
+                                              uint32_t (&S)[6], uint32_t (&Q)[12],
+                                              uint32_t (&mn)[3], uint32_t (&mx)[3])
+{
+    const uint32_t v = corrected<KK>(f, g);
+    const uint32_t sh = 8u * (k & 3);
+    if (in) {
+        S[k >> 1] += v << (16 * (k & 1));
+        Q[k] += v * v;
+        mn[k >> 2] = __vminu4(mn[k >> 2], (v << sh) | ~(0xffu << sh));
+        mx[k >> 2] = __vmaxu4(mx[k >> 2], v << sh);
+    }
+}
+
+template <int GQ>
+__device__ __forceinline__ void relearn_quad(const DevStream &D, long long q0, int npx,
+                                             const uint32_t (&f)[12], const uint32_t (&l)[12],
+                                             const uint32_t (&h)[12], uint32_t g)
+{
+    if (4 * GQ >= npx) return;
+    const bool in0 = px_in_band<4 * GQ>(f, l, h, g) && 4 * GQ < npx;
+    const bool in1 = px_in_band<4 * GQ + 1>(f, l, h, g) && 4 * GQ + 1 < npx;
+    const bool in2 = px_in_band<4 * GQ + 2>(f, l, h, g) && 4 * GQ + 2 < npx;
+    const bool in3 = px_in_band<4 * GQ + 3>(f, l, h, g) && 4 * GQ + 3 < npx;
+    if (!(in0 | in1 | in2 | in3)) return;
+    const long long q = q0 + 4 * GQ;   // first pixel of the group, a multiple of 4
+    uint2 *pS = reinterpret_cast<uint2 *>(D.rS + 3 * q);
+    uint4 *pQ = reinterpret_cast<uint4 *>(D.rQ + 3 * q);
+    uint32_t *pmn = reinterpret_cast<uint32_t *>(D.rmin + 3 * q);
+    uint32_t *pmx = reinterpret_cast<uint32_t *>(D.rmax + 3 * q);
+    uint32_t *pc = reinterpret_cast<uint32_t *>(D.rcnt + q);
+    uint32_t S[6], Q[12], mn[3], mx[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const uint2 a = pS[i];
+        const uint4 b = pQ[i];
+        S[2 * i] = a.x;
+        S[2 * i + 1] = a.y;
+        Q[4 * i] = b.x;
+        Q[4 * i + 1] = b.y;
+        Q[4 * i + 2] = b.z;
+        Q[4 * i + 3] = b.w;
+        mn[i] = pmn[i];
+        mx[i] = pmx[i];
+    }
+    relearn_value<12 * GQ + 0, 0>(f, g, in0, S, Q, mn, mx);
+    relearn_value<12 * GQ + 1, 1>(f, g, in0, S, Q, mn, mx);
+    relearn_value<12 * GQ + 2, 2>(f, g, in0, S, Q, mn, mx);
+    relearn_value<12 * GQ + 3, 3>(f, g, in1, S, Q, mn, mx);
+    relearn_value<12 * GQ + 4, 4>(f, g, in1, S, Q, mn, mx);
+    relearn_value<12 * GQ + 5, 5>(f, g, in1, S, Q, mn, mx);
+    relearn_value<12 * GQ + 6, 6>(f, g, in2, S, Q, mn, mx);
+    relearn_value<12 * GQ + 7, 7>(f, g, in2, S, Q, mn, mx);
+    relearn_value<12 * GQ + 8, 8>(f, g, in2, S, Q, mn, mx);
+    relearn_value<12 * GQ + 9, 9>(f, g, in3, S, Q, mn, mx);
+    relearn_value<12 * GQ + 10, 10>(f, g, in3, S, Q, mn, mx);
+    relearn_value<12 * GQ + 11, 11>(f, g, in3, S, Q, mn, mx);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        pS[i] = make_uint2(S[2 * i], S[2 * i + 1]);
+        pQ[i] = make_uint4(Q[4 * i], Q[4 * i + 1], Q[4 * i + 2], Q[4 * i + 3]);
+        pmn[i] = mn[i];
+        pmx[i] = mx[i];
+    }
+    *pc += (uint32_t)in0 | ((uint32_t)in1 << 8) | ((uint32_t)in2 << 16) | ((uint32_t)in3 << 24);
+}
+
+__global__ void __launch_bounds__(kThreads) k_relearn(BatchDev b)
+{
+    const uint64_t once = policy_evict_first();
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        if (io.frame == nullptr || D.relearn_frames == 0) continue;
+        if (!relearn_window(D.st->lframe_p[b.phase], D.relearn_period, D.relearn_frames)) continue;
+        const uint32_t g = D.st->gain_p[b.phase];
+        const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
+        for (int u = piece.y + threadIdx.x; u < piece.z; u += blockDim.x) {
+            const int y = chunk_row((uint32_t)u, D.cpr_magic), x0 = (u - y * cpr) * kChunkPx;
+            if (x0 >= w) continue;
+            uint32_t f[12], l[12], h[12];
+            load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
+            load48(D.lo + (long long)y * fpitch + 3 * x0, once, l);
+            load48(D.hi + (long long)y * fpitch + 3 * x0, once, h);
+            const int npx = min(kChunkPx, w - x0);
+            const long long q0 = (long long)y * D.rpitch + x0;
+            relearn_quad<0>(D, q0, npx, f, l, h, g);
+            relearn_quad<1>(D, q0, npx, f, l, h, g);
+            relearn_quad<2>(D, q0, npx, f, l, h, g);
+            relearn_quad<3>(D, q0, npx, f, l, h, g);
+        }
     }
 }
 
@@ -721,6 +841,14 @@ cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
     return cudaGetLastError();
 }
 
+cudaError_t launch_relearn(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    (void)num_sms;
+    if (!b.relearn) return cudaSuccess;
+    k_relearn<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     k_skin<<<num_sms * std::max(1, b.skin_ctas_per_sm), kThreads, 0, cs>>>(b);
@@ -764,9 +892,11 @@ cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int nu
     switch (k) {
     case 0: return launch_luma(b, cs, num_sms);
     case 1: return launch_classify(b, cs, num_sms);
-    case 2: return launch_skin(b, cs, num_sms);
-    case 3: return launch_morph(b, cs, num_sms);
-    case 4: return launch_block_cc(b, cs, num_sms);
+    case 2: return launch_relearn(b, cs, num_sms);
+    case 3: return launch_relearn_band(b, cs, num_sms);
+    case 4: return launch_skin(b, cs, num_sms);
+    case 5: return launch_morph(b, cs, num_sms);
+    case 6: return launch_block_cc(b, cs, num_sms);
     default: return launch_finish(b, cs);
     }
 }

@@ -55,6 +55,8 @@ struct __align__(16) StreamState {
     int32_t hist_count;
     int32_t hist_head;
     int32_t frames;               // frames processed since learning
+    uint32_t lframes;             // frames whose gain was computed since learning
+    uint32_t lframe_p[3];         // the number of the frame of each tick phase (kPhases)
     hmi_pointer last;             // pointer of the last frame
 };
 
@@ -74,7 +76,15 @@ struct DevStream {
     // hue arc per sector (0: R max, 1: G max, 2: B max) as two half-open
     // intervals of N = 512 (t + d) + d:  d*A <= N < d*B
     int hueA[3][2], hueB[3][2];
-    const uint8_t *lo, *hi;       // background band, pitch fpitch, RGB interleaved
+    uint8_t *lo, *hi;             // background band, pitch fpitch, RGB interleaved
+    // re-learning (relearn_frames 0: off): window parameters and the sums,
+    // pixel-major RGB over rows of rpitch pixels (a multiple of 16)
+    int relearn_period, relearn_frames, relearn_min, rpitch;
+    int bg_kn, bg_kd, bg_delta;   // band parameters (k = kn / kd, margin delta)
+    uint16_t *rS;                 // sum of corrected values, per pixel-channel
+    uint32_t *rQ;                 // sum of their squares
+    uint8_t *rmin, *rmax;         // their min and max
+    uint8_t *rcnt;                // background frames counted, per pixel
     uint32_t *raw[3];             // raw AND mask bits, (bh*32) x nwords words, by tick phase
     uint32_t *bits;               // mask bits after morphology, same layout
     Comp *comp;                   // bh*nwords*kSlots records
@@ -129,6 +139,7 @@ struct BatchDev {
                                               // gain_p[] and the skin queue, so that up to
                                               // kPhases consecutive ticks can be in flight
     // launch shape (host side; chosen by the plan's tuning)
+    int relearn;                              // some stream of the batch re-learns
     int luma_ctas_per_sm;                     // 0: as many as fit
     int skin_ctas_per_sm;
     int cc_ctas_per_sm;
@@ -145,13 +156,24 @@ constexpr int kThreads = 256;
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
 // The kernels of one tick, in order: 0 luma (and gains), 1 classify (band
-// test), 2 skin (gray and hue tests), 3 morphology, 4 block components (none
-// on the generic morphology path, which labels its blocks itself), 5 finish.
-constexpr int kTickKernels = 6;
+// test), 2 re-learning sums and 3 re-learned bands (no launch unless a stream
+// of the batch re-learns), 4 skin (gray and hue tests), 5 morphology, 6 block
+// components (none on the generic morphology path, which labels its blocks
+// itself), 7 finish.
+constexpr int kTickKernels = 8;
 static_assert(kTickKernels == HMI_TICK_KERNELS, "tick kernel count");
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_relearn(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_relearn_band(const BatchDev &b, cudaStream_t cs, int num_sms);
+
+// Frame f (counted from 1 after learning) is in a re-learning window iff
+// (f - 1) mod period >= period - frames; the window ends with f mod period == 0.
+__host__ __device__ inline bool relearn_window(uint32_t f, int period, int frames)
+{
+    return frames > 0 && period > 0 && f > 0 && (int)((f - 1) % (uint32_t)period) >= period - frames;
+}
 cudaError_t launch_morph(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);

@@ -150,6 +150,38 @@ __device__ __forceinline__ bool high_ok(long long H, long long s, long long n, l
     return gap >= 0 && kd2 * gap * gap >= knD;
 }
 
+// Band of one pixel-channel from its sums over n frames: [min(vmin, L_k) -
+// delta, max(vmax, H_k) + delta] clamped to bytes, L_k / H_k the exact integer
+// edges of mu -/+ k sigma with k = kn / kd.
+__device__ __forceinline__ void band_of(long long s, long long q, long long nn, int kn, int kd, int delta,
+                                        int vmin, int vmax, uint8_t *lo, uint8_t *hi)
+{
+    const long long D = nn * q - s * s;
+    const long long kd2 = (long long)kd * kd, knD = (long long)kn * kn * D;
+    // L' = max(L_k, -1) and H' = min(H_k, 256) give the same clamped band as
+    // the unbounded edges; the predicates are monotone, so start from a
+    // floating estimate and step to the exact edge.  The estimate is FP32
+    // (FP64 is slow on this part) and lands within a step of the edge, so the
+    // predicates are only evaluated next to it, where kd^2 gap^2 stays near
+    // kn^2 D, below 2^63 for n <= 65535 and 8-bit k.
+    const float ksig = (float)kn / (float)kd * sqrtf(__ll2float_rn(D)) / (float)nn;
+    const float mu = __ll2float_rn(s) / (float)nn;
+    const long long lmax = s / nn;   // largest L with n L <= S
+    long long L = (long long)floorf(mu - ksig);
+    L = max(-1ll, min(L, lmax));
+    while (L + 1 <= lmax && low_ok(L + 1, s, nn, kd2, knD)) ++L;
+    while (L > -1 && !low_ok(L, s, nn, kd2, knD)) --L;
+    const long long hmin = (s + nn - 1) / nn;   // smallest H with n H >= S
+    long long H = (long long)ceilf(mu + ksig);
+    H = min(256ll, max(H, hmin));
+    while (H - 1 >= hmin && high_ok(H - 1, s, nn, kd2, knD)) --H;
+    while (H < 256 && !high_ok(H, s, nn, kd2, knD)) ++H;
+    long long a = min((long long)vmin, L) - delta;
+    long long b = max((long long)vmax, H) + delta;
+    *lo = (uint8_t)max(0ll, min(255ll, a));
+    *hi = (uint8_t)max(0ll, min(255ll, b));
+}
+
 __global__ void __launch_bounds__(kThreads) k_learn_band(const uint32_t *S, const uint32_t *Q,
                                                          const uint8_t *vmin, const uint8_t *vmax,
                                                          int n, int kn, int kd, int delta, int w,
@@ -165,40 +197,51 @@ __global__ void __launch_bounds__(kThreads) k_learn_band(const uint32_t *S, cons
         st->hist_count = 0;
         st->hist_head = 0;
         st->frames = 0;
+        st->lframes = 0;
         st->err = 0;
     }
     const long long count = (long long)w * h * 3;
     if (j >= count) return;
-    const long long s = S[j], nn = n;
-    const long long D = nn * (long long)Q[j] - s * s;
-    const long long kd2 = (long long)kd * kd, knD = (long long)kn * kn * D;
-    // L' = max(L_k, -1) and H' = min(H_k, 256) give the same clamped band as
-    // the unbounded edges; the predicates are monotone, so start from a
-    // floating estimate and step to the exact edge.  The estimate is FP32
-    // (FP64 is slow on this part) and lands within a step of the edge, so the
-    // predicates are only evaluated next to it, where kd^2 gap^2 stays near
-    // kn^2 D, below 2^63 for n <= 65535 and 8-bit k.
-    const float ksig = (float)kn / (float)kd * sqrtf(__ll2float_rn(D)) / (float)n;
-    const float mu = __ll2float_rn(s) / (float)n;
-    const long long lmax = s / nn;   // largest L with n L <= S
-    long long L = (long long)floorf(mu - ksig);
-    L = max(-1ll, min(L, lmax));
-    while (L + 1 <= lmax && low_ok(L + 1, s, nn, kd2, knD)) ++L;
-    while (L > -1 && !low_ok(L, s, nn, kd2, knD)) --L;
-    const long long hmin = (s + nn - 1) / nn;   // smallest H with n H >= S
-    long long H = (long long)ceilf(mu + ksig);
-    H = min(256ll, max(H, hmin));
-    while (H - 1 >= hmin && high_ok(H - 1, s, nn, kd2, knD)) --H;
-    while (H < 256 && !high_ok(H, s, nn, kd2, knD)) ++H;
-    long long a = min((long long)vmin[j], L) - delta;
-    long long b = max((long long)vmax[j], H) + delta;
-    a = max(0ll, min(255ll, a));
-    b = max(0ll, min(255ll, b));
     const long long pxi = j / 3, c = j - pxi * 3;
     const long long y = pxi / w, x = pxi - y * w;
     const long long o = y * fpitch + 3 * x + c;
-    lo[o] = (uint8_t)a;
-    hi[o] = (uint8_t)b;
+    band_of(S[j], Q[j], n, kn, kd, delta, vmin[j], vmax[j], lo + o, hi + o);
+}
+
+// k_relearn_band: after the last frame of a re-learning window, every pixel
+// counted at least relearn_min times gets the band of its re-learning sums
+// (n = its count), and every pixel's sums restart.  One thread per 16-px
+// chunk of the streams whose window ends this tick.
+__global__ void __launch_bounds__(kThreads) k_relearn_band(BatchDev b)
+{
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        if (b.io[piece.x].frame == nullptr || D.relearn_frames == 0) continue;
+        const uint32_t f = D.st->lframe_p[b.phase];
+        if (!relearn_window(f, D.relearn_period, D.relearn_frames) || f % (uint32_t)D.relearn_period != 0)
+            continue;
+        const int w = D.w, cpr = 2 * D.nwords;
+        for (int u = piece.y + threadIdx.x; u < piece.z; u += blockDim.x) {
+            const int y = chunk_row((uint32_t)u, D.cpr_magic), x0 = (u - y * cpr) * kChunkPx;
+            for (int k = 0; k < kChunkPx && x0 + k < w; ++k) {
+                const long long q = (long long)y * D.rpitch + x0 + k;
+                const int n = D.rcnt[q];
+                const long long o = (long long)y * D.fpitch + 3LL * (x0 + k);
+                for (int ch = 0; ch < 3; ++ch) {
+                    const long long j = 3 * q + ch;
+                    if (n >= D.relearn_min && n > 0)
+                        band_of(D.rS[j], D.rQ[j], n, D.bg_kn, D.bg_kd, D.bg_delta, D.rmin[j], D.rmax[j],
+                                D.lo + o + ch, D.hi + o + ch);
+                    D.rS[j] = 0;
+                    D.rQ[j] = 0;
+                    D.rmin[j] = 255;
+                    D.rmax[j] = 0;
+                }
+                D.rcnt[q] = 0;
+            }
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_stats(const uint32_t *S, const uint32_t *Q, int n,
@@ -241,6 +284,14 @@ cudaError_t launch_learn_band(const uint32_t *S, const uint32_t *Q, const uint8_
     const unsigned grid = (unsigned)((count + kThreads - 1) / kThreads);
     k_learn_band<<<grid, kThreads, 0, cs>>>(S, Q, vmin, vmax, n, kn, kd, delta, w, h, fpitch,
                                             lo, hi, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relearn_band(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    (void)num_sms;
+    if (!b.relearn) return cudaSuccess;
+    k_relearn_band<<<b.npieces > 0 ? b.npieces : 1, kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ HMI_ERR_NO_MEMORY = -3
 HMI_ERR_DEVICE = -4
 HMI_ERR_DEVICE_TIMEOUT = -5
 HMI_LEARNING = 1          # server results only: a background-learning frame
-HMI_TICK_KERNELS = 6
+HMI_TICK_KERNELS = 8
 
 
 class hmi_params(ctypes.Structure):
@@ -34,7 +34,8 @@ class hmi_params(ctypes.Structure):
                 ("bg_k_num", ctypes.c_uint8), ("bg_k_den", ctypes.c_uint8),
                 ("open_iters", ctypes.c_uint8), ("close_iters", ctypes.c_uint8),
                 ("click_on_pct", ctypes.c_uint8), ("click_off_pct", ctypes.c_uint8),
-                ("reserved", ctypes.c_uint8 * 2)]
+                ("relearn_frames", ctypes.c_uint8), ("relearn_min", ctypes.c_uint8),
+                ("relearn_period", ctypes.c_uint16), ("reserved", ctypes.c_uint16)]
 
 
 class hmi_pointer(ctypes.Structure):
@@ -101,6 +102,7 @@ SIGNATURES = {
     "hmi_batch_profile_kernels": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _I]),
     "hmi_get_background_stats": (_I, [_P, _P, _P]),
     "hmi_get_labels": (_I, [_P, _P]),
+    "hmi_get_band": (_I, [_P, _P, _P]),
     "hmi_export_background": (_I, [_P, _P, _P, _P, _P, _P, _P,
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_I)]),
     "hmi_import_background": (_I, [_P, _P, _P, _P, _P, _I, ctypes.c_uint64]),
@@ -302,7 +304,8 @@ def hmi_batch_profile(b: int, max_ticks: int) -> None:
     _check(load().hmi_batch_profile(b, max_ticks), "hmi_batch_profile")
 
 
-TICK_KERNELS = ("luma", "classify", "skin", "morphology", "block_components", "finish")
+TICK_KERNELS = ("luma", "classify", "relearn", "relearn_band", "skin", "morphology",
+                "block_components", "finish")
 
 
 def hmi_batch_profile_kernels(b: int) -> tuple[int, dict]:
@@ -326,6 +329,10 @@ def hmi_get_background_stats(s: int, mean, std) -> None:
 
 def hmi_get_labels(s: int, labels) -> None:
     _check(load().hmi_get_labels(s, _addr(labels)), "hmi_get_labels")
+
+
+def hmi_get_band(s: int, lo, hi) -> None:
+    _check(load().hmi_get_band(s, _addr(lo), _addr(hi)), "hmi_get_band")
 
 
 def hmi_export_background(s: int, S=None, Q=None, vmin=None, vmax=None, lo=None, hi=None):
@@ -467,6 +474,12 @@ class Stream:
         out = np.empty((self.h, self.w), np.int32)
         hmi_get_labels(self.handle, out)
         return out
+
+    def band(self) -> tuple[np.ndarray, np.ndarray]:
+        lo = np.empty((self.h, self.w, 3), np.uint8)
+        hi = np.empty((self.h, self.w, 3), np.uint8)
+        hmi_get_band(self.handle, lo, hi)
+        return lo, hi
 
     def stats(self):
         mean = np.empty((self.h, self.w, 3), np.float32)

@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(hmi.hmi_params) == 28
+    assert ctypes.sizeof(hmi.hmi_params) == 32
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 56
@@ -38,6 +38,11 @@ def test_defaults_and_status_strings():
     assert (p.gray_tol, p.hue_lo, p.hue_hi, p.bg_margin, p.bg_k_num, p.bg_k_den) == (15, 1472, 256, 2, 5, 2)
     assert (p.open_iters, p.close_iters, p.gain_min_q16, p.gain_max_q16) == (1, 1, 32768, 131072)
     assert (p.min_area, p.click_on_pct, p.click_off_pct, p.click_window) == (50, 80, 90, 30)
+    assert (p.relearn_frames, p.relearn_min, p.relearn_period, p.reserved) == (0, 0, 0, 0)
+    # the oracle's defaults are the library's
+    import oracle
+    for k, v in oracle.DEFAULTS.items():
+        assert getattr(p, k) == v, k
     assert hmi.hmi_status_string(0) == "ok"
     for st in (-1, -2, -3, -4, -5):
         assert hmi.hmi_status_string(st) not in ("ok", "unknown status")
@@ -58,6 +63,14 @@ def test_device_bytes_accounting():
     assert hmi.hmi_stream_device_bytes(32, 32, bad) == 0
     bad = hmi.hmi_default_params(open_iters=9, close_iters=8)
     assert hmi.hmi_stream_device_bytes(32, 32, bad) == 0
+    # re-learning: consistent window parameters, and its sums cost device memory
+    for over in (dict(relearn_frames=5, relearn_min=0, relearn_period=10),
+                 dict(relearn_frames=5, relearn_min=6, relearn_period=10),
+                 dict(relearn_frames=5, relearn_min=2, relearn_period=4),
+                 dict(reserved=1)):
+        assert hmi.hmi_stream_device_bytes(32, 32, hmi.hmi_default_params(**over)) == 0, over
+    rl = hmi.hmi_default_params(relearn_frames=5, relearn_min=3, relearn_period=10)
+    assert hmi.hmi_stream_device_bytes(320, 240, rl) >= b320 + 320 * 240 * 25
 
 
 def test_invalid_arguments_fail_on_host():

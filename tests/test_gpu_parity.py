@@ -483,7 +483,7 @@ def test_profile_counts_classification_kernel():
     assert ticks == 5 and 0 < ms / ticks < 5.0
     t2, per = hmi.hmi_batch_profile_kernels(b)
     assert t2 == 5 and per["classify"] == pytest.approx(ms)
-    assert all(v > 0 for k, v in per.items() if k != "block_components")
+    assert all(v > 0 for k, v in per.items() if k not in ("block_components", "relearn", "relearn_band"))
     hmi.hmi_batch_destroy(b)
     g.close()
 
@@ -599,3 +599,78 @@ def test_autotune_keeps_stream_state():
         hmi.hmi_batch_destroy(b)
     for g in ga + gb:
         g.close()
+
+
+RELEARN = dict(relearn_frames=3, relearn_min=2, relearn_period=5)
+
+
+def _check_band(g, o, what):
+    lo, hi = g.band()
+    for name, a, b in (("lo", lo, o.lo), ("hi", hi, o.hi)):
+        if not np.array_equal(a, b):
+            bad = np.argwhere(a != b)
+            raise AssertionError(f"{what} band {name} differs at {len(bad)} values, first {bad[:4].tolist()}")
+
+
+@pytest.mark.parametrize("cfg,w_over", [(1, None), (2, None), (1, 312)])
+def test_relearning_matches_oracle(cfg, w_over):
+    """Re-learning (window of 3 frames every 5, 2 background frames needed):
+    every frame's mask, labels and pointer, and the band after every frame,
+    equal the oracle's (config 1 and 2 frames; a width that is not a multiple
+    of 16 exercises the padded sums)."""
+    w, h = synth.shape(cfg)
+    if w_over:
+        w = w_over
+    g, o = pair(w, h, **RELEARN)
+    lf = synth.learn_frames(cfg, 0, 10)[:, :, :w]
+    learn_both(g, o, np.ascontiguousarray(lf))
+    for t in range(16):
+        f = np.ascontiguousarray(synth.run_frame(cfg, 0, t)[:, :w])
+        check_frame(g, o, f, dev=t % 2 == 1, what=f"cfg{cfg} w{w} t={t}")
+        _check_band(g, o, f"cfg{cfg} w{w} t={t}")
+    g.close()
+
+
+def test_relearning_in_batches_and_pipelines():
+    """Four streams (two re-learning, two not) in one batch: plain graph ticks
+    and pipelined ticks at depths 2 and 3 all match the oracle frame by frame,
+    bands included."""
+    idx = [0, 20, 33, 50]
+    for mode in ("plain", 2, 3):
+        gs, os_ = [], []
+        for k, i in enumerate(idx):
+            w, h = synth.shape(4, i)
+            over = RELEARN if k % 2 == 0 else {}
+            g, o = pair(w, h, **over)
+            learn_both(g, o, synth.learn_frames(4, i, 8), dev=True)
+            gs.append(g)
+            os_.append(o)
+        b = hmi.hmi_batch_create([g.handle for g in gs])
+        hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), groups=1,
+                                         pipeline_depth=mode if mode != "plain" else 2))
+        s = torch.cuda.current_stream().cuda_stream
+        T = 12
+        frames = [[synth.run_frame(4, i, t) for i in idx] for t in range(T)]
+        dframes = [[_dev(f) for f in fr] for fr in frames]
+        outs = []
+        for t in range(T):
+            m = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+            p = torch.zeros(len(idx) * 40, dtype=torch.uint8, device="cuda")
+            if mode == "plain":
+                hmi.hmi_batch_process_async(b, dframes[t], m, p.data_ptr(), s, True)
+            else:
+                hmi.hmi_batch_process_pipelined(b, dframes[t], m, p.data_ptr(), s, t % 2 == 0)
+            outs.append((m, p))
+        hmi.hmi_batch_flush(b, s)
+        torch.cuda.synchronize()
+        for t in range(T):
+            arr = outs[t][1].cpu().numpy().view(hmi.POINTER_DTYPE)
+            for k in range(len(idx)):
+                m_o, _, p_o, _ = os_[k].process(frames[t][k], want_labels=False)
+                assert np.array_equal(outs[t][0][k].cpu().numpy(), m_o), (mode, t, k)
+                assert_pointer(dict(zip(arr.dtype.names, [x.item() for x in arr[k]])), p_o, f"{mode} t={t} s={k}")
+        for k in range(len(idx)):
+            _check_band(gs[k], os_[k], f"{mode} s={k}")
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
