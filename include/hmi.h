@@ -92,7 +92,13 @@ typedef struct {
     uint8_t relearn_frames; /* [0]      frames of a re-learning window (0: off) */
     uint8_t relearn_min;    /* [0]      background frames a pixel needs in a window */
     uint16_t relearn_period;/* [0]      frames from one window's end to the next */
-    uint16_t reserved;      /* must be zero */
+    /* Tracking (Sec. 2: the Mouse module tracks the hand zone).  0: the hand
+     * is the largest blob.  Otherwise, once a valid pointer has been seen,
+     * the hand is the blob of at least min_area pixels whose bounding box is
+     * nearest (L1 distance, 0 inside) the previous valid pointer's rounded
+     * centroid, if within this many pixels (ties: larger area, then smaller
+     * label); else the largest blob. */
+    uint16_t track_max_dist;/* [0]      pixels */
 } hmi_params;
 
 /* The Mouse module's pointer (Sec. 2): position of the hand zone and its

@@ -89,8 +89,9 @@ def _load():
             "orc_relearn_accumulate": (None, [_P, _P, _P, _SZ, _P, _P, _P, _P, _P]),
             "orc_relearn_apply": (None, [_P, _P, _P, _P, _P, _SZ, _I, _I, _I, _I, _P, _P]),
             "orc_relearn_in_window": (_I, [ctypes.c_longlong, _I, _I]),
+            "orc_pointer_select": (None, [_P, _I, _I, _U32, _I, _P, _P]),
             "orc_process_frame": (None, [_P, _I, _I, _P, _P, _U64, _I, _I, _I, _I, _I,
-                                         _U32, _U32, _U32, _I, _I, _I, _P, _P, _P,
+                                         _U32, _U32, _U32, _I, _I, _I, _I, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
         }
         for name, (res, args) in sig.items():
@@ -119,7 +120,7 @@ DEFAULTS = dict(gray_tol=15, hue_lo=1472, hue_hi=256, bg_margin=2, bg_k_num=5,
                 bg_k_den=2, open_iters=1, close_iters=1, gain_min_q16=32768,
                 gain_max_q16=131072, min_area=50, click_on_pct=80,
                 click_off_pct=90, click_window=30,
-                relearn_frames=0, relearn_min=0, relearn_period=0)
+                relearn_frames=0, relearn_min=0, relearn_period=0, track_max_dist=0)
 
 
 def params(**over) -> dict:
@@ -258,6 +259,16 @@ def label(m: np.ndarray):
     return lab, n
 
 
+def pointer_select(labels: np.ndarray, min_area: int, max_dist: int, track=None):
+    """Tracked pointer choice; returns (pointer dict, new track (valid, x, y))."""
+    labels = np.ascontiguousarray(labels, np.int32)
+    h, w = labels.shape
+    tr = np.zeros(3, np.int32) if track is None else np.array(track, np.int32)
+    p = Pointer()
+    _load().orc_pointer_select(_ptr(labels), w, h, min_area, max_dist, _ptr(tr), ctypes.byref(p))
+    return p.as_dict(), tuple(int(v) for v in tr)
+
+
 def pointer_from_labels(labels: np.ndarray, min_area: int) -> dict:
     labels = np.ascontiguousarray(labels, np.int32)
     h, w = labels.shape
@@ -334,6 +345,7 @@ class OracleStream:
 
     def _reset_relearn(self) -> None:
         self.frames = 0
+        self.track = np.zeros(3, np.int32)   # (valid, x, y) of the tracked point
         self.relearn = Relearn(self.h, self.w) if self.p["relearn_frames"] > 0 else None
 
     def set_background(self, S, Q, vmin, vmax, n: int, syref: int) -> None:
@@ -367,7 +379,8 @@ class OracleStream:
             _ptr(frame), self.w, self.h, _ptr(self.lo), _ptr(self.hi), self.syref,
             p["gray_tol"], p["hue_lo"], p["hue_hi"], p["open_iters"], p["close_iters"],
             p["gain_min_q16"], p["gain_max_q16"], p["min_area"], p["click_on_pct"],
-            p["click_off_pct"], c.window, ctypes.byref(c.click), _ptr(c.hist),
+            p["click_off_pct"], c.window, p["track_max_dist"], _ptr(self.track),
+            ctypes.byref(c.click), _ptr(c.hist),
             ctypes.byref(c.count), _ptr(mask), _ptr(labels), ctypes.byref(ptr),
             ctypes.byref(g))
         # re-learning (Sec. 3.3), after this frame's classification

@@ -435,8 +435,18 @@ int orc_label(const uint8_t *mask, int w, int h, int32_t *labels)
 /* inclusive bounding box; valid iff area >= min_area.  With no component:    */
 /* valid 0, area 0, label -1, box -1, x = y = -1.                             */
 /* ======================================================================== */
-void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_area,
-                             orc_pointer *out)
+/* Pointer (Sec. 2 Mouse module) from a label image.  Reading: the hand is the
+ * largest component (ties: the smaller label).  With tracking (Sec. 2: the
+ * Mouse module "tracks" the hand zone; max_dist > 0) and a tracked point from
+ * an earlier valid frame (track[0] != 0, point track[1], track[2]), the hand is
+ * instead the component of at least min_area pixels whose bounding box is
+ * nearest that point, the distance being max(0, x0 - tx, tx - x1) +
+ * max(0, y0 - ty, ty - y1) and at most max_dist (ties: the larger area, then
+ * the smaller label); with no such component, the largest.  A valid pointer
+ * then moves the tracked point to its rounded centroid,
+ * floor((2 sum + area) / (2 area)) per axis.  track may be NULL (no tracking). */
+void orc_pointer_select(const int32_t *labels, int w, int h, uint32_t min_area, int max_dist,
+                        int32_t *track, orc_pointer *out)
 {
     size_t npx = (size_t)w * (size_t)h;
     /* per-label accumulators, indexed by the label (= a pixel index) */
@@ -465,6 +475,23 @@ void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_a
         if (area[l] == 0) continue;
         if (best < 0 || area[l] > area[best]) best = (int32_t)l;  /* ascending l: ties keep the smaller */
     }
+    if (track && max_dist > 0 && track[0]) {
+        int32_t tb = -1;
+        long long tbd = 0;
+        for (size_t l = 0; l < npx; ++l) {
+            if (area[l] == 0 || area[l] < min_area) continue;
+            long long dx = 0, dy = 0;
+            if (track[1] < bx0[l]) dx = bx0[l] - track[1];
+            if (track[1] > bx1[l]) dx = track[1] - bx1[l];
+            if (track[2] < by0[l]) dy = by0[l] - track[2];
+            if (track[2] > by1[l]) dy = track[2] - by1[l];
+            const long long d = dx + dy;
+            if (d > max_dist) continue;
+            /* ascending l: equal distance and area keep the smaller label */
+            if (tb < 0 || d < tbd || (d == tbd && area[l] > area[tb])) { tb = (int32_t)l; tbd = d; }
+        }
+        if (tb >= 0) best = tb;
+    }
     memset(out, 0, sizeof(*out));
     if (best < 0) {
         out->valid = 0; out->area = 0; out->label = -1;
@@ -478,8 +505,19 @@ void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_a
         out->y = (float)((double)sy[best] / (double)area[best]);
         out->x0 = bx0[best]; out->y0 = by0[best];
         out->x1 = bx1[best]; out->y1 = by1[best];
+        if (track && out->valid) {
+            track[0] = 1;
+            track[1] = (int32_t)((2 * sx[best] + area[best]) / (2 * (uint64_t)area[best]));
+            track[2] = (int32_t)((2 * sy[best] + area[best]) / (2 * (uint64_t)area[best]));
+        }
     }
     free(area); free(sx); free(sy); free(bx0); free(by0); free(bx1); free(by1);
+}
+
+void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_area,
+                             orc_pointer *out)
+{
+    orc_pointer_select(labels, w, h, min_area, 0, NULL, out);
 }
 
 /* Click state machine of one stream (reading of "its state (click or not)").
@@ -526,6 +564,7 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
                        int open_iters, int close_iters,
                        uint32_t gain_min, uint32_t gain_max, uint32_t min_area,
                        int on_pct, int off_pct, int window,
+                       int track_max_dist, int32_t *track,
                        int32_t *click, uint32_t *hist, int32_t *hist_count,
                        uint8_t *mask_out, int32_t *labels_out, orc_pointer *pointer_out,
                        uint32_t *gain_out)
@@ -541,7 +580,7 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
     orc_fg(c, lo, hi, npx, gray_tol, hue_lo, hue_hi, NULL, NULL, NULL, raw);
     orc_morph(raw, w, h, open_iters, close_iters, mask);
     orc_label(mask, w, h, labels);
-    orc_pointer_from_labels(labels, w, h, min_area, pointer_out);
+    orc_pointer_select(labels, w, h, min_area, track_max_dist, track, pointer_out);
     orc_click_update(click, hist, hist_count, window, on_pct, off_pct, pointer_out);
     if (mask_out) memcpy(mask_out, mask, npx);
     if (labels_out) memcpy(labels_out, labels, npx * sizeof(int32_t));

@@ -68,7 +68,6 @@ bool params_valid(const hmi_params &p)
     if (p.open_iters + p.close_iters > 16) return false;
     if (p.gain_min_q16 > p.gain_max_q16 || p.gain_max_q16 > (1u << 24)) return false;
     if (p.click_window > 1024) return false;
-    if (p.reserved) return false;
     if (p.relearn_frames > 0 &&
         (p.relearn_min < 1 || p.relearn_min > p.relearn_frames || p.relearn_period < p.relearn_frames))
         return false;

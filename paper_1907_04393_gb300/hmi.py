@@ -35,7 +35,7 @@ class hmi_params(ctypes.Structure):
                 ("open_iters", ctypes.c_uint8), ("close_iters", ctypes.c_uint8),
                 ("click_on_pct", ctypes.c_uint8), ("click_off_pct", ctypes.c_uint8),
                 ("relearn_frames", ctypes.c_uint8), ("relearn_min", ctypes.c_uint8),
-                ("relearn_period", ctypes.c_uint16), ("reserved", ctypes.c_uint16)]
+                ("relearn_period", ctypes.c_uint16), ("track_max_dist", ctypes.c_uint16)]
 
 
 class hmi_pointer(ctypes.Structure):

@@ -38,7 +38,7 @@ def test_defaults_and_status_strings():
     assert (p.gray_tol, p.hue_lo, p.hue_hi, p.bg_margin, p.bg_k_num, p.bg_k_den) == (15, 1472, 256, 2, 5, 2)
     assert (p.open_iters, p.close_iters, p.gain_min_q16, p.gain_max_q16) == (1, 1, 32768, 131072)
     assert (p.min_area, p.click_on_pct, p.click_off_pct, p.click_window) == (50, 80, 90, 30)
-    assert (p.relearn_frames, p.relearn_min, p.relearn_period, p.reserved) == (0, 0, 0, 0)
+    assert (p.relearn_frames, p.relearn_min, p.relearn_period, p.track_max_dist) == (0, 0, 0, 0)
     # the oracle's defaults are the library's
     import oracle
     for k, v in oracle.DEFAULTS.items():
@@ -66,8 +66,7 @@ def test_device_bytes_accounting():
     # re-learning: consistent window parameters, and its sums cost device memory
     for over in (dict(relearn_frames=5, relearn_min=0, relearn_period=10),
                  dict(relearn_frames=5, relearn_min=6, relearn_period=10),
-                 dict(relearn_frames=5, relearn_min=2, relearn_period=4),
-                 dict(reserved=1)):
+                 dict(relearn_frames=5, relearn_min=2, relearn_period=4)):
         assert hmi.hmi_stream_device_bytes(32, 32, hmi.hmi_default_params(**over)) == 0, over
     rl = hmi.hmi_default_params(relearn_frames=5, relearn_min=3, relearn_period=10)
     assert hmi.hmi_stream_device_bytes(320, 240, rl) >= b320 + 320 * 240 * 25

@@ -558,3 +558,77 @@ def test_relearning_off_changes_nothing():
     for f in frames:
         ra, rb = a.process(f), b.process(f)
         assert np.array_equal(ra[0], rb[0]) and ra[2] == rb[2]
+
+
+# --------------------------------------------------------------------------- #
+# Tracking (Sec. 2: the Mouse module tracks the hand zone)                     #
+# --------------------------------------------------------------------------- #
+def _two_blobs():
+    """A 40x20 label image: blob A (label 0, area 60, 6x10 at x 0..5) and blob
+    B (label 30, area 100, 10x10 at x 30..39), found by the oracle's labelling."""
+    m = np.zeros((20, 40), np.uint8)
+    m[0:10, 0:6] = 1
+    m[0:10, 30:40] = 1
+    return oracle.label(m)[0]
+
+
+def test_tracking_picks_the_blob_nearest_the_tracked_point():
+    lab = _two_blobs()
+    big = oracle.pointer_from_labels(lab, 50)
+    assert big["area"] == 100 and big["label"] == 30
+    p, tr = oracle.pointer_select(lab, 50, 1000, (1, 3, 4))        # inside A's box
+    assert p["area"] == 60 and p["label"] == 0
+    # the tracked point moves to A's rounded centroid: sum x = 10 * (0+..+5) = 150,
+    # (2*150 + 60) // 120 = 3; sum y = 6 * 45 = 270, (540 + 60) // 120 = 5
+    assert tr == (1, 3, 5)
+    p, _ = oracle.pointer_select(lab, 50, 1000, (1, 25, 4))       # 20 from A, 5 from B
+    assert p["label"] == 30
+
+
+def test_tracking_falls_back_to_the_largest():
+    lab = _two_blobs()
+    assert oracle.pointer_select(lab, 50, 1000, (0, 3, 4))[0]["label"] == 30   # no history
+    assert oracle.pointer_select(lab, 50, 0, (1, 3, 4))[0]["label"] == 30      # tracking off
+    # A's box is x 0..5, y 0..9: point (3, 19) is 10 below it: within 10, beyond 9
+    assert oracle.pointer_select(lab, 50, 10, (1, 3, 19))[0]["label"] == 0
+    assert oracle.pointer_select(lab, 50, 9, (1, 3, 19))[0]["label"] == 30
+    assert oracle.pointer_select(lab, 61, 1000, (1, 3, 4))[0]["label"] == 30   # A below min_area
+
+
+def test_tracking_ties_prefer_larger_then_smaller_label():
+    m = np.zeros((20, 40), np.uint8)
+    m[0:10, 0:6] = 1          # label 0, area 60, box x 0..5
+    m[0:10, 15:21] = 1        # label 15, area 60, box x 15..20
+    m[12:20, 30:40] = 1       # larger, far away
+    lab = oracle.label(m)[0]
+    p, _ = oracle.pointer_select(lab, 50, 1000, (1, 10, 4))       # 5 from both
+    assert p["label"] == 0
+    m[0:11, 15:21] = 1        # label 15 now area 66: the larger of the two at distance 5
+    p, _ = oracle.pointer_select(oracle.label(m)[0], 50, 1000, (1, 10, 4))
+    assert p["label"] == 15
+
+
+def test_tracking_in_a_stream_follows_the_hand_past_a_larger_distractor():
+    """Stream level: a small skin blob moves right while a distractor grows
+    larger than it; with tracking the pointer stays on the moving blob."""
+    h, w = 48, 96
+    bg = np.zeros((h, w, 3), np.uint8)
+    bg[..., 2] = 180                                  # blue: never skin
+    skin = np.array([200, 140, 110], np.uint8)
+    def frame(t):
+        f = bg.copy()
+        f[10:22, 4 + 2 * t:16 + 2 * t] = skin         # the hand, 12x12, moving
+        s = 6 + 2 * t
+        f[30:30 + s // 2 + 4, 60:60 + s] = skin       # the distractor, growing
+        return f
+    common = dict(gain_min_q16=65536, gain_max_q16=65536, min_area=20)
+    a = oracle.OracleStream(w, h, **common)
+    b = oracle.OracleStream(w, h, track_max_dist=30, **common)
+    for o in (a, b):
+        o.learn(np.stack([bg] * 3))
+    xs_a, xs_b = [], []
+    for t in range(12):
+        xs_a.append(a.process(frame(t))[2]["x"])
+        xs_b.append(b.process(frame(t))[2]["x"])
+    assert xs_b == sorted(xs_b) and xs_b[-1] < 40     # stayed on the hand
+    assert xs_a[-1] > 60                              # the largest blob is the distractor
