@@ -346,6 +346,7 @@ void fill_devstream(hmi_stream *s)
     D.bg_kn = s->p.bg_k_num;
     D.bg_kd = s->p.bg_k_den;
     D.bg_delta = s->p.bg_margin;
+    D.track_max_dist = s->p.track_max_dist;
     D.relearn_frames = L.rpx ? s->p.relearn_frames : 0;
     D.relearn_min = s->p.relearn_min;
     D.relearn_period = s->p.relearn_period;

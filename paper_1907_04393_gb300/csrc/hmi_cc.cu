@@ -142,6 +142,11 @@ __device__ void finalize_pointer(const DevStream &D, const TickIO &io, bool has,
         P.y = (float)((double)sy / (double)area);
         P.x0 = x0; P.y0 = y0; P.x1 = x1; P.y1 = y1;
     }
+    if (P.valid) {   // the tracked point follows the valid pointer
+        st->track_valid = 1;
+        st->track_x = (int32_t)((2ull * sx + area) / (2ull * area));
+        st->track_y = (int32_t)((2ull * sy + area) / (2ull * area));
+    }
     if (P.valid) {
         const int win = D.click_window;
         if (st->hist_count == 0) {
@@ -218,9 +223,24 @@ struct FinishSmem {
     uint32_t rbase[kActCap + 1]; // first record of each listed block
     uint32_t wsum[kFinishThreads / 32];
     uint32_t nact, nrec, pick;
-    unsigned long long best;
+    unsigned long long best;     // packed (area, ~key) of the largest root
+    uint32_t tdist;              // tracking: least box distance to the tracked point
+    unsigned long long tbest;    // tracking: packed (area, ~key) among the nearest
     bool overflow;
 };
+
+// L1 distance from point (tx, ty) to the box [x0, x1] x [y0, y1] (0 inside).
+__device__ __forceinline__ uint32_t box_dist(int tx, int ty, int x0, int y0, int x1, int y1)
+{
+    const int dx = max(0, max(x0 - tx, tx - x1));
+    const int dy = max(0, max(y0 - ty, ty - y1));
+    return (uint32_t)(dx + dy);
+}
+
+__device__ __forceinline__ bool tracking(const DevStream &D)
+{
+    return D.track_max_dist > 0 && D.st->track_valid;
+}
 
 // Root of x with path halving (every visited node is re-pointed to its
 // grandparent, always an ancestor, so concurrent unions stay correct).
@@ -262,7 +282,8 @@ __device__ __forceinline__ int act_index(const uint32_t *act, uint32_t n, uint32
     return (lo < (int)n && act[lo] == blk) ? lo : -1;
 }
 
-__device__ void finish_global(const DevStream &D, const TickIO &io, unsigned long long *best)
+__device__ void finish_global(const DevStream &D, const TickIO &io, unsigned long long *best,
+                              uint32_t *tdist, unsigned long long *tbest)
 {
     uint32_t *err = &D.st->err;
     const uint32_t nblk = (uint32_t)D.bh * (uint32_t)D.nwords;
@@ -285,7 +306,28 @@ __device__ void finish_global(const DevStream &D, const TickIO &io, unsigned lon
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) finalize_stream(D, io, *best);
+    if (tracking(D)) {   // the root nearest the tracked point (same rule as the shared path)
+        const int tx = D.st->track_x, ty = D.st->track_y;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (uint32_t lb = threadIdx.x; lb < nblk; lb += blockDim.x) {
+                const uint32_t cnt = D.count[lb];
+                for (uint32_t j = 0; j < cnt; ++j) {
+                    const uint32_t id = lb * kSlots + j;
+                    if (ld_parent(D.parent, id) != id) continue;
+                    const Comp &C = D.comp[id];
+                    const uint32_t area = __ldcg(&C.area);
+                    if (area < D.min_area) continue;
+                    const uint32_t d = box_dist(tx, ty, __ldcg(&C.x0), __ldcg(&C.y0), __ldcg(&C.x1), __ldcg(&C.y1));
+                    if (d > (uint32_t)D.track_max_dist) continue;
+                    if (pass == 0) atomicMin(tdist, d);
+                    else if (d == *tdist)
+                        atomicMax(tbest, ((unsigned long long)area << 32) | (unsigned long long)(0xffffffffu - C.key));
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) finalize_stream(D, io, *tbest ? *tbest : *best);
 }
 
 __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
@@ -300,6 +342,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         S.nact = 0;
         S.nrec = 0;
         S.best = 0;
+        S.tdist = 0xffffffffu;
+        S.tbest = 0;
         S.overflow = false;
         if (blockIdx.x == 0) {                   // k_skin and k_block_cc are done with their lists
             *b.cc_count = 0u;
@@ -369,7 +413,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
     }
     __syncthreads();
     if (S.overflow) {
-        finish_global(D, io, &S.best);
+        finish_global(D, io, &S.best, &S.tdist, &S.tbest);
         if (tid == 0) {
             const uint32_t e = D.st->err;
             if (e) atomicOr(b.err, e);
@@ -483,7 +527,22 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
         atomicMax(&S.best, packed);
     }
     __syncthreads();
-    const unsigned long long best = S.best;
+    if (tracking(D)) {   // Sec. 2 tracking: the root nearest the tracked point
+        const int tx = D.st->track_x, ty = D.st->track_y;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (uint32_t r = tid; r < nr; r += blockDim.x) {
+                if (S.parent[r] != r || S.rec[r].area < D.min_area) continue;
+                const Comp &C = S.rec[r];
+                const uint32_t d = box_dist(tx, ty, C.x0, C.y0, C.x1, C.y1);
+                if (d > (uint32_t)D.track_max_dist) continue;
+                if (pass == 0) atomicMin(&S.tdist, d);
+                else if (d == S.tdist)
+                    atomicMax(&S.tbest, ((unsigned long long)C.area << 32) | (unsigned long long)(0xffffffffu - C.key));
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned long long best = S.tbest ? S.tbest : S.best;
     for (uint32_t r = tid; r < nr; r += blockDim.x) {
         if (S.parent[r] == r && best != 0ull &&
             S.rec[r].key == 0xffffffffu - (uint32_t)(best & 0xffffffffull))

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_learn_band(const uint32_t *S, cons
         st->hist_head = 0;
         st->frames = 0;
         st->lframes = 0;
+        st->track_valid = 0;
         st->err = 0;
     }
     const long long count = (long long)w * h * 3;

@@ -674,3 +674,77 @@ def test_relearning_in_batches_and_pipelines():
         hmi.hmi_batch_destroy(b)
         for g in gs:
             g.close()
+
+
+# --------------------------------------------------------------------------- #
+# Tracking (Sec. 2: the Mouse module tracks the hand zone)                     #
+# --------------------------------------------------------------------------- #
+def _track_scene(t, w=96, h=48):
+    f = np.zeros((h, w, 3), np.uint8)
+    f[...] = GRAY
+    f[10:22, 4 + 2 * t:16 + 2 * t] = SKIN          # the hand, moving right
+    s = 6 + 2 * t
+    f[30:30 + s // 2 + 4, 60:60 + s] = SKIN        # a distractor, growing past it
+    return f
+
+
+def test_tracking_matches_oracle():
+    """A moving hand and a growing distractor: with tracking the pointer stays
+    on the hand, frame by frame equal to the oracle; without it, the largest
+    blob wins (also equal to the oracle)."""
+    for dist in (30, 0):
+        g, o = pair(96, 48, track_max_dist=dist, open_iters=0, close_iters=0, min_area=20,
+                    gain_min_q16=65536, gain_max_q16=65536)
+        black_background(g, o)
+        xs = []
+        for t in range(14):
+            xs.append(check_frame(g, o, _track_scene(t), dev=t % 2 == 0, what=f"track{dist} t={t}")["x"])
+        assert (xs[-1] < 45) == (dist > 0), xs
+        g.close()
+
+
+def test_tracking_with_many_components_matches_oracle():
+    """Thousands of components (the general merge path, not the shared-memory
+    one) with tracking on: the chosen blob equals the oracle's."""
+    w, h = 640, 480
+    g, o = pair(w, h, track_max_dist=200, open_iters=0, close_iters=0, min_area=3,
+                gain_min_q16=65536, gain_max_q16=65536)
+    black_background(g, o)
+    for t in range(4):
+        pat = (RNG.random((h, w)) < 0.2).astype(np.uint8)
+        pat[100 + 10 * t:160 + 10 * t, 200:260] = 1    # a large blob that moves
+        check_frame(g, o, pattern_frame(pat), dev=True, what=f"many t={t}")
+    g.close()
+
+
+def test_tracking_in_pipelined_batches():
+    """Tracking streams in a batch under pipelined ticks equal the oracle."""
+    idx = [0, 33, 50]
+    gs, os_ = [], []
+    for i in idx:
+        w, h = synth.shape(4, i)
+        g, o = pair(w, h, track_max_dist=64)
+        learn_both(g, o, synth.learn_frames(4, i, 8), dev=True)
+        gs.append(g)
+        os_.append(o)
+    b = hmi.hmi_batch_create([g.handle for g in gs])
+    hmi.hmi_batch_set_groups(b, 1)
+    s = torch.cuda.current_stream().cuda_stream
+    T = 8
+    frames = [[synth.run_frame(4, i, t) for i in idx] for t in range(T)]
+    dframes = [[_dev(f) for f in fr] for fr in frames]
+    ptrs = []
+    for t in range(T):
+        p = torch.zeros(len(idx) * 40, dtype=torch.uint8, device="cuda")
+        hmi.hmi_batch_process_pipelined(b, dframes[t], None, p.data_ptr(), s, True)
+        ptrs.append(p)
+    hmi.hmi_batch_flush(b, s)
+    torch.cuda.synchronize()
+    for t in range(T):
+        arr = ptrs[t].cpu().numpy().view(hmi.POINTER_DTYPE)
+        for k in range(len(idx)):
+            _, _, p_o, _ = os_[k].process(frames[t][k], want_labels=False)
+            assert_pointer(dict(zip(arr.dtype.names, [x.item() for x in arr[k]])), p_o, f"t={t} s={k}")
+    hmi.hmi_batch_destroy(b)
+    for g in gs:
+        g.close()
