@@ -90,6 +90,8 @@ def _load():
             "orc_relearn_apply": (None, [_P, _P, _P, _P, _P, _SZ, _I, _I, _I, _I, _P, _P]),
             "orc_relearn_in_window": (_I, [ctypes.c_longlong, _I, _I]),
             "orc_pointer_select": (None, [_P, _I, _I, _U32, _I, _P, _P]),
+            "orc_diamond_angle": (ctypes.c_int32, [_I64, _I64]),
+            "orc_interface_event": (None, [_I, ctypes.c_int32, ctypes.c_int32, _I, _P, _I, _P, _P]),
             "orc_process_frame": (None, [_P, _I, _I, _P, _P, _U64, _I, _I, _I, _I, _I,
                                          _U32, _U32, _U32, _I, _I, _I, _I, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
@@ -269,6 +271,22 @@ def pointer_select(labels: np.ndarray, min_area: int, max_dist: int, track=None)
     return p.as_dict(), tuple(int(v) for v in tr)
 
 
+def diamond_angle(dx: int, dy: int) -> int:
+    return _load().orc_diamond_angle(int(dx), int(dy))
+
+
+EVENT_FIELDS = ("zone", "event", "on_wheel", "steer", "left", "right", "throttle")
+
+
+def interface_event(valid: bool, px: int, py: int, click: int, zones, wheel) -> dict:
+    """zones: [(x0, y0, x1, y1, event)], wheel: (on, cx, cy, r_in, r_out, dead_zone)."""
+    z = np.ascontiguousarray(np.array(zones, np.int32).reshape(-1, 5)) if len(zones) else np.zeros((1, 5), np.int32)
+    wl = np.ascontiguousarray(np.array(wheel, np.int32))
+    out = np.zeros(7, np.int32)
+    _load().orc_interface_event(int(valid), int(px), int(py), int(click), _ptr(z), len(zones), _ptr(wl), _ptr(out))
+    return dict(zip(EVENT_FIELDS, (int(v) for v in out)))
+
+
 def pointer_from_labels(labels: np.ndarray, min_area: int) -> dict:
     labels = np.ascontiguousarray(labels, np.int32)
     h, w = labels.shape
@@ -343,6 +361,10 @@ class OracleStream:
         self.learned = True
         self._reset_relearn()
 
+    def set_interface(self, zones, wheel) -> None:
+        """Headless Interface module and wheel (orc_interface_event)."""
+        self.ui = (list(zones), tuple(wheel))
+
     def _reset_relearn(self) -> None:
         self.frames = 0
         self.track = np.zeros(3, np.int32)   # (valid, x, y) of the tracked point
@@ -383,6 +405,11 @@ class OracleStream:
             ctypes.byref(c.click), _ptr(c.hist),
             ctypes.byref(c.count), _ptr(mask), _ptr(labels), ctypes.byref(ptr),
             ctypes.byref(g))
+        # the Interface module's event from this frame's pointer (Sec. 2, 4)
+        if getattr(self, "ui", None) is not None:
+            pd = ptr.as_dict()
+            self.event = interface_event(pd["valid"], self.track[1], self.track[2], pd["click"],
+                                         self.ui[0], self.ui[1])
         # re-learning (Sec. 3.3), after this frame's classification
         self.frames += 1
         if self.relearn is not None and relearn_in_window(self.frames, p["relearn_period"],

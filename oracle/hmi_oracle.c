@@ -587,3 +587,61 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
     if (gain_out) *gain_out = g;
     free(c); free(raw); free(mask); free(labels);
 }
+
+/* ======================================================================== */
+/* Interface module (Sec. 2: with the Mouse module it determines the          */
+/* interface zone activated by the pointer, zones being linked to events)     */
+/* and the driving application (Sec. 4: the hand turns around an imaginary    */
+/* wheel to steer left or right, and the speed is the third control).        */
+/* Reading, headless and integer: the pointer point is the rounded centroid   */
+/* of a valid pointer (floor((2 sum + area) / (2 area)) per axis); the zone   */
+/* is the first listed inclusive rectangle that contains it; the point is on  */
+/* the wheel when r_in^2 <= dx^2 + dy^2 <= r_out^2 around the wheel centre;   */
+/* its angle is the "diamond" pseudo-angle, 4096 units per turn, 0 at the     */
+/* top, growing clockwise (1024 per quadrant: 1024 u / (u + v) in the first,  */
+/* u = dx, v = -dy, and likewise in the others, floor division); steer is     */
+/* that angle in (-2048, 2048]; left and right are steer beyond the dead      */
+/* zone, and throttle is the click state (the closed hand), all three only    */
+/* on the wheel.                                                              */
+/* ======================================================================== */
+int32_t orc_diamond_angle(int64_t dx, int64_t dy)
+{
+    const int64_t u = dx, v = -dy;
+    if (u == 0 && v == 0) return 0;
+    if (u >= 0 && v > 0) return (int32_t)(1024 * u / (u + v));
+    if (u > 0 && v <= 0) return (int32_t)(1024 + 1024 * (-v) / (u - v));
+    if (u <= 0 && v < 0) return (int32_t)(2048 + 1024 * (-u) / (-u - v));
+    return (int32_t)(3072 + 1024 * v / (v - u));
+}
+
+/* valid, (px, py): the pointer point; zones: nzones x (x0, y0, x1, y1, event);
+ * wheel: (on, cx, cy, r_in, r_out, dead_zone).
+ * out: (zone, event, on_wheel, steer, left, right, throttle). */
+void orc_interface_event(int valid, int32_t px, int32_t py, int click, const int32_t *zones,
+                         int nzones, const int32_t *wheel, int32_t *out)
+{
+    for (int k = 0; k < 7; ++k) out[k] = 0;
+    out[0] = -1;
+    out[1] = -1;
+    if (!valid) return;
+    for (int z = 0; z < nzones; ++z) {
+        const int32_t *Z = zones + 5 * z;
+        if (px >= Z[0] && px <= Z[2] && py >= Z[1] && py <= Z[3]) {
+            out[0] = z;
+            out[1] = Z[4];
+            break;
+        }
+    }
+    if (!wheel[0]) return;
+    const int64_t dx = (int64_t)px - wheel[1], dy = (int64_t)py - wheel[2];
+    const int64_t d2 = dx * dx + dy * dy;
+    const int64_t r0 = wheel[3], r1 = wheel[4];
+    if (d2 < r0 * r0 || d2 > r1 * r1) return;
+    int32_t a = orc_diamond_angle(dx, dy);
+    int32_t steer = a > 2048 ? a - 4096 : a;
+    out[2] = 1;
+    out[3] = steer;
+    out[4] = steer < -wheel[5];
+    out[5] = steer > wheel[5];
+    out[6] = click != 0;
+}

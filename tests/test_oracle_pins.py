@@ -632,3 +632,41 @@ def test_tracking_in_a_stream_follows_the_hand_past_a_larger_distractor():
         xs_b.append(b.process(frame(t))[2]["x"])
     assert xs_b == sorted(xs_b) and xs_b[-1] < 40     # stayed on the hand
     assert xs_a[-1] > 60                              # the largest blob is the distractor
+
+
+# --------------------------------------------------------------------------- #
+# Interface module and driving wheel (Sec. 2, Sec. 4)                          #
+# --------------------------------------------------------------------------- #
+def test_diamond_angle_closed_forms():
+    """Axes and diagonals land on exact quarter and eighth turns; the angle
+    grows clockwise and is monotone along a circle."""
+    assert [oracle.diamond_angle(*d) for d in ((0, -5), (5, 0), (0, 5), (-5, 0))] == [0, 1024, 2048, 3072]
+    assert [oracle.diamond_angle(*d) for d in ((3, -3), (3, 3), (-3, 3), (-3, -3))] == [512, 1536, 2560, 3584]
+    assert oracle.diamond_angle(0, 0) == 0
+    import math
+    prev = -1
+    for k in range(360):
+        t = 2 * math.pi * k / 360
+        a = oracle.diamond_angle(round(1000 * math.sin(t)), -round(1000 * math.cos(t)))
+        assert a >= prev or (k > 350 and a < 100), (k, a, prev)
+        prev = a
+
+
+def test_interface_zones_and_wheel():
+    zones = [(0, 0, 99, 99, 7), (50, 50, 149, 149, 8)]
+    wheel = (1, 300, 200, 80, 120, 64)
+    ev = oracle.interface_event(True, 60, 60, 0, zones, wheel)
+    assert (ev["zone"], ev["event"], ev["on_wheel"]) == (0, 7, 0)   # first listed zone wins
+    assert oracle.interface_event(True, 120, 60, 0, zones, wheel)["event"] == 8
+    assert oracle.interface_event(False, 60, 60, 1, zones, wheel)["zone"] == -1
+    top = oracle.interface_event(True, 300, 100, 1, [], wheel)     # straight up, radius 100
+    assert (top["on_wheel"], top["steer"], top["left"], top["right"], top["throttle"]) == (1, 0, 0, 0, 1)
+    right = oracle.interface_event(True, 400, 200, 0, [], wheel)
+    assert (right["steer"], right["right"], right["left"], right["throttle"]) == (1024, 1, 0, 0)
+    left = oracle.interface_event(True, 200, 200, 0, [], wheel)
+    assert (left["steer"], left["left"]) == (-1024, 1)
+    assert oracle.interface_event(True, 300, 150, 0, [], wheel)["on_wheel"] == 0    # radius 50: inside
+    assert oracle.interface_event(True, 300, 50, 0, [], wheel)["on_wheel"] == 0     # radius 150: outside
+    small = oracle.interface_event(True, 305, 100, 0, [], wheel)  # 5 px right of the top: 1024*5/105 = 48
+    assert (small["steer"], small["right"]) == (48, 0)             # inside the dead zone of 64
+    assert oracle.interface_event(True, 310, 100, 0, [], wheel)["right"] == 1   # 1024*10/110 = 93
