@@ -268,6 +268,48 @@ HMI_API int hmi_get_background_stats(const hmi_stream *s, float *mean, float *st
  * component (Mouse module, Sec. 2).  Computed on demand from the last mask. */
 HMI_API int hmi_get_labels(const hmi_stream *s, int32_t *labels);
 
+/* Headless Interface module (Sec. 2: linked to the Mouse module, it finds
+ * the interface zone activated by the pointer; zones are linked to events)
+ * and driving wheel (Sec. 4: the hand turns around an imaginary wheel to
+ * steer left and right; speed is the third control).  Per frame, from the
+ * valid pointer's rounded centroid p = floor((2 sum + area) / (2 area)) per
+ * axis: zone = the first listed inclusive rectangle containing p; on_wheel
+ * iff r_in^2 <= |p - c|^2 <= r_out^2 around the wheel centre c; steer = the
+ * clockwise angle of p around c from the top, as a "diamond" pseudo-angle of
+ * 4096 units per turn (1024 per quadrant: 1024 u / (u + v) in the first,
+ * u = dx, v = -dy, floor division; likewise in the others), wrapped to
+ * (-2048, 2048]; left / right = on the wheel and steer beyond -/+ dead_zone;
+ * throttle = on the wheel and the click state (closed hand).  With no valid
+ * pointer: zone = event = -1, the wheel fields 0.  frame is the number of
+ * frames processed since learning, this one included. */
+#define HMI_MAX_ZONES 16
+typedef struct {
+    int32_t x0, y0, x1, y1;  /* inclusive pixel rectangle */
+    int32_t event;           /* the caller's event id */
+} hmi_zone;
+
+typedef struct {
+    int32_t nzones;          /* 0 .. HMI_MAX_ZONES */
+    hmi_zone zones[HMI_MAX_ZONES];
+    int32_t wheel_on;        /* 0: no wheel */
+    int32_t wheel_cx, wheel_cy;
+    int32_t wheel_r_in, wheel_r_out;   /* 0 <= r_in <= r_out <= 65535 */
+    int32_t dead_zone;       /* 0 .. 2048, pseudo-angle units */
+} hmi_interface;
+
+typedef struct {
+    int32_t zone;            /* index of the activated zone, or -1 */
+    int32_t event;           /* its event id, or -1 */
+    int32_t on_wheel, steer, left, right, throttle;
+    int32_t frame;           /* frames processed when the event was made */
+} hmi_event;
+
+/* Install the stream's interface (copied; waits for the device).  It applies
+ * to the frames processed after the call.  HMI_ERR_INVALID_ARG out of range. */
+HMI_API int hmi_set_interface(hmi_stream *s, const hmi_interface *ui);
+/* The event of the stream's last processed frame (host or device pointer). */
+HMI_API int hmi_get_event(const hmi_stream *s, hmi_event *out);
+
 /* The background band in use (Sec. 3.1 (i)): lo and hi are h*w*3 bytes each
  * (host or device; pixel-major RGB), the learned band or, with re-learning,
  * the band as last re-formed.  HMI_ERR_NOT_LEARNED before learning. */

@@ -113,7 +113,7 @@ struct Arena {
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
     size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits, comp, parent, count, flag, mask,
-        st, hist, ds, ptr, total;
+        st, hist, ds, ptr, ui, total;
     // re-learning sums (only with re-learning on): rows of rpitch pixels
     int rpitch;
     size_t rS, rQ, rmin, rmax, rcnt, rpx;
@@ -151,6 +151,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.hist = a.take((size_t)std::max<int>(p.click_window, 1) * 4);
     L.ds = a.take(sizeof(DevStream));
     L.ptr = a.take(sizeof(hmi_pointer));
+    L.ui = a.take(sizeof(hmi_interface));
     L.rpitch = (int)align_up((size_t)w, 16);
     L.rpx = p.relearn_frames > 0 ? (size_t)h * L.rpitch : 0;
     L.rS = L.rQ = L.rmin = L.rmax = L.rcnt = 0;
@@ -347,6 +348,7 @@ void fill_devstream(hmi_stream *s)
     D.bg_kd = s->p.bg_k_den;
     D.bg_delta = s->p.bg_margin;
     D.track_max_dist = s->p.track_max_dist;
+    D.ui = reinterpret_cast<const hmi_interface *>(a + L.ui);
     D.relearn_frames = L.rpx ? s->p.relearn_frames : 0;
     D.relearn_min = s->p.relearn_min;
     D.relearn_period = s->p.relearn_period;
@@ -2194,6 +2196,27 @@ int hmi_get_labels(const hmi_stream *s, int32_t *labels)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->cs);
     if (!dev) cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e);
+    return HMI_OK;
+}
+
+int hmi_set_interface(hmi_stream *s, const hmi_interface *ui)
+{
+    if (!s || !ui || ui->nzones < 0 || ui->nzones > HMI_MAX_ZONES || ui->wheel_r_in < 0 ||
+        ui->wheel_r_in > ui->wheel_r_out || ui->wheel_r_out > 65535 || ui->dead_zone < 0 ||
+        ui->dead_zone > 2048)
+        return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());   // no tick of the stream may be reading it
+    HMI_CUDA(cudaMemcpy(s->arena + s->L.ui, ui, sizeof(hmi_interface), cudaMemcpyHostToDevice));
+    return HMI_OK;
+}
+
+int hmi_get_event(const hmi_stream *s, hmi_event *out)
+{
+    if (!s || !out) return fail(HMI_ERR_INVALID_ARG);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());   // the last tick may have run on any stream
+    HMI_CUDA(cudaMemcpy(out, &s->st->event, sizeof(hmi_event), cudaMemcpyDefault));
     return HMI_OK;
 }
 

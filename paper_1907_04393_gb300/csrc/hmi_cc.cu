@@ -119,6 +119,53 @@ __device__ void resolve_block(const DevStream &D, uint32_t lb, uint32_t *err)
     }
 }
 
+// The Interface module's event (Sec. 2) and the driving wheel (Sec. 4) from
+// the frame's pointer point (px, py), valid or not; see hmi_interface.
+__device__ int32_t diamond_angle(long long dx, long long dy)
+{
+    const long long u = dx, v = -dy;
+    if (u == 0 && v == 0) return 0;
+    if (u >= 0 && v > 0) return (int32_t)(1024 * u / (u + v));
+    if (u > 0 && v <= 0) return (int32_t)(1024 + 1024 * (-v) / (u - v));
+    if (u <= 0 && v < 0) return (int32_t)(2048 + 1024 * (-u) / (-u - v));
+    return (int32_t)(3072 + 1024 * v / (v - u));
+}
+
+__device__ void interface_event(const DevStream &D, bool valid, int32_t px, int32_t py, int32_t click,
+                                int32_t frame, hmi_event *out)
+{
+    hmi_event E;
+    E.zone = -1;
+    E.event = -1;
+    E.on_wheel = E.steer = E.left = E.right = E.throttle = 0;
+    E.frame = frame;
+    const hmi_interface &U = *D.ui;
+    if (valid) {
+        for (int z = 0; z < U.nzones && z < HMI_MAX_ZONES; ++z) {
+            const hmi_zone &Z = U.zones[z];
+            if (px >= Z.x0 && px <= Z.x1 && py >= Z.y0 && py <= Z.y1) {
+                E.zone = z;
+                E.event = Z.event;
+                break;
+            }
+        }
+        if (U.wheel_on) {
+            const long long dx = (long long)px - U.wheel_cx, dy = (long long)py - U.wheel_cy;
+            const long long d2 = dx * dx + dy * dy;
+            const long long r0 = U.wheel_r_in, r1 = U.wheel_r_out;
+            if (d2 >= r0 * r0 && d2 <= r1 * r1) {
+                const int32_t a = diamond_angle(dx, dy);
+                E.on_wheel = 1;
+                E.steer = a > 2048 ? a - 4096 : a;
+                E.left = E.steer < -U.dead_zone;
+                E.right = E.steer > U.dead_zone;
+                E.throttle = click != 0;
+            }
+        }
+    }
+    *out = E;
+}
+
 // Pointer of one stream from its largest component's statistics (has == 0:
 // no foreground), then the click state machine: A_ref = max area of the last
 // click_window valid frames; a valid frame sets the click when
@@ -173,6 +220,7 @@ __device__ void finalize_pointer(const DevStream &D, const TickIO &io, bool has,
         }
     }
     P.click = st->click;
+    interface_event(D, P.valid != 0, st->track_x, st->track_y, P.click, st->frames + 1, &st->event);
     st->last = P;
     st->frames += 1;
     st->best = 0ull;

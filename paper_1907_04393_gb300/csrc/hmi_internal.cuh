@@ -58,6 +58,7 @@ struct __align__(16) StreamState {
     uint32_t lframes;             // frames whose gain was computed since learning
     uint32_t lframe_p[3];         // the number of the frame of each tick phase (kPhases)
     int32_t track_valid, track_x, track_y;   // tracked point: last valid pointer's rounded centroid
+    hmi_event event;              // the Interface module's event of the last frame
     hmi_pointer last;             // pointer of the last frame
 };
 
@@ -83,6 +84,7 @@ struct DevStream {
     int relearn_period, relearn_frames, relearn_min, rpitch;
     int bg_kn, bg_kd, bg_delta;   // band parameters (k = kn / kd, margin delta)
     int track_max_dist;           // 0: the hand is the largest blob; else tracked
+    const hmi_interface *ui;      // zones and wheel (all zero: none)
     uint16_t *rS;                 // sum of corrected values, per pixel-channel
     uint32_t *rQ;                 // sum of their squares
     uint8_t *rmin, *rmax;         // their min and max

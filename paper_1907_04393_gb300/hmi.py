@@ -54,6 +54,30 @@ class hmi_server_result(ctypes.Structure):
                 ("pointer", hmi_pointer)]
 
 
+HMI_MAX_ZONES = 16
+
+
+class hmi_zone(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_int32), ("y0", ctypes.c_int32), ("x1", ctypes.c_int32),
+                ("y1", ctypes.c_int32), ("event", ctypes.c_int32)]
+
+
+class hmi_interface(ctypes.Structure):
+    _fields_ = [("nzones", ctypes.c_int32), ("zones", hmi_zone * HMI_MAX_ZONES),
+                ("wheel_on", ctypes.c_int32), ("wheel_cx", ctypes.c_int32), ("wheel_cy", ctypes.c_int32),
+                ("wheel_r_in", ctypes.c_int32), ("wheel_r_out", ctypes.c_int32),
+                ("dead_zone", ctypes.c_int32)]
+
+
+class hmi_event(ctypes.Structure):
+    _fields_ = [("zone", ctypes.c_int32), ("event", ctypes.c_int32), ("on_wheel", ctypes.c_int32),
+                ("steer", ctypes.c_int32), ("left", ctypes.c_int32), ("right", ctypes.c_int32),
+                ("throttle", ctypes.c_int32), ("frame", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class hmi_tuning(ctypes.Structure):
     _fields_ = [("piece_chunks", ctypes.c_int32), ("luma_ctas_per_sm", ctypes.c_int32),
                 ("skin_ctas_per_sm", ctypes.c_int32), ("cc_ctas_per_sm", ctypes.c_int32),
@@ -103,6 +127,8 @@ SIGNATURES = {
     "hmi_get_background_stats": (_I, [_P, _P, _P]),
     "hmi_get_labels": (_I, [_P, _P]),
     "hmi_get_band": (_I, [_P, _P, _P]),
+    "hmi_set_interface": (_I, [_P, ctypes.POINTER(hmi_interface)]),
+    "hmi_get_event": (_I, [_P, ctypes.POINTER(hmi_event)]),
     "hmi_export_background": (_I, [_P, _P, _P, _P, _P, _P, _P,
                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(_I)]),
     "hmi_import_background": (_I, [_P, _P, _P, _P, _P, _I, ctypes.c_uint64]),
@@ -331,6 +357,28 @@ def hmi_get_labels(s: int, labels) -> None:
     _check(load().hmi_get_labels(s, _addr(labels)), "hmi_get_labels")
 
 
+def make_interface(zones=(), wheel=None) -> hmi_interface:
+    """zones: [(x0, y0, x1, y1, event)], wheel: (cx, cy, r_in, r_out, dead_zone) or None."""
+    ui = hmi_interface()
+    ui.nzones = len(zones)
+    for k, z in enumerate(zones):
+        ui.zones[k] = hmi_zone(*z)
+    if wheel is not None:
+        ui.wheel_on = 1
+        ui.wheel_cx, ui.wheel_cy, ui.wheel_r_in, ui.wheel_r_out, ui.dead_zone = wheel
+    return ui
+
+
+def hmi_set_interface(s: int, ui: hmi_interface) -> None:
+    _check(load().hmi_set_interface(s, ctypes.byref(ui)), "hmi_set_interface")
+
+
+def hmi_get_event(s: int) -> dict:
+    e = hmi_event()
+    _check(load().hmi_get_event(s, ctypes.byref(e)), "hmi_get_event")
+    return e.as_dict()
+
+
 def hmi_get_band(s: int, lo, hi) -> None:
     _check(load().hmi_get_band(s, _addr(lo), _addr(hi)), "hmi_get_band")
 
@@ -474,6 +522,12 @@ class Stream:
         out = np.empty((self.h, self.w), np.int32)
         hmi_get_labels(self.handle, out)
         return out
+
+    def set_interface(self, ui: hmi_interface) -> None:
+        hmi_set_interface(self.handle, ui)
+
+    def event(self) -> dict:
+        return hmi_get_event(self.handle)
 
     def band(self) -> tuple[np.ndarray, np.ndarray]:
         lo = np.empty((self.h, self.w, 3), np.uint8)

@@ -31,6 +31,8 @@ def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 56
     assert ctypes.sizeof(hmi.hmi_tuning) == 24
+    assert ctypes.sizeof(hmi.hmi_interface) == 4 + 16 * 20 + 6 * 4
+    assert ctypes.sizeof(hmi.hmi_event) == 32
 
 
 def test_defaults_and_status_strings():
@@ -94,7 +96,7 @@ def test_status_constants_match_header():
     import re
     text = open(os.path.join(ROOT, "include", "hmi.h")).read()
     found = dict((k, int(v)) for k, v in re.findall(r"#define (HMI_[A-Z_]+) \(?(-?\d+)\)?", text))
-    names = [k for k in dir(hmi) if re.fullmatch(r"HMI_(OK|ERR_[A-Z_]+|LEARNING|TICK_KERNELS)", k)]
+    names = [k for k in dir(hmi) if re.fullmatch(r"HMI_(OK|ERR_[A-Z_]+|LEARNING|TICK_KERNELS|MAX_ZONES)", k)]
     assert found and set(found) == set(names)
     for k in names:
         assert getattr(hmi, k) == found[k], k

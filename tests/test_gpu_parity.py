@@ -748,3 +748,37 @@ def test_tracking_in_pipelined_batches():
     hmi.hmi_batch_destroy(b)
     for g in gs:
         g.close()
+
+
+# --------------------------------------------------------------------------- #
+# Interface module and driving wheel (Sec. 2, Sec. 4)                          #
+# --------------------------------------------------------------------------- #
+def test_interface_events_match_oracle():
+    """Config 2 (a moving hand that opens and closes): zones on the image's
+    quadrants and a wheel around its centre; every frame's event equals the
+    oracle's, and bad interfaces are refused."""
+    w, h = synth.shape(2)
+    zones = [(0, 0, w // 2 - 1, h // 2 - 1, 11), (w // 2, 0, w - 1, h // 2 - 1, 12),
+             (0, h // 2, w // 2 - 1, h - 1, 13), (w // 2, h // 2, w - 1, h - 1, 14)]
+    wheel = (w // 2, h // 2, 40, 260, 64)
+    g, o = pair(w, h, track_max_dist=80)
+    learn_both(g, o, synth.learn_frames(2, 0, 12))
+    g.set_interface(hmi.make_interface(zones, wheel))
+    o.set_interface(zones, (1,) + wheel)
+    seen = set()
+    for t in range(0, 60, 3):
+        f = synth.run_frame(2, 0, t)
+        check_frame(g, o, f, dev=t % 2 == 0, what=f"t={t}")
+        ev = hmi.hmi_get_event(g.handle)
+        frame_no = ev.pop("frame")
+        assert ev == o.event, (t, ev, o.event)
+        assert frame_no == o.frames
+        seen.add((ev["zone"], ev["on_wheel"]))
+    assert len(seen) >= 3, seen        # the hand visits several zones and the wheel
+    too_many = hmi.make_interface(zones)
+    too_many.nzones = hmi.HMI_MAX_ZONES + 1
+    for bad in (too_many, hmi.make_interface([], (10, 10, 50, 40, 0)),
+                hmi.make_interface([], (10, 10, 5, 40, 4000))):
+        with pytest.raises(hmi.HmiError):
+            g.set_interface(bad)
+    g.close()
