@@ -501,7 +501,7 @@ def run_ours(args) -> None:
     if single is not None:
         line["single_640x480"] = single
     if relearn is not None:
-        line["relearning"] = relearn
+        line["adaptive"] = relearn
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:
@@ -516,19 +516,25 @@ def run_ours(args) -> None:
 
 
 RELEARN_BENCH = dict(relearn_frames=30, relearn_min=20, relearn_period=300)
+TRACK_BENCH = 64
 
 
 def bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
-    """The 64-stream batch again, every stream re-learning (a window of 30
-    frames every 300): pipelined ticks over whole periods, with the same launch
-    shape; the cost is the window ticks' re-learning sums and bands."""
+    """The 64-stream batch again with the adaptive features on every stream:
+    re-learning (a window of 30 frames every 300), tracking, and an interface
+    (four zones and a wheel): pipelined ticks over whole periods, with the
+    same launch shape, then one period of plain ticks timed kernel by kernel."""
     n = len(rings)
     p = hmi.hmi_default_params(**RELEARN_BENCH)
     streams = []
     for i in range(n):
         w, h = synth.shape(CFG, i)
-        st = hmi.Stream(w, h, **RELEARN_BENCH)
+        st = hmi.Stream(w, h, track_max_dist=TRACK_BENCH, **RELEARN_BENCH)
         st.learn(torch.from_numpy(synth.learn_frames(CFG, i)).to(dev))
+        st.set_interface(hmi.make_interface(
+            [(0, 0, w // 2 - 1, h // 2 - 1, 1), (w // 2, 0, w - 1, h // 2 - 1, 2),
+             (0, h // 2, w // 2 - 1, h - 1, 3), (w // 2, h // 2, w - 1, h - 1, 4)],
+            (w // 2, h // 2, h // 8, h // 2, 64)))
         streams.append(st)
     b = hmi.hmi_batch_create([s.handle for s in streams])
     hmi.hmi_batch_set_tuning(b, dict(shape, groups=1))
@@ -559,7 +565,8 @@ def bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
     hmi.hmi_batch_destroy(b)
     for s in streams:
         s.close()
-    return {"params": RELEARN_BENCH, "ms_per_step": ms, "frames_per_s": n / (ms / 1e3),
+    return {"params": dict(RELEARN_BENCH, track_max_dist=TRACK_BENCH, interface="4 zones + wheel"),
+            "ms_per_step": ms, "frames_per_s": n / (ms / 1e3),
             "steps": steps, "launch": "pipelined ticks, the main run's launch shape, one group",
             "per_period_ms": {k: round(v, 3) for k, v in per.items()}, "period_ticks": ticks,
             "sums_ms_per_window_tick": per["relearn"] / p.relearn_frames,

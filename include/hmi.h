@@ -2,7 +2,7 @@
  * hmi.h -- C ABI of the GB300 hand-isolation library (libhmi.so).
  *
  * The library implements the per-frame path of the contactless interface of
- * Magoules & Zou (arXiv 1907.04393): learn a background without the user
+ * Magoules & Zou (arXiv 1907.04393): learn a background with no hand in view
  * (Sec. 2, initialisation step), then for every camera frame correct the
  * brightness (Sec. 2, Sec. 3.2), build the three thresholded images and AND
  * them (Sec. 3.1 (i)-(iii)), clean the mask with erosion/dilation (Sec. 3.1),
@@ -63,8 +63,8 @@ extern "C" {
  * click state and device work buffers.  Created by hmi_create_stream. */
 typedef struct hmi_stream hmi_stream;
 
-/* User-adjustable thresholds (Sec. 2: the FIZI settings are "easily
- * adjustable"; Sec. 3.1: tolerance S and hue thresholds alpha1, alpha2 are set
+/* User-adjustable thresholds (Sec. 2: the FIZI settings can be changed by
+ * the user; Sec. 3.1: tolerance S and hue thresholds alpha1, alpha2 are set
  * by the user).  Defaults in brackets, set by hmi_default_params. */
 typedef struct {
     uint32_t gain_min_q16;  /* [32768]  lower clamp of the brightness gain, Q16 (0.5) */
@@ -81,8 +81,8 @@ typedef struct {
     uint8_t close_iters;    /* [1]      closings (dilate, erode) to connect zones; open+close <= 16 */
     uint8_t click_on_pct;   /* [80]     click when 100*area < on_pct * reference area */
     uint8_t click_off_pct;  /* [90]     release when 100*area > off_pct * reference area */
-    /* Re-learning (Sec. 3.3: the learning is re-initiated partly as the
-     * luminosity evolves).  Off when relearn_frames is 0.  Otherwise the last
+    /* Re-learning (Sec. 3.3: part of the learning is restarted from time to
+     * time as the lighting drifts).  Off when relearn_frames is 0.  Otherwise the last
      * relearn_frames frames of every relearn_period frames (counted from 1
      * after learning) add the gain-corrected values of their background
      * pixels to per-pixel sums; after the window each pixel counted at least
@@ -101,8 +101,8 @@ typedef struct {
     uint16_t track_max_dist;/* [0]      pixels */
 } hmi_params;
 
-/* The Mouse module's pointer (Sec. 2): position of the hand zone and its
- * state "click or not".  With no foreground at all: valid 0, area 0,
+/* The Mouse module's pointer (Sec. 2): position of the hand zone and
+ * whether it is clicked.  With no foreground at all: valid 0, area 0,
  * label -1, box -1, x = y = -1. */
 typedef struct {
     int32_t valid;    /* 1 iff the largest blob has at least min_area pixels */
@@ -127,8 +127,8 @@ HMI_API hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p);
  * Any batch that contains the stream must be destroyed first. */
 HMI_API void hmi_destroy_stream(hmi_stream *s);
 
-/* Learn the background model from n user-free frames (Sec. 2: "the FIZI
- * module learns the background without the user"; Sec. 3.1 (i): per-pixel
+/* Learn the background model from n user-free frames (Sec. 2: the FIZI
+ * module learns the background before the hand enters; Sec. 3.1 (i): per-pixel
  * minimum and maximum).  frames: n consecutive packed RGB8 frames
  * (n*h*w*3 bytes), host or device.  Per pixel and channel the library keeps
  * the exact sums S, Q and the min / max, derives the background band and the
@@ -268,8 +268,8 @@ HMI_API int hmi_get_background_stats(const hmi_stream *s, float *mean, float *st
  * component (Mouse module, Sec. 2).  Computed on demand from the last mask. */
 HMI_API int hmi_get_labels(const hmi_stream *s, int32_t *labels);
 
-/* Headless Interface module (Sec. 2: linked to the Mouse module, it finds
- * the interface zone activated by the pointer; zones are linked to events)
+/* Headless Interface module (Sec. 2: fed by the Mouse module, it finds
+ * which interface zone holds the pointer; each zone maps to an event)
  * and driving wheel (Sec. 4: the hand turns around an imaginary wheel to
  * steer left and right; speed is the third control).  Per frame, from the
  * valid pointer's rounded centroid p = floor((2 sum + area) / (2 area)) per
@@ -366,7 +366,7 @@ HMI_API void hmi_server_destroy(hmi_server *srv);
  * With learn_frames non-NULL the background is learned now from n contiguous
  * host frames (h*w*3 bytes each).  With learn_frames NULL the stream learns
  * online: the first n frames submitted to it are the user-free learning frames
- * (Sec. 2: the FIZI module learns the background without the user), each
+ * (Sec. 2: the FIZI module learns the background with no hand in view), each
  * accumulated by the dispatcher as it arrives and returned with status
  * HMI_LEARNING; the band is formed after the n-th, and later frames are
  * processed.  n: 1..65535. */

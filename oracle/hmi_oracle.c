@@ -43,9 +43,9 @@ static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
 
 /* ======================================================================== */
-/* Step L -- background learning (Sec. 2 "the FIZI module learns the          */
-/* background without the user"; Sec. 3.1 (i) "minimum and maximum values     */
-/* learned in the initialization step"; Sec. 3.3 cites Gaussian background    */
+/* Step L -- background learning (Sec. 2: the FIZI module learns the         */
+/* background before the hand enters; Sec. 3.1 (i): per-pixel minimum and    */
+/* maximum taken during that learning; Sec. 3.3 cites Gaussian background     */
 /* models for the learning).                                                 */
 /* ======================================================================== */
 
@@ -142,8 +142,8 @@ void orc_learn_band(const uint32_t *S, const uint32_t *Q,
 }
 
 /* ======================================================================== */
-/* Re-learning, Sec. 3.3: dealing with the evolution of the luminosity, the  */
-/* learning is sometimes re-initiated partly.                                 */
+/* Re-learning, Sec. 3.3: as the lighting drifts, part of the learning is    */
+/* restarted from time to time.                                               */
 /* Reading: with a period of P frames and a window of the last R of them,     */
 /* every frame of a window adds the gain-corrected values of the pixels that  */
 /* its background test classified as background (all three channels inside  */
@@ -214,8 +214,8 @@ int orc_relearn_in_window(long long f, int period, int frames)
 }
 
 /* ======================================================================== */
-/* Step 1 -- brightness correction (Sec. 2 "The brightness is also corrected"; */
-/* Sec. 3.2 "a filter ... to modify the Luminosity component").               */
+/* Step 1 -- brightness correction (Sec. 2: the running step corrects the    */
+/* brightness; Sec. 3.2: a filter acts on the luminosity component).          */
 /* Reading: the frame is rescaled so that its total luma equals the mean      */
 /* total luma of the learning frames.  A uniform RGB scale leaves hue          */
 /* unchanged and moves luminosity, which is what the filter must do.          */
@@ -302,11 +302,13 @@ static int in_arc(int h, int a1, int a2)
 /* Per-pixel masks on the gain-corrected frame c (H*W*3 bytes):
  *   fg1 (Sec. 3.1 (i))  : 1 iff some channel lies outside [lo_c, hi_c].
  *       Reading: the printed formula keeps pixels between min and max,
- *       which contradicts the sentence above it ("between ... are removed");
+ *       which contradicts the text above it (pixels inside the range are the
+ *       background and are dropped);
  *       the sentence is taken, with inclusive bounds.
  *   fg2 (Sec. 3.1 (ii)) : 1 iff max(c) - min(c) >= S (gray pixels removed).
- *       Reading: the printed formula has no comparison; the sentence
- *       ("lower than a tolerance S ... eliminated") is taken.
+ *       Reading: the printed formula has no comparison; the text
+ *       (pixels whose channel spread is below a tolerance S are dropped) is
+ *       taken.
  *   fg3 (Sec. 3.1 (iii)): 1 iff the hue is defined and inside the arc.
  *   raw = fg1 AND fg2 AND fg3 (the merging step of Sec. 3.1).
  * Any of the output pointers may be NULL. */
@@ -333,8 +335,8 @@ void orc_fg(const uint8_t *c, const uint8_t *lo, const uint8_t *hi, size_t npx,
 }
 
 /* ======================================================================== */
-/* Step 4 -- morphology, Sec. 3.1 "erosion and dilatation operators ... remove */
-/* the small noisy objects and connect neighborhood zones".                   */
+/* Step 4 -- morphology, Sec. 3.1: erosion and dilation clean away small     */
+/* spurious blobs and join nearby regions.                                    */
 /* Reading: 3x3 square element; opening (erode then dilate) open_iters times,  */
 /* then closing (dilate then erode) close_iters times; pixels outside the      */
 /* image are neutral (ignored) for both operators.                             */
@@ -388,8 +390,8 @@ void orc_morph(const uint8_t *raw, int w, int h, int open_iters, int close_iters
 }
 
 /* ======================================================================== */
-/* Step 5a -- connected components (Sec. 2 Mouse module: "tracks the hand     */
-/* corresponding zone" in the binary image).                                  */
+/* Step 5a -- connected components (Sec. 2 Mouse module: it follows the      */
+/* hand's region of the binary image).                                        */
 /* Reading: 8-connectivity; every component is labelled with the smallest     */
 /* linear index y*W + x of its pixels; background is -1.  Plain flood fill:   */
 /* scanning in raster order, the first unlabelled foreground pixel of a       */
@@ -520,7 +522,7 @@ void orc_pointer_from_labels(const int32_t *labels, int w, int h, uint32_t min_a
     orc_pointer_select(labels, w, h, min_area, 0, NULL, out);
 }
 
-/* Click state machine of one stream (reading of "its state (click or not)").
+/* Click state machine of one stream (reading of the pointer's clicked / not-clicked state).
  * hist holds the areas of the last `window` valid frames, oldest first
  * (hist_count entries).  For a valid frame, A_ref = max(hist):
  *   click := 1 if 100*area < on_pct  * A_ref
@@ -589,8 +591,8 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
 }
 
 /* ======================================================================== */
-/* Interface module (Sec. 2: with the Mouse module it determines the          */
-/* interface zone activated by the pointer, zones being linked to events)     */
+/* Interface module (Sec. 2: fed by the Mouse module, it finds which         */
+/* interface zone holds the pointer; each zone maps to an event)             */
 /* and the driving application (Sec. 4: the hand turns around an imaginary    */
 /* wheel to steer left or right, and the speed is the third control).        */
 /* Reading, headless and integer: the pointer point is the rounded centroid   */

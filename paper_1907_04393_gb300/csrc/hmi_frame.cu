@@ -1,13 +1,13 @@
 // hmi_frame.cu -- per-pixel kernels of a tick:
 //   k_luma        frame luma sum per stream; the last CTA turns the sums into the
-//                 brightness gains (Sec. 2 "the brightness is also corrected",
+//                 brightness gains (Sec. 2 brightness correction,
 //                 Sec. 3.2 luminosity filter)
 //   k_classify    gain and background band test (Sec. 3.1 (i)) of every pixel,
 //                 one bit per pixel; chunks with out-of-band pixels are queued
 //   k_skin        gray and hue tests (Sec. 3.1 (ii), (iii)) of the queued
 //                 pixels, clearing those that fail (the AND of the merging step)
-//   k_morph_strip opening/closing on the bit mask (Sec. 3.1 "erosion and
-//                 dilatation") in registers, the 0/1 mask bytes, and the list
+//   k_morph_strip opening/closing on the bit mask (Sec. 3.1 erosion and
+//                 dilation) in registers, the 0/1 mask bytes, and the list
 //                 of 32x32 blocks holding foreground
 //   k_block_cc    8-connected components of each listed block with their
 //                 statistics (Mouse module, Sec. 2)
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kThreads) k_skin(BatchDev b)
 }
 
 // ---------------------------------------------------------------------------
-// k_relearn: re-learning sums (Sec. 3.3, the learning is re-initiated partly).
+// k_relearn: re-learning sums (Sec. 3.3, part of the learning restarted).
 // In a window frame of a stream, every background pixel (all three gain-
 // corrected channels inside the band: the test of k_classify) adds its
 // corrected values to the stream's sums.  One thread per 16-px chunk, four

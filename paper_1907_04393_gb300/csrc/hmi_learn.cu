@@ -1,6 +1,6 @@
 // hmi_learn.cu -- background learning (Sec. 2: the FIZI module learns the
-// background without the user; Sec. 3.1 (i): minimum and maximum values learned
-// in the initialisation step; Sec. 3.3: Gaussian background models).
+// background before the hand enters; Sec. 3.1 (i): per-pixel minimum and
+// maximum taken during that learning; Sec. 3.3: Gaussian background models).
 //   k_learn_accum  exact per pixel-channel sums S = sum v, Q = sum v^2 and the
 //                  min / max over a chunk of frames, plus the frames' luma total
 //                  (k_learn_accum4: the same, four pixels per thread, vectorised)

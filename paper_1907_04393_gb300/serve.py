@@ -7,7 +7,7 @@ leaving (exponential lifetimes) while the trace runs, with admission limited
 by the server's device-memory budget (a refused stream retries every 100 ms,
 and its frames are lost until it is admitted).  A stream's first n_learn
 frames are its user-free learning frames (Sec. 2: the background is learned
-without the user); the server accumulates them online as they arrive.  The
+with no hand in view); the server accumulates them online as they arrive.  The
 trace is replayed in wall-clock time; the latency of a frame is its completion
 time minus its scheduled arrival time, so a submitter running late counts
 against the server, never for it.

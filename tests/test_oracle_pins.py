@@ -210,7 +210,7 @@ def test_band_edges_against_decimal_mu_minus_k_sigma():
 
 
 # --------------------------------------------------------------------------- #
-# Brightness (Sec. 2 "brightness is also corrected"; Sec. 3.2)                 #
+# Brightness (Sec. 2 brightness correction; Sec. 3.2)                          #
 # --------------------------------------------------------------------------- #
 def test_luma8_close_to_bt601():
     cols = RNG.integers(0, 256, size=(5000, 3)).astype(np.uint8)
@@ -285,7 +285,7 @@ def test_band_edges_inclusive():
 
 
 # --------------------------------------------------------------------------- #
-# Morphology (Sec. 3.1 "erosion and dilatation")                               #
+# Morphology (Sec. 3.1 erosion and dilation)                                   #
 # --------------------------------------------------------------------------- #
 SIZES = [(1, 1), (1, 7), (6, 1), (2, 2), (5, 3), (8, 8), (13, 17), (37, 29), (33, 64)]
 
@@ -380,7 +380,7 @@ def test_hand_counted_components():
 
 
 # --------------------------------------------------------------------------- #
-# Pointer and click state (Sec. 2: pointer, "its state (click or not)")        #
+# Pointer and click state (Sec. 2: pointer and its clicked state)             #
 # --------------------------------------------------------------------------- #
 def _ellipse(h, w, cy, cx, a, b):
     yy, xx = np.mgrid[0:h, 0:w]
@@ -464,7 +464,7 @@ def test_click_follows_open_closed_config2():
 
 
 # --------------------------------------------------------------------------- #
-# Re-learning (Sec. 3.3: the learning is re-initiated partly)                 #
+# Re-learning (Sec. 3.3: part of the learning restarted as lighting drifts)   #
 # --------------------------------------------------------------------------- #
 FIXED_GAIN = dict(gain_min_q16=65536, gain_max_q16=65536)   # c' = c: no brightness term
 
