@@ -95,6 +95,13 @@ def _load():
             "orc_process_frame": (None, [_P, _I, _I, _P, _P, _U64, _I, _I, _I, _I, _I,
                                          _U32, _U32, _U32, _I, _I, _I, _I, _P, _P, _P, _P,
                                          _P, _P, _P, _P]),
+            "orc_process_frame_bg": (None, [_P, _I, _I, _P, _P, _P, _U64, _I, _I, _I, _I, _I,
+                                            _U32, _U32, _U32, _I, _I, _I, _I, _P, _P, _P, _P,
+                                            _P, _P, _P, _P]),
+            "orc_mixture_step": (None, [_P, _P, _P, _P, _SZ, _I, _P, _U32, _I, _I, _I, _I,
+                                        _U32, _U32, _P]),
+            "orc_mixture_learn": (None, [_P, _I, _SZ, _I, _P, _P, _P, _P, _I, _I, _I, _U32,
+                                         _U32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -122,7 +129,9 @@ DEFAULTS = dict(gray_tol=15, hue_lo=1472, hue_hi=256, bg_margin=2, bg_k_num=5,
                 bg_k_den=2, open_iters=1, close_iters=1, gain_min_q16=32768,
                 gain_max_q16=131072, min_area=50, click_on_pct=80,
                 click_off_pct=90, click_window=30,
-                relearn_frames=0, relearn_min=0, relearn_period=0, track_max_dist=0)
+                relearn_frames=0, relearn_min=0, relearn_period=0, track_max_dist=0,
+                bg_model=0, mix_k=3, mix_bg_pct=70, mix_sigma0=15, mix_sigma_min=2,
+                mix_rate_n=256)
 
 
 def params(**over) -> dict:
@@ -339,6 +348,67 @@ def relearn_in_window(f: int, period: int, frames: int) -> bool:
     return bool(_load().orc_relearn_in_window(f, period, frames))
 
 
+class _OrcMixture(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_void_p), ("M", ctypes.c_void_p), ("V", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("K", ctypes.c_int), ("t", ctypes.c_uint32),
+                ("rate_n", ctypes.c_int), ("bg_pct", ctypes.c_int), ("ln", ctypes.c_int),
+                ("ld", ctypes.c_int), ("v_init", ctypes.c_uint32), ("v_min", ctypes.c_uint32)]
+
+
+class Mixture:
+    """Per-pixel Gaussian mixture of one stream (orc_mixture_step, Sec. 2 / Sec. 3.3).
+
+    Planes: W (K, npx) Q15 weights, M (K, 3, npx) Q8 means, V (K, npx) Q4
+    variances, C (K, npx) match counts, in storage (fitness) order; t is the
+    number of frames seen so far."""
+
+    def __init__(self, npx: int, K: int, rate_n: int, bg_pct: int, ln: int, ld: int,
+                 sigma0: int, sigma_min: int):
+        self.npx, self.K = int(npx), int(K)
+        self.rate_n, self.bg_pct, self.ln, self.ld = int(rate_n), int(bg_pct), int(ln), int(ld)
+        self.v_init, self.v_min = 16 * int(sigma0) ** 2, 16 * int(sigma_min) ** 2
+        self.W = np.zeros((K, npx), np.uint16)
+        self.M = np.zeros((K, 3, npx), np.uint16)
+        self.V = np.zeros((K, npx), np.uint16)
+        self.C = np.zeros((K, npx), np.uint16)
+        self.t = 0
+
+    @classmethod
+    def from_params(cls, npx: int, p: dict) -> "Mixture":
+        return cls(npx, p["mix_k"], p["mix_rate_n"], p["mix_bg_pct"], p["bg_k_num"],
+                   p["bg_k_den"], p["mix_sigma0"], p["mix_sigma_min"])
+
+    def step(self, x: np.ndarray, classify: bool = True):
+        """One frame x (npx x 3 bytes, or any shape of npx*3 bytes).  Returns
+        fg1 (npx uint8) when classify, else None."""
+        x = _u8(x).reshape(-1)
+        assert x.size == 3 * self.npx
+        self.t += 1
+        fg1 = np.empty(self.npx, np.uint8) if classify else None
+        _load().orc_mixture_step(_ptr(self.W), _ptr(self.M), _ptr(self.V), _ptr(self.C), self.npx,
+                                 self.K, _ptr(x), self.t, self.rate_n, self.bg_pct, self.ln, self.ld,
+                                 self.v_init, self.v_min, _ptr(fg1))
+        return fg1
+
+    def learn(self, frames: np.ndarray) -> None:
+        """The learning frames in order from an empty model (orc_mixture_learn)."""
+        frames = _u8(frames)
+        n = frames.shape[0]
+        assert frames[0].size == 3 * self.npx
+        _load().orc_mixture_learn(_ptr(frames), n, self.npx, self.K, _ptr(self.W), _ptr(self.M),
+                                  _ptr(self.V), _ptr(self.C), self.rate_n, self.ln, self.ld,
+                                  self.v_init, self.v_min)
+        self.t = n
+
+    def descriptor(self, t: int) -> _OrcMixture:
+        return _OrcMixture(_ptr(self.W), _ptr(self.M), _ptr(self.V), _ptr(self.C), self.K, t,
+                           self.rate_n, self.bg_pct, self.ln, self.ld, self.v_init, self.v_min)
+
+    def planes(self) -> np.ndarray:
+        """All state as (6K, npx) uint16: W[k], M[k][ch], V[k], C[k]."""
+        return np.concatenate([self.W, self.M.reshape(3 * self.K, -1), self.V, self.C])
+
+
 class OracleStream:
     """The whole path for one camera stream: learn once, then process frames."""
 
@@ -358,6 +428,10 @@ class OracleStream:
         self.lo, self.hi = learn_band(S, Q, vmin, vmax, n, self.p["bg_k_num"],
                                       self.p["bg_k_den"], self.p["bg_margin"])
         self.syref = ref_luma(frames)
+        self.mix = None
+        if self.p["bg_model"] == 1:
+            self.mix = Mixture.from_params(self.h * self.w, self.p)
+            self.mix.learn(frames)
         self.learned = True
         self._reset_relearn()
 
@@ -372,6 +446,8 @@ class OracleStream:
 
     def set_background(self, S, Q, vmin, vmax, n: int, syref: int) -> None:
         """Install learned sums directly (the state learning would leave)."""
+        assert self.p["bg_model"] == 0, "a mixture stream learns from frames"
+        self.mix = None
         self.n = int(n)
         self.S = np.ascontiguousarray(S, np.uint32)
         self.Q = np.ascontiguousarray(Q, np.uint32)
@@ -397,14 +473,19 @@ class OracleStream:
         ptr = Pointer()
         g = ctypes.c_uint32(0)
         c = self.click
-        _load().orc_process_frame(
-            _ptr(frame), self.w, self.h, _ptr(self.lo), _ptr(self.hi), self.syref,
+        mix = getattr(self, "mix", None)
+        desc = mix.descriptor(mix.t + 1) if mix is not None else None
+        _load().orc_process_frame_bg(
+            _ptr(frame), self.w, self.h, _ptr(self.lo), _ptr(self.hi),
+            ctypes.byref(desc) if desc is not None else None, self.syref,
             p["gray_tol"], p["hue_lo"], p["hue_hi"], p["open_iters"], p["close_iters"],
             p["gain_min_q16"], p["gain_max_q16"], p["min_area"], p["click_on_pct"],
             p["click_off_pct"], c.window, p["track_max_dist"], _ptr(self.track),
             ctypes.byref(c.click), _ptr(c.hist),
             ctypes.byref(c.count), _ptr(mask), _ptr(labels), ctypes.byref(ptr),
             ctypes.byref(g))
+        if mix is not None:
+            mix.t += 1
         # the Interface module's event from this frame's pointer (Sec. 2, 4)
         if getattr(self, "ui", None) is not None:
             pd = ptr.as_dict()

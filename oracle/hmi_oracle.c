@@ -214,6 +214,139 @@ int orc_relearn_in_window(long long f, int period, int frames)
 }
 
 /* ======================================================================== */
+/* Mixture-of-Gaussians background (Sec. 2: the FIZI module learns the        */
+/* background with advanced machine learning; Sec. 3.3 cites Lee's adaptive   */
+/* Gaussian mixture learning for it).  A variant of the learning (step L) and */
+/* of the background test (step 2); the other steps are unchanged.            */
+/* Reading, all integer, per pixel: K components kept in fitness order, each  */
+/* a weight W (Q15), a mean per channel M (Q8), one variance V shared by the  */
+/* three channels (Q4: level^2 * 16) and a match count C (C = 0: empty).  For */
+/* the value x (3 bytes) of frame t, t counted from 1 over the learning and   */
+/* then the running frames:                                                  */
+/*  1. match: the first non-empty component with                             */
+/*       ld^2 * sum_ch (256 x - M)^2 <= ln^2 * V * 4096                       */
+/*     (distance at most lambda = ln / ld standard deviations);               */
+/*  2. decision (running frames only, on the model before this frame): the   */
+/*     pixel is background iff it matched component j and the weights of the */
+/*     components before j sum to at most T percent of all weights (the      */
+/*     fittest components that first exceed T are the background, after      */
+/*     Stauffer and Grimson);                                                 */
+/*  3. update with Lee's per-component rates: a matched component's count    */
+/*     grows by one, and with r = min(C, N) its mean moves by (256 x - M) / r */
+/*     and its variance by (D / 3 - V) / r, D the squared distance of step 1  */
+/*     in Q4 (V clamped to [Vmin, 65535]); with no match the last component   */
+/*     becomes a new one at x (M = 256 x, V = V0, C = 1, W = 0).  Then, with  */
+/*     m = min(t, N), every weight moves by (32768 [matched or new] or 0      */
+/*     [others] - W) / m.  Every division rounds half away from zero; the     */
+/*     1/r and 1/m schedules make early estimates plain averages, and         */
+/*     1/N is the learning rate alpha once enough frames are seen;            */
+/*  4. the components are stably re-sorted: non-empty ones first, by        */
+/*     W / sqrt(V), largest first (a before b iff W_a^2 V_b > W_b^2 V_a       */
+/*     strictly), empty ones last.                                            */
+/* State layout: planes of npx entries, W[k], M[k][ch], V[k], C[k] in this    */
+/* order, k in storage (fitness) order.                                      */
+/* ======================================================================== */
+
+/* round(a / m) for m > 0, halves away from zero */
+static int64_t div_round(int64_t a, int64_t m)
+{
+    const int64_t q = (2 * (a < 0 ? -a : a) + m) / (2 * m);
+    return a < 0 ? -q : q;
+}
+
+void orc_mixture_step(uint16_t *W, uint16_t *M, uint16_t *V, uint16_t *C, size_t npx, int K,
+                      const uint8_t *x, uint32_t t, int rate_n, int bg_pct, int ln, int ld,
+                      uint32_t v_init, uint32_t v_min, uint8_t *fg1)
+{
+    const int64_t mt = (int64_t)(t < (uint32_t)rate_n ? t : (uint32_t)rate_n);
+    for (size_t p = 0; p < npx; ++p) {
+        const uint8_t *px = x + 3 * p;
+        int j = -1;
+        int64_t e[3] = {0, 0, 0};
+        int64_t d2 = 0;
+        for (int k = 0; k < K && j < 0; ++k) {
+            if (C[k * npx + p] == 0) continue;
+            int64_t dk[3], s2 = 0;
+            for (int ch = 0; ch < 3; ++ch) {
+                dk[ch] = 256 * (int64_t)px[ch] - (int64_t)M[(3 * k + ch) * npx + p];
+                s2 += dk[ch] * dk[ch];
+            }
+            if ((int64_t)ld * ld * s2 <= (int64_t)ln * ln * (int64_t)V[k * npx + p] * 4096) {
+                j = k;
+                for (int ch = 0; ch < 3; ++ch) e[ch] = dk[ch];
+                d2 = s2;
+            }
+        }
+        if (fg1) {
+            int64_t total = 0, before = 0;
+            for (int k = 0; k < K; ++k) {
+                total += W[k * npx + p];
+                if (k < j) before += W[k * npx + p];
+            }
+            const int background = (j >= 0) && (100 * before <= (int64_t)bg_pct * total);
+            fg1[p] = (uint8_t)!background;
+        }
+        if (j >= 0) {
+            uint16_t *c = &C[j * npx + p];
+            if (*c < 65535) *c += 1;
+            const int64_t r = *c < rate_n ? *c : rate_n;
+            for (int ch = 0; ch < 3; ++ch) {
+                uint16_t *m = &M[(3 * j + ch) * npx + p];
+                *m = (uint16_t)(*m + div_round(e[ch], r));
+            }
+            const int64_t target = div_round(d2, 3 * 4096);
+            int64_t v = V[j * npx + p];
+            v += div_round(target - v, r);
+            if (v < (int64_t)v_min) v = v_min;
+            if (v > 65535) v = 65535;
+            V[j * npx + p] = (uint16_t)v;
+        } else {
+            j = K - 1;
+            for (int ch = 0; ch < 3; ++ch) M[(3 * j + ch) * npx + p] = (uint16_t)(256 * px[ch]);
+            V[j * npx + p] = (uint16_t)v_init;
+            C[j * npx + p] = 1;
+            W[j * npx + p] = 0;
+        }
+        for (int k = 0; k < K; ++k) {
+            const int64_t w = W[k * npx + p];
+            W[k * npx + p] = (uint16_t)(w + div_round((k == j ? 32768 : 0) - w, mt));
+        }
+        /* stable insertion sort, fittest first */
+        for (int a = 1; a < K; ++a) {
+            for (int b = a; b > 0; --b) {
+                const uint64_t wb = W[b * npx + p], wp = W[(b - 1) * npx + p];
+                const uint64_t vb = V[b * npx + p], vp = V[(b - 1) * npx + p];
+                const int cb = C[b * npx + p] > 0, cp = C[(b - 1) * npx + p] > 0;
+                const int fitter = cb && (!cp || wb * wb * vp > wp * wp * vb);
+                if (!fitter) break;
+                uint16_t tmp;
+#define ORC_SWAP(arr, i0, i1) (tmp = arr[(i0)], arr[(i0)] = arr[(i1)], arr[(i1)] = tmp)
+                ORC_SWAP(W, b * npx + p, (b - 1) * npx + p);
+                ORC_SWAP(V, b * npx + p, (b - 1) * npx + p);
+                ORC_SWAP(C, b * npx + p, (b - 1) * npx + p);
+                for (int ch = 0; ch < 3; ++ch) ORC_SWAP(M, (3 * b + ch) * npx + p, (3 * (b - 1) + ch) * npx + p);
+#undef ORC_SWAP
+            }
+        }
+    }
+}
+
+/* Learning of the mixture: the update of every learning frame in order,     */
+/* from an empty model (all planes zero), with t = 1..n.                     */
+void orc_mixture_learn(const uint8_t *frames, int n, size_t npx, int K, uint16_t *W, uint16_t *M,
+                       uint16_t *V, uint16_t *C, int rate_n, int ln, int ld, uint32_t v_init,
+                       uint32_t v_min)
+{
+    memset(W, 0, sizeof(uint16_t) * npx * K);
+    memset(M, 0, sizeof(uint16_t) * npx * K * 3);
+    memset(V, 0, sizeof(uint16_t) * npx * K);
+    memset(C, 0, sizeof(uint16_t) * npx * K);
+    for (int f = 0; f < n; ++f)
+        orc_mixture_step(W, M, V, C, npx, K, frames + (size_t)f * npx * 3, (uint32_t)(f + 1), rate_n,
+                         100, ln, ld, v_init, v_min, NULL);
+}
+
+/* ======================================================================== */
 /* Step 1 -- brightness correction (Sec. 2: the running step corrects the    */
 /* brightness; Sec. 3.2: a filter acts on the luminosity component).          */
 /* Reading: the frame is rescaled so that its total luma equals the mean      */
@@ -555,13 +688,25 @@ void orc_click_update(int32_t *click, uint32_t *hist, int32_t *hist_count, int w
     out->click = *click;
 }
 
+/* A stream's mixture as the whole-path function takes it: the planes of      */
+/* orc_mixture_step, the number t of the frame being processed and the        */
+/* parameters.                                                                */
+typedef struct {
+    uint16_t *W, *M, *V, *C;
+    int K;
+    uint32_t t;
+    int rate_n, bg_pct, ln, ld;
+    uint32_t v_init, v_min;
+} orc_mixture;
+
 /* ======================================================================== */
 /* One frame through the whole path (Sec. 2 running step):                    */
 /* brightness -> three masks -> AND -> morphology -> components -> pointer.  */
-/* mask_out / labels_out / corrected_out may be NULL.                         */
+/* mask_out / labels_out may be NULL.  mix NULL: the band test with lo / hi;  */
+/* else the mixture's test on the frame number mix->t, then its update.       */
 /* ======================================================================== */
-void orc_process_frame(const uint8_t *frame, int w, int h,
-                       const uint8_t *lo, const uint8_t *hi, uint64_t syref,
+void orc_process_frame_bg(const uint8_t *frame, int w, int h,
+                       const uint8_t *lo, const uint8_t *hi, const orc_mixture *mix, uint64_t syref,
                        int gray_tol, int hue_lo, int hue_hi,
                        int open_iters, int close_iters,
                        uint32_t gain_min, uint32_t gain_max, uint32_t min_area,
@@ -579,7 +724,20 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
     uint64_t sy = orc_luma_sum(frame, npx);
     uint32_t g = orc_gain(sy, syref, gain_min, gain_max);
     orc_apply_gain(frame, npx * 3, g, c);
-    orc_fg(c, lo, hi, npx, gray_tol, hue_lo, hue_hi, NULL, NULL, NULL, raw);
+    if (mix) {
+        /* background test by the mixture (on the model before this frame), */
+        /* then its update; the gray and hue tests as for the band            */
+        uint8_t *fg1 = (uint8_t *)malloc(npx + 1);
+        uint8_t *fg2 = (uint8_t *)malloc(npx + 1);
+        uint8_t *fg3 = (uint8_t *)malloc(npx + 1);
+        orc_mixture_step(mix->W, mix->M, mix->V, mix->C, npx, mix->K, c, mix->t, mix->rate_n,
+                         mix->bg_pct, mix->ln, mix->ld, mix->v_init, mix->v_min, fg1);
+        orc_fg(c, c, c, npx, gray_tol, hue_lo, hue_hi, NULL, fg2, fg3, NULL);
+        for (size_t p = 0; p < npx; ++p) raw[p] = (uint8_t)(fg1[p] && fg2[p] && fg3[p]);
+        free(fg1); free(fg2); free(fg3);
+    } else {
+        orc_fg(c, lo, hi, npx, gray_tol, hue_lo, hue_hi, NULL, NULL, NULL, raw);
+    }
     orc_morph(raw, w, h, open_iters, close_iters, mask);
     orc_label(mask, w, h, labels);
     orc_pointer_select(labels, w, h, min_area, track_max_dist, track, pointer_out);
@@ -588,6 +746,23 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
     if (labels_out) memcpy(labels_out, labels, npx * sizeof(int32_t));
     if (gain_out) *gain_out = g;
     free(c); free(raw); free(mask); free(labels);
+}
+
+void orc_process_frame(const uint8_t *frame, int w, int h,
+                       const uint8_t *lo, const uint8_t *hi, uint64_t syref,
+                       int gray_tol, int hue_lo, int hue_hi,
+                       int open_iters, int close_iters,
+                       uint32_t gain_min, uint32_t gain_max, uint32_t min_area,
+                       int on_pct, int off_pct, int window,
+                       int track_max_dist, int32_t *track,
+                       int32_t *click, uint32_t *hist, int32_t *hist_count,
+                       uint8_t *mask_out, int32_t *labels_out, orc_pointer *pointer_out,
+                       uint32_t *gain_out)
+{
+    orc_process_frame_bg(frame, w, h, lo, hi, NULL, syref, gray_tol, hue_lo, hue_hi, open_iters,
+                         close_iters, gain_min, gain_max, min_area, on_pct, off_pct, window,
+                         track_max_dist, track, click, hist, hist_count, mask_out, labels_out,
+                         pointer_out, gain_out);
 }
 
 /* ======================================================================== */

@@ -670,3 +670,202 @@ def test_interface_zones_and_wheel():
     small = oracle.interface_event(True, 305, 100, 0, [], wheel)  # 5 px right of the top: 1024*5/105 = 48
     assert (small["steer"], small["right"]) == (48, 0)             # inside the dead zone of 64
     assert oracle.interface_event(True, 310, 100, 0, [], wheel)["right"] == 1   # 1024*10/110 = 93
+
+
+# --------------------------------------------------------------------------- #
+# Gaussian mixture background (Sec. 2 advanced learning; Sec. 3.3 cites Lee's  #
+# adaptive mixture learning)                                                   #
+# --------------------------------------------------------------------------- #
+from fractions import Fraction
+
+
+def _mix(npx=1, K=3, N=256, T=70, ln=5, ld=2, s0=15, smin=2):
+    return oracle.Mixture(npx, K, N, T, ln, ld, s0, smin)
+
+
+def test_mixture_hand_worked_fixture(golden_dir):
+    m = _mix()
+    for row in _golden_rows(golden_dir, "mixture_1px.txt"):
+        head, W, M, V, C = row.split("|")
+        t, x0, x1, x2, fg = map(int, head.split())
+        got = m.step(np.array([[x0, x1, x2]], np.uint8))
+        assert m.t == t
+        assert int(got[0]) == fg, t
+        assert m.W[:, 0].tolist() == list(map(int, W.split())), t
+        assert m.M[:, :, 0].reshape(-1).tolist() == list(map(int, M.split())), t
+        assert m.V[:, 0].tolist() == list(map(int, V.split())), t
+        assert m.C[:, 0].tolist() == list(map(int, C.split())), t
+
+
+def test_mixture_constant_pixel_closed_form():
+    """A constant value: one component with the exact mean, full weight and count
+    n; its variance follows V0 * prod_{r=2..n} (1 - 1/r) = V0 / n (telescoping),
+    each of the n - 1 roundings adding at most 1/2 scaled by r/n: |err| <= (n+1)/4."""
+    n, s0 = 40, 15
+    m = _mix(npx=2, s0=s0)
+    x = np.array([[37, 180, 99], [0, 255, 128]], np.uint8)
+    fgs = [m.step(x) for _ in range(n)]
+    assert fgs[0].tolist() == [1, 1] and all(f.tolist() == [0, 0] for f in fgs[1:])
+    assert (m.M[0] == 256 * x.T.astype(np.uint16)).all()
+    assert (m.W[0] == 32768).all() and (m.W[1:] == 0).all()
+    assert (m.C[0] == n).all() and (m.C[1:] == 0).all()
+    exact = 16 * s0 * s0 / n
+    assert (np.abs(m.V[0].astype(float) - exact) <= (n + 1) / 4).all()
+
+
+def test_mixture_mean_is_the_running_average():
+    """With every value matching one component and n <= N, the 1/C rate makes
+    the mean the plain average of the values, within (n+1)/4 in Q8 (each step
+    rounds by at most 1/2; the error of step i is scaled by i/n)."""
+    rng = np.random.default_rng(5)
+    m = _mix(npx=64, ln=15, ld=1, s0=63)         # lambda*sigma far above the spread
+    vals = rng.integers(100, 141, size=(30, 64, 3), dtype=np.uint8)
+    for v in vals:
+        m.step(v)
+    n = len(vals)
+    assert (m.C[0] == n).all() and (m.C[1:] == 0).all()
+    for p in range(64):
+        for ch in range(3):
+            mean = Fraction(int(vals[:, p, ch].astype(int).sum()) * 256, n)
+            assert abs(Fraction(int(m.M[0, ch, p])) - mean) <= Fraction(n + 1, 4)
+
+
+def test_mixture_weights_are_match_frequencies_then_forget_at_rate_1_over_N():
+    """Two values that never match each other.  For t <= N the 1/t rate makes
+    each weight 32768 * (its frames so far) / t (error <= (t+1)/4); after that,
+    frames of B only shrink A's weight by the factor (1 - 1/N) per frame (error
+    <= N/2, the rounding geometric sum)."""
+    rng = np.random.default_rng(9)
+    A, B = np.array([[20, 30, 200]], np.uint8), np.array([[220, 120, 40]], np.uint8)
+    N = 64
+    m = _mix(N=N)
+    seq = rng.random(N) < 0.6
+    nA = 0
+    for t, isA in enumerate(seq, start=1):
+        m.step(A if isA else B)
+        nA += int(isA)
+        comp = {tuple(m.M[k, :, 0] // 256): int(m.W[k, 0]) for k in range(3) if m.C[k, 0]}
+        wA, wB = comp.get((20, 30, 200), 0), comp.get((220, 120, 40), 0)
+        assert abs(wA - Fraction(32768 * nA, t)) <= Fraction(t + 1, 4), t
+        assert abs(wB - Fraction(32768 * (t - nA), t)) <= Fraction(t + 1, 4), t
+    w0 = comp[(20, 30, 200)]
+    for s in range(1, 200):
+        m.step(B)
+        wA = {tuple(m.M[k, :, 0] // 256): int(m.W[k, 0]) for k in range(3) if m.C[k, 0]}.get((20, 30, 200), 0)
+        assert abs(wA - w0 * (1 - 1 / N) ** s) <= N / 2, s
+
+
+def test_mixture_match_radius_is_lambda_sigma():
+    """sigma0 = 4, lambda = 5/2: after one frame at x, a value at Euclidean RGB
+    distance 10 (= lambda sigma) matches, and one just beyond does not."""
+    base = np.array([[100, 100, 100]], np.uint8)
+    for off, match in (((10, 0, 0), True), ((11, 0, 0), False), ((0, 6, 8), True),
+                       ((1, 6, 8), False), ((0, 0, -10), True)):
+        m = _mix(s0=4)
+        m.step(base)
+        fg = m.step((base.astype(int) + off).astype(np.uint8))
+        assert int((m.C[:, 0] > 0).sum()) == (1 if match else 2), off
+        assert int(fg[0]) == (0 if match else 1), off
+
+
+def test_mixture_background_share_threshold():
+    """After A on 60 % and B on 40 % of the frames, A is first in fitness order;
+    B is background iff A's share (0.6) is at most T."""
+    A, B = np.array([[20, 30, 200]], np.uint8), np.array([[220, 120, 40]], np.uint8)
+    for T, b_is_fg in ((70, 0), (50, 1)):
+        m = _mix(T=T)
+        for t in range(50):
+            m.step(A if (t % 5) < 3 else B)
+        assert tuple(m.M[0, :, 0] // 256) == (20, 30, 200)
+        assert int(m.step(A)[0]) == 0
+        assert int(m.step(B)[0]) == b_is_fg, T
+
+
+def test_mixture_fitness_order_is_kept():
+    """After every step: non-empty components first, ordered by W / sqrt(V)."""
+    rng = np.random.default_rng(11)
+    for K in (2, 3, 4):
+        m = _mix(npx=256, K=K, N=16, s0=6)
+        for _ in range(40):
+            m.step(rng.integers(0, 256, size=(256, 3), dtype=np.uint8) // 64 * 64)
+            W, V, C = m.W.astype(object), m.V.astype(object), m.C
+            for k in range(K - 1):
+                assert not ((C[k] == 0) & (C[k + 1] > 0)).any()
+                both = (C[k] > 0) & (C[k + 1] > 0)
+                lhs = W[k] * W[k] * V[k + 1]
+                rhs = W[k + 1] * W[k + 1] * V[k]
+                assert all(l >= r for l, r, b in zip(lhs, rhs, both) if b)
+
+
+def test_mixture_k1_rate1_is_frame_differencing():
+    """K = 1, N = 1: the single component is always the previous frame (matched
+    with rate 1 or replaced), with full weight: plain frame differencing."""
+    rng = np.random.default_rng(3)
+    m = _mix(npx=32, K=1, N=1)
+    prev = None
+    for _ in range(10):
+        x = rng.integers(0, 256, size=(32, 3), dtype=np.uint8)
+        fg = m.step(x)
+        if prev is None:
+            assert (fg == 1).all()
+        assert (m.M[0] == 256 * x.T.astype(np.uint16)).all()
+        assert (m.W[0] == 32768).all()
+        prev = x
+
+
+def test_mixture_stream_finds_the_generated_hand_config1():
+    o = oracle.OracleStream(*synth.shape(1), bg_model=1)
+    o.learn(synth.learn_frames(1))
+    assert o.mix.t == synth.learn_frames(1).shape[0]
+    for t in range(0, 60, 7):
+        _, _, p, _ = o.process(synth.run_frame(1, 0, t))
+        (cx, cy, a, b), = synth.truth(1, 0, t)[0]
+        assert p["valid"] == 1
+        assert abs(p["x"] - cx) < 1.0 and abs(p["y"] - cy) < 1.0
+        assert abs(p["area"] - math.pi * a * b) < 0.1 * math.pi * a * b
+
+
+def test_mixture_background_share_boundary_is_inclusive():
+    """A then B: both weights 16384, equal fitness, A first.  With T = 50 %,
+    B's preceding share is exactly T, which still counts as background."""
+    A, B = np.array([[20, 30, 200]], np.uint8), np.array([[220, 120, 40]], np.uint8)
+    m = _mix(T=50)
+    m.step(A)
+    m.step(B)
+    assert m.W[:2, 0].tolist() == [16384, 16384]
+    assert int(m.step(B)[0]) == 0
+    m = _mix(T=49)
+    m.step(A)
+    m.step(B)
+    assert int(m.step(B)[0]) == 1
+
+
+def test_mixture_first_matching_component_in_fitness_order_is_updated():
+    """A = (100,50,50), then B = (150,50,50) (50 levels apart: a new component),
+    both with weight 16384 and V0; x = (125,50,50) is 25 from both, inside
+    lambda sigma0 = 37.5 of each: it updates A, the first in order (its mean
+    moves half way, rate 1/2), and leaves B alone."""
+    m = _mix()
+    for v in ((100, 50, 50), (150, 50, 50), (125, 50, 50)):
+        m.step(np.array([v], np.uint8))
+    assert m.M[0, :, 0].tolist() == [256 * 100 + 3200, 256 * 50, 256 * 50]
+    assert m.M[1, :, 0].tolist() == [256 * 150, 256 * 50, 256 * 50]
+    assert m.C[:2, 0].tolist() == [2, 1]
+
+
+def test_mixture_variance_tracks_the_mean_squared_deviation():
+    """Values alternating a, a + 12 in one channel (all matching one component).
+    With the 1/C rate, V_n = (V0 + sum_{i=2..n} T_i) / n, T_i = 16 (x_i - mean_{i-1})^2 / 3
+    per channel (Q4); computed here with exact rational running means.  The
+    oracle's roundings stay within (n+1)/4 of V plus what its Q8 means move T."""
+    a, d, n = 90, 12, 60
+    m = _mix()
+    xs = [a + d * (i % 2) for i in range(n)]
+    mean, tot = Fraction(xs[0]), Fraction(0)
+    for i, x in enumerate(xs):
+        m.step(np.array([[x, 50, 50]], np.uint8))
+        if i > 0:
+            tot += Fraction(16, 3) * (x - mean) ** 2
+            mean += (x - mean) / (i + 1)
+    exact = (Fraction(3600) + tot) / n
+    assert abs(int(m.V[0, 0]) - exact) <= Fraction(n + 1, 4) + 10
