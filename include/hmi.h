@@ -99,6 +99,37 @@ typedef struct {
      * centroid, if within this many pixels (ties: larger area, then smaller
      * label); else the largest blob. */
     uint16_t track_max_dist;/* [0]      pixels */
+    /* Background model (Sec. 2: the FIZI module learns the background with
+     * advanced machine learning; Sec. 3.3 cites Lee's adaptive Gaussian
+     * mixture learning).  bg_model 0: the learned band above.  bg_model 1:
+     * per pixel, mix_k Gaussian components over the gain-corrected RGB value,
+     * each a weight W (Q15), a mean per channel M (Q8), one variance V
+     * shared by the channels (Q4: level^2 * 16) and a match count C (0:
+     * empty), kept in fitness order.  For frame t (counted from 1 over the
+     * learning frames, which the mixture learns from an empty model, then the
+     * running frames): the value matches the first non-empty component with
+     * bg_k_den^2 * sum (256 c' - M)^2 <= bg_k_num^2 * V * 4096 (lambda =
+     * bg_k_num / bg_k_den standard deviations); on a running frame it is
+     * background iff it matched component j and the weights before j sum to
+     * at most mix_bg_pct percent of all weights (model before the update).
+     * Update (Lee's rates, every division rounded half away from zero): the
+     * matched component's C grows by one and, with r = min(C, mix_rate_n),
+     * M moves by (256 c' - M) / r and V by (D / 3 - V) / r (D the squared
+     * distance in Q4; V clamped to [16 mix_sigma_min^2, 65535]); with no
+     * match the last component becomes (M = 256 c', V = 16 mix_sigma0^2,
+     * C = 1, W = 0); then with m = min(t, mix_rate_n) every W moves by
+     * (32768 [the matched or new one] or 0 [the others] - W) / m; finally
+     * the components are stably re-sorted, non-empty ones first by
+     * W / sqrt(V) (a before b iff W_a^2 V_b > W_b^2 V_a), empty ones last.
+     * Requires relearn_frames 0 and bg_k_num >= 1; the band is still formed
+     * from the learning frames (hmi_get_band) but not used. */
+    uint8_t bg_model;       /* [0]      0: learned band, 1: Gaussian mixture */
+    uint8_t mix_k;          /* [3]      components per pixel, 1..4 */
+    uint8_t mix_bg_pct;     /* [70]     T: background share of the weights, 1..100 */
+    uint8_t mix_sigma0;     /* [15]     standard deviation of a new component, 1..63 */
+    uint8_t mix_sigma_min;  /* [2]      lower bound of a standard deviation, 1..mix_sigma0 */
+    uint8_t mix_pad;        /* [0]      must be 0 */
+    uint16_t mix_rate_n;    /* [256]    N: the learning rate alpha is 1 / N, 1..65535 */
 } hmi_params;
 
 /* The Mouse module's pointer (Sec. 2): position of the hand zone and
@@ -242,10 +273,11 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
 
 /* Kernel timing of a batch's ticks.  A tick runs HMI_TICK_KERNELS kernels in
  * this order: 0 luma sums and gains, 1 background band test (the per-pixel
- * HBM pass), 2 re-learning sums and 3 re-learned bands (launched only when a
- * stream of the batch re-learns; they act on streams inside a window), 4 gray
- * and hue tests of out-of-band pixels, 5 morphology, 6 block components, 7
- * merge and pointer.  hmi_batch_profile(b, max_ticks)
+ * HBM pass), 2 Gaussian mixture test and update (launched only when a stream
+ * of the batch has bg_model 1), 3 re-learning sums and 4 re-learned bands
+ * (launched only when a stream of the batch re-learns; they act on streams
+ * inside a window), 5 gray and hue tests of out-of-band pixels, 6
+ * morphology, 7 block components, 8 merge and pointer.  hmi_batch_profile(b, max_ticks)
  * starts recording CUDA events between the kernels for each of the next
  * max_ticks ticks (0 stops); the plan must have one group
  * (HMI_ERR_INVALID_ARG otherwise), so that every launch is timed alone.
@@ -253,7 +285,7 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
  * and, for the first n_kernels kernels (1..HMI_TICK_KERNELS), the sum of their
  * durations in milliseconds; hmi_batch_profile_read gives that sum for kernel
  * 1 alone. */
-#define HMI_TICK_KERNELS 8
+#define HMI_TICK_KERNELS 9
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
 HMI_API int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels);
 HMI_API int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms);
@@ -315,6 +347,13 @@ HMI_API int hmi_get_event(const hmi_stream *s, hmi_event *out);
  * the band as last re-formed.  HMI_ERR_NOT_LEARNED before learning. */
 HMI_API int hmi_get_band(const hmi_stream *s, uint8_t *lo, uint8_t *hi);
 
+/* The Gaussian mixture of a bg_model 1 stream (the state after the last
+ * frame): out receives 6 * mix_k planes of h*w uint16 each (host or device),
+ * in the order W[k], M[k][c] (k-major, c = R, G, B), V[k], C[k], k in the
+ * stream's fitness order.  HMI_ERR_INVALID_ARG for a band stream,
+ * HMI_ERR_NOT_LEARNED before learning. */
+HMI_API int hmi_get_mixture(const hmi_stream *s, uint16_t *out);
+
 /* Checkpoint of the learned model.  Export copies (each pointer may be NULL;
  * host or device) the per pixel-channel sums S, Q (uint32, h*w*3), min/max
  * and the derived band lo/hi (uint8, h*w*3, packed like the frame), the
@@ -322,7 +361,9 @@ HMI_API int hmi_get_band(const hmi_stream *s, uint8_t *lo, uint8_t *hi);
  * min, max (all required) for n frames with reference luma syref, derives the
  * band with the stream's parameters and resets the click state, exactly as
  * learning from frames with those sums would.  HMI_ERR_NOT_LEARNED on export
- * before any learning. */
+ * before any learning.  A mixture stream (bg_model 1) exports its learning
+ * sums like any stream, but refuses import (HMI_ERR_INVALID_ARG): its
+ * mixture is learned from frames only. */
 HMI_API int hmi_export_background(const hmi_stream *s, uint32_t *S, uint32_t *Q, uint8_t *vmin,
                                   uint8_t *vmax, uint8_t *lo, uint8_t *hi, uint64_t *syref,
                                   int *n);

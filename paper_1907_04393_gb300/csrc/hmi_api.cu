@@ -71,6 +71,12 @@ bool params_valid(const hmi_params &p)
     if (p.relearn_frames > 0 &&
         (p.relearn_min < 1 || p.relearn_min > p.relearn_frames || p.relearn_period < p.relearn_frames))
         return false;
+    if (p.bg_model > 1 || p.mix_pad != 0) return false;
+    if (p.bg_model == 1 &&
+        (p.mix_k < 1 || p.mix_k > 4 || p.mix_bg_pct < 1 || p.mix_bg_pct > 100 || p.mix_sigma0 < 1 ||
+         p.mix_sigma0 > 63 || p.mix_sigma_min < 1 || p.mix_sigma_min > p.mix_sigma0 ||
+         p.mix_rate_n < 1 || p.bg_k_num < 1 || p.relearn_frames != 0))
+        return false;
     return true;
 }
 
@@ -117,6 +123,10 @@ struct Layout {
     // re-learning sums (only with re-learning on): rows of rpitch pixels
     int rpitch;
     size_t rS, rQ, rmin, rmax, rcnt, rpx;
+    // Gaussian mixture planes (bg_model 1 only): 6 mix_k planes of mplane
+    // uint16 entries, rows of rpitch entries
+    int mix_k;
+    size_t mix, mplane;
 };
 
 Layout make_layout(int w, int h, const hmi_params &p)
@@ -162,6 +172,9 @@ Layout make_layout(int w, int h, const hmi_params &p)
         L.rmax = a.take(L.rpx * 3);
         L.rcnt = a.take(L.rpx);
     }
+    L.mix_k = p.bg_model == 1 ? p.mix_k : 0;
+    L.mplane = (size_t)h * L.rpitch;
+    L.mix = L.mix_k ? a.take(L.mplane * 6 * L.mix_k * 2) : 0;
     L.total = a.off;
     return L;
 }
@@ -358,6 +371,17 @@ void fill_devstream(hmi_stream *s)
     D.rmin = L.rpx ? a + L.rmin : nullptr;
     D.rmax = L.rpx ? a + L.rmax : nullptr;
     D.rcnt = L.rpx ? a + L.rcnt : nullptr;
+    MixView &M = D.mix;
+    M.K = L.mix_k;
+    M.planes = L.mix_k ? reinterpret_cast<uint16_t *>(a + L.mix) : nullptr;
+    M.plane = L.mplane;
+    M.pitch = L.rpitch;
+    M.rate_n = s->p.mix_rate_n;
+    M.bg_pct = s->p.mix_bg_pct;
+    M.lam_a = (uint32_t)s->p.bg_k_den * s->p.bg_k_den;
+    M.lam_b = (uint32_t)s->p.bg_k_num * s->p.bg_k_num * 4096u;
+    M.v_init = 16u * s->p.mix_sigma0 * s->p.mix_sigma0;
+    M.v_min = 16u * s->p.mix_sigma_min * s->p.mix_sigma_min;
 }
 
 void plan_free_graphs(hmi_batch *b)
@@ -570,9 +594,13 @@ int plan_build(hmi_batch *b, int ng)
         bd.skin_count = G.skin_count_p[0];
         bd.skin_list = G.skin_list_p[0];
         bd.phase = 0;
-        bd.relearn = 0;
-        for (int k = 0; k < m; ++k)
-            if (b->s[perm[G.off + k]]->L.rpx) bd.relearn = 1;
+        bd.relearn = bd.any_band = bd.any_mix = 0;
+        for (int k = 0; k < m; ++k) {
+            const hmi_stream *sk = b->s[perm[G.off + k]];
+            if (sk->L.rpx) bd.relearn = 1;
+            if (sk->L.mix_k) bd.any_mix |= 1 << sk->L.mix_k;
+            else bd.any_band = 1;
+        }
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
         bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
         bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
@@ -740,13 +768,13 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
 }
 
 // Stages of a pipelined tick: the first kernel of each of its `depth` stages,
-// then kTickKernels.  Depth 2: {luma, band test, re-learning} {gray/hue,
-// morphology, blocks, finish}; depth 3: {luma} {band test, re-learning}
-// {gray/hue .. finish}.  The first stages are bandwidth-bound, the last is
+// then kTickKernels.  Depth 2: {luma, band test, mixture, re-learning}
+// {gray/hue, morphology, blocks, finish}; depth 3: {luma} {band test, mixture,
+// re-learning} {gray/hue .. finish}.  The first stages are bandwidth-bound, the last is
 // latency-bound; the band is only read and re-formed in the middle stage.
 void stage_bounds(int depth, int *first)
 {
-    constexpr int kTail = 4;   // first kernel of the latency-bound tail (gray/hue tests)
+    constexpr int kTail = kTickTail;   // first kernel of the latency-bound tail (gray/hue tests)
     if (depth >= 3) {
         first[0] = 0;
         first[1] = 1;
@@ -1128,11 +1156,23 @@ int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool p
     int st = flush_pending(b, b->cs);
     if (st != HMI_OK) return st;
     HMI_CUDA(cudaDeviceSynchronize());
-    // the streams' click state and pointer history, put back afterwards
+    // the streams' click state, pointer history and adaptive background
+    // (band, re-learning sums, mixture), put back afterwards
     std::vector<std::pair<void *, size_t>> keep;
     for (hmi_stream *s : b->s) {
+        const Layout &L = s->L;
         keep.emplace_back(s->st, sizeof(StreamState));
         keep.emplace_back(s->ds.hist, sizeof(uint32_t) * std::max<int>(s->p.click_window, 1));
+        keep.emplace_back(s->arena + L.lo, (size_t)L.h * L.fpitch);
+        keep.emplace_back(s->arena + L.hi, (size_t)L.h * L.fpitch);
+        if (L.rpx) {
+            keep.emplace_back(s->arena + L.rS, L.rpx * 3 * 2);
+            keep.emplace_back(s->arena + L.rQ, L.rpx * 3 * 4);
+            keep.emplace_back(s->arena + L.rmin, L.rpx * 3);
+            keep.emplace_back(s->arena + L.rmax, L.rpx * 3);
+            keep.emplace_back(s->arena + L.rcnt, L.rpx);
+        }
+        if (L.mix_k) keep.emplace_back(s->arena + L.mix, L.mplane * 6 * L.mix_k * 2);
     }
     size_t total = 0;
     for (auto &k : keep) total += k.second;
@@ -1323,6 +1363,14 @@ int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
     b->tune.groups = ngroups;
     HMI_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), b->cs));
     return plan_build(b, ngroups);
+}
+
+// An empty Gaussian mixture (every plane zero: no component), before its
+// learning frames.
+cudaError_t enqueue_mix_reset(hmi_stream *s, cudaStream_t cs)
+{
+    if (!s->L.mix_k) return cudaSuccess;
+    return cudaMemsetAsync(s->arena + s->L.mix, 0, s->L.mplane * 6 * s->L.mix_k * 2, cs);
 }
 
 // Band of a stream from its learned sums after n frames (Sec. 3.1 (i)), in
@@ -1614,6 +1662,11 @@ bool server_round(hmi_server *v)
         if (e == cudaSuccess)
             e = launch_learn_accum(s->d_frame, 1, (long long)s->w * s->h, s->d_S, s->d_Q, s->d_vmin,
                                    s->d_vmax, ss->learn_done == 0, s->st, v->cs);
+        if (e == cudaSuccess && s->L.mix_k) {   // the mixture learns the same frame
+            if (ss->learn_done == 0) e = enqueue_mix_reset(s, v->cs);
+            if (e == cudaSuccess)
+                e = launch_mix_learn(s->d_frame, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
+        }
         if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
         if (e != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1953,6 +2006,11 @@ int hmi_default_params(hmi_params *p)
     p->close_iters = 1;
     p->click_on_pct = 80;
     p->click_off_pct = 90;
+    p->mix_k = 3;
+    p->mix_bg_pct = 70;
+    p->mix_sigma0 = 15;
+    p->mix_sigma_min = 2;
+    p->mix_rate_n = 256;
     return HMI_OK;
 }
 
@@ -1996,8 +2054,10 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
     if (s->used) HMI_CUDA(cudaDeviceSynchronize());   // no tick of this stream may be in flight
     // reset the learning luma total
     HMI_CUDA(cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), s->cs));
+    HMI_CUDA(enqueue_mix_reset(s, s->cs));
     if (is_device_ptr(frames)) {
         HMI_CUDA(launch_learn_accum(frames, n, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, 1, s->st, s->cs));
+        if (s->L.mix_k) HMI_CUDA(launch_mix_learn(frames, n, 0u, s->w, s->h, s->ds.mix, s->cs));
     } else {
         // host frames: stream through a bounded staging buffer
         const int per = (int)std::max<size_t>(1, std::min<size_t>((size_t)n, (256u << 20) / fbytes));
@@ -2011,6 +2071,7 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
             const int k = std::min(per, n - i);
             if (cudaMemcpyAsync(stage, frames + (size_t)i * fbytes, fbytes * k, cudaMemcpyHostToDevice, s->cs) != cudaSuccess ||
                 launch_learn_accum(stage, k, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, i == 0, s->st, s->cs) != cudaSuccess ||
+                (s->L.mix_k && launch_mix_learn(stage, k, (uint32_t)i, s->w, s->h, s->ds.mix, s->cs) != cudaSuccess) ||
                 cudaStreamSynchronize(s->cs) != cudaSuccess)
                 status = cuda_fail(cudaErrorUnknown);
         }
@@ -2232,6 +2293,20 @@ int hmi_get_band(const hmi_stream *s, uint8_t *lo, uint8_t *hi)
     return HMI_OK;
 }
 
+int hmi_get_mixture(const hmi_stream *s, uint16_t *out)
+{
+    if (!s || !out || !s->L.mix_k) return fail(HMI_ERR_INVALID_ARG);
+    if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
+    HMI_CUDA(cudaSetDevice(s->dev));
+    HMI_CUDA(cudaDeviceSynchronize());   // the last tick may have run on any stream
+    const size_t row = 2 * (size_t)s->w, plane = (size_t)s->w * s->h;
+    const uint16_t *src = reinterpret_cast<const uint16_t *>(s->arena + s->L.mix);
+    for (int p = 0; p < 6 * s->L.mix_k; ++p)
+        HMI_CUDA(cudaMemcpy2D(out + p * plane, row, src + p * s->L.mplane, 2 * (size_t)s->L.rpitch, row,
+                              s->h, cudaMemcpyDefault));
+    return HMI_OK;
+}
+
 int hmi_export_background(const hmi_stream *s, uint32_t *S, uint32_t *Q, uint8_t *vmin,
                           uint8_t *vmax, uint8_t *lo, uint8_t *hi, uint64_t *syref, int *n)
 {
@@ -2256,6 +2331,7 @@ int hmi_import_background(hmi_stream *s, const uint32_t *S, const uint32_t *Q, c
 {
     if (!s || !S || !Q || !vmin || !vmax || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
     if (syref > (uint64_t)255 * s->w * s->h) return fail(HMI_ERR_INVALID_ARG);
+    if (s->L.mix_k) return fail(HMI_ERR_INVALID_ARG);   // a mixture is learned from frames only
     HMI_CUDA(cudaSetDevice(s->dev));
     HMI_CUDA(cudaDeviceSynchronize());
     const size_t cnt = (size_t)s->w * s->h * 3;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         const int4 piece = b.pieces[pc];
         const DevStream &D = b.ds[piece.x];
         const TickIO io = b.io[piece.x];
-        if (io.frame == nullptr) continue;   // no frame for this stream this tick
+        if (io.frame == nullptr || D.mix.K != 0) continue;   // no frame this tick, or a mixture stream
         const uint32_t g = D.st->gain_p[b.phase];
         const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
         const uint8_t *lo = D.lo, *hi = D.hi;
@@ -837,6 +837,7 @@ cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     (void)num_sms;
+    if (!b.any_band) return cudaSuccess;
     k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
@@ -892,11 +893,12 @@ cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int nu
     switch (k) {
     case 0: return launch_luma(b, cs, num_sms);
     case 1: return launch_classify(b, cs, num_sms);
-    case 2: return launch_relearn(b, cs, num_sms);
-    case 3: return launch_relearn_band(b, cs, num_sms);
-    case 4: return launch_skin(b, cs, num_sms);
-    case 5: return launch_morph(b, cs, num_sms);
-    case 6: return launch_block_cc(b, cs, num_sms);
+    case 2: return launch_mix(b, cs, num_sms);
+    case 3: return launch_relearn(b, cs, num_sms);
+    case 4: return launch_relearn_band(b, cs, num_sms);
+    case 5: return launch_skin(b, cs, num_sms);
+    case 6: return launch_morph(b, cs, num_sms);
+    case 7: return launch_block_cc(b, cs, num_sms);
     default: return launch_finish(b, cs);
     }
 }

@@ -58,8 +58,21 @@ struct __align__(16) StreamState {
     uint32_t lframes;             // frames whose gain was computed since learning
     uint32_t lframe_p[3];         // the number of the frame of each tick phase (kPhases)
     int32_t track_valid, track_x, track_y;   // tracked point: last valid pointer's rounded centroid
+    uint32_t nlearn;              // learning frames of the background (set when the band is formed)
     hmi_event event;              // the Interface module's event of the last frame
     hmi_pointer last;             // pointer of the last frame
+};
+
+// Gaussian mixture background of a stream (bg_model 1): 6 K planes of uint16,
+// W[k] (Q15), M[k][c] (Q8), V[k] (Q4), C[k], each h rows of `pitch` entries.
+struct MixView {
+    uint16_t *planes;
+    size_t plane;                 // entries per plane (h * pitch)
+    int K;                        // components per pixel; 0: a band stream
+    int pitch;                    // entries per plane row (a multiple of 16)
+    int rate_n, bg_pct;           // N (rates 1/min(., N)) and T in percent
+    uint32_t lam_a, lam_b;        // match iff lam_a * d2 <= lam_b * V (kd^2, kn^2 * 4096)
+    uint32_t v_init, v_min;       // 16 sigma0^2 and 16 sigma_min^2
 };
 
 // Read-only description of a stream as the kernels see it.
@@ -85,6 +98,7 @@ struct DevStream {
     int bg_kn, bg_kd, bg_delta;   // band parameters (k = kn / kd, margin delta)
     int track_max_dist;           // 0: the hand is the largest blob; else tracked
     const hmi_interface *ui;      // zones and wheel (all zero: none)
+    MixView mix;                  // Gaussian mixture (mix.K 0: the band test)
     uint16_t *rS;                 // sum of corrected values, per pixel-channel
     uint32_t *rQ;                 // sum of their squares
     uint8_t *rmin, *rmax;         // their min and max
@@ -144,6 +158,8 @@ struct BatchDev {
                                               // kPhases consecutive ticks can be in flight
     // launch shape (host side; chosen by the plan's tuning)
     int relearn;                              // some stream of the batch re-learns
+    int any_band;                             // some stream has the band test
+    int any_mix;                              // bit K: some stream has a K-component mixture
     int luma_ctas_per_sm;                     // 0: as many as fit
     int skin_ctas_per_sm;
     int cc_ctas_per_sm;
@@ -160,17 +176,24 @@ constexpr int kThreads = 256;
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------
 // The kernels of one tick, in order: 0 luma (and gains), 1 classify (band
-// test), 2 re-learning sums and 3 re-learned bands (no launch unless a stream
-// of the batch re-learns), 4 skin (gray and hue tests), 5 morphology, 6 block
+// test), 2 mixture test and update (no launch without mixture streams), 3
+// re-learning sums and 4 re-learned bands (no launch unless a stream of the
+// batch re-learns), 5 skin (gray and hue tests), 6 morphology, 7 block
 // components (none on the generic morphology path, which labels its blocks
-// itself), 7 finish.
-constexpr int kTickKernels = 8;
+// itself), 8 finish.
+constexpr int kTickKernels = 9;
+constexpr int kTickTail = 5;       // first kernel of the latency-bound tail (skin)
 static_assert(kTickKernels == HMI_TICK_KERNELS, "tick kernel count");
 cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_relearn(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_relearn_band(const BatchDev &b, cudaStream_t cs, int num_sms);
+cudaError_t launch_mix(const BatchDev &b, cudaStream_t cs, int num_sms);
+// The mixture update of nf dense learning frames (h*w*3 bytes each), frame i
+// being frame number t0 + i + 1 of the stream.
+cudaError_t launch_mix_learn(const uint8_t *frames, int nf, uint32_t t0, int w, int h,
+                             const MixView &mix, cudaStream_t cs);
 
 // Frame f (counted from 1 after learning) is in a re-learning window iff
 // (f - 1) mod period >= period - frames; the window ends with f mod period == 0.

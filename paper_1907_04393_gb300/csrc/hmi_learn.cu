@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(kThreads) k_learn_band(const uint32_t *S, cons
         st->frames = 0;
         st->lframes = 0;
         st->track_valid = 0;
+        st->nlearn = (uint32_t)n;
         st->err = 0;
     }
     const long long count = (long long)w * h * 3;

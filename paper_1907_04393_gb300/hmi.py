@@ -23,7 +23,7 @@ HMI_ERR_NO_MEMORY = -3
 HMI_ERR_DEVICE = -4
 HMI_ERR_DEVICE_TIMEOUT = -5
 HMI_LEARNING = 1          # server results only: a background-learning frame
-HMI_TICK_KERNELS = 8
+HMI_TICK_KERNELS = 9
 
 
 class hmi_params(ctypes.Structure):
@@ -35,7 +35,11 @@ class hmi_params(ctypes.Structure):
                 ("open_iters", ctypes.c_uint8), ("close_iters", ctypes.c_uint8),
                 ("click_on_pct", ctypes.c_uint8), ("click_off_pct", ctypes.c_uint8),
                 ("relearn_frames", ctypes.c_uint8), ("relearn_min", ctypes.c_uint8),
-                ("relearn_period", ctypes.c_uint16), ("track_max_dist", ctypes.c_uint16)]
+                ("relearn_period", ctypes.c_uint16), ("track_max_dist", ctypes.c_uint16),
+                ("bg_model", ctypes.c_uint8), ("mix_k", ctypes.c_uint8),
+                ("mix_bg_pct", ctypes.c_uint8), ("mix_sigma0", ctypes.c_uint8),
+                ("mix_sigma_min", ctypes.c_uint8), ("mix_pad", ctypes.c_uint8),
+                ("mix_rate_n", ctypes.c_uint16)]
 
 
 class hmi_pointer(ctypes.Structure):
@@ -127,6 +131,7 @@ SIGNATURES = {
     "hmi_get_background_stats": (_I, [_P, _P, _P]),
     "hmi_get_labels": (_I, [_P, _P]),
     "hmi_get_band": (_I, [_P, _P, _P]),
+    "hmi_get_mixture": (_I, [_P, _P]),
     "hmi_set_interface": (_I, [_P, ctypes.POINTER(hmi_interface)]),
     "hmi_get_event": (_I, [_P, ctypes.POINTER(hmi_event)]),
     "hmi_export_background": (_I, [_P, _P, _P, _P, _P, _P, _P,
@@ -330,7 +335,7 @@ def hmi_batch_profile(b: int, max_ticks: int) -> None:
     _check(load().hmi_batch_profile(b, max_ticks), "hmi_batch_profile")
 
 
-TICK_KERNELS = ("luma", "classify", "relearn", "relearn_band", "skin", "morphology",
+TICK_KERNELS = ("luma", "classify", "mixture", "relearn", "relearn_band", "skin", "morphology",
                 "block_components", "finish")
 
 
@@ -381,6 +386,10 @@ def hmi_get_event(s: int) -> dict:
 
 def hmi_get_band(s: int, lo, hi) -> None:
     _check(load().hmi_get_band(s, _addr(lo), _addr(hi)), "hmi_get_band")
+
+
+def hmi_get_mixture(s: int, out) -> None:
+    _check(load().hmi_get_mixture(s, _addr(out)), "hmi_get_mixture")
 
 
 def hmi_export_background(s: int, S=None, Q=None, vmin=None, vmax=None, lo=None, hi=None):
@@ -534,6 +543,14 @@ class Stream:
         hi = np.empty((self.h, self.w, 3), np.uint8)
         hmi_get_band(self.handle, lo, hi)
         return lo, hi
+
+    def mixture(self) -> np.ndarray:
+        """The Gaussian mixture (bg_model 1) as (6 mix_k, h*w) uint16 planes:
+        W[k], M[k][c], V[k], C[k]."""
+        k = self.params.mix_k
+        out = np.empty((6 * k, self.h * self.w), np.uint16)
+        hmi_get_mixture(self.handle, out)
+        return out
 
     def stats(self):
         mean = np.empty((self.h, self.w, 3), np.float32)

@@ -26,7 +26,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts():
-    assert ctypes.sizeof(hmi.hmi_params) == 32
+    assert ctypes.sizeof(hmi.hmi_params) == 40
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 56
@@ -72,6 +72,19 @@ def test_device_bytes_accounting():
         assert hmi.hmi_stream_device_bytes(32, 32, hmi.hmi_default_params(**over)) == 0, over
     rl = hmi.hmi_default_params(relearn_frames=5, relearn_min=3, relearn_period=10)
     assert hmi.hmi_stream_device_bytes(320, 240, rl) >= b320 + 320 * 240 * 25
+    # the Gaussian mixture: valid parameters only, 12 bytes per pixel and component
+    for over in (dict(bg_model=2), dict(bg_model=1, mix_k=0), dict(bg_model=1, mix_k=5),
+                 dict(bg_model=1, mix_bg_pct=0), dict(bg_model=1, mix_bg_pct=101),
+                 dict(bg_model=1, mix_sigma0=0), dict(bg_model=1, mix_sigma0=64),
+                 dict(bg_model=1, mix_sigma_min=0), dict(bg_model=1, mix_sigma_min=16),
+                 dict(bg_model=1, mix_rate_n=0), dict(bg_model=1, bg_k_num=0),
+                 dict(bg_model=1, relearn_frames=5, relearn_min=3, relearn_period=10),
+                 dict(mix_pad=1)):
+        assert hmi.hmi_stream_device_bytes(32, 32, hmi.hmi_default_params(**over)) == 0, over
+    for k in (1, 2, 3, 4):
+        mx = hmi.hmi_default_params(bg_model=1, mix_k=k)
+        assert hmi.hmi_stream_device_bytes(320, 240, mx) >= b320 + 320 * 240 * 12 * k
+    assert hmi.hmi_stream_device_bytes(32, 32, hmi.hmi_default_params(bg_model=0, mix_k=0)) > 0
 
 
 def test_invalid_arguments_fail_on_host():

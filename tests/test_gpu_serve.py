@@ -97,24 +97,27 @@ def test_trace_replay_small():
     assert pl["errors"] == 0 and pl["frames"] > 0
 
 
-def test_online_learning_equals_learned_up_front():
+@pytest.mark.parametrize("over", [{}, dict(bg_model=1, mix_k=3)])
+def test_online_learning_equals_learned_up_front(over):
     """Streams admitted without learning frames take their first n submitted
     frames as the user-free learning frames (status HMI_LEARNING, empty
     pointer) while another stream is processed in the same ticks; their later
-    results equal those of streams learned from the same frames up front."""
+    results equal those of streams learned from the same frames up front
+    (with the band, and with the Gaussian mixture learned frame by frame)."""
     srcs = [3, 70, 150, 250]
     n_learn, nframes = 6, 5
     learn = {s: synth.learn_frames(5, s, n_learn) for s in srcs}
     frames = {s: [synth.run_frame(5, s, t) for t in range(nframes)] for s in srcs}
     alone = {}
     for s in srcs:
-        st = hmi.Stream(*synth.shape(5, s))
+        st = hmi.Stream(*synth.shape(5, s), **over)
         st.learn(learn[s])
         alone[s] = [st.process(f, mask=False)[1] for f in frames[s]]
         st.close()
     srv = hmi.hmi_server_create(1 << 34, 16)
     busy = srcs[0]            # learned up front, busy while the others learn
-    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), None,
+    prm = hmi.hmi_default_params(**over)
+    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), prm,
                                    learn[s] if s == busy else None, n_learn) for s in srcs}
     seq = {s: ([] if s == busy else list(learn[s])) + frames[s] for s in srcs}
     tag_of, tag = {}, 0
