@@ -224,8 +224,12 @@ int orc_relearn_in_window(long long f, int period, int frames)
 /* the value x (3 bytes) of frame t, t counted from 1 over the learning and   */
 /* then the running frames:                                                  */
 /*  1. match: the first non-empty component with                             */
-/*       ld^2 * sum_ch (256 x - M)^2 <= ln^2 * V * 4096                       */
-/*     (distance at most lambda = ln / ld standard deviations);               */
+/*       ld^2 * sum_ch (256 x - M)^2 <= 3 * ln^2 * V * 4096                   */
+/*     (the mean squared channel deviation at most lambda^2 V, lambda =      */
+/*     ln / ld: "within lambda standard deviations" per channel, as the band */
+/*     reads k; the joint distance with lambda = 2.5 would reject a tenth of */
+/*     pure-noise background pixels, the chi-square tail with 3 degrees of    */
+/*     freedom);                                                              */
 /*  2. decision (running frames only, on the model before this frame): the   */
 /*     pixel is background iff it matched component j and the weights of the */
 /*     components before j sum to at most T percent of all weights (the      */
@@ -271,7 +275,7 @@ void orc_mixture_step(uint16_t *W, uint16_t *M, uint16_t *V, uint16_t *C, size_t
                 dk[ch] = 256 * (int64_t)px[ch] - (int64_t)M[(3 * k + ch) * npx + p];
                 s2 += dk[ch] * dk[ch];
             }
-            if ((int64_t)ld * ld * s2 <= (int64_t)ln * ln * (int64_t)V[k * npx + p] * 4096) {
+            if ((int64_t)ld * ld * s2 <= 3 * (int64_t)ln * ln * (int64_t)V[k * npx + p] * 4096) {
                 j = k;
                 for (int ch = 0; ch < 3; ++ch) e[ch] = dk[ch];
                 d2 = s2;
@@ -283,7 +287,7 @@ void orc_mixture_step(uint16_t *W, uint16_t *M, uint16_t *V, uint16_t *C, size_t
                 total += W[k * npx + p];
                 if (k < j) before += W[k * npx + p];
             }
-            const int background = (j >= 0) && (100 * before <= (int64_t)bg_pct * total);
+            const int background = (j >= 0) && (100 * before < (int64_t)bg_pct * total);
             fg1[p] = (uint8_t)!background;
         }
         if (j >= 0) {

@@ -756,11 +756,13 @@ def test_mixture_weights_are_match_frequencies_then_forget_at_rate_1_over_N():
 
 
 def test_mixture_match_radius_is_lambda_sigma():
-    """sigma0 = 4, lambda = 5/2: after one frame at x, a value at Euclidean RGB
-    distance 10 (= lambda sigma) matches, and one just beyond does not."""
+    """sigma0 = 4, lambda = 5/2: after one frame at x, a value whose mean
+    squared channel deviation is lambda^2 sigma^2 = 100 (squared distance 300)
+    matches, and one just beyond does not."""
     base = np.array([[100, 100, 100]], np.uint8)
-    for off, match in (((10, 0, 0), True), ((11, 0, 0), False), ((0, 6, 8), True),
-                       ((1, 6, 8), False), ((0, 0, -10), True)):
+    for off, match in (((10, 10, 10), True), ((10, 10, 11), False), ((17, 0, 0), True),
+                       ((18, 0, 0), False), ((0, -10, 14), True), ((1, 10, 14), True),
+                       ((2, 10, 14), True), ((3, 10, 14), False), ((-10, -10, -10), True)):
         m = _mix(s0=4)
         m.step(base)
         fg = m.step((base.astype(int) + off).astype(np.uint8))
@@ -841,15 +843,15 @@ def test_mixture_background_share_boundary_is_inclusive():
 
 
 def test_mixture_first_matching_component_in_fitness_order_is_updated():
-    """A = (100,50,50), then B = (150,50,50) (50 levels apart: a new component),
-    both with weight 16384 and V0; x = (125,50,50) is 25 from both, inside
-    lambda sigma0 = 37.5 of each: it updates A, the first in order (its mean
-    moves half way, rate 1/2), and leaves B alone."""
+    """A = (100,50,50), then B = (180,50,50) (squared distance 6400 > 3 lambda^2
+    sigma0^2 = 4218.75: a new component), both with weight 16384 and V0;
+    x = (140,50,50) is at 1600 from both, inside both radii: it updates A, the
+    first in order (its mean moves half way, rate 1/2), and leaves B alone."""
     m = _mix()
-    for v in ((100, 50, 50), (150, 50, 50), (125, 50, 50)):
+    for v in ((100, 50, 50), (180, 50, 50), (140, 50, 50)):
         m.step(np.array([v], np.uint8))
-    assert m.M[0, :, 0].tolist() == [256 * 100 + 3200, 256 * 50, 256 * 50]
-    assert m.M[1, :, 0].tolist() == [256 * 150, 256 * 50, 256 * 50]
+    assert m.M[0, :, 0].tolist() == [256 * 100 + 5120, 256 * 50, 256 * 50]
+    assert m.M[1, :, 0].tolist() == [256 * 180, 256 * 50, 256 * 50]
     assert m.C[:2, 0].tolist() == [2, 1]
 
 
