@@ -287,7 +287,7 @@ void orc_mixture_step(uint16_t *W, uint16_t *M, uint16_t *V, uint16_t *C, size_t
                 total += W[k * npx + p];
                 if (k < j) before += W[k * npx + p];
             }
-            const int background = (j >= 0) && (100 * before < (int64_t)bg_pct * total);
+            const int background = (j >= 0) && (100 * before <= (int64_t)bg_pct * total);
             fg1[p] = (uint8_t)!background;
         }
         if (j >= 0) {
