@@ -37,8 +37,21 @@ WORKLOAD = ("64-stream batch: 32x320x240 + 16x640x480 + 12x1280x720 + 4x1920x108
 # algorithmic bytes per pixel of the classification (background test) kernel:
 # frame 3 B + band lo/hi 6 B read, 1 bit written
 CLASSIFY_BYTES_PER_PX = 3 + 6 + 1 / 8
-KERNELS_PER_TICK = 6          # per stream group: luma, classify, skin, morphology, blocks, finish
-PROFILE_FILE = os.path.join(ROOT, "profiles", "k_classify_64stream.txt")
+KERNELS_PER_TICK = 6          # per stream group: luma, classify or mixture, skin, morphology, blocks, finish
+# the Gaussian mixture background with its default 3 components: frame 3 B,
+# 12 B of state per component read and written, 1 bit written
+MIX_BENCH = dict(bg_model=1, mix_k=3)
+MIX_BYTES_PER_PX = 3 + 2 * 12 * MIX_BENCH["mix_k"] + 1 / 8
+# per background model: the per-pixel kernel, its algorithmic bytes per pixel,
+# its committed ncu summary and the sources its hash covers
+BG_MODELS = {
+    "band": dict(params={}, kernel="classify", bytes_per_px=CLASSIFY_BYTES_PER_PX,
+                 profile=os.path.join(ROOT, "profiles", "k_classify_64stream.txt"),
+                 sources=("hmi_frame.cu", "hmi_internal.cuh")),
+    "mixture": dict(params=MIX_BENCH, kernel="mixture", bytes_per_px=MIX_BYTES_PER_PX,
+                    profile=os.path.join(ROOT, "profiles", "k_mix_64stream.txt"),
+                    sources=("hmi_mix.cu", "hmi_internal.cuh")),
+}
 
 
 # --------------------------------------------------------------------------- #
@@ -53,11 +66,11 @@ def peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    """Hash of the per-pixel kernels' code (comments and blank lines left out,
+def kernel_source_hash(sources=BG_MODELS["band"]["sources"]) -> str:
+    """Hash of a per-pixel kernel's code (comments and blank lines left out,
     so that a comment edit does not orphan the committed counters)."""
     h = hashlib.sha256()
-    for f in ("hmi_frame.cu", "hmi_internal.cuh"):
+    for f in sources:
         with open(os.path.join(ROOT, "paper_1907_04393_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].rstrip()
@@ -66,17 +79,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_per_px():
-    """DRAM bytes per pixel of k_classify from the committed ncu summary, if it
-    was taken on the current kernel source."""
+def profiled_traffic_per_px(model: str = "band"):
+    """DRAM bytes per pixel of the model's per-pixel kernel from the committed
+    ncu summary, if it was taken on the current kernel source."""
+    m = BG_MODELS[model]
     try:
         kv = {}
-        with open(PROFILE_FILE) as f:
+        with open(m["profile"]) as f:
             for line in f:
                 if "=" in line and not line.startswith("#"):
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("source_hash") != kernel_source_hash():
+        if kv.get("source_hash") != kernel_source_hash(m["sources"]):
             return None
         return float(kv["dram_bytes_per_px"])
     except Exception:
@@ -307,7 +321,7 @@ def run_ours(args) -> None:
     px_per_tick = 0
     for i in range(n):
         w, h = synth.shape(CFG, i)
-        st = hmi.Stream(w, h)
+        st = hmi.Stream(w, h, **BG_MODELS[args.bg_model]["params"])
         st.learn(torch.from_numpy(synth.learn_frames(CFG, i)).to(dev))
         streams.append(st)
         rings.append([torch.from_numpy(synth.run_frame(CFG, i, t)).to(dev) for t in range(RING)])
@@ -409,7 +423,8 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     one_chain_ms = r0.elapsed_time(r1) / roof_steps
     prof_ticks, per_kernel = hmi.hmi_batch_profile_kernels(batch)
-    prof_ms = per_kernel["classify"]
+    model = BG_MODELS[args.bg_model]
+    prof_ms = per_kernel[model["kernel"]]
     hmi.hmi_batch_profile(batch, 0)
     hmi.hmi_batch_set_groups(batch, plain_groups)
 
@@ -433,8 +448,16 @@ def run_ours(args) -> None:
     relearn = None
     if not args.no_relearn:
         relearn = bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape_used, args)
-        if args.relearn_eval:
-            relearn["quality"] = bench_relearn_quality(hmi, synth, torch, dev, args.relearn_eval)
+
+    # ---- the Gaussian mixture background on every stream ------------------
+    mixture = None
+    if not args.no_mixture and args.bg_model == "band":
+        mixture = bench_mixture_cost(hmi, synth, torch, dev, cs, rings, shape_used, args)
+
+    # ---- background quality under drift: band, re-learning, mixture -------
+    quality = None
+    if args.quality_frames:
+        quality = bench_background_quality(hmi, synth, torch, dev, args.quality_frames)
 
     # ---- single 640x480 stream (the other configuration of the metric) ---
     single = None
@@ -460,8 +483,8 @@ def run_ours(args) -> None:
     peak, peak_kind = peaks()
     value = whole_job_rate(n * args.steps, world, ms)
     classify_ms = prof_ms / max(prof_ticks, 1)
-    achieved = CLASSIFY_BYTES_PER_PX * px_per_tick / (classify_ms / 1e3) / 1e9
-    traffic_px = profiled_traffic_per_px()
+    achieved = model["bytes_per_px"] * px_per_tick / (classify_ms / 1e3) / 1e9
+    traffic_px = profiled_traffic_per_px(args.bg_model)
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -483,13 +506,14 @@ def run_ours(args) -> None:
                         "groups": plain_groups, "steps": plain_steps,
                         "launch": "hmi_batch_process_async, one CUDA graph per tick"},
         "mpx_per_s": px_per_tick * args.steps * world / (ms / 1e3) / 1e6,
-        "roofline": {"bound": "hbm", "kernel": "k_classify", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "k_" + ("classify" if args.bg_model == "band" else "mix<3>"),
+                     "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic_px * px_per_tick) if traffic_px else None,
-                     "algorithmic_bytes_per_launch": CLASSIFY_BYTES_PER_PX * px_per_tick,
+                     "algorithmic_bytes_per_launch": model["bytes_per_px"] * px_per_tick,
                      "launch_ms": classify_ms, "launches_timed": prof_ticks,
                      "timed_in": "single-chain pass of the same workload, CUDA events around the "
-                                 "classify kernel alone (no other kernel overlaps it)",
+                                 f"{model['kernel']} kernel alone (no other kernel overlaps it)",
                      "single_chain_ms_per_step": one_chain_ms,
                      "single_chain_kernels_us": {k: v / max(prof_ticks, 1) * 1e3 for k, v in per_kernel.items()}},
         "e2e": {"value": n * e2e_steps * world / e2e_s, "unit": "frames/s",
@@ -500,8 +524,14 @@ def run_ours(args) -> None:
     }
     if single is not None:
         line["single_640x480"] = single
+    if args.bg_model != "band":
+        line["config"]["background"] = dict(MIX_BENCH)
     if relearn is not None:
         line["adaptive"] = relearn
+    if mixture is not None:
+        line["mixture"] = mixture
+    if quality is not None:
+        line["background_quality"] = quality
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:
@@ -573,29 +603,109 @@ def bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
             "band_reform_ms_per_window_end": per["relearn_band"]}
 
 
-def bench_relearn_quality(hmi, synth, torch, dev, frames: int) -> dict:
+def bench_mixture_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
+    """The 64-stream batch with the Gaussian mixture background (3 components)
+    on every stream: pipelined ticks with the main run's launch shape, then
+    plain ticks timed kernel by kernel, the mixture kernel against HBM."""
+    n = len(rings)
+    streams, px = [], 0
+    for i in range(n):
+        w, h = synth.shape(CFG, i)
+        st = hmi.Stream(w, h, **MIX_BENCH)
+        st.learn(torch.from_numpy(synth.learn_frames(CFG, i)).to(dev))
+        streams.append(st)
+        px += w * h
+    b = hmi.hmi_batch_create([s.handle for s in streams])
+    hmi.hmi_batch_set_tuning(b, dict(shape, groups=1))
+    masks = [torch.empty((s.h, s.w), dtype=torch.uint8, device=dev) for s in streams]
+    ptrs = torch.zeros(n * 40, dtype=torch.uint8, device=dev)
+    steps = max(50, min(args.steps, 1000))
+
+    def run(k0, count, pipelined):
+        for k in range(k0, k0 + count):
+            fr = [rings[i][k % RING] for i in range(n)]
+            if pipelined:
+                hmi.hmi_batch_process_pipelined(b, fr, masks, ptrs.data_ptr(), cs.cuda_stream, True)
+            else:
+                hmi.hmi_batch_process_async(b, fr, masks, ptrs.data_ptr(), cs.cuda_stream, True)
+        if pipelined:
+            hmi.hmi_batch_flush(b, cs.cuda_stream)
+
+    run(0, max(args.warmup, 3), True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cs)
+    run(0, steps, True)
+    e1.record(cs)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = max(10, min(steps, 300))
+    hmi.hmi_batch_profile(b, prof)
+    run(0, prof, False)
+    ticks, per = hmi.hmi_batch_profile_kernels(b)
+    hmi.hmi_batch_profile(b, 0)
+    hmi.hmi_batch_destroy(b)
+    for st in streams:
+        st.close()
+    mix_ms = per["mixture"] / max(ticks, 1)
+    peak, peak_kind = peaks()
+    achieved = MIX_BYTES_PER_PX * px / (mix_ms / 1e3) / 1e9
+    traffic_px = profiled_traffic_per_px("mixture")
+    return {"params": dict(MIX_BENCH), "ms_per_step": ms, "frames_per_s": n / (ms / 1e3),
+            "mpx_per_s": px / (ms / 1e3) / 1e6, "steps": steps,
+            "launch": "pipelined ticks, the main run's launch shape, one group",
+            "roofline": {"bound": "hbm", "kernel": "k_mix<3>", "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": (traffic_px * px) if traffic_px else None,
+                         "algorithmic_bytes_per_launch": MIX_BYTES_PER_PX * px,
+                         "launch_ms": mix_ms, "launches_timed": ticks},
+            "single_chain_kernels_us": {k: round(v / max(ticks, 1) * 1e3, 2) for k, v in per.items()}}
+
+
+# the gray and hue tests opened to every coloured pixel and morphology off, so
+# that the final mask is the background test's own decision
+BG_TEST_ONLY = dict(gray_tol=0, hue_lo=0, hue_hi=1535, open_iters=0, close_iters=0)
+
+
+def bench_background_quality(hmi, synth, torch, dev, frames: int) -> dict:
     """1920x1080 drifting scene (the third single-stream workload: gradient
-    drift of one level per 50 frames, brightness flicker): share of pixels the
-    background test puts outside the band, with and without re-learning."""
+    drift of one level per 50 frames, brightness flicker, two moving hands)
+    with three background models: the learned band alone, the band with
+    re-learning, and the Gaussian mixture; the gray/hue tests and morphology
+    are neutral, so the mask is the background test's decision.  At every
+    100th frame: the share of non-hand pixels the test calls foreground (false
+    foreground) and the share of hand pixels it calls foreground (recall)."""
     import numpy as np
     w, h = synth.shape(3)
     lf = torch.from_numpy(synth.learn_frames(3, 0)).to(dev)
-    out = {"frames": frames, "params": RELEARN_BENCH}
-    for name, over in (("off", {}), ("on", RELEARN_BENCH)):
-        st = hmi.Stream(w, h, **over)
+    models = {"band": {}, "band_relearn": RELEARN_BENCH, "mixture": MIX_BENCH}
+    streams = {}
+    for name, over in models.items():
+        st = hmi.Stream(w, h, **BG_TEST_ONLY, **over)
         st.learn(lf)
-        series = []
-        for t in range(frames):
-            f = synth.run_frame(3, 0, t)
-            st.process(torch.from_numpy(f).to(dev), mask=False)
-            if (t + 1) % 100 == 0:
-                lo, hi = st.band()
-                g = st.last_gain()
-                c = np.minimum(255, (f.astype(np.uint32) * g + 32768) >> 16)
-                series.append(round(float(((c < lo) | (c > hi)).any(axis=2).mean()), 4))
+        streams[name] = st
+    yy, xx = np.mgrid[0:h, 0:w].astype(np.float32)
+    false_fg = {k: [] for k in models}
+    recall = {k: [] for k in models}
+    for t in range(frames):
+        fd = torch.from_numpy(synth.run_frame(3, 0, t)).to(dev)
+        last = (t + 1) % 100 == 0
+        region = None
+        if last:
+            region = np.zeros((h, w), bool)
+            for cx, cy, a, b in synth.truth(3, 0, t)[0]:
+                region |= ((xx - cx) / a) ** 2 + ((yy - cy) / b) ** 2 <= 1.0
+        for name, st in streams.items():
+            m, _ = st.process(fd, mask=last)
+            if last:
+                false_fg[name].append(round(float((m[~region] != 0).mean()), 5))
+                recall[name].append(round(float((m[region] != 0).mean()), 4))
+    for st in streams.values():
         st.close()
-        out[f"out_of_band_share_every_100_frames_{name}"] = series
-    return out
+    return {"frames": frames, "models": {k: dict(v) for k, v in models.items()},
+            "neutral_params": dict(BG_TEST_ONLY),
+            "false_foreground_share_every_100_frames": false_fg,
+            "hand_recall_every_100_frames": recall}
 
 
 def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
@@ -690,8 +800,11 @@ def main():
     ap.add_argument("--no-single", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-relearn", action="store_true", help="skip the re-learning cost run")
-    ap.add_argument("--relearn-eval", type=int, default=0,
-                    help="frames of the 1080p drifting scene to evaluate re-learning on (0: skip)")
+    ap.add_argument("--no-mixture", action="store_true", help="skip the Gaussian mixture run")
+    ap.add_argument("--bg-model", choices=sorted(BG_MODELS), default="band",
+                    help="background model of every stream of the main workload")
+    ap.add_argument("--quality-frames", type=int, default=1200,
+                    help="frames of the 1080p drifting scene to compare the background models on (0: skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",
                     help="ticks of the timed region: pipelined (stage overlap) or plain")

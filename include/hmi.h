@@ -108,8 +108,9 @@ typedef struct {
      * empty), kept in fitness order.  For frame t (counted from 1 over the
      * learning frames, which the mixture learns from an empty model, then the
      * running frames): the value matches the first non-empty component with
-     * bg_k_den^2 * sum (256 c' - M)^2 <= bg_k_num^2 * V * 4096 (lambda =
-     * bg_k_num / bg_k_den standard deviations); on a running frame it is
+     * bg_k_den^2 * sum (256 c' - M)^2 <= 3 * bg_k_num^2 * V * 4096 (the mean
+     * squared channel deviation within lambda^2 V, lambda = bg_k_num /
+     * bg_k_den, as the band reads k per channel); on a running frame it is
      * background iff it matched component j and the weights before j sum to
      * at most mix_bg_pct percent of all weights (model before the update).
      * Update (Lee's rates, every division rounded half away from zero): the

@@ -123,10 +123,10 @@ struct Layout {
     // re-learning sums (only with re-learning on): rows of rpitch pixels
     int rpitch;
     size_t rS, rQ, rmin, rmax, rcnt, rpx;
-    // Gaussian mixture planes (bg_model 1 only): 6 mix_k planes of mplane
-    // uint16 entries, rows of rpitch entries
+    // Gaussian mixture (bg_model 1 only): mbytes of 32-pixel tiles, nwords
+    // per row, 6 mix_k uint16 fields of 32 pixels each
     int mix_k;
-    size_t mix, mplane;
+    size_t mix, mbytes;
 };
 
 Layout make_layout(int w, int h, const hmi_params &p)
@@ -173,8 +173,8 @@ Layout make_layout(int w, int h, const hmi_params &p)
         L.rcnt = a.take(L.rpx);
     }
     L.mix_k = p.bg_model == 1 ? p.mix_k : 0;
-    L.mplane = (size_t)h * L.rpitch;
-    L.mix = L.mix_k ? a.take(L.mplane * 6 * L.mix_k * 2) : 0;
+    L.mbytes = (size_t)h * L.nwords * 32 * 6 * L.mix_k * 2;
+    L.mix = L.mix_k ? a.take(L.mbytes) : 0;
     L.total = a.off;
     return L;
 }
@@ -374,14 +374,14 @@ void fill_devstream(hmi_stream *s)
     MixView &M = D.mix;
     M.K = L.mix_k;
     M.planes = L.mix_k ? reinterpret_cast<uint16_t *>(a + L.mix) : nullptr;
-    M.plane = L.mplane;
-    M.pitch = L.rpitch;
+    M.tiles_x = L.nwords;
     M.rate_n = s->p.mix_rate_n;
     M.bg_pct = s->p.mix_bg_pct;
     M.lam_a = (uint32_t)s->p.bg_k_den * s->p.bg_k_den;
-    M.lam_b = (uint32_t)s->p.bg_k_num * s->p.bg_k_num * 4096u;
+    M.lam_b = 3u * s->p.bg_k_num * s->p.bg_k_num * 4096u;
     M.v_init = 16u * s->p.mix_sigma0 * s->p.mix_sigma0;
     M.v_min = 16u * s->p.mix_sigma_min * s->p.mix_sigma_min;
+    M.recip_n = recip40(2u * s->p.mix_rate_n);
 }
 
 void plan_free_graphs(hmi_batch *b)
@@ -1172,7 +1172,7 @@ int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool p
             keep.emplace_back(s->arena + L.rmax, L.rpx * 3);
             keep.emplace_back(s->arena + L.rcnt, L.rpx);
         }
-        if (L.mix_k) keep.emplace_back(s->arena + L.mix, L.mplane * 6 * L.mix_k * 2);
+        if (L.mix_k) keep.emplace_back(s->arena + L.mix, L.mbytes);
     }
     size_t total = 0;
     for (auto &k : keep) total += k.second;
@@ -1370,7 +1370,7 @@ int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
 cudaError_t enqueue_mix_reset(hmi_stream *s, cudaStream_t cs)
 {
     if (!s->L.mix_k) return cudaSuccess;
-    return cudaMemsetAsync(s->arena + s->L.mix, 0, s->L.mplane * 6 * s->L.mix_k * 2, cs);
+    return cudaMemsetAsync(s->arena + s->L.mix, 0, s->L.mbytes, cs);
 }
 
 // Band of a stream from its learned sums after n frames (Sec. 3.1 (i)), in
@@ -2299,11 +2299,16 @@ int hmi_get_mixture(const hmi_stream *s, uint16_t *out)
     if (!s->learned) return fail(HMI_ERR_NOT_LEARNED);
     HMI_CUDA(cudaSetDevice(s->dev));
     HMI_CUDA(cudaDeviceSynchronize());   // the last tick may have run on any stream
-    const size_t row = 2 * (size_t)s->w, plane = (size_t)s->w * s->h;
-    const uint16_t *src = reinterpret_cast<const uint16_t *>(s->arena + s->L.mix);
-    for (int p = 0; p < 6 * s->L.mix_k; ++p)
-        HMI_CUDA(cudaMemcpy2D(out + p * plane, row, src + p * s->L.mplane, 2 * (size_t)s->L.rpitch, row,
-                              s->h, cudaMemcpyDefault));
+    const int F = 6 * s->L.mix_k;
+    std::vector<uint16_t> tiles(s->L.mbytes / 2), dense((size_t)F * s->w * s->h);
+    HMI_CUDA(cudaMemcpy(tiles.data(), s->arena + s->L.mix, s->L.mbytes, cudaMemcpyDeviceToHost));
+    const size_t plane = (size_t)s->w * s->h;
+    for (int y = 0; y < s->h; ++y)
+        for (int x = 0; x < s->w; ++x) {
+            const size_t t = mix_tile(s->ds.mix, x, y) + (x & 31);
+            for (int f = 0; f < F; ++f) dense[f * plane + (size_t)y * s->w + x] = tiles[t + 32 * f];
+        }
+    HMI_CUDA(cudaMemcpy(out, dense.data(), dense.size() * 2, cudaMemcpyDefault));
     return HMI_OK;
 }
 

@@ -63,17 +63,36 @@ struct __align__(16) StreamState {
     hmi_pointer last;             // pointer of the last frame
 };
 
-// Gaussian mixture background of a stream (bg_model 1): 6 K planes of uint16,
-// W[k] (Q15), M[k][c] (Q8), V[k] (Q4), C[k], each h rows of `pitch` entries.
+// Gaussian mixture background of a stream (bg_model 1): 6 K fields of uint16
+// per pixel, W[k] (Q15), M[k][c] (Q8), V[k] (Q4), C[k], stored by tiles of 32
+// pixels of a row (one mask word): tile (y, x / 32) holds, field after field,
+// the 32 pixels' values, so that a warp's pixel state is one contiguous block
+// and every field is at a fixed offset from it.
 struct MixView {
     uint16_t *planes;
-    size_t plane;                 // entries per plane (h * pitch)
     int K;                        // components per pixel; 0: a band stream
-    int pitch;                    // entries per plane row (a multiple of 16)
+    int tiles_x;                  // tiles per row (the row's mask words)
     int rate_n, bg_pct;           // N (rates 1/min(., N)) and T in percent
-    uint32_t lam_a, lam_b;        // match iff lam_a * d2 <= lam_b * V (kd^2, kn^2 * 4096)
+    uint32_t lam_a, lam_b;        // match iff lam_a * d2 <= lam_b * V (kd^2, 3 kn^2 4096)
     uint32_t v_init, v_min;       // 16 sigma0^2 and 16 sigma_min^2
+    unsigned long long recip_n;   // recip40(2N): rounded division by N in one multiply
 };
+
+// First entry of the 32-pixel tile holding pixel (x, y) of a mixture.
+__host__ __device__ inline size_t mix_tile(const MixView &G, int x, int y)
+{
+    return ((size_t)y * G.tiles_x + (size_t)(x >> 5)) * (size_t)(6 * G.K) * 32u;
+}
+
+// Division by a divisor shared by many numerators, by one multiply: with
+// R = ceil(2^40 / d) and 2 <= d < 2^18, 2^40 <= R d <= 2^40 + 2^18, so
+// floor(n R / 2^40) = floor(n / d) for every n < 2^22 (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// Theorem 4.2 with N = 22, l = 18).
+__host__ __device__ inline unsigned long long recip40(uint32_t d)
+{
+    return ((1ull << 40) + d - 1) / d;
+}
 
 // Read-only description of a stream as the kernels see it.
 struct DevStream {
