@@ -207,13 +207,22 @@ HMI_API int hmi_batch_get_groups(const hmi_batch *b);
 
 /* Process one frame per stream of the batch.  Synchronous form: buffers may be
  * host or device; frames[i] is the frame of the i-th stream given at creation.
- * masks / ptrs as in hmi_process_batch. */
+ * masks / ptrs as in hmi_process_batch.  A frame in pinned (page-locked) host
+ * memory whose stream width is a multiple of 16 and whose address is 16-byte
+ * aligned is read over the host link by the luma pass itself, which stores it
+ * into a device staging frame as it sums it (one pass, no copy engine); other
+ * host frames are copied first.  The batch remembers the pinned buffers it has
+ * seen: they must stay pinned while the batch may be given them. */
 HMI_API int hmi_batch_process(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                       hmi_pointer *ptrs);
 
-/* Asynchronous form on cuda_stream: every buffer must be device memory; ptrs
- * (device, n entries) may be NULL.  With use_graph != 0 the tick is replayed
- * from a CUDA graph captured on first use. */
+/* Asynchronous form on cuda_stream: every buffer must be device memory, except
+ * frames, which may also be pinned host memory read in the luma pass as above
+ * (stream width a multiple of 16, 16-byte aligned; other host frames:
+ * HMI_ERR_INVALID_ARG); such a frame must stay valid and unchanged until
+ * cuda_stream has passed the call.  ptrs (device, n entries) may be NULL.
+ * With use_graph != 0 the tick is replayed from a CUDA graph captured on first
+ * use. */
 HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                             hmi_pointer *ptrs, void *cuda_stream, int use_graph);
 

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
@@ -118,6 +119,7 @@ struct Arena {
 
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
+    size_t frame_ph[kPhases];     // staging frames for pinned host frames, by tick phase
     size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits, comp, parent, count, flag, mask,
         st, hist, ds, ptr, ui, total;
     // re-learning sums (only with re-learning on): rows of rpitch pixels
@@ -144,6 +146,8 @@ Layout make_layout(int w, int h, const hmi_params &p)
     const size_t bitrows = (size_t)L.bh * 32 * L.nwords * 4;
     Arena a;
     L.frame = a.take((size_t)h * L.fpitch + 64);
+    L.frame_ph[0] = L.frame;
+    for (int k = 1; k < kPhases; ++k) L.frame_ph[k] = a.take((size_t)h * L.fpitch + 64);
     L.lo = a.take((size_t)h * L.fpitch + 64);
     L.hi = a.take((size_t)h * L.fpitch + 64);
     L.S = a.take(L.npx * 3 * 4);
@@ -316,6 +320,24 @@ struct hmi_batch {
     {
         if (seen.size() >= 65536) seen.clear();
         seen.insert(p);
+    }
+    // pinned host buffers already validated, with their device-accessible
+    // address (the caller keeps them pinned while the batch uses them)
+    std::unordered_map<const void *, const uint8_t *> pinned;
+    const uint8_t *pinned_dev(const void *p)
+    {
+        auto it = pinned.find(p);
+        if (it != pinned.end()) return it->second;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+        if (pinned.size() >= 65536) pinned.clear();
+        const uint8_t *d = static_cast<const uint8_t *>(at.devicePointer);
+        pinned.emplace(p, d);
+        return d;
     }
 };
 
@@ -917,10 +939,19 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
             dev = is_device_ptr(f);
             if (dev) b->remember_device(f);
         }
-        if (async_mode && !dev) return fail(HMI_ERR_INVALID_ARG);
+        // a pinned host frame with 16-pixel rows: k_luma copies it into the
+        // tick phase's staging frame while it sums it (no copy engine, one
+        // pass over the host link)
+        const uint8_t *pin = (!dev && (s->w % 16) == 0) ? b->pinned_dev(f) : nullptr;
+        if (pin && (reinterpret_cast<uintptr_t>(pin) & 15u) != 0) pin = nullptr;
+        t.src = pin;
+        if (async_mode && !dev && !pin) return fail(HMI_ERR_INVALID_ARG);
         if (dev && (s->w % 16) == 0 && (reinterpret_cast<uintptr_t>(f) & 15u) == 0) {
             t.frame = f;
             t.frame_pitch = 3LL * s->w;
+        } else if (pin) {
+            t.frame = s->arena + s->L.frame_ph[slot % kPhases];
+            t.frame_pitch = s->L.fpitch;   // 3 w: w is a multiple of 16
         } else {
             if (3 * (size_t)s->w == (size_t)s->L.fpitch) {
                 HMI_CUDA(cudaMemcpyAsync(s->d_frame, f, 3 * (size_t)s->w * s->h, cudaMemcpyDefault, cs));
@@ -1687,6 +1718,7 @@ bool server_round(hmi_server *v)
             TickIO &t = io[b->pos[i]];
             t.mask = nullptr;
             t.ptr_out = v->d_ptrs + i;
+            t.src = nullptr;
             if (take[i].f.host && !take[i].learning) {
                 s->used = true;
                 t.frame = s->d_frame;

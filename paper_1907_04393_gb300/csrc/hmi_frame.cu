@@ -56,6 +56,27 @@ __device__ __forceinline__ void load48(const uint8_t *src, uint64_t pol, uint32_
     w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
 }
 
+// 48 bytes of a pinned host frame (read once over the host link, through the
+// non-coherent path, no L2 policy), and their store into the staging frame.
+__device__ __forceinline__ void load48_host(const uint8_t *src, uint32_t (&w)[12])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(src);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 r;
+        asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(q + k));
+        w[4 * k] = r.x; w[4 * k + 1] = r.y; w[4 * k + 2] = r.z; w[4 * k + 3] = r.w;
+    }
+}
+
+__device__ __forceinline__ void store48(uint8_t *dst, const uint32_t (&w)[12])
+{
+    uint4 *q = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) q[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+
 __device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
 {
     return __byte_perm(w[b >> 2], 0u, 0x4440u | (uint32_t)(b & 3));
@@ -139,7 +160,12 @@ __global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
                     const int y = chunk_row((uint32_t)uu, magic), x0 = (uu - y * cpr) * kChunkPx;
                     if (x0 < w) {
                         npx[q] = min(kChunkPx, w - x0);
-                        load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
+                        if (io.src) {   // a pinned host frame: w is a multiple of 16, rows dense
+                            load48_host(io.src + (long long)y * 3 * w + 3 * x0, f[q]);
+                            store48(const_cast<uint8_t *>(io.frame) + (long long)y * io.frame_pitch + 3 * x0, f[q]);
+                        } else {
+                            load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, keep, f[q]);
+                        }
                     }
                 }
             }

@@ -145,6 +145,9 @@ __device__ __forceinline__ int chunk_row(uint32_t u, uint32_t magic)
 struct TickIO {
     const uint8_t *frame;         // frame of this tick
     long long frame_pitch;        // bytes between rows of `frame`
+    const uint8_t *src;           // a pinned host frame (device-accessible address, dense
+                                  // rows of 3 w bytes, w a multiple of 16) that k_luma
+                                  // copies into `frame` as it sums it; null: none
     uint8_t *mask;                // h*w mask out (device) or null
     hmi_pointer *ptr_out;         // pointer out (device) or null
 };

@@ -314,8 +314,8 @@ def _pinned(a: np.ndarray, offset: int = 0):
 
 def test_batch_pinned_host_frames():
     """Frames in page-locked host memory, aligned and misaligned, through the
-    synchronous batch form; an asynchronous call with a host frame is refused;
-    every result equals the oracle's."""
+    synchronous batch form; an asynchronous call with a misaligned host frame
+    is refused; every result equals the oracle's."""
     idx = [0, 20, 33, 50, 61, 63]
     gs, os_ = _batch_streams(4, idx)
     b = hmi.hmi_batch_create([g.handle for g in gs])
@@ -336,6 +336,70 @@ def test_batch_pinned_host_frames():
         hmi.hmi_batch_destroy(b)
         for g in gs:
             g.close()
+
+
+@pytest.mark.parametrize("mode", ["async", 2, 3])
+def test_pinned_host_frames_in_stream_ordered_ticks(mode):
+    """Pinned host frames given to the asynchronous and pipelined forms are read
+    by the luma pass over the host link into per-phase staging frames; masks
+    and pointers equal those of a twin batch given the same frames in device
+    memory, tick by tick (consecutive ticks in flight use distinct staging)."""
+    idx = [0, 20, 33, 50, 61]
+    T = 7
+    frames = [[synth.run_frame(4, i, t) for i in idx] for t in range(T)]
+    pins = [[_pinned(f) for f in fr] for fr in frames]
+    devs = [[_dev(f) for f in fr] for fr in frames]
+    s = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name, src in (("pinned", pins), ("device", devs)):
+        gs, _ = _batch_streams(4, idx)
+        b = hmi.hmi_batch_create([g.handle for g in gs])
+        hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), groups=1,
+                                         pipeline_depth=mode if mode != "async" else 2))
+        res = []
+        for t in range(T):
+            m = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+            p = torch.zeros(len(idx) * 40, dtype=torch.uint8, device="cuda")
+            if mode == "async":
+                hmi.hmi_batch_process_async(b, src[t], m, p.data_ptr(), s, t % 2 == 0)
+            else:
+                hmi.hmi_batch_process_pipelined(b, src[t], m, p.data_ptr(), s, t % 2 == 0)
+            res.append((m, p))
+        hmi.hmi_batch_flush(b, s)
+        torch.cuda.synchronize()
+        out[name] = [([x.cpu().numpy() for x in m], p.cpu().numpy()) for m, p in res]
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()
+    for t in range(T):
+        assert np.array_equal(out["pinned"][t][1], out["device"][t][1]), (mode, t)
+        for k in range(len(idx)):
+            assert np.array_equal(out["pinned"][t][0][k], out["device"][t][0][k]), (mode, t, k)
+
+
+def test_pinned_host_frames_rows_not_multiple_of_16():
+    """A pinned host frame of a stream whose width is not a multiple of 16 is
+    copied first in the synchronous form (results equal the oracle's) and
+    refused by the asynchronous form."""
+    g, o = pair(312, 40)
+    lf = np.ascontiguousarray(synth.learn_frames(1, 0, 6)[:, :40, :312])
+    learn_both(g, o, lf)
+    b = hmi.hmi_batch_create([g.handle])
+    try:
+        f = np.ascontiguousarray(synth.run_frame(1, 0, 3)[:40, :312])
+        pin = _pinned(f)
+        masks = [np.empty((40, 312), np.uint8)]
+        ptrs = np.zeros(1, hmi.POINTER_DTYPE)
+        hmi.hmi_batch_process(b, [pin], masks, ptrs)
+        m_o, _, p_o, _ = o.process(f)
+        assert np.array_equal(masks[0], m_o)
+        assert_pointer(dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[0]])), p_o, "312 wide")
+        with pytest.raises(hmi.HmiError) as e:
+            hmi.hmi_batch_process_async(b, [pin], None, None, torch.cuda.current_stream().cuda_stream, False)
+        assert e.value.status == hmi.HMI_ERR_INVALID_ARG
+    finally:
+        hmi.hmi_batch_destroy(b)
+        g.close()
 
 
 def test_batch_group_count_does_not_change_results():
