@@ -1456,6 +1456,7 @@ struct SrvTake {
     SrvFrame f;
     SrvStream *ss = nullptr;
     bool learning = false;
+    const uint8_t *src = nullptr;   // a pinned frame the luma pass reads itself
 };
 
 hmi_pointer empty_pointer()
@@ -1672,6 +1673,17 @@ bool server_round(hmi_server *v)
         hmi_stream *s = ss->s;
         take[i].learning = ss->learn_done < ss->learn_n;
         any_active = any_active || !take[i].learning;
+        take[i].src = nullptr;
+        if (!take[i].learning && (s->w % 16) == 0) {
+            // pinned frame with 16-pixel rows: no copy, the luma pass reads it
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, f.host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                at.devicePointer != nullptr && (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) == 0) {
+                take[i].src = static_cast<const uint8_t *>(at.devicePointer);
+                continue;
+            }
+            (void)cudaGetLastError();
+        }
         cudaError_t e;
         if (take[i].learning || 3 * (size_t)s->w == (size_t)s->L.fpitch)
             e = cudaMemcpyAsync(s->d_frame, f.host, f.bytes, cudaMemcpyHostToDevice, v->cs);
@@ -1723,6 +1735,10 @@ bool server_round(hmi_server *v)
                 s->used = true;
                 t.frame = s->d_frame;
                 t.frame_pitch = s->L.fpitch;
+                if (take[i].src) {
+                    t.src = take[i].src;
+                    t.frame = s->arena + s->L.frame_ph[slot % kPhases];
+                }
             } else {
                 t.frame = nullptr;
                 t.frame_pitch = 0;
@@ -1737,7 +1753,9 @@ bool server_round(hmi_server *v)
         }
     }
     rec.issued_ns = now_ns();
-    if (status == HMI_OK && cudaStreamSynchronize(v->cs) != cudaSuccess) {
+    // whatever was enqueued has finished with the round's host frames (read
+    // by copies or by the luma pass) before they are given back
+    if (cudaStreamSynchronize(v->cs) != cudaSuccess) {
         (void)cudaGetLastError();
         status = HMI_ERR_DEVICE;
     }
