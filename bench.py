@@ -878,7 +878,7 @@ def main():
     ap.add_argument("--serve-budget", type=float, default=0.9,
                     help="device budget as a fraction of the 256 streams' demand")
     ap.add_argument("--sweep-seconds", type=float, default=5.0)
-    ap.add_argument("--sweep-rates", default="1,2,4,8")
+    ap.add_argument("--sweep-rates", default="1,2,4,8,16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

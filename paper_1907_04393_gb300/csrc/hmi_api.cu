@@ -235,6 +235,9 @@ bool is_device_ptr(const void *p)
 }  // namespace
 
 struct hmi_batch;
+struct hmi_stream;
+// learning from frames without preparing the single-frame plan (the server's)
+extern "C" int learn_background(hmi_stream *s, const uint8_t *frames, int n);
 
 struct hmi_stream {
     int dev = 0;
@@ -1496,6 +1499,8 @@ struct hmi_server {
     cudaStream_t cs = nullptr;
     hmi_pointer *h_ptrs = nullptr, *d_ptrs = nullptr;
     int ptr_cap = 0;
+    LearnItem *h_items = nullptr, *d_items = nullptr;   // a round's learning frames
+    int item_cap = 0;
     uint64_t ticks = 0, frames = 0;
     std::vector<hmi_server_round> rounds;   // ring of kRoundLog records (under mu)
     uint64_t rounds_written = 0;
@@ -1674,11 +1679,15 @@ bool server_round(hmi_server *v)
         take[i].learning = ss->learn_done < ss->learn_n;
         any_active = any_active || !take[i].learning;
         take[i].src = nullptr;
-        if (!take[i].learning && (s->w % 16) == 0) {
-            // pinned frame with 16-pixel rows: no copy, the luma pass reads it
+        // a pinned frame needs no copy: the luma pass reads a frame to process
+        // (16-pixel rows, 16-byte aligned), the batched learning kernel a
+        // learning frame (pixels a multiple of 4, 4-byte aligned)
+        const bool rows16 = (s->w % 16) == 0, quads = ((size_t)s->w * s->h) % 4 == 0;
+        if (take[i].learning ? quads : rows16) {
             cudaPointerAttributes at;
             if (cudaPointerGetAttributes(&at, f.host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-                at.devicePointer != nullptr && (reinterpret_cast<uintptr_t>(at.devicePointer) & 15u) == 0) {
+                at.devicePointer != nullptr &&
+                (reinterpret_cast<uintptr_t>(at.devicePointer) & (take[i].learning ? 3u : 15u)) == 0) {
                 take[i].src = static_cast<const uint8_t *>(at.devicePointer);
                 continue;
             }
@@ -1695,20 +1704,61 @@ bool server_round(hmi_server *v)
             status = HMI_ERR_DEVICE;
         }
     }
+    // learning frames: their sums in one launch for the whole round (a burst
+    // of new streams learns at once), except frames the batch cannot take
+    if (status == HMI_OK && v->item_cap < n) {
+        cudaFreeHost(v->h_items);
+        cudaFree(v->d_items);
+        v->h_items = nullptr;
+        v->d_items = nullptr;
+        v->item_cap = 0;
+        if (cudaMallocHost(&v->h_items, sizeof(LearnItem) * n) == cudaSuccess &&
+            cudaMalloc(&v->d_items, sizeof(LearnItem) * n) == cudaSuccess)
+            v->item_cap = n;
+        else
+            status = HMI_ERR_NO_MEMORY;
+    }
+    int nitems = 0;
+    unsigned long long quads = 0;
     for (int i = 0; i < n && status == HMI_OK; ++i) {
         if (!take[i].f.host || !take[i].learning) continue;
         SrvStream *ss = take[i].ss;
         hmi_stream *s = ss->s;
+        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
+        const long long npx = (long long)s->w * s->h;
         cudaError_t e = cudaSuccess;
         if (ss->learn_done == 0)
             e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
-        if (e == cudaSuccess)
-            e = launch_learn_accum(s->d_frame, 1, (long long)s->w * s->h, s->d_S, s->d_Q, s->d_vmin,
-                                   s->d_vmax, ss->learn_done == 0, s->st, v->cs);
-        if (e == cudaSuccess && s->L.mix_k) {   // the mixture learns the same frame
+        if (e == cudaSuccess && npx % 4 == 0 && (reinterpret_cast<uintptr_t>(fr) & 3u) == 0) {
+            v->h_items[nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
+                                             ss->learn_done == 0};
+            quads += (unsigned long long)(npx / 4);
+        } else if (e == cudaSuccess) {
+            e = launch_learn_accum(fr, 1, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, ss->learn_done == 0,
+                                   s->st, v->cs);
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            status = HMI_ERR_DEVICE;
+        }
+    }
+    if (status == HMI_OK && nitems > 0 &&
+        (cudaMemcpyAsync(v->d_items, v->h_items, sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
+             cudaSuccess ||
+         launch_learn_batch(v->d_items, nitems, quads, v->cs) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        status = HMI_ERR_DEVICE;
+    }
+    for (int i = 0; i < n && status == HMI_OK; ++i) {
+        if (!take[i].f.host || !take[i].learning) continue;
+        SrvStream *ss = take[i].ss;
+        hmi_stream *s = ss->s;
+        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
+        cudaError_t e = cudaSuccess;
+        if (s->L.mix_k) {   // the mixture learns the same frame
             if (ss->learn_done == 0) e = enqueue_mix_reset(s, v->cs);
             if (e == cudaSuccess)
-                e = launch_mix_learn(s->d_frame, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
+                e = launch_mix_learn(fr, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
         }
         if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
         if (e != cudaSuccess) {
@@ -1862,6 +1912,8 @@ void hmi_server_destroy(hmi_server *v)
         for (auto *p : kv.second) cudaFreeHost(p);
     cudaFreeHost(v->h_ptrs);
     cudaFree(v->d_ptrs);
+    cudaFreeHost(v->h_items);
+    cudaFree(v->d_items);
     if (v->cs) cudaStreamDestroy(v->cs);
     delete v;
 }
@@ -1897,7 +1949,7 @@ int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uin
     HMI_CUDA(cudaSetDevice(v->dev));
     hmi_stream *s = hmi_create_stream(w, h, p);
     int st = s ? HMI_OK : g_last_error;
-    if (s) st = hmi_learn_background(s, learn_frames, n);
+    if (s) st = learn_background(s, learn_frames, n);
     if (st != HMI_OK) {
         if (s) hmi_destroy_stream(s);
         std::lock_guard<std::mutex> lk(v->mu);
@@ -2096,6 +2148,15 @@ void hmi_destroy_stream(hmi_stream *s)
 }
 
 int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
+{
+    const int st = learn_background(s, frames, n);
+    // the single-frame launch plan is made now rather than by the first
+    // hmi_process_frame (best effort: that call makes it otherwise)
+    if (st == HMI_OK && !self_plan(s)) (void)cudaGetLastError();
+    return st;
+}
+
+int learn_background(hmi_stream *s, const uint8_t *frames, int n)
 {
     if (!s || !frames || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(s->dev));

@@ -233,6 +233,19 @@ cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t 
 cudaError_t launch_learn_accum(const uint8_t *frames, int nf, long long npx, uint32_t *S,
                                uint32_t *Q, uint8_t *vmin, uint8_t *vmax, int first,
                                StreamState *st, cudaStream_t cs);
+// One learning frame of a stream, for k_learn_batch: frame (device-accessible,
+// packed rows, npx % 4 == 0, 4-byte aligned), the stream's sums, first frame
+// or not, and its first quad (4 pixels) in the launch.
+struct LearnItem {
+    const uint8_t *frame;
+    uint32_t *S, *Q;
+    uint8_t *vmin, *vmax;
+    StreamState *st;
+    unsigned long long quad0;
+    int first;
+};
+cudaError_t launch_learn_batch(const LearnItem *items, int nitems, unsigned long long total_quads,
+                               cudaStream_t cs);
 cudaError_t launch_learn_band(const uint32_t *S, const uint32_t *Q, const uint8_t *vmin,
                               const uint8_t *vmax, int n, int kn, int kd, int delta, int w,
                               int h, int fpitch, uint8_t *lo, uint8_t *hi, StreamState *st,

@@ -63,7 +63,66 @@ __global__ void __launch_bounds__(kThreads) k_learn_accum(const uint8_t *__restr
 // Same sums, four pixels (twelve channel values) per thread: the frame bytes,
 // min and max as three 32-bit words each (byte-wise min / max on packed
 // bytes), S and Q as three 128-bit words each.  Needs npx % 4 == 0, frames
-// 4-byte aligned and S, Q 16-byte aligned.
+// 4-byte aligned and S, Q 16-byte aligned.  Returns the frames' luma total
+// over the four pixels.  Frame i is at frame0 + i * fstride.
+__device__ __forceinline__ unsigned long long learn_quad(const uint8_t *frame0, long long fstride, int nf,
+                                                         long long quad, uint32_t *S, uint32_t *Q,
+                                                         uint8_t *vmin, uint8_t *vmax, int first)
+{
+    unsigned long long luma = 0;
+    uint4 *S4 = reinterpret_cast<uint4 *>(S) + 3 * quad;
+    uint4 *Q4 = reinterpret_cast<uint4 *>(Q) + 3 * quad;
+    uint32_t *mn4 = reinterpret_cast<uint32_t *>(vmin) + 3 * quad;
+    uint32_t *mx4 = reinterpret_cast<uint32_t *>(vmax) + 3 * quad;
+    uint32_t s[12], q[12], mn[3], mx[3];
+    if (first) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s[k] = q[k] = 0u;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = 0xffffffffu;
+            mx[k] = 0u;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint4 a = S4[k], b = Q4[k];
+            s[4 * k] = a.x; s[4 * k + 1] = a.y; s[4 * k + 2] = a.z; s[4 * k + 3] = a.w;
+            q[4 * k] = b.x; q[4 * k + 1] = b.y; q[4 * k + 2] = b.z; q[4 * k + 3] = b.w;
+            mn[k] = mn4[k];
+            mx[k] = mx4[k];
+        }
+    }
+    for (int i = 0; i < nf; ++i) {
+        const uint32_t *f = reinterpret_cast<const uint32_t *>(frame0 + (long long)i * fstride) + 3 * quad;
+        uint32_t wv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            wv[k] = __ldg(f + k);
+            mn[k] = __vminu4(mn[k], wv[k]);
+            mx[k] = __vmaxu4(mx[k], wv[k]);
+        }
+        uint32_t v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            v[k] = (wv[k >> 2] >> (8 * (k & 3))) & 0xffu;
+            s[k] += v[k];
+            q[k] += v[k] * v[k];
+        }
+#pragma unroll
+        for (int px = 0; px < 4; ++px)
+            luma += (77u * v[3 * px] + 150u * v[3 * px + 1] + 29u * v[3 * px + 2] + 128u) >> 8;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        S4[k] = make_uint4(s[4 * k], s[4 * k + 1], s[4 * k + 2], s[4 * k + 3]);
+        Q4[k] = make_uint4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
+        mn4[k] = mn[k];
+        mx4[k] = mx[k];
+    }
+    return luma;
+}
+
 __global__ void __launch_bounds__(kThreads) k_learn_accum4(const uint8_t *__restrict__ frames,
                                                            int nf, long long npx,
                                                            uint32_t *S, uint32_t *Q,
@@ -73,58 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_learn_accum4(const uint8_t *__rest
     __shared__ unsigned long long red[kThreads / 32];
     const long long quad = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long luma = 0;
-    if (quad < npx / 4) {
-        uint4 *S4 = reinterpret_cast<uint4 *>(S) + 3 * quad;
-        uint4 *Q4 = reinterpret_cast<uint4 *>(Q) + 3 * quad;
-        uint32_t *mn4 = reinterpret_cast<uint32_t *>(vmin) + 3 * quad;
-        uint32_t *mx4 = reinterpret_cast<uint32_t *>(vmax) + 3 * quad;
-        uint32_t s[12], q[12], mn[3], mx[3];
-        if (first) {
-#pragma unroll
-            for (int k = 0; k < 12; ++k) s[k] = q[k] = 0u;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                mn[k] = 0xffffffffu;
-                mx[k] = 0u;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const uint4 a = S4[k], b = Q4[k];
-                s[4 * k] = a.x; s[4 * k + 1] = a.y; s[4 * k + 2] = a.z; s[4 * k + 3] = a.w;
-                q[4 * k] = b.x; q[4 * k + 1] = b.y; q[4 * k + 2] = b.z; q[4 * k + 3] = b.w;
-                mn[k] = mn4[k];
-                mx[k] = mx4[k];
-            }
-        }
-        for (int i = 0; i < nf; ++i) {
-            const uint32_t *f = reinterpret_cast<const uint32_t *>(frames + (long long)i * npx * 3) + 3 * quad;
-            uint32_t wv[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                wv[k] = __ldg(f + k);
-                mn[k] = __vminu4(mn[k], wv[k]);
-                mx[k] = __vmaxu4(mx[k], wv[k]);
-            }
-            uint32_t v[12];
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-                v[k] = (wv[k >> 2] >> (8 * (k & 3))) & 0xffu;
-                s[k] += v[k];
-                q[k] += v[k] * v[k];
-            }
-#pragma unroll
-            for (int px = 0; px < 4; ++px)
-                luma += (77u * v[3 * px] + 150u * v[3 * px + 1] + 29u * v[3 * px + 2] + 128u) >> 8;
-        }
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            S4[k] = make_uint4(s[4 * k], s[4 * k + 1], s[4 * k + 2], s[4 * k + 3]);
-            Q4[k] = make_uint4(q[4 * k], q[4 * k + 1], q[4 * k + 2], q[4 * k + 3]);
-            mn4[k] = mn[k];
-            mx4[k] = mx[k];
-        }
-    }
+    if (quad < npx / 4) luma = learn_quad(frames, npx * 3, nf, quad, S, Q, vmin, vmax, first);
     for (int o = 16; o > 0; o >>= 1) luma += __shfl_xor_sync(0xffffffffu, luma, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = luma;
     __syncthreads();
@@ -132,6 +140,36 @@ __global__ void __launch_bounds__(kThreads) k_learn_accum4(const uint8_t *__rest
         unsigned long long t = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
         if (t) atomicAdd(&st->learn_luma, t);
+    }
+}
+
+// One learning frame of each of several streams in one launch (a server round
+// whose new streams are all learning at once): item e covers quads [quad0,
+// quad0 + npx / 4) of the launch.  A warp whose lanes all belong to one item
+// adds its luma total with one atomic, a warp across items lane by lane.
+__global__ void __launch_bounds__(kThreads) k_learn_batch(const LearnItem *items, int nitems,
+                                                          unsigned long long total)
+{
+    const unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int e = -1;
+    unsigned long long luma = 0;
+    if (g < total) {
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].quad0 <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        e = lo;
+        const LearnItem it = items[e];
+        luma = learn_quad(it.frame, 0, 1, (long long)(g - it.quad0), it.S, it.Q, it.vmin, it.vmax, it.first);
+    }
+    const int e0 = __shfl_sync(0xffffffffu, e, 0);
+    if (__all_sync(0xffffffffu, e == e0)) {
+        for (int o = 16; o > 0; o >>= 1) luma += __shfl_xor_sync(0xffffffffu, luma, o);
+        if ((threadIdx.x & 31) == 0 && e0 >= 0 && luma) atomicAdd(&items[e0].st->learn_luma, luma);
+    } else if (e >= 0 && luma) {
+        atomicAdd(&items[e].st->learn_luma, luma);
     }
 }
 
@@ -274,6 +312,15 @@ cudaError_t launch_learn_accum(const uint8_t *frames, int nf, long long npx, uin
         const unsigned grid = (unsigned)((npx + kThreads - 1) / kThreads);
         k_learn_accum<<<grid, kThreads, 0, cs>>>(frames, nf, npx, S, Q, vmin, vmax, first, st);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_learn_batch(const LearnItem *items, int nitems, unsigned long long total_quads,
+                               cudaStream_t cs)
+{
+    if (nitems < 1 || total_quads == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((total_quads + kThreads - 1) / kThreads);
+    k_learn_batch<<<grid, kThreads, 0, cs>>>(items, nitems, total_quads);
     return cudaGetLastError();
 }
 
