@@ -145,3 +145,57 @@ def test_online_learning_equals_learned_up_front(over):
             st, p = got[(s, skip + t)]
             assert st == hmi.HMI_OK and p == alone[s][t], (s, t)
     hmi.hmi_server_destroy(srv)
+
+
+def test_online_learning_odd_sizes():
+    """Streams whose pixel count is not a multiple of 4 (learning frames summed
+    one launch per frame, not in the round's batch) or whose width is not a
+    multiple of 16 (frames copied, not read in place by the luma pass), next
+    to a regular stream: online learning equals learning up front."""
+    rng = np.random.default_rng(77)
+    shapes = [(37, 29), (40, 24), (64, 48)]
+    n_learn, nframes = 4, 4
+    base = {sh: rng.integers(0, 256, size=(sh[1], sh[0], 3)) for sh in shapes}
+    learn = {sh: np.clip(base[sh] + rng.integers(-2, 3, size=(n_learn,) + base[sh].shape), 0, 255).astype(np.uint8)
+             for sh in shapes}
+    frames = {}
+    for sh in shapes:
+        fr = []
+        for t in range(nframes):
+            f = np.clip(base[sh] + rng.integers(-2, 3, size=base[sh].shape), 0, 255).astype(np.uint8)
+            f[5:15, 5:20] = (200, 120, 90)       # a skin-coloured blob
+            fr.append(f)
+        frames[sh] = fr
+    alone = {}
+    for sh in shapes:
+        st = hmi.Stream(*sh)
+        st.learn(learn[sh])
+        alone[sh] = [st.process(f, mask=False)[1] for f in frames[sh]]
+        st.close()
+    srv = hmi.hmi_server_create(1 << 34, 16)
+    ids = {sh: hmi.hmi_server_admit(srv, sh[0], sh[1], None, None, n_learn) for sh in shapes}
+    tag_of, tag = {}, 0
+    pinned = {}
+    for k in range(n_learn + nframes):
+        for sh in shapes:
+            f = learn[sh][k] if k < n_learn else frames[sh][k - n_learn]
+            buf = torch.from_numpy(np.ascontiguousarray(f)).pin_memory()
+            pinned[(sh, k)] = buf
+            tag += 1
+            tag_of[tag] = (sh, k)
+            assert hmi.hmi_server_submit(srv, ids[sh], buf.numpy(), tag) == hmi.HMI_OK
+    got = {}
+    buf = (hmi.hmi_server_result * 64)()
+    while len(got) < tag:
+        n = hmi.hmi_server_poll(srv, buf, 2_000_000)
+        assert n > 0, "server stalled"
+        for i in range(n):
+            r = buf[i]
+            got[tag_of[r.tag]] = (r.status, r.pointer.as_dict())
+    for sh in shapes:
+        for k in range(n_learn):
+            assert got[(sh, k)][0] == hmi.HMI_LEARNING, (sh, k)
+        for t in range(nframes):
+            st, p = got[(sh, n_learn + t)]
+            assert st == hmi.HMI_OK and p == alone[sh][t], (sh, t)
+    hmi.hmi_server_destroy(srv)
