@@ -499,7 +499,8 @@ def run_ours(args) -> None:
     # ---- single 640x480 stream (the other configuration of the metric) ---
     single = None
     if not args.no_single:
-        single = bench_single(hmi, synth, torch, dev, cs, args)
+        single = bench_single(hmi, synth, torch, dev, cs, args, 2)
+        single_hd = bench_single(hmi, synth, torch, dev, cs, args, 3)
 
     hmi.hmi_batch_destroy(batch)
     for s in streams:
@@ -563,6 +564,7 @@ def run_ours(args) -> None:
     }
     if single is not None:
         line["single_640x480"] = single
+        line["single_1920x1080"] = single_hd
     if args.bg_model != "band":
         line["config"]["background"] = dict(MIX_BENCH)
     if relearn is not None:
@@ -747,27 +749,48 @@ def bench_background_quality(hmi, synth, torch, dev, frames: int) -> dict:
             "hand_recall_every_100_frames": recall}
 
 
-def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
-    """640x480 single stream: graph replay throughput, and per-frame latency of
-    the synchronous API with a pinned host frame (host mask, host pointer)."""
-    w, h = synth.shape(2)
+def bench_single(hmi, synth, torch, dev, cs, args, cfg: int = 2) -> dict:
+    """One stream of the given single-stream configuration (640x480 or
+    1920x1080): launch shape autotuned for it, pipelined graph-tick
+    throughput, the band-test kernel timed alone in plain ticks (its share of
+    HBM), and per-frame latency of the synchronous API with a pinned host frame
+    (host mask, host pointer)."""
+    w, h = synth.shape(cfg)
     st = hmi.Stream(w, h)
-    st.learn(torch.from_numpy(synth.learn_frames(2)).to(dev))
-    ring = [torch.from_numpy(synth.run_frame(2, 0, t)).to(dev) for t in range(16)]
+    st.learn(torch.from_numpy(synth.learn_frames(cfg)).to(dev))
+    ring = [torch.from_numpy(synth.run_frame(cfg, 0, t)).to(dev) for t in range(16)]
     mask = torch.empty((h, w), dtype=torch.uint8, device=dev)
     ptr = torch.zeros(40, dtype=torch.uint8, device=dev)
     b = hmi.hmi_batch_create([st.handle])
-    for k in range(20):
+    shape, _ = hmi.hmi_batch_autotune(b, [ring[0]], 30, True)
+
+    def tick(k):
         hmi.hmi_batch_process_async(b, [ring[k % 16]], [mask], ptr.data_ptr(), cs.cuda_stream, True)
+
+    def tick_pipelined(k):
+        hmi.hmi_batch_process_pipelined(b, [ring[k % 16]], [mask], ptr.data_ptr(), cs.cuda_stream, True)
+
+    for k in range(20):
+        tick_pipelined(k)
+    hmi.hmi_batch_flush(b, cs.cuda_stream)
     torch.cuda.synchronize()
     steps = max(100, min(args.steps * 4, 4000))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cs)
     for k in range(steps):
-        hmi.hmi_batch_process_async(b, [ring[k % 16]], [mask], ptr.data_ptr(), cs.cuda_stream, True)
+        tick_pipelined(k)
+    hmi.hmi_batch_flush(b, cs.cuda_stream)
     e1.record(cs)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    prof = min(steps, 1000)
+    hmi.hmi_batch_profile(b, prof)
+    for k in range(prof):
+        tick(k)
+    ticks, per = hmi.hmi_batch_profile_kernels(b)
+    hmi.hmi_batch_profile(b, 0)
+    cls_ms = per["classify"] / max(ticks, 1)
+    peak, peak_kind = peaks()
     host = [r.cpu().pin_memory() for r in ring]
     hmask = np.empty((h, w), np.uint8)
     hp = hmi.hmi_pointer()
@@ -779,8 +802,13 @@ def bench_single(hmi, synth, torch, dev, cs, args) -> dict:
     hmi.hmi_batch_destroy(b)
     st.close()
     lat.sort()
+    achieved = CLASSIFY_BYTES_PER_PX * w * h / (cls_ms / 1e3) / 1e9
     return {"frames_per_s": steps / (ms / 1e3), "mpx_per_s": steps * w * h / (ms / 1e3) / 1e6,
-            "ms_per_frame": ms / steps,
+            "ms_per_frame": ms / steps, "tuning": shape,
+            "launch": "pipelined graph ticks (results one call later), launch shape autotuned for the stream",
+            "classify": {"launch_us": cls_ms * 1e3, "achieved_GBps": achieved, "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_px": CLASSIFY_BYTES_PER_PX},
+            "kernels_us": {k: round(v / max(ticks, 1) * 1e3, 2) for k, v in per.items()},
             "e2e_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99) - 1],
                                "api": "hmi_process_frame, pinned host frame, host mask + pointer"}}
 
