@@ -226,10 +226,10 @@ int orc_relearn_in_window(long long f, int period, int frames)
 /*  1. match: the first non-empty component with                             */
 /*       ld^2 * sum_ch (256 x - M)^2 <= 3 * ln^2 * V * 4096                   */
 /*     (the mean squared channel deviation at most lambda^2 V, lambda =      */
-/*     ln / ld: "within lambda standard deviations" per channel, as the band */
-/*     reads k; the joint distance with lambda = 2.5 would reject a tenth of */
-/*     pure-noise background pixels, the chi-square tail with 3 degrees of    */
-/*     freedom);                                                              */
+/*     ln / ld: within lambda standard deviations, read per channel as the   */
+/*     band reads k; the joint distance with lambda = 2.5 would reject a     */
+/*     tenth of pure-noise background pixels, the chi-square tail with 3     */
+/*     degrees of freedom);                                                   */
 /*  2. decision (running frames only, on the model before this frame): the   */
 /*     pixel is background iff it matched component j and the weights of the */
 /*     components before j sum to at most T percent of all weights (the      */
