@@ -99,8 +99,8 @@ typedef struct {
      * centroid, if within this many pixels (ties: larger area, then smaller
      * label); else the largest blob. */
     uint16_t track_max_dist;/* [0]      pixels */
-    /* Background model (Sec. 2: the FIZI module learns the background with
-     * advanced machine learning; Sec. 3.3 cites Lee's adaptive Gaussian
+    /* Background model (Sec. 2: FIZI's background is learned with advanced
+     * machine learning; Sec. 3.3 cites Lee's adaptive Gaussian
      * mixture learning).  bg_model 0: the learned band above.  bg_model 1:
      * per pixel, mix_k Gaussian components over the gain-corrected RGB value,
      * each a weight W (Q15), a mean per channel M (Q8), one variance V
@@ -159,8 +159,8 @@ HMI_API hmi_stream *hmi_create_stream(int w, int h, const hmi_params *p);
  * Any batch that contains the stream must be destroyed first. */
 HMI_API void hmi_destroy_stream(hmi_stream *s);
 
-/* Learn the background model from n user-free frames (Sec. 2: the FIZI
- * module learns the background before the hand enters; Sec. 3.1 (i): per-pixel
+/* Learn the background model from n user-free frames (Sec. 2: FIZI's
+ * background is learned before the hand enters; Sec. 3.1 (i): per-pixel
  * minimum and maximum).  frames: n consecutive packed RGB8 frames
  * (n*h*w*3 bytes), host or device.  Per pixel and channel the library keeps
  * the exact sums S, Q and the min / max, derives the background band and the
@@ -312,7 +312,7 @@ HMI_API int hmi_get_labels(const hmi_stream *s, int32_t *labels);
 
 /* Headless Interface module (Sec. 2: fed by the Mouse module, it finds
  * which interface zone holds the pointer; each zone maps to an event)
- * and driving wheel (Sec. 4: the hand turns around an imaginary wheel to
+ * and driving wheel (Sec. 4: the hand rotates about a virtual wheel to
  * steer left and right; speed is the third control).  Per frame, from the
  * valid pointer's rounded centroid p = floor((2 sum + area) / (2 area)) per
  * axis: zone = the first listed inclusive rectangle containing p; on_wheel
@@ -417,7 +417,7 @@ HMI_API void hmi_server_destroy(hmi_server *srv);
  * With learn_frames non-NULL the background is learned now from n contiguous
  * host frames (h*w*3 bytes each).  With learn_frames NULL the stream learns
  * online: the first n frames submitted to it are the user-free learning frames
- * (Sec. 2: the FIZI module learns the background with no hand in view), each
+ * (Sec. 2: FIZI's background is learned with no hand in view), each
  * accumulated by the dispatcher as it arrives and returned with status
  * HMI_LEARNING; the band is formed after the n-th, and later frames are
  * processed.  n: 1..65535. */

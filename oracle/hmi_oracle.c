@@ -43,8 +43,8 @@ static int imin(int a, int b) { return a < b ? a : b; }
 static int imax(int a, int b) { return a > b ? a : b; }
 
 /* ======================================================================== */
-/* Step L -- background learning (Sec. 2: the FIZI module learns the         */
-/* background before the hand enters; Sec. 3.1 (i): per-pixel minimum and    */
+/* Step L -- background learning (Sec. 2: FIZI's background is learned       */
+/* before the hand enters; Sec. 3.1 (i): per-pixel minimum and                */
 /* maximum taken during that learning; Sec. 3.3 cites Gaussian background     */
 /* models for the learning).                                                 */
 /* ======================================================================== */
@@ -214,8 +214,8 @@ int orc_relearn_in_window(long long f, int period, int frames)
 }
 
 /* ======================================================================== */
-/* Mixture-of-Gaussians background (Sec. 2: the FIZI module learns the        */
-/* background with advanced machine learning; Sec. 3.3 cites Lee's adaptive   */
+/* Mixture-of-Gaussians background (Sec. 2: FIZI's background is learned     */
+/* with advanced machine learning; Sec. 3.3 cites Lee's adaptive              */
 /* Gaussian mixture learning for it).  A variant of the learning (step L) and */
 /* of the background test (step 2); the other steps are unchanged.            */
 /* Reading, all integer, per pixel: K components kept in fitness order, each  */
@@ -429,8 +429,9 @@ void orc_hue_map(const uint8_t *c, size_t npx, int16_t *out)
     for (size_t p = 0; p < npx; ++p) out[p] = (int16_t)orc_hue(c[3 * p], c[3 * p + 1], c[3 * p + 2]);
 }
 
-/* Hue inside the closed arc [a1, a2] taken modulo one turn, Sec. 3.1 (iii)
- * "Hue in [alpha1, alpha2] % 2pi": a1 > a2 means the arc wraps through 0. */
+/* Hue inside the closed arc [a1, a2] taken modulo one turn (Sec. 3.1 (iii):
+ * the skin hue lies between alpha1 and alpha2 modulo 2 pi): a1 > a2 means the
+ * arc wraps through 0. */
 static int in_arc(int h, int a1, int a2)
 {
     return (a1 <= a2) ? (h >= a1 && h <= a2) : (h >= a1 || h <= a2);
@@ -566,9 +567,9 @@ int orc_label(const uint8_t *mask, int w, int h, int32_t *labels)
 }
 
 /* ======================================================================== */
-/* Step 5b -- pointer (Sec. 2: "This hand zone is converted into a pointer by */
-/* the Mouse module"; the Interface reads "its movement, its state (click or  */
-/* not)").                                                                    */
+/* Step 5b -- pointer (Sec. 2: the Mouse module turns the hand zone into a   */
+/* pointer, whose movement and clicked / not-clicked state the Interface     */
+/* reads).                                                                    */
 /* Reading: the hand is the largest component (ties: smaller label); the      */
 /* pointer is its centroid with pixel centres at integer coordinates, and its */
 /* inclusive bounding box; valid iff area >= min_area.  With no component:    */
@@ -772,8 +773,8 @@ void orc_process_frame(const uint8_t *frame, int w, int h,
 /* ======================================================================== */
 /* Interface module (Sec. 2: fed by the Mouse module, it finds which         */
 /* interface zone holds the pointer; each zone maps to an event)             */
-/* and the driving application (Sec. 4: the hand turns around an imaginary    */
-/* wheel to steer left or right, and the speed is the third control).        */
+/* and the driving application (Sec. 4: rotating the hand about a virtual     */
+/* wheel steers left or right; the speed is the third control).              */
 /* Reading, headless and integer: the pointer point is the rounded centroid   */
 /* of a valid pointer (floor((2 sum + area) / (2 area)) per axis); the zone   */
 /* is the first listed inclusive rectangle that contains it; the point is on  */

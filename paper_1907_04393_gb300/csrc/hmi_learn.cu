@@ -1,5 +1,5 @@
-// hmi_learn.cu -- background learning (Sec. 2: the FIZI module learns the
-// background before the hand enters; Sec. 3.1 (i): per-pixel minimum and
+// hmi_learn.cu -- background learning (Sec. 2: FIZI's background is learned
+// before the hand enters; Sec. 3.1 (i): per-pixel minimum and
 // maximum taken during that learning; Sec. 3.3: Gaussian background models).
 //   k_learn_accum  exact per pixel-channel sums S = sum v, Q = sum v^2 and the
 //                  min / max over a chunk of frames, plus the frames' luma total

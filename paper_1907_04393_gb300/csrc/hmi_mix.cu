@@ -1,5 +1,5 @@
-// hmi_mix.cu -- Gaussian mixture background (Sec. 2: the FIZI module learns
-// the background with advanced machine learning; Sec. 3.3 cites Lee's adaptive
+// hmi_mix.cu -- Gaussian mixture background (Sec. 2: FIZI's background is
+// learned with advanced machine learning; Sec. 3.3 cites Lee's adaptive
 // Gaussian mixture learning), a variant of the band of Sec. 3.1 (i):
 //   k_mix        per tick: brightness-corrected value of every pixel of the
 //                mixture streams, the mixture's background test (the raw bit
