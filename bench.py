@@ -827,7 +827,8 @@ def bench_serving(hmi, args) -> dict:
     rates = [float(x) for x in args.sweep_rates.split(",") if x]
     sweep = None
     if rates and args.sweep_seconds > 0:
-        sweep = serve.sweep(bank, rates, args.sweep_seconds)
+        # twice the 256 streams' demand: never reached, so no stream is refused
+        sweep = serve.sweep(bank, rates, args.sweep_seconds, budget_bytes=2 * demand)
     tr = serve.make_trace(args.serve_seconds)
     main_run = serve.run_served(tr, bank, budget)
     out = {"workload": "256 streams (128x320x240, 64x640x480, 48x1280x720, 16x1920x1080 RGB8), "

@@ -1888,6 +1888,20 @@ hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue)
         fail(HMI_ERR_DEVICE);
         return nullptr;
     }
+    // Map the stream-arena pool up to the budget (at most a quarter of the free
+    // device memory) now, so that admitting a burst of streams later only
+    // sub-allocates; the pool keeps freed memory while any stream lives.
+    size_t free_b = 0, total_b = 0;
+    cudaMemPool_t pool = arena_pool(v->dev);
+    if (pool && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const size_t want = std::min(device_budget_bytes, free_b / 4);
+        void *p = nullptr;
+        if (want > 0 && cudaMallocFromPoolAsync(&p, want, pool, v->cs) == cudaSuccess) {
+            cudaFreeAsync(p, v->cs);
+            cudaStreamSynchronize(v->cs);
+        }
+    }
+    (void)cudaGetLastError();
     v->worker = std::thread(server_loop, v);
     return v;
 }

@@ -345,13 +345,15 @@ def meets_slo(r: dict) -> bool:
             r.get("dropped_queue_full", 0) <= DROP_BUDGET * offered)
 
 
-def sweep(bank: FrameBank, rates, duration: float, n_learn: int = N_LEARN, seed: int = 1907043935):
+def sweep(bank: FrameBank, rates, duration: float, n_learn: int = N_LEARN, seed: int = 1907043935,
+          budget_bytes: int = 1 << 50):
     """Served and plain forms over the same traces at each arrival-rate scale
-    (no memory limit on admission, so that only the serving form differs)."""
+    (a device budget no trace reaches, so that only the serving form
+    differs)."""
     rows = []
     for r in rates:
         tr = make_trace(duration, rate_scale=r, seed=seed + int(r * 1000))
-        srv = run_served(tr, bank, 1 << 50, n_learn)
+        srv = run_served(tr, bank, budget_bytes, n_learn)
         pln = run_plain(tr, bank, n_learn)
         rows.append({"rate_scale": r, "served": srv, "plain": pln})
     best = {}
