@@ -483,22 +483,25 @@ def run_ours(args) -> None:
 
     # ---- re-learning on every stream: its cost on the same workload -------
     relearn = None
-    if not args.no_relearn:
+    # (the extra measurements below run on one-GPU runs only: a multi-GPU run
+    # holds every GPU, and its line reports the scaled main workload)
+    extras = world == 1
+    if extras and not args.no_relearn:
         relearn = bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape_used, args)
 
     # ---- the Gaussian mixture background on every stream ------------------
     mixture = None
-    if not args.no_mixture and args.bg_model == "band":
+    if extras and not args.no_mixture and args.bg_model == "band":
         mixture = bench_mixture_cost(hmi, synth, torch, dev, cs, rings, shape_used, args)
 
     # ---- background quality under drift: band, re-learning, mixture -------
     quality = None
-    if args.quality_frames:
+    if extras and args.quality_frames:
         quality = bench_background_quality(hmi, synth, torch, dev, args.quality_frames)
 
     # ---- single 640x480 stream (the other configuration of the metric) ---
     single = None
-    if not args.no_single:
+    if extras and not args.no_single:
         single = bench_single(hmi, synth, torch, dev, cs, args, 2)
         single_hd = bench_single(hmi, synth, torch, dev, cs, args, 3)
 
