@@ -412,7 +412,7 @@ typedef struct {
  * streams; max_queue: frames a stream may have pending (1..64).  Creation maps
  * the library's stream-memory pool up to the budget (at most a quarter of the
  * free device memory), so that admitting a burst of streams later allocates
- * nothing new from the driver. */
+ * nothing new from the CUDA driver. */
 HMI_API hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue);
 HMI_API void hmi_server_destroy(hmi_server *srv);
 /* Create a stream (Sec. 2, initialisation) and reserve its device bytes in

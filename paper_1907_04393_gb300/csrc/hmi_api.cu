@@ -186,7 +186,7 @@ Layout make_layout(int w, int h, const hmi_params &p)
 // Stream state comes from a stream-ordered memory pool owned by the library
 // (one per device, memory kept while any stream lives), so that creating and
 // destroying streams, as a server admitting and retiring cameras does, needs
-// neither the driver's allocator nor a device-wide synchronisation of its own.
+// neither the CUDA driver's allocator nor a device-wide synchronisation of its own.
 struct ArenaPools {
     std::mutex mu;
     cudaMemPool_t pool[64] = {};
