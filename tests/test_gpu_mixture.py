@@ -198,3 +198,19 @@ def test_mixture_api_errors():
     assert e.value.status == hmi.HMI_ERR_INVALID_ARG
     band.close()
     mix.close()
+
+
+def test_mixture_full_hd_stream():
+    """The third configuration's 1920x1080 stream (two hands, drift, flicker)
+    with the mixture: learning from its 30 frames and two running frames give
+    the oracle's whole mixture state, masks, labels and pointers."""
+    w, h = synth.shape(3)
+    g, o = pair(w, h, bg_model=1, mix_k=3)
+    lf = synth.learn_frames(3)
+    g.learn(_dev(lf))
+    o.learn(lf)
+    _check_mix(g, o, "1080p learned")
+    for t in (0, 1):
+        check_frame(g, o, synth.run_frame(3, 0, t), dev=t == 1, what=f"1080p t={t}")
+    _check_mix(g, o, "1080p after 2 frames")
+    g.close()
