@@ -1,12 +1,19 @@
 // hmi_api.cu -- host implementation of the C ABI declared in include/hmi.h.
 //
-// A stream owns one device arena (all of its buffers, allocated at creation)
-// and a one-stream launch plan.  A launch plan (hmi_batch) owns the device
-// tables the tick kernels read (stream descriptors, work pieces, prefix sums),
-// a ring of per-tick pointer slots (pinned host mirror + device copy + event),
-// and optionally one CUDA graph per slot that replays the whole tick: the
-// slot's pointer upload, then the luma, classification, morphology + block
-// components, and per-stream finish (merge, resolve, pointer) kernels.
+// A stream owns one device arena (all of its buffers, taken from a
+// library-owned stream-ordered memory pool at creation) and, once learned, a
+// one-stream launch plan.  A launch plan (hmi_batch) owns the device tables
+// the tick kernels read (stream descriptors, work pieces, prefix sums), a ring
+// of per-tick pointer slots (pinned host mirror + device copy + event), and
+// optionally one CUDA graph per slot that replays the whole tick: the slot's
+// pointer upload, then the luma (which also brings pinned host frames over),
+// band test or mixture, re-learning, gray/hue, morphology + block components
+// and per-stream finish (merge, resolve, pointer, interface event) kernels.
+//
+// In order below: layouts and the pool; plans (build, re-plan, groups,
+// graphs, pipelined stages); ticks (slot preparation, synchronous,
+// asynchronous and pipelined forms, tuning and autotuning); learning; the
+// server (admission, rounds, batched learning); the exported C functions.
 #include <cuda_runtime.h>
 
 #include <algorithm>
