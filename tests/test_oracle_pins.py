@@ -871,3 +871,40 @@ def test_mixture_variance_tracks_the_mean_squared_deviation():
             mean += (x - mean) / (i + 1)
     exact = (Fraction(3600) + tot) / n
     assert abs(int(m.V[0, 0]) - exact) <= Fraction(n + 1, 4) + 10
+
+
+def test_mixture_variance_clamps_at_both_ends():
+    """A constant value drives V down to exactly Vmin = 16 sigma_min^2 and
+    keeps it there; one far value that still matches (lambda 15) pulls V up to
+    the 65535 ceiling."""
+    m = _mix(s0=15, smin=2)
+    x = np.array([[90, 100, 110]], np.uint8)
+    for _ in range(200):
+        m.step(x)
+    assert int(m.V[0, 0]) == 16 * 2 * 2
+    m = _mix(ln=15, ld=1, s0=63, smin=1, N=1)
+    m.step(np.array([[0, 0, 0]], np.uint8))
+    m.step(np.array([[255, 255, 255]], np.uint8))      # D / 3 = 255^2 * 16 > 65535
+    assert int(m.C[0, 0]) == 2 and int(m.V[0, 0]) == 65535
+
+
+def test_mixture_match_count_saturates():
+    m = _mix(N=8)
+    x = np.array([[10, 200, 30]], np.uint8)
+    for _ in range(65540):
+        m.step(x, classify=False)
+    assert int(m.C[0, 0]) == 65535
+    assert int(m.W[0, 0]) == 32768 and (m.M[0, :, 0] == 256 * x[0].astype(np.uint16)).all()
+
+
+def test_mixture_learning_is_the_update_without_decisions():
+    """orc_mixture_learn from an empty model equals stepping the same frames
+    one by one (t = 1..n) with no background decisions."""
+    rng = np.random.default_rng(21)
+    frames = rng.integers(0, 256, size=(9, 5, 7, 3), dtype=np.uint8) // 32 * 32
+    a, b = _mix(npx=35, K=4, N=4, s0=9), _mix(npx=35, K=4, N=4, s0=9)
+    a.learn(frames)
+    for f in frames:
+        b.step(f, classify=False)
+    assert a.t == b.t == 9
+    assert np.array_equal(a.planes(), b.planes())
