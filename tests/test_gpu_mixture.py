@@ -214,3 +214,32 @@ def test_mixture_full_hd_stream():
         check_frame(g, o, synth.run_frame(3, 0, t), dev=t == 1, what=f"1080p t={t}")
     _check_mix(g, o, "1080p after 2 frames")
     g.close()
+
+
+def test_mixture_extremes():
+    """Counts saturate (65535 learning frames), variances reach both clamps
+    (a constant pixel decays to Vmin; a far value that still matches with
+    lambda 15 and sigma0 63 clamps at 65535): the GPU state equals the oracle's."""
+    rng = np.random.default_rng(8)
+    w, h, n = 8, 8, 65535
+    base = rng.integers(0, 51, size=(1, h, w, 3), dtype=np.uint8)
+    lf = np.repeat(base, n, axis=0)
+    # rows 0-3 end with a far value F (a new component, V0) and then F - 100,
+    # which only that component matches: its variance jumps to the ceiling;
+    # rows 4-7 stay constant: their count saturates, their variance is Vmin
+    lf[-2, :4] = 255 - base[0, :4]
+    lf[-1, :4] = 155 - base[0, :4]
+    over = dict(bg_model=1, mix_k=2, mix_rate_n=1, bg_k_num=15, bg_k_den=1, mix_sigma0=63,
+                mix_sigma_min=1)
+    g, o = pair(w, h, **over)
+    g.learn(lf)
+    o.learn(lf)
+    _check_mix(g, o, "extremes learned")
+    planes = o.mix.planes()
+    assert planes[5 * 2:].max() == 65535                # some count saturated
+    assert planes[4 * 2:5 * 2].max() == 65535           # some variance at the ceiling
+    for t in range(3):
+        f = np.ascontiguousarray(base[0] if t % 2 == 0 else 255 - base[0])
+        check_frame(g, o, f, what=f"extremes t={t}")
+    _check_mix(g, o, "extremes after 3 frames")
+    g.close()
