@@ -220,6 +220,25 @@ def test_luma8_close_to_bt601():
         assert abs(y - ref) <= 1.5
 
 
+def test_luma8_hand_worked_fixture(golden_dir):
+    """Hand-worked luma values where the rounding term of the integer luma
+    decides the result, and a small frame's exact luma sum."""
+    rows = [[c.strip() for c in r.split("|")] for r in _golden_rows(golden_dir, "luma_rounding.txt")]
+    decided = 0
+    for row in rows:
+        if row[0].startswith("frame"):
+            _, h, w = row[0].split()
+            px = [tuple(map(int, p.split())) for line in row[1].split(";") for p in line.split(",")]
+            frame = np.array(px, np.uint8).reshape(int(h), int(w), 3)
+            assert oracle.luma_sum(frame) == int(row[2])
+            continue
+        r, g, b = map(int, row[0].split())
+        assert 77 * r + 150 * g + 29 * b + 128 == int(row[1]), row   # the fixture's own arithmetic
+        assert oracle.luma_sum(np.array([[[r, g, b]]], np.uint8)) == int(row[2]), row
+        decided += row[3].startswith("r")
+    assert decided >= 6
+
+
 def test_ref_luma_is_floor_of_mean():
     f = RNG.integers(0, 256, size=(7, 9, 11, 3), dtype=np.uint8)
     sums = [oracle.luma_sum(x) for x in f]
@@ -436,6 +455,23 @@ def test_click_state_machine_hand_worked():
                           label=0), 80, 90)["click"] for a in (100, 100, 70, 70, 70)]
     # A_ref: -,100,100,100(hist 100,70),70(hist 70,70): 7000 > 6300 -> clear
     assert out == [0, 0, 1, 1, 0]
+
+
+def test_click_state_machine_strict_boundaries():
+    """The click is set only when 100*area is strictly below on_pct*A_ref and
+    cleared only when strictly above off_pct*A_ref: equality changes nothing."""
+    def run(areas, on, off, window=30):
+        st = oracle.ClickState(window)
+        return [st.update(dict(valid=1, click=0, x=0.0, y=0.0, area=a, x0=0, y0=0, x1=0, y1=0,
+                               label=0), on, off)["click"] for a in areas]
+    # A_ref stays 100: 8000 == 80*100 keeps 0; 5000 < 8000 sets; 9000 == 90*100
+    # keeps 1; 9100 > 9000 clears
+    assert run([100, 80, 50, 90, 91], 80, 90) == [0, 0, 1, 1, 0]
+    # one unit either side of each boundary
+    assert run([100, 79], 80, 90) == [0, 1]
+    assert run([100, 50, 91], 80, 90) == [0, 1, 0]
+    # on and off at the same percentage: equality neither sets nor clears
+    assert run([200, 150, 100, 150, 151], 75, 75) == [0, 0, 1, 1, 0]
 
 
 # --------------------------------------------------------------------------- #
