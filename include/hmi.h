@@ -471,16 +471,24 @@ HMI_API int hmi_server_rounds(hmi_server *srv, hmi_server_round *out, int max_ro
  * device, or a host program that owns all device memory through its own pool.
  * It returns, in *gain_out (device memory, one uint32), the same clamped Q16
  * gain round(syref / SY) that hmi_process_frame applies, SY being the frame's
- * integer luma sum.  frame: device memory, h rows of 3*w bytes.  The work runs
- * on cuda_stream (NULL = legacy default stream); the result is ready when that
+ * integer luma sum.  frame: h rows of 3*w bytes that the current device can
+ * read (its device memory, managed memory, or pinned / registered host memory);
+ * gain_out: device or managed memory of the current device, 4-byte aligned.
+ * Anything else, and syref > 255*w*h (larger than any frame of this size can
+ * sum to), is rejected with HMI_ERR_INVALID_ARG before any work is enqueued;
+ * every error is also recorded for hmi_last_error.  The work runs on
+ * cuda_stream (NULL = legacy default stream); the result is ready when that
  * stream reaches this point.
  * Scratch: a fixed 32 KiB array built into the library, one copy per GPU that
  * loads it, kept until the process exits.  Frames of more than 4,194,304
  * sixteen-pixel row chunks (h * ceil(w/16); 8192 x 8192 is the largest square)
- * and w or h beyond 8192 are rejected with HMI_ERR_INVALID_ARG.  The first
- * call on a device looks up that device's scratch address, so make it before
- * any stream capture.  All calls share the scratch: calls that overlap on the
- * GPU race and must be serialised by the caller.  Calls no allocator. */
+ * and w or h beyond 8192 are rejected with HMI_ERR_INVALID_ARG.  A call outside
+ * a stream capture looks up the current device's scratch address afresh; a
+ * call made while cuda_stream is capturing reuses the address found by the
+ * last call outside one, so make at least one call on the device before any
+ * capture (and one after a device reset before capturing again).  All calls
+ * share the scratch: calls that overlap on the GPU race and must be serialised
+ * by the caller.  Calls no allocator. */
 HMI_API int hmi_frame_gain_noalloc(const uint8_t *frame, int w, int h, uint64_t syref,
                                    uint32_t gain_min_q16, uint32_t gain_max_q16,
                                    uint32_t *gain_out, void *cuda_stream);

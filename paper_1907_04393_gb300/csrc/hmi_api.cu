@@ -54,6 +54,13 @@ int cuda_fail(cudaError_t e)
     return fail(HMI_ERR_DEVICE);
 }
 
+}  // namespace
+
+// Thread-local status of the last failed call, for the other translation units.
+int hmi::set_error(int status) { return fail(status); }
+
+namespace {
+
 #define HMI_CUDA(call)                               \
     do {                                             \
         cudaError_t e_ = (call);                     \

@@ -194,6 +194,10 @@ constexpr int kPhases = 3;
 // Threads per CTA of every kernel of a tick.
 constexpr int kThreads = 256;
 
+// Records `status` as the calling thread's last error (hmi_last_error) and
+// returns it (hmi_api.cu).
+int set_error(int status);
+
 // ---------------------------------------------------------------------------
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)
 // ---------------------------------------------------------------------------

@@ -105,19 +105,43 @@ k_frame_gain_noalloc(const uint8_t *__restrict__ frame, int w, int h, int vec, l
 std::mutex g_na_mu;
 void *g_na_ptr[kNaMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
-cudaError_t na_scratch(int dev, unsigned long long **out)
+// Device address of the scratch array on device `dev` (current).  Outside a
+// stream capture it is looked up on every call, so that a device reset or a
+// new primary context never leaves a stale address behind; inside a capture
+// the address found by the last call outside one is used (none yet: an error,
+// since the lookup may have to load the module, which a capture forbids).
+cudaError_t na_scratch(int dev, cudaStream_t cs, unsigned long long **out)
 {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(cs, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess) return e;
         g_na_ptr[dev] = p;
+    } else if (!g_na_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = static_cast<unsigned long long *>(g_na_ptr[dev]);
     return cudaSuccess;
+}
+
+// Memory that a kernel on device `dev` may read (device_only false: device or
+// managed memory of that device, or pinned / registered host memory mapped at
+// the same address) or write (device_only true: device or managed memory of
+// that device only).
+bool na_reachable(const void *p, int dev, bool device_only)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return !device_only && at.type == cudaMemoryTypeHost && at.devicePointer == p;
 }
 
 }  // namespace
@@ -129,30 +153,35 @@ extern "C" int hmi_frame_gain_noalloc(const uint8_t *frame, int w, int h, uint64
 {
     using namespace hmi;
     if (!frame || !gain_out || w < 1 || h < 1 || w > kMaxDim || h > kMaxDim ||
-        gain_min_q16 > gain_max_q16 || gain_max_q16 > (1u << 24))
-        return HMI_ERR_INVALID_ARG;
+        gain_min_q16 > gain_max_q16 || gain_max_q16 > (1u << 24) ||
+        (reinterpret_cast<uintptr_t>(gain_out) & 3u) != 0 ||
+        syref > 255ull * (uint64_t)w * (uint64_t)h)   // no frame of this size has a larger luma sum
+        return set_error(HMI_ERR_INVALID_ARG);
     const long long chunks = (long long)h * ((w + 15) / 16);
-    if (chunks > (long long)kNaCtas * kNaChunksPerCta) return HMI_ERR_INVALID_ARG;
+    if (chunks > (long long)kNaCtas * kNaChunksPerCta) return set_error(HMI_ERR_INVALID_ARG);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
         (void)cudaGetLastError();
-        return HMI_ERR_DEVICE;
+        return set_error(HMI_ERR_DEVICE);
     }
-    unsigned long long *scratch = nullptr;
-    if (na_scratch(dev, &scratch) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return HMI_ERR_DEVICE;
-    }
+    // the frame must be readable and the gain writable by this device's kernels
+    if (!na_reachable(frame, dev, false) || !na_reachable(gain_out, dev, true))
+        return set_error(HMI_ERR_INVALID_ARG);
     cudaStream_t cs = reinterpret_cast<cudaStream_t>(cuda_stream);
+    unsigned long long *scratch = nullptr;
+    if (na_scratch(dev, cs, &scratch) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return set_error(HMI_ERR_DEVICE);
+    }
     // the completion counter must start at zero even if an earlier call was cut short
     if (cudaMemsetAsync(scratch + kNaCounter, 0, sizeof(unsigned long long), cs) != cudaSuccess) {
         (void)cudaGetLastError();
-        return HMI_ERR_DEVICE;
+        return set_error(HMI_ERR_DEVICE);
     }
     const int vec = ((w % 16) == 0 && (reinterpret_cast<uintptr_t>(frame) & 15u) == 0) ? 1 : 0;
     const unsigned grid = (unsigned)((chunks + kNaChunksPerCta - 1) / kNaChunksPerCta);
     k_frame_gain_noalloc<<<grid, 256, 0, cs>>>(frame, w, h, vec, chunks, syref, gain_min_q16,
                                                gain_max_q16, gain_out, scratch);
-    if (cudaGetLastError() != cudaSuccess) return HMI_ERR_DEVICE;
+    if (cudaGetLastError() != cudaSuccess) return set_error(HMI_ERR_DEVICE);
     return HMI_OK;
 }
