@@ -205,6 +205,15 @@ HMI_API void hmi_batch_destroy(hmi_batch *b);
 HMI_API int hmi_batch_set_groups(hmi_batch *b, int groups);
 HMI_API int hmi_batch_get_groups(const hmi_batch *b);
 
+/* Failure detection: the bound on every bounded device loop and wait of the
+ * batch's ticks (union-find steps of the component merge, the persistent
+ * tick's waits for a stream's earlier steps).  0 restores the default, 2^22.
+ * A loop that runs out sets the stream's error flag and lets the tick end;
+ * the next synchronous call returns HMI_ERR_DEVICE_TIMEOUT (that frame's
+ * results are not to be trusted) and clears it.  Re-makes the plan (waits for
+ * the device).  Lowering it lets a test make a loop run out without any fault. */
+HMI_API int hmi_batch_set_loop_limit(hmi_batch *b, uint32_t limit);
+
 /* Process one frame per stream of the batch.  Synchronous form: buffers may be
  * host or device; frames[i] is the frame of the i-th stream given at creation.
  * masks / ptrs as in hmi_process_batch.  A frame in pinned (page-locked) host
@@ -228,13 +237,25 @@ HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, 
 
 /* Launch shape of a batch's ticks.  piece_chunks: 16-pixel chunks per CTA
  * work piece of the per-pixel kernels (the tile; a multiple of 32 in
- * 32..65536, default 512); luma_ctas_per_sm: CTAs per SM of the luma pass
- * (0 = as many as fit, else 1..32); skin_ctas_per_sm, cc_ctas_per_sm: grid
- * of the gray/hue pass and of the block-component pass, in CTAs per SM
- * (1..32, default 8); groups: stream groups of plain ticks (0 = min(2, n),
- * else 1..64); pipeline_depth: stages of a pipelined tick (2 or 3, see
- * hmi_batch_process_pipelined; default 2).  Results never depend on the
- * tuning. */
+ * 32..65536, default 512); luma_ctas_per_sm: CTAs per SM of the luma pass,
+ * and of the persistent tick below (0 = as many as fit, else 1..32);
+ * skin_ctas_per_sm, cc_ctas_per_sm: grid of the gray/hue pass and of the
+ * block-component pass, in CTAs per SM (1..32, default 8); groups: stream
+ * groups of plain ticks (0 = one when every stream can use the persistent
+ * tick, else min(2, n); or 1..64); pipeline_depth: stages of a pipelined
+ * tick (2 or 3, see hmi_batch_process_pipelined; default 2).
+ * fused (default 1): a group whose streams all use the background band
+ * (bg_model 0) with the same open_iters + close_iters, at most 4, runs its whole tick in one
+ * persistent launch, whose CTAs take work items from a queue in order (per
+ * stream: luma sums, then band / gray / hue tests, then morphology and block
+ * components, then the merge of the components into the pointer), each item
+ * waiting (bounded) only for the stream's items of the step before; 0 runs
+ * the chain of kernels of HMI_TICK_KERNELS.  queue_lag: queue positions
+ * between a stream's last item of one step and its first of the next
+ * (0 = twice the persistent grid, else 1..2^20); merge_defer: 1 puts every
+ * stream's merge at the end of the queue (the merge schedule of the
+ * components), 0 right after its blocks (default).  Results never depend on
+ * the tuning. */
 typedef struct {
     int32_t piece_chunks;
     int32_t luma_ctas_per_sm;
@@ -242,6 +263,9 @@ typedef struct {
     int32_t cc_ctas_per_sm;
     int32_t groups;
     int32_t pipeline_depth;
+    int32_t fused;
+    int32_t queue_lag;
+    int32_t merge_defer;
 } hmi_tuning;
 
 /* Replace the batch's launch shape (re-makes the plan; waits for the device).
@@ -294,7 +318,9 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
  * hmi_batch_profile_kernels waits for them and gives the number of ticks timed
  * and, for the first n_kernels kernels (1..HMI_TICK_KERNELS), the sum of their
  * durations in milliseconds; hmi_batch_profile_read gives that sum for kernel
- * 1 alone. */
+ * 1 alone.  With the persistent tick (hmi_tuning.fused), kernel 0 is the
+ * whole tick but re-learning (kernels 3 and 4), the other kernels launch
+ * nothing, and hmi_batch_profile_read gives kernel 0. */
 #define HMI_TICK_KERNELS 9
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
 HMI_API int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels);

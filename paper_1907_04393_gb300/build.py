@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libhmi.so")
-SOURCES = ["hmi_frame.cu", "hmi_cc.cu", "hmi_learn.cu", "hmi_mix.cu", "hmi_api.cu", "hmi_noalloc.cu"]
+SOURCES = ["hmi_frame.cu", "hmi_tick.cu", "hmi_cc.cu", "hmi_learn.cu", "hmi_mix.cu", "hmi_api.cu",
+           "hmi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-fvisibility=hidden"]

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "hmi_internal.cuh"
+#include "hmi_queue.h"
 
 using namespace hmi;
 
@@ -70,9 +71,10 @@ namespace {
 constexpr int kRing = 12;         // per-tick pointer slots of a launch plan (a multiple of kPhases)
 // Default launch shape (hmi_tuning): 16-px chunks per CTA piece of the
 // per-pixel kernels (512 = 8192 px), luma CTAs per SM (0 = as many as fit),
-// skin-test and block-component CTAs per SM, stream groups (0 = min(2, n)),
-// stages of a pipelined tick.
-constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2};
+// skin-test and block-component CTAs per SM, stream groups (0 = by the
+// streams, see default_groups), stages of a pipelined tick, the persistent
+// tick on, its queue lag chosen from the grid, merges interleaved.
+constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2, 1, 0, 0};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -288,6 +290,7 @@ struct hmi_batch {
     int dev = 0;
     int n = 0;
     hmi_tuning tune{};            // launch shape of the plan
+    uint32_t loop_limit = 0;      // bound of the device loops (0: kLoopLimit)
     int cap = 0;                  // streams the per-batch buffers hold
     size_t plan_cap = 0;          // bytes of the plan table buffer
     std::vector<hmi_stream *> s;  // user order
@@ -533,8 +536,15 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<uint32_t> tpre, bpre, spre;
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
+        bool any_mix = false;
         size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn[kPhases], o_skl[kPhases];
+        // persistent tick: work queue and per-stream progress
+        bool fused = false;
+        std::vector<int4> items;
+        std::vector<TickSync> sync;
+        size_t o_items = 0, o_sync = 0, o_head = 0;
     };
+    const long long tick_grid = (long long)b->num_sms * tick_ctas_per_sm(b->tune.luma_ctas_per_sm);
     std::vector<Tables> T(ng);
     Arena a;
     const size_t o_ds = a.take(sizeof(DevStream) * n);
@@ -559,6 +569,21 @@ int plan_build(hmi_batch *b, int ng)
             t.uniform_halo = (t.uniform_halo == -2 || t.uniform_halo == halo) ? halo : -1;
             for (int c = 0; c < chunks; c += b->tune.piece_chunks)
                 t.pieces.push_back(make_int4(k, c, std::min(chunks, c + b->tune.piece_chunks), 0));
+            if (L.mix_k) t.any_mix = true;
+        }
+        t.fused = b->tune.fused && !t.any_mix && t.uniform_halo >= 0 && t.uniform_halo <= kStripMaxHalo;
+        if (t.fused) {
+            std::vector<int> ch(m), sp(m);
+            for (int k = 0; k < m; ++k) {
+                const Layout &L = b->s[perm[b->groups[g].off + k]]->L;
+                ch[k] = L.h * 2 * L.nwords;
+                sp[k] = L.bh * L.strips_x;
+            }
+            const long long lag = b->tune.queue_lag > 0 ? b->tune.queue_lag : 2 * tick_grid;
+            t.items = tick_queue(ch, sp, b->tune.piece_chunks, lag, b->tune.merge_defer != 0, &t.sync);
+            t.o_items = a.take(sizeof(int4) * t.items.size());
+            t.o_sync = a.take(sizeof(TickSync) * m);
+            t.o_head = a.take(sizeof(uint32_t) * 2);
         }
         t.o_c = a.take(sizeof(unsigned long long) * (m + 1));
         t.o_t = a.take(sizeof(uint32_t) * (m + 1));
@@ -603,6 +628,9 @@ int plan_build(hmi_batch *b, int ng)
              cudaMemcpyAsync(A + t.o_b, t.bpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
              cudaMemcpyAsync(A + t.o_s, t.spre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
              cudaMemcpyAsync(A + t.o_p, t.pieces.data(), sizeof(int4) * t.pieces.size(), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+             (!t.fused ||
+              (cudaMemcpyAsync(A + t.o_items, t.items.data(), sizeof(int4) * t.items.size(), cudaMemcpyHostToDevice, up) == cudaSuccess &&
+               cudaMemcpyAsync(A + t.o_sync, t.sync.data(), sizeof(TickSync) * m, cudaMemcpyHostToDevice, up) == cudaSuccess)) &&
              (G.cs || cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) == cudaSuccess) &&
              (G.ev_luma || cudaEventCreateWithFlags(&G.ev_luma, cudaEventDisableTiming) == cudaSuccess) &&
              (G.ev_done || cudaEventCreateWithFlags(&G.ev_done, cudaEventDisableTiming) == cudaSuccess);
@@ -640,6 +668,13 @@ int plan_build(hmi_batch *b, int ng)
             if (sk->L.mix_k) bd.any_mix |= 1 << sk->L.mix_k;
             else bd.any_band = 1;
         }
+        bd.fused = t.fused ? 1 : 0;
+        bd.items = t.fused ? reinterpret_cast<const int4 *>(A + t.o_items) : nullptr;
+        bd.nitems = t.fused ? (int)t.items.size() : 0;
+        bd.sync = t.fused ? reinterpret_cast<TickSync *>(A + t.o_sync) : nullptr;
+        bd.tick_head = t.fused ? reinterpret_cast<uint32_t *>(A + t.o_head) : nullptr;
+        bd.tick_exit = t.fused ? bd.tick_head + 1 : nullptr;
+        bd.loop_limit = b->loop_limit ? b->loop_limit : kLoopLimit;
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
         bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
         bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
@@ -688,6 +723,17 @@ bool batch_alloc_io(hmi_batch *b, int cap)
     b->d_err = reinterpret_cast<uint32_t *>(b->arena + o_err);
     b->cap = cap;
     return true;
+}
+
+// Stream groups of a plan left at groups = 0: one when every stream can run
+// in the persistent tick (band streams: a group's persistent launch already
+// fills the GPU), else two overlapping chains.
+int default_groups(hmi_stream *const *s, int n, const hmi_tuning &t)
+{
+    bool fusable = t.fused != 0;
+    for (int i = 0; i < n && fusable; ++i)
+        fusable = s[i]->L.mix_k == 0 && 2 * (s[i]->p.open_iters + s[i]->p.close_iters) <= kStripMaxHalo;
+    return fusable ? 1 : std::min(2, n);
 }
 
 hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
@@ -811,10 +857,13 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
 // {gray/hue, morphology, blocks, finish}; depth 3: {luma} {band test, mixture,
 // re-learning} {gray/hue .. finish}.  The first stages are bandwidth-bound, the last is
 // latency-bound; the band is only read and re-formed in the middle stage.
-void stage_bounds(int depth, int *first)
+void stage_bounds(int depth, int *first, bool fused)
 {
     constexpr int kTail = kTickTail;   // first kernel of the latency-bound tail (gray/hue tests)
-    if (depth >= 3) {
+    if (fused) {   // the persistent tick is one launch: the whole tick is the first stage
+        first[0] = 0;
+        for (int j = 1; j <= kPhases; ++j) first[j] = kTickKernels;
+    } else if (depth >= 3) {
         first[0] = 0;
         first[1] = 1;
         first[2] = kTail;
@@ -833,7 +882,7 @@ void stage_bounds(int depth, int *first)
 cudaError_t enqueue_pipelined(hmi_batch *b, int slot, const int *pend, int npend, int depth, cudaStream_t cs)
 {
     int first[kPhases + 1];
-    stage_bounds(depth, first);
+    stage_bounds(depth, first, b->groups[0].bd.fused != 0);
     cudaStream_t side[kPhases - 1] = {b->groups[0].cs, b->cs2};
     cudaError_t e;
     if (npend > 0 && (e = cudaEventRecord(b->ev_fork, cs)) != cudaSuccess) return e;
@@ -879,7 +928,7 @@ int flush_pending(hmi_batch *b, cudaStream_t cs)
 {
     if (b->npend == 0) return HMI_OK;
     int first[kPhases + 1];
-    stage_bounds(b->pend_depth, first);
+    stage_bounds(b->pend_depth, first, b->groups[0].bd.fused != 0);
     const int npend = b->npend;
     b->npend = 0;
     HMI_CUDA(cudaStreamWaitEvent(cs, b->pipe_ev, 0));
@@ -1136,14 +1185,14 @@ int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *
     return HMI_OK;
 }
 
-int default_groups(int n) { return std::min(2, n); }
-
 bool tuning_ok(const hmi_tuning &t)
 {
     return t.piece_chunks >= 32 && t.piece_chunks <= 65536 && t.piece_chunks % 32 == 0 &&
            t.luma_ctas_per_sm >= 0 && t.luma_ctas_per_sm <= 32 && t.skin_ctas_per_sm >= 1 &&
            t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
-           t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases;
+           t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases &&
+           (t.fused == 0 || t.fused == 1) && t.queue_lag >= 0 && t.queue_lag <= (1 << 20) &&
+           (t.merge_defer == 0 || t.merge_defer == 1);
 }
 
 // Apply a launch shape: the plan is re-made with the device idle.
@@ -1157,7 +1206,7 @@ int batch_retune(hmi_batch *b, const hmi_tuning &t)
     plan_free(b);
     for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
     b->tune = t;
-    return plan_build(b, t.groups > 0 ? t.groups : default_groups(b->n));
+    return plan_build(b, t.groups > 0 ? t.groups : default_groups(b->s.data(), b->n, t));
 }
 
 // Microseconds per tick of `ticks` ticks of `frames` with the current plan
@@ -2241,9 +2290,19 @@ int hmi_process_frame_async(hmi_stream *s, const uint8_t *frame, uint8_t *mask_o
     return batch_async(s->self, &frame, masks, pointer_out, cuda_stream, 0);
 }
 
-hmi_batch *hmi_batch_create(hmi_stream *const *s, int n) { return batch_new(s, n, default_groups(n)); }
+hmi_batch *hmi_batch_create(hmi_stream *const *s, int n)
+{
+    return streams_ok(s, n) ? batch_new(s, n, default_groups(s, n, kDefaultTuning)) : batch_new(s, n, 1);
+}
 
 int hmi_batch_set_groups(hmi_batch *b, int groups) { return batch_set_groups(b, groups); }
+
+int hmi_batch_set_loop_limit(hmi_batch *b, uint32_t limit)
+{
+    if (!b) return fail(HMI_ERR_INVALID_ARG);
+    b->loop_limit = limit;
+    return batch_retune(b, b->tune);
+}
 
 int hmi_batch_get_groups(const hmi_batch *b)
 {
@@ -2305,7 +2364,7 @@ int hmi_process_batch(hmi_stream *const *s, int n, const uint8_t *const *frames,
     std::lock_guard<std::mutex> lk(g_cache_mu);
     if (!g_cache || g_cache->n != n || !std::equal(g_cache->s.begin(), g_cache->s.end(), s)) {
         batch_free(g_cache);
-        g_cache = batch_new(s, n, default_groups(n));
+        g_cache = batch_new(s, n, streams_ok(s, n) ? default_groups(s, n, kDefaultTuning) : 1);
         if (!g_cache) return g_last_error;
     }
     return batch_sync(g_cache, frames, masks, ptrs);
@@ -2351,7 +2410,7 @@ int hmi_batch_profile_read(hmi_batch *b, int *ticks, double *total_ms)
     double ms[HMI_TICK_KERNELS];
     const int st = hmi_batch_profile_kernels(b, ticks, ms, HMI_TICK_KERNELS);
     if (st != HMI_OK) return st;
-    *total_ms = ms[1];
+    *total_ms = b->groups[0].bd.fused ? ms[0] : ms[1];   // the per-pixel HBM pass
     return HMI_OK;
 }
 

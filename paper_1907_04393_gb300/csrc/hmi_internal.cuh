@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "hmi.h"
+#include "hmi_queue.h"
 
 namespace hmi {
 
@@ -182,7 +183,15 @@ struct BatchDev {
     int relearn;                              // some stream of the batch re-learns
     int any_band;                             // some stream has the band test
     int any_mix;                              // bit K: some stream has a K-component mixture
-    int luma_ctas_per_sm;                     // 0: as many as fit
+    uint32_t loop_limit;                      // steps of every bounded device loop (0: kLoopLimit)
+    // persistent tick (fused != 0): the whole path of the group in one launch
+    int fused;
+    const int4 *items;                        // work queue, in order
+    int nitems;
+    TickSync *sync;                           // per stream
+    uint32_t *tick_head;                      // next item to take
+    uint32_t *tick_exit;                      // CTAs that have left the launch
+    int luma_ctas_per_sm;                     // 0: as many as fit (also the persistent grid)
     int skin_ctas_per_sm;
     int cc_ctas_per_sm;
 };
@@ -228,6 +237,10 @@ __host__ __device__ inline bool relearn_window(uint32_t f, int period, int frame
     return frames > 0 && period > 0 && f > 0 && (int)((f - 1) % (uint32_t)period) >= period - frames;
 }
 cudaError_t launch_morph(const BatchDev &b, cudaStream_t cs, int num_sms);
+// The persistent tick (hmi_tick.cu), and the CTAs per SM its grid has for a
+// requested number (0: as many as fit).
+cudaError_t launch_tick(const BatchDev &b, cudaStream_t cs, int num_sms);
+int tick_ctas_per_sm(int requested);
 cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms);
 cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs);
 cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int num_sms);

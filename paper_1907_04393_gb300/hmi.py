@@ -85,7 +85,9 @@ class hmi_event(ctypes.Structure):
 class hmi_tuning(ctypes.Structure):
     _fields_ = [("piece_chunks", ctypes.c_int32), ("luma_ctas_per_sm", ctypes.c_int32),
                 ("skin_ctas_per_sm", ctypes.c_int32), ("cc_ctas_per_sm", ctypes.c_int32),
-                ("groups", ctypes.c_int32), ("pipeline_depth", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("pipeline_depth", ctypes.c_int32),
+                ("fused", ctypes.c_int32), ("queue_lag", ctypes.c_int32),
+                ("merge_defer", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +121,7 @@ SIGNATURES = {
     "hmi_batch_process": (_I, [_P, _P, _P, _P]),
     "hmi_batch_process_async": (_I, [_P, _P, _P, _P, _P, _I]),
     "hmi_batch_set_groups": (_I, [_P, _I]),
+    "hmi_batch_set_loop_limit": (_I, [_P, ctypes.c_uint32]),
     "hmi_batch_get_groups": (_I, [_P]),
     "hmi_batch_set_tuning": (_I, [_P, ctypes.POINTER(hmi_tuning)]),
     "hmi_batch_get_tuning": (_I, [_P, ctypes.POINTER(hmi_tuning)]),
@@ -318,6 +321,11 @@ def hmi_batch_process_pipelined(b: int, frames, masks, ptrs, cuda_stream: int, u
 
 def hmi_batch_flush(b: int, cuda_stream: int) -> None:
     _check(load().hmi_batch_flush(b, cuda_stream), "hmi_batch_flush")
+
+
+def hmi_batch_set_loop_limit(b: int, limit: int) -> None:
+    """Bound of the batch's device loops and waits (0: the default)."""
+    _check(load().hmi_batch_set_loop_limit(b, limit), "hmi_batch_set_loop_limit")
 
 
 def hmi_batch_set_groups(b: int, groups: int) -> None:

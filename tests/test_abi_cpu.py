@@ -30,7 +30,7 @@ def test_struct_layouts():
     assert ctypes.sizeof(hmi.hmi_pointer) == 40
     assert ctypes.sizeof(hmi.hmi_server_result) == 72
     assert ctypes.sizeof(hmi.hmi_server_round) == 56
-    assert ctypes.sizeof(hmi.hmi_tuning) == 24
+    assert ctypes.sizeof(hmi.hmi_tuning) == 36
     assert ctypes.sizeof(hmi.hmi_interface) == 4 + 16 * 20 + 6 * 4
     assert ctypes.sizeof(hmi.hmi_event) == 32
 

@@ -269,14 +269,18 @@ def _compare_batch(gs, os_, frames, masks_g, ptrs_g, what):
         assert_pointer(ptrs_g[i], p_o, f"{what} stream {i}")
 
 
-def test_batch_config4_sync_async_graph():
-    """64 mixed-resolution streams in one launch per stage; each stream's result
+@pytest.mark.parametrize("fused", [1, 0])
+def test_batch_config4_sync_async_graph(fused):
+    """64 mixed-resolution streams in one launch per tick (the persistent tick)
+    or one launch per stage (the chain of kernels); each stream's result
     equals its result alone (the oracle processes every stream alone)."""
     n = synth.num_streams(4)
     gs, os_ = _batch_streams(4, range(n))
     handles = [g.handle for g in gs]
     b = hmi.hmi_batch_create(handles)
     try:
+        hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=fused, groups=0))
+        assert hmi.hmi_batch_get_groups(b) == (1 if fused else 2)
         for t in range(4):
             frames = [synth.run_frame(4, i, t) for i in range(n)]
             mode = ("sync", "async", "graph", "graph")[t]
@@ -532,11 +536,13 @@ def test_checkpoint_roundtrip():
     b.close()
 
 
-def test_profile_counts_classification_kernel():
+@pytest.mark.parametrize("fused", [0, 1])
+def test_profile_counts_classification_kernel(fused):
     w, h = synth.shape(3)
     g = hmi.Stream(w, h)
     g.learn(_dev(synth.learn_frames(3, 0, 4)))
     b = hmi.hmi_batch_create([g.handle])
+    hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=fused))
     f = _dev(synth.run_frame(3, 0, 0))
     m = torch.empty((h, w), dtype=torch.uint8, device="cuda")
     hmi.hmi_batch_profile(b, 5)
@@ -546,8 +552,12 @@ def test_profile_counts_classification_kernel():
     ticks, ms = hmi.hmi_batch_profile_read(b)
     assert ticks == 5 and 0 < ms / ticks < 5.0
     t2, per = hmi.hmi_batch_profile_kernels(b)
-    assert t2 == 5 and per["classify"] == pytest.approx(ms)
-    assert all(v > 0 for k, v in per.items() if k not in ("block_components", "relearn", "relearn_band"))
+    if fused:   # one persistent launch: the first kernel is the whole tick
+        assert t2 == 5 and per["luma"] == pytest.approx(ms)
+        assert all(v < per["luma"] for k, v in per.items() if k != "luma")
+    else:
+        assert t2 == 5 and per["classify"] == pytest.approx(ms)
+        assert all(v > 0 for k, v in per.items() if k not in ("block_components", "relearn", "relearn_band"))
     hmi.hmi_batch_destroy(b)
     g.close()
 
@@ -620,9 +630,23 @@ def test_tuning_does_not_change_results():
             hmi.hmi_batch_process(b, frames, masks, ptrs)
             plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
             _compare_batch(gs, os_, frames, masks, plist, f"tuned t={t}")
+        # the persistent tick with a small grid, small pieces, a short queue
+        # lag (classify items wait for the gain) and every merge deferred
+        for shape in ({"piece_chunks": 64, "luma_ctas_per_sm": 1, "fused": 1, "queue_lag": 3,
+                       "merge_defer": 1, "groups": 1},
+                      {"piece_chunks": 2048, "fused": 1, "queue_lag": 1 << 20, "groups": 2}):
+            hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), **shape))
+            for t in range(2, 4):
+                frames = [synth.run_frame(4, i, t) for i in idx]
+                masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+                ptrs = np.zeros(len(idx), hmi.POINTER_DTYPE)
+                hmi.hmi_batch_process(b, frames, masks, ptrs)
+                plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
+                _compare_batch(gs, os_, frames, masks, plist, f"persistent {shape} t={t}")
         for bad in ({"piece_chunks": 100}, {"piece_chunks": 0}, {"skin_ctas_per_sm": 0},
                     {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65},
-                    {"pipeline_depth": 1}, {"pipeline_depth": 4}):
+                    {"pipeline_depth": 1}, {"pipeline_depth": 4}, {"fused": 2},
+                    {"queue_lag": -1}, {"queue_lag": (1 << 20) + 1}, {"merge_defer": 3}):
             t = dict(hmi.hmi_batch_get_tuning(b), **bad)
             with pytest.raises(hmi.HmiError) as e:
                 hmi.hmi_batch_set_tuning(b, t)
