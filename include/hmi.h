@@ -244,18 +244,18 @@ HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, 
  * groups of plain ticks (0 = one when every stream can use the persistent
  * tick, else min(2, n); or 1..64); pipeline_depth: stages of a pipelined
  * tick (2 or 3, see hmi_batch_process_pipelined; default 2).
- * fused (default 1): a group whose streams all use the background band
- * (bg_model 0) with the same open_iters + close_iters, at most 4, runs its whole tick in one
- * persistent launch, whose CTAs take work items from a queue in order (per
- * stream: luma sums, then band / gray / hue tests, then morphology and block
- * components, then the merge of the components into the pointer), each item
+ * fused (default 0): with 1, a group whose streams all use the background band
+ * (bg_model 0) with the same open_iters + close_iters, at most 2, runs the
+ * per-pixel part of its tick (kernels 0, 1, 5 and 6 below) in one persistent
+ * launch, whose CTAs take work items from a queue in order (per stream: luma
+ * sums, then band / gray / hue tests, then morphology strips), each item
  * waiting (bounded) only for the stream's items of the step before; 0 runs
  * the chain of kernels of HMI_TICK_KERNELS.  queue_lag: queue positions
  * between a stream's last item of one step and its first of the next
- * (0 = twice the persistent grid, else 1..2^20); merge_defer: 1 puts every
- * stream's merge at the end of the queue (the merge schedule of the
- * components), 0 right after its blocks (default).  Results never depend on
- * the tuning. */
+ * (0 = twice the persistent grid, else 1..2^20).  merge_threads: threads of
+ * the CTA that merges one stream's block components into its pointer (the
+ * merge schedule: 256, 512 or 1024; 0 = 512).  Results never depend on the
+ * tuning. */
 typedef struct {
     int32_t piece_chunks;
     int32_t luma_ctas_per_sm;
@@ -265,7 +265,7 @@ typedef struct {
     int32_t pipeline_depth;
     int32_t fused;
     int32_t queue_lag;
-    int32_t merge_defer;
+    int32_t merge_threads;
 } hmi_tuning;
 
 /* Replace the batch's launch shape (re-makes the plan; waits for the device).
@@ -275,8 +275,9 @@ HMI_API int hmi_batch_get_tuning(const hmi_batch *b, hmi_tuning *t);
 
 /* Search the launch shape (Sec. 3.3: the GPU computation is autotuned):
  * time `ticks` ticks (2..10000) of frames (device memory, one per stream) for
- * each candidate, changing one parameter at a time (piece size, then the
- * luma, skin and block-component grids, then the pipeline depth for pipelined
+ * each candidate, changing one parameter at a time (the tick form, the piece
+ * size, the luma, skin and block-component grids and the merge CTA size,
+ * then the pipeline depth for pipelined
  * ticks or the group count for plain ticks), keep the fastest, apply it and return it in *best with its time per
  * tick in microseconds (either may be NULL).  pipelined != 0 times pipelined
  * ticks (one group), else plain graph ticks.  The streams' click state and

@@ -73,8 +73,9 @@ constexpr int kRing = 12;         // per-tick pointer slots of a launch plan (a 
 // per-pixel kernels (512 = 8192 px), luma CTAs per SM (0 = as many as fit),
 // skin-test and block-component CTAs per SM, stream groups (0 = by the
 // streams, see default_groups), stages of a pipelined tick, the persistent
-// tick on, its queue lag chosen from the grid, merges interleaved.
-constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2, 1, 0, 0};
+// tick off (the chain of kernels measured faster on the 64-stream batch), its
+// queue lag chosen from the grid, 512 threads per stream merge.
+constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2, 0, 0, 0};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -136,8 +137,8 @@ struct Arena {
 struct Layout {
     int w, h, nwords, bh, tiles_x, strips_x, fpitch;
     size_t frame_ph[kPhases];     // staging frames for pinned host frames, by tick phase
-    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits, comp, parent, count, flag, mask,
-        st, hist, ds, ptr, ui, total;
+    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits[kPhases], comp, parent,
+        count[kPhases], flag[kPhases], mask, st, hist, ds, ptr, ui, total;
     // re-learning sums (only with re-learning on): rows of rpitch pixels
     int rpitch;
     size_t rS, rQ, rmin, rmax, rcnt, rpx;
@@ -171,15 +172,17 @@ Layout make_layout(int w, int h, const hmi_params &p)
     L.vmin = a.take(L.npx * 3);
     L.vmax = a.take(L.npx * 3);
     for (int k = 0; k < kPhases; ++k) L.raw[k] = a.take(bitrows);   // one per tick phase
-    L.bits = a.take(bitrows);
+    for (int k = 0; k < kPhases; ++k) L.bits[k] = a.take(bitrows);
     L.comp = a.take(nblk * kSlots * sizeof(Comp));
     L.parent = a.take(nblk * kSlots * 4);
-    L.count = a.take(nblk * 4);
-    L.flag = a.take(nblk * 4);
+    for (int k = 0; k < kPhases; ++k) {
+        L.count[k] = a.take(nblk * 4);
+        L.flag[k] = a.take(nblk * 4);
+    }
     L.mask = a.take(L.npx);
     L.st = a.take(sizeof(StreamState));
     L.hist = a.take((size_t)std::max<int>(p.click_window, 1) * 4);
-    L.ds = a.take(sizeof(DevStream));
+    L.ds = a.take(sizeof(DevStream) * kPhases);   // one descriptor per tick phase
     L.ptr = a.take(sizeof(hmi_pointer));
     L.ui = a.take(sizeof(hmi_interface));
     L.rpitch = (int)align_up((size_t)w, 16);
@@ -261,8 +264,9 @@ struct hmi_stream {
     hmi_params p{};
     Layout L{};
     uint8_t *arena = nullptr;
-    DevStream ds{};          // host copy
-    DevStream *d_ds = nullptr;
+    DevStream ds{};          // host copy (the buffers of tick phase 0)
+    DevStream ds_phase[kPhases]{};   // host copies of the descriptor of each tick phase
+    DevStream *d_ds = nullptr;       // device copies, kPhases of them
     StreamState *st = nullptr;
     uint8_t *d_frame = nullptr, *d_mask = nullptr;
     uint32_t *d_S = nullptr, *d_Q = nullptr;
@@ -282,6 +286,8 @@ struct Group {
     BatchDev bd{};                // io, phase and skin queue are set per tick slot
     uint32_t *skin_count_p[kPhases] = {};   // skin queue of each tick phase
     uint2 *skin_list_p[kPhases] = {};
+    uint32_t *cc_count_p[kPhases] = {};     // listed blocks of each tick phase
+    uint2 *cc_list_p[kPhases] = {};
     cudaStream_t cs = nullptr;    // branch stream (also joins graph capture)
     cudaEvent_t ev_luma = nullptr, ev_done = nullptr;
 };
@@ -298,6 +304,7 @@ struct hmi_batch {
     std::vector<Group> groups;
     uint8_t *arena = nullptr;     // per-batch device buffers
     uint8_t *plan = nullptr;      // per-plan device tables
+    const DevStream *ds_tab = nullptr;   // in plan: kPhases tables of n descriptors
     TickIO *h_io = nullptr;       // pinned mirrors, kRing x n, permuted order
     TickIO *d_io = nullptr;       // device copies, kRing x n
     hmi_pointer *d_ptrs = nullptr;  // n pointers for the synchronous form, user order
@@ -366,6 +373,16 @@ namespace {
 std::mutex g_cache_mu;
 hmi_batch *g_cache = nullptr;    // plan reused by hmi_process_batch
 
+// The descriptor a tick of phase k uses: its own bit mask, block counts and flags.
+DevStream phase_view(const DevStream &D, int k)
+{
+    DevStream V = D;
+    V.bits = D.bits_p[k];
+    V.count = D.count_p[k];
+    V.flag = D.flag_p[k];
+    return V;
+}
+
 void fill_devstream(hmi_stream *s)
 {
     DevStream &D = s->ds;
@@ -392,11 +409,16 @@ void fill_devstream(hmi_stream *s)
     D.lo = a + L.lo;
     D.hi = a + L.hi;
     for (int k = 0; k < kPhases; ++k) D.raw[k] = reinterpret_cast<uint32_t *>(a + L.raw[k]);
-    D.bits = reinterpret_cast<uint32_t *>(a + L.bits);
+    for (int k = 0; k < kPhases; ++k) {
+        D.bits_p[k] = reinterpret_cast<uint32_t *>(a + L.bits[k]);
+        D.count_p[k] = reinterpret_cast<uint32_t *>(a + L.count[k]);
+        D.flag_p[k] = reinterpret_cast<uint32_t *>(a + L.flag[k]);
+    }
+    D.bits = D.bits_p[0];
+    D.count = D.count_p[0];
+    D.flag = D.flag_p[0];
     D.comp = reinterpret_cast<Comp *>(a + L.comp);
     D.parent = reinterpret_cast<uint32_t *>(a + L.parent);
-    D.count = reinterpret_cast<uint32_t *>(a + L.count);
-    D.flag = reinterpret_cast<uint32_t *>(a + L.flag);
     D.st = reinterpret_cast<StreamState *>(a + L.st);
     D.hist = reinterpret_cast<uint32_t *>(a + L.hist);
     D.bg_kn = s->p.bg_k_num;
@@ -537,7 +559,7 @@ int plan_build(hmi_batch *b, int ng)
         std::vector<int4> pieces;
         int max_halo = 0, uniform_halo = 0;
         bool any_mix = false;
-        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn, o_ccl, o_skn[kPhases], o_skl[kPhases];
+        size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn[kPhases], o_ccl[kPhases], o_skn[kPhases], o_skl[kPhases];
         // persistent tick: work queue and per-stream progress
         bool fused = false;
         std::vector<int4> items;
@@ -547,7 +569,7 @@ int plan_build(hmi_batch *b, int ng)
     const long long tick_grid = (long long)b->num_sms * tick_ctas_per_sm(b->tune.luma_ctas_per_sm);
     std::vector<Tables> T(ng);
     Arena a;
-    const size_t o_ds = a.take(sizeof(DevStream) * n);
+    const size_t o_ds = a.take(sizeof(DevStream) * n * kPhases);   // a descriptor table per tick phase
     for (int g = 0; g < ng; ++g) {
         Tables &t = T[g];
         const int m = b->groups[g].cnt;
@@ -562,7 +584,7 @@ int plan_build(hmi_batch *b, int ng)
             const int chunks = L.h * 2 * L.nwords;
             t.cpre[k + 1] = t.cpre[k] + (unsigned long long)chunks;
             t.tpre[k + 1] = t.tpre[k] + (uint32_t)(L.bh * L.tiles_x);
-            t.spre[k + 1] = t.spre[k] + (uint32_t)(((L.h + 15) / 16) * L.strips_x);
+            t.spre[k + 1] = t.spre[k] + (uint32_t)(((L.h + kStripRows - 1) / kStripRows) * L.strips_x);
             t.bpre[k + 1] = t.bpre[k] + (uint32_t)(L.bh * L.nwords);
             const int halo = 2 * (st->p.open_iters + st->p.close_iters);
             t.max_halo = std::max(t.max_halo, halo);
@@ -571,16 +593,16 @@ int plan_build(hmi_batch *b, int ng)
                 t.pieces.push_back(make_int4(k, c, std::min(chunks, c + b->tune.piece_chunks), 0));
             if (L.mix_k) t.any_mix = true;
         }
-        t.fused = b->tune.fused && !t.any_mix && t.uniform_halo >= 0 && t.uniform_halo <= kStripMaxHalo;
+        t.fused = b->tune.fused && !t.any_mix && t.uniform_halo >= 0 && t.uniform_halo <= kTickMaxHalo;
         if (t.fused) {
             std::vector<int> ch(m), sp(m);
             for (int k = 0; k < m; ++k) {
                 const Layout &L = b->s[perm[b->groups[g].off + k]]->L;
                 ch[k] = L.h * 2 * L.nwords;
-                sp[k] = L.bh * L.strips_x;
+                sp[k] = ((L.h + kStripRows - 1) / kStripRows) * L.strips_x;   // morphology strips
             }
             const long long lag = b->tune.queue_lag > 0 ? b->tune.queue_lag : 2 * tick_grid;
-            t.items = tick_queue(ch, sp, b->tune.piece_chunks, lag, b->tune.merge_defer != 0, &t.sync);
+            t.items = tick_queue(ch, sp, b->tune.piece_chunks, lag, &t.sync);
             t.o_items = a.take(sizeof(int4) * t.items.size());
             t.o_sync = a.take(sizeof(TickSync) * m);
             t.o_head = a.take(sizeof(uint32_t) * 2);
@@ -591,9 +613,9 @@ int plan_build(hmi_batch *b, int ng)
         t.o_s = a.take(sizeof(uint32_t) * (m + 1));
         t.o_done = a.take(sizeof(uint32_t) * 4);
         t.o_p = a.take(sizeof(int4) * std::max<size_t>(t.pieces.size(), 1));
-        t.o_ccn = a.take(sizeof(uint32_t));
-        t.o_ccl = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
         for (int k = 0; k < kPhases; ++k) {
+            t.o_ccn[k] = a.take(sizeof(uint32_t));
+            t.o_ccl[k] = a.take(sizeof(uint2) * std::max<size_t>(t.bpre[m], 1));
             t.o_skn[k] = a.take(sizeof(uint32_t));
             t.o_skl[k] = a.take(sizeof(uint2) * std::max<size_t>(t.cpre[m], 1));
         }
@@ -615,10 +637,12 @@ int plan_build(hmi_batch *b, int ng)
     // vectors that live until the synchronisation at the end.
     uint8_t *A = b->plan;
     cudaStream_t up = b->cs;
-    std::vector<DevStream> ds(n);
-    for (int p = 0; p < n; ++p) ds[p] = b->s[perm[p]]->ds;
+    std::vector<DevStream> ds((size_t)n * kPhases);
+    for (int k = 0; k < kPhases; ++k)
+        for (int p = 0; p < n; ++p) ds[(size_t)k * n + p] = b->s[perm[p]]->ds_phase[k];
     bool ok = cudaMemsetAsync(A, 0, a.off, up) == cudaSuccess &&
-              cudaMemcpyAsync(A + o_ds, ds.data(), sizeof(DevStream) * n, cudaMemcpyHostToDevice, up) == cudaSuccess;
+              cudaMemcpyAsync(A + o_ds, ds.data(), sizeof(DevStream) * n * kPhases, cudaMemcpyHostToDevice, up) == cudaSuccess;
+    b->ds_tab = reinterpret_cast<const DevStream *>(A + o_ds);
     for (int g = 0; ok && g < ng; ++g) {
         Tables &t = T[g];
         Group &G = b->groups[g];
@@ -652,14 +676,16 @@ int plan_build(hmi_batch *b, int ng)
         bd.pieces = reinterpret_cast<const int4 *>(A + t.o_p);
         bd.npieces = (int)t.pieces.size();
         bd.err = b->d_err;
-        bd.cc_count = reinterpret_cast<uint32_t *>(A + t.o_ccn);
-        bd.cc_list = reinterpret_cast<uint2 *>(A + t.o_ccl);
         for (int k = 0; k < kPhases; ++k) {
+            G.cc_count_p[k] = reinterpret_cast<uint32_t *>(A + t.o_ccn[k]);
+            G.cc_list_p[k] = reinterpret_cast<uint2 *>(A + t.o_ccl[k]);
             G.skin_count_p[k] = reinterpret_cast<uint32_t *>(A + t.o_skn[k]);
             G.skin_list_p[k] = reinterpret_cast<uint2 *>(A + t.o_skl[k]);
         }
         bd.skin_count = G.skin_count_p[0];
         bd.skin_list = G.skin_list_p[0];
+        bd.cc_count = G.cc_count_p[0];
+        bd.cc_list = G.cc_list_p[0];
         bd.phase = 0;
         bd.relearn = bd.any_band = bd.any_mix = 0;
         for (int k = 0; k < m; ++k) {
@@ -675,6 +701,7 @@ int plan_build(hmi_batch *b, int ng)
         bd.tick_head = t.fused ? reinterpret_cast<uint32_t *>(A + t.o_head) : nullptr;
         bd.tick_exit = t.fused ? bd.tick_head + 1 : nullptr;
         bd.loop_limit = b->loop_limit ? b->loop_limit : kLoopLimit;
+        bd.merge_threads = b->tune.merge_threads ? b->tune.merge_threads : 512;
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;
         bd.skin_ctas_per_sm = b->tune.skin_ctas_per_sm;
         bd.cc_ctas_per_sm = b->tune.cc_ctas_per_sm;
@@ -732,7 +759,7 @@ int default_groups(hmi_stream *const *s, int n, const hmi_tuning &t)
 {
     bool fusable = t.fused != 0;
     for (int i = 0; i < n && fusable; ++i)
-        fusable = s[i]->L.mix_k == 0 && 2 * (s[i]->p.open_iters + s[i]->p.close_iters) <= kStripMaxHalo;
+        fusable = s[i]->L.mix_k == 0 && 2 * (s[i]->p.open_iters + s[i]->p.close_iters) <= kTickMaxHalo;
     return fusable ? 1 : std::min(2, n);
 }
 
@@ -802,8 +829,11 @@ BatchDev tick_dev(const hmi_batch *b, const Group &G, int slot)
     BatchDev bd = G.bd;
     bd.io = b->d_io + (size_t)slot * b->n + G.off;
     bd.phase = slot % kPhases;
+    bd.ds = b->ds_tab + (size_t)bd.phase * b->n + G.off;   // this phase's bit mask, counts, flags
     bd.skin_count = G.skin_count_p[bd.phase];
     bd.skin_list = G.skin_list_p[bd.phase];
+    bd.cc_count = G.cc_count_p[bd.phase];
+    bd.cc_list = G.cc_list_p[bd.phase];
     return bd;
 }
 
@@ -860,9 +890,11 @@ cudaError_t enqueue_tick(hmi_batch *b, int slot, cudaStream_t cs, const cudaEven
 void stage_bounds(int depth, int *first, bool fused)
 {
     constexpr int kTail = kTickTail;   // first kernel of the latency-bound tail (gray/hue tests)
-    if (fused) {   // the persistent tick is one launch: the whole tick is the first stage
-        first[0] = 0;
-        for (int j = 1; j <= kPhases; ++j) first[j] = kTickKernels;
+    if (fused) {   // {persistent tick, re-learning} {block components, merge}; a third stage
+        first[0] = 0;   // would part re-learning from the band test it follows
+        first[1] = kTail;
+        first[2] = kTickKernels;
+        first[3] = kTickKernels;
     } else if (depth >= 3) {
         first[0] = 0;
         first[1] = 1;
@@ -1192,7 +1224,8 @@ bool tuning_ok(const hmi_tuning &t)
            t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
            t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases &&
            (t.fused == 0 || t.fused == 1) && t.queue_lag >= 0 && t.queue_lag <= (1 << 20) &&
-           (t.merge_defer == 0 || t.merge_defer == 1);
+           (t.merge_threads == 0 || t.merge_threads == 256 || t.merge_threads == 512 ||
+            t.merge_threads == 1024);
 }
 
 // Apply a launch shape: the plan is re-made with the device idle.
@@ -1291,10 +1324,12 @@ int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool p
         int32_t hmi_tuning::*field;
         std::vector<int32_t> values;
     };
-    std::vector<Axis> axes = {{&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
+    std::vector<Axis> axes = {{&hmi_tuning::fused, {0, 1}},
+                              {&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
                               {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
                               {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},
-                              {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}}};
+                              {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}},
+                              {&hmi_tuning::merge_threads, {256, 512, 1024}}};
     if (pipelined) axes.push_back({&hmi_tuning::pipeline_depth, {2, 3}});
     else axes.push_back({&hmi_tuning::groups, {1, 2, 3}});
     for (const Axis &ax : axes) {
@@ -1412,8 +1447,9 @@ hmi_stream *create_stream_on(int w, int h, const hmi_params *p, cudaStream_t ord
     s->d_ds = reinterpret_cast<DevStream *>(a + s->L.ds);
     s->d_ptr = reinterpret_cast<hmi_pointer *>(a + s->L.ptr);
     fill_devstream(s);
+    for (int k = 0; k < kPhases; ++k) s->ds_phase[k] = phase_view(s->ds, k);
     bool ok = cudaMemsetAsync(s->arena, 0, s->L.total, cs) == cudaSuccess &&
-              cudaMemcpyAsync(s->d_ds, &s->ds, sizeof(DevStream), cudaMemcpyHostToDevice, cs) == cudaSuccess &&
+              cudaMemcpyAsync(s->d_ds, s->ds_phase, sizeof(DevStream) * kPhases, cudaMemcpyHostToDevice, cs) == cudaSuccess &&
               (order != nullptr || cudaStreamSynchronize(cs) == cudaSuccess);
     if (!ok) {
         (void)cudaGetLastError();

@@ -16,24 +16,25 @@
 
 namespace hmi {
 
-constexpr int kFinishThreads = 512;
 constexpr int kActCap = 2048;
 constexpr int kRecCap = 1024;
-using FinishSmemK = FinishSmem<kFinishThreads, kActCap, kRecCap>;
+template <int NT>
+using FinishSmemK = FinishSmem<NT, kActCap, kRecCap>;
 
-// One CTA per stream (the chained form of a tick).
-__global__ void __launch_bounds__(kFinishThreads) k_finish(BatchDev b)
+// One CTA of NT threads per stream: the merge of its block components.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_finish(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FinishSmemK &S = *reinterpret_cast<FinishSmemK *>(smem_raw);
+    FinishSmemK<NT> &S = *reinterpret_cast<FinishSmemK<NT> *>(smem_raw);
     if (threadIdx.x == 0 && blockIdx.x == 0) {   // k_skin and k_block_cc are done with their lists
         *b.cc_count = 0u;
         *b.skin_count = 0u;
     }
     const TickIO io = b.io[blockIdx.x];
     if (io.frame == nullptr) return;             // no frame this tick: pointer and click unchanged
-    finish_stream<kFinishThreads, kActCap, kRecCap>(b.ds[blockIdx.x], io, S, b.err,
-                                                    b.loop_limit ? b.loop_limit : kLoopLimit);
+    finish_stream<NT, kActCap, kRecCap>(b.ds[blockIdx.x], io, S, b.err,
+                                        b.loop_limit ? b.loop_limit : kLoopLimit);
 }
 
 // Labels of one stream: warp per 32x32 block.
@@ -47,7 +48,8 @@ __global__ void __launch_bounds__(kThreads) k_labels(const DevStream *dsp, int32
     const int by = blk / D.nwords, bx = blk - by * D.nwords;
     const int y = by * kBlock + lane, xb = bx * kWordPx;
     const int npx = min(kWordPx, D.w - xb);
-    uint32_t m = D.bits[(long long)y * D.nwords + bx];
+    const uint32_t *bits = D.bits_p[min(D.st->last_phase, 2u)];   // the last finished frame's mask
+    uint32_t m = bits[(long long)y * D.nwords + bx];
     int32_t *row = labels + (long long)y * D.w + xb;
     if (y < D.h)
         for (int i = 0; i < npx; ++i) row[i] = -1;
@@ -73,20 +75,30 @@ __global__ void __launch_bounds__(kThreads) k_labels(const DevStream *dsp, int32
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs)
+template <int NT>
+static cudaError_t launch_finish_nt(const BatchDev &b, cudaStream_t cs)
 {
     static bool attr_set[64] = {};   // the shared-memory opt-in is per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(FinishSmemK));
+        e = cudaFuncSetAttribute(k_finish<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FinishSmemK<NT>));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    k_finish<<<b.n, kFinishThreads, sizeof(FinishSmemK), cs>>>(b);
+    k_finish<NT><<<b.n, NT, sizeof(FinishSmemK<NT>), cs>>>(b);
     return cudaGetLastError();
+}
+
+cudaError_t launch_finish(const BatchDev &b, cudaStream_t cs)
+{
+    switch (b.merge_threads) {
+    case 256: return launch_finish_nt<256>(b, cs);
+    case 1024: return launch_finish_nt<1024>(b, cs);
+    default: return launch_finish_nt<512>(b, cs);
+    }
 }
 
 cudaError_t launch_labels(const DevStream *ds_dev, const DevStream &ds, int32_t *labels,

@@ -224,6 +224,8 @@ __device__ __forceinline__ void finalize_pointer(const DevStream &D, const TickI
         }
     }
     P.click = st->click;
+    for (int k = 0; k < 3; ++k)   // the phase whose bit mask holds this frame, for the labels
+        if (D.bits == D.bits_p[k]) st->last_phase = (uint32_t)k;
     interface_event(D, P.valid != 0, st->track_x, st->track_y, P.click, st->frames + 1, &st->event);
     st->last = P;
     st->frames += 1;
@@ -473,7 +475,7 @@ __device__ __forceinline__ void finish_stream(const DevStream &D, const TickIO &
             const uint32_t e = D.st->err;
             if (e) {
                 atomicOr(batch_err, e);
-                D.st->err = 0u;
+                atomicAnd(&D.st->err, ~e);   // flags raised meanwhile stay for the next report
             }
         }
         return;
@@ -618,7 +620,7 @@ __device__ __forceinline__ void finish_stream(const DevStream &D, const TickIO &
         const uint32_t e = D.st->err;   // this frame's errors are reported once, through the batch
         if (e) {
             atomicOr(batch_err, e);
-            D.st->err = 0u;
+            atomicAnd(&D.st->err, ~e);   // flags raised meanwhile stay for the next report
         }
     }
 }

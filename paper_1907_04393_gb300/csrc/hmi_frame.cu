@@ -3,9 +3,11 @@
 //                 brightness gains (Sec. 2 brightness correction,
 //                 Sec. 3.2 luminosity filter)
 //   k_classify    gain and background band test (Sec. 3.1 (i)) of every pixel,
-//                 one bit per pixel; chunks with out-of-band pixels are queued
-//   k_skin        gray and hue tests (Sec. 3.1 (ii), (iii)) of the queued
-//                 pixels, clearing those that fail (the AND of the merging step)
+//                 then the gray and hue tests (Sec. 3.1 (ii), (iii)) of its
+//                 out-of-band pixels and the AND (the merging step), one bit
+//                 per pixel
+//   k_skin        the gray and hue tests of the pixels that the mixture
+//                 background queued (bg_model 1 streams)
 //   k_morph_strip opening/closing on the bit mask (Sec. 3.1 erosion and
 //                 dilation) in registers, the 0/1 mask bytes, and the list
 //                 of 32x32 blocks holding foreground
@@ -116,14 +118,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
 // ---------------------------------------------------------------------------
 // k_classify
 // ---------------------------------------------------------------------------
-// One thread per 16-pixel chunk: the background test on all 16 pixels.  The
-// word of out-of-band pixels is stored as the raw mask; chunks that have any
-// are appended (warp-aggregated) to the skin queue, where k_skin runs the gray
-// and hue tests on just those pixels and clears the ones that fail.  Out-of-
-// band pixels are a few percent (the hand, camera noise), so the skin tests
-// run densely instead of stalling whole warps here.
+// One thread per 16-pixel chunk: the background test on all 16 pixels; the
+// warp then lists its out-of-band pixels (a few percent: the hand, camera
+// noise) in shared memory and its lanes share the gray and hue tests of that
+// list, so that the raw mask word stored is the AND of the three tests.
 __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
 {
+    __shared__ uint8_t table[256];
+    __shared__ SkinSmem skin[kThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31;
     const uint64_t once = policy_evict_first();
     for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
@@ -132,6 +134,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         const TickIO io = b.io[piece.x];
         if (io.frame == nullptr || D.mix.K != 0) continue;   // no frame this tick, or a mixture stream
         const uint32_t g = D.st->gain_p[b.phase];
+        __syncthreads();   // the previous piece is done with the table
+        fill_table(table, g);
+        __syncthreads();
         const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
         const uint8_t *lo = D.lo, *hi = D.hi;
         uint32_t *raw = D.raw[b.phase];
@@ -139,33 +144,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
         for (int base = piece.y + (tid & ~31); base < piece.z; base += blockDim.x) {
             const int u = base + lane;
             uint32_t bits = 0;
+            uint32_t f[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) f[k] = 0u;
             int y = 0, j = 0;
             if (u < piece.z) {
                 y = chunk_row((uint32_t)u, D.cpr_magic);
                 j = u - y * cpr;
                 const int x0 = j * kChunkPx;
                 if (x0 < w) {
-                    uint32_t f[12], l[12], h[12];
+                    uint32_t l[12], h[12];
                     load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                     load48(lo + (long long)y * fpitch + 3 * x0, once, l);
                     load48(hi + (long long)y * fpitch + 3 * x0, once, h);
-                    bits = outside_bits<kChunkPx - 1>(f, l, h, g);
+                    bits = band_outside16(f, l, h, TableCorr{table});
                     const int npx = w - x0;
                     if (npx < kChunkPx) bits &= (1u << npx) - 1u;
                 }
             }
+            // gray and hue tests of the warp's out-of-band pixels, then the AND
+            bits &= ~skin_fail_warp(bits, f, D, g, skin[tid >> 5], lane);
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
             if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
-            const unsigned want = __ballot_sync(kFull, bits != 0u);
-            if (want) {
-                uint32_t slot0 = 0;
-                if (lane == __ffs(want) - 1) slot0 = atomicAdd(b.skin_count, (uint32_t)__popc(want));
-                slot0 = __shfl_sync(kFull, slot0, __ffs(want) - 1);
-                if (bits) {
-                    const uint32_t slot = slot0 + (uint32_t)__popc(want & ((1u << lane) - 1u));
-                    b.skin_list[slot] = make_uint2(((uint32_t)piece.x << 16) | bits, (uint32_t)u);
-                }
-            }
         }
     }
 }
@@ -326,105 +326,6 @@ __global__ void __launch_bounds__(kThreads) k_relearn(BatchDev b)
             relearn_quad<2>(D, q0, npx, f, l, h, g);
             relearn_quad<3>(D, q0, npx, f, l, h, g);
         }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_morph_strip: one warp per strip of 16 output rows x 30 words (960 px),
-// lane j = word column (lanes 0 and 31 are the left/right halo words), rows
-// (32 + 2*HR with HR = 2*(open+close) halo rows) held in registers.  Each
-// operator neutralises out-of-image pixels (1 for erosion, 0 for dilation),
-// forms the horizontal 3-pixel AND/OR with the neighbour lanes' words, then
-// the vertical 3-row AND/OR.  Garbage from the strip's own edges moves one
-// pixel per operator and never reaches the interior (HR rows, 32 - HR bits).
-// ---------------------------------------------------------------------------
-constexpr int kStripWords = 30;
-constexpr int kStripWarps = 4;
-constexpr int kStripRows = 16;
-
-template <int HR>
-__device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
-                                            int lane, int sidx, uint32_t *cc_count, uint2 *cc_list,
-                                            const uint32_t *__restrict__ raw)
-{
-    constexpr int R = kStripRows + 2 * HR;
-    const int w = D.w, h = D.h, nwords = D.nwords;
-    const int kw = tx * kStripWords - 1 + lane;
-    const bool col_ok = kw >= 0 && kw < nwords;
-    const uint32_t wmask = !col_ok ? 0u : ((kw == nwords - 1 && (w & 31)) ? ((1u << (w & 31)) - 1u) : 0xffffffffu);
-    const int y0 = ty * kStripRows;
-    const int ybase = y0 - HR;
-    const int rlo = max(0, -ybase), rhi = min(R, h - ybase);   // rows inside the image
-    uint32_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int y = ybase + r;
-        v[r] = (col_ok && r >= rlo && r < rhi) ? raw[(long long)y * nwords + kw] : 0u;
-    }
-    // strips away from every image edge need no neutral out-of-image pixels
-    const bool edge = rlo > 0 || rhi < R || __any_sync(kFull, wmask != 0xffffffffu);
-    const int nops = 2 * (D.open_iters + D.close_iters);   // == HR
-    for (int op = 0; op < nops; ++op) {
-        const bool ero = (op < 2 * D.open_iters) ? ((op & 1) == 0) : (((op - 2 * D.open_iters) & 1) == 1);
-        if (edge) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
-                v[r] = ero ? (v[r] | ~vm) : (v[r] & vm);
-            }
-        }
-        uint32_t prev = 0, cur = 0;
-#pragma unroll
-        for (int r = 0; r <= R; ++r) {
-            uint32_t nxt = cur;
-            if (r < R) {
-                const uint32_t x = v[r];
-                const uint32_t L = __shfl_up_sync(kFull, x, 1);
-                const uint32_t Rt = __shfl_down_sync(kFull, x, 1);
-                nxt = ero ? (x & ((x << 1) | (L >> 31)) & ((x >> 1) | (Rt << 31)))
-                          : (x | (x << 1) | (L >> 31) | (x >> 1) | (Rt << 31));
-            }
-            if (r == 1) {
-                v[0] = ero ? (cur & nxt) : (cur | nxt);
-            } else if (r >= 2) {
-                v[r - 1] = ero ? (prev & cur & nxt) : (prev | cur | nxt);
-            }
-            prev = cur;
-            cur = nxt;
-        }
-    }
-    // interior: global bit mask and mask bytes
-    const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
-    if (!interior) return;
-    uint32_t any = 0;
-#pragma unroll
-    for (int i = 0; i < kStripRows; ++i) {
-        const int r = HR + i, y = y0 + i;
-        const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
-        any |= fin;
-        D.bits[(long long)y * nwords + kw] = fin;
-        if (io.mask != nullptr && y < h) {
-            uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
-            const int npx = min(kWordPx, w - kw * kWordPx);
-            if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-                uint32_t q[8];
-#pragma unroll
-                for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
-                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-                __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
-                __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
-            } else {
-                for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
-            }
-        }
-    }
-    // the 32x32 block of this word: the upper strip of a block clears its
-    // count; the first strip to find pixels in it lists it for k_block_cc
-    const uint32_t blk = (uint32_t)((y0 / kBlock) * nwords + kw);
-    if ((ty & 1) == 0) D.count[blk] = 0u;
-    if (any != 0u && atomicOr(D.flag + blk, 1u) == 0u) {
-        const uint32_t slot = atomicAdd(cc_count, 1u);
-        cc_list[slot] = make_uint2((uint32_t)sidx, blk);
     }
 }
 
@@ -637,8 +538,8 @@ cudaError_t launch_luma(const BatchDev &b, cudaStream_t cs, int num_sms)
 
 cudaError_t launch_classify(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    (void)num_sms;
-    if (!b.any_band) return cudaSuccess;
+    (void)num_sms;   // one CTA per piece: CTAs of the tail kernels of the previous
+    if (!b.any_band) return cudaSuccess;   // tick find SMs as pieces finish
     k_classify<<<grid_for_pieces(b.npieces), kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
@@ -653,6 +554,7 @@ cudaError_t launch_relearn(const BatchDev &b, cudaStream_t cs, int num_sms)
 
 cudaError_t launch_skin(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
+    if (!b.any_mix) return cudaSuccess;   // band streams are tested in k_classify
     k_skin<<<num_sms * std::max(1, b.skin_ctas_per_sm), kThreads, 0, cs>>>(b);
     return cudaGetLastError();
 }
@@ -691,11 +593,13 @@ cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 
 cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int num_sms)
 {
-    if (b.fused) {   // one persistent launch does every kernel's work but re-learning
+    if (b.fused) {   // one persistent launch does the per-pixel work of kernels 0, 1, 5 and 6
         switch (k) {
         case 0: return launch_tick(b, cs, num_sms);
         case 3: return launch_relearn(b, cs, num_sms);
         case 4: return launch_relearn_band(b, cs, num_sms);
+        case 7: return launch_block_cc(b, cs, num_sms);
+        case 8: return launch_finish(b, cs);
         default: return cudaSuccess;
         }
     }

@@ -21,6 +21,7 @@ constexpr int kMorphTW = 8;        // morphology tile width in words (256 px)
 constexpr int kMorphRows = 32;     // morphology tile height (one CC block row)
 constexpr int kMaxHalo = 32;       // 2 * (open_iters + close_iters) <= 32
 constexpr int kStripMaxHalo = 8;   // register strips handle halos up to 8 rows
+constexpr int kTickMaxHalo = 4;    // ... and up to 4 rows inside the persistent tick
 constexpr int kMaxDim = 8192;
 constexpr int kMaxBatch = 4096;
 constexpr uint32_t kLoopLimit = 1u << 22;  // bound on every device-side retry loop
@@ -60,6 +61,7 @@ struct __align__(16) StreamState {
     uint32_t lframe_p[3];         // the number of the frame of each tick phase (kPhases)
     int32_t track_valid, track_x, track_y;   // tracked point: last valid pointer's rounded centroid
     uint32_t nlearn;              // learning frames of the background (set when the band is formed)
+    uint32_t last_phase;          // tick phase of the last finished frame (its bits give the labels)
     hmi_event event;              // the Interface module's event of the last frame
     hmi_pointer last;             // pointer of the last frame
 };
@@ -124,11 +126,14 @@ struct DevStream {
     uint8_t *rmin, *rmax;         // their min and max
     uint8_t *rcnt;                // background frames counted, per pixel
     uint32_t *raw[3];             // raw AND mask bits, (bh*32) x nwords words, by tick phase
+    // bits, count and flag are those of one tick phase (the plan keeps a
+    // descriptor table per phase; *_p hold every phase's buffers)
     uint32_t *bits;               // mask bits after morphology, same layout
     Comp *comp;                   // bh*nwords*kSlots records
     uint32_t *parent;             // union-find parent per record
     uint32_t *count;              // components per CC block
     uint32_t *flag;               // per CC block: listed for components this tick
+    uint32_t *bits_p[3], *count_p[3], *flag_p[3];
     StreamState *st;
     uint32_t *hist;               // click_window areas (ring)
 };
@@ -184,6 +189,7 @@ struct BatchDev {
     int any_band;                             // some stream has the band test
     int any_mix;                              // bit K: some stream has a K-component mixture
     uint32_t loop_limit;                      // steps of every bounded device loop (0: kLoopLimit)
+    int merge_threads;                        // threads of a stream's merge CTA (256, 512, 1024)
     // persistent tick (fused != 0): the whole path of the group in one launch
     int fused;
     const int4 *items;                        // work queue, in order

@@ -8,6 +8,7 @@
 
 #include <stdint.h>
 
+#include "hmi_band.h"
 #include "hmi_ccfill.cuh"
 #include "hmi_internal.cuh"
 
@@ -149,6 +150,20 @@ __device__ __forceinline__ uint32_t outside_bits(const uint32_t (&f)[12], const 
     }
 }
 
+// The frame's table of corrected values (shared memory) as the word
+// correction of the packed band test (hmi_band.h).
+struct TableCorr {
+    const uint8_t *t;
+    __device__ __forceinline__ uint32_t operator()(uint32_t w) const { return corrected_word(w, t); }
+};
+
+// Fill the CTA's table of corrected values for gain g (blockDim.x >= 256);
+// the caller synchronises before and after.
+__device__ __forceinline__ void fill_table(uint8_t *table, uint32_t g)
+{
+    if (threadIdx.x < 256) table[threadIdx.x] = (uint8_t)corrected_value(threadIdx.x, g);
+}
+
 // Gray and hue tests of one pixel (Sec. 3.1 (ii), (iii)) on the corrected
 // values: not gray (max - min >= S) and hue inside the arc.  The hue test
 // compares N = 512 (t + d) + d against d-scaled interval ends, which equals
@@ -227,6 +242,165 @@ __device__ __forceinline__ void emit_block_components(const DevStream &D, uint32
     if (lane == 0) {
         if (ncomp > kSlots) atomicOr(&D.st->err, kErrSlots);
         D.count[blk] = (uint32_t)min(ncomp, kSlots);
+    }
+}
+
+struct SkinSmem {                 // per warp: the classify item's gray / hue queue
+    uint32_t f[32][12];           // frame words of the lanes' chunks
+    uint16_t list[32 * kChunkPx]; // queued pixels: lane << 4 | pixel
+    uint32_t fail[32];            // pixels of each lane's chunk that fail
+};
+
+// Gray and hue tests of a warp's out-of-band pixels: the warp lists them
+// (lane << 4 | pixel) in shared memory and every lane takes pixels in turn, so
+// that a chunk with many candidate pixels (the hand) does not stall the warp
+// behind one lane.  Returns this lane's pixels that fail.
+__device__ __forceinline__ uint32_t skin_fail_warp(uint32_t bits, const uint32_t (&f)[12],
+                                                   const DevStream &D, uint32_t g, SkinSmem &S,
+                                                   int lane)
+{
+    if (__ballot_sync(kFull, bits != 0u) == 0u) return 0u;
+    const uint32_t cnt = (uint32_t)__popc(bits);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    if (bits) {
+        uint4 *dst = reinterpret_cast<uint4 *>(S.f[lane]);
+        dst[0] = make_uint4(f[0], f[1], f[2], f[3]);
+        dst[1] = make_uint4(f[4], f[5], f[6], f[7]);
+        dst[2] = make_uint4(f[8], f[9], f[10], f[11]);
+        uint32_t pos = incl - cnt;
+        for (uint32_t m = bits; m; m &= m - 1u) S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+    }
+    S.fail[lane] = 0u;
+    __syncwarp();
+    for (uint32_t i = (uint32_t)lane; i < total; i += 32u) {
+        const uint32_t e = S.list[i];
+        const int ln = (int)(e >> 4), k = (int)(e & 15u);
+        const uint8_t *px = reinterpret_cast<const uint8_t *>(S.f[ln]) + 3 * k;
+        if (!skin_rgb(px[0], px[1], px[2], D, g)) atomicOr(&S.fail[ln], 1u << k);
+    }
+    __syncwarp();
+    const uint32_t fail = S.fail[lane];
+    __syncwarp();
+    return fail;
+}
+
+// ---------------------------------------------------------------------------
+// k_morph_strip: one warp per strip of kStripRows output rows x 30 words (960 px),
+// lane j = word column (lanes 0 and 31 are the left/right halo words), rows
+// (32 + 2*HR with HR = 2*(open+close) halo rows) held in registers.  Each
+// operator neutralises out-of-image pixels (1 for erosion, 0 for dilation),
+// forms the horizontal 3-pixel AND/OR with the neighbour lanes' words, then
+// the vertical 3-row AND/OR.  Garbage from the strip's own edges moves one
+// pixel per operator and never reaches the interior (HR rows, 32 - HR bits).
+// ---------------------------------------------------------------------------
+constexpr int kStripWords = 30;
+constexpr int kStripWarps = 4;
+
+
+// One 3x3 erosion (ERO) or dilation of the strip's R rows of one word column
+// (lane), out-of-image pixels made neutral first when the strip touches an
+// image edge.  A compile-time operator, so that each row step is one
+// expression; the caller's loop over operators stays a loop, which keeps the
+// kernel small enough for the instruction cache.
+template <bool ERO, int R>
+__device__ __forceinline__ void morph_pass(uint32_t (&v)[R], bool edge, int rlo, int rhi, uint32_t wmask)
+{
+    if (edge) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
+            v[r] = ERO ? (v[r] | ~vm) : (v[r] & vm);
+        }
+    }
+    uint32_t prev = 0, cur = 0;
+#pragma unroll
+    for (int r = 0; r <= R; ++r) {
+        uint32_t nxt = cur;
+        if (r < R) {
+            const uint32_t x = v[r];
+            const uint32_t L = __shfl_up_sync(kFull, x, 1);
+            const uint32_t Rt = __shfl_down_sync(kFull, x, 1);
+            nxt = ERO ? (x & ((x << 1) | (L >> 31)) & ((x >> 1) | (Rt << 31)))
+                      : (x | (x << 1) | (L >> 31) | (x >> 1) | (Rt << 31));
+        }
+        if (r == 1) {
+            v[0] = ERO ? (cur & nxt) : (cur | nxt);
+        } else if (r >= 2) {
+            v[r - 1] = ERO ? (prev & cur & nxt) : (prev | cur | nxt);
+        }
+        prev = cur;
+        cur = nxt;
+    }
+}
+
+template <int HR>
+__device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
+                                            int lane, int sidx, uint32_t *cc_count, uint2 *cc_list,
+                                            const uint32_t *raw)
+{
+    constexpr int R = kStripRows + 2 * HR;
+    const int w = D.w, h = D.h, nwords = D.nwords;
+    const int kw = tx * kStripWords - 1 + lane;
+    const bool col_ok = kw >= 0 && kw < nwords;
+    const uint32_t wmask = !col_ok ? 0u : ((kw == nwords - 1 && (w & 31)) ? ((1u << (w & 31)) - 1u) : 0xffffffffu);
+    const int y0 = ty * kStripRows;
+    const int ybase = y0 - HR;
+    const int rlo = max(0, -ybase), rhi = min(R, h - ybase);   // rows inside the image
+    uint32_t v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = ybase + r;
+        // at L2: in the persistent tick the raw bits come from other CTAs of the launch
+        v[r] = (col_ok && r >= rlo && r < rhi) ? __ldcg(raw + (long long)y * nwords + kw) : 0u;
+    }
+    // strips away from every image edge need no neutral out-of-image pixels
+    const bool edge = rlo > 0 || rhi < R || __any_sync(kFull, wmask != 0xffffffffu);
+    // open_iters x (erode, dilate), then close_iters x (dilate, erode)
+    const int open2 = 2 * D.open_iters;
+#pragma unroll 1
+    for (int op = 0; op < HR; ++op) {   // HR == 2 (open + close) operators
+        const bool ero = (op < open2) ? ((op & 1) == 0) : (((op - open2) & 1) == 1);
+        if (ero) morph_pass<true>(v, edge, rlo, rhi, wmask);
+        else morph_pass<false>(v, edge, rlo, rhi, wmask);
+    }
+    // interior: global bit mask and mask bytes
+    const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
+    if (!interior) return;
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < kStripRows; ++i) {
+        const int r = HR + i, y = y0 + i;
+        const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
+        any |= fin;
+        D.bits[(long long)y * nwords + kw] = fin;
+        if (io.mask != nullptr && y < h) {
+            uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
+            const int npx = min(kWordPx, w - kw * kWordPx);
+            if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
+                uint32_t q[8];
+#pragma unroll
+                for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
+                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+                __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
+                __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
+            } else {
+                for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
+            }
+        }
+    }
+    // the 32x32 block of this word: the upper strip of a block clears its
+    // count; the first strip to find pixels in it lists it for k_block_cc
+    const uint32_t blk = (uint32_t)((y0 / kBlock) * nwords + kw);
+    if ((y0 % kBlock) == 0) D.count[blk] = 0u;   // the top strip of the block
+    if (any != 0u && atomicOr(D.flag + blk, 1u) == 0u) {
+        const uint32_t slot = atomicAdd(cc_count, 1u);
+        cc_list[slot] = make_uint2((uint32_t)sidx, blk);
     }
 }
 

@@ -1,8 +1,8 @@
-// hmi_tick.cu -- the whole per-frame path of every band-test stream of a batch
-// in one persistent launch per tick.
+// hmi_tick.cu -- the per-pixel work of every band-test stream of a batch in
+// one persistent launch per tick.
 //
 // The launch's CTAs take work items from a queue, in order, with one atomic
-// counter.  Per stream there are four kinds of item, each kind depending only
+// counter.  Per stream there are three kinds of item, each kind depending only
 // on the stream's items of the kind before it:
 //   luma      a chunk range: the frame's integer luma sum (Sec. 2 brightness
 //             correction, Sec. 3.2 luminosity filter); the last luma item of
@@ -10,12 +10,12 @@
 //   classify  a chunk range: gain, background band test (Sec. 3.1 (i)), gray
 //             and hue tests (Sec. 3.1 (ii), (iii)) of the out-of-band pixels
 //             and their AND, as raw mask bits
-//   blocks    up to eight 32-row strips: opening and closing (Sec. 3.1
-//             erosion and dilation) in registers, the 0/1 mask bytes, and the
-//             8-connected components of every 32x32 block with their statistics
-//   merge     the stream's union-find across block borders, the largest (or
-//             tracked) component, pointer, click state and Interface event
-//             (Mouse and Interface modules, Sec. 2)
+//   strips    up to eight strips of 16 rows: opening and closing (Sec. 3.1
+//             erosion and dilation) in registers, the mask bits and 0/1 mask
+//             bytes, and the list of 32x32 blocks holding foreground
+// The blocks' components and their merge into the pointer (Mouse module,
+// Sec. 2) follow in the tick's last two kernels, which a pipelined tick runs
+// beside the next tick's persistent launch.
 // A stream's counter of finished items of one kind releases the next kind
 // (bounded waits; a wait that runs out sets an error flag and lets the item
 // go on, so the tick always ends).  The planner orders the queue so that a
@@ -29,27 +29,16 @@
 #include <algorithm>
 
 #include "hmi_ccfill.cuh"
-#include "hmi_finish.cuh"
 #include "hmi_internal.cuh"
 #include "hmi_pixel.cuh"
 
 namespace hmi {
 
 constexpr int kTickWarps = kThreads / 32;
-constexpr int kTickAct = 1024;   // merge item: listed blocks held in shared memory
-constexpr int kTickRec = 768;    // merge item: component records held in shared memory
 constexpr uint32_t kErrWait = 16u;
 
-struct SkinSmem {                 // per warp: the classify item's gray / hue queue
-    uint32_t f[32][12];           // frame words of the lanes' chunks
-    uint16_t list[32 * kChunkPx]; // queued pixels: lane << 4 | pixel
-    uint32_t fail[32];            // pixels of each lane's chunk that fail
-};
-
-union TickSmem {
-    FinishSmem<kThreads, kTickAct, kTickRec> fin;
+struct TickSmem {
     SkinSmem skin[kTickWarps];
-    uint32_t tile[kTickWarps][kBlock][kBlock + 1];   // blocks item: one strip's final bits
 };
 
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
@@ -189,46 +178,8 @@ __device__ __forceinline__ void item_luma(const BatchDev &b, int s, int c0, int 
 // ---------------------------------------------------------------------------
 // classify item
 // ---------------------------------------------------------------------------
-// Gray and hue tests of a warp's out-of-band pixels: the warp lists them
-// (lane << 4 | pixel) in shared memory and every lane takes pixels in turn, so
-// that a chunk with many candidate pixels (the hand) does not stall the warp
-// behind one lane.  Returns this lane's pixels that fail.
-__device__ __forceinline__ uint32_t skin_fail_warp(uint32_t bits, const uint32_t (&f)[12],
-                                                   const DevStream &D, uint32_t g, SkinSmem &S,
-                                                   int lane)
-{
-    if (__ballot_sync(kFull, bits != 0u) == 0u) return 0u;
-    const uint32_t cnt = (uint32_t)__popc(bits);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += t;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (bits) {
-        uint4 *dst = reinterpret_cast<uint4 *>(S.f[lane]);
-        dst[0] = make_uint4(f[0], f[1], f[2], f[3]);
-        dst[1] = make_uint4(f[4], f[5], f[6], f[7]);
-        dst[2] = make_uint4(f[8], f[9], f[10], f[11]);
-        uint32_t pos = incl - cnt;
-        for (uint32_t m = bits; m; m &= m - 1u) S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
-    }
-    S.fail[lane] = 0u;
-    __syncwarp();
-    for (uint32_t i = (uint32_t)lane; i < total; i += 32u) {
-        const uint32_t e = S.list[i];
-        const int ln = (int)(e >> 4), k = (int)(e & 15u);
-        const uint8_t *px = reinterpret_cast<const uint8_t *>(S.f[ln]) + 3 * k;
-        if (!skin_rgb(px[0], px[1], px[2], D, g)) atomicOr(&S.fail[ln], 1u << k);
-    }
-    __syncwarp();
-    const uint32_t fail = S.fail[lane];
-    __syncwarp();
-    return fail;
-}
-
-__device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, int c1, TickSmem &sm)
+__device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, int c1, TickSmem &sm,
+                                              uint8_t *table)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const DevStream &D = b.ds[s];
@@ -237,6 +188,8 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
     if (tid == 0) wait_stage(&Y.stage, 1u, b.loop_limit, &D.st->err);
     __syncthreads();
     const uint32_t g = __ldcg(&D.st->gain_p[b.phase]);
+    fill_table(table, g);
+    __syncthreads();
     const uint64_t once = policy_evict_first();
     const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
     uint32_t *raw = D.raw[b.phase];
@@ -258,7 +211,7 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
                 load48_cg(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                 load48(D.lo + (long long)y * fpitch + 3 * x0, once, l);
                 load48(D.hi + (long long)y * fpitch + 3 * x0, once, h);
-                bits = outside_bits<kChunkPx - 1>(f, l, h, g);
+                bits = band_outside16(f, l, h, TableCorr{table});
                 const int npx = w - x0;
                 if (npx < kChunkPx) bits &= (1u << npx) - 1u;
             }
@@ -273,119 +226,20 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
 }
 
 // ---------------------------------------------------------------------------
-// blocks item
+// strips item
 // ---------------------------------------------------------------------------
-constexpr int kStripWords = 30;
-
-// One warp: opening and closing of the strip of 32 rows (one block row) x 30
-// words (lane j = word column tx * 30 - 1 + j; lanes 0 and 31 are halo words),
-// with HR = 2 (open + close) halo rows above and below held in registers; each
-// operator first makes out-of-image pixels neutral (1 for erosion, 0 for
-// dilation) and then takes the horizontal and vertical 3-pixel AND / OR.
-// Garbage from the strip's own edges moves one pixel per operator and never
-// reaches the interior.  The final bits go to the bit mask and the mask bytes,
-// and every 32x32 block of the strip gets its components (or a zero count).
 template <int HR>
-__device__ __forceinline__ void blocks_strip(const DevStream &D, const TickIO &io, const uint32_t *raw,
-                                             int ty, int tx, int lane, uint32_t (*tile)[kBlock + 1])
-{
-    constexpr int R = kBlock + 2 * HR;
-    const int w = D.w, h = D.h, nwords = D.nwords;
-    const int kw = tx * kStripWords - 1 + lane;
-    const bool col_ok = kw >= 0 && kw < nwords;
-    const uint32_t wmask = !col_ok ? 0u : ((kw == nwords - 1 && (w & 31)) ? ((1u << (w & 31)) - 1u) : 0xffffffffu);
-    const int y0 = ty * kBlock;
-    const int ybase = y0 - HR;
-    const int rlo = max(0, -ybase), rhi = min(R, h - ybase);   // rows inside the image
-    uint32_t v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int y = ybase + r;
-        v[r] = (col_ok && r >= rlo && r < rhi) ? __ldcg(raw + (long long)y * nwords + kw) : 0u;
-    }
-    const bool edge = rlo > 0 || rhi < R || __any_sync(kFull, wmask != 0xffffffffu);
-    const int nops = 2 * (D.open_iters + D.close_iters);   // == HR
-    for (int op = 0; op < nops; ++op) {
-        const bool ero = (op < 2 * D.open_iters) ? ((op & 1) == 0) : (((op - 2 * D.open_iters) & 1) == 1);
-        if (edge) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const uint32_t vm = (r >= rlo && r < rhi) ? wmask : 0u;
-                v[r] = ero ? (v[r] | ~vm) : (v[r] & vm);
-            }
-        }
-        uint32_t prev = 0, cur = 0;
-#pragma unroll
-        for (int r = 0; r <= R; ++r) {
-            uint32_t nxt = cur;
-            if (r < R) {
-                const uint32_t x = v[r];
-                const uint32_t L = __shfl_up_sync(kFull, x, 1);
-                const uint32_t Rt = __shfl_down_sync(kFull, x, 1);
-                nxt = ero ? (x & ((x << 1) | (L >> 31)) & ((x >> 1) | (Rt << 31)))
-                          : (x | (x << 1) | (L >> 31) | (x >> 1) | (Rt << 31));
-            }
-            if (r == 1) {
-                v[0] = ero ? (cur & nxt) : (cur | nxt);
-            } else if (r >= 2) {
-                v[r - 1] = ero ? (prev & cur & nxt) : (prev | cur | nxt);
-            }
-            prev = cur;
-            cur = nxt;
-        }
-    }
-    const bool interior = lane >= 1 && lane <= kStripWords && col_ok;
-    // final bits through shared memory (the rows leave registers early)
-#pragma unroll
-    for (int i = 0; i < kBlock; ++i) {
-        const int r = HR + i;
-        tile[i][lane] = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
-    }
-    uint32_t any = 0;
-    for (int i = 0; i < kBlock && interior; ++i) {
-        const int y = y0 + i;
-        const uint32_t fin = tile[i][lane];
-        any |= fin;
-        D.bits[(long long)y * nwords + kw] = fin;
-        if (io.mask != nullptr && y < h) {
-            uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
-            const int npx = min(kWordPx, w - kw * kWordPx);
-            if (npx == kWordPx && ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0)) {
-                uint32_t q[8];
-#pragma unroll
-                for (int n4 = 0; n4 < 8; ++n4) q[n4] = (((fin >> (4 * n4)) & 0xfu) * 0x00204081u) & 0x01010101u;
-                uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-                __stcs(d4, make_uint4(q[0], q[1], q[2], q[3]));
-                __stcs(d4 + 1, make_uint4(q[4], q[5], q[6], q[7]));
-            } else {
-                for (int x = 0; x < npx; ++x) dst[x] = (uint8_t)((fin >> x) & 1u);
-            }
-        }
-    }
-    __syncwarp();
-    if (interior && any == 0u) D.count[ty * nwords + kw] = 0u;
-    // the components of each non-empty block, one block at a time (lane r
-    // holds row r of the block)
-    for (unsigned m = __ballot_sync(kFull, interior && any != 0u); m; m &= m - 1u) {
-        const int jj = __ffs(m) - 1;
-        const int kj = tx * kStripWords - 1 + jj;
-        emit_block_components(D, tile[lane][jj], lane, ty * nwords + kj, kj * kWordPx, y0);
-    }
-    __syncwarp();
-}
-
-template <int HR>
-__device__ __forceinline__ void item_blocks_hr(const BatchDev &b, int s, int k0, int k1, TickSmem &sm)
+__device__ __forceinline__ void item_strips_hr(const BatchDev &b, int s, int k0, int k1)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int k = k0 + warp;
-    if (k >= k1) return;
+    if (k >= k1) return;   // warp-uniform
     const DevStream &D = b.ds[s];
     const int ty = k / D.strips_x, tx = k - ty * D.strips_x;
-    blocks_strip<HR>(D, b.io[s], D.raw[b.phase], ty, tx, lane, sm.tile[warp]);
+    morph_strip<HR>(D, b.io[s], ty, tx, lane, s, b.cc_count, b.cc_list, D.raw[b.phase]);
 }
 
-__device__ __forceinline__ void item_blocks(const BatchDev &b, int s, int k0, int k1, TickSmem &sm)
+__device__ __forceinline__ void item_strips(const BatchDev &b, int s, int k0, int k1)
 {
     const int tid = threadIdx.x;
     const DevStream &D = b.ds[s];
@@ -393,32 +247,14 @@ __device__ __forceinline__ void item_blocks(const BatchDev &b, int s, int k0, in
     if (tid == 0) wait_stage(&Y.stage, 2u, b.loop_limit, &D.st->err);
     __syncthreads();
     (void)ld_acquire(&Y.stage);   // every thread: raw bits of other CTAs are visible
-    switch (b.uniform_halo) {
-    case 0: item_blocks_hr<0>(b, s, k0, k1, sm); break;
-    case 2: item_blocks_hr<2>(b, s, k0, k1, sm); break;
-    case 4: item_blocks_hr<4>(b, s, k0, k1, sm); break;
-    case 6: item_blocks_hr<6>(b, s, k0, k1, sm); break;
-    default: item_blocks_hr<8>(b, s, k0, k1, sm); break;
+    switch (b.uniform_halo) {   // the planner keeps halos above kTickMaxHalo in the chain
+    case 0: item_strips_hr<0>(b, s, k0, k1); break;
+    case 2: item_strips_hr<2>(b, s, k0, k1); break;
+    default: item_strips_hr<4>(b, s, k0, k1); break;
     }
     __threadfence();
     __syncthreads();
-    if (tid == 0) finish_item(&Y.m, Y.nm, &Y.stage, 3u);
-}
-
-// ---------------------------------------------------------------------------
-// merge item
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void item_merge(const BatchDev &b, int s, TickSmem &sm)
-{
-    const int tid = threadIdx.x;
-    const DevStream &D = b.ds[s];
-    TickSync &Y = b.sync[s];
-    if (tid == 0) wait_stage(&Y.stage, 3u, b.loop_limit, &D.st->err);
-    __syncthreads();
-    (void)ld_acquire(&Y.stage);   // every thread: block records of other CTAs are visible
-    finish_stream<kThreads, kTickAct, kTickRec>(D, b.io[s], sm.fin, b.err, b.loop_limit);
-    __syncthreads();
-    if (tid == 0) st_release(&Y.stage, 0u);   // the stream is ready for the next tick
+    if (tid == 0) finish_item(&Y.m, Y.nm, &Y.stage, 0u);   // the stream is ready for the next tick
 }
 
 // ---------------------------------------------------------------------------
@@ -429,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_tick(BatchDev b)
     extern __shared__ __align__(16) unsigned char tick_smem[];
     TickSmem &sm = *reinterpret_cast<TickSmem *>(tick_smem);
     __shared__ unsigned long long red[kTickWarps];
+    __shared__ uint8_t table[256];   // corrected values of a classify item's frame
     __shared__ int s_next;
     const int tid = threadIdx.x;
     if (tid == 0) s_next = (int)atomicAdd(b.tick_head, 1u);
@@ -442,9 +279,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_tick(BatchDev b)
         if (b.io[s].frame != nullptr) {                     // CTA-uniform: no frame, no work
             switch (kind) {
             case kItemLuma: item_luma(b, s, e.y, e.z, red); break;
-            case kItemClassify: item_classify(b, s, e.y, e.z, sm); break;
-            case kItemBlocks: item_blocks(b, s, e.y, e.z, sm); break;
-            default: item_merge(b, s, sm); break;
+            case kItemClassify: item_classify(b, s, e.y, e.z, sm, table); break;
+            default: item_strips(b, s, e.y, e.z); break;
             }
         }
         __syncthreads();

@@ -87,7 +87,7 @@ class hmi_tuning(ctypes.Structure):
                 ("skin_ctas_per_sm", ctypes.c_int32), ("cc_ctas_per_sm", ctypes.c_int32),
                 ("groups", ctypes.c_int32), ("pipeline_depth", ctypes.c_int32),
                 ("fused", ctypes.c_int32), ("queue_lag", ctypes.c_int32),
-                ("merge_defer", ctypes.c_int32)]
+                ("merge_threads", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -557,7 +557,8 @@ def test_profile_counts_classification_kernel(fused):
         assert all(v < per["luma"] for k, v in per.items() if k != "luma")
     else:
         assert t2 == 5 and per["classify"] == pytest.approx(ms)
-        assert all(v > 0 for k, v in per.items() if k not in ("block_components", "relearn", "relearn_band"))
+        assert all(v > 0 for k, v in per.items()
+                   if k not in ("mixture", "skin", "block_components", "relearn", "relearn_band"))
     hmi.hmi_batch_destroy(b)
     g.close()
 
@@ -631,10 +632,12 @@ def test_tuning_does_not_change_results():
             plist = [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(len(idx))]
             _compare_batch(gs, os_, frames, masks, plist, f"tuned t={t}")
         # the persistent tick with a small grid, small pieces, a short queue
-        # lag (classify items wait for the gain) and every merge deferred
+        # lag (classify items wait for the gain) and small merge CTAs; then
+        # large pieces, no lag before the tail, large merge CTAs, two groups
         for shape in ({"piece_chunks": 64, "luma_ctas_per_sm": 1, "fused": 1, "queue_lag": 3,
-                       "merge_defer": 1, "groups": 1},
-                      {"piece_chunks": 2048, "fused": 1, "queue_lag": 1 << 20, "groups": 2}):
+                       "merge_threads": 256, "groups": 1},
+                      {"piece_chunks": 2048, "fused": 1, "queue_lag": 1 << 20, "merge_threads": 1024,
+                       "groups": 2}):
             hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), **shape))
             for t in range(2, 4):
                 frames = [synth.run_frame(4, i, t) for i in idx]
@@ -646,7 +649,7 @@ def test_tuning_does_not_change_results():
         for bad in ({"piece_chunks": 100}, {"piece_chunks": 0}, {"skin_ctas_per_sm": 0},
                     {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65},
                     {"pipeline_depth": 1}, {"pipeline_depth": 4}, {"fused": 2},
-                    {"queue_lag": -1}, {"queue_lag": (1 << 20) + 1}, {"merge_defer": 3}):
+                    {"queue_lag": -1}, {"queue_lag": (1 << 20) + 1}, {"merge_threads": 384}):
             t = dict(hmi.hmi_batch_get_tuning(b), **bad)
             with pytest.raises(hmi.HmiError) as e:
                 hmi.hmi_batch_set_tuning(b, t)
@@ -870,3 +873,104 @@ def test_interface_events_match_oracle():
         with pytest.raises(hmi.HmiError):
             g.set_interface(bad)
     g.close()
+
+
+# --------------------------------------------------------------------------- #
+# The persistent tick (hmi_tuning.fused = 1) against the oracle                #
+# --------------------------------------------------------------------------- #
+def _fused_batch(gs, **over):
+    b = hmi.hmi_batch_create([g.handle for g in gs])
+    hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=1, groups=1, **over))
+    return b
+
+
+def _batch_step(b, gs, frames, host=False):
+    n = len(gs)
+    if host:
+        masks = [np.empty((g.h, g.w), np.uint8) for g in gs]
+        ptrs = np.zeros(n, hmi.POINTER_DTYPE)
+        hmi.hmi_batch_process(b, frames, masks, ptrs)
+        return masks, [dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]])) for i in range(n)]
+    dframes = [_dev(f) for f in frames]
+    dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in gs]
+    dptrs = torch.zeros(n * 40, dtype=torch.uint8, device="cuda")
+    hmi.hmi_batch_process_async(b, dframes, dmasks, dptrs.data_ptr(), torch.cuda.current_stream().cuda_stream, True)
+    torch.cuda.synchronize()
+    arr = dptrs.cpu().numpy().view(hmi.POINTER_DTYPE)
+    return [m.cpu().numpy() for m in dmasks], [dict(zip(arr.dtype.names, [x.item() for x in arr[i]])) for i in range(n)]
+
+
+@pytest.mark.parametrize("cfg,frames,piece", [(1, range(0, 60, 3), 64), (2, range(0, 300, 15), 512),
+                                              (3, range(0, 600, 100), 1024)])
+def test_persistent_tick_single_stream_configs(cfg, frames, piece):
+    """Single streams of the three plain configurations, one stream per
+    persistent launch (every classify item waits for the stream's gain)."""
+    w, h = synth.shape(cfg)
+    g, o = pair(w, h)
+    learn_both(g, o, synth.learn_frames(cfg), dev=True)
+    b = _fused_batch([g], piece_chunks=piece)
+    try:
+        for t in frames:
+            fr = synth.run_frame(cfg, 0, t)
+            masks, ptrs = _batch_step(b, [g], [fr], host=(t % 2 == 1))
+            m_o, l_o, p_o, gain_o = o.process(fr)
+            assert g.last_gain() == gain_o, f"cfg{cfg} t={t} gain"
+            assert np.array_equal(masks[0], m_o), f"cfg{cfg} t={t} mask"
+            assert np.array_equal(g.labels(), l_o), f"cfg{cfg} t={t} labels"
+            assert_pointer(ptrs[0], p_o, f"cfg{cfg} t={t}")
+    finally:
+        hmi.hmi_batch_destroy(b)
+        g.close()
+
+
+def test_persistent_tick_ragged_sizes_pinned_and_pipelined():
+    """Ragged frame sizes (rows not a multiple of 16 or 32 pixels, tiny
+    frames) in one persistent launch, then the 16-aligned ones from pinned host
+    frames (copied into staging by the luma items) in pipelined calls."""
+    shapes = [(1, 1), (17, 5), (33, 33), (100, 75), (321, 241), (64, 48), (320, 240), (160, 96)]
+    gs, os_ = [], []
+    for w, h in shapes:
+        g, o = pair(w, h)
+        lf = RNG.integers(0, 256, size=(3, h, w, 3), dtype=np.uint8)
+        learn_both(g, o, lf, dev=True)
+        gs.append(g)
+        os_.append(o)
+    b = _fused_batch(gs, piece_chunks=32, queue_lag=7)
+    try:
+        for t in range(3):
+            frames = [RNG.integers(0, 256, size=(g.h, g.w, 3), dtype=np.uint8) for g in gs]
+            masks, ptrs = _batch_step(b, gs, frames)
+            for i, (g, o) in enumerate(zip(gs, os_)):
+                m_o, l_o, p_o, _ = o.process(frames[i])
+                assert np.array_equal(masks[i], m_o), f"{shapes[i]} t={t} mask"
+                assert np.array_equal(g.labels(), l_o), f"{shapes[i]} t={t} labels"
+                assert_pointer(ptrs[i], p_o, f"{shapes[i]} t={t}")
+    finally:
+        hmi.hmi_batch_destroy(b)
+    sel = [i for i, (w, h) in enumerate(shapes) if w % 16 == 0]
+    ga, oa = [gs[i] for i in sel], [os_[i] for i in sel]
+    b = _fused_batch(ga, pipeline_depth=2)
+    try:
+        s = torch.cuda.current_stream().cuda_stream
+        dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in ga]
+        dptrs = [torch.zeros(len(ga) * 40, dtype=torch.uint8, device="cuda") for _ in range(4)]
+        pinned, expect = [], []
+        for t in range(4):
+            frames = [synth.run_frame(4, 3 + i, t)[:g.h, :g.w].copy() for i, g in enumerate(ga)]
+            pinned.append([_pinned(f) for f in frames])
+            expect.append([o.process(f) for o, f in zip(oa, frames)])
+            hmi.hmi_batch_process_pipelined(b, pinned[t], dmasks if t == 3 else None, dptrs[t].data_ptr(), s, True)
+        hmi.hmi_batch_flush(b, s)
+        torch.cuda.synchronize()
+        for t in range(4):
+            arr = dptrs[t].cpu().numpy().view(hmi.POINTER_DTYPE)
+            for i in range(len(ga)):
+                assert_pointer(dict(zip(arr.dtype.names, [x.item() for x in arr[i]])), expect[t][i][2],
+                               f"pinned pipelined t={t} stream {i}")
+        for i in range(len(ga)):
+            assert np.array_equal(dmasks[i].cpu().numpy(), expect[3][i][0])
+            assert np.array_equal(ga[i].labels(), expect[3][i][1])
+    finally:
+        hmi.hmi_batch_destroy(b)
+        for g in gs:
+            g.close()

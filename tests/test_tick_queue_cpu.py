@@ -1,7 +1,7 @@
 """The persistent tick's work queue (the planner in csrc/hmi_queue.h), on the CPU.
 
 The kernel's CTAs take items in queue order, and an item waits only for its
-stream's items of the step before (luma -> classify -> blocks -> merge).  The
+stream's items of the step before (luma -> classify -> morphology strips).  The
 launch ends for any grid size only if every stream's steps come in that order
 in the queue; these tests build the planner with g++ and check that order,
 that the items cover every chunk and strip exactly once, that the counts the
@@ -32,20 +32,25 @@ def planner(tmp_path_factory):
                     os.path.join(ROOT, "tests", "native", "tick_queue_main.cpp"), "-o", exe],
                    check=True, capture_output=True)
 
-    def run(shapes, piece=512, lag=0, defer=False):
-        args = [exe, str(piece), str(lag), str(int(defer))]
+    def run(shapes, piece=512, lag=0):
+        args = [exe, str(piece), str(lag)]
         for w, h in shapes:
             args += [str(w), str(h)]
         out = subprocess.run(args, check=True, capture_output=True, text=True).stdout.split("\n")
-        items = [tuple(map(int, l.split())) for l in out if l and not l.startswith("sync")]
+        global STRIP_ROWS
+        STRIP_ROWS = int(out[0].split()[1])
+        items = [tuple(map(int, l.split())) for l in out[1:] if l and not l.startswith("sync")]
         sync = [tuple(map(int, l.split()[1:])) for l in out if l.startswith("sync")]
         return items, sync
     return run
 
 
+STRIP_ROWS = 8
+
+
 def geometry(w, h):
-    nwords, bh = (w + 31) // 32, (h + 31) // 32
-    return h * 2 * nwords, bh * ((nwords + 29) // 30)
+    nwords = (w + 31) // 32
+    return h * 2 * nwords, -(-h // STRIP_ROWS) * ((nwords + 29) // 30)
 
 
 def check_queue(shapes, items, sync, piece):
@@ -58,11 +63,11 @@ def check_queue(shapes, items, sync, piece):
             rng = sorted((b, e) for _, b, e in pos[(s, kind)])
             assert rng[0][0] == 0 and rng[-1][1] == n
             assert all(a[1] == c[0] for a, c in zip(rng, rng[1:])), (s, kind)   # exact cover
-        assert len(pos[(s, 3)]) == 1
         assert sync[s] == (len(pos[(s, 0)]), len(pos[(s, 1)]), len(pos[(s, 2)]))
         assert sync[s][0] == -(-chunks // piece)
+        assert {k for (t, k) in pos if t == s} == {0, 1, 2}
         # every step after every item of the step before
-        for k in range(3):
+        for k in range(2):
             assert max(i for i, _, _ in pos[(s, k)]) < min(i for i, _, _ in pos[(s, k + 1)]), (s, k)
 
 
@@ -98,10 +103,9 @@ def simulate(items, sync, ctas, dur):
             progressed = True
             if sl[2] == 0:
                 finished += 1
-                if kind < 3:
-                    done[s][kind] += 1
-                    if done[s][kind] == sync[s][kind]:
-                        stage[s] = kind + 1
+                done[s][kind] += 1
+                if done[s][kind] == sync[s][kind]:
+                    stage[s] = kind + 1
                 sl[0], sl[2] = sl[1], None
                 sl[1] = head if head < len(items) else None
                 head += 1
@@ -110,8 +114,8 @@ def simulate(items, sync, ctas, dur):
 
 
 def test_queue_order_and_cover_64_stream_mix(planner):
-    for piece, lag, defer in ((512, 0, False), (512, 912, False), (128, 300, True), (2048, 5, False)):
-        items, sync = planner(MIX64, piece, lag, defer)
+    for piece, lag in ((512, 0), (512, 912), (128, 300), (2048, 5)):
+        items, sync = planner(MIX64, piece, lag)
         check_queue(MIX64, items, sync, piece)
 
 
@@ -139,11 +143,11 @@ def test_queue_lag_separates_luma_and_classify(planner):
 
 def test_queue_drains_for_any_grid(planner):
     shapes = [(320, 240), (64, 64), (1920, 1080), (100, 37), (640, 480), (33, 1)]
-    for lag, defer in ((0, False), (3, False), (50, True)):
-        items, sync = planner(shapes, 256, lag, defer)
+    for lag in (0, 3, 50):
+        items, sync = planner(shapes, 256, lag)
         check_queue(shapes, items, sync, 256)
         for ctas in (1, 2, 7, 64, 1000):
-            simulate(items, sync, ctas, dur={0: 3, 1: 5, 2: 2, 3: 9})
+            simulate(items, sync, ctas, dur={0: 3, 1: 5, 2: 2})
 
 
 def test_queue_single_stream(planner):
@@ -151,4 +155,4 @@ def test_queue_single_stream(planner):
     check_queue([(640, 480)], items, sync, 512)
     kinds = [it[0] for it in items]
     assert kinds == sorted(kinds)              # one stream: the steps in turn
-    simulate(items, sync, 456, dur={0: 3, 1: 5, 2: 2, 3: 9})
+    simulate(items, sync, 456, dur={0: 3, 1: 5, 2: 2})
