@@ -34,10 +34,15 @@ CFG = 4
 RING = 4
 WORKLOAD = ("64-stream batch: 32x320x240 + 16x640x480 + 12x1280x720 + 4x1920x1080 RGB8, "
             "26.7 Mpx per tick, each stream with its own learned background")
-# algorithmic bytes per pixel of the classification (background test) kernel:
-# frame 3 B + band lo/hi 6 B read, 1 bit written
+# algorithmic bytes per pixel of the classification (background, gray and hue
+# test) kernel: frame 3 B + band lo/hi 6 B read, 1 bit written
 CLASSIFY_BYTES_PER_PX = 3 + 6 + 1 / 8
-KERNELS_PER_TICK = 6          # per stream group: luma, classify or mixture, skin, morphology, blocks, finish
+# algorithmic bytes per pixel of the whole per-pixel stage (luma, band, gray /
+# hue, morphology): the frame read once (3 B), the band (6 B), the 0/1 mask (1 B)
+K2_BYTES_PER_PX = 3 + 6 + 1
+# per-pixel kernels of a tick in the chained form (kernel indices of a tick)
+K2_KERNELS = ("luma", "classify", "skin", "morphology")
+KERNELS_PER_TICK = 5          # per stream group: luma, classify, morphology, blocks, finish
 # the Gaussian mixture background with its default 3 components: frame 3 B,
 # 12 B of state per component read and written, 1 bit written
 MIX_BENCH = dict(bg_model=1, mix_k=3)
@@ -189,9 +194,9 @@ class OraclePool:
     """The oracle as it stands (single threaded), one spawned process per core,
     each owning a fixed share of the workload's streams."""
 
-    def __init__(self, cfg: int, n_streams: int, workers: int):
+    def __init__(self, cfg: int, n_streams: int, workers: int, owned=None):
         ctx = mp.get_context("spawn")
-        self.owned = [list(range(j, n_streams, workers)) for j in range(workers)]
+        self.owned = owned if owned is not None else [list(range(j, n_streams, workers)) for j in range(workers)]
         self.owned = [o for o in self.owned if o]
         self.conns, self.procs = [], []
         for o in self.owned:
@@ -224,6 +229,19 @@ class OraclePool:
                 pass
         for p in self.procs:
             p.join(timeout=10)
+
+
+def k2_roofline(per_kernel: dict, ticks: int, px: int, fused: bool, peak: float, peak_kind: str) -> dict:
+    """The per-pixel stage against HBM: K2_BYTES_PER_PX x px over the summed
+    CUDA-event times of its kernels (the persistent tick's one launch when
+    fused), from a single-chain pass where each kernel is timed alone."""
+    names = ("luma",) if fused else K2_KERNELS
+    ms = sum(per_kernel[k] for k in names) / max(ticks, 1)
+    achieved = K2_BYTES_PER_PX * px / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_skin", "k_morph_strip"],
+            "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": achieved / peak, "algorithmic_bytes_per_tick": K2_BYTES_PER_PX * px,
+            "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks}
 
 
 def max_over_ranks(x: float, dev) -> float:
@@ -314,6 +332,17 @@ def run_ours(args) -> None:
             pool.close()
         cpu = {"frames": sum(r["frames"] for r in rs), "px": sum(r["px"] for r in rs),
                "seconds": sum(r["seconds"] for r in rs), "cores": pool.cores}
+        # the oracle on one core: one process owning a sample of the mix (four
+        # 320x240, two 640x480, one 1280x720 and one 1920x1080 stream), each
+        # stream-frame timed once
+        one = OraclePool(CFG, synth.num_streams(CFG), 1, owned=[list(SINGLE_CORE_SAMPLE)])
+        try:
+            one.run(0)
+            r1 = [one.run(1 + k) for k in range(2)]
+        finally:
+            one.close()
+        cpu["single"] = {"frames": sum(r["frames"] for r in r1), "px": sum(r["px"] for r in r1),
+                         "seconds": sum(r["seconds"] for r in r1)}
 
     hmi.load()
     # ---- serving: 256-stream arrival trace (rank 0 of a 1-GPU run), first,
@@ -431,9 +460,16 @@ def run_ours(args) -> None:
     one_chain_ms = r0.elapsed_time(r1) / roof_steps
     prof_ticks, per_kernel = hmi.hmi_batch_profile_kernels(batch)
     model = BG_MODELS[args.bg_model]
-    prof_ms = per_kernel[model["kernel"]]
+    fused_main = bool(hmi.hmi_batch_get_tuning(batch)["fused"])
+    prof_ms = per_kernel["luma" if fused_main else model["kernel"]]
     hmi.hmi_batch_profile(batch, 0)
-    hmi.hmi_batch_set_groups(batch, plain_groups)
+
+    # ---- the other form of the tick (persistent launch or chain), timed the
+    # same way, for the record -------------------------------------------------
+    other = None
+    if args.bg_model == "band" and world == 1:
+        other = bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px_per_tick, args, fused_main)
+    hmi.hmi_batch_set_tuning(batch, dict(shape_used, groups=plain_groups))
 
     # ---- end to end through the synchronous API with host buffers --------
     host_frames = []
@@ -449,6 +485,16 @@ def run_ours(args) -> None:
     for k in range(e2e_steps):
         hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], masks, host_ptrs)
     e2e_sync_s = max_over_ranks(time.perf_counter() - s0, dev)
+    # the same with every mask copied back to pinned host memory too
+    host_masks = [torch.empty((m.shape[0], m.shape[1]), dtype=torch.uint8).pin_memory().numpy() for m in masks]
+    for k in range(3):
+        hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], host_masks, host_ptrs)
+    torch.cuda.synchronize()
+    s0 = time.perf_counter()
+    for k in range(e2e_steps):
+        hmi.hmi_batch_process(batch, [host_frames[i][k % RING] for i in range(n)], host_masks, host_ptrs)
+    e2e_mask_s = max_over_ranks(time.perf_counter() - s0, dev)
+    mask_bytes = sum(int(m.size) for m in host_masks)
     h2d = sum(int(host_frames[i][0].numel()) for i in range(n))
 
     # ---- end to end through the pipelined API: the same pinned host frames
@@ -519,8 +565,9 @@ def run_ours(args) -> None:
     peak, peak_kind = peaks()
     value = whole_job_rate(n * args.steps, world, ms)
     classify_ms = prof_ms / max(prof_ticks, 1)
-    achieved = model["bytes_per_px"] * px_per_tick / (classify_ms / 1e3) / 1e9
-    traffic_px = profiled_traffic_per_px(args.bg_model)
+    roof_bytes_px = K2_BYTES_PER_PX if fused_main else model["bytes_per_px"]
+    achieved = roof_bytes_px * px_per_tick / (classify_ms / 1e3) / 1e9
+    traffic_px = None if fused_main else profiled_traffic_per_px(args.bg_model)
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -542,16 +589,20 @@ def run_ours(args) -> None:
                         "groups": plain_groups, "steps": plain_steps,
                         "launch": "hmi_batch_process_async, one CUDA graph per tick"},
         "mpx_per_s": px_per_tick * args.steps * world / (ms / 1e3) / 1e6,
-        "roofline": {"bound": "hbm", "kernel": "k_" + ("classify" if args.bg_model == "band" else "mix<3>"),
+        "roofline": {"bound": "hbm",
+                     "kernel": "k_tick" if fused_main else "k_" + ("classify" if args.bg_model == "band" else "mix<3>"),
                      "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic_px * px_per_tick) if traffic_px else None,
-                     "algorithmic_bytes_per_launch": model["bytes_per_px"] * px_per_tick,
+                     "algorithmic_bytes_per_launch": roof_bytes_px * px_per_tick,
                      "launch_ms": classify_ms, "launches_timed": prof_ticks,
                      "timed_in": "single-chain pass of the same workload, CUDA events around the "
-                                 f"{model['kernel']} kernel alone (no other kernel overlaps it)",
+                                 f"{'persistent tick' if fused_main else model['kernel']} kernel alone "
+                                 "(no other kernel overlaps it)",
                      "single_chain_ms_per_step": one_chain_ms,
                      "single_chain_kernels_us": {k: v / max(prof_ticks, 1) * 1e3 for k, v in per_kernel.items()}},
+        "k2": k2_roofline(per_kernel, prof_ticks, px_per_tick, fused_main, peak, peak_kind)
+              if args.bg_model == "band" else None,
         "e2e": {"value": n * e2e_steps * world / e2e_s, "unit": "frames/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": n * 40,
                 "h2d_GBps": h2d * e2e_steps / e2e_s / 1e9, "pipeline_depth": e2e_depth,
@@ -561,13 +612,19 @@ def run_ours(args) -> None:
                        "pointers copied back to pinned host memory; wall clock, flush and a final "
                        "synchronize inside the timed region; launch shape autotuned on the host frames",
                 "sync": {"value": n * e2e_steps * world / e2e_sync_s, "unit": "frames/s",
-                         "api": "hmi_batch_process (synchronous), same host buffers, host pointers"}},
-        "gpu_launches": KERNELS_PER_TICK * groups * args.steps,
+                         "api": "hmi_batch_process (synchronous), same host buffers, host pointers"},
+                "sync_host_masks": {"value": n * e2e_steps * world / e2e_mask_s, "unit": "frames/s",
+                                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": mask_bytes + n * 40,
+                                    "api": "hmi_batch_process (synchronous), pinned host frames, every "
+                                           "0/1 mask and pointer copied back to pinned host memory"}},
+        "gpu_launches": (3 if fused_main else KERNELS_PER_TICK) * groups * args.steps,
         "clocks": clk,
     }
     if single is not None:
         line["single_640x480"] = single
         line["single_1920x1080"] = single_hd
+    if other is not None:
+        line["other_tick_form"] = other
     if args.bg_model != "band":
         line["config"]["background"] = dict(MIX_BENCH)
     if relearn is not None:
@@ -583,14 +640,74 @@ def run_ours(args) -> None:
                                 "cores": cpu["cores"], "kind": "oracle",
                                 "sample": f"{cpu['frames']} stream-frames ({args.cpu_ticks} ticks of "
                                           f"all 64 streams), {cpu['px'] / 1e6:.0f} Mpx",
-                                "mpx_per_s": cpu["px"] / cpu["seconds"] / 1e6}
+                                "mpx_per_s": cpu["px"] / cpu["seconds"] / 1e6,
+                                "single_thread": {
+                                    "frames_per_s": cpu["single"]["frames"] / cpu["single"]["seconds"],
+                                    "mpx_per_s": cpu["single"]["px"] / cpu["single"]["seconds"] / 1e6,
+                                    "cores": 1,
+                                    "sample": f"{cpu['single']['frames']} stream-frames: 2 rounds over streams "
+                                              f"{list(SINGLE_CORE_SAMPLE)} of the mix (4x320x240, 2x640x480, "
+                                              f"1x1280x720, 1x1920x1080), "
+                                              f"{cpu['single']['px'] / 1e6:.1f} Mpx"}}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
 RELEARN_BENCH = dict(relearn_frames=30, relearn_min=20, relearn_period=300)
+# streams of the 64-stream mix for the one-core oracle timing, in the mix's own
+# proportions of sizes (indices 0-31: 320x240, 32-47: 640x480, 48-59:
+# 1280x720, 60-63: 1920x1080)
+SINGLE_CORE_SAMPLE = (0, 8, 16, 24, 32, 40, 48, 60)
 TRACK_BENCH = 64
+
+
+def bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px, args, fused_main) -> dict:
+    """The 64-stream batch with the other form of the tick: the persistent
+    launch (hmi_tuning.fused = 1; its best piece size of a short search) if the
+    main run used the chain of kernels, else the chain.  Pipelined ticks, then
+    a single-chain pass with its per-pixel stage timed by CUDA events."""
+    import torch
+    peak, peak_kind = peaks()
+    base = dict(hmi.hmi_batch_get_tuning(batch), groups=1, fused=0 if fused_main else 1)
+
+    def pipelined(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(args.warmup):
+            hmi.hmi_batch_process_pipelined(batch, [rings[i][k % RING] for i in range(n)], masks,
+                                            ptrs.data_ptr(), cs.cuda_stream, True)
+        hmi.hmi_batch_flush(batch, cs.cuda_stream)
+        torch.cuda.synchronize()
+        e0.record(cs)
+        for k in range(steps):
+            hmi.hmi_batch_process_pipelined(batch, [rings[i][k % RING] for i in range(n)], masks,
+                                            ptrs.data_ptr(), cs.cuda_stream, True)
+        hmi.hmi_batch_flush(batch, cs.cuda_stream)
+        e1.record(cs)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(20, min(args.steps, 500))
+    best = None
+    for piece in ((1024, 2048, 4096) if not fused_main else (base["piece_chunks"],)):
+        t = dict(base, piece_chunks=piece)
+        hmi.hmi_batch_set_tuning(batch, t)
+        ms = pipelined(steps)
+        if best is None or ms < best[1]:
+            best = (t, ms)
+    hmi.hmi_batch_set_tuning(batch, best[0])
+    hmi.hmi_batch_profile(batch, steps)
+    for k in range(steps):
+        hmi.hmi_batch_process_async(batch, [rings[i][k % RING] for i in range(n)], masks, ptrs.data_ptr(),
+                                    cs.cuda_stream, True)
+    ticks, per = hmi.hmi_batch_profile_kernels(batch)
+    hmi.hmi_batch_profile(batch, 0)
+    fused = bool(best[0]["fused"])
+    return {"form": "persistent tick (one launch for luma, band/gray/hue and morphology items)" if fused
+                    else "chain of kernels",
+            "tuning": best[0], "pipelined_ms_per_step": best[1], "frames_per_s": n / (best[1] / 1e3),
+            "k2": k2_roofline(per, ticks, px, fused, peak, peak_kind),
+            "single_chain_kernels_us": {k: round(v / max(ticks, 1) * 1e3, 2) for k, v in per.items()}}
 
 
 def bench_relearn_cost(hmi, synth, torch, dev, cs, rings, shape, args) -> dict:
@@ -792,7 +909,8 @@ def bench_single(hmi, synth, torch, dev, cs, args, cfg: int = 2) -> dict:
         tick(k)
     ticks, per = hmi.hmi_batch_profile_kernels(b)
     hmi.hmi_batch_profile(b, 0)
-    cls_ms = per["classify"] / max(ticks, 1)
+    fused = bool(shape["fused"])
+    cls_ms = per["luma" if fused else "classify"] / max(ticks, 1)
     peak, peak_kind = peaks()
     host = [r.cpu().pin_memory() for r in ring]
     hmask = np.empty((h, w), np.uint8)
@@ -805,12 +923,15 @@ def bench_single(hmi, synth, torch, dev, cs, args, cfg: int = 2) -> dict:
     hmi.hmi_batch_destroy(b)
     st.close()
     lat.sort()
-    achieved = CLASSIFY_BYTES_PER_PX * w * h / (cls_ms / 1e3) / 1e9
+    bpp = K2_BYTES_PER_PX if fused else CLASSIFY_BYTES_PER_PX
+    achieved = bpp * w * h / (cls_ms / 1e3) / 1e9
     return {"frames_per_s": steps / (ms / 1e3), "mpx_per_s": steps * w * h / (ms / 1e3) / 1e6,
             "ms_per_frame": ms / steps, "tuning": shape,
             "launch": "pipelined graph ticks (results one call later), launch shape autotuned for the stream",
-            "classify": {"launch_us": cls_ms * 1e3, "achieved_GBps": achieved, "frac": achieved / peak,
-                         "peak_kind": peak_kind, "bytes_per_px": CLASSIFY_BYTES_PER_PX},
+            "classify": {"kernel": "k_tick" if fused else "k_classify", "launch_us": cls_ms * 1e3,
+                         "achieved_GBps": achieved, "frac": achieved / peak,
+                         "peak_kind": peak_kind, "bytes_per_px": bpp},
+            "k2": k2_roofline(per, ticks, w * h, fused, peak, peak_kind),
             "kernels_us": {k: round(v / max(ticks, 1) * 1e3, 2) for k, v in per.items()},
             "e2e_latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99) - 1],
                                "api": "hmi_process_frame, pinned host frame, host mask + pointer"}}
@@ -849,12 +970,17 @@ def bench_serving(hmi, args) -> dict:
                 "after_first_s", "submit_lag_ms_p99")
         out["sweep"] = [{"rate_scale": r["rate_scale"],
                          "served": {k: r["served"][k] for k in keep if k in r["served"]},
-                         "plain": {k: r["plain"][k] for k in keep if k in r["plain"]}} for r in rows]
+                         "plain": {k: r["plain"][k] for k in keep if k in r["plain"]},
+                         "plain_async": {k: r["plain_async"][k] for k in keep + ("cuda_streams",)
+                                         if k in r["plain_async"]}} for r in rows]
         out["sweep_trace_s"] = args.sweep_seconds
         out["max_frames_per_s_at_p99_le_5ms"] = best
         out["slo"] = f"p99 <= {serve.SLO_MS} ms, no errors, <= {serve.DROP_BUDGET:.0%} of offered frames dropped"
         out["plain_form"] = "one synchronous hmi_process_frame per frame in arrival order, one thread, " \
                             "streams learned before the trace (no learning work timed)"
+        out["plain_async_form"] = "per frame: host-to-device copy, hmi_process_frame_async and a pointer " \
+                                  "read-back on one of 8 CUDA streams (stream id mod 8), latency taken by a " \
+                                  "completion thread when the frame's event has passed; streams learned up front"
         out["order"] = "sweep first, then the full-length trace"
     return out
 

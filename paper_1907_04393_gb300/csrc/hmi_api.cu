@@ -853,6 +853,7 @@ cudaError_t enqueue_kernels(hmi_batch *b, int slot, cudaStream_t cs, int k0, int
     cudaError_t e;
     if (ev && (e = cudaEventRecordWithFlags(ev[k0], cs, flags)) != cudaSuccess) return e;
     for (int k = k0; k < k1; ++k) {
+        NvtxRange range(tick_kernel_name(k));
         if ((e = launch_tick_kernel(k, bd, cs, b->num_sms)) != cudaSuccess) return e;
         if (ev && (e = cudaEventRecordWithFlags(ev[k + 1], cs, flags)) != cudaSuccess) return e;
     }
@@ -1125,6 +1126,7 @@ bool all_learned(hmi_batch *b)
 int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                hmi_pointer *ptrs)
 {
+    NvtxRange range("hmi tick (synchronous)");
     if (!b || !frames) return fail(HMI_ERR_INVALID_ARG);
     if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
     HMI_CUDA(cudaSetDevice(b->dev));
@@ -1147,9 +1149,10 @@ int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks
     HMI_CUDA(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, b->cs));
     HMI_CUDA(cudaStreamSynchronize(b->cs));
     if (*b->h_err) {
+        const uint32_t e = *b->h_err;
         *b->h_err = 0;
         HMI_CUDA(cudaMemset(b->d_err, 0, sizeof(uint32_t)));
-        return fail(HMI_ERR_DEVICE_TIMEOUT);
+        return fail((e & kErrBounds) ? HMI_ERR_DEVICE : HMI_ERR_DEVICE_TIMEOUT);
     }
     return HMI_OK;
 }
@@ -1157,6 +1160,7 @@ int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks
 int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                 hmi_pointer *ptrs, void *cuda_stream, int use_graph)
 {
+    NvtxRange range("hmi tick (asynchronous)");
     if (!b || !frames) return fail(HMI_ERR_INVALID_ARG);
     if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
     if (ptrs && !is_device_ptr(ptrs)) return fail(HMI_ERR_INVALID_ARG);
@@ -1176,6 +1180,7 @@ int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *mask
 int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                     hmi_pointer *ptrs, void *cuda_stream, int use_graph)
 {
+    NvtxRange range("hmi tick (pipelined)");
     if (!b || !frames || b->groups.size() != 1) return fail(HMI_ERR_INVALID_ARG);
     if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
     if (ptrs && !is_device_ptr(ptrs)) return fail(HMI_ERR_INVALID_ARG);
@@ -1280,6 +1285,7 @@ int time_ticks(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipel
 int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined,
                    hmi_tuning *best_out, double *best_us_out)
 {
+    NvtxRange range("hmi autotune");
     if (!b || !frames || ticks < 2 || ticks > 10000) return fail(HMI_ERR_INVALID_ARG);
     if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
     HMI_CUDA(cudaSetDevice(b->dev));
@@ -1596,10 +1602,24 @@ struct hmi_server {
     hmi_batch *plan = nullptr;
     std::vector<int> plan_ids;
     cudaStream_t cs = nullptr;
-    hmi_pointer *h_ptrs = nullptr, *d_ptrs = nullptr;
+    // per-round buffers, two sets: a round is posted after the next one has
+    // been issued (its pointers, error word and learning table stay put)
+    hmi_pointer *h_ptrs[2] = {}, *d_ptrs[2] = {};
     int ptr_cap = 0;
-    LearnItem *h_items = nullptr, *d_items = nullptr;   // a round's learning frames
+    LearnItem *h_items[2] = {}, *d_items = nullptr;   // a round's learning frames
     int item_cap = 0;
+    uint32_t *h_err[2] = {};      // the plan's error word after each round (pinned)
+    cudaEvent_t ev[2] = {};       // end of each round's device work
+    int next_buf = 0;
+    struct Flight {               // a round issued to the device, not yet posted
+        std::vector<SrvTake> take;
+        std::vector<int> ids;     // stream ids of the plan's streams, in plan order
+        hmi_server_round rec;
+        bool any_active = false;
+        int status = HMI_OK;
+        int buf = 0;
+    };
+    std::deque<Flight> flights;   // oldest first, at most two
     uint64_t ticks = 0, frames = 0;
     std::vector<hmi_server_round> rounds;   // ring of kRoundLog records (under mu)
     uint64_t rounds_written = 0;
@@ -1623,6 +1643,33 @@ uint8_t *pool_get(hmi_server *v, size_t bytes)
     return p;
 }
 
+// A dispatcher round is issued (copies, learning, tick and the read-back of
+// pointers and the error word, all on the server's CUDA stream, closed by an
+// event) and posted later, once its event has completed, so that the next
+// round's host work and issue overlap this round's device work.  Rounds that
+// change the set of streams (creation, retirement, re-plan) wait until no
+// round is in flight.
+void complete_round(hmi_server *v);
+
+// Post every round in flight (waiting for the device).
+void drain_rounds(hmi_server *v)
+{
+    while (!v->flights.empty()) complete_round(v);
+}
+
+// Whether the next round has setup work (streams to create or retire, or a
+// plan to re-make).
+bool setup_pending(hmi_server *v)
+{
+    std::unique_lock<std::mutex> lk(v->mu);
+    if (v->dirty) return true;
+    for (auto &kv : v->streams) {
+        const SrvStream &ss = kv.second;
+        if (ss.pending || ss.failed || (ss.releasing && ss.q.empty())) return true;
+    }
+    return false;
+}
+
 // One dispatcher round; returns false when there was nothing to do.
 constexpr int kRoundLog = 16384;
 
@@ -1633,8 +1680,17 @@ void log_round(hmi_server *v, const hmi_server_round &rec)   // under v->mu
     v->rounds_written += 1;
 }
 
-bool server_round(hmi_server *v)
+bool server_issue(hmi_server *v)
 {
+    NvtxRange range("hmi server round: issue");
+    if (!v->flights.empty() && setup_pending(v)) drain_rounds(v);
+    // Setup (creating, retiring streams, re-making the plan) is applied only
+    // with no round in flight: a round's kernels read the plan's tables and
+    // its streams' arenas until it is posted.  Only this thread issues rounds,
+    // so `idle` holds for the whole call; setup that an admission or release
+    // asks for meanwhile waits for the next idle round (the check above drains
+    // for it).
+    const bool idle = v->flights.empty();
     std::vector<SrvTake> take;
     std::vector<hmi_stream *> dead;
     std::vector<int> replan_ids;
@@ -1666,13 +1722,13 @@ bool server_round(hmi_server *v)
                 }
                 ss.q.clear();
             }
-            if ((ss.releasing || ss.failed) && ss.q.empty() && !ss.pending) {
+            if (idle && (ss.releasing || ss.failed) && ss.q.empty() && !ss.pending) {
                 if (ss.s) dead.push_back(ss.s);
                 v->used -= ss.bytes;
                 it = v->streams.erase(it);
                 v->dirty = true;
             } else {
-                if (ss.pending) {
+                if (ss.pending && idle) {
                     creates.push_back(&ss);
                     ss.pending = false;
                 }
@@ -1698,7 +1754,7 @@ bool server_round(hmi_server *v)
     }
     {
         std::unique_lock<std::mutex> lk(v->mu);
-        if (v->dirty) {
+        if (v->dirty && idle) {
             rec.replanned = 1;
             replan_ids.clear();
             for (auto &kv : v->streams) {
@@ -1752,18 +1808,24 @@ bool server_round(hmi_server *v)
     hmi_batch *b = v->plan;
     const int n = b ? b->n : 0;
     int status = b ? HMI_OK : HMI_ERR_NO_MEMORY;
+    if (status == HMI_OK && (v->ptr_cap < n || v->item_cap < n)) drain_rounds(v);   // buffers in use
+    // per-round buffers grow geometrically (streams join a few at a time, and
+    // every allocation may wait for the device)
+    const int cap = std::max(n, std::max(256, 2 * std::max(v->ptr_cap, v->item_cap)));
     if (status == HMI_OK && v->ptr_cap < n) {
-        cudaFreeHost(v->h_ptrs);
-        cudaFree(v->d_ptrs);
-        v->h_ptrs = nullptr;
-        v->d_ptrs = nullptr;
-        v->ptr_cap = 0;
-        if (cudaMallocHost(&v->h_ptrs, sizeof(hmi_pointer) * n) == cudaSuccess &&
-            cudaMalloc(&v->d_ptrs, sizeof(hmi_pointer) * n) == cudaSuccess)
-            v->ptr_cap = n;
-        else
-            status = HMI_ERR_NO_MEMORY;
+        bool ok = true;
+        for (int k = 0; k < 2; ++k) {
+            cudaFreeHost(v->h_ptrs[k]);
+            cudaFree(v->d_ptrs[k]);
+            v->h_ptrs[k] = nullptr;
+            v->d_ptrs[k] = nullptr;
+            ok = ok && cudaMallocHost(&v->h_ptrs[k], sizeof(hmi_pointer) * cap) == cudaSuccess &&
+                 cudaMalloc(&v->d_ptrs[k], sizeof(hmi_pointer) * cap) == cudaSuccess;
+        }
+        v->ptr_cap = ok ? cap : 0;
+        if (!ok) status = HMI_ERR_NO_MEMORY;
     }
+    const int buf = v->next_buf;
     // All of the round's host-to-device copies go first, back to back on the
     // copy engine: a learning frame densely into its stream's frame buffer, a
     // frame to process at the buffer's pitch.  Then the learning kernels (the
@@ -1806,14 +1868,16 @@ bool server_round(hmi_server *v)
     // learning frames: their sums in one launch for the whole round (a burst
     // of new streams learns at once), except frames the batch cannot take
     if (status == HMI_OK && v->item_cap < n) {
-        cudaFreeHost(v->h_items);
+        cudaFreeHost(v->h_items[0]);
+        cudaFreeHost(v->h_items[1]);
         cudaFree(v->d_items);
-        v->h_items = nullptr;
+        v->h_items[0] = v->h_items[1] = nullptr;
         v->d_items = nullptr;
         v->item_cap = 0;
-        if (cudaMallocHost(&v->h_items, sizeof(LearnItem) * n) == cudaSuccess &&
-            cudaMalloc(&v->d_items, sizeof(LearnItem) * n) == cudaSuccess)
-            v->item_cap = n;
+        if (cudaMallocHost(&v->h_items[0], sizeof(LearnItem) * cap) == cudaSuccess &&
+            cudaMallocHost(&v->h_items[1], sizeof(LearnItem) * cap) == cudaSuccess &&
+            cudaMalloc(&v->d_items, sizeof(LearnItem) * cap) == cudaSuccess)
+            v->item_cap = cap;
         else
             status = HMI_ERR_NO_MEMORY;
     }
@@ -1829,8 +1893,8 @@ bool server_round(hmi_server *v)
         if (ss->learn_done == 0)
             e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
         if (e == cudaSuccess && npx % 4 == 0 && (reinterpret_cast<uintptr_t>(fr) & 3u) == 0) {
-            v->h_items[nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
-                                             ss->learn_done == 0};
+            v->h_items[buf][nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
+                                                  ss->learn_done == 0};
             quads += (unsigned long long)(npx / 4);
         } else if (e == cudaSuccess) {
             e = launch_learn_accum(fr, 1, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, ss->learn_done == 0,
@@ -1842,7 +1906,7 @@ bool server_round(hmi_server *v)
         }
     }
     if (status == HMI_OK && nitems > 0 &&
-        (cudaMemcpyAsync(v->d_items, v->h_items, sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
+        (cudaMemcpyAsync(v->d_items, v->h_items[buf], sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
              cudaSuccess ||
          launch_learn_batch(v->d_items, nitems, quads, v->cs) != cudaSuccess)) {
         (void)cudaGetLastError();
@@ -1878,7 +1942,7 @@ bool server_round(hmi_server *v)
             hmi_stream *s = b->s[i];
             TickIO &t = io[b->pos[i]];
             t.mask = nullptr;
-            t.ptr_out = v->d_ptrs + i;
+            t.ptr_out = v->d_ptrs[buf] + i;
             t.src = nullptr;
             if (take[i].f.host && !take[i].learning) {
                 s->used = true;
@@ -1895,55 +1959,80 @@ bool server_round(hmi_server *v)
         }
         status = run_tick(b, slot, v->cs, false);
         if (status == HMI_OK &&
-            (cudaMemcpyAsync(v->h_ptrs, v->d_ptrs, sizeof(hmi_pointer) * n, cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
-             cudaMemcpyAsync(b->h_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess)) {
+            (cudaMemcpyAsync(v->h_ptrs[buf], v->d_ptrs[buf], sizeof(hmi_pointer) * n, cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
+             cudaMemcpyAsync(v->h_err[buf], b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
+             cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), v->cs) != cudaSuccess)) {
             (void)cudaGetLastError();
             status = HMI_ERR_DEVICE;
         }
     }
-    rec.issued_ns = now_ns();
     // whatever was enqueued has finished with the round's host frames (read
-    // by copies or by the luma pass) before they are given back
-    if (cudaStreamSynchronize(v->cs) != cudaSuccess) {
+    // by copies or by the luma pass) when the event has completed; they are
+    // given back when the round is posted
+    if (cudaEventRecord(v->ev[buf], v->cs) != cudaSuccess) {
         (void)cudaGetLastError();
         status = HMI_ERR_DEVICE;
     }
-    if (status == HMI_OK && any_active && *b->h_err) {
-        *b->h_err = 0;
-        cudaMemset(b->d_err, 0, sizeof(uint32_t));
-        status = HMI_ERR_DEVICE_TIMEOUT;
-    }
-    const uint64_t t_done = now_ns();
-    rec.done_ns = t_done;
+    rec.issued_ns = now_ns();
     rec.streams = n;
+    hmi_server::Flight F;
+    F.take = std::move(take);
+    F.ids = v->plan_ids;
+    F.rec = rec;
+    F.any_active = any_active;
+    F.status = status;
+    F.buf = buf;
+    v->flights.push_back(std::move(F));
+    v->next_buf ^= 1;
+    return true;
+}
+
+// Post the oldest round in flight: wait for its device work, then hand its
+// results (and its pooled host frames) back.
+void complete_round(hmi_server *v)
+{
+    NvtxRange range("hmi server round: post");
+    hmi_server::Flight F = std::move(v->flights.front());
+    v->flights.pop_front();
+    int status = F.status;
+    if (cudaEventSynchronize(v->ev[F.buf]) != cudaSuccess) {
+        (void)cudaGetLastError();
+        status = HMI_ERR_DEVICE;
+    }
+    if (status == HMI_OK && F.any_active && *v->h_err[F.buf])
+        status = (*v->h_err[F.buf] & kErrBounds) ? HMI_ERR_DEVICE : HMI_ERR_DEVICE_TIMEOUT;
+    *v->h_err[F.buf] = 0;
+    const uint64_t t_done = now_ns();
+    hmi_server_round &rec = F.rec;
+    rec.done_ns = t_done;
     std::unique_lock<std::mutex> lk(v->mu);
     v->ticks += 1;
-    for (int i = 0; i < (int)take.size(); ++i) {
-        const SrvFrame &f = take[i].f;
+    for (int i = 0; i < (int)F.take.size(); ++i) {
+        const SrvFrame &f = F.take[i].f;
         if (!f.host) continue;
         hmi_server_result r;
         memset(&r, 0, sizeof(r));
-        r.stream_id = v->plan_ids[i];
+        r.stream_id = F.ids[i];
         r.status = status;
         r.tag = f.tag;
         r.submit_ns = f.submit_ns;
         r.done_ns = t_done;
-        if (status == HMI_OK && take[i].learning) {
+        if (status == HMI_OK && F.take[i].learning) {
             r.status = HMI_LEARNING;
             r.pointer = empty_pointer();
         } else if (status == HMI_OK) {
-            r.pointer = v->h_ptrs[i];
+            r.pointer = v->h_ptrs[F.buf][i];
         }
         v->done.push_back(r);
         if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
         v->frames += 1;
-        if (!take[i].learning) rec.frames += 1;
+        if (!F.take[i].learning) rec.frames += 1;
     }
     log_round(v, rec);
     lk.unlock();
     v->done_cv.notify_all();
-    return true;
 }
+
 
 void server_loop(hmi_server *v)
 {
@@ -1953,12 +2042,21 @@ void server_loop(hmi_server *v)
             std::unique_lock<std::mutex> lk(v->mu);
             if (v->stop) break;
         }
-        if (!server_round(v)) {
-            std::unique_lock<std::mutex> lk(v->mu);
-            if (v->stop) break;
-            v->work_cv.wait_for(lk, std::chrono::microseconds(500));
+        // post the rounds whose device work has finished
+        while (!v->flights.empty() && cudaEventQuery(v->ev[v->flights.front().buf]) == cudaSuccess)
+            complete_round(v);
+        (void)cudaGetLastError();   // a query of unfinished work reports cudaErrorNotReady
+        const bool issued = v->flights.size() < 2 && server_issue(v);
+        if (issued) continue;
+        if (!v->flights.empty()) {
+            complete_round(v);   // nothing new to issue: wait for the device
+            continue;
         }
+        std::unique_lock<std::mutex> lk(v->mu);
+        if (v->stop) break;
+        v->work_cv.wait_for(lk, std::chrono::microseconds(500));
     }
+    drain_rounds(v);
 }
 
 }  // namespace
@@ -1980,13 +2078,23 @@ hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue)
     }
     v->budget = device_budget_bytes;
     v->max_queue = max_queue;
-    if (cudaGetDevice(&v->dev) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&v->cs, cudaStreamNonBlocking) != cudaSuccess) {
+    bool ok = cudaGetDevice(&v->dev) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&v->cs, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < 2; ++k)
+        ok = cudaEventCreateWithFlags(&v->ev[k], cudaEventDisableTiming) == cudaSuccess &&
+             cudaMallocHost(&v->h_err[k], sizeof(uint32_t)) == cudaSuccess;
+    if (!ok) {
         (void)cudaGetLastError();
+        for (int k = 0; k < 2; ++k) {
+            if (v->ev[k]) cudaEventDestroy(v->ev[k]);
+            if (v->h_err[k]) cudaFreeHost(v->h_err[k]);
+        }
+        if (v->cs) cudaStreamDestroy(v->cs);
         delete v;
         fail(HMI_ERR_DEVICE);
         return nullptr;
     }
+    *v->h_err[0] = *v->h_err[1] = 0;
     // Map the stream-arena pool up to the budget (at most a quarter of the free
     // device memory) now, so that admitting a burst of streams later only
     // sub-allocates; the pool keeps freed memory while any stream lives.
@@ -2023,9 +2131,13 @@ void hmi_server_destroy(hmi_server *v)
     }
     for (auto &kv : v->pool)
         for (auto *p : kv.second) cudaFreeHost(p);
-    cudaFreeHost(v->h_ptrs);
-    cudaFree(v->d_ptrs);
-    cudaFreeHost(v->h_items);
+    for (int k = 0; k < 2; ++k) {
+        cudaFreeHost(v->h_ptrs[k]);
+        cudaFree(v->d_ptrs[k]);
+        cudaFreeHost(v->h_items[k]);
+        cudaFreeHost(v->h_err[k]);
+        if (v->ev[k]) cudaEventDestroy(v->ev[k]);
+    }
     cudaFree(v->d_items);
     if (v->cs) cudaStreamDestroy(v->cs);
     delete v;
@@ -2271,6 +2383,7 @@ int hmi_learn_background(hmi_stream *s, const uint8_t *frames, int n)
 
 int learn_background(hmi_stream *s, const uint8_t *frames, int n)
 {
+    NvtxRange range("hmi learn background");
     if (!s || !frames || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(s->dev));
     const long long npx = (long long)s->w * s->h;

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_luma(BatchDev b)
                 npx[q] = 0;
                 if (uu < c1) {
                     const int y = chunk_row((uint32_t)uu, magic), x0 = (uu - y * cpr) * kChunkPx;
-                    if (x0 < w) {
+                    if (x0 < w && HMI_IN_BOUNDS(y < D.h && 3LL * (x0 + kChunkPx) <= io.frame_pitch, &D.st->err)) {
                         npx[q] = min(kChunkPx, w - x0);
                         if (io.src) {   // a pinned host frame: w is a multiple of 16, rows dense
                             load48_host(io.src + (long long)y * 3 * w + 3 * x0, f[q]);
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
                 y = chunk_row((uint32_t)u, D.cpr_magic);
                 j = u - y * cpr;
                 const int x0 = j * kChunkPx;
-                if (x0 < w) {
+                if (x0 < w && HMI_IN_BOUNDS(y < D.h && 3LL * (x0 + kChunkPx) <= io.frame_pitch &&
+                                                3 * (x0 + kChunkPx) <= fpitch, &D.st->err)) {
                     uint32_t l[12], h[12];
                     load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, once, f);
                     load48(lo + (long long)y * fpitch + 3 * x0, once, l);
@@ -165,7 +166,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
             // gray and hue tests of the warp's out-of-band pixels, then the AND
             bits &= ~skin_fail_warp(bits, f, D, g, skin[tid >> 5], lane);
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
-            if (u < piece.z && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+            if (u < piece.z && (u & 1) == 0 &&
+                HMI_IN_BOUNDS(y < D.bh * kBlock && (j >> 1) < D.nwords, &D.st->err))
+                raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
         }
     }
 }
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
     if (io.frame == nullptr) return;       // no frame for this stream this tick
     const int ls = (int)(strip - b.strip_prefix[lo]);
     const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
-    morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, D.raw[b.phase]);
+    morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
 }
 
 // k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
@@ -360,6 +363,7 @@ __global__ void __launch_bounds__(kBlockCcWarps * 32) k_block_cc(BatchDev b)
     for (uint32_t it = blockIdx.x * kBlockCcWarps + (threadIdx.x >> 5); it < n;
          it += gridDim.x * kBlockCcWarps) {
         const uint2 e = b.cc_list[it];
+        if (!HMI_IN_BOUNDS(e.x < (uint32_t)b.n, b.err)) continue;   // warp-uniform
         const DevStream &D = b.ds[e.x];
         const int by = (int)e.y / D.nwords, bx = (int)e.y - by * D.nwords;
         const uint32_t m = __ldcg(D.bits + (long long)(by * kBlock + lane) * D.nwords + bx);

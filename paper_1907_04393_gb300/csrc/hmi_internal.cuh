@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "hmi.h"
@@ -31,6 +32,16 @@ constexpr uint32_t kErrUnionLoop = 1u;
 constexpr uint32_t kErrFindLoop = 2u;
 constexpr uint32_t kErrSlots = 4u;
 constexpr uint32_t kErrRoot = 8u;
+constexpr uint32_t kErrBounds = 32u;   // debug builds: an index failed its bounds check
+
+// Bounds check of a computed index in debug builds (compiled with HMI_DEBUG):
+// false, with kErrBounds recorded in *err, when cond fails, so that the caller
+// skips the access; the kernel goes on (no trap).  Always true otherwise.
+#ifdef HMI_DEBUG
+#define HMI_IN_BOUNDS(cond, err) ((cond) ? true : (atomicOr((err), kErrBounds), false))
+#else
+#define HMI_IN_BOUNDS(cond, err) true
+#endif
 
 // One 8-connected component of a 32x32 block, later the accumulator of its
 // whole component when it is the root.  64 bytes.
@@ -212,6 +223,24 @@ constexpr int kThreads = 256;
 // Records `status` as the calling thread's last error (hmi_last_error) and
 // returns it (hmi_api.cu).
 int set_error(int status);
+
+// An NVTX range over a host scope (a learning call, a tick, a server round,
+// the enqueue of a tick kernel), so that a timeline tool shows the stages.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// Name of tick kernel k (kernel order of a tick, see kTickKernels).
+inline const char *tick_kernel_name(int k)
+{
+    static const char *names[] = {"hmi luma",    "hmi classify",  "hmi mixture",
+                                  "hmi relearn", "hmi relearn band", "hmi skin",
+                                  "hmi morphology", "hmi block components", "hmi merge"};
+    return (k >= 0 && k < 9) ? names[k] : "hmi kernel";
+}
 
 // ---------------------------------------------------------------------------
 // Launchers (hmi_frame.cu, hmi_cc.cu, hmi_learn.cu)

@@ -198,6 +198,7 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
 __device__ __forceinline__ void emit_block_components(const DevStream &D, uint32_t m, int lane,
                                                       int blk, int xb, int yb)
 {
+    if (!HMI_IN_BOUNDS((uint32_t)blk < (uint32_t)(D.bh * D.nwords), &D.st->err)) return;   // warp-uniform
     Comp *out = D.comp + (long long)blk * kSlots;
     uint32_t *parent = D.parent + (long long)blk * kSlots;
     int ncomp = 0;
@@ -274,7 +275,9 @@ __device__ __forceinline__ uint32_t skin_fail_warp(uint32_t bits, const uint32_t
         dst[1] = make_uint4(f[4], f[5], f[6], f[7]);
         dst[2] = make_uint4(f[8], f[9], f[10], f[11]);
         uint32_t pos = incl - cnt;
-        for (uint32_t m = bits; m; m &= m - 1u) S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
+        for (uint32_t m = bits; m; m &= m - 1u)
+            if (HMI_IN_BOUNDS(pos < 32u * kChunkPx, &D.st->err))
+                S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
     }
     S.fail[lane] = 0u;
     __syncwarp();
@@ -342,7 +345,7 @@ __device__ __forceinline__ void morph_pass(uint32_t (&v)[R], bool edge, int rlo,
 template <int HR>
 __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io, int ty, int tx,
                                             int lane, int sidx, uint32_t *cc_count, uint2 *cc_list,
-                                            const uint32_t *raw)
+                                            uint32_t cc_cap, const uint32_t *raw)
 {
     constexpr int R = kStripRows + 2 * HR;
     const int w = D.w, h = D.h, nwords = D.nwords;
@@ -378,6 +381,7 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
         const int r = HR + i, y = y0 + i;
         const uint32_t fin = v[r] & ((r >= rlo && r < rhi) ? wmask : 0u);
         any |= fin;
+        if (!HMI_IN_BOUNDS(y < D.bh * kBlock, &D.st->err)) break;
         D.bits[(long long)y * nwords + kw] = fin;
         if (io.mask != nullptr && y < h) {
             uint8_t *dst = io.mask + (long long)y * w + kw * kWordPx;
@@ -397,10 +401,11 @@ __device__ __forceinline__ void morph_strip(const DevStream &D, const TickIO &io
     // the 32x32 block of this word: the upper strip of a block clears its
     // count; the first strip to find pixels in it lists it for k_block_cc
     const uint32_t blk = (uint32_t)((y0 / kBlock) * nwords + kw);
+    if (!HMI_IN_BOUNDS(blk < (uint32_t)(D.bh * nwords), &D.st->err)) return;
     if ((y0 % kBlock) == 0) D.count[blk] = 0u;   // the top strip of the block
     if (any != 0u && atomicOr(D.flag + blk, 1u) == 0u) {
         const uint32_t slot = atomicAdd(cc_count, 1u);
-        cc_list[slot] = make_uint2((uint32_t)sidx, blk);
+        if (HMI_IN_BOUNDS(slot < cc_cap, &D.st->err)) cc_list[slot] = make_uint2((uint32_t)sidx, blk);
     }
 }
 

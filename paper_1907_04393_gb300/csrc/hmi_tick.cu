@@ -218,7 +218,8 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
         }
         bits &= ~skin_fail_warp(bits, f, D, g, S, lane);
         const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
-        if (u < c1 && (u & 1) == 0) raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+        if (u < c1 && (u & 1) == 0 && HMI_IN_BOUNDS(y < D.bh * kBlock && (j >> 1) < D.nwords, &D.st->err))
+            raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
     }
     __threadfence();
     __syncthreads();
@@ -236,7 +237,7 @@ __device__ __forceinline__ void item_strips_hr(const BatchDev &b, int s, int k0,
     if (k >= k1) return;   // warp-uniform
     const DevStream &D = b.ds[s];
     const int ty = k / D.strips_x, tx = k - ty * D.strips_x;
-    morph_strip<HR>(D, b.io[s], ty, tx, lane, s, b.cc_count, b.cc_list, D.raw[b.phase]);
+    morph_strip<HR>(D, b.io[s], ty, tx, lane, s, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
 }
 
 __device__ __forceinline__ void item_strips(const BatchDev &b, int s, int k0, int k1)

@@ -167,15 +167,19 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libhmi.so (building it first if it is missing or stale)."""
+    """Load libhmi.so (building it first if it is missing or stale).  With
+    HMI_DEBUG_BUILD=1 in the environment, the debug build (every computed index
+    of the per-pixel kernels bounds-checked) is loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"libhmi.so not found at {_build.LIB}; run the build first")
-    lib = ctypes.CDLL(_build.LIB)
+    debug = os.environ.get("HMI_DEBUG_BUILD") == "1"
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if build_if_missing and not _build.up_to_date(debug):
+        _build.build(debug=debug)
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhmi.so not found at {path}; run the build first")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
         f.restype = res

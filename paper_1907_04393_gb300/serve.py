@@ -18,7 +18,13 @@ Two ways to serve the same trace:
   * ``run_plain``: one synchronous ``hmi_process_frame`` call per frame, in
     arrival order, from one worker thread, with every stream created and
     learned before the trace starts (its learning frames are skipped, so the
-    plain form does no learning work while it is timed).
+    plain form does no learning work while it is timed);
+  * ``run_plain_async``: the same per-stream calls made asynchronous: each
+    frame is copied to its stream's device buffer and processed by
+    ``hmi_process_frame_async`` on one of several CUDA streams, its pointer
+    read back, and a completion thread takes the latency when the frame's
+    event has passed, so that the frames of different streams overlap on
+    the device.
 
 Frames come from a bank of pinned host buffers per generator stream: a ring of
 ``LEARN_RING`` distinct learning frames, cycled through the n_learn learning
@@ -334,6 +340,96 @@ def _run_plain(trace: Trace, bank: FrameBank, n_learn: int, max_backlog_s: float
     return out
 
 
+def run_plain_async(trace: Trace, bank: FrameBank, n_learn: int = N_LEARN, n_cuda_streams: int = 8,
+                    max_backlog_s: float = 1.0) -> dict:
+    """Asynchronous per-stream launches: streams learned up front; at its
+    arrival time a frame is enqueued on CUDA stream idx mod n_cuda_streams as
+    a host-to-device copy into its stream's device frame, an asynchronous
+    per-frame call and a device-to-host copy of its pointer, closed by an
+    event; a completion thread observes the events in submission order."""
+    with _no_gc_pauses():
+        return _run_plain_async(trace, bank, n_learn, n_cuda_streams, max_backlog_s)
+
+
+def _run_plain_async(trace: Trace, bank: FrameBank, n_learn: int, n_cuda_streams: int,
+                     max_backlog_s: float) -> dict:
+    import collections
+    import torch
+    lib = hmi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    streams, dframe, dptr, hptr = {}, {}, {}, {}
+    for sp in trace.streams:
+        s = hmi.Stream(sp.w, sp.h)
+        s.learn(bank.learn_block(sp.src, n_learn))
+        streams[sp.idx] = s
+        dframe[sp.idx] = torch.empty((sp.h, sp.w, 3), dtype=torch.uint8, device=dev)
+        dptr[sp.idx] = torch.zeros(40, dtype=torch.uint8, device=dev)
+        hptr[sp.idx] = torch.zeros(40, dtype=torch.uint8).pin_memory()
+    css = [torch.cuda.Stream(device=dev) for _ in range(n_cuda_streams)]
+    src = {sp.idx: sp.src for sp in trace.streams}
+    at, ai, an = _arrivals(trace)
+    now = lib.hmi_server_now_ns
+    proc = lib.hmi_process_frame_async
+    pending = collections.deque()
+    cv = threading.Condition()
+    lat, errors = [], [0]
+    done_flag = [False]
+
+    def completer():
+        while True:
+            with cv:
+                while not pending and not done_flag[0]:
+                    cv.wait(0.01)
+                if not pending and done_flag[0]:
+                    return
+                ev, due = pending.popleft()
+            ev.synchronize()
+            lat.append((now() - due) * 1e-6)
+
+    th = threading.Thread(target=completer, daemon=True)
+    th.start()
+    saturated = False
+    limit = int(max_backlog_s * 1e9)
+    t0 = now()
+    for t, idx, n in zip(at, ai, an):
+        if n < n_learn:
+            continue                          # learned up front
+        due = t0 + int(t * 1e9)
+        delay = due - now()
+        if delay > 150_000:
+            time.sleep((delay - 100_000) * 1e-9)
+        elif -delay > limit:
+            saturated = True
+            break
+        cs = css[idx % n_cuda_streams]
+        with torch.cuda.stream(cs):
+            k = n - n_learn
+            frame = bank.run[src[idx]][k % len(bank.run[src[idx]])]
+            dframe[idx].copy_(frame.view(dframe[idx].shape), non_blocking=True)
+            if proc(streams[idx].handle, dframe[idx].data_ptr(), None, dptr[idx].data_ptr(),
+                    cs.cuda_stream) != hmi.HMI_OK:
+                errors[0] += 1
+            hptr[idx].copy_(dptr[idx], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(cs)
+        with cv:
+            pending.append((ev, due))
+            cv.notify()
+    with cv:
+        done_flag[0] = True
+        cv.notify()
+    th.join()
+    wall = (now() - t0) * 1e-9
+    torch.cuda.synchronize()
+    for s in streams.values():
+        s.close()
+    out = {"frames": len(lat), "frames_per_s": len(lat) / wall, "wall_s": wall, "errors": errors[0],
+           "offered_frames_per_s": trace.frames / trace.duration, "saturated": saturated,
+           "cuda_streams": n_cuda_streams}
+    out.update(_latency_stats(lat))
+    return out
+
+
 DROP_BUDGET = 0.01
 
 
@@ -355,9 +451,10 @@ def sweep(bank: FrameBank, rates, duration: float, n_learn: int = N_LEARN, seed:
         tr = make_trace(duration, rate_scale=r, seed=seed + int(r * 1000))
         srv = run_served(tr, bank, budget_bytes, n_learn)
         pln = run_plain(tr, bank, n_learn)
-        rows.append({"rate_scale": r, "served": srv, "plain": pln})
+        pla = run_plain_async(tr, bank, n_learn)
+        rows.append({"rate_scale": r, "served": srv, "plain": pln, "plain_async": pla})
     best = {}
-    for arm in ("served", "plain"):
+    for arm in ("served", "plain", "plain_async"):
         ok = [row[arm]["frames_per_s"] for row in rows if meets_slo(row[arm])]
         best[arm] = max(ok) if ok else 0.0
     return rows, best

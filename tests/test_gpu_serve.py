@@ -95,6 +95,8 @@ def test_trace_replay_small():
     assert out["p99_ms"] < 1000
     pl = serve.run_plain(tr, bank, 3)
     assert pl["errors"] == 0 and pl["frames"] > 0
+    pa = serve.run_plain_async(tr, bank, 3, n_cuda_streams=4)
+    assert pa["errors"] == 0 and pa["frames"] > 0 and pa["p99_ms"] < 1000
 
 
 @pytest.mark.parametrize("over", [{}, dict(bg_model=1, mix_k=3)])
@@ -199,3 +201,102 @@ def test_online_learning_odd_sizes():
             st, p = got[(sh, n_learn + t)]
             assert st == hmi.HMI_OK and p == alone[sh][t], (sh, t)
     hmi.hmi_server_destroy(srv)
+
+
+def _submit_all(srv, ids, seq, pinned=False):
+    """Submit seq[s][k] for every stream, interleaved k by k; returns the tag
+    map and the buffers that must outlive the results."""
+    tag_of, tag, keep = {}, 0, []
+    for k in range(max(len(v) for v in seq.values())):
+        for s, frs in seq.items():
+            if k >= len(frs):
+                continue
+            tag += 1
+            tag_of[tag] = (s, k)
+            if pinned:
+                buf = torch.from_numpy(np.ascontiguousarray(frs[k])).pin_memory()
+                keep.append(buf)
+                assert hmi.hmi_server_submit_ref(srv, ids[s], buf.numpy(), tag) == hmi.HMI_OK
+            else:
+                assert hmi.hmi_server_submit(srv, ids[s], np.ascontiguousarray(frs[k]), tag) == hmi.HMI_OK
+    return tag_of, keep
+
+
+def _collect(srv, tag_of):
+    got = {}
+    buf = (hmi.hmi_server_result * 256)()
+    while len(got) < len(tag_of):
+        n = hmi.hmi_server_poll(srv, buf, 2_000_000)
+        assert n > 0, "server stalled"
+        for i in range(n):
+            r = buf[i]
+            got[tag_of[r.tag]] = (r.status, r.pointer.as_dict())
+    return got
+
+
+def test_rounds_overlap_on_the_device_results_equal_alone():
+    """Frames keep arriving while earlier rounds are still on the GPU: the
+    dispatcher issues a round before the previous one is posted (the round log
+    shows a round issued before its predecessor was done), and every stream's
+    pointers still equal those of the same frames processed alone."""
+    srcs = [0, 5, 40, 100, 130, 160, 195, 230, 241, 250]
+    n_learn, nframes = 4, 12
+    learn = {s: synth.learn_frames(5, s, n_learn) for s in srcs}
+    frames = {s: [synth.run_frame(5, s, t) for t in range(nframes)] for s in srcs}
+    alone = {}
+    for s in srcs:
+        st = hmi.Stream(*synth.shape(5, s))
+        st.learn(learn[s])
+        alone[s] = [st.process(f, mask=False)[1] for f in frames[s]]
+        st.close()
+    srv = hmi.hmi_server_create(1 << 34, 32)
+    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), None, learn[s], n_learn) for s in srcs}
+    tag_of, keep = _submit_all(srv, ids, frames, pinned=True)
+    got = _collect(srv, tag_of)
+    for s in srcs:
+        for t in range(nframes):
+            st, p = got[(s, t)]
+            assert st == hmi.HMI_OK and p == alone[s][t], (s, t)
+    rec = hmi.hmi_server_rounds(srv)
+    work = rec[rec["frames"] > 0]
+    overlapped = int(np.sum(work["issued_ns"][1:] < work["done_ns"][:-1]))
+    assert overlapped > 0, "no round was issued while the previous one was in flight"
+    hmi.hmi_server_destroy(srv)
+    del keep
+
+
+def test_config5_streams_against_oracle_through_the_server():
+    """Eight streams of the serving workload, two of each resolution, admitted
+    with online learning (their first 30 submitted frames are the learning
+    frames) and served interleaved: every pointer (area, box, label = smallest
+    pixel index, centroid, click state) equals the CPU oracle's for the same
+    stream learned from the same 30 frames."""
+    import oracle
+    srcs = [3, 77, 140, 185, 200, 233, 244, 255]   # 320x240 x2, 640x480 x2, 1280x720 x2, 1920x1080 x2
+    n_learn, nframes = 30, 16
+    learn = {s: synth.learn_frames(5, s, n_learn) for s in srcs}
+    frames = {s: [synth.run_frame(5, s, t) for t in range(nframes)] for s in srcs}
+    srv = hmi.hmi_server_create(1 << 34, 64)
+    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), None, None, n_learn) for s in srcs}
+    seq = {s: list(learn[s]) + frames[s] for s in srcs}
+    tag_of, keep = _submit_all(srv, ids, seq)
+    got = _collect(srv, tag_of)
+    hmi.hmi_server_destroy(srv)
+    sizes = set()
+    for s in srcs:
+        w, h = synth.shape(5, s)
+        sizes.add((w, h))
+        o = oracle.OracleStream(w, h)
+        o.learn(learn[s])
+        for k in range(n_learn):
+            assert got[(s, k)][0] == hmi.HMI_LEARNING, (s, k)
+        for t in range(nframes):
+            _, _, p_o, _ = o.process(frames[s][t], want_labels=False)
+            st, p = got[(s, n_learn + t)]
+            assert st == hmi.HMI_OK, (s, t)
+            for key in ("valid", "click", "area", "x0", "y0", "x1", "y1", "label"):
+                assert p[key] == p_o[key], (s, t, key, p[key], p_o[key])
+            for key in ("x", "y"):
+                assert p[key] == pytest.approx(p_o[key], rel=1e-5, abs=1e-6), (s, t, key)
+    assert sizes == {(320, 240), (640, 480), (1280, 720), (1920, 1080)}
+    del keep
