@@ -52,7 +52,7 @@ MIX_BYTES_PER_PX = 3 + 2 * 12 * MIX_BENCH["mix_k"] + 1 / 8
 BG_MODELS = {
     "band": dict(params={}, kernel="classify", bytes_per_px=CLASSIFY_BYTES_PER_PX,
                  profile=os.path.join(ROOT, "profiles", "k_classify_64stream.txt"),
-                 sources=("hmi_frame.cu", "hmi_internal.cuh")),
+                 sources=("hmi_frame.cu", "hmi_pixel.cuh", "hmi_band.h", "hmi_internal.cuh", "hmi_queue.h")),
     "mixture": dict(params=MIX_BENCH, kernel="mixture", bytes_per_px=MIX_BYTES_PER_PX,
                     profile=os.path.join(ROOT, "profiles", "k_mix_64stream.txt"),
                     sources=("hmi_mix.cu", "hmi_internal.cuh")),
@@ -388,6 +388,8 @@ def run_ours(args) -> None:
         if pipelined:
             hmi.hmi_batch_flush(batch, cs.cuda_stream)   # the last tick's second stage
 
+    if args.fused >= 0:
+        hmi.hmi_batch_set_tuning(batch, dict(hmi.hmi_batch_get_tuning(batch), fused=args.fused))
     # launch shape: searched by the library's autotuner (untimed), or the default
     tuned = None
     if not args.no_autotune:
@@ -467,7 +469,7 @@ def run_ours(args) -> None:
     # ---- the other form of the tick (persistent launch or chain), timed the
     # same way, for the record -------------------------------------------------
     other = None
-    if args.bg_model == "band" and world == 1:
+    if args.bg_model == "band" and world == 1 and not args.no_other_form:
         other = bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px_per_tick, args, fused_main)
     hmi.hmi_batch_set_tuning(batch, dict(shape_used, groups=plain_groups))
 
@@ -1014,6 +1016,11 @@ def main():
     ap.add_argument("--quality-frames", type=int, default=1200,
                     help="frames of the 1080p drifting scene to compare the background models on (0: skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--fused", type=int, choices=[-1, 0, 1], default=-1,
+                    help="tick form: 1 the persistent launch, 0 the chain of kernels, -1 the library "
+                         "default (or the autotuner's choice)")
+    ap.add_argument("--no-other-form", action="store_true",
+                    help="skip timing the other form of the tick")
     ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",
                     help="ticks of the timed region: pipelined (stage overlap) or plain")
     ap.add_argument("--groups", type=int, default=0,
