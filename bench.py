@@ -40,8 +40,10 @@ CLASSIFY_BYTES_PER_PX = 3 + 6 + 1 / 8
 # algorithmic bytes per pixel of the whole per-pixel stage (luma, band, gray /
 # hue, morphology): the frame read once (3 B), the band (6 B), the 0/1 mask (1 B)
 K2_BYTES_PER_PX = 3 + 6 + 1
-# per-pixel kernels of a tick in the chained form (kernel indices of a tick)
-K2_KERNELS = ("luma", "classify", "skin", "morphology")
+# per-pixel kernels of a tick in the chained form (kernel indices of a tick):
+# the band streams' gray and hue tests run inside the classify kernel, so the
+# skin kernel launches only for mixture streams
+K2_KERNELS = ("luma", "classify", "morphology")
 KERNELS_PER_TICK = 5          # per stream group: luma, classify, morphology, blocks, finish
 # the Gaussian mixture background with its default 3 components: frame 3 B,
 # 12 B of state per component read and written, 1 bit written
@@ -238,7 +240,7 @@ def k2_roofline(per_kernel: dict, ticks: int, px: int, fused: bool, peak: float,
     names = ("luma",) if fused else K2_KERNELS
     ms = sum(per_kernel[k] for k in names) / max(ticks, 1)
     achieved = K2_BYTES_PER_PX * px / (ms / 1e3) / 1e9
-    return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_skin", "k_morph_strip"],
+    return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_morph_strip"],
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak, "algorithmic_bytes_per_tick": K2_BYTES_PER_PX * px,
             "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks}
