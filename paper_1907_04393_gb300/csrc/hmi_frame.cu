@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_classify(BatchDev b)
                 }
             }
             // gray and hue tests of the warp's out-of-band pixels, then the AND
-            bits &= ~skin_fail_warp(bits, f, D, g, skin[tid >> 5], lane);
+            bits &= ~skin_fail_warp(bits, f, D, table, skin[tid >> 5], lane);
             const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
             if (u < piece.z && (u & 1) == 0 &&
                 HMI_IN_BOUNDS(y < D.bh * kBlock && (j >> 1) < D.nwords, &D.st->err))
@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_relearn(BatchDev b)
 }
 
 template <int HR>
-__global__ void __launch_bounds__(kStripWarps * 32) k_morph_strip(BatchDev b)
+__global__ void __launch_bounds__(kStripWarps * 32, 5) k_morph_strip(BatchDev b)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t strip = blockIdx.x * kStripWarps + warp;

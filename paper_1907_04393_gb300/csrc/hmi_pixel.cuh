@@ -168,10 +168,8 @@ __device__ __forceinline__ void fill_table(uint8_t *table, uint32_t g)
 // values: not gray (max - min >= S) and hue inside the arc.  The hue test
 // compares N = 512 (t + d) + d against d-scaled interval ends, which equals
 // testing h = base - 256 + floor(N / 2d) without a division.
-__device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, const DevStream &D,
-                                         uint32_t gain)
+__device__ __forceinline__ bool skin_corrected(int r, int g, int b, const DevStream &D)
 {
-    const int r = corr(r0, gain), g = corr(g0, gain), b = corr(b0, gain);
     const int mx = max(r, max(g, b));
     const int mn = min(r, min(g, b));
     const int d = mx - mn;
@@ -187,6 +185,12 @@ __device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, 
     const bool hue = ((N >= d * D.hueA[sec][0]) & (N < d * D.hueB[sec][0])) |
                      ((N >= d * D.hueA[sec][1]) & (N < d * D.hueB[sec][1]));
     return (d > 0) & (d >= D.gray_tol) & hue;
+}
+
+__device__ __forceinline__ bool skin_rgb(uint32_t r0, uint32_t g0, uint32_t b0, const DevStream &D,
+                                         uint32_t gain)
+{
+    return skin_corrected(corr(r0, gain), corr(g0, gain), corr(b0, gain), D);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,46 +250,61 @@ __device__ __forceinline__ void emit_block_components(const DevStream &D, uint32
     }
 }
 
-struct SkinSmem {                 // per warp: the classify item's gray / hue queue
+struct __align__(16) SkinSmem {   // per warp: the classify item's gray / hue queue
     uint32_t f[32][12];           // frame words of the lanes' chunks
     uint16_t list[32 * kChunkPx]; // queued pixels: lane << 4 | pixel
     uint32_t fail[32];            // pixels of each lane's chunk that fail
 };
 
-// Gray and hue tests of a warp's out-of-band pixels: the warp lists them
-// (lane << 4 | pixel) in shared memory and every lane takes pixels in turn, so
-// that a chunk with many candidate pixels (the hand) does not stall the warp
-// behind one lane.  Returns this lane's pixels that fail.
+// Gray and hue tests of a warp's out-of-band pixels, on corrected values from
+// the frame's table.  When the candidates are spread over the lanes (camera
+// noise: a pixel or two per chunk), each lane tests its own; when a few lanes
+// hold most of them (the hand), the warp lists them (lane << 4 | pixel) in
+// shared memory and every lane takes pixels in turn, so that a chunk with
+// many candidate pixels does not stall the warp behind one lane.  Returns this
+// lane's pixels that fail.
 __device__ __forceinline__ uint32_t skin_fail_warp(uint32_t bits, const uint32_t (&f)[12],
-                                                   const DevStream &D, uint32_t g, SkinSmem &S,
-                                                   int lane)
+                                                   const DevStream &D, const uint8_t *table,
+                                                   SkinSmem &S, int lane)
 {
-    if (__ballot_sync(kFull, bits != 0u) == 0u) return 0u;
     const uint32_t cnt = (uint32_t)__popc(bits);
+    const uint32_t total = __reduce_add_sync(kFull, cnt);
+    if (total == 0u) return 0u;
+    const uint32_t most = __reduce_max_sync(kFull, cnt);
+    if (bits) {
+        uint4 *dst = reinterpret_cast<uint4 *>(S.f[lane]);
+        dst[0] = make_uint4(f[0], f[1], f[2], f[3]);
+        dst[1] = make_uint4(f[4], f[5], f[6], f[7]);
+        dst[2] = make_uint4(f[8], f[9], f[10], f[11]);
+    }
+    if (most <= (total + 31u) / 32u + 1u) {   // warp-uniform: each lane its own pixels
+        const uint8_t *row = reinterpret_cast<const uint8_t *>(S.f[lane]);
+        uint32_t fail = 0;
+        for (uint32_t m = bits; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            const uint8_t *px = row + 3 * k;
+            if (!skin_corrected(table[px[0]], table[px[1]], table[px[2]], D)) fail |= 1u << k;
+        }
+        __syncwarp();   // S.f is free again
+        return fail;
+    }
     uint32_t incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t t = __shfl_up_sync(kFull, incl, o);
         if (lane >= o) incl += t;
     }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    if (bits) {
-        uint4 *dst = reinterpret_cast<uint4 *>(S.f[lane]);
-        dst[0] = make_uint4(f[0], f[1], f[2], f[3]);
-        dst[1] = make_uint4(f[4], f[5], f[6], f[7]);
-        dst[2] = make_uint4(f[8], f[9], f[10], f[11]);
-        uint32_t pos = incl - cnt;
-        for (uint32_t m = bits; m; m &= m - 1u)
-            if (HMI_IN_BOUNDS(pos < 32u * kChunkPx, &D.st->err))
-                S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
-    }
+    uint32_t pos = incl - cnt;
+    for (uint32_t m = bits; m; m &= m - 1u)
+        if (HMI_IN_BOUNDS(pos < 32u * kChunkPx, &D.st->err))
+            S.list[pos++] = (uint16_t)((lane << 4) | (__ffs(m) - 1));
     S.fail[lane] = 0u;
     __syncwarp();
     for (uint32_t i = (uint32_t)lane; i < total; i += 32u) {
         const uint32_t e = S.list[i];
         const int ln = (int)(e >> 4), k = (int)(e & 15u);
         const uint8_t *px = reinterpret_cast<const uint8_t *>(S.f[ln]) + 3 * k;
-        if (!skin_rgb(px[0], px[1], px[2], D, g)) atomicOr(&S.fail[ln], 1u << k);
+        if (!skin_corrected(table[px[0]], table[px[1]], table[px[2]], D)) atomicOr(&S.fail[ln], 1u << k);
     }
     __syncwarp();
     const uint32_t fail = S.fail[lane];

@@ -216,7 +216,7 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
                 if (npx < kChunkPx) bits &= (1u << npx) - 1u;
             }
         }
-        bits &= ~skin_fail_warp(bits, f, D, g, S, lane);
+        bits &= ~skin_fail_warp(bits, f, D, table, S, lane);
         const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
         if (u < c1 && (u & 1) == 0 && HMI_IN_BOUNDS(y < D.bh * kBlock && (j >> 1) < D.nwords, &D.st->err))
             raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
