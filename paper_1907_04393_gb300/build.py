@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libhmi.so")
 # per-pixel kernels is bounds-checked (a failed check records an error flag and
 # skips the access)
 LIB_DEBUG = os.path.join(OUT_DIR, "libhmi_debug.so")
-SOURCES = ["hmi_frame.cu", "hmi_tick.cu", "hmi_cc.cu", "hmi_learn.cu", "hmi_mix.cu", "hmi_api.cu",
+SOURCES = ["hmi_frame.cu", "hmi_tick.cu", "hmi_cc.cu", "hmi_learn.cu", "hmi_mix.cu", "hmi_api.cu", "hmi_tune.cu", "hmi_server.cu",
            "hmi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC",

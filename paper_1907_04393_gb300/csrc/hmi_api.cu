@@ -13,7 +13,8 @@
 // In order below: layouts and the pool; plans (build, re-plan, groups,
 // graphs, pipelined stages); ticks (slot preparation, synchronous,
 // asynchronous and pipelined forms, tuning and autotuning); learning; the
-// server (admission, rounds, batched learning); the exported C functions.
+// exported C functions.  The server (hmi_server_*) is in hmi_server.cu; the
+// structures both files use are in hmi_host.h.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,42 +34,34 @@
 #include <unordered_set>
 #include <vector>
 
-#include "hmi_internal.cuh"
+#include "hmi_host.h"
 #include "hmi_queue.h"
 
 using namespace hmi;
 
 namespace {
-
 thread_local int g_last_error = HMI_OK;
+}  // namespace
 
-int fail(int status)
+int hmi::fail(int status)
 {
     g_last_error = status;
     return status;
 }
 
-int cuda_fail(cudaError_t e)
+int hmi::cuda_fail(cudaError_t e)
 {
     (void)cudaGetLastError();
     (void)e;
     return fail(HMI_ERR_DEVICE);
 }
 
-}  // namespace
-
 // Thread-local status of the last failed call, for the other translation units.
 int hmi::set_error(int status) { return fail(status); }
 
 namespace {
 
-#define HMI_CUDA(call)                               \
-    do {                                             \
-        cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return cuda_fail(e_); \
-    } while (0)
 
-constexpr int kRing = 12;         // per-tick pointer slots of a launch plan (a multiple of kPhases)
 // Default launch shape (hmi_tuning): 16-px chunks per CTA piece of the
 // per-pixel kernels (512 = 8192 px), luma CTAs per SM (0 = as many as fit),
 // skin-test and block-component CTAs per SM, stream groups (0 = by the
@@ -77,7 +70,6 @@ constexpr int kRing = 12;         // per-tick pointer slots of a launch plan (a 
 // queue lag chosen from the grid, 512 threads per stream merge.
 constexpr hmi_tuning kDefaultTuning = {512, 0, 8, 8, 0, 2, 0, 0, 0};
 
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool params_valid(const hmi_params &p)
 {
@@ -134,19 +126,6 @@ struct Arena {
     }
 };
 
-struct Layout {
-    int w, h, nwords, bh, tiles_x, strips_x, fpitch;
-    size_t frame_ph[kPhases];     // staging frames for pinned host frames, by tick phase
-    size_t npx, frame, lo, hi, S, Q, vmin, vmax, raw[kPhases], bits[kPhases], comp, parent,
-        count[kPhases], flag[kPhases], mask, st, hist, ds, ptr, ui, total;
-    // re-learning sums (only with re-learning on): rows of rpitch pixels
-    int rpitch;
-    size_t rS, rQ, rmin, rmax, rcnt, rpx;
-    // Gaussian mixture (bg_model 1 only): mbytes of 32-pixel tiles, nwords
-    // per row, 6 mix_k uint16 fields of 32 pixels each
-    int mix_k;
-    size_t mix, mbytes;
-};
 
 Layout make_layout(int w, int h, const hmi_params &p)
 {
@@ -214,7 +193,9 @@ struct ArenaPools {
 };
 ArenaPools g_pools;
 
-cudaMemPool_t arena_pool(int dev)
+}  // namespace
+
+cudaMemPool_t hmi::arena_pool(int dev)
 {
     if (dev < 0 || dev >= 64) return nullptr;
     std::lock_guard<std::mutex> lk(g_pools.mu);
@@ -240,6 +221,8 @@ cudaMemPool_t arena_pool(int dev)
     return g_pools.pool[dev];
 }
 
+namespace {
+
 bool is_device_ptr(const void *p)
 {
     if (p == nullptr) return false;
@@ -253,120 +236,7 @@ bool is_device_ptr(const void *p)
 
 }  // namespace
 
-struct hmi_batch;
-struct hmi_stream;
-// learning from frames without preparing the single-frame plan (the server's)
-extern "C" int learn_background(hmi_stream *s, const uint8_t *frames, int n);
 
-struct hmi_stream {
-    int dev = 0;
-    int w = 0, h = 0;
-    hmi_params p{};
-    Layout L{};
-    uint8_t *arena = nullptr;
-    DevStream ds{};          // host copy (the buffers of tick phase 0)
-    DevStream ds_phase[kPhases]{};   // host copies of the descriptor of each tick phase
-    DevStream *d_ds = nullptr;       // device copies, kPhases of them
-    StreamState *st = nullptr;
-    uint8_t *d_frame = nullptr, *d_mask = nullptr;
-    uint32_t *d_S = nullptr, *d_Q = nullptr;
-    uint8_t *d_vmin = nullptr, *d_vmax = nullptr;
-    hmi_pointer *d_ptr = nullptr;
-    int learned = 0;
-    int n_learn = 0;
-    bool pooled = false;         // arena from the library's memory pool
-    bool used = false;           // has been given frames (learning must wait for its work)
-    cudaStream_t cs = nullptr;
-    hmi_batch *self = nullptr;   // one-stream plan of hmi_process_frame, made on first use
-};
-
-// One chain of tick kernels over a subset of the batch's streams.
-struct Group {
-    int off = 0, cnt = 0;         // range in the permuted stream order
-    BatchDev bd{};                // io, phase and skin queue are set per tick slot
-    uint32_t *skin_count_p[kPhases] = {};   // skin queue of each tick phase
-    uint2 *skin_list_p[kPhases] = {};
-    uint32_t *cc_count_p[kPhases] = {};     // listed blocks of each tick phase
-    uint2 *cc_list_p[kPhases] = {};
-    cudaStream_t cs = nullptr;    // branch stream (also joins graph capture)
-    cudaEvent_t ev_luma = nullptr, ev_done = nullptr;
-};
-
-struct hmi_batch {
-    int dev = 0;
-    int n = 0;
-    hmi_tuning tune{};            // launch shape of the plan
-    uint32_t loop_limit = 0;      // bound of the device loops (0: kLoopLimit)
-    int cap = 0;                  // streams the per-batch buffers hold
-    size_t plan_cap = 0;          // bytes of the plan table buffer
-    std::vector<hmi_stream *> s;  // user order
-    std::vector<int> pos;         // user index -> permuted position
-    std::vector<Group> groups;
-    uint8_t *arena = nullptr;     // per-batch device buffers
-    uint8_t *plan = nullptr;      // per-plan device tables
-    const DevStream *ds_tab = nullptr;   // in plan: kPhases tables of n descriptors
-    TickIO *h_io = nullptr;       // pinned mirrors, kRing x n, permuted order
-    TickIO *d_io = nullptr;       // device copies, kRing x n
-    hmi_pointer *d_ptrs = nullptr;  // n pointers for the synchronous form, user order
-    uint32_t *d_err = nullptr;    // batch error word (device)
-    uint32_t *h_err = nullptr;    // pinned
-    cudaEvent_t slot_ev[kRing] = {};
-    bool slot_used[kRing] = {};
-    int next = 0;
-    cudaStream_t cs = nullptr;    // origin stream of the synchronous form and of graph capture
-    cudaEvent_t ev_fork = nullptr;
-    int num_sms = 1;
-    cudaGraphExec_t graph[kRing] = {};     // plain tick graphs
-    // profiling tick graphs (single group): an event-record node before the
-    // first kernel and after each, retargeted to the tick's events at launch;
-    // the source graph is kept alive for its node handles
-    cudaGraph_t pgraph_src[kRing] = {};
-    cudaGraphExec_t pgraph[kRing] = {};
-    cudaGraphNode_t ev_node[kRing][kTickKernels + 1] = {};
-    cudaEvent_t dummy_ev[kTickKernels + 1] = {};
-    // pipelined ticks (single group): slots of the ticks still in flight,
-    // newest first (pend[j] has run stages 0 .. j and runs stage j + 1 next),
-    // the depth they were started with, an event at the end of the last
-    // pipelined call, a second branch stream and the branches' end events,
-    // and per slot the graph of a full pipelined call
-    int npend = 0;
-    int pend[kPhases - 1] = {};
-    int pend_depth = 0;
-    cudaEvent_t pipe_ev = nullptr;
-    cudaStream_t cs2 = nullptr;
-    cudaEvent_t side_done[kPhases - 1] = {};
-    cudaGraphExec_t pipe_graph[kRing] = {};
-    // profiling of the classification kernel (single-group plans)
-    std::vector<cudaEvent_t> prof_ev;
-    int prof_max = 0, prof_used = 0;
-    // device buffers already validated (skips a pointer-attribute query per
-    // buffer per tick); bounded, cleared when full
-    std::unordered_set<const void *> seen;
-    bool seen_device(const void *p) const { return seen.count(p) != 0; }
-    void remember_device(const void *p)
-    {
-        if (seen.size() >= 65536) seen.clear();
-        seen.insert(p);
-    }
-    // pinned host buffers already validated, with their device-accessible
-    // address (the caller keeps them pinned while the batch uses them)
-    std::unordered_map<const void *, const uint8_t *> pinned;
-    const uint8_t *pinned_dev(const void *p)
-    {
-        auto it = pinned.find(p);
-        if (it != pinned.end()) return it->second;
-        cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return nullptr;
-        }
-        if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
-        if (pinned.size() >= 65536) pinned.clear();
-        const uint8_t *d = static_cast<const uint8_t *>(at.devicePointer);
-        pinned.emplace(p, d);
-        return d;
-    }
-};
 
 namespace {
 
@@ -471,7 +341,9 @@ void group_destroy(Group &g)
     g.ev_luma = g.ev_done = nullptr;
 }
 
-void plan_free(hmi_batch *b)
+}  // namespace
+
+void hmi::plan_free(hmi_batch *b)
 {
     plan_free_graphs(b);
     for (auto &g : b->groups) group_destroy(g);
@@ -481,9 +353,7 @@ void plan_free(hmi_batch *b)
     b->plan_cap = 0;
 }
 
-int flush_pending(hmi_batch *b, cudaStream_t cs);
-
-int batch_free(hmi_batch *b)
+int hmi::batch_free(hmi_batch *b)
 {
     if (!b) return HMI_OK;
     cudaSetDevice(b->dev);
@@ -511,11 +381,15 @@ int batch_free(hmi_batch *b)
     return HMI_OK;
 }
 
+namespace {
+
 // Build the launch plan with `ng` stream groups: streams are dealt to groups
 // by pixel count (largest first, to the least-loaded group); each group gets
 // its own descriptor array, prefix tables, work pieces, counters and
 // component list, and its own branch stream.
-int plan_build(hmi_batch *b, int ng)
+}  // namespace
+
+int hmi::plan_build(hmi_batch *b, int ng)
 {
     const int n = b->n;
     ng = std::max(1, std::min(ng, n));
@@ -715,6 +589,8 @@ int plan_build(hmi_batch *b, int ng)
     return HMI_OK;
 }
 
+namespace {
+
 bool streams_ok(hmi_stream *const *s, int n)
 {
     if (!s || n < 1 || n > kMaxBatch) return false;
@@ -755,7 +631,9 @@ bool batch_alloc_io(hmi_batch *b, int cap)
 // Stream groups of a plan left at groups = 0: one when every stream can run
 // in the persistent tick (band streams: a group's persistent launch already
 // fills the GPU), else two overlapping chains.
-int default_groups(hmi_stream *const *s, int n, const hmi_tuning &t)
+}  // namespace
+
+int hmi::default_groups(hmi_stream *const *s, int n, const hmi_tuning &t)
 {
     bool fusable = t.fused != 0;
     for (int i = 0; i < n && fusable; ++i)
@@ -763,7 +641,8 @@ int default_groups(hmi_stream *const *s, int n, const hmi_tuning &t)
     return fusable ? 1 : std::min(2, n);
 }
 
-hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
+
+hmi_batch *hmi::batch_new(hmi_stream *const *s, int n, int ngroups)
 {
     if (!streams_ok(s, n)) {
         fail(HMI_ERR_INVALID_ARG);
@@ -813,6 +692,8 @@ hmi_batch *batch_new(hmi_stream *const *s, int n, int ngroups)
     }
     return b;
 }
+
+namespace {
 
 // Kernels of one tick with the slot's pointer table.  Each group runs its
 // chain (luma, classify, morphology, block components, finish) on its own
@@ -957,7 +838,9 @@ int build_pipe_graph(hmi_batch *b, int slot, int depth)
 
 // Run the remaining stages of the in-flight pipelined ticks on cs, oldest
 // first.
-int flush_pending(hmi_batch *b, cudaStream_t cs)
+}  // namespace
+
+int hmi::flush_pending(hmi_batch *b, cudaStream_t cs)
 {
     if (b->npend == 0) return HMI_OK;
     int first[kPhases + 1];
@@ -971,6 +854,8 @@ int flush_pending(hmi_batch *b, cudaStream_t cs)
     }
     return HMI_OK;
 }
+
+namespace {
 
 // Capture one tick into a graph: the plain form, or (profiling, single group)
 // the form with event-record nodes around each kernel.
@@ -1076,7 +961,9 @@ int prepare_slot(hmi_batch *b, int slot, const uint8_t *const *frames, uint8_t *
     return HMI_OK;
 }
 
-int acquire_slot(hmi_batch *b)
+}  // namespace
+
+int hmi::acquire_slot(hmi_batch *b)
 {
     const int slot = b->next;
     b->next = (b->next + 1) % kRing;
@@ -1087,7 +974,8 @@ int acquire_slot(hmi_batch *b)
     return slot;
 }
 
-int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
+
+int hmi::run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
 {
     const cudaEvent_t *ev = nullptr;
     if (b->prof_used < b->prof_max && b->groups.size() == 1) {
@@ -1116,12 +1004,15 @@ int run_tick(hmi_batch *b, int slot, cudaStream_t cs, bool use_graph)
     return HMI_OK;
 }
 
-bool all_learned(hmi_batch *b)
+
+bool hmi::all_learned(hmi_batch *b)
 {
     for (auto s : b->s)
         if (!s->learned) return false;
     return true;
 }
+
+namespace {
 
 int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                hmi_pointer *ptrs)
@@ -1157,7 +1048,9 @@ int batch_sync(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks
     return HMI_OK;
 }
 
-int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+}  // namespace
+
+int hmi::batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                 hmi_pointer *ptrs, void *cuda_stream, int use_graph)
 {
     NvtxRange range("hmi tick (asynchronous)");
@@ -1177,7 +1070,8 @@ int batch_async(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *mask
     return run_tick(b, slot, cs, use_graph != 0);
 }
 
-int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
+
+int hmi::batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *masks,
                     hmi_pointer *ptrs, void *cuda_stream, int use_graph)
 {
     NvtxRange range("hmi tick (pipelined)");
@@ -1222,151 +1116,7 @@ int batch_pipelined(hmi_batch *b, const uint8_t *const *frames, uint8_t *const *
     return HMI_OK;
 }
 
-bool tuning_ok(const hmi_tuning &t)
-{
-    return t.piece_chunks >= 32 && t.piece_chunks <= 65536 && t.piece_chunks % 32 == 0 &&
-           t.luma_ctas_per_sm >= 0 && t.luma_ctas_per_sm <= 32 && t.skin_ctas_per_sm >= 1 &&
-           t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
-           t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases &&
-           (t.fused == 0 || t.fused == 1) && t.queue_lag >= 0 && t.queue_lag <= (1 << 20) &&
-           (t.merge_threads == 0 || t.merge_threads == 256 || t.merge_threads == 512 ||
-            t.merge_threads == 1024);
-}
-
-// Apply a launch shape: the plan is re-made with the device idle.
-int batch_retune(hmi_batch *b, const hmi_tuning &t)
-{
-    if (!b || !tuning_ok(t)) return fail(HMI_ERR_INVALID_ARG);
-    HMI_CUDA(cudaSetDevice(b->dev));
-    const int st = flush_pending(b, b->cs);
-    if (st != HMI_OK) return st;
-    HMI_CUDA(cudaDeviceSynchronize());
-    plan_free(b);
-    for (int i = 0; i < kRing; ++i) b->slot_used[i] = false;
-    b->tune = t;
-    return plan_build(b, t.groups > 0 ? t.groups : default_groups(b->s.data(), b->n, t));
-}
-
-// Microseconds per tick of `ticks` ticks of `frames` with the current plan
-// (pipelined or plain graph ticks on the batch's own stream, masks and
-// pointers not written), after three untimed ticks.
-int time_ticks(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined, double *us)
-{
-    auto one = [&]() {
-        return pipelined ? batch_pipelined(b, frames, nullptr, nullptr, b->cs, 1)
-                         : batch_async(b, frames, nullptr, nullptr, b->cs, 1);
-    };
-    for (int i = 0; i < 3; ++i) {
-        const int st = one();
-        if (st != HMI_OK) return st;
-    }
-    int st = flush_pending(b, b->cs);
-    if (st != HMI_OK) return st;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        if (e0) cudaEventDestroy(e0);
-        return cuda_fail(cudaErrorMemoryAllocation);
-    }
-    cudaEventRecord(e0, b->cs);
-    for (int i = 0; i < ticks && st == HMI_OK; ++i) st = one();
-    if (st == HMI_OK) st = flush_pending(b, b->cs);
-    cudaEventRecord(e1, b->cs);
-    float ms = 0.f;
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (st != HMI_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(e);
-    *us = 1e3 * ms / ticks;
-    return HMI_OK;
-}
-
-int batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined,
-                   hmi_tuning *best_out, double *best_us_out)
-{
-    NvtxRange range("hmi autotune");
-    if (!b || !frames || ticks < 2 || ticks > 10000) return fail(HMI_ERR_INVALID_ARG);
-    if (!all_learned(b)) return fail(HMI_ERR_NOT_LEARNED);
-    HMI_CUDA(cudaSetDevice(b->dev));
-    int st = flush_pending(b, b->cs);
-    if (st != HMI_OK) return st;
-    HMI_CUDA(cudaDeviceSynchronize());
-    // the streams' click state, pointer history and adaptive background
-    // (band, re-learning sums, mixture), put back afterwards
-    std::vector<std::pair<void *, size_t>> keep;
-    for (hmi_stream *s : b->s) {
-        const Layout &L = s->L;
-        keep.emplace_back(s->st, sizeof(StreamState));
-        keep.emplace_back(s->ds.hist, sizeof(uint32_t) * std::max<int>(s->p.click_window, 1));
-        keep.emplace_back(s->arena + L.lo, (size_t)L.h * L.fpitch);
-        keep.emplace_back(s->arena + L.hi, (size_t)L.h * L.fpitch);
-        if (L.rpx) {
-            keep.emplace_back(s->arena + L.rS, L.rpx * 3 * 2);
-            keep.emplace_back(s->arena + L.rQ, L.rpx * 3 * 4);
-            keep.emplace_back(s->arena + L.rmin, L.rpx * 3);
-            keep.emplace_back(s->arena + L.rmax, L.rpx * 3);
-            keep.emplace_back(s->arena + L.rcnt, L.rpx);
-        }
-        if (L.mix_k) keep.emplace_back(s->arena + L.mix, L.mbytes);
-    }
-    size_t total = 0;
-    for (auto &k : keep) total += k.second;
-    uint8_t *save = nullptr;
-    HMI_CUDA(cudaMalloc(&save, total));
-    size_t off = 0;
-    for (auto &k : keep) {
-        cudaMemcpyAsync(save + off, k.first, k.second, cudaMemcpyDeviceToDevice, b->cs);
-        off += k.second;
-    }
-    const hmi_tuning start = b->tune;
-    hmi_tuning cur = start;
-    if (pipelined) cur.groups = 1;
-    double cur_us = 0.0;
-    st = batch_retune(b, cur);
-    if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &cur_us);
-    // one parameter at a time, each over its candidate values
-    struct Axis {
-        int32_t hmi_tuning::*field;
-        std::vector<int32_t> values;
-    };
-    std::vector<Axis> axes = {{&hmi_tuning::fused, {0, 1}},
-                              {&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
-                              {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
-                              {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},
-                              {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}},
-                              {&hmi_tuning::merge_threads, {256, 512, 1024}}};
-    if (pipelined) axes.push_back({&hmi_tuning::pipeline_depth, {2, 3}});
-    else axes.push_back({&hmi_tuning::groups, {1, 2, 3}});
-    for (const Axis &ax : axes) {
-        for (int32_t v : ax.values) {
-            if (st != HMI_OK || cur.*ax.field == v) continue;
-            hmi_tuning cand = cur;
-            cand.*ax.field = v;
-            double us = 0.0;
-            st = batch_retune(b, cand);
-            if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &us);
-            if (st == HMI_OK && us < cur_us) {
-                cur = cand;
-                cur_us = us;
-            }
-        }
-    }
-    const int st_apply = batch_retune(b, st == HMI_OK ? cur : start);
-    cudaDeviceSynchronize();
-    off = 0;
-    for (auto &k : keep) {
-        cudaMemcpy(k.first, save + off, k.second, cudaMemcpyDeviceToDevice);
-        off += k.second;
-    }
-    cudaFree(save);
-    if (st != HMI_OK) return st;
-    if (st_apply != HMI_OK) return st_apply;
-    if (best_out) *best_out = cur;
-    if (best_us_out) *best_us_out = cur_us;
-    return HMI_OK;
-}
-
+namespace {
 int batch_set_groups(hmi_batch *b, int ng)
 {
     if (!b || ng < 1 || ng > 64) return fail(HMI_ERR_INVALID_ARG);
@@ -1400,7 +1150,9 @@ void release_arena(hmi_stream *s)
 // CUDA stream `order` (no host synchronisation: usable by work enqueued on
 // `order`, and by any work once `order` has been synchronised), or, with
 // order NULL, on its own CUDA stream and synchronised before returning.
-hmi_stream *create_stream_on(int w, int h, const hmi_params *p, cudaStream_t order)
+}  // namespace
+
+hmi_stream *hmi::create_stream_on(int w, int h, const hmi_params *p, cudaStream_t order)
 {
     hmi_params d;
     hmi_default_params(&d);
@@ -1468,6 +1220,8 @@ hmi_stream *create_stream_on(int w, int h, const hmi_params *p, cudaStream_t ord
     return s;
 }
 
+namespace {
+
 hmi_batch *self_plan(hmi_stream *s)
 {
     if (!s->self) {
@@ -1485,7 +1239,9 @@ hmi_batch *self_plan(hmi_stream *s)
 // reusing its buffers, branch streams and events where they are large enough,
 // so that a plan can follow streams joining and leaving without allocating on
 // every change.  The batch's error word is cleared.
-int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
+}  // namespace
+
+int hmi::batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
 {
     if (!b || !streams_ok(s, n) || s[0]->dev != b->dev) return fail(HMI_ERR_INVALID_ARG);
     HMI_CUDA(cudaSetDevice(b->dev));
@@ -1504,17 +1260,25 @@ int batch_replan(hmi_batch *b, hmi_stream *const *s, int n, int ngroups)
     return plan_build(b, ngroups);
 }
 
+namespace {
+
 // An empty Gaussian mixture (every plane zero: no component), before its
 // learning frames.
-cudaError_t enqueue_mix_reset(hmi_stream *s, cudaStream_t cs)
+}  // namespace
+
+cudaError_t hmi::enqueue_mix_reset(hmi_stream *s, cudaStream_t cs)
 {
     if (!s->L.mix_k) return cudaSuccess;
     return cudaMemsetAsync(s->arena + s->L.mix, 0, s->L.mbytes, cs);
 }
 
+namespace {
+
 // Band of a stream from its learned sums after n frames (Sec. 3.1 (i)), in
 // the padded row layout; the padding bytes are zeroed first.
-cudaError_t enqueue_band(hmi_stream *s, int n, cudaStream_t cs)
+}  // namespace
+
+cudaError_t hmi::enqueue_band(hmi_stream *s, int n, cudaStream_t cs)
 {
     const size_t bytes = (size_t)s->h * s->L.fpitch;
     cudaError_t e = cudaSuccess;
@@ -1536,764 +1300,6 @@ cudaError_t enqueue_band(hmi_stream *s, int n, cudaStream_t cs)
 }
 
 
-// ===========================================================================
-// Server: admission by device-memory budget, resident streams, continuous
-// batching by a dispatcher thread (one tick over all admitted streams per
-// round, streams without a pending frame marked inactive by a null frame).
-// ===========================================================================
-struct SrvFrame {
-    const uint8_t *host = nullptr;   // pinned copy, or the caller's buffer
-    size_t bytes = 0;
-    uint64_t tag = 0, submit_ns = 0;
-    bool owned = false;              // host is a pooled copy to give back
-};
-
-struct SrvStream {
-    hmi_stream *s = nullptr;         // null until the dispatcher has created it
-    int w = 0, h = 0;
-    hmi_params p{};
-    size_t bytes = 0;
-    bool pending = false;            // admitted, creation left to the dispatcher
-    bool failed = false;             // creation failed: queued frames are returned as errors
-    bool releasing = false;
-    int learn_n = 0, learn_done = 0;   // online learning: frames wanted / taken
-    std::deque<SrvFrame> q;
-};
-
-struct SrvTake {
-    SrvFrame f;
-    SrvStream *ss = nullptr;
-    bool learning = false;
-    const uint8_t *src = nullptr;   // a pinned frame the luma pass reads itself
-};
-
-hmi_pointer empty_pointer()
-{
-    hmi_pointer p;
-    memset(&p, 0, sizeof(p));
-    p.x = p.y = -1.0f;
-    p.x0 = p.y0 = p.x1 = p.y1 = -1;
-    p.label = -1;
-    return p;
-}
-
-uint64_t now_ns()
-{
-    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
-               std::chrono::steady_clock::now().time_since_epoch())
-        .count();
-}
-
-}  // namespace
-
-struct hmi_server {
-    int dev = 0;
-    size_t budget = 0, used = 0;
-    int max_queue = 8;
-    std::mutex mu;
-    std::condition_variable work_cv, done_cv;
-    std::map<int, SrvStream> streams;
-    int next_id = 1;
-    std::deque<hmi_server_result> done;
-    std::map<size_t, std::vector<uint8_t *>> pool;   // free pinned buffers by size
-    bool stop = false, dirty = false;
-    std::thread worker;
-    // dispatcher-only state
-    hmi_batch *plan = nullptr;
-    std::vector<int> plan_ids;
-    cudaStream_t cs = nullptr;
-    // per-round buffers, two sets: a round is posted after the next one has
-    // been issued (its pointers, error word and learning table stay put)
-    hmi_pointer *h_ptrs[2] = {}, *d_ptrs[2] = {};
-    int ptr_cap = 0;
-    LearnItem *h_items[2] = {}, *d_items = nullptr;   // a round's learning frames
-    int item_cap = 0;
-    uint32_t *h_err[2] = {};      // the plan's error word after each round (pinned)
-    cudaEvent_t ev[2] = {};       // end of each round's device work
-    int next_buf = 0;
-    struct Flight {               // a round issued to the device, not yet posted
-        std::vector<SrvTake> take;
-        std::vector<int> ids;     // stream ids of the plan's streams, in plan order
-        hmi_server_round rec;
-        bool any_active = false;
-        int status = HMI_OK;
-        int buf = 0;
-    };
-    std::deque<Flight> flights;   // oldest first, at most two
-    uint64_t ticks = 0, frames = 0;
-    std::vector<hmi_server_round> rounds;   // ring of kRoundLog records (under mu)
-    uint64_t rounds_written = 0;
-};
-
-namespace {
-
-uint8_t *pool_get(hmi_server *v, size_t bytes)
-{
-    auto &fl = v->pool[bytes];
-    if (!fl.empty()) {
-        uint8_t *p = fl.back();
-        fl.pop_back();
-        return p;
-    }
-    uint8_t *p = nullptr;
-    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return nullptr;
-    }
-    return p;
-}
-
-// A dispatcher round is issued (copies, learning, tick and the read-back of
-// pointers and the error word, all on the server's CUDA stream, closed by an
-// event) and posted later, once its event has completed, so that the next
-// round's host work and issue overlap this round's device work.  Rounds that
-// change the set of streams (creation, retirement, re-plan) wait until no
-// round is in flight.
-void complete_round(hmi_server *v);
-
-// Post every round in flight (waiting for the device).
-void drain_rounds(hmi_server *v)
-{
-    while (!v->flights.empty()) complete_round(v);
-}
-
-// Whether the next round has setup work (streams to create or retire, or a
-// plan to re-make).
-bool setup_pending(hmi_server *v)
-{
-    std::unique_lock<std::mutex> lk(v->mu);
-    if (v->dirty) return true;
-    for (auto &kv : v->streams) {
-        const SrvStream &ss = kv.second;
-        if (ss.pending || ss.failed || (ss.releasing && ss.q.empty())) return true;
-    }
-    return false;
-}
-
-// One dispatcher round; returns false when there was nothing to do.
-constexpr int kRoundLog = 16384;
-
-void log_round(hmi_server *v, const hmi_server_round &rec)   // under v->mu
-{
-    if (v->rounds.size() < (size_t)kRoundLog) v->rounds.push_back(rec);
-    else v->rounds[v->rounds_written % kRoundLog] = rec;
-    v->rounds_written += 1;
-}
-
-bool server_issue(hmi_server *v)
-{
-    NvtxRange range("hmi server round: issue");
-    if (!v->flights.empty() && setup_pending(v)) drain_rounds(v);
-    // Setup (creating, retiring streams, re-making the plan) is applied only
-    // with no round in flight: a round's kernels read the plan's tables and
-    // its streams' arenas until it is posted.  Only this thread issues rounds,
-    // so `idle` holds for the whole call; setup that an admission or release
-    // asks for meanwhile waits for the next idle round (the check above drains
-    // for it).
-    const bool idle = v->flights.empty();
-    std::vector<SrvTake> take;
-    std::vector<hmi_stream *> dead;
-    std::vector<int> replan_ids;
-    std::vector<hmi_stream *> replan_s;
-    hmi_server_round rec;
-    memset(&rec, 0, sizeof(rec));
-    rec.start_ns = now_ns();
-    std::vector<SrvStream *> creates;
-    {
-        std::unique_lock<std::mutex> lk(v->mu);
-        // retire released streams whose queues are empty, and streams whose
-        // creation failed (their frames come back with the error)
-        bool posted = false;
-        for (auto it = v->streams.begin(); it != v->streams.end();) {
-            SrvStream &ss = it->second;
-            if (ss.failed) {
-                for (const SrvFrame &f : ss.q) {
-                    hmi_server_result r;
-                    memset(&r, 0, sizeof(r));
-                    r.stream_id = it->first;
-                    r.status = HMI_ERR_NO_MEMORY;
-                    r.tag = f.tag;
-                    r.submit_ns = f.submit_ns;
-                    r.done_ns = now_ns();
-                    r.pointer = empty_pointer();
-                    v->done.push_back(r);
-                    if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
-                    posted = true;
-                }
-                ss.q.clear();
-            }
-            if (idle && (ss.releasing || ss.failed) && ss.q.empty() && !ss.pending) {
-                if (ss.s) dead.push_back(ss.s);
-                v->used -= ss.bytes;
-                it = v->streams.erase(it);
-                v->dirty = true;
-            } else {
-                if (ss.pending && idle) {
-                    creates.push_back(&ss);
-                    ss.pending = false;
-                }
-                ++it;
-            }
-        }
-        if (posted) v->done_cv.notify_all();
-    }
-    rec.created = (int32_t)creates.size();
-    rec.retired = (int32_t)dead.size();
-    if (!creates.empty()) {
-        // device state of newly admitted streams, in the order of this
-        // thread's CUDA stream (all later work on them runs on it too)
-        std::vector<hmi_stream *> made(creates.size());
-        for (size_t k = 0; k < creates.size(); ++k)
-            made[k] = create_stream_on(creates[k]->w, creates[k]->h, &creates[k]->p, v->cs);
-        std::unique_lock<std::mutex> lk(v->mu);
-        for (size_t k = 0; k < creates.size(); ++k) {
-            creates[k]->s = made[k];
-            creates[k]->failed = made[k] == nullptr;
-        }
-        v->dirty = true;
-    }
-    {
-        std::unique_lock<std::mutex> lk(v->mu);
-        if (v->dirty && idle) {
-            rec.replanned = 1;
-            replan_ids.clear();
-            for (auto &kv : v->streams) {
-                if (!kv.second.s) continue;
-                replan_ids.push_back(kv.first);
-                replan_s.push_back(kv.second.s);
-            }
-            v->dirty = false;
-        }
-    }
-    if (rec.replanned) {
-        // Re-made in place with the lock released (no tick is in flight
-        // between rounds, and only this thread erases streams), so that
-        // admissions and submissions are not held up by it.
-        v->plan_ids = replan_ids;
-        if (!replan_s.empty()) {
-            if (!v->plan)
-                v->plan = batch_new(replan_s.data(), (int)replan_s.size(), 1);
-            else if (batch_replan(v->plan, replan_s.data(), (int)replan_s.size(), 1) != HMI_OK) {
-                batch_free(v->plan);
-                v->plan = nullptr;
-            }
-        }
-    }
-    for (auto *d : dead) hmi_destroy_stream(d);   // no plan refers to them now
-    {
-        std::unique_lock<std::mutex> lk(v->mu);
-        take.resize(v->plan_ids.size());
-        bool any = false;
-        for (size_t i = 0; i < v->plan_ids.size(); ++i) {
-            auto it = v->streams.find(v->plan_ids[i]);
-            if (it == v->streams.end()) continue;   // cannot happen: only this thread erases
-            SrvStream &st = it->second;
-            take[i].ss = &st;   // map nodes stay put
-            if (!st.q.empty()) {
-                take[i].f = st.q.front();
-                st.q.pop_front();
-                any = true;
-            }
-        }
-        rec.setup_ns = now_ns();
-        if (!any) {
-            if (rec.replanned || rec.created || rec.retired) {
-                rec.issued_ns = rec.done_ns = rec.setup_ns;
-                rec.streams = (int32_t)v->plan_ids.size();
-                log_round(v, rec);
-            }
-            return rec.replanned != 0;
-        }
-    }
-    hmi_batch *b = v->plan;
-    const int n = b ? b->n : 0;
-    int status = b ? HMI_OK : HMI_ERR_NO_MEMORY;
-    if (status == HMI_OK && (v->ptr_cap < n || v->item_cap < n)) drain_rounds(v);   // buffers in use
-    // per-round buffers grow geometrically (streams join a few at a time, and
-    // every allocation may wait for the device)
-    const int cap = std::max(n, std::max(256, 2 * std::max(v->ptr_cap, v->item_cap)));
-    if (status == HMI_OK && v->ptr_cap < n) {
-        bool ok = true;
-        for (int k = 0; k < 2; ++k) {
-            cudaFreeHost(v->h_ptrs[k]);
-            cudaFree(v->d_ptrs[k]);
-            v->h_ptrs[k] = nullptr;
-            v->d_ptrs[k] = nullptr;
-            ok = ok && cudaMallocHost(&v->h_ptrs[k], sizeof(hmi_pointer) * cap) == cudaSuccess &&
-                 cudaMalloc(&v->d_ptrs[k], sizeof(hmi_pointer) * cap) == cudaSuccess;
-        }
-        v->ptr_cap = ok ? cap : 0;
-        if (!ok) status = HMI_ERR_NO_MEMORY;
-    }
-    const int buf = v->next_buf;
-    // All of the round's host-to-device copies go first, back to back on the
-    // copy engine: a learning frame densely into its stream's frame buffer, a
-    // frame to process at the buffer's pitch.  Then the learning kernels (the
-    // band is formed after a stream's last learning frame), then one tick over
-    // the plan, in which learning streams are inactive (null frame).
-    bool any_active = false;
-    for (int i = 0; i < n && status == HMI_OK; ++i) {
-        const SrvFrame &f = take[i].f;
-        if (!f.host) continue;
-        SrvStream *ss = take[i].ss;
-        hmi_stream *s = ss->s;
-        take[i].learning = ss->learn_done < ss->learn_n;
-        any_active = any_active || !take[i].learning;
-        take[i].src = nullptr;
-        // a pinned frame needs no copy: the luma pass reads a frame to process
-        // (16-pixel rows, 16-byte aligned), the batched learning kernel a
-        // learning frame (pixels a multiple of 4, 4-byte aligned)
-        const bool rows16 = (s->w % 16) == 0, quads = ((size_t)s->w * s->h) % 4 == 0;
-        if (take[i].learning ? quads : rows16) {
-            cudaPointerAttributes at;
-            if (cudaPointerGetAttributes(&at, f.host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
-                at.devicePointer != nullptr &&
-                (reinterpret_cast<uintptr_t>(at.devicePointer) & (take[i].learning ? 3u : 15u)) == 0) {
-                take[i].src = static_cast<const uint8_t *>(at.devicePointer);
-                continue;
-            }
-            (void)cudaGetLastError();
-        }
-        cudaError_t e;
-        if (take[i].learning || 3 * (size_t)s->w == (size_t)s->L.fpitch)
-            e = cudaMemcpyAsync(s->d_frame, f.host, f.bytes, cudaMemcpyHostToDevice, v->cs);
-        else
-            e = cudaMemcpy2DAsync(s->d_frame, s->L.fpitch, f.host, 3 * (size_t)s->w, 3 * (size_t)s->w, s->h,
-                                  cudaMemcpyHostToDevice, v->cs);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            status = HMI_ERR_DEVICE;
-        }
-    }
-    // learning frames: their sums in one launch for the whole round (a burst
-    // of new streams learns at once), except frames the batch cannot take
-    if (status == HMI_OK && v->item_cap < n) {
-        cudaFreeHost(v->h_items[0]);
-        cudaFreeHost(v->h_items[1]);
-        cudaFree(v->d_items);
-        v->h_items[0] = v->h_items[1] = nullptr;
-        v->d_items = nullptr;
-        v->item_cap = 0;
-        if (cudaMallocHost(&v->h_items[0], sizeof(LearnItem) * cap) == cudaSuccess &&
-            cudaMallocHost(&v->h_items[1], sizeof(LearnItem) * cap) == cudaSuccess &&
-            cudaMalloc(&v->d_items, sizeof(LearnItem) * cap) == cudaSuccess)
-            v->item_cap = cap;
-        else
-            status = HMI_ERR_NO_MEMORY;
-    }
-    int nitems = 0;
-    unsigned long long quads = 0;
-    for (int i = 0; i < n && status == HMI_OK; ++i) {
-        if (!take[i].f.host || !take[i].learning) continue;
-        SrvStream *ss = take[i].ss;
-        hmi_stream *s = ss->s;
-        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
-        const long long npx = (long long)s->w * s->h;
-        cudaError_t e = cudaSuccess;
-        if (ss->learn_done == 0)
-            e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
-        if (e == cudaSuccess && npx % 4 == 0 && (reinterpret_cast<uintptr_t>(fr) & 3u) == 0) {
-            v->h_items[buf][nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
-                                                  ss->learn_done == 0};
-            quads += (unsigned long long)(npx / 4);
-        } else if (e == cudaSuccess) {
-            e = launch_learn_accum(fr, 1, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, ss->learn_done == 0,
-                                   s->st, v->cs);
-        }
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            status = HMI_ERR_DEVICE;
-        }
-    }
-    if (status == HMI_OK && nitems > 0 &&
-        (cudaMemcpyAsync(v->d_items, v->h_items[buf], sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
-             cudaSuccess ||
-         launch_learn_batch(v->d_items, nitems, quads, v->cs) != cudaSuccess)) {
-        (void)cudaGetLastError();
-        status = HMI_ERR_DEVICE;
-    }
-    for (int i = 0; i < n && status == HMI_OK; ++i) {
-        if (!take[i].f.host || !take[i].learning) continue;
-        SrvStream *ss = take[i].ss;
-        hmi_stream *s = ss->s;
-        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
-        cudaError_t e = cudaSuccess;
-        if (s->L.mix_k) {   // the mixture learns the same frame
-            if (ss->learn_done == 0) e = enqueue_mix_reset(s, v->cs);
-            if (e == cudaSuccess)
-                e = launch_mix_learn(fr, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
-        }
-        if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            status = HMI_ERR_DEVICE;
-            break;
-        }
-        if (++ss->learn_done == ss->learn_n) {
-            s->learned = 1;
-            s->n_learn = ss->learn_n;
-        }
-        rec.learning += 1;
-    }
-    if (status == HMI_OK && any_active) {
-        const int slot = acquire_slot(b);
-        TickIO *io = b->h_io + (size_t)slot * n;
-        for (int i = 0; i < n; ++i) {
-            hmi_stream *s = b->s[i];
-            TickIO &t = io[b->pos[i]];
-            t.mask = nullptr;
-            t.ptr_out = v->d_ptrs[buf] + i;
-            t.src = nullptr;
-            if (take[i].f.host && !take[i].learning) {
-                s->used = true;
-                t.frame = s->d_frame;
-                t.frame_pitch = s->L.fpitch;
-                if (take[i].src) {
-                    t.src = take[i].src;
-                    t.frame = s->arena + s->L.frame_ph[slot % kPhases];
-                }
-            } else {
-                t.frame = nullptr;
-                t.frame_pitch = 0;
-            }
-        }
-        status = run_tick(b, slot, v->cs, false);
-        if (status == HMI_OK &&
-            (cudaMemcpyAsync(v->h_ptrs[buf], v->d_ptrs[buf], sizeof(hmi_pointer) * n, cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
-             cudaMemcpyAsync(v->h_err[buf], b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, v->cs) != cudaSuccess ||
-             cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), v->cs) != cudaSuccess)) {
-            (void)cudaGetLastError();
-            status = HMI_ERR_DEVICE;
-        }
-    }
-    // whatever was enqueued has finished with the round's host frames (read
-    // by copies or by the luma pass) when the event has completed; they are
-    // given back when the round is posted
-    if (cudaEventRecord(v->ev[buf], v->cs) != cudaSuccess) {
-        (void)cudaGetLastError();
-        status = HMI_ERR_DEVICE;
-    }
-    rec.issued_ns = now_ns();
-    rec.streams = n;
-    hmi_server::Flight F;
-    F.take = std::move(take);
-    F.ids = v->plan_ids;
-    F.rec = rec;
-    F.any_active = any_active;
-    F.status = status;
-    F.buf = buf;
-    v->flights.push_back(std::move(F));
-    v->next_buf ^= 1;
-    return true;
-}
-
-// Post the oldest round in flight: wait for its device work, then hand its
-// results (and its pooled host frames) back.
-void complete_round(hmi_server *v)
-{
-    NvtxRange range("hmi server round: post");
-    hmi_server::Flight F = std::move(v->flights.front());
-    v->flights.pop_front();
-    int status = F.status;
-    if (cudaEventSynchronize(v->ev[F.buf]) != cudaSuccess) {
-        (void)cudaGetLastError();
-        status = HMI_ERR_DEVICE;
-    }
-    if (status == HMI_OK && F.any_active && *v->h_err[F.buf])
-        status = (*v->h_err[F.buf] & kErrBounds) ? HMI_ERR_DEVICE : HMI_ERR_DEVICE_TIMEOUT;
-    *v->h_err[F.buf] = 0;
-    const uint64_t t_done = now_ns();
-    hmi_server_round &rec = F.rec;
-    rec.done_ns = t_done;
-    std::unique_lock<std::mutex> lk(v->mu);
-    v->ticks += 1;
-    for (int i = 0; i < (int)F.take.size(); ++i) {
-        const SrvFrame &f = F.take[i].f;
-        if (!f.host) continue;
-        hmi_server_result r;
-        memset(&r, 0, sizeof(r));
-        r.stream_id = F.ids[i];
-        r.status = status;
-        r.tag = f.tag;
-        r.submit_ns = f.submit_ns;
-        r.done_ns = t_done;
-        if (status == HMI_OK && F.take[i].learning) {
-            r.status = HMI_LEARNING;
-            r.pointer = empty_pointer();
-        } else if (status == HMI_OK) {
-            r.pointer = v->h_ptrs[F.buf][i];
-        }
-        v->done.push_back(r);
-        if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
-        v->frames += 1;
-        if (!F.take[i].learning) rec.frames += 1;
-    }
-    log_round(v, rec);
-    lk.unlock();
-    v->done_cv.notify_all();
-}
-
-
-void server_loop(hmi_server *v)
-{
-    cudaSetDevice(v->dev);
-    for (;;) {
-        {
-            std::unique_lock<std::mutex> lk(v->mu);
-            if (v->stop) break;
-        }
-        // post the rounds whose device work has finished
-        while (!v->flights.empty() && cudaEventQuery(v->ev[v->flights.front().buf]) == cudaSuccess)
-            complete_round(v);
-        (void)cudaGetLastError();   // a query of unfinished work reports cudaErrorNotReady
-        const bool issued = v->flights.size() < 2 && server_issue(v);
-        if (issued) continue;
-        if (!v->flights.empty()) {
-            complete_round(v);   // nothing new to issue: wait for the device
-            continue;
-        }
-        std::unique_lock<std::mutex> lk(v->mu);
-        if (v->stop) break;
-        v->work_cv.wait_for(lk, std::chrono::microseconds(500));
-    }
-    drain_rounds(v);
-}
-
-}  // namespace
-
-extern "C" {
-
-uint64_t hmi_server_now_ns(void) { return now_ns(); }
-
-hmi_server *hmi_server_create(size_t device_budget_bytes, int max_queue)
-{
-    if (max_queue < 1 || max_queue > 64) {
-        fail(HMI_ERR_INVALID_ARG);
-        return nullptr;
-    }
-    hmi_server *v = new (std::nothrow) hmi_server();
-    if (!v) {
-        fail(HMI_ERR_NO_MEMORY);
-        return nullptr;
-    }
-    v->budget = device_budget_bytes;
-    v->max_queue = max_queue;
-    bool ok = cudaGetDevice(&v->dev) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&v->cs, cudaStreamNonBlocking) == cudaSuccess;
-    for (int k = 0; ok && k < 2; ++k)
-        ok = cudaEventCreateWithFlags(&v->ev[k], cudaEventDisableTiming) == cudaSuccess &&
-             cudaMallocHost(&v->h_err[k], sizeof(uint32_t)) == cudaSuccess;
-    if (!ok) {
-        (void)cudaGetLastError();
-        for (int k = 0; k < 2; ++k) {
-            if (v->ev[k]) cudaEventDestroy(v->ev[k]);
-            if (v->h_err[k]) cudaFreeHost(v->h_err[k]);
-        }
-        if (v->cs) cudaStreamDestroy(v->cs);
-        delete v;
-        fail(HMI_ERR_DEVICE);
-        return nullptr;
-    }
-    *v->h_err[0] = *v->h_err[1] = 0;
-    // Map the stream-arena pool up to the budget (at most a quarter of the free
-    // device memory) now, so that admitting a burst of streams later only
-    // sub-allocates; the pool keeps freed memory while any stream lives.
-    size_t free_b = 0, total_b = 0;
-    cudaMemPool_t pool = arena_pool(v->dev);
-    if (pool && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
-        const size_t want = std::min(device_budget_bytes, free_b / 4);
-        void *p = nullptr;
-        if (want > 0 && cudaMallocFromPoolAsync(&p, want, pool, v->cs) == cudaSuccess) {
-            cudaFreeAsync(p, v->cs);
-            cudaStreamSynchronize(v->cs);
-        }
-    }
-    (void)cudaGetLastError();
-    v->worker = std::thread(server_loop, v);
-    return v;
-}
-
-void hmi_server_destroy(hmi_server *v)
-{
-    if (!v) return;
-    {
-        std::lock_guard<std::mutex> lk(v->mu);
-        v->stop = true;
-    }
-    v->work_cv.notify_all();
-    if (v->worker.joinable()) v->worker.join();
-    cudaSetDevice(v->dev);
-    batch_free(v->plan);
-    for (auto &kv : v->streams) {
-        for (auto &f : kv.second.q)
-            if (f.owned) cudaFreeHost(const_cast<uint8_t *>(f.host));
-        hmi_destroy_stream(kv.second.s);
-    }
-    for (auto &kv : v->pool)
-        for (auto *p : kv.second) cudaFreeHost(p);
-    for (int k = 0; k < 2; ++k) {
-        cudaFreeHost(v->h_ptrs[k]);
-        cudaFree(v->d_ptrs[k]);
-        cudaFreeHost(v->h_items[k]);
-        cudaFreeHost(v->h_err[k]);
-        if (v->ev[k]) cudaEventDestroy(v->ev[k]);
-    }
-    cudaFree(v->d_items);
-    if (v->cs) cudaStreamDestroy(v->cs);
-    delete v;
-}
-
-int hmi_server_admit(hmi_server *v, int w, int h, const hmi_params *p, const uint8_t *learn_frames,
-                     int n, int *stream_id)
-{
-    if (!v || !stream_id || n < 1 || n > 65535) return fail(HMI_ERR_INVALID_ARG);
-    const size_t bytes = hmi_stream_device_bytes(w, h, p);
-    if (bytes == 0) return fail(HMI_ERR_INVALID_ARG);
-    {
-        std::lock_guard<std::mutex> lk(v->mu);
-        if (v->used + bytes > v->budget) return fail(HMI_ERR_NO_MEMORY);
-        v->used += bytes;   // reserved while the stream is set up
-    }
-    if (!learn_frames) {
-        // online learning: a reservation only; the dispatcher creates the
-        // stream at its next round, and frames may be queued meanwhile
-        std::lock_guard<std::mutex> lk(v->mu);
-        const int id = v->next_id++;
-        SrvStream &ss = v->streams[id];
-        ss.w = w;
-        ss.h = h;
-        if (p) ss.p = *p;
-        else hmi_default_params(&ss.p);
-        ss.bytes = bytes;
-        ss.pending = true;
-        ss.learn_n = n;
-        *stream_id = id;
-        v->work_cv.notify_all();
-        return HMI_OK;
-    }
-    HMI_CUDA(cudaSetDevice(v->dev));
-    hmi_stream *s = hmi_create_stream(w, h, p);
-    int st = s ? HMI_OK : g_last_error;
-    if (s) st = learn_background(s, learn_frames, n);
-    if (st != HMI_OK) {
-        if (s) hmi_destroy_stream(s);
-        std::lock_guard<std::mutex> lk(v->mu);
-        v->used -= bytes;
-        return fail(st);
-    }
-    std::lock_guard<std::mutex> lk(v->mu);
-    const int id = v->next_id++;
-    SrvStream &ss = v->streams[id];
-    ss.s = s;
-    ss.w = w;
-    ss.h = h;
-    ss.p = s->p;
-    ss.bytes = bytes;
-    v->dirty = true;
-    *stream_id = id;
-    return HMI_OK;
-}
-
-int hmi_server_release(hmi_server *v, int stream_id)
-{
-    if (!v) return fail(HMI_ERR_INVALID_ARG);
-    std::lock_guard<std::mutex> lk(v->mu);
-    auto it = v->streams.find(stream_id);
-    if (it == v->streams.end() || it->second.releasing) return fail(HMI_ERR_INVALID_ARG);
-    it->second.releasing = true;
-    v->work_cv.notify_all();
-    return HMI_OK;
-}
-
-static int server_enqueue(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag, bool copy)
-{
-    if (!v || !frame) return fail(HMI_ERR_INVALID_ARG);
-    size_t bytes;
-    {
-        std::lock_guard<std::mutex> lk(v->mu);
-        auto it = v->streams.find(stream_id);
-        if (it == v->streams.end() || it->second.releasing) return fail(HMI_ERR_INVALID_ARG);
-        if ((int)it->second.q.size() >= v->max_queue) return fail(HMI_ERR_NO_MEMORY);
-        bytes = 3 * (size_t)it->second.w * it->second.h;
-    }
-    SrvFrame f;
-    f.bytes = bytes;
-    f.tag = tag;
-    f.submit_ns = now_ns();
-    f.owned = copy;
-    if (copy) {
-        uint8_t *buf;
-        {
-            std::lock_guard<std::mutex> lk(v->mu);
-            buf = pool_get(v, bytes);
-        }
-        if (!buf) return fail(HMI_ERR_NO_MEMORY);
-        memcpy(buf, frame, bytes);
-        f.host = buf;
-    } else {
-        f.host = frame;
-    }
-    {
-        std::lock_guard<std::mutex> lk(v->mu);
-        auto it = v->streams.find(stream_id);
-        if (it == v->streams.end() || it->second.releasing) {
-            if (copy) v->pool[bytes].push_back(const_cast<uint8_t *>(f.host));
-            return fail(HMI_ERR_INVALID_ARG);
-        }
-        it->second.q.push_back(f);
-    }
-    v->work_cv.notify_all();
-    return HMI_OK;
-}
-
-int hmi_server_submit(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag)
-{
-    return server_enqueue(v, stream_id, frame, tag, true);
-}
-
-int hmi_server_submit_ref(hmi_server *v, int stream_id, const uint8_t *frame, uint64_t tag)
-{
-    return server_enqueue(v, stream_id, frame, tag, false);
-}
-
-int hmi_server_poll(hmi_server *v, hmi_server_result *out, int max_results, int wait_us)
-{
-    if (!v || !out || max_results < 1) return fail(HMI_ERR_INVALID_ARG);
-    std::unique_lock<std::mutex> lk(v->mu);
-    if (v->done.empty() && wait_us > 0)
-        v->done_cv.wait_for(lk, std::chrono::microseconds(wait_us), [&] { return !v->done.empty(); });
-    int k = 0;
-    while (k < max_results && !v->done.empty()) {
-        out[k++] = v->done.front();
-        v->done.pop_front();
-    }
-    return k;
-}
-
-int hmi_server_rounds(hmi_server *v, hmi_server_round *out, int max_rounds)
-{
-    if (!v || !out || max_rounds < 1) return fail(HMI_ERR_INVALID_ARG);
-    std::lock_guard<std::mutex> lk(v->mu);
-    const uint64_t have = std::min<uint64_t>(v->rounds_written, v->rounds.size());
-    const uint64_t k = std::min<uint64_t>(have, (uint64_t)max_rounds);
-    for (uint64_t i = 0; i < k; ++i) {
-        const uint64_t r = v->rounds_written - k + i;   // oldest of the last k first
-        out[i] = v->rounds[r % kRoundLog];
-    }
-    return (int)k;
-}
-
-int hmi_server_stats(hmi_server *v, size_t *bytes_admitted, uint64_t *ticks, uint64_t *frames)
-{
-    if (!v) return fail(HMI_ERR_INVALID_ARG);
-    std::lock_guard<std::mutex> lk(v->mu);
-    if (bytes_admitted) *bytes_admitted = v->used;
-    if (ticks) *ticks = v->ticks;
-    if (frames) *frames = v->frames;
-    return HMI_OK;
-}
-
-}  // extern "C"
 
 // ===========================================================================
 // C ABI
