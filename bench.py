@@ -233,17 +233,49 @@ class OraclePool:
             p.join(timeout=10)
 
 
+def copy_same_bytes_us(nbytes: int, reps: int = 10) -> float:
+    """Median time of a plain device-to-device copy that moves nbytes in all
+    (nbytes / 2 read, nbytes / 2 written), L2 flushed before each: what HBM
+    gives one kernel of that traffic on this GPU, launch ramp and tail
+    included.  The measured peak comes from a multi-GiB copy; kernels of a
+    few hundred MB reach a smaller share of it."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    half = max(nbytes // 2, 1 << 20)
+    src = torch.empty(half, dtype=torch.uint8, device=dev).fill_(1)
+    dst = torch.empty_like(src)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ts = []
+    for _ in range(reps):
+        flush.fill_(0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dst.copy_(src)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e3)
+    del src, dst, flush
+    ts.sort()
+    return ts[len(ts) // 2]
+
+
 def k2_roofline(per_kernel: dict, ticks: int, px: int, fused: bool, peak: float, peak_kind: str) -> dict:
     """The per-pixel stage against HBM: K2_BYTES_PER_PX x px over the summed
     CUDA-event times of its kernels (the persistent tick's one launch when
-    fused), from a single-chain pass where each kernel is timed alone."""
+    fused), from a single-chain pass where each kernel is timed alone.  Beside
+    it, a plain copy of the same traffic timed the same way (one launch)."""
     names = ("luma",) if fused else K2_KERNELS
     ms = sum(per_kernel[k] for k in names) / max(ticks, 1)
-    achieved = K2_BYTES_PER_PX * px / (ms / 1e3) / 1e9
+    nbytes = K2_BYTES_PER_PX * px
+    achieved = nbytes / (ms / 1e3) / 1e9
+    copy_us = copy_same_bytes_us(nbytes)
     return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_morph_strip"],
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-            "frac": achieved / peak, "algorithmic_bytes_per_tick": K2_BYTES_PER_PX * px,
-            "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks}
+            "frac": achieved / peak, "algorithmic_bytes_per_tick": nbytes,
+            "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks,
+            "copy_same_bytes": {"us": copy_us, "GBs": nbytes / copy_us / 1e3,
+                                "frac_of_peak": nbytes / copy_us / 1e3 / peak,
+                                "stage_over_copy": ms * 1e3 / copy_us}}
 
 
 def max_over_ranks(x: float, dev) -> float:
