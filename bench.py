@@ -269,13 +269,19 @@ def k2_roofline(per_kernel: dict, ticks: int, px: int, fused: bool, peak: float,
     nbytes = K2_BYTES_PER_PX * px
     achieved = nbytes / (ms / 1e3) / 1e9
     copy_us = copy_same_bytes_us(nbytes)
+    # the same for each kernel's own traffic: frame (3 B/px); frame, band and
+    # raw bits (9.125 B/px); raw bits in, bits and mask bytes out (1.25 B/px)
+    per_copy = {} if fused else {k: copy_same_bytes_us(int(bpp * px))
+                                 for k, bpp in (("luma", 3.0), ("classify", 9.125), ("morphology", 1.25))}
     return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_morph_strip"],
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak, "algorithmic_bytes_per_tick": nbytes,
             "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks,
             "copy_same_bytes": {"us": copy_us, "GBs": nbytes / copy_us / 1e3,
                                 "frac_of_peak": nbytes / copy_us / 1e3 / peak,
-                                "stage_over_copy": ms * 1e3 / copy_us}}
+                                "stage_over_copy": ms * 1e3 / copy_us},
+            "copy_per_kernel_traffic_us": per_copy,
+            "stage_over_per_kernel_copies": (ms * 1e3 / sum(per_copy.values())) if per_copy else None}
 
 
 def max_over_ranks(x: float, dev) -> float:
