@@ -44,7 +44,14 @@ struct SrvTake {
     SrvStream *ss = nullptr;
     bool learning = false;
     const uint8_t *src = nullptr;   // a pinned frame the luma pass reads itself
+    std::vector<SrvFrame> more;     // further queued learning frames of a learning stream
 };
+
+// Learning frames a learning stream may give one round: its queue drains this
+// many times faster while it learns (a round processes at most one frame of a
+// stream that already runs), so a burst of streams joining at once does not
+// leave them behind their arrivals.
+constexpr int kLearnPerRound = 4;
 
 hmi_pointer empty_pointer()
 {
@@ -272,6 +279,13 @@ bool server_issue(hmi_server *v)
                 take[i].f = st.q.front();
                 st.q.pop_front();
                 any = true;
+                // a learning stream's later learning frames join the round too
+                // (learn_done is this thread's own state)
+                int more = st.s ? std::min(kLearnPerRound - 1, st.learn_n - st.learn_done - 1) : 0;
+                for (; more > 0 && !st.q.empty(); --more) {
+                    take[i].more.push_back(st.q.front());
+                    st.q.pop_front();
+                }
             }
         }
         rec.setup_ns = now_ns();
@@ -353,66 +367,101 @@ bool server_issue(hmi_server *v)
         v->h_items[0] = v->h_items[1] = nullptr;
         v->d_items = nullptr;
         v->item_cap = 0;
-        if (cudaMallocHost(&v->h_items[0], sizeof(LearnItem) * cap) == cudaSuccess &&
-            cudaMallocHost(&v->h_items[1], sizeof(LearnItem) * cap) == cudaSuccess &&
-            cudaMalloc(&v->d_items, sizeof(LearnItem) * cap) == cudaSuccess)
+        const size_t per = sizeof(LearnItem) * (size_t)cap * kLearnPerRound;   // a table per layer
+        if (cudaMallocHost(&v->h_items[0], per) == cudaSuccess && cudaMallocHost(&v->h_items[1], per) == cudaSuccess &&
+            cudaMalloc(&v->d_items, per) == cudaSuccess)
             v->item_cap = cap;
         else
             status = HMI_ERR_NO_MEMORY;
     }
-    int nitems = 0;
-    unsigned long long quads = 0;
-    for (int i = 0; i < n && status == HMI_OK; ++i) {
-        if (!take[i].f.host || !take[i].learning) continue;
-        SrvStream *ss = take[i].ss;
-        hmi_stream *s = ss->s;
-        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
-        const long long npx = (long long)s->w * s->h;
-        cudaError_t e = cudaSuccess;
-        if (ss->learn_done == 0)
-            e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
-        if (e == cudaSuccess && npx % 4 == 0 && (reinterpret_cast<uintptr_t>(fr) & 3u) == 0) {
-            v->h_items[buf][nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
-                                                  ss->learn_done == 0};
-            quads += (unsigned long long)(npx / 4);
-        } else if (e == cudaSuccess) {
-            e = launch_learn_accum(fr, 1, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, ss->learn_done == 0,
-                                   s->st, v->cs);
+    // Learning frames in layers: layer 0 holds each learning stream's frame of
+    // this round, layer k its k-th further learning frame; one batched launch
+    // per layer, so that a stream's frames add to its sums one after the
+    // other.  A layer's table has its own host and device region (the copies
+    // of earlier layers may not have run yet).
+    for (int layer = 0; layer < kLearnPerRound && status == HMI_OK; ++layer) {
+        LearnItem *items = v->h_items[buf] + (size_t)layer * v->item_cap;
+        LearnItem *d_items = v->d_items + (size_t)layer * v->item_cap;
+        int nitems = 0, in_layer = 0;
+        unsigned long long quads = 0;
+        for (int i = 0; i < n && status == HMI_OK; ++i) {
+            if (!take[i].f.host || !take[i].learning || (int)take[i].more.size() < layer) continue;
+            SrvStream *ss = take[i].ss;
+            hmi_stream *s = ss->s;
+            const long long npx = (long long)s->w * s->h;
+            const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
+            cudaError_t e = cudaSuccess;
+            if (layer > 0) {   // a pinned frame is read in place, others go to the frame buffer
+                const SrvFrame &m = take[i].more[layer - 1];
+                cudaPointerAttributes at;
+                fr = nullptr;
+                if (npx % 4 == 0 && cudaPointerGetAttributes(&at, m.host) == cudaSuccess &&
+                    at.type == cudaMemoryTypeHost && at.devicePointer != nullptr &&
+                    (reinterpret_cast<uintptr_t>(at.devicePointer) & 3u) == 0)
+                    fr = static_cast<const uint8_t *>(at.devicePointer);
+                (void)cudaGetLastError();
+                if (!fr) {
+                    fr = s->d_frame;   // free again: the layers before have been enqueued
+                    e = cudaMemcpyAsync(s->d_frame, m.host, m.bytes, cudaMemcpyHostToDevice, v->cs);
+                }
+            }
+            if (e == cudaSuccess && layer == 0 && ss->learn_done == 0)
+                e = cudaMemsetAsync(&s->st->learn_luma, 0, sizeof(unsigned long long), v->cs);
+            if (e == cudaSuccess && npx % 4 == 0 && (reinterpret_cast<uintptr_t>(fr) & 3u) == 0) {
+                items[nitems++] = LearnItem{fr, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, s->st, quads,
+                                            ss->learn_done == 0};
+                quads += (unsigned long long)(npx / 4);
+            } else if (e == cudaSuccess) {
+                e = launch_learn_accum(fr, 1, npx, s->d_S, s->d_Q, s->d_vmin, s->d_vmax, ss->learn_done == 0,
+                                       s->st, v->cs);
+            }
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                status = HMI_ERR_DEVICE;
+            }
+            ++in_layer;
         }
-        if (e != cudaSuccess) {
+        if (in_layer == 0) break;
+        if (status == HMI_OK && nitems > 0 &&
+            (cudaMemcpyAsync(d_items, items, sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
+                 cudaSuccess ||
+             launch_learn_batch(d_items, nitems, quads, v->cs) != cudaSuccess)) {
             (void)cudaGetLastError();
             status = HMI_ERR_DEVICE;
         }
-    }
-    if (status == HMI_OK && nitems > 0 &&
-        (cudaMemcpyAsync(v->d_items, v->h_items[buf], sizeof(LearnItem) * nitems, cudaMemcpyHostToDevice, v->cs) !=
-             cudaSuccess ||
-         launch_learn_batch(v->d_items, nitems, quads, v->cs) != cudaSuccess)) {
-        (void)cudaGetLastError();
-        status = HMI_ERR_DEVICE;
-    }
-    for (int i = 0; i < n && status == HMI_OK; ++i) {
-        if (!take[i].f.host || !take[i].learning) continue;
-        SrvStream *ss = take[i].ss;
-        hmi_stream *s = ss->s;
-        const uint8_t *fr = take[i].src ? take[i].src : s->d_frame;
-        cudaError_t e = cudaSuccess;
-        if (s->L.mix_k) {   // the mixture learns the same frame
-            if (ss->learn_done == 0) e = enqueue_mix_reset(s, v->cs);
-            if (e == cudaSuccess)
-                e = launch_mix_learn(fr, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
+        for (int i = 0; i < n && status == HMI_OK; ++i) {
+            if (!take[i].f.host || !take[i].learning || (int)take[i].more.size() < layer) continue;
+            SrvStream *ss = take[i].ss;
+            hmi_stream *s = ss->s;
+            cudaError_t e = cudaSuccess;
+            if (s->L.mix_k) {   // the mixture learns the same frame
+                const uint8_t *fr = layer == 0 ? (take[i].src ? take[i].src : s->d_frame) : nullptr;
+                if (layer > 0) {
+                    cudaPointerAttributes at;
+                    const SrvFrame &m = take[i].more[layer - 1];
+                    if (cudaPointerGetAttributes(&at, m.host) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+                        at.devicePointer != nullptr &&
+                        (reinterpret_cast<uintptr_t>(at.devicePointer) & 3u) == 0 && ((long long)s->w * s->h) % 4 == 0)
+                        fr = static_cast<const uint8_t *>(at.devicePointer);
+                    (void)cudaGetLastError();
+                    if (!fr) fr = s->d_frame;   // copied there above
+                }
+                if (ss->learn_done == 0) e = enqueue_mix_reset(s, v->cs);
+                if (e == cudaSuccess)
+                    e = launch_mix_learn(fr, 1, (uint32_t)ss->learn_done, s->w, s->h, s->ds.mix, v->cs);
+            }
+            if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                status = HMI_ERR_DEVICE;
+                break;
+            }
+            if (++ss->learn_done == ss->learn_n) {
+                s->learned = 1;
+                s->n_learn = ss->learn_n;
+            }
+            rec.learning += 1;
         }
-        if (e == cudaSuccess && ss->learn_done + 1 == ss->learn_n) e = enqueue_band(s, ss->learn_n, v->cs);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            status = HMI_ERR_DEVICE;
-            break;
-        }
-        if (++ss->learn_done == ss->learn_n) {
-            s->learned = 1;
-            s->n_learn = ss->learn_n;
-        }
-        rec.learning += 1;
     }
     if (status == HMI_OK && any_active) {
         const int slot = acquire_slot(b);
@@ -506,6 +555,13 @@ void complete_round(hmi_server *v)
         if (f.owned) v->pool[f.bytes].push_back(const_cast<uint8_t *>(f.host));
         v->frames += 1;
         if (!F.take[i].learning) rec.frames += 1;
+        for (const SrvFrame &m : F.take[i].more) {   // the stream's further learning frames
+            r.tag = m.tag;
+            r.submit_ns = m.submit_ns;
+            v->done.push_back(r);
+            if (m.owned) v->pool[m.bytes].push_back(const_cast<uint8_t *>(m.host));
+            v->frames += 1;
+        }
     }
     log_round(v, rec);
     lk.unlock();

@@ -207,18 +207,19 @@ def _submit_all(srv, ids, seq, pinned=False):
     """Submit seq[s][k] for every stream, interleaved k by k; returns the tag
     map and the buffers that must outlive the results."""
     tag_of, tag, keep = {}, 0, []
-    for k in range(max(len(v) for v in seq.values())):
-        for s, frs in seq.items():
-            if k >= len(frs):
-                continue
-            tag += 1
-            tag_of[tag] = (s, k)
-            if pinned:
-                buf = torch.from_numpy(np.ascontiguousarray(frs[k])).pin_memory()
-                keep.append(buf)
-                assert hmi.hmi_server_submit_ref(srv, ids[s], buf.numpy(), tag) == hmi.HMI_OK
-            else:
-                assert hmi.hmi_server_submit(srv, ids[s], np.ascontiguousarray(frs[k]), tag) == hmi.HMI_OK
+    order = [(s, k) for k in range(max(len(v) for v in seq.values())) for s, frs in seq.items() if k < len(frs)]
+    # pinned buffers are made before the first submission, so that frames
+    # arrive faster than rounds finish and rounds queue up behind each other
+    bufs = {sk: torch.from_numpy(np.ascontiguousarray(seq[sk[0]][sk[1]])).pin_memory() for sk in order} \
+        if pinned else {}
+    keep.extend(bufs.values())
+    for s, k in order:
+        tag += 1
+        tag_of[tag] = (s, k)
+        if pinned:
+            assert hmi.hmi_server_submit_ref(srv, ids[s], bufs[(s, k)].numpy(), tag) == hmi.HMI_OK
+        else:
+            assert hmi.hmi_server_submit(srv, ids[s], np.ascontiguousarray(seq[s][k]), tag) == hmi.HMI_OK
     return tag_of, keep
 
 
