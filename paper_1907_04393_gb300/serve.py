@@ -446,13 +446,15 @@ def sweep(bank: FrameBank, rates, duration: float, n_learn: int = N_LEARN, seed:
     """Served and plain forms over the same traces at each arrival-rate scale
     (a device budget no trace reaches, so that only the serving form
     differs)."""
+    # every rate's served run first, then the plain forms (they saturate from
+    # the second rate on and leave host and device busy for a while after)
+    traces = {r: make_trace(duration, rate_scale=r, seed=seed + int(r * 1000)) for r in rates}
+    served = {r: run_served(traces[r], bank, budget_bytes, n_learn) for r in rates}
     rows = []
     for r in rates:
-        tr = make_trace(duration, rate_scale=r, seed=seed + int(r * 1000))
-        srv = run_served(tr, bank, budget_bytes, n_learn)
-        pln = run_plain(tr, bank, n_learn)
-        pla = run_plain_async(tr, bank, n_learn)
-        rows.append({"rate_scale": r, "served": srv, "plain": pln, "plain_async": pla})
+        pln = run_plain(traces[r], bank, n_learn)
+        pla = run_plain_async(traces[r], bank, n_learn)
+        rows.append({"rate_scale": r, "served": served[r], "plain": pln, "plain_async": pla})
     best = {}
     for arm in ("served", "plain", "plain_async"):
         ok = [row[arm]["frames_per_s"] for row in rows if meets_slo(row[arm])]
