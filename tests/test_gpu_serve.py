@@ -149,6 +149,52 @@ def test_online_learning_equals_learned_up_front(over):
     hmi.hmi_server_destroy(srv)
 
 
+@pytest.mark.parametrize("over", [{}, dict(bg_model=1, mix_k=3)])
+def test_queued_learning_frames_taken_several_per_round(over):
+    """Every frame of two streams is queued before the dispatcher has created
+    them, so that each round takes several learning frames of a stream at once
+    (summed in layers, one batched launch each; the mixture frame by frame in
+    order): the round log shows such a round, and the results equal those of
+    streams learned from the same frames up front.  One stream's frames are
+    pinned (read in place), the other's copied."""
+    srcs = [20, 190]
+    n_learn, nframes = 11, 4
+    learn = {s: synth.learn_frames(5, s, n_learn) for s in srcs}
+    frames = {s: [synth.run_frame(5, s, t) for t in range(nframes)] for s in srcs}
+    alone = {}
+    for s in srcs:
+        st = hmi.Stream(*synth.shape(5, s), **over)
+        st.learn(learn[s])
+        alone[s] = [st.process(f, mask=False)[1] for f in frames[s]]
+        st.close()
+    seq = {s: list(learn[s]) + frames[s] for s in srcs}
+    pinned = {(s, k): torch.from_numpy(np.ascontiguousarray(seq[s][k])).pin_memory()
+              for s in srcs[:1] for k in range(len(seq[s]))}
+    srv = hmi.hmi_server_create(1 << 34, 64)
+    prm = hmi.hmi_default_params(**over)
+    ids = {s: hmi.hmi_server_admit(srv, *synth.shape(5, s), prm, None, n_learn) for s in srcs}
+    tag_of, tag = {}, 0
+    for s in srcs:
+        for k in range(len(seq[s])):
+            tag += 1
+            tag_of[tag] = (s, k)
+            if (s, k) in pinned:
+                assert hmi.hmi_server_submit_ref(srv, ids[s], pinned[(s, k)].numpy(), tag) == hmi.HMI_OK
+            else:
+                assert hmi.hmi_server_submit(srv, ids[s], np.ascontiguousarray(seq[s][k]), tag) == hmi.HMI_OK
+    got = _collect(srv, tag_of)
+    rec = hmi.hmi_server_rounds(srv)
+    hmi.hmi_server_destroy(srv)
+    assert int(rec["learning"].max()) > len(srcs), "no round took several learning frames of a stream"
+    for s in srcs:
+        for k in range(n_learn):
+            assert got[(s, k)][0] == hmi.HMI_LEARNING, (s, k)
+        for t in range(nframes):
+            st, p = got[(s, n_learn + t)]
+            assert st == hmi.HMI_OK and p == alone[s][t], (s, t)
+    del pinned
+
+
 def test_online_learning_odd_sizes():
     """Streams whose pixel count is not a multiple of 4 (learning frames summed
     one launch per frame, not in the round's batch) or whose width is not a
