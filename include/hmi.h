@@ -420,9 +420,12 @@ HMI_API size_t hmi_stream_device_bytes(int w, int h, const hmi_params *p);
  * streams stays within a budget, keeps every admitted stream's state resident,
  * and runs a dispatcher thread that continuously batches: whenever frames are
  * pending it runs one tick over all admitted streams, taking at most one
- * frame (the oldest) per stream, so each stream's frames stay in order.
- * Results carry the submit and completion times (hmi_server_now_ns clock).
- * All calls are thread-safe.
+ * frame (the oldest) per stream to process, so each stream's frames stay in
+ * order; a stream still learning online gives up to four queued learning
+ * frames to a round, added to its sums in arrival order.  A round is issued
+ * while the previous one is still on the device, and its results are posted
+ * once its device work has finished.  Results carry the submit and completion
+ * times (hmi_server_now_ns clock).  All calls are thread-safe.
  * ------------------------------------------------------------------------- */
 typedef struct hmi_server hmi_server;
 
