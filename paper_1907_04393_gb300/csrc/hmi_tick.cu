@@ -34,11 +34,7 @@
 
 namespace hmi {
 
-// CTAs of four warps: an item's CTA barriers span few warps, and more CTAs per
-// SM keep working while one waits for its stream.
-constexpr int kTickThreads = 128;
-constexpr int kTickWarps = kTickThreads / 32;
-constexpr int kTickCtasPerSm = 6;   // at most 80 registers a thread
+constexpr int kTickWarps = kThreads / 32;
 constexpr uint32_t kErrWait = 16u;
 
 struct TickSmem {
@@ -123,12 +119,12 @@ __device__ __forceinline__ void item_luma(const BatchDev &b, int s, int c0, int 
     const int w = D.w, cpr = 2 * D.nwords;
     const uint32_t magic = D.cpr_magic;
     unsigned long long acc = 0;
-    for (int u = c0 + tid; u < c1; u += kLumaPerThread * kTickThreads) {
+    for (int u = c0 + tid; u < c1; u += kLumaPerThread * kThreads) {
         uint32_t f[kLumaPerThread][12];
         int npx[kLumaPerThread];
 #pragma unroll
         for (int q = 0; q < kLumaPerThread; ++q) {
-            const int uu = u + q * kTickThreads;
+            const int uu = u + q * kThreads;
             npx[q] = 0;
             if (uu < c1) {
                 const int y = chunk_row((uint32_t)uu, magic), x0 = (uu - y * cpr) * kChunkPx;
@@ -192,14 +188,14 @@ __device__ __forceinline__ void item_classify(const BatchDev &b, int s, int c0, 
     if (tid == 0) wait_stage(&Y.stage, 1u, b.loop_limit, &D.st->err);
     __syncthreads();
     const uint32_t g = __ldcg(&D.st->gain_p[b.phase]);
-    for (int i = tid; i < 256; i += kTickThreads) table[i] = (uint8_t)corrected_value((uint32_t)i, g);
+    fill_table(table, g);
     __syncthreads();
     const uint64_t once = policy_evict_first();
     const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
     uint32_t *raw = D.raw[b.phase];
     SkinSmem &S = sm.skin[warp];
     // warp-uniform loop, so that chunk pairs can combine with a shuffle
-    for (int base = c0 + (tid & ~31); base < c1; base += kTickThreads) {
+    for (int base = c0 + (tid & ~31); base < c1; base += kThreads) {
         const int u = base + lane;
         uint32_t bits = 0;
         uint32_t f[12];
@@ -237,11 +233,11 @@ template <int HR>
 __device__ __forceinline__ void item_strips_hr(const BatchDev &b, int s, int k0, int k1)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int k = k0 + warp;
+    if (k >= k1) return;   // warp-uniform
     const DevStream &D = b.ds[s];
-    for (int k = k0 + warp; k < k1; k += kTickWarps) {   // warp-uniform
-        const int ty = k / D.strips_x, tx = k - ty * D.strips_x;
-        morph_strip<HR>(D, b.io[s], ty, tx, lane, s, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
-    }
+    const int ty = k / D.strips_x, tx = k - ty * D.strips_x;
+    morph_strip<HR>(D, b.io[s], ty, tx, lane, s, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
 }
 
 __device__ __forceinline__ void item_strips(const BatchDev &b, int s, int k0, int k1)
@@ -265,7 +261,7 @@ __device__ __forceinline__ void item_strips(const BatchDev &b, int s, int k0, in
 // ---------------------------------------------------------------------------
 // the persistent kernel
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTickThreads, kTickCtasPerSm) k_tick(BatchDev b)
+__global__ void __launch_bounds__(kThreads, 3) k_tick(BatchDev b)
 {
     extern __shared__ __align__(16) unsigned char tick_smem[];
     TickSmem &sm = *reinterpret_cast<TickSmem *>(tick_smem);
@@ -310,7 +306,7 @@ int tick_ctas_per_sm(int requested)
         int n = 0;
         if (cudaFuncSetAttribute(k_tick, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(TickSmem)) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick, kTickThreads, sizeof(TickSmem)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tick, kThreads, sizeof(TickSmem)) != cudaSuccess ||
             n < 1) {
             (void)cudaGetLastError();
             n = 1;
@@ -324,7 +320,7 @@ cudaError_t launch_tick(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     const int per = tick_ctas_per_sm(b.luma_ctas_per_sm);
     const int grid = std::max(1, std::min(b.nitems, num_sms * per));
-    k_tick<<<grid, kTickThreads, sizeof(TickSmem), cs>>>(b);
+    k_tick<<<grid, kThreads, sizeof(TickSmem), cs>>>(b);
     return cudaGetLastError();
 }
 
