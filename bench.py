@@ -365,7 +365,16 @@ def run_ours(args) -> None:
         if world > 1:
             dist.barrier()
 
-    # CPU baseline first (spawned processes, no CUDA in them)
+    hmi.load()
+    # ---- serving: 256-stream arrival trace (rank 0 of a 1-GPU run), first of
+    # all, in a fresh process: its latency tails come from host threads ------
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve:
+        serving = bench_serving(hmi, args)
+        torch.cuda.empty_cache()
+
+    # CPU baseline after the serving workload (spawned processes: no CUDA
+    # state of this process reaches them)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool = OraclePool(CFG, synth.num_streams(CFG), host_workers(synth.num_streams(CFG)))
@@ -388,13 +397,6 @@ def run_ours(args) -> None:
         cpu["single"] = {"frames": sum(r["frames"] for r in r1), "px": sum(r["px"] for r in r1),
                          "seconds": sum(r["seconds"] for r in r1)}
 
-    hmi.load()
-    # ---- serving: 256-stream arrival trace (rank 0 of a 1-GPU run), first,
-    # in a fresh process: its latency tails come from host threads ---------
-    serving = None
-    if rank == 0 and world == 1 and not args.no_serve:
-        serving = bench_serving(hmi, args)
-        torch.cuda.empty_cache()
 
     n = synth.num_streams(CFG)
     streams, rings, masks = [], [], []
