@@ -216,10 +216,19 @@ def _addr(x) -> int | None:
 
 
 def _ptr_array(items) -> ctypes.Array:
+    if isinstance(items, ctypes.Array):   # built once by ptr_array and reused
+        return items
     arr = (ctypes.c_void_p * len(items))()
     for i, x in enumerate(items):
         arr[i] = _addr(x)
     return arr
+
+
+def ptr_array(items) -> ctypes.Array:
+    """The C array of buffer addresses that the batch calls take for their
+    frames and masks.  Passing one built once (the buffers must stay alive and
+    in place) saves converting every tensor on every call."""
+    return _ptr_array(list(items))
 
 
 # --------------------------------------------------------------------------- #

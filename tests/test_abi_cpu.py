@@ -137,3 +137,15 @@ def test_autotune_cache_roundtrip(tmp_path, monkeypatch):
     c = autotune.tune(1, shapes, None, "GB300", False, cache_path=path)
     assert not c["cached"] and calls["search"] == 2
     assert a["key"] != c["key"] and autotune.key("GB300", shapes, True) == a["key"]
+
+
+def test_pointer_arrays_built_once_are_passed_through():
+    """A batch call given the array of buffer addresses that ptr_array built
+    uses it as it is; given buffers, it builds the same addresses itself."""
+    import ctypes
+    import numpy as np
+    from paper_1907_04393_gb300 import hmi
+    bufs = [np.zeros(64, np.uint8), np.zeros(32, np.uint8)]
+    arr = hmi.ptr_array(bufs)
+    assert isinstance(arr, ctypes.Array) and hmi._ptr_array(arr) is arr
+    assert list(arr) == [b.ctypes.data for b in bufs] == list(hmi._ptr_array(bufs))
