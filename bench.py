@@ -48,6 +48,8 @@ K2_BYTES_PER_PX = 3 + 6 + 1
 # the band streams' gray and hue tests run inside the classify kernel, so the
 # skin kernel launches only for mixture streams
 K2_KERNELS = ("luma", "classify", "morphology")
+# the one launch of the per-pixel stage in the other tick forms (hmi_tuning.fused)
+FUSED_KERNEL = {1: "k_tick", 2: "k_stage"}
 KERNELS_PER_TICK = 5          # per stream group: luma, classify, morphology, blocks, finish
 # the Gaussian mixture background with its default 3 components: frame 3 B,
 # 12 B of state per component read and written, 1 bit written
@@ -277,7 +279,7 @@ def k2_roofline(per_kernel: dict, ticks: int, px: int, fused: bool, peak: float,
     # raw bits (9.125 B/px); raw bits in, bits and mask bytes out (1.25 B/px)
     per_copy = {} if fused else {k: copy_same_bytes_us(int(bpp * px))
                                  for k, bpp in (("luma", 3.0), ("classify", 9.125), ("morphology", 1.25))}
-    return {"bound": "hbm", "kernels": ["k_tick"] if fused else ["k_luma", "k_classify", "k_morph_strip"],
+    return {"bound": "hbm", "kernels": [FUSED_KERNEL[int(fused)]] if fused else ["k_luma", "k_classify", "k_morph_strip"],
             "achieved": achieved, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
             "frac": achieved / peak, "algorithmic_bytes_per_tick": nbytes,
             "bytes_per_px": K2_BYTES_PER_PX, "stage_ms": ms, "ticks_timed": ticks,
@@ -514,15 +516,16 @@ def run_ours(args) -> None:
     one_chain_ms = r0.elapsed_time(r1) / roof_steps
     prof_ticks, per_kernel = hmi.hmi_batch_profile_kernels(batch)
     model = BG_MODELS[args.bg_model]
-    fused_main = bool(hmi.hmi_batch_get_tuning(batch)["fused"])
+    fused_main = int(hmi.hmi_batch_get_tuning(batch)["fused"])   # 0: the chain
     prof_ms = per_kernel["luma" if fused_main else model["kernel"]]
     hmi.hmi_batch_profile(batch, 0)
 
-    # ---- the other form of the tick (persistent launch or chain), timed the
-    # same way, for the record -------------------------------------------------
+    # ---- the other forms of the tick (chain, persistent launch, cooperative
+    # stage), timed the same way, for the record ------------------------------
     other = None
     if args.bg_model == "band" and world == 1 and not args.no_other_form:
-        other = bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px_per_tick, args, fused_main)
+        other = [bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px_per_tick, args, f)
+                 for f in (0, 1, 2) if f != fused_main]
     hmi.hmi_batch_set_tuning(batch, dict(shape_used, groups=plain_groups))
 
     # ---- end to end through the synchronous API with host buffers --------
@@ -648,14 +651,14 @@ def run_ours(args) -> None:
                         "launch": "hmi_batch_process_async, one CUDA graph per tick"},
         "mpx_per_s": px_per_tick * args.steps * world / (ms / 1e3) / 1e6,
         "roofline": {"bound": "hbm",
-                     "kernel": "k_tick" if fused_main else "k_" + ("classify" if args.bg_model == "band" else "mix<3>"),
+                     "kernel": FUSED_KERNEL[fused_main] if fused_main else "k_" + ("classify" if args.bg_model == "band" else "mix<3>"),
                      "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": (traffic_px * px_per_tick) if traffic_px else None,
                      "algorithmic_bytes_per_launch": roof_bytes_px * px_per_tick,
                      "launch_ms": classify_ms, "launches_timed": prof_ticks,
                      "timed_in": "single-chain pass of the same workload, CUDA events around the "
-                                 f"{'persistent tick' if fused_main else model['kernel']} kernel alone "
+                                 f"{FUSED_KERNEL[fused_main] if fused_main else model['kernel']} kernel alone "
                                  "(no other kernel overlaps it)",
                      "single_chain_ms_per_step": one_chain_ms,
                      "single_chain_kernels_us": {k: v / max(prof_ticks, 1) * 1e3 for k, v in per_kernel.items()}},
@@ -682,7 +685,7 @@ def run_ours(args) -> None:
         line["single_640x480"] = single
         line["single_1920x1080"] = single_hd
     if other is not None:
-        line["other_tick_form"] = other
+        line["other_tick_forms"] = other
     if args.bg_model != "band":
         line["config"]["background"] = dict(MIX_BENCH)
     if relearn is not None:
@@ -720,14 +723,21 @@ SINGLE_CORE_SAMPLE = (0, 8, 16, 24, 32, 40, 48, 60)
 TRACK_BENCH = 64
 
 
-def bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px, args, fused_main) -> dict:
-    """The 64-stream batch with the other form of the tick: the persistent
-    launch (hmi_tuning.fused = 1; its best piece size of a short search) if the
-    main run used the chain of kernels, else the chain.  Pipelined ticks, then
-    a single-chain pass with its per-pixel stage timed by CUDA events."""
+FORM_NAMES = {0: "chain of kernels",
+              1: "persistent tick (one launch for luma, band/gray/hue and morphology items)",
+              2: "cooperative per-pixel stage (one launch, luma / band, gray, hue / morphology "
+                 "phases between grid barriers)"}
+
+
+def bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px, args, form) -> dict:
+    """The 64-stream batch with another form of the tick (hmi_tuning.fused:
+    0 the chain, 1 the persistent launch, 2 the cooperative stage; the best
+    piece size of a short search for the one-launch forms).  Pipelined ticks,
+    then a single-chain pass with its per-pixel stage timed by CUDA events."""
     import torch
     peak, peak_kind = peaks()
-    base = dict(hmi.hmi_batch_get_tuning(batch), groups=1, fused=0 if fused_main else 1)
+    base = dict(hmi.hmi_batch_get_tuning(batch), groups=1, fused=form)
+    fused_main = form == 0
 
     def pipelined(steps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -760,9 +770,8 @@ def bench_other_form(hmi, batch, rings, masks, ptrs, cs, n, px, args, fused_main
                                     cs.cuda_stream, True)
     ticks, per = hmi.hmi_batch_profile_kernels(batch)
     hmi.hmi_batch_profile(batch, 0)
-    fused = bool(best[0]["fused"])
-    return {"form": "persistent tick (one launch for luma, band/gray/hue and morphology items)" if fused
-                    else "chain of kernels",
+    fused = int(best[0]["fused"])
+    return {"form": FORM_NAMES[fused],
             "tuning": best[0], "pipelined_ms_per_step": best[1], "frames_per_s": n / (best[1] / 1e3),
             "k2": k2_roofline(per, ticks, px, fused, peak, peak_kind),
             "single_chain_kernels_us": {k: round(v / max(ticks, 1) * 1e3, 2) for k, v in per.items()}}
@@ -967,7 +976,7 @@ def bench_single(hmi, synth, torch, dev, cs, args, cfg: int = 2) -> dict:
         tick(k)
     ticks, per = hmi.hmi_batch_profile_kernels(b)
     hmi.hmi_batch_profile(b, 0)
-    fused = bool(shape["fused"])
+    fused = int(shape["fused"])
     cls_ms = per["luma" if fused else "classify"] / max(ticks, 1)
     peak, peak_kind = peaks()
     host = [r.cpu().pin_memory() for r in ring]
@@ -986,7 +995,7 @@ def bench_single(hmi, synth, torch, dev, cs, args, cfg: int = 2) -> dict:
     return {"frames_per_s": steps / (ms / 1e3), "mpx_per_s": steps * w * h / (ms / 1e3) / 1e6,
             "ms_per_frame": ms / steps, "tuning": shape,
             "launch": "pipelined graph ticks (results one call later), launch shape autotuned for the stream",
-            "classify": {"kernel": "k_tick" if fused else "k_classify", "launch_us": cls_ms * 1e3,
+            "classify": {"kernel": FUSED_KERNEL[fused] if fused else "k_classify", "launch_us": cls_ms * 1e3,
                          "achieved_GBps": achieved, "frac": achieved / peak,
                          "peak_kind": peak_kind, "bytes_per_px": bpp},
             "k2": k2_roofline(per, ticks, w * h, fused, peak, peak_kind),
@@ -1073,9 +1082,9 @@ def main():
     ap.add_argument("--quality-frames", type=int, default=1200,
                     help="frames of the 1080p drifting scene to compare the background models on (0: skip)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
-    ap.add_argument("--fused", type=int, choices=[-1, 0, 1], default=-1,
-                    help="tick form: 1 the persistent launch, 0 the chain of kernels, -1 the library "
-                         "default (or the autotuner's choice)")
+    ap.add_argument("--fused", type=int, choices=[-1, 0, 1, 2], default=-1,
+                    help="tick form: 1 the persistent launch, 2 the cooperative per-pixel stage, 0 the "
+                         "chain of kernels, -1 the library default (or the autotuner's choice)")
     ap.add_argument("--no-other-form", action="store_true",
                     help="skip timing the other form of the tick")
     ap.add_argument("--mode", choices=["pipelined", "plain"], default="pipelined",

@@ -249,8 +249,11 @@ HMI_API int hmi_batch_process_async(hmi_batch *b, const uint8_t *const *frames, 
  * per-pixel part of its tick (kernels 0, 1, 5 and 6 below) in one persistent
  * launch, whose CTAs take work items from a queue in order (per stream: luma
  * sums, then band / gray / hue tests, then morphology strips), each item
- * waiting (bounded) only for the stream's items of the step before; 0 runs
- * the chain of kernels of HMI_TICK_KERNELS.  queue_lag: queue positions
+ * waiting (bounded) only for the stream's items of the step before; with 2,
+ * such a group (open_iters + close_iters at most 4) runs them in one
+ * cooperative launch of three phases (luma sums; gains and band / gray / hue
+ * tests; morphology strips) separated by grid barriers with bounded waits; 0
+ * runs the chain of kernels of HMI_TICK_KERNELS.  queue_lag: queue positions
  * between a stream's last item of one step and its first of the next
  * (0 = twice the persistent grid, else 1..2^20).  merge_threads: threads of
  * the CTA that merges one stream's block components into its pointer (the
@@ -319,9 +322,10 @@ HMI_API int hmi_batch_flush(hmi_batch *b, void *cuda_stream);
  * hmi_batch_profile_kernels waits for them and gives the number of ticks timed
  * and, for the first n_kernels kernels (1..HMI_TICK_KERNELS), the sum of their
  * durations in milliseconds; hmi_batch_profile_read gives that sum for kernel
- * 1 alone.  With the persistent tick (hmi_tuning.fused), kernel 0 is the
- * whole tick but re-learning (kernels 3 and 4), the other kernels launch
- * nothing, and hmi_batch_profile_read gives kernel 0. */
+ * 1 alone.  With the persistent tick or the cooperative stage
+ * (hmi_tuning.fused 1 or 2), kernel 0 is the whole per-pixel stage (kernels
+ * 0, 1, 5 and 6), kernels 1, 2, 5 and 6 launch nothing, and
+ * hmi_batch_profile_read gives kernel 0. */
 #define HMI_TICK_KERNELS 9
 HMI_API int hmi_batch_profile(hmi_batch *b, int max_ticks);
 HMI_API int hmi_batch_profile_kernels(hmi_batch *b, int *ticks, double *ms, int n_kernels);

@@ -434,8 +434,9 @@ int hmi::plan_build(hmi_batch *b, int ng)
         int max_halo = 0, uniform_halo = 0;
         bool any_mix = false;
         size_t o_c, o_t, o_b, o_s, o_done, o_p, o_ccn[kPhases], o_ccl[kPhases], o_skn[kPhases], o_skl[kPhases];
-        // persistent tick: work queue and per-stream progress
-        bool fused = false;
+        // persistent tick (fused 1): work queue and per-stream progress;
+        // fused 2: the cooperative per-pixel stage
+        int fused = 0;
         std::vector<int4> items;
         std::vector<TickSync> sync;
         size_t o_items = 0, o_sync = 0, o_head = 0;
@@ -467,8 +468,11 @@ int hmi::plan_build(hmi_batch *b, int ng)
                 t.pieces.push_back(make_int4(k, c, std::min(chunks, c + b->tune.piece_chunks), 0));
             if (L.mix_k) t.any_mix = true;
         }
-        t.fused = b->tune.fused && !t.any_mix && t.uniform_halo >= 0 && t.uniform_halo <= kTickMaxHalo;
-        if (t.fused) {
+        const bool band_only = !t.any_mix && t.uniform_halo >= 0;
+        t.fused = (b->tune.fused == 1 && band_only && t.uniform_halo <= kTickMaxHalo)     ? 1
+                  : (b->tune.fused == 2 && band_only && t.uniform_halo <= kStripMaxHalo) ? 2
+                                                                                        : 0;
+        if (t.fused == 1) {
             std::vector<int> ch(m), sp(m);
             for (int k = 0; k < m; ++k) {
                 const Layout &L = b->s[perm[b->groups[g].off + k]]->L;
@@ -526,7 +530,7 @@ int hmi::plan_build(hmi_batch *b, int ng)
              cudaMemcpyAsync(A + t.o_b, t.bpre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
              cudaMemcpyAsync(A + t.o_s, t.spre.data(), sizeof(uint32_t) * (m + 1), cudaMemcpyHostToDevice, up) == cudaSuccess &&
              cudaMemcpyAsync(A + t.o_p, t.pieces.data(), sizeof(int4) * t.pieces.size(), cudaMemcpyHostToDevice, up) == cudaSuccess &&
-             (!t.fused ||
+             (t.fused != 1 ||
               (cudaMemcpyAsync(A + t.o_items, t.items.data(), sizeof(int4) * t.items.size(), cudaMemcpyHostToDevice, up) == cudaSuccess &&
                cudaMemcpyAsync(A + t.o_sync, t.sync.data(), sizeof(TickSync) * m, cudaMemcpyHostToDevice, up) == cudaSuccess)) &&
              (G.cs || cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) == cudaSuccess) &&
@@ -568,12 +572,13 @@ int hmi::plan_build(hmi_batch *b, int ng)
             if (sk->L.mix_k) bd.any_mix |= 1 << sk->L.mix_k;
             else bd.any_band = 1;
         }
-        bd.fused = t.fused ? 1 : 0;
-        bd.items = t.fused ? reinterpret_cast<const int4 *>(A + t.o_items) : nullptr;
-        bd.nitems = t.fused ? (int)t.items.size() : 0;
-        bd.sync = t.fused ? reinterpret_cast<TickSync *>(A + t.o_sync) : nullptr;
-        bd.tick_head = t.fused ? reinterpret_cast<uint32_t *>(A + t.o_head) : nullptr;
-        bd.tick_exit = t.fused ? bd.tick_head + 1 : nullptr;
+        bd.fused = t.fused;
+        const bool queue = t.fused == 1;
+        bd.items = queue ? reinterpret_cast<const int4 *>(A + t.o_items) : nullptr;
+        bd.nitems = queue ? (int)t.items.size() : 0;
+        bd.sync = queue ? reinterpret_cast<TickSync *>(A + t.o_sync) : nullptr;
+        bd.tick_head = queue ? reinterpret_cast<uint32_t *>(A + t.o_head) : nullptr;
+        bd.tick_exit = queue ? bd.tick_head + 1 : nullptr;
         bd.loop_limit = b->loop_limit ? b->loop_limit : kLoopLimit;
         bd.merge_threads = b->tune.merge_threads ? b->tune.merge_threads : 512;
         bd.luma_ctas_per_sm = b->tune.luma_ctas_per_sm;

@@ -351,6 +351,207 @@ __global__ void __launch_bounds__(kStripWarps * 32, 5) k_morph_strip(BatchDev b)
     morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
 }
 
+// ---------------------------------------------------------------------------
+// k_stage (hmi_tuning.fused = 2): the per-pixel stage of a tick in one
+// cooperative launch, whose CTAs are all resident at once: the luma sums of
+// every piece, a grid barrier, the gain (each CTA forms it from the stream's
+// complete sum) with the band, gray and hue tests of every piece, a second
+// grid barrier, then the morphology strips.  Three phases in one launch
+// instead of three launches: one ramp and one tail, which is what dominates
+// a tick of one small stream.  Frame and raw-bit reads after a barrier go
+// through L2 (other CTAs of the launch wrote them).  Every barrier wait is
+// bounded (by kLoopLimit steps, not by a plan's lowered loop limit: a barrier
+// that let CTAs through early would leave a stream's luma sum to the next
+// tick); a wait that runs out flags the batch's error word and goes on.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kErrStageWait = 16u;
+
+__device__ __forceinline__ void load48_l2(const uint8_t *src, uint64_t pol, uint32_t (&w)[12])
+{
+    const uint4 *q = reinterpret_cast<const uint4 *>(src);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        uint4 r;
+        asm volatile("ld.global.cg.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                     : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                     : "l"(q + k), "l"(pol));
+        w[4 * k] = r.x; w[4 * k + 1] = r.y; w[4 * k + 2] = r.z; w[4 * k + 3] = r.w;
+    }
+}
+
+// Every CTA of the launch arrives; thread 0 then waits (bounded) until
+// `target` arrivals are counted at *ctr.
+__device__ __forceinline__ void stage_barrier(uint32_t *ctr, uint32_t target, uint32_t limit, uint32_t *err)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        for (uint32_t it = 0;; ++it) {
+            uint32_t v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (it >= limit) {
+                atomicOr(err, kErrStageWait);
+                break;
+            }
+            __nanosleep(it < 16 ? 32 : 128);
+        }
+    }
+    __syncthreads();
+}
+
+// Q16 gain of a stream from its complete luma sum (the luma pass's formula).
+__device__ __forceinline__ uint32_t stream_gain(const DevStream &D)
+{
+    const unsigned long long sy = __ldcg(&D.st->sy);
+    const unsigned long long syref = D.st->syref;
+    unsigned long long g = (sy == 0) ? 65536ull : ((syref << 16) + sy / 2) / sy;
+    if (g < D.gain_min) g = D.gain_min;
+    if (g > D.gain_max) g = D.gain_max;
+    return (uint32_t)g;
+}
+
+template <int HR>
+__global__ void __launch_bounds__(kThreads, 2) k_stage(BatchDev b)
+{
+    __shared__ unsigned long long red[kThreads / 32];
+    __shared__ uint8_t table[256];
+    __shared__ SkinSmem skin[kThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t pol = policy_evict_first();
+    const uint32_t limit = kLoopLimit;
+
+    // 1. luma sums, a piece at a time
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        if (io.frame == nullptr) continue;   // CTA-uniform
+        const int w = D.w, cpr = 2 * D.nwords;
+        unsigned long long acc = 0;
+        for (int u = piece.y + tid; u < piece.z; u += kLumaChunks * kThreads) {
+            uint32_t f[kLumaChunks][12];
+            int npx[kLumaChunks];
+#pragma unroll
+            for (int q = 0; q < kLumaChunks; ++q) {
+                const int uu = u + q * kThreads;
+                npx[q] = 0;
+                if (uu < piece.z) {
+                    const int y = chunk_row((uint32_t)uu, D.cpr_magic), x0 = (uu - y * cpr) * kChunkPx;
+                    if (x0 < w && HMI_IN_BOUNDS(y < D.h && 3LL * (x0 + kChunkPx) <= io.frame_pitch, &D.st->err)) {
+                        npx[q] = min(kChunkPx, w - x0);
+                        if (io.src) {   // a pinned host frame: w is a multiple of 16, rows dense
+                            load48_host(io.src + (long long)y * 3 * w + 3 * x0, f[q]);
+                            store48(const_cast<uint8_t *>(io.frame) + (long long)y * io.frame_pitch + 3 * x0, f[q]);
+                        } else {
+                            load48(io.frame + (long long)y * io.frame_pitch + 3 * x0, pol, f[q]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kLumaChunks; ++q)
+                if (npx[q] > 0) acc += (npx[q] == kChunkPx) ? luma_sum16(f[q]) : luma_sum_n(f[q], npx[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) red[warp] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long t = 0;
+            for (int i = 0; i < kThreads / 32; ++i) t += red[i];
+            atomicAdd(&D.st->sy, t);
+        }
+        __syncthreads();
+    }
+    stage_barrier(b.done + 2, gridDim.x, limit, b.err);
+
+    // 2. gain, band test, gray and hue tests, AND: raw mask bits
+    for (int pc = blockIdx.x; pc < b.npieces; pc += gridDim.x) {
+        const int4 piece = b.pieces[pc];
+        const DevStream &D = b.ds[piece.x];
+        const TickIO io = b.io[piece.x];
+        if (io.frame == nullptr) continue;   // CTA-uniform
+        const uint32_t g = stream_gain(D);
+        __syncthreads();   // the previous piece is done with the table
+        fill_table(table, g);
+        __syncthreads();
+        const int w = D.w, cpr = 2 * D.nwords, fpitch = D.fpitch;
+        uint32_t *raw = D.raw[b.phase];
+        for (int base = piece.y + (tid & ~31); base < piece.z; base += kThreads) {   // warp-uniform
+            const int u = base + lane;
+            uint32_t bits = 0;
+            uint32_t f[12];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) f[k] = 0u;
+            int y = 0, j = 0;
+            if (u < piece.z) {
+                y = chunk_row((uint32_t)u, D.cpr_magic);
+                j = u - y * cpr;
+                const int x0 = j * kChunkPx;
+                if (x0 < w && HMI_IN_BOUNDS(y < D.h && 3LL * (x0 + kChunkPx) <= io.frame_pitch &&
+                                                3 * (x0 + kChunkPx) <= fpitch, &D.st->err)) {
+                    uint32_t l[12], h[12];
+                    load48_l2(io.frame + (long long)y * io.frame_pitch + 3 * x0, pol, f);
+                    load48(D.lo + (long long)y * fpitch + 3 * x0, pol, l);
+                    load48(D.hi + (long long)y * fpitch + 3 * x0, pol, h);
+                    bits = band_outside16(f, l, h, TableCorr{table});
+                    const int npx = w - x0;
+                    if (npx < kChunkPx) bits &= (1u << npx) - 1u;
+                }
+            }
+            bits &= ~skin_fail_warp(bits, f, D, table, skin[warp], lane);
+            const uint32_t other = __shfl_xor_sync(kFull, bits, 1);
+            if (u < piece.z && (u & 1) == 0 &&
+                HMI_IN_BOUNDS(y < D.bh * kBlock && (j >> 1) < D.nwords, &D.st->err))
+                raw[(long long)y * D.nwords + (j >> 1)] = bits | (other << 16);
+        }
+    }
+    stage_barrier(b.done + 2, 2u * gridDim.x, limit, b.err);
+
+    // every luma sum has been read: the gains into the streams' state
+    if (blockIdx.x == 0) {
+        for (int s = tid; s < b.n; s += kThreads) {
+            if (b.io[s].frame == nullptr) continue;
+            const DevStream &D = b.ds[s];
+            StreamState *st = D.st;
+            const uint32_t g = stream_gain(D);
+            st->gain = g;
+            st->gain_p[b.phase] = g;
+            st->sy = 0;
+            st->lframes += 1;
+            st->lframe_p[b.phase] = st->lframes;
+        }
+    }
+
+    // 3. opening and closing of the raw bits, strip by strip (a warp each)
+    for (uint32_t strip = blockIdx.x * (kThreads / 32) + warp; strip < b.total_strips;
+         strip += gridDim.x * (kThreads / 32)) {   // warp-uniform
+        int lo = 0, hi = b.n;                   // largest s with strip_prefix[s] <= strip
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (b.strip_prefix[mid] <= strip) lo = mid; else hi = mid;
+        }
+        const DevStream &D = b.ds[lo];
+        const TickIO io = b.io[lo];
+        if (io.frame == nullptr) continue;
+        const int ls = (int)(strip - b.strip_prefix[lo]);
+        const int ty = ls / D.strips_x, tx = ls - ty * D.strips_x;
+        morph_strip<HR>(D, io, ty, tx, lane, lo, b.cc_count, b.cc_list, b.total_blocks, D.raw[b.phase]);
+    }
+
+    // the last CTA out resets the barrier counter for the next tick
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(b.done + 3, 1u) == gridDim.x - 1u) {
+            b.done[2] = 0u;
+            b.done[3] = 0u;
+        }
+    }
+}
+
 // k_block_cc: one warp per listed non-empty 32x32 block (any stream of the
 // batch): its 8-connected components and their statistics; its flag is
 // cleared for the next tick.
@@ -586,6 +787,41 @@ cudaError_t launch_morph(const BatchDev &b, cudaStream_t cs, int num_sms)
     return cudaGetLastError();
 }
 
+// The cooperative per-pixel stage: as many CTAs as are resident at once (or
+// as there are pieces or strip groups, if fewer), launched so that the CUDA
+// driver guarantees they all run together.
+template <int HR>
+static cudaError_t launch_stage_hr(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    static int fit[64];
+    const int per_fit = resident_ctas(k_stage<HR>, kThreads, fit);
+    const int per = b.luma_ctas_per_sm > 0 ? std::min(b.luma_ctas_per_sm, per_fit) : per_fit;
+    const long long work = std::max<long long>(b.npieces, ((long long)b.total_strips + 7) / 8);
+    const int grid = (int)std::max<long long>(1, std::min<long long>((long long)num_sms * per, work));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = cs;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_stage<HR>, b);
+}
+
+static cudaError_t launch_stage(const BatchDev &b, cudaStream_t cs, int num_sms)
+{
+    switch (b.uniform_halo) {   // the plan keeps this form to halos of the strip path
+    case 0: return launch_stage_hr<0>(b, cs, num_sms);
+    case 2: return launch_stage_hr<2>(b, cs, num_sms);
+    case 4: return launch_stage_hr<4>(b, cs, num_sms);
+    case 6: return launch_stage_hr<6>(b, cs, num_sms);
+    default: return launch_stage_hr<8>(b, cs, num_sms);
+    }
+}
+
 cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 {
     if (!strip_path(b)) return cudaSuccess;   // k_morph_cc labels its blocks itself
@@ -597,6 +833,16 @@ cudaError_t launch_block_cc(const BatchDev &b, cudaStream_t cs, int num_sms)
 
 cudaError_t launch_tick_kernel(int k, const BatchDev &b, cudaStream_t cs, int num_sms)
 {
+    if (b.fused == 2) {   // one cooperative launch does kernels 0, 1, 5 and 6
+        switch (k) {
+        case 0: return launch_stage(b, cs, num_sms);
+        case 3: return launch_relearn(b, cs, num_sms);
+        case 4: return launch_relearn_band(b, cs, num_sms);
+        case 7: return launch_block_cc(b, cs, num_sms);
+        case 8: return launch_finish(b, cs);
+        default: return cudaSuccess;
+        }
+    }
     if (b.fused) {   // one persistent launch does the per-pixel work of kernels 0, 1, 5 and 6
         switch (k) {
         case 0: return launch_tick(b, cs, num_sms);

@@ -201,7 +201,8 @@ struct BatchDev {
     int any_mix;                              // bit K: some stream has a K-component mixture
     uint32_t loop_limit;                      // steps of every bounded device loop (0: kLoopLimit)
     int merge_threads;                        // threads of a stream's merge CTA (256, 512, 1024)
-    // persistent tick (fused != 0): the whole path of the group in one launch
+    // tick form of the per-pixel kernels: 0 the chain, 1 the persistent tick
+    // (queue below), 2 the cooperative per-pixel stage (counters done[2..3])
     int fused;
     const int4 *items;                        // work queue, in order
     int nitems;

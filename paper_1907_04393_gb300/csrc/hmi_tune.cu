@@ -2,9 +2,10 @@
 // with a new shape, and the autotuner, which times whole ticks of the caller's
 // frames for each candidate shape on the plan's own streams (stream state
 // saved and restored around the search) and keeps the fastest.  The axes are
-// the persistent tick or the chain of kernels, the piece size of the
-// per-pixel kernels, CTAs per SM of the luma, skin and block kernels, the
-// threads of a stream's merge CTA, and the pipeline depth or stream groups.
+// the tick form (the chain of kernels, the persistent tick or the cooperative
+// per-pixel stage), the piece size of the per-pixel kernels, CTAs per SM of
+// the luma, skin and block kernels, the threads of a stream's merge CTA, and
+// the pipeline depth or stream groups.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,7 +21,7 @@ bool hmi::tuning_ok(const hmi_tuning &t)
            t.luma_ctas_per_sm >= 0 && t.luma_ctas_per_sm <= 32 && t.skin_ctas_per_sm >= 1 &&
            t.skin_ctas_per_sm <= 32 && t.cc_ctas_per_sm >= 1 && t.cc_ctas_per_sm <= 32 &&
            t.groups >= 0 && t.groups <= 64 && t.pipeline_depth >= 2 && t.pipeline_depth <= kPhases &&
-           (t.fused == 0 || t.fused == 1) && t.queue_lag >= 0 && t.queue_lag <= (1 << 20) &&
+           (t.fused >= 0 && t.fused <= 2) && t.queue_lag >= 0 && t.queue_lag <= (1 << 20) &&
            (t.merge_threads == 0 || t.merge_threads == 256 || t.merge_threads == 512 ||
             t.merge_threads == 1024);
 }
@@ -41,7 +42,9 @@ int hmi::batch_retune(hmi_batch *b, const hmi_tuning &t)
 
 // Microseconds per tick of `ticks` ticks of `frames` with the current plan
 // (pipelined or plain graph ticks on the batch's own stream, masks and
-// pointers not written), after three untimed ticks.
+// pointers not written), after untimed ticks that build the graph of every
+// per-tick slot (a slot's graph is made on its first use; timing that would
+// rank shapes by graph instantiation, not by their ticks).
 namespace {
 
 int time_ticks(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipelined, double *us)
@@ -50,7 +53,7 @@ int time_ticks(hmi_batch *b, const uint8_t *const *frames, int ticks, bool pipel
         return pipelined ? batch_pipelined(b, frames, nullptr, nullptr, b->cs, 1)
                          : batch_async(b, frames, nullptr, nullptr, b->cs, 1);
     };
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < kRing + 3; ++i) {
         const int st = one();
         if (st != HMI_OK) return st;
     }
@@ -126,7 +129,7 @@ int hmi::batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, b
         int32_t hmi_tuning::*field;
         std::vector<int32_t> values;
     };
-    std::vector<Axis> axes = {{&hmi_tuning::fused, {0, 1}},
+    std::vector<Axis> axes = {{&hmi_tuning::fused, {0, 1, 2}},
                               {&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
                               {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
                               {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},

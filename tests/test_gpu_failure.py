@@ -21,7 +21,7 @@ def _ptr_dict(ptrs, i=0):
     return dict(zip(ptrs.dtype.names, [x.item() for x in ptrs[i]]))
 
 
-@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("fused", [1, 0, 2])
 def test_loop_bound_runs_out_then_stream_recovers(fused):
     w, h = synth.shape(1)
     lf = synth.learn_frames(1)

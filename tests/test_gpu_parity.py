@@ -275,7 +275,7 @@ def _compare_batch(gs, os_, frames, masks_g, ptrs_g, what):
         assert_pointer(ptrs_g[i], p_o, f"{what} stream {i}")
 
 
-@pytest.mark.parametrize("fused", [1, 0])
+@pytest.mark.parametrize("fused", [1, 0, 2])
 def test_batch_config4_sync_async_graph(fused):
     """64 mixed-resolution streams in one launch per tick (the persistent tick)
     or one launch per stage (the chain of kernels); each stream's result
@@ -542,7 +542,7 @@ def test_checkpoint_roundtrip():
     b.close()
 
 
-@pytest.mark.parametrize("fused", [0, 1])
+@pytest.mark.parametrize("fused", [0, 1, 2])
 def test_profile_counts_classification_kernel(fused):
     w, h = synth.shape(3)
     g = hmi.Stream(w, h)
@@ -558,9 +558,9 @@ def test_profile_counts_classification_kernel(fused):
     ticks, ms = hmi.hmi_batch_profile_read(b)
     assert ticks == 5 and 0 < ms / ticks < 5.0
     t2, per = hmi.hmi_batch_profile_kernels(b)
-    if fused:   # one persistent launch: the first kernel is the whole tick
+    if fused:   # one launch for the per-pixel stage: the first kernel is all of it
         assert t2 == 5 and per["luma"] == pytest.approx(ms)
-        assert all(v < per["luma"] for k, v in per.items() if k != "luma")
+        assert all(per[k] < per["luma"] for k in ("classify", "skin", "morphology"))
     else:
         assert t2 == 5 and per["classify"] == pytest.approx(ms)
         assert all(v > 0 for k, v in per.items()
@@ -643,7 +643,9 @@ def test_tuning_does_not_change_results():
         for shape in ({"piece_chunks": 64, "luma_ctas_per_sm": 1, "fused": 1, "queue_lag": 3,
                        "merge_threads": 256, "groups": 1},
                       {"piece_chunks": 2048, "fused": 1, "queue_lag": 1 << 20, "merge_threads": 1024,
-                       "groups": 2}):
+                       "groups": 2},
+                      {"piece_chunks": 96, "luma_ctas_per_sm": 1, "fused": 2, "groups": 1},
+                      {"piece_chunks": 4096, "fused": 2, "groups": 2}):
             hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), **shape))
             for t in range(2, 4):
                 frames = [synth.run_frame(4, i, t) for i in idx]
@@ -654,7 +656,7 @@ def test_tuning_does_not_change_results():
                 _compare_batch(gs, os_, frames, masks, plist, f"persistent {shape} t={t}")
         for bad in ({"piece_chunks": 100}, {"piece_chunks": 0}, {"skin_ctas_per_sm": 0},
                     {"cc_ctas_per_sm": 33}, {"luma_ctas_per_sm": -1}, {"groups": 65},
-                    {"pipeline_depth": 1}, {"pipeline_depth": 4}, {"fused": 2},
+                    {"pipeline_depth": 1}, {"pipeline_depth": 4}, {"fused": 3}, {"fused": -1},
                     {"queue_lag": -1}, {"queue_lag": (1 << 20) + 1}, {"merge_threads": 384}):
             t = dict(hmi.hmi_batch_get_tuning(b), **bad)
             with pytest.raises(hmi.HmiError) as e:
@@ -884,9 +886,9 @@ def test_interface_events_match_oracle():
 # --------------------------------------------------------------------------- #
 # The persistent tick (hmi_tuning.fused = 1) against the oracle                #
 # --------------------------------------------------------------------------- #
-def _fused_batch(gs, **over):
+def _fused_batch(gs, fused=1, **over):
     b = hmi.hmi_batch_create([g.handle for g in gs])
-    hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=1, groups=1, **over))
+    hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=fused, groups=1, **over))
     return b
 
 
@@ -906,15 +908,17 @@ def _batch_step(b, gs, frames, host=False):
     return [m.cpu().numpy() for m in dmasks], [dict(zip(arr.dtype.names, [x.item() for x in arr[i]])) for i in range(n)]
 
 
+@pytest.mark.parametrize("fused", [1, 2])
 @pytest.mark.parametrize("cfg,frames,piece", [(1, range(0, 60, 3), 64), (2, range(0, 300, 15), 512),
                                               (3, range(0, 600, 100), 1024)])
-def test_persistent_tick_single_stream_configs(cfg, frames, piece):
+def test_persistent_tick_single_stream_configs(cfg, frames, piece, fused):
     """Single streams of the three plain configurations, one stream per
-    persistent launch (every classify item waits for the stream's gain)."""
+    persistent launch (every classify item waits for the stream's gain) or
+    per cooperative launch (every band test waits at the grid barrier)."""
     w, h = synth.shape(cfg)
     g, o = pair(w, h)
     learn_both(g, o, synth.learn_frames(cfg), dev=True)
-    b = _fused_batch([g], piece_chunks=piece)
+    b = _fused_batch([g], fused=fused, piece_chunks=piece)
     try:
         for t in frames:
             fr = synth.run_frame(cfg, 0, t)
@@ -929,10 +933,12 @@ def test_persistent_tick_single_stream_configs(cfg, frames, piece):
         g.close()
 
 
-def test_persistent_tick_ragged_sizes_pinned_and_pipelined():
+@pytest.mark.parametrize("fused", [1, 2])
+def test_persistent_tick_ragged_sizes_pinned_and_pipelined(fused):
     """Ragged frame sizes (rows not a multiple of 16 or 32 pixels, tiny
-    frames) in one persistent launch, then the 16-aligned ones from pinned host
-    frames (copied into staging by the luma items) in pipelined calls."""
+    frames) in one persistent (or cooperative) launch, then the 16-aligned
+    ones from pinned host frames (copied into staging by the luma pass) in
+    pipelined calls."""
     shapes = [(1, 1), (17, 5), (33, 33), (100, 75), (321, 241), (64, 48), (320, 240), (160, 96)]
     gs, os_ = [], []
     for w, h in shapes:
@@ -941,7 +947,7 @@ def test_persistent_tick_ragged_sizes_pinned_and_pipelined():
         learn_both(g, o, lf, dev=True)
         gs.append(g)
         os_.append(o)
-    b = _fused_batch(gs, piece_chunks=32, queue_lag=7)
+    b = _fused_batch(gs, fused=fused, piece_chunks=32, queue_lag=7)
     try:
         for t in range(3):
             frames = [RNG.integers(0, 256, size=(g.h, g.w, 3), dtype=np.uint8) for g in gs]
@@ -955,7 +961,7 @@ def test_persistent_tick_ragged_sizes_pinned_and_pipelined():
         hmi.hmi_batch_destroy(b)
     sel = [i for i, (w, h) in enumerate(shapes) if w % 16 == 0]
     ga, oa = [gs[i] for i in sel], [os_[i] for i in sel]
-    b = _fused_batch(ga, pipeline_depth=2)
+    b = _fused_batch(ga, fused=fused, pipeline_depth=2)
     try:
         s = torch.cuda.current_stream().cuda_stream
         dmasks = [torch.empty((g.h, g.w), dtype=torch.uint8, device="cuda") for g in ga]
