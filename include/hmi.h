@@ -278,11 +278,12 @@ HMI_API int hmi_batch_get_tuning(const hmi_batch *b, hmi_tuning *t);
 
 /* Search the launch shape (Sec. 3.3: the GPU computation is autotuned):
  * time `ticks` ticks (2..10000) of frames (device memory, one per stream) for
- * each candidate, changing one parameter at a time (the tick form, the piece
- * size, the luma, skin and block-component grids and the merge CTA size,
- * then the pipeline depth for pipelined
- * ticks or the group count for plain ticks), keep the fastest, apply it and return it in *best with its time per
- * tick in microseconds (either may be NULL).  pipelined != 0 times pipelined
+ * each candidate (after untimed ticks that build every per-tick graph): the
+ * tick form and the piece size together, then one parameter at a time (the
+ * luma, skin and block-component grids, the merge CTA size, then the pipeline
+ * depth for pipelined ticks or the group count for plain ticks); keep the
+ * fastest, apply it and return it in *best with its time per tick in
+ * microseconds (either may be NULL).  pipelined != 0 times pipelined
  * ticks (one group), else plain graph ticks.  The streams' click state and
  * pointer history are restored afterwards; their last labels are those of the
  * last tuning tick. */

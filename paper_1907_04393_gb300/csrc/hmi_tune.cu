@@ -5,7 +5,8 @@
 // the tick form (the chain of kernels, the persistent tick or the cooperative
 // per-pixel stage), the piece size of the per-pixel kernels, CTAs per SM of
 // the luma, skin and block kernels, the threads of a stream's merge CTA, and
-// the pipeline depth or stream groups.
+// the pipeline depth or stream groups; the form and the piece size are
+// searched together, the others one at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -124,14 +125,30 @@ int hmi::batch_autotune(hmi_batch *b, const uint8_t *const *frames, int ticks, b
     double cur_us = 0.0;
     st = batch_retune(b, cur);
     if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &cur_us);
-    // one parameter at a time, each over its candidate values
+    // the tick form and the piece size together (each form has its own best
+    // piece size: a form ranked at another form's piece size can lose to it
+    // there and win at its own), then the other parameters one at a time
+    const hmi_tuning base = cur;
+    for (int32_t f : {0, 1, 2}) {
+        for (int32_t p : {128, 256, 512, 1024, 2048}) {
+            if (st != HMI_OK || (f == cur.fused && p == cur.piece_chunks)) continue;
+            hmi_tuning cand = base;
+            cand.fused = f;
+            cand.piece_chunks = p;
+            double us = 0.0;
+            st = batch_retune(b, cand);
+            if (st == HMI_OK) st = time_ticks(b, frames, ticks, pipelined, &us);
+            if (st == HMI_OK && us < cur_us) {
+                cur = cand;
+                cur_us = us;
+            }
+        }
+    }
     struct Axis {
         int32_t hmi_tuning::*field;
         std::vector<int32_t> values;
     };
-    std::vector<Axis> axes = {{&hmi_tuning::fused, {0, 1, 2}},
-                              {&hmi_tuning::piece_chunks, {128, 256, 512, 1024, 2048}},
-                              {&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
+    std::vector<Axis> axes = {{&hmi_tuning::luma_ctas_per_sm, {0, 2, 3, 4, 6}},
                               {&hmi_tuning::skin_ctas_per_sm, {4, 8, 16}},
                               {&hmi_tuning::cc_ctas_per_sm, {4, 8, 16}},
                               {&hmi_tuning::merge_threads, {256, 512, 1024}}};
