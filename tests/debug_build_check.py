@@ -1,6 +1,6 @@
 """Run by tests/test_gpu_debug_build.py in a child process with
 HMI_DEBUG_BUILD=1: the bounds-checked build of the library on tiny and ragged
-frames through the per-frame path and both forms of a batch tick, against the
+frames through the per-frame path and the three forms of a batch tick, against the
 CPU oracle, with guard bands around every output buffer (host and device)
 that must come back untouched.  A failed bounds check in a kernel surfaces as
 HMI_ERR_DEVICE (an exception here).  Prints "ok"."""
@@ -63,10 +63,10 @@ def main():
             p = pview.view(hmi.POINTER_DTYPE)[0]
             assert int(p["area"]) == p_o["area"] and int(p["label"]) == p_o["label"]
             assert guards_intact(mbuf) and guards_intact(pbuf) and guards_intact(lbuf)
-    # both forms of a batch tick, device buffers with guard bands
+    # the three forms of a batch tick, device buffers with guard bands
     b = hmi.hmi_batch_create([g.handle for g, _ in pairs])
     try:
-        for fused in (0, 1):
+        for fused in (0, 1, 2):
             hmi.hmi_batch_set_tuning(b, dict(hmi.hmi_batch_get_tuning(b), fused=fused, groups=0,
                                              piece_chunks=32))
             frames = [rng.integers(0, 256, size=(g.h, g.w, 3), dtype=np.uint8) for g, _ in pairs]
