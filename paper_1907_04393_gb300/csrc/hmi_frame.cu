@@ -14,6 +14,9 @@
 //   k_block_cc    8-connected components of each listed block with their
 //                 statistics (Mouse module, Sec. 2)
 //   k_morph_cc    generic form of the last two for mixed morphology settings
+//   k_stage       k_luma, k_classify and k_morph_strip as the three phases of
+//                 one cooperative launch, separated by grid barriers (the
+//                 same Sec. 2, 3.1 and 3.2 steps, one launch ramp and tail)
 // All are integer/bit work, bound by HBM bandwidth, issue rate or latency;
 // nothing here is a dense contraction, so no tensor-core path is used.
 #include <algorithm>
